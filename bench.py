@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark: batched TaylorF2 lnL evaluations per second on one GB300 (or N, weak scaling).
+
+Workload (one step): one gwl_loglike call over a batch of 8192 proposals for
+a 3-detector, 8 s, 20-1024 Hz network (8033 bins per detector, coloured
+Gaussian noise, 11-D aligned-spin BBH injection at SNR 15-30); half the
+proposals are prior draws and half perturb the injection.  Inputs are
+synthetic and seeded; the injection is produced by the device library's own
+template (gwl_waveform), so the GPU leg runs no oracle code.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gwl|reference]
+
+Prints one JSON line (rank 0).  ``value`` is the mixed-precision path's
+device-timed throughput with inputs resident in HBM; L2 (129 MB) is flushed
+by writing a 256 MB buffer between timed steps (the step inputs are < 1 MB).
+``e2e`` is the same metric through gwl_loglike_host (host buffers, copies in
+the timed region).  ``roofline`` refers to the dominant kernel (the windowed
+bin loop), timed by the library's CUDA events on the launch stream.
+``cpu_baseline`` times the FP64 oracle on the host cores on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1909_11873_gb300 import inputs as I  # noqa: E402
+
+METRIC = "lnL evals/s (BBH 3-det 8s, 11-D)"
+CONFIG = "c2"
+BATCH = 8192
+SEED = 2
+# Algorithmic FP32 operations per in-band (proposal, bin) of the mixed path
+# with 3 detectors (flops, FMA = 2): float-float common phase 112, per detector
+# 27 (phase completion, reduction to [-1/2, 1/2], argument scaling, 4 FMA of
+# the accumulation) -> 112 + 3 * 27 = 193; plus 6 MUFU sin/cos (separate pipe).
+FLOPS_PER_BIN_MIXED = 193
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gwl", choices=["gwl", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def device_event(ctx, precision):
+    """The benchmark event, with the injection made by the device library (no oracle on this leg)."""
+    from paper_1909_11873_gb300 import gwl
+    import torch
+
+    cache = {}
+
+    def zero_ctx(ev):
+        key = id(ev.geom)
+        if key not in cache:
+            full = I.Sampling(np.arange(11, dtype=np.int32), np.zeros(11), np.zeros(11, dtype=np.int32),
+                              np.zeros(11), np.ones(11), np.zeros(11, dtype=np.int32))
+            cache[key] = gwl.Context(ev.freqs, np.zeros_like(ev.strain), ev.psd, ev.geom, gwl.GWL_FP64, ev.fcut_mode,
+                                     ev.gmst, ev.t_ref, full)
+        return cache[key]
+
+    def waveform(ev, th):
+        c = zero_ctx(ev)
+        h = gwl.waveform(c, torch.from_numpy(np.ascontiguousarray(th[None])).cuda()).cpu().numpy()[0]
+        return h[..., 0] + 1j * h[..., 1]
+
+    def snr2(ev, th):
+        c = zero_ctx(ev)
+        return -2.0 * float(gwl.loglike(c, torch.from_numpy(np.ascontiguousarray(th[None])).cuda()).cpu()[0])
+
+    ev = I.make_event(CONFIG, SEED, waveform, snr2)
+    for c in cache.values():
+        c.close()
+    return ev
+
+
+def run_gwl(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1909_11873_gb300 import build, gwl
+
+    if not os.path.exists(gwl.LIB_PATH):
+        build.build()
+    ev = device_event(None, None)
+    theta_full = I.proposals(ev, BATCH, SEED + 1000 * rank)
+    theta_np = np.ascontiguousarray(I.reduced(theta_full, ev.sampling))
+    theta = torch.from_numpy(theta_np).cuda()
+    lnl = torch.empty(BATCH, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(ctx, steps, warmup, host=False):
+        pin_t = torch.from_numpy(theta_np).pin_memory() if host else None
+        pin_l = torch.empty(BATCH, dtype=torch.float64).pin_memory() if host else None
+        for _ in range(warmup):
+            if host:
+                ctx.gwl_loglike_host(pin_t.numpy(), pin_l.numpy(), stream)
+            else:
+                ctx.gwl_loglike(theta, lnl, stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        l0 = ctx.launch_count()
+        wall0 = time.perf_counter()
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record(stream)
+            if host:
+                ctx.gwl_loglike_host(pin_t.numpy(), pin_l.numpy(), stream)
+            else:
+                ctx.gwl_loglike(theta, lnl, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if world > 1:
+            torch.distributed.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return sum(ms) / len(ms), ctx.launch_count() - l0, wall
+
+    results = {}
+    ctxs = {}
+    for prec in (gwl.GWL_FP64, gwl.GWL_MIXED):
+        ctx = gwl.Context.from_event(ev, prec)
+        ctxs[prec] = ctx
+        steps = args.steps if prec == gwl.GWL_MIXED else max(3, args.steps // 5)
+        with ClockSampler(local) as clk:
+            ms, launches, wall = timed(ctx, steps, args.warmup)
+        ctx.gwl_sync()
+        results[prec] = dict(ms=ms, launches=launches, clocks=clk.summary(), steps=steps, wall=wall)
+
+    mixed = ctxs[gwl.GWL_MIXED]
+    # dominant kernel timing (library CUDA events on the launch stream) over a separate timed pass
+    mixed.gwl_profile(True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        mixed.gwl_loglike(theta, lnl, stream)
+    torch.cuda.synchronize()
+    prof = {k: mixed.gwl_profile_read(k) for k in (gwl.KERNEL_PROLOGUE, gwl.KERNEL_BINS, gwl.KERNEL_COMBINE)}
+    mixed.gwl_profile(False)
+
+    # end-to-end with host buffers
+    ms_e2e, _, _ = timed(mixed, max(5, args.steps // 2), args.warmup, host=True)
+
+    # algorithmic work of one launch: in-band (proposal, bin) pairs (ncut from the prologue's f_ISCO)
+    eta = theta_full[:, 1] / (1 + theta_full[:, 1]) ** 2
+    fisco = 1.0 / (6 ** 1.5 * math.pi * theta_full[:, 0] * eta ** -0.6 * 4.925490947e-6)
+    ncut = np.searchsorted(ev.freqs, fisco, side="right")
+    pairs = float(ncut.sum())
+    bins_ms, bins_n = prof[gwl.KERNEL_BINS]
+    per_launch_s = bins_ms / bins_n * 1e-3
+    peaks = measured_peaks()
+    clk = results[gwl.GWL_MIXED]["clocks"]
+    fclk = (clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    import torch as _t
+    n_sm = _t.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * fclk / 1e12
+    achieved = FLOPS_PER_BIN_MIXED * pairs / per_launch_s / 1e12
+
+    ms = torch.tensor([results[gwl.GWL_MIXED]["ms"]], device="cuda")
+    ms64 = torch.tensor([results[gwl.GWL_FP64]["ms"]], device="cuda")
+    mse = torch.tensor([ms_e2e], device="cuda")
+    if world > 1:
+        for t in (ms, ms64, mse):
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms, ms64, mse = ms.item(), ms64.item(), mse.item()
+    value = world * BATCH / (ms * 1e-3)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32x2-phase/f32/f64",
+        "data": "synthetic (seeded coloured Gaussian noise + TaylorF2 injection from the device template)",
+        "config": {"workload": "3-det BBH, 8 s, 20-1024 Hz, 8033 bins/det, 11-D, batch 8192 proposals per GPU",
+                   "global_batch": BATCH * world, "bins_per_det": int(ev.M), "n_det": int(ev.n_det),
+                   "in_band_pairs_per_batch": int(pairs), "precision": "mixed",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "fp64_path": {"value": world * BATCH / (ms64 * 1e-3), "ms_per_step": ms64, "steps": results[gwl.GWL_FP64]["steps"],
+                      "speedup_mixed_over_fp64": ms64 / ms},
+        "e2e": {"value": world * BATCH / (mse * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": int(theta_np.nbytes),
+                "d2h_bytes_per_step": int(BATCH * 8)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_window<3,mixed> (windowed bin loop)",
+                     "peak_basis": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 flop x {fclk / 1e6:.0f} MHz (derived)",
+                     "flops_per_pair": FLOPS_PER_BIN_MIXED, "pairs_per_launch": int(pairs),
+                     "kernel_ms": per_launch_s * 1e3,
+                     "share_of_step": bins_ms / bins_n / ms},
+        "kernel_ms": {"prologue": prof[gwl.KERNEL_PROLOGUE][0] / max(prof[gwl.KERNEL_PROLOGUE][1], 1),
+                      "bins": bins_ms / bins_n,
+                      "combine": prof[gwl.KERNEL_COMBINE][0] / max(prof[gwl.KERNEL_COMBINE][1], 1)},
+        "clocks": clk,
+        "gpu_launches": int(results[gwl.GWL_MIXED]["launches"]),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(theta_full, args.cpu_seconds, use_device_event=ev)
+    for c in ctxs.values():
+        c.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def oracle_event():
+    import oracle
+
+    def wf(ev, th):
+        return oracle.waveform(ev, th)
+
+    def snr2(ev, th):
+        return -2.0 * oracle.loglike(ev.with_strain(np.zeros_like(ev.strain)), th[None])[0]
+
+    return I.make_event(CONFIG, SEED, wf, snr2)
+
+
+def cpu_baseline(theta_full, seconds, use_device_event=None):
+    """The FP64 oracle (as it stands) on all host cores, repeated over the batch until ~seconds elapse."""
+    import oracle
+
+    ev = oracle_event()
+    n = os.cpu_count() or 1
+    sample = theta_full[:1024]
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.loglike(ev, sample, n_threads=n)
+        done += sample.shape[0]
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "evals/s", "cores": n, "kind": "oracle",
+            "sample": f"{done} evaluations = repeated first 1024 proposals of the 8192-proposal batch "
+                      f"(same event, oracle-made injection), {el:.1f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    ev = oracle_event()
+    theta_full = I.proposals(ev, BATCH, SEED)
+    n = os.cpu_count() or 1
+    sample = theta_full[:512]
+    for _ in range(args.warmup):
+        oracle.loglike(ev, sample[:64], n_threads=n)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.loglike(ev, sample, n_threads=n)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = sample.shape[0] / (ms * 1e-3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3-det BBH, 8 s, 20-1024 Hz, 8033 bins/det, 11-D; each step 512 of the 8192 proposals",
+                   "global_batch": BATCH, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": n, "kind": "oracle",
+                         "sample": "512 proposals of the 8192-proposal batch per step"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gwl(args)
+
+
+if __name__ == "__main__":
+    main()

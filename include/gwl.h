@@ -1,0 +1,207 @@
+/*
+ * gwl.h -- C ABI of the GB300 batched gravitational-wave likelihood library.
+ *
+ * The library evaluates, for many parameter vectors at once, the
+ * frequency-domain Gaussian-noise log-likelihood of Smith, Ashton, Vajpeyi &
+ * Talbot (2020), Eq. 2, read as the log-likelihood ratio
+ *
+ *     lnL(theta) = sum_det [ <d|h(theta)> - 1/2 <h(theta)|h(theta)> ],
+ *     <a|b> = 4 df Re sum_j conj(a_j) b_j / S_j,
+ *
+ * with an aligned-spin TaylorF2 inspiral template (Newtonian amplitude,
+ * 3.5PN phase, h = 0 above the ISCO frequency), and the constrained
+ * random-walk replacement step of static parallel nested sampling
+ * (Section 3, Algorithm 1: candidates are accepted iff lnL >= L*).
+ *
+ * Conventions
+ *   - Every function returns an int status: GWL_OK (0) or a negative
+ *     GWL_ERR_* code; gwl_last_error() returns a text for the calling thread's
+ *     last failure.  Argument errors are reported synchronously.  Errors that
+ *     kernels detect (a bounded wait that ran out) are latched in the context
+ *     and reported by the next gwl_sync().
+ *   - "dev" pointers are device pointers owned by the caller (e.g. torch
+ *     tensors); "host" pointers are ordinary host memory.  Compute calls
+ *     enqueue on the caller's CUDA stream (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream) and return without synchronising, except
+ *     the *_host variants, which copy, compute and synchronise.
+ *   - Parameter order of the full 11-D vector (GWL_P_*):
+ *       Mc [detector-frame Msun], q = m2/m1 in (0,1], chi1z, chi2z,
+ *       dL [Mpc], iota, psi, ra, dec [rad], tc [s, relative to t_ref],
+ *       phic [rad].
+ *     A context samples n_dim of them (param_map); the others keep
+ *     fixed_theta.  theta arrays passed to the library hold the n_dim sampled
+ *     coordinates per row, row-major [B][n_dim], FP64.
+ *   - An unphysical row (q outside (0,1], Mc <= 0 or dL <= 0, or a non-finite
+ *     value) yields lnL = -inf and a zero gradient; it is not an error.
+ *   - A context is not thread-safe; calls on one context must not overlap
+ *     (they share its scratch buffers).
+ */
+#ifndef GWL_H
+#define GWL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWL_OK 0
+#define GWL_ERR_ARG (-1)       /* invalid argument (null pointer, size, option) */
+#define GWL_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define GWL_ERR_TIMEOUT (-3)   /* a kernel's bounded wait ran out (latched) */
+#define GWL_ERR_NONFINITE (-4) /* reserved */
+#define GWL_ERR_NOMEM (-5)     /* device allocation failed */
+
+#define GWL_FP64 0  /* plain FP64: phase, sincos and sums in double precision */
+#define GWL_MIXED 1 /* float-float phase, exact mod-1 reduction, FP32 sincos and
+                       sums, FP64 combination */
+
+#define GWL_FCUT_ISCO 0 /* h = 0 above f_ISCO = 1/(6^{3/2} pi M) */
+#define GWL_FCUT_BAND 1 /* template continued to the top of the band */
+
+#define GWL_N_PARAM 11
+#define GWL_MAX_DET 4
+
+enum {
+  GWL_P_MC = 0, GWL_P_Q, GWL_P_CHI1, GWL_P_CHI2, GWL_P_DL, GWL_P_IOTA,
+  GWL_P_PSI, GWL_P_RA, GWL_P_DEC, GWL_P_TC, GWL_P_PHIC
+};
+
+/* Unit-cube prior maps used by ns_replace (u in [0,1] -> parameter). */
+#define GWL_PRIOR_UNIFORM 0 /* lo + u (hi - lo) */
+#define GWL_PRIOR_VOLUME 1  /* [lo^3 + u (hi^3 - lo^3)]^{1/3} (uniform in volume) */
+#define GWL_PRIOR_SINE 2    /* arccos(1 - 2u), on [0, pi] */
+#define GWL_PRIOR_COSINE 3  /* arcsin(2u - 1), on [-pi/2, pi/2] */
+
+/* One L-shaped detector in Earth-fixed Cartesian axes: vertex position [m]
+ * and unit vectors along the two (perpendicular) arms.  The detector tensor
+ * is D = (x x - y y)/2, F+ = D:e+, Fx = D:ex, and the arrival delay relative
+ * to the Earth's centre is dt = -(vertex . n)/c for a source in direction n. */
+typedef struct {
+  double vertex[3];
+  double xarm[3];
+  double yarm[3];
+} gwl_detector;
+
+typedef struct {
+  int precision;     /* GWL_FP64 or GWL_MIXED */
+  int fcut_mode;     /* GWL_FCUT_ISCO or GWL_FCUT_BAND */
+  double gmst;       /* Greenwich sidereal angle [rad]; Earth rotation over the
+                        segment is ignored; ra enters as ra - gmst */
+  double t_ref;      /* reference time [s] from the segment start; the template's
+                        coalescence time is t_ref + tc */
+  int n_dim;         /* number of sampled parameters, 1..11 */
+  int param_map[GWL_N_PARAM];      /* [n_dim] index into the 11-D vector */
+  double fixed_theta[GWL_N_PARAM]; /* values of the parameters not sampled */
+  /* unit-cube prior of each sampled coordinate (used by ns_replace) */
+  int prior_kind[GWL_N_PARAM];
+  double prior_lo[GWL_N_PARAM];
+  double prior_hi[GWL_N_PARAM];
+  int periodic[GWL_N_PARAM]; /* 1: the coordinate wraps in the unit cube */
+} gwl_options;
+
+typedef struct gwl_ctx gwl_ctx;
+
+/* Create a context for one data segment (Eq. 2's d, S and detectors).
+ *   freqs  host [n_bins]          uniformly spaced ascending frequencies [Hz]
+ *                                 f_j = f_0 + j df, f_0 > 0 (checked to 1e-9 df)
+ *   strain host [n_det][n_bins][2] complex frequency-domain data d_j (re, im)
+ *   psd    host [n_det][n_bins]   one-sided noise PSD S_j > 0
+ *   dets   host [n_det]           detector geometry, 1 <= n_det <= GWL_MAX_DET
+ *   opt    host                   options (copied)
+ * The library copies the inputs to the device, builds its tables there
+ * (basis functions of the PN phase, data weights, <h|h> prefix sums) and owns
+ * them until gwl_destroy.  Uses the current CUDA device.  *out receives the
+ * context, or NULL on failure. */
+int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const double* psd,
+               const gwl_detector* dets, int n_det, const gwl_options* opt, gwl_ctx** out);
+
+/* Batched log-likelihood (Eq. 2 as the log-likelihood ratio).
+ *   theta_dev dev [B][n_dim] FP64 sampled coordinates
+ *   lnl_dev   dev [B]        FP64 output
+ * B >= 0 (B = 0 is a no-op). */
+int gwl_loglike(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, void* stream);
+
+/* As gwl_loglike with host buffers: copies theta to the device, evaluates,
+ * copies lnL back and synchronises the stream before returning. */
+int gwl_loglike_host(gwl_ctx* ctx, const double* theta_host, int64_t B, double* lnl_host,
+                     void* stream);
+
+/* Log-likelihood and its gradient with respect to the n_dim sampled
+ * coordinates (adjoint accumulation over bins; the ISCO cut index is held
+ * fixed, i.e. the gradient of the piecewise-smooth lnL).
+ *   grad_dev dev [B][n_dim] FP64 output */
+int gwl_grad(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, double* grad_dev,
+             void* stream);
+
+/* Detector-projected template h_d(f_j) of each row, as evaluated by the
+ * device path (zero above the cut).
+ *   h_dev dev [B][n_det][n_bins][2] FP64 output */
+int gwl_waveform(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* h_dev, void* stream);
+
+/* Constrained random-walk replacement (Algorithm 1's parallel sampling step
+ * with a fixed-length random walk).  Each of n_chains chains starts at a live
+ * point chosen uniformly among the K - 1 points other than `worst`, then makes
+ * walk_len steps u' = u + scale * chol z in the unit cube (z standard normal);
+ * periodic coordinates wrap, any other coordinate outside [0,1] rejects the
+ * step; a step is accepted iff lnL(theta(u')) >= lnl_star.
+ *   live_u   dev [K][n_dim]      unit-cube coordinates of the live points
+ *   live_lnl dev [K]             their lnL
+ *   chol     dev [n_dim][n_dim]  lower-triangular step matrix (row-major)
+ *   out_u    dev [n_chains][n_dim], out_lnl dev [n_chains],
+ *   out_nacc dev [n_chains] int32 accepted steps (0 = the chain returns its
+ *            start point), out_start dev [n_chains] int32 (may be NULL).
+ * Random numbers: Philox4x32-10 (Salmon et al. 2011) with key = (seed low,
+ * seed high 32 bits) and counter = (block, step, chain, counter low 32 bits);
+ * step 0 block 0 word 0 picks the start (index = floor(w (K-1) / 2^32),
+ * skipping `worst`); step s >= 1, block b gives normals 4b..4b+3 by
+ * Box-Muller on word pairs: u1 = (w0 + 1) 2^-32, u2 = w1 2^-32,
+ * z = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2). */
+int ns_replace(gwl_ctx* ctx, const double* live_u, const double* live_lnl, int64_t K, int64_t worst,
+               double lnl_star, uint64_t seed, uint64_t counter, int64_t n_chains, int walk_len,
+               double scale, const double* chol, double* out_u, double* out_lnl, int32_t* out_nacc,
+               int32_t* out_start, void* stream);
+
+/* Synchronise the context's last stream and return the latched device
+ * status (GWL_OK or GWL_ERR_TIMEOUT); clears the latch. */
+int gwl_sync(gwl_ctx* ctx);
+
+/* Tuning knobs (0 keeps the current value): window = bins staged in shared
+ * memory per work item; slice = proposals per work item; ctas_per_sm = grid
+ * size multiplier over the SM count. */
+int gwl_set_tuning(gwl_ctx* ctx, int window, int slice, int ctas_per_sm);
+
+/* Kernel classes for gwl_profile_read. */
+#define GWL_KERNEL_PROLOGUE 0 /* per-proposal coefficients */
+#define GWL_KERNEL_BINS 1     /* windowed bin loop of gwl_loglike */
+#define GWL_KERNEL_COMBINE 2  /* per-proposal combination */
+#define GWL_KERNEL_GRAD 3     /* windowed bin loop of gwl_grad */
+#define GWL_KERNEL_WALK 4     /* random-walk proposal/accept steps of ns_replace */
+#define GWL_KERNEL_KINDS 5
+
+/* Enable (1) or disable (0) per-kernel timing: while enabled, the library
+ * records a CUDA event pair around every launch of its kernels on the launch
+ * stream.  Enabling resets the accumulated totals. */
+int gwl_profile(gwl_ctx* ctx, int enable);
+
+/* Wait for the recorded events and return the accumulated device time [ms]
+ * and launch count of one kernel class since profiling was enabled. */
+int gwl_profile_read(gwl_ctx* ctx, int kind, double* total_ms, int64_t* count);
+
+/* Device bytes held by the context (tables + scratch). */
+int64_t gwl_device_bytes(const gwl_ctx* ctx);
+
+/* Number of kernel launches the context has issued since creation. */
+int64_t gwl_launch_count(const gwl_ctx* ctx);
+
+/* Free the context's device memory.  NULL is ignored. */
+void gwl_destroy(gwl_ctx* ctx);
+
+/* Text of the calling thread's last error ("" if none). */
+const char* gwl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWL_H */

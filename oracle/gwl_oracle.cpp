@@ -234,11 +234,14 @@ T pn_psi(const PNPhase<T>& P, double f) {
   return 3.0 / (128.0 * P.eta * v5) * series;
 }
 
+// Rows outside the physical domain (q not in (0,1], Mc <= 0, dL <= 0) or with a
+// non-finite entry have lnL = -inf by definition of the interface.
 template <class T>
 bool physical(const T* th) {
   double q = val(th[P_Q]), mc = val(th[P_MC]), dl = val(th[P_DL]);
-  return q > 0.0 && q <= 1.0 && mc > 0.0 && dl > 0.0 &&
-         std::isfinite(val(th[P_CHI1])) && std::isfinite(val(th[P_CHI2]));
+  bool ok = q > 0.0 && q <= 1.0 && mc > 0.0 && dl > 0.0;
+  for (int k = 0; k < P_N; ++k) ok = ok && std::isfinite(val(th[k]));
+  return ok;
 }
 
 // Upper frequency cut: f_ISCO = 1/(6^{3/2} pi M) in ISCO mode, otherwise +inf.

@@ -1,0 +1,375 @@
+// gwl_api.cu -- the C ABI (include/gwl.h): argument checks, device memory,
+// error reporting.  All arithmetic of the likelihood runs in the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gwl_internal.h"
+
+namespace gwl {
+cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, cudaStream_t st);
+int64_t partials_needed(const gwl_ctx* c, int64_t B);
+}  // namespace gwl
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? GWL_ERR_NOMEM : GWL_ERR_CUDA, "%s: %s", where,
+              cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dev_alloc(gwl_ctx* c, T** p, int64_t n) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)(n > 0 ? n : 1));
+  if (e == cudaSuccess) c->bytes += (int64_t)sizeof(T) * (n > 0 ? n : 1);
+  return e;
+}
+
+template <class T>
+void dev_free(gwl_ctx* c, T*& p, int64_t n) {
+  if (p) {
+    cudaFree(p);
+    c->bytes -= (int64_t)sizeof(T) * (n > 0 ? n : 1);
+  }
+  p = nullptr;
+}
+
+// Grow the per-proposal and partial-sum scratch to hold a batch of B.
+int ensure_scratch(gwl_ctx* c, int64_t B) {
+  cudaError_t e;
+  if (B > c->prop_cap) {
+    int64_t cap = B > 2 * c->prop_cap ? B : 2 * c->prop_cap;
+    dev_free(c, c->d_pm, c->prop_cap);
+    dev_free(c, c->d_pf, c->prop_cap);
+    dev_free(c, c->d_pc, c->prop_cap);
+    c->prop_cap = 0;
+    if ((e = dev_alloc(c, &c->d_pm, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
+    if ((e = dev_alloc(c, &c->d_pf, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
+    if ((e = dev_alloc(c, &c->d_pc, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
+    c->prop_cap = cap;
+  }
+  const int64_t need = gwl::partials_needed(c, B);
+  if (need > c->partials_cap) {
+    int64_t cap = need > 2 * c->partials_cap ? need : 2 * c->partials_cap;
+    dev_free(c, c->d_partials, c->partials_cap);
+    c->partials_cap = 0;
+    if ((e = dev_alloc(c, &c->d_partials, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
+    c->partials_cap = cap;
+  }
+  return GWL_OK;
+}
+
+int ensure_io(gwl_ctx* c, int64_t n) {
+  if (n <= c->io_cap) return GWL_OK;
+  dev_free(c, c->d_io, c->io_cap);
+  c->io_cap = 0;
+  cudaError_t e = dev_alloc(c, &c->d_io, n);
+  if (e != cudaSuccess) return cuda_fail(e, "io staging");
+  c->io_cap = n;
+  return GWL_OK;
+}
+
+int check_ctx(const gwl_ctx* c) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return fail(GWL_ERR_ARG, "context belongs to device %d but device %d is current", c->device, dev);
+  return GWL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gwl_last_error(void) { return g_err.c_str(); }
+
+int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const double* psd,
+               const gwl_detector* dets, int n_det, const gwl_options* opt, gwl_ctx** out) {
+  if (!out) return fail(GWL_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!freqs || !strain || !psd || !dets || !opt) return fail(GWL_ERR_ARG, "null input pointer");
+  if (n_bins < 2 || n_bins > (int64_t)1 << 30) return fail(GWL_ERR_ARG, "n_bins=%lld out of range", (long long)n_bins);
+  if (n_det < 1 || n_det > GWL_MAX_DET) return fail(GWL_ERR_ARG, "n_det=%d out of range [1,%d]", n_det, GWL_MAX_DET);
+  if (opt->precision != GWL_FP64 && opt->precision != GWL_MIXED) return fail(GWL_ERR_ARG, "bad precision");
+  if (opt->fcut_mode != GWL_FCUT_ISCO && opt->fcut_mode != GWL_FCUT_BAND) return fail(GWL_ERR_ARG, "bad fcut_mode");
+  if (opt->n_dim < 1 || opt->n_dim > GWL_N_PARAM) return fail(GWL_ERR_ARG, "n_dim=%d out of range", opt->n_dim);
+  bool used[GWL_N_PARAM] = {false};
+  for (int i = 0; i < opt->n_dim; ++i) {
+    const int k = opt->param_map[i];
+    if (k < 0 || k >= GWL_N_PARAM || used[k]) return fail(GWL_ERR_ARG, "bad param_map[%d]=%d", i, k);
+    used[k] = true;
+    if (opt->prior_kind[i] < 0 || opt->prior_kind[i] > 3) return fail(GWL_ERR_ARG, "bad prior_kind[%d]", i);
+  }
+  const double f0 = freqs[0];
+  const double df = (freqs[n_bins - 1] - freqs[0]) / (double)(n_bins - 1);
+  if (!(f0 > 0.0) || !(df > 0.0)) return fail(GWL_ERR_ARG, "frequencies must be positive and ascending");
+  for (int64_t j = 0; j < n_bins; ++j) {
+    if (std::fabs(freqs[j] - (f0 + (double)j * df)) > 1e-9 * df)
+      return fail(GWL_ERR_ARG, "frequencies are not uniformly spaced at bin %lld", (long long)j);
+  }
+  for (int64_t i = 0; i < (int64_t)n_det * n_bins; ++i)
+    if (!(psd[i] > 0.0) || !std::isfinite(psd[i])) return fail(GWL_ERR_ARG, "psd[%lld] not positive", (long long)i);
+  for (int64_t i = 0; i < 2 * (int64_t)n_det * n_bins; ++i)
+    if (!std::isfinite(strain[i])) return fail(GWL_ERR_ARG, "strain[%lld] not finite", (long long)i);
+
+  gwl_ctx* c = new (std::nothrow) gwl_ctx();
+  if (!c) return fail(GWL_ERR_NOMEM, "host allocation failed");
+  int rc = GWL_OK;
+  double* d_strain = nullptr;
+  double* d_psd = nullptr;
+  cudaError_t e;
+  do {
+    if ((e = cudaGetDevice(&c->device)) != cudaSuccess) { rc = cuda_fail(e, "cudaGetDevice"); break; }
+    if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) {
+      rc = cuda_fail(e, "device attribute");
+      break;
+    }
+    c->M = n_bins;
+    c->n_det = n_det;
+    c->f0 = f0;
+    c->df = df;
+    c->opt = *opt;
+    c->row_floats = gwl::mixed_row_floats(n_det);
+    c->row_doubles = gwl::f64_row_doubles(n_det);
+    if ((e = dev_alloc(c, &c->d_freqs, n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_geom, 9 * n_det)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_H, (int64_t)n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_tab_mixed, n_bins * c->row_floats)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_tab_f64, n_bins * c->row_doubles)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_status, 4)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = cudaMalloc(&d_strain, sizeof(double) * 2 * n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = cudaMalloc(&d_psd, sizeof(double) * n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    double geom[9 * GWL_MAX_DET];
+    for (int d = 0; d < n_det; ++d)
+      for (int k = 0; k < 3; ++k) {
+        geom[9 * d + k] = dets[d].vertex[k];
+        geom[9 * d + 3 + k] = dets[d].xarm[k];
+        geom[9 * d + 6 + k] = dets[d].yarm[k];
+      }
+    if ((e = cudaMemcpy(c->d_freqs, freqs, sizeof(double) * n_bins, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_geom, geom, sizeof(double) * 9 * n_det, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d_strain, strain, sizeof(double) * 2 * n_det * n_bins, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(d_psd, psd, sizeof(double) * n_det * n_bins, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c->d_status, 0, 4 * sizeof(int))) != cudaSuccess) {
+      rc = cuda_fail(e, "copy inputs");
+      break;
+    }
+    if ((e = gwl::launch_build_tables(c, d_strain, d_psd, 0)) != cudaSuccess) { rc = cuda_fail(e, "build tables"); break; }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "build tables"); break; }
+    gwl::SegInfo& s = c->seg;
+    s.freqs = c->d_freqs;
+    s.H = c->d_H;
+    s.geom = c->d_geom;
+    s.M = n_bins;
+    s.n_det = n_det;
+    s.fcut_mode = opt->fcut_mode;
+    s.f0 = f0;
+    s.df = df;
+    s.gmst = opt->gmst;
+    s.t_ref = opt->t_ref;
+    s.n_dim = opt->n_dim;
+    for (int k = 0; k < GWL_N_PARAM; ++k) {
+      s.fixed[k] = opt->fixed_theta[k];
+      s.param_map[k] = k < opt->n_dim ? opt->param_map[k] : 0;
+    }
+  } while (false);
+  if (d_strain) cudaFree(d_strain);
+  if (d_psd) cudaFree(d_psd);
+  if (rc != GWL_OK) {
+    gwl_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return GWL_OK;
+}
+
+int gwl_loglike(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (B < 0) return fail(GWL_ERR_ARG, "B < 0");
+  if (B == 0) return GWL_OK;
+  if (!theta_dev || !lnl_dev) return fail(GWL_ERR_ARG, "null device pointer");
+  if ((rc = ensure_scratch(c, B))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  cudaError_t e = gwl::launch_loglike(c, theta_dev, B, lnl_dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_loglike");
+  return GWL_OK;
+}
+
+int gwl_loglike_host(gwl_ctx* c, const double* theta_host, int64_t B, double* lnl_host, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (B < 0) return fail(GWL_ERR_ARG, "B < 0");
+  if (B == 0) return GWL_OK;
+  if (!theta_host || !lnl_host) return fail(GWL_ERR_ARG, "null host pointer");
+  const int64_t nt = B * c->opt.n_dim;
+  if ((rc = ensure_io(c, nt + B))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(c->d_io, theta_host, sizeof(double) * nt, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy theta");
+  if ((rc = gwl_loglike(c, c->d_io, B, c->d_io + nt, stream))) return rc;
+  e = cudaMemcpyAsync(lnl_host, c->d_io + nt, sizeof(double) * B, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy lnL");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronise");
+  return GWL_OK;
+}
+
+int gwl_waveform(gwl_ctx* c, const double* theta_dev, int64_t B, double* h_dev, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (B < 0 || B > 65535) return fail(GWL_ERR_ARG, "B=%lld out of range [0, 65535]", (long long)B);
+  if (B == 0) return GWL_OK;
+  if (!theta_dev || !h_dev) return fail(GWL_ERR_ARG, "null device pointer");
+  if ((rc = ensure_scratch(c, B))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  cudaError_t e = gwl::launch_waveform(c, theta_dev, B, h_dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_waveform");
+  return GWL_OK;
+}
+
+int gwl_grad(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, double* grad_dev, void* stream) {
+  (void)theta_dev; (void)lnl_dev; (void)grad_dev; (void)stream; (void)B;
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  return fail(GWL_ERR_ARG, "gwl_grad: not available in this build");
+}
+
+int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, int64_t worst, double lnl_star,
+               uint64_t seed, uint64_t counter, int64_t n_chains, int walk_len, double scale, const double* chol,
+               double* out_u, double* out_lnl, int32_t* out_nacc, int32_t* out_start, void* stream) {
+  (void)live_u; (void)live_lnl; (void)K; (void)worst; (void)lnl_star; (void)seed; (void)counter;
+  (void)n_chains; (void)walk_len; (void)scale; (void)chol; (void)out_u; (void)out_lnl; (void)out_nacc;
+  (void)out_start; (void)stream;
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  return fail(GWL_ERR_ARG, "ns_replace: not available in this build");
+}
+
+int gwl_sync(gwl_ctx* c) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_sync");
+  int st = 0;
+  e = cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_sync status");
+  if (st) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    if (st & gwl::kStatusTimeout) return fail(GWL_ERR_TIMEOUT, "a kernel's bounded wait ran out");
+  }
+  return GWL_OK;
+}
+
+int gwl_set_tuning(gwl_ctx* c, int window, int slice, int ctas_per_sm) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  if (window < 0 || slice < 0 || ctas_per_sm < 0) return fail(GWL_ERR_ARG, "negative tuning value");
+  if (window) {
+    const size_t row = c->opt.precision == GWL_MIXED ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
+    if ((size_t)window * row > 200 * 1024) return fail(GWL_ERR_ARG, "window of %d bins exceeds shared memory", window);
+    if (c->opt.precision == GWL_MIXED) c->window_mixed = window; else c->window_f64 = window;
+  }
+  if (slice) c->slice = slice;
+  if (ctas_per_sm) c->ctas_per_sm = ctas_per_sm;
+  return GWL_OK;
+}
+
+int gwl_profile(gwl_ctx* c, int enable) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  for (int k = 0; k < GWL_KERNEL_KINDS; ++k) {
+    for (auto& pr : c->prof_pending[k]) {
+      c->event_pool.push_back(pr.first);
+      c->event_pool.push_back(pr.second);
+    }
+    c->prof_pending[k].clear();
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+  }
+  c->profiling = enable != 0;
+  return GWL_OK;
+}
+
+int gwl_profile_read(gwl_ctx* c, int kind, double* total_ms, int64_t* count) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  if (kind < 0 || kind >= GWL_KERNEL_KINDS) return fail(GWL_ERR_ARG, "bad kernel kind %d", kind);
+  for (auto& pr : c->prof_pending[kind]) {
+    cudaError_t e = cudaEventSynchronize(pr.second);
+    if (e != cudaSuccess) return cuda_fail(e, "profile");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e != cudaSuccess) return cuda_fail(e, "profile");
+    c->prof_ms[kind] += ms;
+    c->prof_n[kind] += 1;
+    c->event_pool.push_back(pr.first);
+    c->event_pool.push_back(pr.second);
+  }
+  c->prof_pending[kind].clear();
+  if (total_ms) *total_ms = c->prof_ms[kind];
+  if (count) *count = c->prof_n[kind];
+  return GWL_OK;
+}
+
+int64_t gwl_device_bytes(const gwl_ctx* c) { return c ? c->bytes : 0; }
+int64_t gwl_launch_count(const gwl_ctx* c) { return c ? c->launches : 0; }
+
+void gwl_destroy(gwl_ctx* c) {
+  if (!c) return;
+  gwl_profile(c, 0);
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  c->event_pool.clear();
+  dev_free(c, c->d_freqs, c->M);
+  dev_free(c, c->d_geom, 9 * c->n_det);
+  dev_free(c, c->d_H, (int64_t)c->n_det * c->M);
+  dev_free(c, c->d_tab_mixed, c->M * c->row_floats);
+  dev_free(c, c->d_tab_f64, c->M * c->row_doubles);
+  dev_free(c, c->d_pm, c->prop_cap);
+  dev_free(c, c->d_pf, c->prop_cap);
+  dev_free(c, c->d_pc, c->prop_cap);
+  dev_free(c, c->d_partials, c->partials_cap);
+  dev_free(c, c->d_io, c->io_cap);
+  dev_free(c, c->d_status, 4);
+  delete c;
+}
+
+}  // extern "C"
+
+namespace gwl {
+static cudaEvent_t take_event(gwl_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+ProfScope::ProfScope(gwl_ctx* c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) {
+  if (!c->profiling) return;
+  e0 = take_event(c);
+  e1 = take_event(c);
+  if (e0) cudaEventRecord(e0, st);
+}
+ProfScope::~ProfScope() {
+  if (!c->profiling || !e0 || !e1) return;
+  cudaEventRecord(e1, st);
+  c->prof_pending[kind].emplace_back(e0, e1);
+}
+}  // namespace gwl

@@ -1,0 +1,79 @@
+// gwl_internal.h -- host-side context and kernel launch wrappers (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/gwl.h"
+#include "gwl_device.cuh"
+
+struct gwl_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int64_t M = 0;
+  int n_det = 0;
+  double f0 = 0.0, df = 0.0;
+  gwl_options opt{};
+  gwl::SegInfo seg{};  // device pointers inside
+
+  // device tables (owned)
+  double* d_freqs = nullptr;   // [M]
+  double* d_geom = nullptr;    // [n_det][9]
+  double* d_H = nullptr;       // [n_det][M]
+  float* d_tab_mixed = nullptr;  // [M][mixed_row_floats]
+  double* d_tab_f64 = nullptr;   // [M][f64_row_doubles]
+  int row_floats = 0, row_doubles = 0;
+
+  // device scratch (owned, grown on demand)
+  gwl::PropMixed* d_pm = nullptr;
+  gwl::PropF64* d_pf = nullptr;
+  gwl::PropCommon* d_pc = nullptr;
+  int64_t prop_cap = 0;
+  double* d_partials = nullptr;  // [B][n_windows][2 n_det]
+  int64_t partials_cap = 0;      // in doubles
+  double* d_io = nullptr;        // staging for the host-buffer entry points
+  int64_t io_cap = 0;            // in doubles
+  int* d_status = nullptr;       // [0] latched status bits, [1] max cut over the batch
+
+  // tuning
+  int window_mixed = 1024, window_f64 = 512, slice = 64, ctas_per_sm = 2;
+
+  int64_t launches = 0;
+  int64_t bytes = 0;
+  cudaStream_t last_stream = nullptr;
+
+  // optional per-kernel timing with CUDA events recorded on the launch stream
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[GWL_KERNEL_KINDS];
+  std::vector<cudaEvent_t> event_pool;
+  double prof_ms[GWL_KERNEL_KINDS] = {0};
+  int64_t prof_n[GWL_KERNEL_KINDS] = {0};
+};
+
+namespace gwl {
+// Records a start event now and a stop event when it goes out of scope, on
+// the launch stream, if the context has profiling enabled.
+struct ProfScope {
+  gwl_ctx* c;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ProfScope(gwl_ctx* c_, int kind_, cudaStream_t st_);
+  ~ProfScope();
+};
+}  // namespace gwl
+
+namespace gwl {
+
+// a1: tables
+cudaError_t launch_build_tables(gwl_ctx* c, const double* d_strain, const double* d_psd, cudaStream_t st);
+
+// a2-a6: batched log-likelihood
+cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st);
+
+// device-path template, for diagnostics and injections
+cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st);
+
+}  // namespace gwl

@@ -1,0 +1,113 @@
+// gwl_tables.cu -- per-segment tables, built once by gwl_create.
+//
+// For every bin j (f = f_j):
+//   basis   B_m(f) = f^{-5/3}, f^{-1}, f^{-2/3}, f^{-1/3}, ln f, f^{1/3}, f^{1/3} ln f, f^{2/3}
+//   data    G_d,j = 4 df conj(d_d,j) f^{-7/6} / S_d,j * e^{-2 pi i f t_ref}
+//   norm    H_d[j] = sum_{i <= j} 4 df f_i^{-7/3} / S_d,i   (inclusive prefix)
+// so that, with r_d,j = sum_m c_m B_m(f_j) + tau_d f_j in cycles,
+//   <d|h>_d = Re[K_d sum_j G_d,j e^{-2 pi i r_d,j}],   <h|h>_d = |K_d|^2 H_d[ncut - 1]
+// (Eq. 2 of the paper, split into a data-dependent and a template-dependent part).
+#include "gwl_internal.h"
+
+namespace gwl {
+
+__global__ void k_table_rows(const double* __restrict__ freqs, const double* __restrict__ strain,
+                             const double* __restrict__ psd, int64_t M, int n_det, double df, double t_ref,
+                             float* __restrict__ tab_m, int row_f, double* __restrict__ tab_d, int row_d,
+                             double* __restrict__ hterm) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double f = freqs[j];
+  const double c1 = cbrt(f);
+  const double lf = log(f);
+  double b[kNBasis];
+  b[0] = 1.0 / (f * c1 * c1);
+  b[1] = 1.0 / f;
+  b[2] = 1.0 / (c1 * c1);
+  b[3] = 1.0 / c1;
+  b[4] = lf;
+  b[5] = c1;
+  b[6] = c1 * lf;
+  b[7] = c1 * c1;
+  float* rm = tab_m + j * row_f;
+  double* rd = tab_d + j * row_d;
+#pragma unroll
+  for (int m = 0; m < kNBasis; ++m) {
+    float hi, lo;
+    split_f64(b[m], hi, lo);
+    rm[m] = hi;
+    rm[kNBasis + m] = lo;
+    rd[m] = b[m];
+  }
+  float fh, fl;
+  split_f64(f, fh, fl);
+  rm[16] = fh;
+  rm[17] = fl;
+  rd[8] = f;
+  // e^{-2 pi i f t_ref}: reduce f t_ref to [0, 1) cycles first
+  const double x = f * t_ref;
+  const double fr = x - floor(x);
+  double sr, cr;
+  sincospi(2.0 * fr, &sr, &cr);
+  const double f76 = pow(f, -7.0 / 6.0);
+  for (int d = 0; d < n_det; ++d) {
+    const double S = psd[(int64_t)d * M + j];
+    const double w = 4.0 * df * f76 / S;
+    const double dr = strain[2 * ((int64_t)d * M + j)];
+    const double di = strain[2 * ((int64_t)d * M + j) + 1];
+    const double gr = w * (dr * cr - di * sr);
+    const double gi = -w * (dr * sr + di * cr);
+    rd[9 + 2 * d] = gr;
+    rd[10 + 2 * d] = gi;
+    rm[18 + 2 * d] = (float)gr;
+    rm[19 + 2 * d] = (float)gi;
+    hterm[(int64_t)d * M + j] = 4.0 * df * f76 * f76 / S;
+  }
+  for (int k = 18 + 2 * n_det; k < row_f; ++k) rm[k] = 0.0f;
+  for (int k = 9 + 2 * n_det; k < row_d; ++k) rd[k] = 0.0;
+}
+
+// In-place inclusive prefix sum of one detector's row, one CTA per detector.
+// Each thread sums a contiguous segment serially; segment totals are scanned
+// serially by thread 0; the order of additions is fixed (deterministic).
+__global__ void k_prefix_scan(double* __restrict__ H, int64_t M) {
+  __shared__ double tot[1024];
+  double* h = H + (int64_t)blockIdx.x * M;
+  const int T = blockDim.x;
+  const int64_t seg = (M + T - 1) / T;
+  const int64_t a = threadIdx.x * seg;
+  const int64_t b = a + seg < M ? a + seg : M;
+  double s = 0.0;
+  for (int64_t j = a; j < b; ++j) s += h[j];
+  tot[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double run = 0.0;
+    for (int t = 0; t < T; ++t) {
+      const double v = tot[t];
+      tot[t] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  double run = tot[threadIdx.x];
+  for (int64_t j = a; j < b; ++j) {
+    run += h[j];
+    h[j] = run;
+  }
+}
+
+cudaError_t launch_build_tables(gwl_ctx* c, const double* d_strain, const double* d_psd, cudaStream_t st) {
+  const int T = 256;
+  const int64_t nb = (c->M + T - 1) / T;
+  k_table_rows<<<(unsigned)nb, T, 0, st>>>(c->d_freqs, d_strain, d_psd, c->M, c->n_det, c->df, c->opt.t_ref,
+                                            c->d_tab_mixed, c->row_floats, c->d_tab_f64, c->row_doubles, c->d_H);
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_prefix_scan<<<c->n_det, 1024, 0, st>>>(c->d_H, c->M);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace gwl

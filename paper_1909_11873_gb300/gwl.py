@@ -1,0 +1,236 @@
+"""Thin ctypes binding of ``libgwl.so`` (include/gwl.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  If the compiled library is missing, importing this module
+raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgwl.so")
+
+GWL_OK = 0
+GWL_FP64 = 0
+GWL_MIXED = 1
+GWL_FCUT_ISCO = 0
+GWL_FCUT_BAND = 1
+N_PARAM = 11
+MAX_DET = 4
+
+# exported symbols declared in include/gwl.h
+EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_grad", "gwl_waveform", "ns_replace",
+           "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
+           "gwl_launch_count", "gwl_destroy", "gwl_last_error")
+KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
+
+
+class GwlDetector(C.Structure):
+    _fields_ = [("vertex", C.c_double * 3), ("xarm", C.c_double * 3), ("yarm", C.c_double * 3)]
+
+
+class GwlOptions(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("fcut_mode", C.c_int),
+        ("gmst", C.c_double),
+        ("t_ref", C.c_double),
+        ("n_dim", C.c_int),
+        ("param_map", C.c_int * N_PARAM),
+        ("fixed_theta", C.c_double * N_PARAM),
+        ("prior_kind", C.c_int * N_PARAM),
+        ("prior_lo", C.c_double * N_PARAM),
+        ("prior_hi", C.c_double * N_PARAM),
+        ("periodic", C.c_int * N_PARAM),
+    ]
+
+
+class GwlError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GwlError(f"{LIB_PATH} not found: build it with paper_1909_11873_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, i64, i32, d, u64 = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_uint64
+        L.gwl_create.argtypes = [P, i64, P, P, P, i32, C.POINTER(GwlOptions), C.POINTER(P)]
+        L.gwl_loglike.argtypes = [P, P, i64, P, P]
+        L.gwl_loglike_host.argtypes = [P, P, i64, P, P]
+        L.gwl_grad.argtypes = [P, P, i64, P, P, P]
+        L.gwl_waveform.argtypes = [P, P, i64, P, P]
+        L.ns_replace.argtypes = [P, P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, P]
+        L.gwl_sync.argtypes = [P]
+        L.gwl_set_tuning.argtypes = [P, i32, i32, i32]
+        L.gwl_profile.argtypes = [P, i32]
+        L.gwl_profile_read.argtypes = [P, i32, C.POINTER(d), C.POINTER(i64)]
+        L.gwl_device_bytes.argtypes = [P]
+        L.gwl_device_bytes.restype = i64
+        L.gwl_launch_count.argtypes = [P]
+        L.gwl_launch_count.restype = i64
+        L.gwl_destroy.argtypes = [P]
+        L.gwl_destroy.restype = None
+        L.gwl_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != GWL_OK:
+        raise GwlError(f"{what} failed ({rc}): {lib().gwl_last_error().decode()}")
+
+
+def _ptr(t) -> int:
+    """Device or host address of a torch tensor / numpy array (contiguity checked)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def detectors(geom: np.ndarray):
+    g = np.asarray(geom, dtype=np.float64).reshape(-1, 9)
+    arr = (GwlDetector * g.shape[0])()
+    for i, row in enumerate(g):
+        arr[i].vertex[:] = row[0:3].tolist()
+        arr[i].xarm[:] = row[3:6].tolist()
+        arr[i].yarm[:] = row[6:9].tolist()
+    return arr
+
+
+def options(precision: int, fcut_mode: int, gmst: float, t_ref: float, sampling) -> GwlOptions:
+    o = GwlOptions()
+    o.precision = precision
+    o.fcut_mode = fcut_mode
+    o.gmst = gmst
+    o.t_ref = t_ref
+    D = len(sampling.param_map)
+    o.n_dim = D
+    for i in range(D):
+        o.param_map[i] = int(sampling.param_map[i])
+        o.prior_kind[i] = int(sampling.kind[i])
+        o.prior_lo[i] = float(sampling.lo[i])
+        o.prior_hi[i] = float(sampling.hi[i])
+        o.periodic[i] = int(sampling.periodic[i])
+    for k in range(N_PARAM):
+        o.fixed_theta[k] = float(sampling.fixed[k])
+    return o
+
+
+class Context:
+    """One data segment on the current CUDA device (wraps a ``gwl_ctx*``)."""
+
+    def __init__(self, freqs, strain, psd, geom, precision, fcut_mode, gmst, t_ref, sampling):
+        fr = np.ascontiguousarray(freqs, dtype=np.float64)
+        st = np.ascontiguousarray(np.stack([np.real(strain), np.imag(strain)], axis=-1), dtype=np.float64)
+        ps = np.ascontiguousarray(psd, dtype=np.float64)
+        dets = detectors(geom)
+        self.opt = options(precision, fcut_mode, gmst, t_ref, sampling)
+        self.n_dim = self.opt.n_dim
+        self.n_det = len(dets)
+        self.M = fr.size
+        h = C.c_void_p()
+        _check(lib().gwl_create(fr.ctypes.data, fr.size, st.ctypes.data, ps.ctypes.data, dets, len(dets),
+                                C.byref(self.opt), C.byref(h)), "gwl_create")
+        self._h = h
+
+    @classmethod
+    def from_event(cls, ev, precision=GWL_MIXED, sampling=None):
+        return cls(ev.freqs, ev.strain, ev.psd, ev.geom, precision, ev.fcut_mode, ev.gmst, ev.t_ref,
+                   sampling if sampling is not None else ev.sampling)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gwl_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- compute entry points (same names as the C ABI)
+    def gwl_loglike(self, theta, lnl, stream=None):
+        _check(lib().gwl_loglike(self._h, _ptr(theta), theta.shape[0], _ptr(lnl), _stream(stream)), "gwl_loglike")
+
+    def gwl_loglike_host(self, theta: np.ndarray, lnl: np.ndarray, stream=None):
+        _check(lib().gwl_loglike_host(self._h, _ptr(theta), theta.shape[0], _ptr(lnl), _stream(stream)),
+               "gwl_loglike_host")
+
+    def gwl_grad(self, theta, lnl, grad, stream=None):
+        _check(lib().gwl_grad(self._h, _ptr(theta), theta.shape[0], _ptr(lnl), _ptr(grad), _stream(stream)),
+               "gwl_grad")
+
+    def gwl_waveform(self, theta, h, stream=None):
+        _check(lib().gwl_waveform(self._h, _ptr(theta), theta.shape[0], _ptr(h), _stream(stream)), "gwl_waveform")
+
+    def ns_replace(self, live_u, live_lnl, worst, lnl_star, seed, counter, n_chains, walk_len, scale, chol,
+                   out_u, out_lnl, out_nacc, out_start=None, stream=None):
+        _check(lib().ns_replace(self._h, _ptr(live_u), _ptr(live_lnl), live_u.shape[0], int(worst), float(lnl_star),
+                                int(seed), int(counter), int(n_chains), int(walk_len), float(scale), _ptr(chol),
+                                _ptr(out_u), _ptr(out_lnl), _ptr(out_nacc), _ptr(out_start), _stream(stream)),
+               "ns_replace")
+
+    def gwl_sync(self):
+        _check(lib().gwl_sync(self._h), "gwl_sync")
+
+    def gwl_set_tuning(self, window=0, slice=0, ctas_per_sm=0):
+        _check(lib().gwl_set_tuning(self._h, int(window), int(slice), int(ctas_per_sm)), "gwl_set_tuning")
+
+    def gwl_profile(self, enable: bool):
+        _check(lib().gwl_profile(self._h, int(bool(enable))), "gwl_profile")
+
+    def gwl_profile_read(self, kind: int):
+        """(total device ms, launch count) of one kernel class since profiling was enabled."""
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(lib().gwl_profile_read(self._h, int(kind), C.byref(ms), C.byref(n)), "gwl_profile_read")
+        return ms.value, n.value
+
+    def device_bytes(self) -> int:
+        return lib().gwl_device_bytes(self._h)
+
+    def launch_count(self) -> int:
+        return lib().gwl_launch_count(self._h)
+
+
+# ---- convenience wrappers used by tests and the benchmark (torch tensors in, torch tensors out)
+def loglike(ctx: Context, theta, stream=None):
+    import torch
+    out = torch.empty(theta.shape[0], dtype=torch.float64, device=theta.device)
+    ctx.gwl_loglike(theta, out, stream)
+    return out
+
+
+def waveform(ctx: Context, theta, stream=None):
+    import torch
+    out = torch.empty((theta.shape[0], ctx.n_det, ctx.M, 2), dtype=torch.float64, device=theta.device)
+    ctx.gwl_waveform(theta, out, stream)
+    return out

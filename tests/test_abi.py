@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every symbol include/gwl.h declares (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1909_11873_gb300 import build as B
+from paper_1909_11873_gb300 import gwl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return gwl.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gwl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\*?([A-Za-z_][A-Za-z0-9_]*)\s*\(", src, re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert "gwl_create" in names and "ns_replace" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(gwl.EXPORTS)
+
+
+def test_argument_errors_are_synchronous(L):
+    """Invalid arguments fail with GWL_ERR_ARG before any device work."""
+    out = C.c_void_p()
+    f = np.arange(16, dtype=np.float64) + 20.0
+    s = np.zeros((1, 16, 2))
+    p = np.ones((1, 16))
+    dets = gwl.detectors(np.zeros(9))
+    opt = gwl.GwlOptions()
+    opt.n_dim = 1
+    assert L.gwl_create(None, 16, s.ctypes.data, p.ctypes.data, dets, 1, C.byref(opt), C.byref(out)) == -1
+    assert L.gwl_create(f.ctypes.data, 16, s.ctypes.data, p.ctypes.data, dets, 0, C.byref(opt), C.byref(out)) == -1
+    assert b"n_det" in L.gwl_last_error()
+    bad = f.copy()
+    bad[5] += 0.01
+    assert L.gwl_create(bad.ctypes.data, 16, s.ctypes.data, p.ctypes.data, dets, 1, C.byref(opt), C.byref(out)) == -1
+    assert b"uniformly" in L.gwl_last_error()
+    neg = -p
+    assert L.gwl_create(f.ctypes.data, 16, s.ctypes.data, neg.ctypes.data, dets, 1, C.byref(opt), C.byref(out)) == -1
+    opt.precision = 7
+    assert L.gwl_create(f.ctypes.data, 16, s.ctypes.data, p.ctypes.data, dets, 1, C.byref(opt), C.byref(out)) == -1
+    assert L.gwl_loglike(None, None, 1, None, None) == -1
+    assert out.value is None
