@@ -162,6 +162,34 @@ int ns_replace(gwl_ctx* ctx, const double* live_u, const double* live_lnl, int64
                double scale, const double* chol, double* out_u, double* out_lnl, int32_t* out_nacc,
                int32_t* out_start, void* stream);
 
+/* Size of the fixed device array used by gwl_loglike_static (16 MiB). */
+#define GWL_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* gwl_loglike for callers that cannot allocate device memory at call time.
+ * (The paper has no counterpart; this is an interface addition.)  Some hosts
+ * hand all free device memory to their own caching allocator, so a raw
+ * cudaMalloc can fail; others run in loops that must not block, and
+ * cudaMalloc/cudaFree may synchronise the device.  This entry point computes
+ * exactly what gwl_loglike computes, with the same kernels, but takes its
+ * per-call scratch (per-proposal coefficients and per-window partial sums)
+ * from a fixed file-scope device array of GWL_STATIC_SCRATCH_BYTES, which the
+ * library's CUDA module reserves on every device that loads it and keeps until
+ * the process exits.  It calls no cudaMalloc, cudaFree or allocating routine;
+ * per-kernel profiling (gwl_profile) is suspended for the call.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - A batch needs about (272 + 16 n_det ceil(n_bins / window)) bytes per
+ *     proposal, window being the context's bin window (gwl_set_tuning); a
+ *     batch that does not fit returns GWL_ERR_ARG with the sizes in the error
+ *     text and launches nothing.
+ *   - All calls on a device share the array and it keeps the previous call's
+ *     contents (each call rewrites what it reads; the batch's work counters
+ *     are cleared on the stream first).  Calls whose kernels overlap on the
+ *     GPU -- from different streams, threads or contexts -- race on the array
+ *     and must be serialised by the caller. */
+int gwl_loglike_static(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, void* stream);
+
 /* Synchronise the context's last stream and return the latched device
  * status (GWL_OK or GWL_ERR_TIMEOUT); clears the latch. */
 int gwl_sync(gwl_ctx* ctx);

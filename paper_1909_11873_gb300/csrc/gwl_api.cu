@@ -94,6 +94,18 @@ int check_ctx(const gwl_ctx* c) {
 
 }  // namespace
 
+namespace gwl {
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+}  // namespace gwl
+
 extern "C" {
 
 const char* gwl_last_error(void) { return g_err.c_str(); }

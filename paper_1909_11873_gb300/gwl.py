@@ -23,7 +23,7 @@ N_PARAM = 11
 MAX_DET = 4
 
 # exported symbols declared in include/gwl.h
-EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_grad", "gwl_waveform", "ns_replace",
+EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "gwl_grad", "gwl_waveform", "ns_replace",
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error")
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
         L.gwl_create.argtypes = [P, i64, P, P, P, i32, C.POINTER(GwlOptions), C.POINTER(P)]
         L.gwl_loglike.argtypes = [P, P, i64, P, P]
         L.gwl_loglike_host.argtypes = [P, P, i64, P, P]
+        L.gwl_loglike_static.argtypes = [P, P, i64, P, P]
         L.gwl_grad.argtypes = [P, P, i64, P, P, P]
         L.gwl_waveform.argtypes = [P, P, i64, P, P]
         L.ns_replace.argtypes = [P, P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, P]
@@ -183,6 +184,11 @@ class Context:
     def gwl_loglike_host(self, theta: np.ndarray, lnl: np.ndarray, stream=None):
         _check(lib().gwl_loglike_host(self._h, _ptr(theta), theta.shape[0], _ptr(lnl), _stream(stream)),
                "gwl_loglike_host")
+
+    def gwl_loglike_static(self, theta, lnl, stream=None):
+        """gwl_loglike with its scratch in the library's fixed device array (no allocation)."""
+        _check(lib().gwl_loglike_static(self._h, _ptr(theta), theta.shape[0], _ptr(lnl), _stream(stream)),
+               "gwl_loglike_static")
 
     def gwl_grad(self, theta, lnl, grad, stream=None):
         _check(lib().gwl_grad(self._h, _ptr(theta), theta.shape[0], _ptr(lnl), _ptr(grad), _stream(stream)),
