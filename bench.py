@@ -52,8 +52,9 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--soak-seconds", type=float, default=1.5)
     ap.add_argument("--impl", default="gwl", choices=["gwl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -118,7 +119,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "untimed soak of the same step + the timed steps"}
 
 
 def measured_peaks():
@@ -180,7 +181,7 @@ def run_gwl(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(ctx, steps, warmup, host=False):
+    def timed(ctx, steps, warmup, host=False, soak=0.0):
         pin_t = torch.from_numpy(theta_np).pin_memory() if host else None
         pin_l = torch.empty(BATCH, dtype=torch.float64).pin_memory() if host else None
         for _ in range(warmup):
@@ -189,6 +190,13 @@ def run_gwl(args):
             else:
                 ctx.gwl_loglike(theta, lnl, stream)
         torch.cuda.synchronize()
+        # untimed soak at load so that the clock sampler sees the GPU under this workload
+        t_end = time.perf_counter() + soak
+        while time.perf_counter() < t_end:
+            for _ in range(50):
+                flush.fill_(1.0)
+                ctx.gwl_loglike(theta, lnl, stream)
+            torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -217,7 +225,7 @@ def run_gwl(args):
         ctxs[prec] = ctx
         steps = args.steps if prec == gwl.GWL_MIXED else max(3, args.steps // 5)
         with ClockSampler(local) as clk:
-            ms, launches, wall = timed(ctx, steps, args.warmup)
+            ms, launches, wall = timed(ctx, steps, args.warmup, soak=args.soak_seconds)
         ctx.gwl_sync()
         results[prec] = dict(ms=ms, launches=launches, clocks=clk.summary(), steps=steps, wall=wall)
 

@@ -10,8 +10,8 @@
 #include "gwl_internal.h"
 
 namespace gwl {
-cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, cudaStream_t st);
 int64_t partials_needed(const gwl_ctx* c, int64_t B);
+int64_t work_needed(const gwl_ctx* c);
 }  // namespace gwl
 
 namespace {
@@ -62,6 +62,13 @@ int ensure_scratch(gwl_ctx* c, int64_t B) {
     if ((e = dev_alloc(c, &c->d_pf, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
     if ((e = dev_alloc(c, &c->d_pc, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
     c->prop_cap = cap;
+  }
+  const int64_t wneed = gwl::work_needed(c);
+  if (wneed > c->work_cap) {
+    dev_free(c, c->d_work, c->work_cap);
+    c->work_cap = 0;
+    if ((e = dev_alloc(c, &c->d_work, wneed)) != cudaSuccess) return cuda_fail(e, "scratch");
+    c->work_cap = wneed;
   }
   const int64_t need = gwl::partials_needed(c, B);
   if (need > c->partials_cap) {
@@ -356,6 +363,7 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_pc, c->prop_cap);
   dev_free(c, c->d_partials, c->partials_cap);
   dev_free(c, c->d_io, c->io_cap);
+  dev_free(c, c->d_work, c->work_cap);
   dev_free(c, c->d_status, 4);
   delete c;
 }

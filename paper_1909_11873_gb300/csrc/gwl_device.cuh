@@ -33,10 +33,14 @@ constexpr int kNBasis = 8;  // basis functions besides f itself
 constexpr int kStatusTimeout = 1;
 
 // Per-bin table rows.
-//  mixed: float [bh 0..7 | bl 0..7 | fh fl | G_d (re, im) x n_det | pad]  (16-B multiple)
-//  fp64 : double [b 0..7 | f | G_d (re, im) x n_det | pad]               (16-B multiple)
-__host__ __device__ constexpr int mixed_row_floats(int ndet) { return ((18 + 2 * ndet) + 3) / 4 * 4; }
-__host__ __device__ constexpr int f64_row_doubles(int ndet) { return ((9 + 2 * ndet) + 1) / 2 * 2; }
+//  mixed: float [bh 0..7 | bl 0..7 | fh fl | G_d (re, im) x n_det | pad]
+//  fp64 : double [b 0..7 | f | G_d (re, im) x n_det | pad]
+// Rows are padded to an odd number of 16-byte units: when the 32 lanes of a
+// warp read 32 consecutive rows with 16-byte vector loads, the 8 lanes of each
+// shared-memory phase then hit 8 different 16-byte bank groups (no conflicts).
+__host__ __device__ constexpr int odd_units(int units) { return (units % 2) ? units : units + 1; }
+__host__ __device__ constexpr int mixed_row_floats(int ndet) { return 4 * odd_units((18 + 2 * ndet + 3) / 4); }
+__host__ __device__ constexpr int f64_row_doubles(int ndet) { return 2 * odd_units((9 + 2 * ndet + 1) / 2); }
 
 // Per-proposal coefficients read warp-uniformly by the bin loop.
 struct alignas(16) PropMixed {
@@ -137,20 +141,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ------------------------------------------------------------- prologue
-struct Prologue {
-  double c[kNBasis];    // basis coefficients [cycles]
-  double tau[kMaxDet];  // tc + dt_d [s]
-  double Kr[kMaxDet], Ki[kMaxDet];
-  double hh;
-  int ncut;
-  int flag;
-};
+// Constants of the model evaluated at compile time.
+constexpr double kLnPi = 1.1447298858494002;            // ln(pi)
+constexpr double kLn4 = 1.3862943611198906;             // ln(4)
+constexpr double kLn6 = 1.791759469228055;              // ln(6)
+constexpr double kSix32 = 14.696938456699069;           // 6^{3/2}
+constexpr double kAmpConst = 0.21278751013966343;       // sqrt(5/24) pi^{-2/3}
 
 // Full 11-D parameter vector from the sampled coordinates of one row.
 __device__ __forceinline__ void expand_theta(const SegInfo& s, const double* row, double th[11]) {
 #pragma unroll
   for (int k = 0; k < 11; ++k) th[k] = s.fixed[k];
   for (int i = 0; i < s.n_dim; ++i) th[s.param_map[i]] = row[i];
+}
+
+__device__ __forceinline__ bool physical(const double th[11]) {
+  bool ok = th[1] > 0.0 && th[1] <= 1.0 && th[0] > 0.0 && th[4] > 0.0;
+#pragma unroll
+  for (int k = 0; k < 11; ++k) ok = ok && isfinite(th[k]);
+  return ok;
 }
 
 // Number of bins with freqs[j] <= fc (bins ascend): estimate from the grid,
@@ -167,55 +176,22 @@ __device__ __forceinline__ int count_bins_le(const SegInfo& s, double fc) {
   return (int)(j + 1);
 }
 
-__device__ inline void antenna_dev(const double* g, double psi, double ra, double dec, double gmst, double& Fp,
-                                   double& Fx, double& dt) {
-  double sl, cl, sd, cd, sp, cp;
-  sincos(ra - gmst, &sl, &cl);
-  sincos(dec, &sd, &cd);
-  sincos(psi, &sp, &cp);
-  const double n[3] = {cd * cl, cd * sl, sd};
-  const double eE[3] = {-sl, cl, 0.0};
-  const double eN[3] = {-sd * cl, -sd * sl, cd};
-  double X[3], Y[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    X[i] = cp * eE[i] + sp * eN[i];
-    Y[i] = -sp * eE[i] + cp * eN[i];
-  }
-  // F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2; contract via the arm projections
-  const double* x = g + 3;
-  const double* y = g + 6;
-  double xX = x[0] * X[0] + x[1] * X[1] + x[2] * X[2];
-  double xY = x[0] * Y[0] + x[1] * Y[1] + x[2] * Y[2];
-  double yX = y[0] * X[0] + y[1] * X[1] + y[2] * X[2];
-  double yY = y[0] * Y[0] + y[1] * Y[1] + y[2] * Y[2];
-  Fp = 0.5 * ((xX * xX - xY * xY) - (yX * yX - yY * yY));
-  Fx = (xX * xY - yX * yY);
-  dt = -(g[0] * n[0] + g[1] * n[1] + g[2] * n[2]) / kC;
-}
+// Intrinsic part: masses and spins -> basis coefficients c_m [cycles], the
+// constant PN phase [cycles], the frequency cut and the amplitude A.  FP64.
+struct Intrinsic {
+  double c[kNBasis];
+  double ccyc;
+  double amp;
+  int ncut;
+};
 
-// theta (11-D) -> basis coefficients, delays, K_d, <h|h>, cut.  FP64.
-__device__ inline void prologue(const SegInfo& s, const double th[11], Prologue& o) {
+__device__ inline void prologue_intrinsic(const SegInfo& s, const double th[11], Intrinsic& o) {
   const double mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dl = th[4];
-  const double iota = th[5], psi = th[6], ra = th[7], dec = th[8], tc = th[9], phic = th[10];
-  bool ok = q > 0.0 && q <= 1.0 && mc > 0.0 && dl > 0.0;
-#pragma unroll
-  for (int k = 0; k < 11; ++k) ok = ok && isfinite(th[k]);
-  o.flag = ok ? 0 : 1;
-  o.hh = 0.0;
-  o.ncut = 0;
-#pragma unroll
-  for (int m = 0; m < kNBasis; ++m) o.c[m] = 0.0;
-#pragma unroll
-  for (int d = 0; d < kMaxDet; ++d) o.tau[d] = o.Kr[d] = o.Ki[d] = 0.0;
-  if (!ok) return;
-
   const double opq = 1.0 + q;
   const double eta = q / (opq * opq);
   const double delta = (1.0 - q) / opq;  // sqrt(1 - 4 eta) for q <= 1
-  const double x1 = 1.0 / opq, x2 = q / opq;
+  const double x1 = 1.0 / opq, x2 = q * x1;
   const double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
-  const double Ms = mc * pow(eta, -0.6) * kTsun;  // total mass [s]
   const double eta2 = eta * eta;
 
   // PN phase coefficients phi_k
@@ -236,48 +212,69 @@ __device__ inline void prologue(const SegInfo& s, const double th[11], Prologue&
                      (5345.0 / 36.0) * eta2 * eta) * chis +
                     delta * (-25150083775.0 / 3048192.0 + (26804935.0 / 6048.0) * eta - (1985.0 / 48.0) * eta2) * chia;
 
-  // v^k = (a f)^{k/3} with a = pi M: fold a^{k/3} into the coefficients.
-  const double a = kPi * Ms;
-  const double la = log(a);
-  const double a13 = cbrt(a);
+  // a = pi M [s], M = Mc eta^{-3/5}; v^k = (a f)^{k/3}: fold a^{k/3} into c_m.
+  const double lmc = log(kPi * kTsun * mc);  // ln(pi Mc T_sun)
+  const double la = lmc - 0.6 * log(eta);    // ln a
+  const double a13 = exp(la * (1.0 / 3.0));
   const double am13 = 1.0 / a13;
+  const double am23 = am13 * am13;
   const double pref = 3.0 / (128.0 * eta) / (2.0 * kPi);  // radians -> cycles
-  o.c[0] = pref * am13 * am13 * am13 * am13 * am13;                         // f^{-5/3}
-  o.c[1] = pref * p2 / a;                                                   // f^{-1}
-  o.c[2] = pref * p3 * am13 * am13;                                         // f^{-2/3}
-  o.c[3] = pref * p4 * am13;                                                // f^{-1/3}
-  o.c[4] = pref * p5c;                                                      // ln f   (3 ln v = ln a + ln f)
-  o.c[5] = pref * a13 * (p6c - (6848.0 / 21.0) * log(4.0) - (6848.0 / 63.0) * la);  // f^{1/3}
-  o.c[6] = pref * a13 * (-6848.0 / 63.0);                                  // f^{1/3} ln f
-  o.c[7] = pref * p7 * a13 * a13;                                           // f^{2/3}
+  o.c[0] = pref * am23 * am23 * am13;  // f^{-5/3}
+  o.c[1] = pref * p2 * am23 * am13;     // f^{-1}
+  o.c[2] = pref * p3 * am23;            // f^{-2/3}
+  o.c[3] = pref * p4 * am13;            // f^{-1/3}
+  o.c[4] = pref * p5c;                  // ln f    (3 ln v = ln a + ln f)
+  o.c[5] = pref * a13 * (p6c - (6848.0 / 21.0) * kLn4 - (6848.0 / 63.0) * la);  // f^{1/3}
+  o.c[6] = pref * a13 * (-6848.0 / 63.0);                                     // f^{1/3} ln f
+  o.c[7] = pref * p7 * a13 * a13;                                             // f^{2/3}
   // constant PN phase [cycles]: phi5 (1 + ln a - 3 ln v_lso), v_lso = 6^{-1/2}
-  const double ccyc = pref * p5c * (1.0 + la + 1.5 * log(6.0));
-
-  // frequency cut
+  o.ccyc = pref * p5c * (1.0 + la + 1.5 * kLn6);
   if (s.fcut_mode == 0) {
-    const double fisco = 1.0 / (pow(6.0, 1.5) * kPi * Ms);
-    o.ncut = count_bins_le(s, fisco);
+    const double a3 = a13 * a13 * a13;  // = pi M
+    o.ncut = count_bins_le(s, 1.0 / (kSix32 * a3));
   } else {
     o.ncut = (int)s.M;
   }
+  // A = sqrt(5/24) pi^{-2/3} (Mc T_sun)^{5/6} c / dL
+  o.amp = kAmpConst * exp((5.0 / 6.0) * (lmc - kLnPi)) * kC / (dl * kMpc);
+}
 
-  const double amp = sqrt(5.0 / 24.0) * pow(kPi, -2.0 / 3.0) * pow(mc * kTsun, 5.0 / 6.0) * kC / (dl * kMpc);
+// Extrinsic part: sky position, polarisation angle and inclination ->
+// per-detector delay tau_d = tc + dt_d and complex response
+// P_d = F+_d (1 + cos^2 i)/2 - i Fx_d cos i.  FP64.
+struct Extrinsic {
+  double tau[kMaxDet];
+  double Pr[kMaxDet], Pi[kMaxDet];
+};
+
+__device__ inline void prologue_extrinsic(const SegInfo& s, const double th[11], Extrinsic& o) {
+  const double iota = th[5], psi = th[6], ra = th[7], dec = th[8], tc = th[9];
+  double sl, cl, sd, cd, sp, cp;
+  sincos(ra - s.gmst, &sl, &cl);
+  sincos(dec, &sd, &cd);
+  sincos(psi, &sp, &cp);
   const double ci = cos(iota);
-  const double cfrac = ccyc - rint(ccyc);
-  double sa, ca;
-  sincos(phic + 0.25 * kPi - 2.0 * kPi * cfrac, &sa, &ca);
-  double hh = 0.0;
-  for (int d = 0; d < s.n_det; ++d) {
-    double Fp, Fx, dt;
-    antenna_dev(s.geom + 9 * d, psi, ra, dec, s.gmst, Fp, Fx, dt);
-    o.tau[d] = tc + dt;
-    const double pr = Fp * 0.5 * (1.0 + ci * ci);
-    const double pi = -Fx * ci;
-    o.Kr[d] = amp * (pr * ca - pi * sa);
-    o.Ki[d] = amp * (pr * sa + pi * ca);
-    if (o.ncut > 0) hh += amp * amp * (pr * pr + pi * pi) * s.H[(int64_t)d * s.M + o.ncut - 1];
+  const double n0 = cd * cl, n1 = cd * sl, n2 = sd;
+  // wave-frame axes X = cos psi e_E + sin psi e_N, Y = -sin psi e_E + cos psi e_N
+  const double X0 = -cp * sl - sp * sd * cl, X1 = cp * cl - sp * sd * sl, X2 = sp * cd;
+  const double Y0 = sp * sl - cp * sd * cl, Y1 = -sp * cl - cp * sd * sl, Y2 = cp * cd;
+  const double hp = 0.5 * (1.0 + ci * ci);
+#pragma unroll
+  for (int d = 0; d < kMaxDet; ++d) {
+    if (d >= s.n_det) {
+      o.tau[d] = o.Pr[d] = o.Pi[d] = 0.0;
+      continue;
+    }
+    const double* g = s.geom + 9 * d;
+    const double xX = g[3] * X0 + g[4] * X1 + g[5] * X2, xY = g[3] * Y0 + g[4] * Y1 + g[5] * Y2;
+    const double yX = g[6] * X0 + g[7] * X1 + g[8] * X2, yY = g[6] * Y0 + g[7] * Y1 + g[8] * Y2;
+    // F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2
+    const double Fp = 0.5 * ((xX * xX - xY * xY) - (yX * yX - yY * yY));
+    const double Fx = xX * xY - yX * yY;
+    o.tau[d] = tc - (g[0] * n0 + g[1] * n1 + g[2] * n2) / kC;
+    o.Pr[d] = Fp * hp;
+    o.Pi[d] = -Fx * ci;
   }
-  o.hh = hh;
 }
 
 }  // namespace gwl

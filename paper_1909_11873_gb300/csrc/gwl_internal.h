@@ -35,10 +35,12 @@ struct gwl_ctx {
   int64_t partials_cap = 0;      // in doubles
   double* d_io = nullptr;        // staging for the host-buffer entry points
   int64_t io_cap = 0;            // in doubles
-  int* d_status = nullptr;       // [0] latched status bits, [1] max cut over the batch
+  int* d_work = nullptr;         // [0] largest cut of the batch, [1 + w] proposal counter of window w
+  int64_t work_cap = 0;          // in ints
+  int* d_status = nullptr;       // [0] latched status bits
 
   // tuning
-  int window_mixed = 1024, window_f64 = 512, slice = 64, ctas_per_sm = 2;
+  int window_mixed = 640, window_f64 = 384, slice = 64, ctas_per_sm = 3;
 
   int64_t launches = 0;
   int64_t bytes = 0;

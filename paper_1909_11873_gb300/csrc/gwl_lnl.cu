@@ -7,14 +7,19 @@
 // template, regrouped so that per bin and detector only the phase, one
 // sincos and four multiply-adds remain.
 //
-// Work decomposition: the bins are cut into windows of W bins; a work item is
-// (window, slice of proposals).  A CTA stages its window's table rows in
-// shared memory with one bulk asynchronous copy (cp.async.bulk, completion on
-// an mbarrier, bounded wait), then each warp takes one proposal at a time with
-// its 32 lanes striding over the window's bins; the per-lane sums are reduced
-// with warp shuffles and written as one partial per (proposal, window).  A
-// final kernel adds the partials of each proposal in window order (FP64) and
-// forms lnL.  No atomics touch the sums, so results are deterministic.
+// Work decomposition: a prologue kernel turns each parameter row into its
+// coefficients (two warps per 32 rows: one for the masses and spins, one for
+// the sky position and orientation).  The bins are cut into windows of W bins;
+// each CTA of the bin-loop kernel is assigned a window, stages the window's
+// table rows in shared memory with one bulk asynchronous copy (cp.async.bulk,
+// completion on an mbarrier, bounded wait), and its warps then take proposals
+// one at a time from the window's atomic counter, the 32 lanes striding over
+// the window's bins two bins per iteration.  Per-lane sums are reduced with
+// warp shuffles.  When the whole batch fits one window the warp forms lnL at
+// once; otherwise it writes one partial per (proposal, window) and a final
+// kernel adds them in window order (FP64).  The counters only schedule work:
+// no atomics touch the sums, so results are deterministic.  The three kernels
+// are chained with programmatic dependent launch.
 //
 // Precision modes:
 //   GWL_FP64  -- phase as an FP64 FMA chain, FP64 sincospi, FP64 sums.
@@ -33,72 +38,253 @@
 
 namespace gwl {
 
+// ---------------------------------------------------------------- launch helper
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------- prologue
-__global__ void k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B, int precision,
-                           PropMixed* __restrict__ pm, PropF64* __restrict__ pf, PropCommon* __restrict__ pc,
-                           int* __restrict__ status) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int ncut = 0;
-  if (p < B) {
-    double th[11];
-    expand_theta(s, theta + p * s.n_dim, th);
-    Prologue o;
-    prologue(s, th, o);
-    PropCommon cm;
+// 128 threads per CTA, 32 rows.  The FP64 work of a row is spread over four
+// warps so that more warps keep the (narrow) FP64 pipe busy:
+//   phase 1  warp 0: ln(pi Mc T), ln(eta) -> a^{1/3}, amplitude, frequency cut
+//            warp 1: PN phase coefficients phi_k (polynomials in eta, spins)
+//            warp 2: sky direction -> per-detector delays tau_d
+//            warp 3: sin/cos of psi, cos of iota
+//   phase 2  warp 0: basis coefficients c_m and the constant PN phase
+//            warp 1: antenna patterns -> complex responses P_d
+//   phase 3  warp 2: K_d, <h|h>, cut; the batch's largest cut
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B,
+                                                  PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
+                                                  PropCommon* __restrict__ pc, int* __restrict__ work) {
+  __shared__ double sh_la[32], sh_a13[32], sh_amp[32], sh_ccyc[32];
+  __shared__ double sh_phi[6][32];
+  __shared__ double sh_sky[4][32];   // sin/cos of (ra - gmst), sin/cos of dec
+  __shared__ double sh_ori[3][32];   // sin psi, cos psi, cos iota
+  __shared__ double sh_P[2 * kMaxDet][32];
+  __shared__ int sh_ncut[32];
+  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+  const int64_t p = (int64_t)blockIdx.x * 32 + lane;
+  const bool valid = p < B;
+  double th[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) th[k] = 1.0;
+  if (valid) expand_theta(s, theta + p * s.n_dim, th);
+  const bool ok = valid && physical(th);
+  if (!ok) {  // keep every transcendental below on a harmless argument
+    th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
+  }
+  const double mc = th[0], q = th[1];
+  const double opq = 1.0 + q;
+  const double eta = q / (opq * opq);
+
+  // ---- phase 1
+  if (role == 0) {
+    const double lmc = log(kPi * kTsun * mc);  // ln(pi Mc T_sun)
+    const double la = lmc - 0.6 * log(eta);    // ln a, a = pi M
+    const double a13 = exp(la * (1.0 / 3.0));
+    sh_la[lane] = la;
+    sh_a13[lane] = a13;
+    sh_amp[lane] = kAmpConst * exp((5.0 / 6.0) * (lmc - kLnPi)) * kC / (th[4] * kMpc);
+    int ncut = (int)s.M;
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, 1.0 / (kSix32 * a13 * a13 * a13));
+    sh_ncut[lane] = ok ? ncut : 0;
+  } else if (role == 1) {
+    const double chi1 = th[2], chi2 = th[3];
+    const double delta = (1.0 - q) / opq;
+    const double x1 = 1.0 / opq, x2 = q * x1;
+    const double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
+    const double eta2 = eta * eta;
+    const double beta =
+        ((113.0 / 12.0) * x1 * x1 + 6.25 * eta) * chi1 + ((113.0 / 12.0) * x2 * x2 + 6.25 * eta) * chi2;
+    const double gam = (732985.0 / 2268.0 - (24260.0 / 81.0) * eta - (340.0 / 9.0) * eta2) * chis +
+                       (732985.0 / 2268.0 + (140.0 / 9.0) * eta) * delta * chia;
+    sh_phi[0][lane] = (20.0 / 9.0) * (743.0 / 336.0 + (11.0 / 4.0) * eta);
+    sh_phi[1][lane] = -16.0 * kPi + 4.0 * beta;
+    sh_phi[2][lane] = 10.0 * (3058673.0 / 1016064.0 + (5429.0 / 1008.0) * eta + (617.0 / 144.0) * eta2) -
+                      10.0 * (79.0 / 8.0) * eta * chi1 * chi2;
+    sh_phi[3][lane] = kPi * (38645.0 / 756.0 - (65.0 / 9.0) * eta) - gam;
+    sh_phi[4][lane] = 11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kGammaE +
+                      eta * (-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) +
+                      (76055.0 / 1728.0) * eta2 - (127825.0 / 1296.0) * eta2 * eta +
+                      kPi * ((2270.0 / 3.0) * delta * chia + (2270.0 / 3.0 - 520.0 * eta) * chis);
+    sh_phi[5][lane] =
+        kPi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta2) +
+        (-25150083775.0 / 3048192.0 + (10566655595.0 / 762048.0) * eta - (1042165.0 / 3024.0) * eta2 +
+         (5345.0 / 36.0) * eta2 * eta) * chis +
+        delta * (-25150083775.0 / 3048192.0 + (26804935.0 / 6048.0) * eta - (1985.0 / 48.0) * eta2) * chia;
+  } else if (role == 2) {
+    double sl, cl, sd, cd;
+    sincos(th[7] - s.gmst, &sl, &cl);
+    sincos(th[8], &sd, &cd);
+    sh_sky[0][lane] = sl;
+    sh_sky[1][lane] = cl;
+    sh_sky[2][lane] = sd;
+    sh_sky[3][lane] = cd;
+    const double n0 = cd * cl, n1 = cd * sl, n2 = sd;
+    if (valid) {
+#pragma unroll
+      for (int d = 0; d < kMaxDet; ++d) {
+        double tau = 0.0;
+        if (d < s.n_det && ok) {
+          const double* g = s.geom + 9 * d;
+          tau = th[9] - (g[0] * n0 + g[1] * n1 + g[2] * n2) / kC;
+        }
+        if (MIXED) split_f64(tau, pm[p].th[d], pm[p].tl[d]);
+        else pf[p].tau[d] = tau;
+      }
+    }
+  } else {
+    double sp, cp;
+    sincos(th[6], &sp, &cp);
+    sh_ori[0][lane] = sp;
+    sh_ori[1][lane] = cp;
+    sh_ori[2][lane] = cos(th[5]);
+  }
+  __syncthreads();
+
+  // ---- phase 2
+  if (role == 0) {
+    const double la = sh_la[lane], a13 = sh_a13[lane];
+    const double am13 = 1.0 / a13, am23 = am13 * am13;
+    const double pref = 3.0 / (128.0 * eta) / (2.0 * kPi);  // radians -> cycles
+    double c[kNBasis];
+    c[0] = pref * am23 * am23 * am13;                                                   // f^{-5/3}
+    c[1] = pref * sh_phi[0][lane] * am23 * am13;                                        // f^{-1}
+    c[2] = pref * sh_phi[1][lane] * am23;                                               // f^{-2/3}
+    c[3] = pref * sh_phi[2][lane] * am13;                                               // f^{-1/3}
+    c[4] = pref * sh_phi[3][lane];                                                      // ln f
+    c[5] = pref * a13 * (sh_phi[4][lane] - (6848.0 / 21.0) * kLn4 - (6848.0 / 63.0) * la);  // f^{1/3}
+    c[6] = pref * a13 * (-6848.0 / 63.0);                                               // f^{1/3} ln f
+    c[7] = pref * sh_phi[5][lane] * a13 * a13;                                          // f^{2/3}
+    // constant PN phase [cycles]: phi5 (1 + ln a - 3 ln v_lso), v_lso = 6^{-1/2}
+    sh_ccyc[lane] = pref * sh_phi[3][lane] * (1.0 + la + 1.5 * kLn6);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < kNBasis; ++m) {
+        const double cm = ok ? c[m] : 0.0;
+        if (MIXED) split_f64(cm, pm[p].ch[m], pm[p].cl[m]);
+        else pf[p].c[m] = cm;
+      }
+    }
+  } else if (role == 1) {
+    const double sl = sh_sky[0][lane], cl = sh_sky[1][lane], sd = sh_sky[2][lane], cd = sh_sky[3][lane];
+    const double sp = sh_ori[0][lane], cp = sh_ori[1][lane], ci = sh_ori[2][lane];
+    // wave-frame axes X = cos psi e_E + sin psi e_N, Y = -sin psi e_E + cos psi e_N
+    const double X0 = -cp * sl - sp * sd * cl, X1 = cp * cl - sp * sd * sl, X2 = sp * cd;
+    const double Y0 = sp * sl - cp * sd * cl, Y1 = -sp * cl - cp * sd * sl, Y2 = cp * cd;
+    const double hp = 0.5 * (1.0 + ci * ci);
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
-      cm.Kr[d] = o.Kr[d];
-      cm.Ki[d] = o.Ki[d];
+      double Pr = 0.0, Pi = 0.0;
+      if (d < s.n_det) {
+        const double* g = s.geom + 9 * d;
+        const double xX = g[3] * X0 + g[4] * X1 + g[5] * X2, xY = g[3] * Y0 + g[4] * Y1 + g[5] * Y2;
+        const double yX = g[6] * X0 + g[7] * X1 + g[8] * X2, yY = g[6] * Y0 + g[7] * Y1 + g[8] * Y2;
+        // F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2
+        Pr = 0.5 * ((xX * xX - xY * xY) - (yX * yX - yY * yY)) * hp;
+        Pi = -(xX * xY - yX * yY) * ci;
+      }
+      sh_P[2 * d][lane] = Pr;
+      sh_P[2 * d + 1][lane] = Pi;
     }
-    cm.hh = o.hh;
-    cm.ncut = o.flag ? 0 : o.ncut;
-    cm.flag = o.flag;
-    pc[p] = cm;
-    if (precision == GWL_MIXED) {
-      PropMixed q;
-#pragma unroll
-      for (int m = 0; m < kNBasis; ++m) split_f64(o.c[m], q.ch[m], q.cl[m]);
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) split_f64(o.tau[d], q.th[d], q.tl[d]);
-      pm[p] = q;
-    } else {
-      PropF64 q;
-#pragma unroll
-      for (int m = 0; m < kNBasis; ++m) q.c[m] = o.c[m];
-#pragma unroll
-      for (int d = 0; d < kMaxDet; ++d) q.tau[d] = o.tau[d];
-      pf[p] = q;
-    }
-    ncut = cm.ncut;
   }
-  // largest cut of the batch: one atomic per warp
+  __syncthreads();
+
+  // ---- phase 3
+  if (role == 2) {
+    const int ncut = sh_ncut[lane];
+    if (valid) {
+      PropCommon cm;
+      double hh = 0.0;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) ncut = max(ncut, __shfl_xor_sync(0xffffffffu, ncut, off));
-  if ((threadIdx.x & 31) == 0 && ncut > 0) atomicMax(&status[1], ncut);
+      for (int d = 0; d < kMaxDet; ++d) cm.Kr[d] = cm.Ki[d] = 0.0;
+      if (ok) {
+        const double amp = sh_amp[lane];
+        const double ccyc = sh_ccyc[lane];
+        // K_d = A P_d e^{i (phic + pi/4 - 2 pi ccyc)}
+        double ang = th[10] + 0.25 * kPi - 2.0 * kPi * (ccyc - rint(ccyc));
+        ang -= 2.0 * kPi * rint(ang * (0.5 / kPi));
+        double sa, ca;
+        if (MIXED) {
+          float sf, cf;
+          sincosf((float)ang, &sf, &cf);
+          sa = sf;
+          ca = cf;
+        } else {
+          sincos(ang, &sa, &ca);
+        }
+        for (int d = 0; d < s.n_det; ++d) {
+          const double Pr = sh_P[2 * d][lane], Pi = sh_P[2 * d + 1][lane];
+          cm.Kr[d] = amp * (Pr * ca - Pi * sa);
+          cm.Ki[d] = amp * (Pr * sa + Pi * ca);
+          if (ncut > 0) hh += amp * amp * (Pr * Pr + Pi * Pi) * s.H[(int64_t)d * s.M + ncut - 1];
+        }
+      }
+      cm.hh = hh;
+      cm.ncut = ncut;
+      cm.flag = ok ? 0 : 1;
+      pc[p] = cm;
+    }
+    // largest cut of the batch: one atomic per warp
+    int nm = valid ? ncut : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
+    if (lane == 0 && nm > 0) atomicMax(&work[0], nm);
+  }
 }
 
 // ---------------------------------------------------------------- per-bin bodies
+// Row element counts actually read (without the trailing pad unit).
+template <int NDET> struct RowM { static constexpr int n = (18 + 2 * NDET + 3) / 4 * 4; };
+template <int NDET> struct RowD { static constexpr int n = (9 + 2 * NDET + 1) / 2 * 2; };
+
 template <int NDET>
-__device__ __forceinline__ void bin_mixed(const float* __restrict__ row, const float (&ch)[kNBasis],
+__device__ __forceinline__ void load_row(const float* __restrict__ row, float (&v)[RowM<NDET>::n]) {
+#pragma unroll
+  for (int k = 0; k < RowM<NDET>::n / 4; ++k)
+    *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
+}
+template <int NDET>
+__device__ __forceinline__ void load_row(const double* __restrict__ row, double (&v)[RowD<NDET>::n]) {
+#pragma unroll
+  for (int k = 0; k < RowD<NDET>::n / 2; ++k)
+    *reinterpret_cast<double2*>(&v[2 * k]) = reinterpret_cast<const double2*>(row)[k];
+}
+
+template <int NDET>
+__device__ __forceinline__ void bin_mixed(const float (&v)[RowM<NDET>::n], const float (&ch)[kNBasis],
                                           const float (&cl)[kNBasis], const float (&th)[NDET],
                                           const float (&tl)[NDET], float (&U)[NDET], float (&V)[NDET]) {
   // common phase S = sum_m c_m B_m as an unevaluated float pair (s, lo)
   float s, lo;
   {
     float e;
-    two_prod(ch[0], row[0], s, e);
-    lo = __fmaf_rn(cl[0], row[0], __fmaf_rn(ch[0], row[kNBasis], e));
+    two_prod(ch[0], v[0], s, e);
+    lo = __fmaf_rn(cl[0], v[0], __fmaf_rn(ch[0], v[kNBasis], e));
   }
 #pragma unroll
   for (int m = 1; m < kNBasis; ++m) {
-    const float bh = row[m], bl = row[kNBasis + m];
+    const float bh = v[m], bl = v[kNBasis + m];
     float p, e, t, q;
     two_prod(ch[m], bh, p, e);
     two_sum(s, p, t, q);
     s = t;
     lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
   }
-  const float fh = row[16], fl = row[17];
+  const float fh = v[16], fl = v[17];
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     // r_d = S + tau_d f, then its fractional part in [-1/2, 1/2]
@@ -107,11 +293,14 @@ __device__ __forceinline__ void bin_mixed(const float* __restrict__ row, const f
     e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
     two_sum(s, p, t, q);
     const float l = lo + (e + q);
-    const float n = rintf(t);
+    // nearest integer of t by the 1.5 * 2^23 shift (exact for |t| < 2^22); the
+    // shift runs on the FMA pipe, whereas a rounding instruction would occupy
+    // the narrow conversion pipe
+    const float n = __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
     const float fr = __fadd_rn(__fsub_rn(t, n), l);  // t - n is exact
     float sn, cs;
     __sincosf(6.283185307179586f * fr, &sn, &cs);
-    const float gr = row[18 + 2 * d], gi = row[19 + 2 * d];
+    const float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
     // (gr + i gi)(cs - i sn)
     U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
     V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
@@ -119,18 +308,18 @@ __device__ __forceinline__ void bin_mixed(const float* __restrict__ row, const f
 }
 
 template <int NDET>
-__device__ __forceinline__ void bin_f64(const double* __restrict__ row, const double (&c)[kNBasis],
+__device__ __forceinline__ void bin_f64(const double (&v)[RowD<NDET>::n], const double (&c)[kNBasis],
                                         const double (&tau)[NDET], double (&U)[NDET], double (&V)[NDET]) {
-  double r = c[0] * row[0];
+  double r = c[0] * v[0];
 #pragma unroll
-  for (int m = 1; m < kNBasis; ++m) r = fma(c[m], row[m], r);
-  const double f = row[8];
+  for (int m = 1; m < kNBasis; ++m) r = fma(c[m], v[m], r);
+  const double f = v[8];
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     const double rd = fma(tau[d], f, r);
     double sn, cs;
     sincospi(2.0 * rd, &sn, &cs);
-    const double gr = row[9 + 2 * d], gi = row[10 + 2 * d];
+    const double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
     U[d] = fma(gr, cs, fma(gi, sn, U[d]));
     V[d] = fma(gi, cs, fma(-gr, sn, V[d]));
   }
@@ -139,33 +328,106 @@ __device__ __forceinline__ void bin_f64(const double* __restrict__ row, const do
 // ---------------------------------------------------------------- windowed bin loop
 struct WinArgs {
   const void* tab;
-  int row_elems;  // floats (mixed) or doubles (fp64) per row
+  int row_elems;  // floats (mixed) or doubles (fp64) per row, padded
   int64_t M;
   int CH;         // bins per window
   int64_t B;
-  int slice;      // proposals per work item
   int nw_total;   // ceil(M / CH)
   const PropCommon* pc;
   const void* prop;  // PropMixed* or PropF64*
-  double* partials;  // [B][nw_total][2 NDET]
-  int* status;
+  void* partials;    // [B][nw_total][2 NDET] float (mixed) or double (fp64)
+  int* work;         // [0] largest cut, [1 + w] proposal counter of window w
+  int* status;       // latched error bits
 };
 
+template <int NDET, bool MIXED, typename Acc>
+__device__ __forceinline__ void window_sums(const WinArgs& a, const void* __restrict__ smv, int64_t p, int j0,
+                                            int jend, int lane, Acc (&Ud)[NDET], Acc (&Vd)[NDET]) {
+  if constexpr (MIXED) {
+    const float* sm = reinterpret_cast<const float*>(smv);
+    const PropMixed* P = reinterpret_cast<const PropMixed*>(a.prop) + p;
+    float ch[kNBasis], cl[kNBasis], th[NDET], tl[NDET];
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) {
+      ch[m] = P->ch[m];
+      cl[m] = P->cl[m];
+    }
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      th[d] = P->th[d];
+      tl[d] = P->tl[d];
+    }
+    float U[NDET], V[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
+    int j = j0 + lane;
+    for (; j + 32 < jend; j += 64) {
+      float v0[RowM<NDET>::n], v1[RowM<NDET>::n];
+      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v0);
+      load_row<NDET>(sm + (int64_t)(j + 32 - j0) * a.row_elems, v1);
+      bin_mixed<NDET>(v0, ch, cl, th, tl, U, V);
+      bin_mixed<NDET>(v1, ch, cl, th, tl, U, V);
+    }
+    if (j < jend) {
+      float v0[RowM<NDET>::n];
+      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v0);
+      bin_mixed<NDET>(v0, ch, cl, th, tl, U, V);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        U[d] += __shfl_xor_sync(0xffffffffu, U[d], off);
+        V[d] += __shfl_xor_sync(0xffffffffu, V[d], off);
+      }
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      Ud[d] = U[d];
+      Vd[d] = V[d];
+    }
+  } else {
+    const double* sm = reinterpret_cast<const double*>(smv);
+    const PropF64* P = reinterpret_cast<const PropF64*>(a.prop) + p;
+    double c[kNBasis], tau[NDET];
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) c[m] = P->c[m];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) tau[d] = P->tau[d];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = 0.0;
+    for (int j = j0 + lane; j < jend; j += 32) {
+      double v[RowD<NDET>::n];
+      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
+      bin_f64<NDET>(v, c, tau, Ud, Vd);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
+        Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
+      }
+  }
+}
+
 template <int NDET, bool MIXED>
-__global__ void __launch_bounds__(256) k_window(WinArgs a) {
+__global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
+  cudaGridDependencySynchronize();  // the prologue's outputs are visible past this point
   using Elem = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
 
-  const int maxn = a.status[1];
+  using Acc = Elem;  // per-window partial sums: FP32 (mixed) or FP64
+  const int maxn = a.work[0];
   int nw = (maxn + a.CH - 1) / a.CH;
   if (nw > a.nw_total) nw = a.nw_total;
-  const int64_t nsl = (a.B + a.slice - 1) / a.slice;
-  const int64_t nitems = (int64_t)nw * nsl;
-  if ((int64_t)blockIdx.x >= nitems) return;  // uniform across the CTA
+  if (nw < 1) return;  // no proposal has a bin in band
+  const int G = gridDim.x;
+  const int wstep = G >= nw ? nw : G;
+  int w = G >= nw ? (int)(blockIdx.x % nw) : (int)blockIdx.x;
 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -173,18 +435,15 @@ __global__ void __launch_bounds__(256) k_window(WinArgs a) {
   }
   __syncthreads();
 
-  int loaded = -1;
   uint32_t parity = 0;
-  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int w = (int)(item / nsl);
-    const int64_t sl = item - (int64_t)w * nsl;
+  for (; w < nw; w += wstep) {
     const int j0 = w * a.CH;
     int64_t j1l = (int64_t)j0 + a.CH;
     if (j1l > a.M) j1l = a.M;
     if (j1l > maxn) j1l = maxn;
-    const int j1 = (int)j1l;
-    if (w != loaded) {
-      __syncthreads();  // every warp is done with the previous window
+    const int j1 = j1l > j0 ? (int)j1l : j0;
+    __syncthreads();  // every warp is done with the previous window
+    if (j1 > j0) {
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
         const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
@@ -193,73 +452,24 @@ __global__ void __launch_bounds__(256) k_window(WinArgs a) {
       }
       if (!mbar_wait_bounded(&bar, parity, a.status)) return;
       parity ^= 1u;
-      loaded = w;
     }
-    const int64_t pbeg = sl * a.slice;
-    const int64_t pend = pbeg + a.slice < a.B ? pbeg + a.slice : a.B;
-    for (int64_t p = pbeg + warp; p < pend; p += nwarps) {
+    int* ctr = a.work + 1 + w;
+    while (true) {
+      int pi = 0;
+      if (lane == 0) pi = atomicAdd(ctr, 1);
+      pi = __shfl_sync(0xffffffffu, pi, 0);
+      if (pi >= a.B) break;
+      const int64_t p = pi;
       const int ncut = a.pc[p].ncut;
       if (ncut <= j0) continue;
-      const int jend = ncut < j1 ? ncut : j1;
-      if constexpr (MIXED) {
-        const PropMixed* P = reinterpret_cast<const PropMixed*>(a.prop) + p;
-        float ch[kNBasis], cl[kNBasis], th[NDET], tl[NDET];
-#pragma unroll
-        for (int m = 0; m < kNBasis; ++m) {
-          ch[m] = P->ch[m];
-          cl[m] = P->cl[m];
-        }
+      Acc U[NDET], V[NDET];
+      window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
+      if (lane == 0) {
+        Acc* o = reinterpret_cast<Acc*>(a.partials) + ((int64_t)p * a.nw_total + w) * (2 * NDET);
 #pragma unroll
         for (int d = 0; d < NDET; ++d) {
-          th[d] = P->th[d];
-          tl[d] = P->tl[d];
-        }
-        float U[NDET], V[NDET];
-#pragma unroll
-        for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
-        for (int j = j0 + lane; j < jend; j += 32)
-          bin_mixed<NDET>(sm + (int64_t)(j - j0) * a.row_elems, ch, cl, th, tl, U, V);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            U[d] += __shfl_xor_sync(0xffffffffu, U[d], off);
-            V[d] += __shfl_xor_sync(0xffffffffu, V[d], off);
-          }
-        if (lane == 0) {
-          double* o = a.partials + ((int64_t)p * a.nw_total + w) * (2 * NDET);
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            o[2 * d] = (double)U[d];
-            o[2 * d + 1] = (double)V[d];
-          }
-        }
-      } else {
-        const PropF64* P = reinterpret_cast<const PropF64*>(a.prop) + p;
-        double c[kNBasis], tau[NDET];
-#pragma unroll
-        for (int m = 0; m < kNBasis; ++m) c[m] = P->c[m];
-#pragma unroll
-        for (int d = 0; d < NDET; ++d) tau[d] = P->tau[d];
-        double U[NDET], V[NDET];
-#pragma unroll
-        for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0;
-        for (int j = j0 + lane; j < jend; j += 32)
-          bin_f64<NDET>(sm + (int64_t)(j - j0) * a.row_elems, c, tau, U, V);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            U[d] += __shfl_xor_sync(0xffffffffu, U[d], off);
-            V[d] += __shfl_xor_sync(0xffffffffu, V[d], off);
-          }
-        if (lane == 0) {
-          double* o = a.partials + ((int64_t)p * a.nw_total + w) * (2 * NDET);
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            o[2 * d] = U[d];
-            o[2 * d + 1] = V[d];
-          }
+          o[2 * d] = U[d];
+          o[2 * d + 1] = V[d];
         }
       }
     }
@@ -267,9 +477,12 @@ __global__ void __launch_bounds__(256) k_window(WinArgs a) {
 }
 
 // ---------------------------------------------------------------- combination
-template <int NDET>
-__global__ void k_finalize(const PropCommon* __restrict__ pc, const double* __restrict__ partials, int64_t B,
-                           int CH, int nw_total, double* __restrict__ lnl) {
+// lnL_p = sum_d [Re K_d U_d - Im K_d V_d] - <h|h>/2, with U, V summed over the
+// proposal's windows in window order (FP64).
+template <int NDET, typename Acc>
+__global__ void k_finalize(const PropCommon* __restrict__ pc, const Acc* __restrict__ partials, int64_t B, int CH,
+                           int nw_total, double* __restrict__ lnl) {
+  cudaGridDependencySynchronize();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= B) return;
   const PropCommon c = pc[p];
@@ -278,14 +491,14 @@ __global__ void k_finalize(const PropCommon* __restrict__ pc, const double* __re
     return;
   }
   const int nwp = (c.ncut + CH - 1) / CH;
-  const double* q = partials + (int64_t)p * nw_total * (2 * NDET);
+  const Acc* q = partials + (int64_t)p * nw_total * (2 * NDET);
   double acc = 0.0;
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     double U = 0.0, V = 0.0;
     for (int w = 0; w < nwp; ++w) {
-      U += q[w * (2 * NDET) + 2 * d];
-      V += q[w * (2 * NDET) + 2 * d + 1];
+      U += (double)q[w * (2 * NDET) + 2 * d];
+      V += (double)q[w * (2 * NDET) + 2 * d + 1];
     }
     acc += c.Kr[d] * U - c.Ki[d] * V;
   }
@@ -324,24 +537,41 @@ __global__ void k_waveform(SegInfo s, const PropF64* __restrict__ pf, const Prop
 }
 
 // ---------------------------------------------------------------- launchers
+static int window_of(const gwl_ctx* c, int precision) {
+  int CH = precision == GWL_MIXED ? c->window_mixed : c->window_f64;
+  return CH > c->M ? (int)c->M : CH;
+}
+
+int64_t partials_needed(const gwl_ctx* c, int64_t B) {
+  const int CH = window_of(c, c->opt.precision);
+  const int64_t nw = (c->M + CH - 1) / CH;
+  return B * nw * 2 * c->n_det;
+}
+
+int64_t work_needed(const gwl_ctx* c) {
+  const int CH = window_of(c, c->opt.precision);
+  return 1 + (c->M + CH - 1) / CH;
+}
+
 template <int NDET, bool MIXED>
 static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_window<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  {
-    ProfScope ps(c, GWL_KERNEL_BINS, st);
-    k_window<NDET, MIXED><<<grid, 256, smem, st>>>(a);
+  static size_t smem_set = 0;  // per template instance: raise the dynamic shared-memory limit when it grows
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_window<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
   }
+  ProfScope ps(c, GWL_KERNEL_BINS, st);
+  cudaError_t e = launch_pdl(k_window<NDET, MIXED>, dim3(grid), dim3(256), smem, st, a);
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
 template <int NDET>
 static cudaError_t run_pipeline(gwl_ctx* c, int64_t B, double* lnl, cudaStream_t st) {
   const bool mixed = c->opt.precision == GWL_MIXED;
-  int CH = mixed ? c->window_mixed : c->window_f64;
-  if (CH > c->M) CH = (int)c->M;
+  const int CH = window_of(c, c->opt.precision);
   const int nw_total = (int)((c->M + CH - 1) / CH);
   WinArgs a;
   a.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
@@ -349,51 +579,47 @@ static cudaError_t run_pipeline(gwl_ctx* c, int64_t B, double* lnl, cudaStream_t
   a.M = c->M;
   a.CH = CH;
   a.B = B;
-  a.slice = c->slice;
   a.nw_total = nw_total;
   a.pc = c->d_pc;
   a.prop = mixed ? (const void*)c->d_pm : (const void*)c->d_pf;
   a.partials = c->d_partials;
+  a.work = c->d_work;
   a.status = c->d_status;
   const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double));
-  const int64_t nsl = (B + c->slice - 1) / c->slice;
-  int64_t items = nsl * nw_total;
-  int64_t grid = (int64_t)c->num_sms * c->ctas_per_sm;
-  if (grid > items) grid = items;
-  if (grid < 1) grid = 1;
-  cudaError_t e = mixed ? run_window<NDET, true>(c, a, (int)grid, smem, st)
-                        : run_window<NDET, false>(c, a, (int)grid, smem, st);
+  const int grid = c->num_sms * c->ctas_per_sm;
+  cudaError_t e = mixed ? run_window<NDET, true>(c, a, grid, smem, st) : run_window<NDET, false>(c, a, grid, smem, st);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_COMBINE, st);
-    k_finalize<NDET><<<(unsigned)((B + 255) / 256), 256, 0, st>>>(c->d_pc, c->d_partials, B, CH, nw_total, lnl);
+    const dim3 g((unsigned)((B + 63) / 64)), b(64);  // small CTAs: the combination is FP64 latency-bound
+    if (mixed)
+      e = launch_pdl(k_finalize<NDET, float>, g, b, 0, st, (const PropCommon*)c->d_pc,
+                     (const float*)c->d_partials, B, CH, nw_total, lnl);
+    else
+      e = launch_pdl(k_finalize<NDET, double>, g, b, 0, st, (const PropCommon*)c->d_pc,
+                     (const double*)c->d_partials, B, CH, nw_total, lnl);
   }
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
-int64_t partials_needed(const gwl_ctx* c, int64_t B) {
-  const int CHm = c->window_mixed < c->M ? c->window_mixed : (int)c->M;
-  const int CHf = c->window_f64 < c->M ? c->window_f64 : (int)c->M;
-  const int CH = c->opt.precision == GWL_MIXED ? CHm : CHf;
-  const int64_t nw = (c->M + CH - 1) / CH;
-  return B * nw * 2 * c->n_det;
-}
-
-cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(c->d_status + 1, 0, sizeof(int), st);
+cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int precision, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c), st);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
-    k_prologue<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(c->seg, theta, B, c->opt.precision, c->d_pm, c->d_pf,
-                                                             c->d_pc, c->d_status);
+    const unsigned nb = (unsigned)((B + 31) / 32);
+    if (precision == GWL_MIXED)
+      k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work);
+    else
+      k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work);
   }
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
-  cudaError_t e = launch_prologue(c, theta, B, st);
+  cudaError_t e = launch_prologue(c, theta, B, c->opt.precision, st);
   if (e != cudaSuccess) return e;
   switch (c->n_det) {
     case 1: return run_pipeline<1>(c, B, lnl, st);
@@ -404,11 +630,8 @@ cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* l
 }
 
 cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st) {
-  // the waveform is always produced in FP64: run the FP64 prologue
-  const int saved = c->opt.precision;
-  c->opt.precision = GWL_FP64;
-  cudaError_t e = launch_prologue(c, theta, B, st);
-  c->opt.precision = saved;
+  // the waveform is always produced in FP64
+  cudaError_t e = launch_prologue(c, theta, B, GWL_FP64, st);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((c->M + 255) / 256), (unsigned)B);
   k_waveform<<<grid, 256, 0, st>>>(c->seg, c->d_pf, c->d_pc, c->d_tab_f64, c->row_doubles, h);

@@ -1,0 +1,76 @@
+"""Run one workload through the library a fixed number of times (for profilers such as ncu).
+
+  python -m paper_1909_11873_gb300.profile_run --config c2 --precision mixed --iters 5 [--entry loglike|grad]
+
+The event is synthetic and seeded; its injection is produced by the library's
+own template, so no test infrastructure is involved.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def device_event(name, seed):
+    import torch
+
+    from . import gwl
+    from . import inputs as I
+
+    cache = {}
+
+    def zctx(ev):
+        if "c" not in cache:
+            full = I.Sampling(np.arange(11, dtype=np.int32), np.zeros(11), np.zeros(11, dtype=np.int32),
+                              np.zeros(11), np.ones(11), np.zeros(11, dtype=np.int32))
+            cache["c"] = gwl.Context(ev.freqs, np.zeros_like(ev.strain), ev.psd, ev.geom, gwl.GWL_FP64, ev.fcut_mode,
+                                     ev.gmst, ev.t_ref, full)
+        return cache["c"]
+
+    def waveform(ev, th):
+        h = gwl.waveform(zctx(ev), torch.from_numpy(np.ascontiguousarray(th[None])).cuda()).cpu().numpy()[0]
+        return h[..., 0] + 1j * h[..., 1]
+
+    def snr2(ev, th):
+        return -2.0 * float(gwl.loglike(zctx(ev), torch.from_numpy(np.ascontiguousarray(th[None])).cuda()).cpu()[0])
+
+    ev = I.make_event(name, seed, waveform, snr2)
+    for c in cache.values():
+        c.close()
+    return ev
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--iters", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--entry", default="loglike", choices=["loglike", "grad"])
+    a = ap.parse_args()
+    import torch
+
+    from . import build, gwl
+    from . import inputs as I
+
+    build.build()
+    ev = device_event(a.config, a.seed)
+    B = a.batch or I.CONFIGS[a.config]["batch"]
+    th = torch.from_numpy(I.reduced(I.proposals(ev, B, a.seed), ev.sampling)).cuda()
+    ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED if a.precision == "mixed" else gwl.GWL_FP64)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(th)
+    for _ in range(a.iters):
+        if a.entry == "grad":
+            ctx.gwl_grad(th, out, grad)
+        else:
+            ctx.gwl_loglike(th, out)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    print(f"{a.config} {a.precision} {a.entry} B={B} iters={a.iters} lnL[0]={out[0].item():.6f}")
+
+
+if __name__ == "__main__":
+    main()
