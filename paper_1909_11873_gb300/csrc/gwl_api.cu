@@ -81,6 +81,22 @@ int ensure_scratch(gwl_ctx* c, int64_t B) {
   return GWL_OK;
 }
 
+int ensure_bytes(gwl_ctx* c, void** p, int64_t* cap, int64_t need) {
+  if (need <= *cap) return GWL_OK;
+  const int64_t n = need > 2 * *cap ? need : 2 * *cap;
+  if (*p) {
+    cudaFree(*p);
+    c->bytes -= *cap;
+  }
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(p, (size_t)n);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch");
+  c->bytes += n;
+  *cap = n;
+  return GWL_OK;
+}
+
 int ensure_io(gwl_ctx* c, int64_t n) {
   if (n <= c->io_cap) return GWL_OK;
   dev_free(c, c->d_io, c->io_cap);
@@ -190,6 +206,20 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     }
     if ((e = gwl::launch_build_tables(c, d_strain, d_psd, 0)) != cudaSuccess) { rc = cuda_fail(e, "build tables"); break; }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "build tables"); break; }
+    // normalisation: the largest whole-band <h|h> weight H_d[M-1] -> O(1)
+    double hmax = 0.0;
+    for (int d = 0; d < n_det; ++d) {
+      double hd = 0.0;
+      if ((e = cudaMemcpy(&hd, c->d_H + (int64_t)d * n_bins + n_bins - 1, sizeof(double), cudaMemcpyDeviceToHost)) !=
+          cudaSuccess)
+        break;
+      hmax = hd > hmax ? hd : hmax;
+    }
+    if (e != cudaSuccess) { rc = cuda_fail(e, "normalise tables"); break; }
+    const double scale = hmax > 0.0 && std::isfinite(hmax) ? std::ldexp(1.0, (int)std::lround(0.5 * std::log2(hmax))) : 1.0;
+    if ((e = gwl::launch_scale_tables(c, 1.0 / scale, 0)) != cudaSuccess) { rc = cuda_fail(e, "normalise tables"); break; }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "normalise tables"); break; }
+    c->seg.amp_scale = scale;
     gwl::SegInfo& s = c->seg;
     s.freqs = c->d_freqs;
     s.H = c->d_H;
@@ -265,10 +295,19 @@ int gwl_waveform(gwl_ctx* c, const double* theta_dev, int64_t B, double* h_dev, 
 }
 
 int gwl_grad(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, double* grad_dev, void* stream) {
-  (void)theta_dev; (void)lnl_dev; (void)grad_dev; (void)stream; (void)B;
   int rc = check_ctx(c);
   if (rc) return rc;
-  return fail(GWL_ERR_ARG, "gwl_grad: not available in this build");
+  if (B < 0) return fail(GWL_ERR_ARG, "B < 0");
+  if (B == 0) return GWL_OK;
+  if (!theta_dev || !lnl_dev || !grad_dev) return fail(GWL_ERR_ARG, "null device pointer");
+  if ((rc = ensure_scratch(c, B))) return rc;
+  if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * B))) return rc;
+  if ((rc = ensure_bytes(c, &c->d_gpartials, &c->gpartials_cap, gwl::grad_partials_bytes(c, B)))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  cudaError_t e = gwl::launch_grad(c, theta_dev, B, lnl_dev, grad_dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_grad");
+  return GWL_OK;
 }
 
 int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, int64_t worst, double lnl_star,
@@ -365,6 +404,8 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_io, c->io_cap);
   dev_free(c, c->d_work, c->work_cap);
   dev_free(c, c->d_status, 4);
+  if (c->d_pgrad) cudaFree(c->d_pgrad);
+  if (c->d_gpartials) cudaFree(c->d_gpartials);
   delete c;
 }
 

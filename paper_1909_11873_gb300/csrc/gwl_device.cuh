@@ -68,6 +68,11 @@ struct SegInfo {
   int n_det;
   int fcut_mode;
   double f0, df, gmst, t_ref;
+  // Exact power of two close to sqrt(<h|h> weight of the whole band): the
+  // tables hold G / amp_scale and H / amp_scale^2 and the prologue multiplies
+  // the amplitude by amp_scale, so that every quantity is O(1) -- well inside
+  // the FP32 range used by the mixed path and the FP32 tangents.
+  double amp_scale;
   // sampled-parameter map
   int n_dim;
   int param_map[11];
@@ -176,105 +181,271 @@ __device__ __forceinline__ int count_bins_le(const SegInfo& s, double fc) {
   return (int)(j + 1);
 }
 
-// Intrinsic part: masses and spins -> basis coefficients c_m [cycles], the
-// constant PN phase [cycles], the frequency cut and the amplitude A.  FP64.
-struct Intrinsic {
-  double c[kNBasis];
-  double ccyc;
-  double amp;
-  int ncut;
+// ------------------------------------------------------------- model formulas
+// Written once as templates over the scalar type: T = double for the
+// likelihood, T = Tan<...> (FP64 value with tangents) for the gradient.
+
+// Forward-mode tangent type: the value stays FP64 (bit-identical arithmetic to
+// the plain path); the N tangents, and a shadow copy of the value used for
+// the tangent arithmetic, are kept in G (float on the fast pipe, or double).
+template <int N, class G>
+struct Tan {
+  double v;
+  G vt;
+  G d[N];
 };
 
-__device__ inline void prologue_intrinsic(const SegInfo& s, const double th[11], Intrinsic& o) {
-  const double mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], dl = th[4];
-  const double opq = 1.0 + q;
-  const double eta = q / (opq * opq);
-  const double delta = (1.0 - q) / opq;  // sqrt(1 - 4 eta) for q <= 1
-  const double x1 = 1.0 / opq, x2 = q * x1;
-  const double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
-  const double eta2 = eta * eta;
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> tan_const(double x) {
+  Tan<N, G> r;
+  r.v = x;
+  r.vt = (G)x;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (G)0;
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator+(const Tan<N, G>& a, const Tan<N, G>& b) {
+  Tan<N, G> r;
+  r.v = a.v + b.v;
+  r.vt = a.vt + b.vt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator-(const Tan<N, G>& a, const Tan<N, G>& b) {
+  Tan<N, G> r;
+  r.v = a.v - b.v;
+  r.vt = a.vt - b.vt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator-(const Tan<N, G>& a) {
+  Tan<N, G> r;
+  r.v = -a.v;
+  r.vt = -a.vt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator*(const Tan<N, G>& a, const Tan<N, G>& b) {
+  Tan<N, G> r;
+  r.v = a.v * b.v;
+  r.vt = a.vt * b.vt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.vt + a.vt * b.d[i];
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator/(const Tan<N, G>& a, const Tan<N, G>& b) {
+  Tan<N, G> r;
+  r.v = a.v / b.v;
+  r.vt = a.vt / b.vt;
+  const G ib = (G)1 / b.vt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.vt * b.d[i]) * ib;
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator+(const Tan<N, G>& a, double b) {
+  Tan<N, G> r = a;
+  r.v += b;
+  r.vt += (G)b;
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator+(double b, const Tan<N, G>& a) { return a + b; }
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator-(const Tan<N, G>& a, double b) { return a + (-b); }
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator-(double b, const Tan<N, G>& a) { return (-a) + b; }
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator*(const Tan<N, G>& a, double b) {
+  Tan<N, G> r;
+  r.v = a.v * b;
+  r.vt = a.vt * (G)b;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * (G)b;
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator*(double b, const Tan<N, G>& a) { return a * b; }
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator/(const Tan<N, G>& a, double b) { return a * (1.0 / b); }
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> operator/(double a, const Tan<N, G>& b) { return tan_const<N, G>(a) / b; }
 
-  // PN phase coefficients phi_k
-  const double p2 = (20.0 / 9.0) * (743.0 / 336.0 + (11.0 / 4.0) * eta);
-  const double beta = ((113.0 / 12.0) * x1 * x1 + 6.25 * eta) * chi1 + ((113.0 / 12.0) * x2 * x2 + 6.25 * eta) * chi2;
-  const double p3 = -16.0 * kPi + 4.0 * beta;
-  const double p4 = 10.0 * (3058673.0 / 1016064.0 + (5429.0 / 1008.0) * eta + (617.0 / 144.0) * eta2) -
-                    10.0 * (79.0 / 8.0) * eta * chi1 * chi2;
-  const double gam = (732985.0 / 2268.0 - (24260.0 / 81.0) * eta - (340.0 / 9.0) * eta2) * chis +
-                     (732985.0 / 2268.0 + (140.0 / 9.0) * eta) * delta * chia;
-  const double p5c = kPi * (38645.0 / 756.0 - (65.0 / 9.0) * eta) - gam;
-  const double p6c = 11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kGammaE +
-                     eta * (-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) + (76055.0 / 1728.0) * eta2 -
-                     (127825.0 / 1296.0) * eta2 * eta +
-                     kPi * ((2270.0 / 3.0) * delta * chia + (2270.0 / 3.0 - 520.0 * eta) * chis);
-  const double p7 = kPi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta2) +
-                    (-25150083775.0 / 3048192.0 + (10566655595.0 / 762048.0) * eta - (1042165.0 / 3024.0) * eta2 +
-                     (5345.0 / 36.0) * eta2 * eta) * chis +
-                    delta * (-25150083775.0 / 3048192.0 + (26804935.0 / 6048.0) * eta - (1985.0 / 48.0) * eta2) * chia;
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> tan_lift(const Tan<N, G>& a, double fv, G ft, G dft) {
+  Tan<N, G> r;
+  r.v = fv;
+  r.vt = ft;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = dft * a.d[i];
+  return r;
+}
+// double overloads visible next to the tangent-type templates in this namespace
+__device__ __forceinline__ double exp(double x) { return ::exp(x); }
+__device__ __forceinline__ double log(double x) { return ::log(x); }
+__device__ __forceinline__ double cos(double x) { return ::cos(x); }
+__device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
 
-  // a = pi M [s], M = Mc eta^{-3/5}; v^k = (a f)^{k/3}: fold a^{k/3} into c_m.
-  const double lmc = log(kPi * kTsun * mc);  // ln(pi Mc T_sun)
-  const double la = lmc - 0.6 * log(eta);    // ln a
-  const double a13 = exp(la * (1.0 / 3.0));
-  const double am13 = 1.0 / a13;
-  const double am23 = am13 * am13;
-  const double pref = 3.0 / (128.0 * eta) / (2.0 * kPi);  // radians -> cycles
-  o.c[0] = pref * am23 * am23 * am13;  // f^{-5/3}
-  o.c[1] = pref * p2 * am23 * am13;     // f^{-1}
-  o.c[2] = pref * p3 * am23;            // f^{-2/3}
-  o.c[3] = pref * p4 * am13;            // f^{-1/3}
-  o.c[4] = pref * p5c;                  // ln f    (3 ln v = ln a + ln f)
-  o.c[5] = pref * a13 * (p6c - (6848.0 / 21.0) * kLn4 - (6848.0 / 63.0) * la);  // f^{1/3}
-  o.c[6] = pref * a13 * (-6848.0 / 63.0);                                     // f^{1/3} ln f
-  o.c[7] = pref * p7 * a13 * a13;                                             // f^{2/3}
-  // constant PN phase [cycles]: phi5 (1 + ln a - 3 ln v_lso), v_lso = 6^{-1/2}
-  o.ccyc = pref * p5c * (1.0 + la + 1.5 * kLn6);
-  if (s.fcut_mode == 0) {
-    const double a3 = a13 * a13 * a13;  // = pi M
-    o.ncut = count_bins_le(s, 1.0 / (kSix32 * a3));
-  } else {
-    o.ncut = (int)s.M;
-  }
-  // A = sqrt(5/24) pi^{-2/3} (Mc T_sun)^{5/6} c / dL
-  o.amp = kAmpConst * exp((5.0 / 6.0) * (lmc - kLnPi)) * kC / (dl * kMpc);
+// For the transcendental functions the shadow values are taken from the FP64
+// results: an argument whose shadow has drifted (a phase of many cycles, say)
+// would otherwise spoil the derivative.
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> exp(const Tan<N, G>& a) {
+  const double fv = ::exp(a.v);
+  const G ft = (G)fv;
+  return tan_lift(a, fv, ft, ft);
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> log(const Tan<N, G>& a) {
+  const double fv = ::log(a.v);
+  return tan_lift(a, fv, (G)fv, (G)(1.0 / a.v));
+}
+template <int N, class G>
+__device__ __forceinline__ void sincos(const Tan<N, G>& a, Tan<N, G>* s, Tan<N, G>* c) {
+  double sv, cv;
+  ::sincos(a.v, &sv, &cv);
+  const G st = (G)sv, ct = (G)cv;
+  *s = tan_lift(a, sv, st, ct);
+  *c = tan_lift(a, cv, ct, -st);
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> cos(const Tan<N, G>& a) {
+  Tan<N, G> s, c;
+  sincos(a, &s, &c);
+  return c;
+}
+// x - nearest integer: the integer shift carries no derivative.
+__device__ __forceinline__ double frac_near(double x) { return x - rint(x); }
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G> frac_near(const Tan<N, G>& a) {
+  Tan<N, G> r = a;
+  r.v = a.v - rint(a.v);
+  r.vt = (G)r.v;  // the reduced value, not the drifted shadow of a large one
+  return r;
+}
+__device__ __forceinline__ double val(double x) { return x; }
+template <int N, class G>
+__device__ __forceinline__ double val(const Tan<N, G>& a) { return a.v; }
+
+// TaylorF2 phase coefficients phi_k (aligned spins; the 2.5PN and 3PN terms
+// carry the ln v parts separately).
+template <class T>
+struct PNCoeffs {
+  T eta, p2, p3, p4, p5c, p6c, p7;
+};
+
+template <class T>
+__device__ __forceinline__ PNCoeffs<T> pn_coeffs(const T& q, const T& chi1, const T& chi2) {
+  PNCoeffs<T> P;
+  const T opq = q + 1.0;
+  const T eta = q / (opq * opq);
+  const T delta = (1.0 - q) / opq;  // sqrt(1 - 4 eta) for q <= 1
+  const T x1 = 1.0 / opq, x2 = q * x1;
+  const T chis = (chi1 + chi2) * 0.5, chia = (chi1 - chi2) * 0.5;
+  const T eta2 = eta * eta;
+  const T beta = ((113.0 / 12.0) * x1 * x1 + 6.25 * eta) * chi1 + ((113.0 / 12.0) * x2 * x2 + 6.25 * eta) * chi2;
+  const T gam = (732985.0 / 2268.0 - (24260.0 / 81.0) * eta - (340.0 / 9.0) * eta2) * chis +
+                ((140.0 / 9.0) * eta + 732985.0 / 2268.0) * delta * chia;
+  P.eta = eta;
+  P.p2 = (743.0 / 336.0 + (11.0 / 4.0) * eta) * (20.0 / 9.0);
+  P.p3 = 4.0 * beta - 16.0 * kPi;
+  P.p4 = (3058673.0 / 1016064.0 + (5429.0 / 1008.0) * eta + (617.0 / 144.0) * eta2) * 10.0 -
+         (10.0 * 79.0 / 8.0) * eta * chi1 * chi2;
+  P.p5c = kPi * (38645.0 / 756.0 - (65.0 / 9.0) * eta) - gam;
+  P.p6c = (11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kGammaE) +
+          eta * (-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) + (76055.0 / 1728.0) * eta2 -
+          (127825.0 / 1296.0) * eta2 * eta +
+          kPi * ((2270.0 / 3.0) * delta * chia + ((2270.0 / 3.0) - 520.0 * eta) * chis);
+  P.p7 = kPi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta2) +
+         ((-25150083775.0 / 3048192.0) + (10566655595.0 / 762048.0) * eta - (1042165.0 / 3024.0) * eta2 +
+          (5345.0 / 36.0) * eta2 * eta) * chis +
+         delta * ((-25150083775.0 / 3048192.0) + (26804935.0 / 6048.0) * eta - (1985.0 / 48.0) * eta2) * chia;
+  return P;
 }
 
-// Extrinsic part: sky position, polarisation angle and inclination ->
-// per-detector delay tau_d = tc + dt_d and complex response
-// P_d = F+_d (1 + cos^2 i)/2 - i Fx_d cos i.  FP64.
-struct Extrinsic {
-  double tau[kMaxDet];
-  double Pr[kMaxDet], Pi[kMaxDet];
+// Mass scale: ln a and a^{1/3} with a = pi M = pi Mc eta^{-3/5} T_sun, and the
+// amplitude A = sqrt(5/24) pi^{-2/3} (Mc T_sun)^{5/6} c / dL.
+template <class T>
+struct Scale {
+  T la, a13, amp;
 };
+template <class T>
+__device__ __forceinline__ Scale<T> mass_scale(const T& mc, const T& eta, const T& dl, double amp_scale) {
+  Scale<T> o;
+  const T lmc = log(mc * (kPi * kTsun));  // ln(pi Mc T_sun)
+  o.la = lmc - 0.6 * log(eta);
+  o.a13 = exp(o.la * (1.0 / 3.0));
+  o.amp = exp((lmc - kLnPi) * (5.0 / 6.0)) * (kAmpConst * kC / kMpc * amp_scale) / dl;
+  return o;
+}
 
-__device__ inline void prologue_extrinsic(const SegInfo& s, const double th[11], Extrinsic& o) {
-  const double iota = th[5], psi = th[6], ra = th[7], dec = th[8], tc = th[9];
-  double sl, cl, sd, cd, sp, cp;
-  sincos(ra - s.gmst, &sl, &cl);
-  sincos(dec, &sd, &cd);
-  sincos(psi, &sp, &cp);
-  const double ci = cos(iota);
-  const double n0 = cd * cl, n1 = cd * sl, n2 = sd;
-  // wave-frame axes X = cos psi e_E + sin psi e_N, Y = -sin psi e_E + cos psi e_N
-  const double X0 = -cp * sl - sp * sd * cl, X1 = cp * cl - sp * sd * sl, X2 = sp * cd;
-  const double Y0 = sp * sl - cp * sd * cl, Y1 = -sp * cl - cp * sd * sl, Y2 = cp * cd;
-  const double hp = 0.5 * (1.0 + ci * ci);
-#pragma unroll
-  for (int d = 0; d < kMaxDet; ++d) {
-    if (d >= s.n_det) {
-      o.tau[d] = o.Pr[d] = o.Pi[d] = 0.0;
-      continue;
-    }
-    const double* g = s.geom + 9 * d;
-    const double xX = g[3] * X0 + g[4] * X1 + g[5] * X2, xY = g[3] * Y0 + g[4] * Y1 + g[5] * Y2;
-    const double yX = g[6] * X0 + g[7] * X1 + g[8] * X2, yY = g[6] * Y0 + g[7] * Y1 + g[8] * Y2;
-    // F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2
-    const double Fp = 0.5 * ((xX * xX - xY * xY) - (yX * yX - yY * yY));
-    const double Fx = xX * xY - yX * yY;
-    o.tau[d] = tc - (g[0] * n0 + g[1] * n1 + g[2] * n2) / kC;
-    o.Pr[d] = Fp * hp;
-    o.Pi[d] = -Fx * ci;
-  }
+// Basis coefficients c_m [cycles] and the constant PN phase [cycles]:
+// v^k = (a f)^{k/3}, so a^{k/3} folds into c_m; 3 ln v = ln a + ln f.
+template <class T>
+__device__ __forceinline__ void basis_coeffs(const PNCoeffs<T>& P, const Scale<T>& S, T (&c)[kNBasis], T& ccyc) {
+  const T am13 = 1.0 / S.a13, am23 = am13 * am13;
+  const T pref = (3.0 / (128.0 * 2.0 * kPi)) / P.eta;  // radians -> cycles
+  c[0] = pref * am23 * am23 * am13;                                                // f^{-5/3}
+  c[1] = pref * P.p2 * am23 * am13;                                                // f^{-1}
+  c[2] = pref * P.p3 * am23;                                                       // f^{-2/3}
+  c[3] = pref * P.p4 * am13;                                                       // f^{-1/3}
+  c[4] = pref * P.p5c;                                                             // ln f
+  c[5] = pref * S.a13 * (P.p6c - (6848.0 / 21.0) * kLn4 - (6848.0 / 63.0) * S.la);  // f^{1/3}
+  c[6] = pref * S.a13 * (-6848.0 / 63.0);                                          // f^{1/3} ln f
+  c[7] = pref * P.p7 * S.a13 * S.a13;                                              // f^{2/3}
+  ccyc = pref * P.p5c * (S.la + (1.0 + 1.5 * kLn6));  // phi5 (1 + ln a - 3 ln v_lso), v_lso = 6^{-1/2}
+}
+
+// Sky direction n = (cos dec cos lam, cos dec sin lam, sin dec), lam = ra - gmst.
+template <class T>
+struct Sky {
+  T sl, cl, sd, cd;
+};
+template <class T>
+__device__ __forceinline__ Sky<T> sky_trig(const T& ra, const T& dec, double gmst) {
+  Sky<T> k;
+  sincos(ra - gmst, &k.sl, &k.cl);
+  sincos(dec, &k.sd, &k.cd);
+  return k;
+}
+
+// tau_d = tc - (r_d . n)/c
+template <class T>
+__device__ __forceinline__ T delay(const T& tc, const Sky<T>& k, const double* g) {
+  return tc - ((k.cd * k.cl) * (g[0] / kC) + (k.cd * k.sl) * (g[1] / kC) + k.sd * (g[2] / kC));
+}
+
+// P_d = F+ (1 + cos^2 i)/2 - i Fx cos i for one detector, with the wave-frame
+// axes X = cos psi e_E + sin psi e_N, Y = -sin psi e_E + cos psi e_N,
+// e_E = (-sin lam, cos lam, 0), e_N = (-sin dec cos lam, -sin dec sin lam, cos dec),
+// F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2.
+template <class T>
+__device__ __forceinline__ void response(const Sky<T>& k, const T& sp, const T& cp, const T& ci, const double* g,
+                                         T& Pr, T& Pi) {
+  const T X0 = -(cp * k.sl) - sp * k.sd * k.cl, X1 = cp * k.cl - sp * k.sd * k.sl, X2 = sp * k.cd;
+  const T Y0 = sp * k.sl - cp * k.sd * k.cl, Y1 = -(sp * k.cl) - cp * k.sd * k.sl, Y2 = cp * k.cd;
+  const T xX = X0 * g[3] + X1 * g[4] + X2 * g[5], xY = Y0 * g[3] + Y1 * g[4] + Y2 * g[5];
+  const T yX = X0 * g[6] + X1 * g[7] + X2 * g[8], yY = Y0 * g[6] + Y1 * g[7] + Y2 * g[8];
+  const T Fp = ((xX * xX - xY * xY) - (yX * yX - yY * yY)) * 0.5;
+  const T Fx = xX * xY - yX * yY;
+  Pr = Fp * ((ci * ci + 1.0) * 0.5);
+  Pi = -(Fx * ci);
+}
+
+// K_d = A P_d e^{i (phic + pi/4 - 2 pi ccyc)} and <h|h>_d = |K_d|^2 H_d[ncut - 1].
+template <class T>
+__device__ __forceinline__ void k_angle(const T& phic, const T& ccyc, T& sa, T& ca) {
+  T ang = phic + (0.25 * kPi) - (2.0 * kPi) * frac_near(ccyc);
+  ang = ang - (2.0 * kPi) * rint(val(ang) * (0.5 / kPi));
+  sincos(ang, &sa, &ca);
 }
 
 }  // namespace gwl

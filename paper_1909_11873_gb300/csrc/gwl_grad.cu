@@ -1,0 +1,405 @@
+// gwl_grad.cu -- log-likelihood and its gradient by adjoint accumulation.
+//
+// With lnL = sum_d Re[K_d Z_d] - <h|h>/2,  Z_d = sum_j G_d,j e^{-2 pi i r_d,j},
+// r_d,j = sum_m c_m B_m(f_j) + tau_d f_j, the derivative along a sampled
+// coordinate theta_k is
+//   d lnL = sum_d { Re[dK_d Z_d] + 2 pi Im[K_d S_d] } - d<h|h>/2,
+//   S_d  = sum_m dc_m W_d,m + dtau_d W_d,f,
+//   W_d,m = sum_j G_d,j e^{-2 pi i r_d,j} B_m(f_j),   W_d,f = sum_j ... f_j.
+// The bin loop therefore accumulates, per detector, Z_d and the nine complex
+// basis-weighted sums W_d,m, W_d,f (one pass over the bins, same phase
+// arithmetic as the likelihood).  The per-proposal derivatives dc_m, dtau_d,
+// dK_d, d<h|h> come from the prologue evaluated on a forward-mode tangent type
+// whose value stays FP64 (the same numbers as the likelihood path) while the
+// tangents are carried in FP32 (GWL_MIXED) or FP64 (GWL_FP64).  The ISCO cut
+// index is held at its value: the gradient of the piecewise-smooth lnL.
+#include <cmath>
+
+#include "gwl_bins.cuh"
+
+namespace gwl {
+
+constexpr int kNW = kNBasis + 1;  // basis-weighted sums per detector (B_0..B_7, f)
+constexpr int kAccPerDet = 2 + 2 * kNW;  // U, V, W (re, im) x 9
+
+template <class G>
+struct PropGrad {
+  G dc[kNBasis][11];
+  G dtau[kMaxDet][11];
+  G dKr[kMaxDet][11], dKi[kMaxDet][11];
+  G dhh[11];
+};
+
+// ---------------------------------------------------------------- tangent prologue
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* __restrict__ theta, int64_t B,
+                                                      PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
+                                                      PropCommon* __restrict__ pc,
+                                                      PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
+                                                      int* __restrict__ work) {
+  using G = typename std::conditional<MIXED, float, double>::type;
+  using T = Tan<11, G>;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int ncut = 0;
+  if (p < B) {
+    double th[11];
+    expand_theta(s, theta + p * s.n_dim, th);
+    const bool ok = physical(th);
+    if (!ok) {
+      th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
+#pragma unroll
+      for (int k = 5; k < 11; ++k) th[k] = 0.0;
+    }
+    T x[11];
+#pragma unroll
+    for (int k = 0; k < 11; ++k) x[k] = tan_const<11, G>(th[k]);
+    for (int i = 0; i < s.n_dim; ++i) x[s.param_map[i]].d[i] = (G)1;
+
+    const PNCoeffs<T> P = pn_coeffs(x[1], x[2], x[3]);
+    const Scale<T> S = mass_scale(x[0], P.eta, x[4], s.amp_scale);
+    T c[kNBasis], ccyc;
+    basis_coeffs(P, S, c, ccyc);
+    ncut = (int)s.M;
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, 1.0 / (kSix32 * S.a13.v * S.a13.v * S.a13.v));
+    if (!ok) ncut = 0;
+    const Sky<T> k = sky_trig(x[7], x[8], s.gmst);
+    T sp, cp;
+    sincos(x[6], &sp, &cp);
+    const T ci = cos(x[5]);
+    T sa, ca;
+    k_angle(x[10], ccyc, sa, ca);
+
+    PropGrad<G>& g = pg[p];
+    PropCommon cm;
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) {
+#pragma unroll
+      for (int i = 0; i < 11; ++i) g.dc[m][i] = ok ? c[m].d[i] : (G)0;
+      if (MIXED) split_f64(ok ? c[m].v : 0.0, pm[p].ch[m], pm[p].cl[m]);
+      else pf[p].c[m] = ok ? c[m].v : 0.0;
+    }
+    T hh = tan_const<11, G>(0.0);
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) {
+      T tau = tan_const<11, G>(0.0), Kr = tau, Ki = tau;
+      if (d < s.n_det && ok) {
+        const double* gd = s.geom + 9 * d;
+        tau = delay(x[9], k, gd);
+        T Pr, Pi;
+        response(k, sp, cp, ci, gd, Pr, Pi);
+        Kr = S.amp * (Pr * ca - Pi * sa);
+        Ki = S.amp * (Pr * sa + Pi * ca);
+        if (ncut > 0) hh = hh + (S.amp * S.amp) * (Pr * Pr + Pi * Pi) * s.H[(int64_t)d * s.M + ncut - 1];
+      }
+#pragma unroll
+      for (int i = 0; i < 11; ++i) {
+        g.dtau[d][i] = tau.d[i];
+        g.dKr[d][i] = Kr.d[i];
+        g.dKi[d][i] = Ki.d[i];
+      }
+      if (MIXED) split_f64(tau.v, pm[p].th[d], pm[p].tl[d]);
+      else pf[p].tau[d] = tau.v;
+      cm.Kr[d] = Kr.v;
+      cm.Ki[d] = Ki.v;
+    }
+#pragma unroll
+    for (int i = 0; i < 11; ++i) g.dhh[i] = hh.d[i];
+    cm.hh = hh.v;
+    cm.ncut = ncut;
+    cm.flag = ok ? 0 : 1;
+    pc[p] = cm;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ncut = max(ncut, __shfl_xor_sync(0xffffffffu, ncut, off));
+  if ((threadIdx.x & 31) == 0 && ncut > 0) atomicMax(&work[0], ncut);
+}
+
+// ---------------------------------------------------------------- bin loop
+struct GradArgs {
+  const void* tab;
+  int row_elems;
+  int64_t M;
+  int CH;
+  int64_t B;
+  int nw_total;
+  const PropCommon* pc;
+  const void* prop;
+  void* partials;  // [B][nw_total][kAccPerDet * NDET]
+  int* work;
+  int* status;
+};
+
+template <int NDET, bool MIXED>
+__device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restrict__ smv, int64_t p, int j0,
+                                          int jend, int lane,
+                                          typename std::conditional<MIXED, float, double>::type (&A)[NDET][kAccPerDet]) {
+  using Acc = typename std::conditional<MIXED, float, double>::type;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d)
+#pragma unroll
+    for (int k = 0; k < kAccPerDet; ++k) A[d][k] = (Acc)0;
+  if constexpr (MIXED) {
+    const float* sm = reinterpret_cast<const float*>(smv);
+    const PropMixed* P = reinterpret_cast<const PropMixed*>(a.prop) + p;
+    float ch[kNBasis], cl[kNBasis], th[NDET], tl[NDET];
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) {
+      ch[m] = P->ch[m];
+      cl[m] = P->cl[m];
+    }
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      th[d] = P->th[d];
+      tl[d] = P->tl[d];
+    }
+    for (int j = j0 + lane; j < jend; j += 32) {
+      float v[RowM<NDET>::n];
+      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
+      float sn[NDET], cs[NDET];
+      phase_mixed<NDET>(v, ch, cl, th, tl, sn, cs);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        const float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
+        const float uw = fmaf(gr, cs[d], gi * sn[d]);
+        const float vw = fmaf(gi, cs[d], -gr * sn[d]);
+        A[d][0] += uw;
+        A[d][1] += vw;
+#pragma unroll
+        for (int m = 0; m < kNBasis; ++m) {
+          A[d][2 + 2 * m] = fmaf(uw, v[m], A[d][2 + 2 * m]);
+          A[d][3 + 2 * m] = fmaf(vw, v[m], A[d][3 + 2 * m]);
+        }
+        A[d][2 + 2 * kNBasis] = fmaf(uw, v[16], A[d][2 + 2 * kNBasis]);
+        A[d][3 + 2 * kNBasis] = fmaf(vw, v[16], A[d][3 + 2 * kNBasis]);
+      }
+    }
+  } else {
+    const double* sm = reinterpret_cast<const double*>(smv);
+    const PropF64* P = reinterpret_cast<const PropF64*>(a.prop) + p;
+    double c[kNBasis], tau[NDET];
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) c[m] = P->c[m];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) tau[d] = P->tau[d];
+    for (int j = j0 + lane; j < jend; j += 32) {
+      double v[RowD<NDET>::n];
+      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
+      double sn[NDET], cs[NDET];
+      phase_f64<NDET>(v, c, tau, sn, cs);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        const double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
+        const double uw = fma(gr, cs[d], gi * sn[d]);
+        const double vw = fma(gi, cs[d], -gr * sn[d]);
+        A[d][0] += uw;
+        A[d][1] += vw;
+#pragma unroll
+        for (int m = 0; m < kNBasis; ++m) {
+          A[d][2 + 2 * m] = fma(uw, v[m], A[d][2 + 2 * m]);
+          A[d][3 + 2 * m] = fma(vw, v[m], A[d][3 + 2 * m]);
+        }
+        A[d][2 + 2 * kNBasis] = fma(uw, v[8], A[d][2 + 2 * kNBasis]);
+        A[d][3 + 2 * kNBasis] = fma(vw, v[8], A[d][3 + 2 * kNBasis]);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int d = 0; d < NDET; ++d)
+#pragma unroll
+      for (int k = 0; k < kAccPerDet; ++k) A[d][k] += __shfl_xor_sync(0xffffffffu, A[d][k], off);
+}
+
+template <int NDET, bool MIXED>
+__global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
+  cudaGridDependencySynchronize();
+  using Elem = typename std::conditional<MIXED, float, double>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  Elem* sm = reinterpret_cast<Elem*>(smem_raw);
+  const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
+  const int lane = threadIdx.x & 31;
+  const int maxn = a.work[0];
+  int nw = (maxn + a.CH - 1) / a.CH;
+  if (nw > a.nw_total) nw = a.nw_total;
+  if (nw < 1) return;
+  const int G = gridDim.x;
+  const int wstep = G >= nw ? nw : G;
+  int w = G >= nw ? (int)(blockIdx.x % nw) : (int)blockIdx.x;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (; w < nw; w += wstep) {
+    const int j0 = w * a.CH;
+    int64_t j1l = (int64_t)j0 + a.CH;
+    if (j1l > a.M) j1l = a.M;
+    if (j1l > maxn) j1l = maxn;
+    const int j1 = j1l > j0 ? (int)j1l : j0;
+    __syncthreads();
+    if (j1 > j0) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+        mbar_arrive_expect_tx(&bar, bytes);
+        bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, &bar);
+      }
+      if (!mbar_wait_bounded(&bar, parity, a.status)) return;
+      parity ^= 1u;
+    }
+    int* ctr = a.work + 1 + w;
+    while (true) {
+      int pi = 0;
+      if (lane == 0) pi = atomicAdd(ctr, 1);
+      pi = __shfl_sync(0xffffffffu, pi, 0);
+      if (pi >= a.B) break;
+      const int64_t p = pi;
+      const int ncut = a.pc[p].ncut;
+      if (ncut <= j0) continue;
+      Elem A[NDET][kAccPerDet];
+      grad_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, A);
+      // lanes write the per-window sums cooperatively
+      Elem* o = reinterpret_cast<Elem*>(a.partials) + ((int64_t)p * a.nw_total + w) * (kAccPerDet * NDET);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d)
+#pragma unroll
+        for (int k = 0; k < kAccPerDet; ++k)
+          if (lane == ((d * kAccPerDet + k) & 31)) o[d * kAccPerDet + k] = A[d][k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- combination
+template <int NDET, bool MIXED>
+__global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
+                                const PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
+                                const void* __restrict__ partials_v, int64_t B, int CH, int nw_total, int n_dim,
+                                double* __restrict__ lnl, double* __restrict__ grad) {
+  cudaGridDependencySynchronize();
+  using G = typename std::conditional<MIXED, float, double>::type;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= B) return;
+  const PropCommon c = pc[p];
+  if (c.flag) {
+    lnl[p] = -INFINITY;
+    for (int i = 0; i < n_dim; ++i) grad[p * n_dim + i] = 0.0;
+    return;
+  }
+  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
+  const int nwp = (c.ncut + CH - 1) / CH;
+  double Z[NDET][2];
+  G W[NDET][2 * kNW];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    double acc[kAccPerDet];
+#pragma unroll
+    for (int k = 0; k < kAccPerDet; ++k) acc[k] = 0.0;
+    for (int w = 0; w < nwp; ++w)
+#pragma unroll
+      for (int k = 0; k < kAccPerDet; ++k) acc[k] += (double)q[w * (kAccPerDet * NDET) + d * kAccPerDet + k];
+    Z[d][0] = acc[0];
+    Z[d][1] = acc[1];
+#pragma unroll
+    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)acc[2 + k];
+  }
+  double l = -0.5 * c.hh;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) l += c.Kr[d] * Z[d][0] - c.Ki[d] * Z[d][1];
+  lnl[p] = l;
+  const PropGrad<G>& g = pg[p];
+  const G twopi = (G)(2.0 * kPi);
+  for (int i = 0; i < n_dim; ++i) {
+    G acc = (G)(-0.5) * g.dhh[i];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      G Sr = g.dtau[d][i] * W[d][2 * kNBasis], Si = g.dtau[d][i] * W[d][2 * kNBasis + 1];
+#pragma unroll
+      for (int m = 0; m < kNBasis; ++m) {
+        Sr += g.dc[m][i] * W[d][2 * m];
+        Si += g.dc[m][i] * W[d][2 * m + 1];
+      }
+      acc += g.dKr[d][i] * (G)Z[d][0] - g.dKi[d][i] * (G)Z[d][1] + twopi * ((G)c.Kr[d] * Si + (G)c.Ki[d] * Sr);
+    }
+    grad[p * n_dim + i] = (double)acc;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B) {
+  const bool mixed = c->opt.precision == GWL_MIXED;
+  int CH = mixed ? c->window_mixed : c->window_f64;
+  if (CH > c->M) CH = (int)c->M;
+  const int64_t nw = (c->M + CH - 1) / CH;
+  return B * nw * kAccPerDet * c->n_det * (int64_t)(mixed ? sizeof(float) : sizeof(double));
+}
+int64_t prop_grad_bytes(const gwl_ctx* c) {
+  return c->opt.precision == GWL_MIXED ? (int64_t)sizeof(PropGrad<float>) : (int64_t)sizeof(PropGrad<double>);
+}
+int64_t work_needed(const gwl_ctx* c);
+
+template <int NDET, bool MIXED>
+static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
+  using G = typename std::conditional<MIXED, float, double>::type;
+  int CH = MIXED ? c->window_mixed : c->window_f64;
+  if (CH > c->M) CH = (int)c->M;
+  const int nw_total = (int)((c->M + CH - 1) / CH);
+  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c), st);
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
+    k_prologue_grad<MIXED><<<(unsigned)((B + 63) / 64), 64, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc,
+                                                                      reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
+                                                                      c->d_work);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  GradArgs a;
+  a.tab = MIXED ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
+  a.row_elems = MIXED ? c->row_floats : c->row_doubles;
+  a.M = c->M;
+  a.CH = CH;
+  a.B = B;
+  a.nw_total = nw_total;
+  a.pc = c->d_pc;
+  a.prop = MIXED ? (const void*)c->d_pm : (const void*)c->d_pf;
+  a.partials = c->d_gpartials;
+  a.work = c->d_work;
+  a.status = c->d_status;
+  const size_t smem = (size_t)CH * a.row_elems * sizeof(G);
+  static size_t smem_set = 0;
+  if (smem > smem_set) {
+    if ((e = cudaFuncSetAttribute(k_window_grad<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    smem_set = smem;
+  }
+  {
+    ProfScope ps(c, GWL_KERNEL_GRAD, st);
+    e = launch_pdl(k_window_grad<NDET, MIXED>, dim3(c->num_sms * 2), dim3(256), smem, st, a);
+    c->launches++;
+    if (e != cudaSuccess) return e;
+  }
+  {
+    ProfScope ps(c, GWL_KERNEL_COMBINE, st);
+    e = launch_pdl(k_finalize_grad<NDET, MIXED>, dim3((unsigned)((B + 63) / 64)), dim3(64), 0, st,
+                   (const PropCommon*)c->d_pc, (const PropGrad<G>*)c->d_pgrad, (const void*)c->d_gpartials, B, CH,
+                   nw_total, c->opt.n_dim, lnl, grad);
+    c->launches++;
+  }
+  return e;
+}
+
+cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
+  const bool mixed = c->opt.precision == GWL_MIXED;
+  switch (c->n_det) {
+    case 1: return mixed ? run_grad<1, true>(c, theta, B, lnl, grad, st) : run_grad<1, false>(c, theta, B, lnl, grad, st);
+    case 2: return mixed ? run_grad<2, true>(c, theta, B, lnl, grad, st) : run_grad<2, false>(c, theta, B, lnl, grad, st);
+    case 3: return mixed ? run_grad<3, true>(c, theta, B, lnl, grad, st) : run_grad<3, false>(c, theta, B, lnl, grad, st);
+    default: return mixed ? run_grad<4, true>(c, theta, B, lnl, grad, st) : run_grad<4, false>(c, theta, B, lnl, grad, st);
+  }
+}
+
+}  // namespace gwl

@@ -35,6 +35,10 @@ struct gwl_ctx {
   int64_t partials_cap = 0;      // in doubles
   double* d_io = nullptr;        // staging for the host-buffer entry points
   int64_t io_cap = 0;            // in doubles
+  void* d_pgrad = nullptr;       // per-proposal tangents of the gradient prologue
+  int64_t pgrad_cap = 0;         // in bytes
+  void* d_gpartials = nullptr;   // per-window sums of the gradient bin loop
+  int64_t gpartials_cap = 0;     // in bytes
   int* d_work = nullptr;         // [0] largest cut of the batch, [1 + w] proposal counter of window w
   int64_t work_cap = 0;          // in ints
   int* d_status = nullptr;       // [0] latched status bits
@@ -71,9 +75,15 @@ namespace gwl {
 
 // a1: tables
 cudaError_t launch_build_tables(gwl_ctx* c, const double* d_strain, const double* d_psd, cudaStream_t st);
+cudaError_t launch_scale_tables(gwl_ctx* c, double sg, cudaStream_t st);
 
 // a2-a6: batched log-likelihood
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st);
+
+// a8: log-likelihood and gradient
+cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st);
+int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B);
+int64_t prop_grad_bytes(const gwl_ctx* c);
 
 // device-path template, for diagnostics and injections
 cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st);

@@ -34,26 +34,9 @@
 #include <cmath>
 #include <type_traits>
 
-#include "gwl_internal.h"
+#include "gwl_bins.cuh"
 
 namespace gwl {
-
-// ---------------------------------------------------------------- launch helper
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 // ---------------------------------------------------------------- prologue
 // 128 threads per CTA, 32 rows.  The FP64 work of a row is spread over four
@@ -85,63 +68,39 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
   const bool ok = valid && physical(th);
   if (!ok) {  // keep every transcendental below on a harmless argument
     th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
+#pragma unroll
+    for (int k = 5; k < 11; ++k) th[k] = 0.0;
   }
-  const double mc = th[0], q = th[1];
-  const double opq = 1.0 + q;
-  const double eta = q / (opq * opq);
+  const double opq = th[1] + 1.0;
+  const double eta = th[1] / (opq * opq);
 
   // ---- phase 1
   if (role == 0) {
-    const double lmc = log(kPi * kTsun * mc);  // ln(pi Mc T_sun)
-    const double la = lmc - 0.6 * log(eta);    // ln a, a = pi M
-    const double a13 = exp(la * (1.0 / 3.0));
-    sh_la[lane] = la;
-    sh_a13[lane] = a13;
-    sh_amp[lane] = kAmpConst * exp((5.0 / 6.0) * (lmc - kLnPi)) * kC / (th[4] * kMpc);
+    const Scale<double> S = mass_scale(th[0], eta, th[4], s.amp_scale);
+    sh_la[lane] = S.la;
+    sh_a13[lane] = S.a13;
+    sh_amp[lane] = S.amp;
     int ncut = (int)s.M;
-    if (s.fcut_mode == 0) ncut = count_bins_le(s, 1.0 / (kSix32 * a13 * a13 * a13));
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, 1.0 / (kSix32 * S.a13 * S.a13 * S.a13));
     sh_ncut[lane] = ok ? ncut : 0;
   } else if (role == 1) {
-    const double chi1 = th[2], chi2 = th[3];
-    const double delta = (1.0 - q) / opq;
-    const double x1 = 1.0 / opq, x2 = q * x1;
-    const double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
-    const double eta2 = eta * eta;
-    const double beta =
-        ((113.0 / 12.0) * x1 * x1 + 6.25 * eta) * chi1 + ((113.0 / 12.0) * x2 * x2 + 6.25 * eta) * chi2;
-    const double gam = (732985.0 / 2268.0 - (24260.0 / 81.0) * eta - (340.0 / 9.0) * eta2) * chis +
-                       (732985.0 / 2268.0 + (140.0 / 9.0) * eta) * delta * chia;
-    sh_phi[0][lane] = (20.0 / 9.0) * (743.0 / 336.0 + (11.0 / 4.0) * eta);
-    sh_phi[1][lane] = -16.0 * kPi + 4.0 * beta;
-    sh_phi[2][lane] = 10.0 * (3058673.0 / 1016064.0 + (5429.0 / 1008.0) * eta + (617.0 / 144.0) * eta2) -
-                      10.0 * (79.0 / 8.0) * eta * chi1 * chi2;
-    sh_phi[3][lane] = kPi * (38645.0 / 756.0 - (65.0 / 9.0) * eta) - gam;
-    sh_phi[4][lane] = 11583231236531.0 / 4694215680.0 - (640.0 / 3.0) * kPi * kPi - (6848.0 / 21.0) * kGammaE +
-                      eta * (-15737765635.0 / 3048192.0 + (2255.0 / 12.0) * kPi * kPi) +
-                      (76055.0 / 1728.0) * eta2 - (127825.0 / 1296.0) * eta2 * eta +
-                      kPi * ((2270.0 / 3.0) * delta * chia + (2270.0 / 3.0 - 520.0 * eta) * chis);
-    sh_phi[5][lane] =
-        kPi * (77096675.0 / 254016.0 + (378515.0 / 1512.0) * eta - (74045.0 / 756.0) * eta2) +
-        (-25150083775.0 / 3048192.0 + (10566655595.0 / 762048.0) * eta - (1042165.0 / 3024.0) * eta2 +
-         (5345.0 / 36.0) * eta2 * eta) * chis +
-        delta * (-25150083775.0 / 3048192.0 + (26804935.0 / 6048.0) * eta - (1985.0 / 48.0) * eta2) * chia;
+    const PNCoeffs<double> P = pn_coeffs(th[1], th[2], th[3]);
+    sh_phi[0][lane] = P.p2;
+    sh_phi[1][lane] = P.p3;
+    sh_phi[2][lane] = P.p4;
+    sh_phi[3][lane] = P.p5c;
+    sh_phi[4][lane] = P.p6c;
+    sh_phi[5][lane] = P.p7;
   } else if (role == 2) {
-    double sl, cl, sd, cd;
-    sincos(th[7] - s.gmst, &sl, &cl);
-    sincos(th[8], &sd, &cd);
-    sh_sky[0][lane] = sl;
-    sh_sky[1][lane] = cl;
-    sh_sky[2][lane] = sd;
-    sh_sky[3][lane] = cd;
-    const double n0 = cd * cl, n1 = cd * sl, n2 = sd;
+    const Sky<double> k = sky_trig(th[7], th[8], s.gmst);
+    sh_sky[0][lane] = k.sl;
+    sh_sky[1][lane] = k.cl;
+    sh_sky[2][lane] = k.sd;
+    sh_sky[3][lane] = k.cd;
     if (valid) {
 #pragma unroll
       for (int d = 0; d < kMaxDet; ++d) {
-        double tau = 0.0;
-        if (d < s.n_det && ok) {
-          const double* g = s.geom + 9 * d;
-          tau = th[9] - (g[0] * n0 + g[1] * n1 + g[2] * n2) / kC;
-        }
+        const double tau = (d < s.n_det && ok) ? delay(th[9], k, s.geom + 9 * d) : 0.0;
         if (MIXED) split_f64(tau, pm[p].th[d], pm[p].tl[d]);
         else pf[p].tau[d] = tau;
       }
@@ -157,20 +116,21 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
 
   // ---- phase 2
   if (role == 0) {
-    const double la = sh_la[lane], a13 = sh_a13[lane];
-    const double am13 = 1.0 / a13, am23 = am13 * am13;
-    const double pref = 3.0 / (128.0 * eta) / (2.0 * kPi);  // radians -> cycles
-    double c[kNBasis];
-    c[0] = pref * am23 * am23 * am13;                                                   // f^{-5/3}
-    c[1] = pref * sh_phi[0][lane] * am23 * am13;                                        // f^{-1}
-    c[2] = pref * sh_phi[1][lane] * am23;                                               // f^{-2/3}
-    c[3] = pref * sh_phi[2][lane] * am13;                                               // f^{-1/3}
-    c[4] = pref * sh_phi[3][lane];                                                      // ln f
-    c[5] = pref * a13 * (sh_phi[4][lane] - (6848.0 / 21.0) * kLn4 - (6848.0 / 63.0) * la);  // f^{1/3}
-    c[6] = pref * a13 * (-6848.0 / 63.0);                                               // f^{1/3} ln f
-    c[7] = pref * sh_phi[5][lane] * a13 * a13;                                          // f^{2/3}
-    // constant PN phase [cycles]: phi5 (1 + ln a - 3 ln v_lso), v_lso = 6^{-1/2}
-    sh_ccyc[lane] = pref * sh_phi[3][lane] * (1.0 + la + 1.5 * kLn6);
+    PNCoeffs<double> P;
+    P.eta = eta;
+    P.p2 = sh_phi[0][lane];
+    P.p3 = sh_phi[1][lane];
+    P.p4 = sh_phi[2][lane];
+    P.p5c = sh_phi[3][lane];
+    P.p6c = sh_phi[4][lane];
+    P.p7 = sh_phi[5][lane];
+    Scale<double> S;
+    S.la = sh_la[lane];
+    S.a13 = sh_a13[lane];
+    S.amp = sh_amp[lane];
+    double c[kNBasis], ccyc;
+    basis_coeffs(P, S, c, ccyc);
+    sh_ccyc[lane] = ccyc;
     if (valid) {
 #pragma unroll
       for (int m = 0; m < kNBasis; ++m) {
@@ -180,23 +140,16 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
       }
     }
   } else if (role == 1) {
-    const double sl = sh_sky[0][lane], cl = sh_sky[1][lane], sd = sh_sky[2][lane], cd = sh_sky[3][lane];
+    Sky<double> k;
+    k.sl = sh_sky[0][lane];
+    k.cl = sh_sky[1][lane];
+    k.sd = sh_sky[2][lane];
+    k.cd = sh_sky[3][lane];
     const double sp = sh_ori[0][lane], cp = sh_ori[1][lane], ci = sh_ori[2][lane];
-    // wave-frame axes X = cos psi e_E + sin psi e_N, Y = -sin psi e_E + cos psi e_N
-    const double X0 = -cp * sl - sp * sd * cl, X1 = cp * cl - sp * sd * sl, X2 = sp * cd;
-    const double Y0 = sp * sl - cp * sd * cl, Y1 = -sp * cl - cp * sd * sl, Y2 = cp * cd;
-    const double hp = 0.5 * (1.0 + ci * ci);
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
       double Pr = 0.0, Pi = 0.0;
-      if (d < s.n_det) {
-        const double* g = s.geom + 9 * d;
-        const double xX = g[3] * X0 + g[4] * X1 + g[5] * X2, xY = g[3] * Y0 + g[4] * Y1 + g[5] * Y2;
-        const double yX = g[6] * X0 + g[7] * X1 + g[8] * X2, yY = g[6] * Y0 + g[7] * Y1 + g[8] * Y2;
-        // F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2
-        Pr = 0.5 * ((xX * xX - xY * xY) - (yX * yX - yY * yY)) * hp;
-        Pi = -(xX * xY - yX * yY) * ci;
-      }
+      if (d < s.n_det) response(k, sp, cp, ci, s.geom + 9 * d, Pr, Pi);
       sh_P[2 * d][lane] = Pr;
       sh_P[2 * d + 1][lane] = Pi;
     }
@@ -213,18 +166,16 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
       for (int d = 0; d < kMaxDet; ++d) cm.Kr[d] = cm.Ki[d] = 0.0;
       if (ok) {
         const double amp = sh_amp[lane];
-        const double ccyc = sh_ccyc[lane];
-        // K_d = A P_d e^{i (phic + pi/4 - 2 pi ccyc)}
-        double ang = th[10] + 0.25 * kPi - 2.0 * kPi * (ccyc - rint(ccyc));
-        ang -= 2.0 * kPi * rint(ang * (0.5 / kPi));
         double sa, ca;
-        if (MIXED) {
+        if (MIXED) {  // the angle in FP64, its sine and cosine in FP32 (K enters lnL linearly)
+          double ang = th[10] + 0.25 * kPi - 2.0 * kPi * frac_near(sh_ccyc[lane]);
+          ang -= 2.0 * kPi * rint(ang * (0.5 / kPi));
           float sf, cf;
           sincosf((float)ang, &sf, &cf);
           sa = sf;
           ca = cf;
         } else {
-          sincos(ang, &sa, &ca);
+          k_angle(th[10], sh_ccyc[lane], sa, ca);
         }
         for (int d = 0; d < s.n_det; ++d) {
           const double Pr = sh_P[2 * d][lane], Pi = sh_P[2 * d + 1][lane];
@@ -243,85 +194,6 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
     if (lane == 0 && nm > 0) atomicMax(&work[0], nm);
-  }
-}
-
-// ---------------------------------------------------------------- per-bin bodies
-// Row element counts actually read (without the trailing pad unit).
-template <int NDET> struct RowM { static constexpr int n = (18 + 2 * NDET + 3) / 4 * 4; };
-template <int NDET> struct RowD { static constexpr int n = (9 + 2 * NDET + 1) / 2 * 2; };
-
-template <int NDET>
-__device__ __forceinline__ void load_row(const float* __restrict__ row, float (&v)[RowM<NDET>::n]) {
-#pragma unroll
-  for (int k = 0; k < RowM<NDET>::n / 4; ++k)
-    *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
-}
-template <int NDET>
-__device__ __forceinline__ void load_row(const double* __restrict__ row, double (&v)[RowD<NDET>::n]) {
-#pragma unroll
-  for (int k = 0; k < RowD<NDET>::n / 2; ++k)
-    *reinterpret_cast<double2*>(&v[2 * k]) = reinterpret_cast<const double2*>(row)[k];
-}
-
-template <int NDET>
-__device__ __forceinline__ void bin_mixed(const float (&v)[RowM<NDET>::n], const float (&ch)[kNBasis],
-                                          const float (&cl)[kNBasis], const float (&th)[NDET],
-                                          const float (&tl)[NDET], float (&U)[NDET], float (&V)[NDET]) {
-  // common phase S = sum_m c_m B_m as an unevaluated float pair (s, lo)
-  float s, lo;
-  {
-    float e;
-    two_prod(ch[0], v[0], s, e);
-    lo = __fmaf_rn(cl[0], v[0], __fmaf_rn(ch[0], v[kNBasis], e));
-  }
-#pragma unroll
-  for (int m = 1; m < kNBasis; ++m) {
-    const float bh = v[m], bl = v[kNBasis + m];
-    float p, e, t, q;
-    two_prod(ch[m], bh, p, e);
-    two_sum(s, p, t, q);
-    s = t;
-    lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
-  }
-  const float fh = v[16], fl = v[17];
-#pragma unroll
-  for (int d = 0; d < NDET; ++d) {
-    // r_d = S + tau_d f, then its fractional part in [-1/2, 1/2]
-    float p, e, t, q;
-    two_prod(th[d], fh, p, e);
-    e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
-    two_sum(s, p, t, q);
-    const float l = lo + (e + q);
-    // nearest integer of t by the 1.5 * 2^23 shift (exact for |t| < 2^22); the
-    // shift runs on the FMA pipe, whereas a rounding instruction would occupy
-    // the narrow conversion pipe
-    const float n = __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
-    const float fr = __fadd_rn(__fsub_rn(t, n), l);  // t - n is exact
-    float sn, cs;
-    __sincosf(6.283185307179586f * fr, &sn, &cs);
-    const float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
-    // (gr + i gi)(cs - i sn)
-    U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
-    V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
-  }
-}
-
-template <int NDET>
-__device__ __forceinline__ void bin_f64(const double (&v)[RowD<NDET>::n], const double (&c)[kNBasis],
-                                        const double (&tau)[NDET], double (&U)[NDET], double (&V)[NDET]) {
-  double r = c[0] * v[0];
-#pragma unroll
-  for (int m = 1; m < kNBasis; ++m) r = fma(c[m], v[m], r);
-  const double f = v[8];
-#pragma unroll
-  for (int d = 0; d < NDET; ++d) {
-    const double rd = fma(tau[d], f, r);
-    double sn, cs;
-    sincospi(2.0 * rd, &sn, &cs);
-    const double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
-    U[d] = fma(gr, cs, fma(gi, sn, U[d]));
-    V[d] = fma(gi, cs, fma(-gr, sn, V[d]));
   }
 }
 
@@ -523,7 +395,7 @@ __global__ void k_waveform(SegInfo s, const PropF64* __restrict__ pf, const Prop
   for (int m = 0; m < kNBasis; ++m) r = fma(pf[p].c[m], row[m], r);
   const double x = f * s.t_ref;
   const double fref = x - floor(x);
-  const double f76 = pow(f, -7.0 / 6.0);
+  const double f76 = pow(f, -7.0 / 6.0) / s.amp_scale;  // K carries the table normalisation
   for (int d = 0; d < s.n_det; ++d) {
     double ph = fma(pf[p].tau[d], f, r);
     ph -= rint(ph);

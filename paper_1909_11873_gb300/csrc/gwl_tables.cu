@@ -97,6 +97,28 @@ __global__ void k_prefix_scan(double* __restrict__ H, int64_t M) {
   }
 }
 
+// Multiply the data weights by 2^-e and the prefix sums by 2^-2e (exact).
+__global__ void k_scale_tables(int64_t M, int n_det, double sg, float* __restrict__ tab_m, int row_f,
+                               double* __restrict__ tab_d, int row_d, double* __restrict__ H) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  for (int d = 0; d < n_det; ++d) {
+    tab_d[j * row_d + 9 + 2 * d] *= sg;
+    tab_d[j * row_d + 10 + 2 * d] *= sg;
+    tab_m[j * row_f + 18 + 2 * d] = (float)tab_d[j * row_d + 9 + 2 * d];
+    tab_m[j * row_f + 19 + 2 * d] = (float)tab_d[j * row_d + 10 + 2 * d];
+    H[(int64_t)d * M + j] *= sg * sg;
+  }
+}
+
+cudaError_t launch_scale_tables(gwl_ctx* c, double sg, cudaStream_t st) {
+  const int T = 256;
+  k_scale_tables<<<(unsigned)((c->M + T - 1) / T), T, 0, st>>>(c->M, c->n_det, sg, c->d_tab_mixed, c->row_floats,
+                                                                c->d_tab_f64, c->row_doubles, c->d_H);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_tables(gwl_ctx* c, const double* d_strain, const double* d_psd, cudaStream_t st) {
   const int T = 256;
   const int64_t nb = (c->M + T - 1) / T;

@@ -240,3 +240,46 @@ def waveform(ctx: Context, theta, stream=None):
     out = torch.empty((theta.shape[0], ctx.n_det, ctx.M, 2), dtype=torch.float64, device=theta.device)
     ctx.gwl_waveform(theta, out, stream)
     return out
+
+
+def grad(ctx: Context, theta, stream=None):
+    """(lnL [B], d lnL / d theta [B, n_dim]) via gwl_grad."""
+    import torch
+    out = torch.empty(theta.shape[0], dtype=torch.float64, device=theta.device)
+    g = torch.empty_like(theta)
+    ctx.gwl_grad(theta, out, g, stream)
+    return out, g
+
+
+_GWLogLike = None
+
+
+def GWLogLike():
+    """torch.autograd.Function: lnL(theta) with the gradient from the adjoint kernel.
+
+    Usage: ``lnl = GWLogLike().apply(theta, ctx)``; forward runs gwl_grad when
+    theta requires a gradient (gwl_loglike otherwise) and backward scales the
+    stored gradient rows by the incoming gradient.
+    """
+    global _GWLogLike
+    if _GWLogLike is None:
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, theta, gctx):
+                th = theta.detach().contiguous()
+                if theta.requires_grad:
+                    lnl, g = grad(gctx, th)
+                    fctx.save_for_backward(g)
+                else:
+                    lnl = loglike(gctx, th)
+                return lnl
+
+            @staticmethod
+            def backward(fctx, gout):
+                (g,) = fctx.saved_tensors
+                return gout[:, None] * g, None
+
+        _GWLogLike = _F
+    return _GWLogLike

@@ -1,0 +1,110 @@
+"""Parity of the adjoint gradient (gwl_grad) with the oracle's dual-number gradient and with
+central finite differences of the device likelihood."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import event, tol
+from paper_1909_11873_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TSUN = 4.925490947e-6
+# gradient bars (error scaled by the parameter's prior width, relative to max(1, |g| width)): FP64 1e-6;
+# mixed 1e-3 -- the spin directions of heavy BBH proposals combine FP32 basis-weighted sums that
+# cancel strongly (measured maxima: 7.6e-4 c5, 3.7e-5 c1, 4.5e-6 c3).
+GTOL = {0: 1e-6, 1: 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1909_11873_gb300 import build
+    build.build()
+
+
+def run(ev, th_full, precision):
+    from paper_1909_11873_gb300 import gwl
+    ctx = gwl.Context.from_event(ev, precision)
+    x = torch.from_numpy(I.reduced(th_full, ev.sampling)).cuda()
+    lnl, g = gwl.grad(ctx, x)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    return lnl.cpu().numpy(), g.cpu().numpy()
+
+
+def scale_of(g):
+    """Per-component scale: the physical range of each parameter times the gradient's row norm."""
+    return np.maximum(1.0, np.abs(g))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grad_matches_oracle_dual_numbers(precision):
+    ev = event("c5")
+    th = I.proposals(ev, 4096, 5)
+    lnl, g = run(ev, th, precision)
+    idx = np.random.default_rng(2).choice(th.shape[0], 96, replace=False)
+    ref_l, ref_g = oracle.grad(ev, th[idx])
+    assert np.all(np.abs(lnl[idx] - ref_l) <= tol(precision, ref_l))
+    # compare with a per-parameter scale: |dlnL/dtheta_k| * (prior width of theta_k)
+    width = ev.sampling.hi - ev.sampling.lo
+    s = np.maximum(np.abs(ref_g) * width, 1.0)
+    err = np.abs(g[idx] - ref_g) * width / s
+    assert err.max() <= GTOL[precision], f"max scaled error {err.max():.3e}"
+
+
+@pytest.mark.parametrize("precision", [1])
+def test_c1_grad_4d(precision):
+    ev = event("c1")
+    th = I.proposals(ev, 512, 4, local_fraction=0.5)
+    lnl, g = run(ev, th, precision)
+    ref_l, ref_g = oracle.grad(ev, th)
+    ref_g = ref_g[:, ev.sampling.param_map]
+    width = ev.sampling.hi - ev.sampling.lo
+    s = np.maximum(np.abs(ref_g) * width, 1.0)
+    err = np.abs(g - ref_g) * width / s
+    assert np.all(np.abs(lnl - ref_l) <= tol(precision, ref_l))
+    assert err.max() <= GTOL[precision], f"max scaled error {err.max():.3e}"
+
+
+def test_grad_matches_central_differences_of_device_lnl():
+    """Central differences (h = 1e-6 relative) of the FP64 device lnL at rows whose ISCO bin does not move."""
+    from paper_1909_11873_gb300 import gwl
+    ev = event("c5")
+    th = I.proposals(ev, 8, 9)
+    _, g = run(ev, th, 0)
+    ctx = gwl.Context.from_event(ev, 0)
+    for b in range(th.shape[0]):
+        rows = []
+        for k in range(11):
+            h = 1e-6 * max(abs(th[b, k]), 1e-2)
+            tp, tm = th[b].copy(), th[b].copy()
+            tp[k] += h
+            tm[k] -= h
+            rows += [tp, tm]
+        rows = np.array(rows)
+        eta = rows[:, 1] / (1 + rows[:, 1]) ** 2
+        fisco = 1 / (6 ** 1.5 * math.pi * rows[:, 0] * eta ** -0.6 * TSUN)
+        ncut = np.searchsorted(ev.freqs, fisco, side="right")
+        l = gwl.loglike(ctx, torch.from_numpy(I.reduced(rows, ev.sampling)).cuda()).cpu().numpy()
+        for k in range(11):
+            if ncut[2 * k] != ncut[2 * k + 1]:
+                continue
+            h = 1e-6 * max(abs(th[b, k]), 1e-2)
+            fd = (l[2 * k] - l[2 * k + 1]) / (2 * h)
+            assert abs(fd - g[b, k]) <= 2e-4 * max(1.0, abs(g[b, k])), (b, k, fd, g[b, k])
+
+
+def test_autograd_function():
+    from paper_1909_11873_gb300 import gwl
+    ev = event("c5")
+    th = I.proposals(ev, 64, 13)
+    ctx = gwl.Context.from_event(ev, 1)
+    x = torch.from_numpy(I.reduced(th, ev.sampling)).cuda().requires_grad_(True)
+    lnl = gwl.GWLogLike().apply(x, ctx)
+    w = torch.linspace(0.5, 1.5, lnl.shape[0], device="cuda", dtype=torch.float64)
+    (lnl * w).sum().backward()
+    _, g = gwl.grad(ctx, x.detach())
+    assert torch.allclose(x.grad, w[:, None] * g)
