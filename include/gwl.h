@@ -162,6 +162,41 @@ int ns_replace(gwl_ctx* ctx, const double* live_u, const double* live_lnl, int64
                double scale, const double* chol, double* out_u, double* out_lnl, int32_t* out_nacc,
                int32_t* out_start, void* stream);
 
+/* Result of ns_run. */
+typedef struct {
+  double lnZ;                 /* log evidence (natural log, likelihood-ratio units) */
+  double lnZ_err;             /* sqrt(H / K) */
+  double H;                   /* information, sum_i p_i ln L_i - ln Z */
+  int64_t n_dead;             /* dead points including the final live set */
+  int64_t n_proposals;        /* K + rounds * n_chains * walk_len */
+  int64_t rounds;             /* parallel sampling rounds that changed the state */
+  double scale;               /* walk scale at the end */
+  double acceptance;          /* mean fraction of accepted walk steps per round */
+  double consumed_per_round;  /* mean candidates used per round (Eq. 5 predicts K ln(1 + n_chains/K)) */
+  double dlogz;               /* ln(Z + Lmax X) - ln Z at the last round */
+  int64_t n_dead_returned;    /* dead points copied to the optional output arrays */
+} gwl_ns_result;
+
+/* Static parallel nested sampling (Section 3, Algorithm 1) on the context's
+ * likelihood and prior, all state on the device.  K live points are drawn
+ * from the prior (Philox words with step word 0xFFFFFFFF, point index k and
+ * call word 0xFFFFFFFF; u = (w + 1/2) 2^-32).  Each round r: L* = worst live
+ * lnL; the walk step matrix is scale times the Cholesky factor of the
+ * live-set covariance in the unit cube; ns_replace's walks run with call
+ * counter r; the candidates then replace successive worst points in chain
+ * order, a candidate not above the current worst being discarded, until they
+ * run out.  Dead point i has weight dX_i = X_{i-1} - X_i, X_i = e^{-i/K}; the
+ * final live points enter with X_N/(K+1) each.  The walk scale adapts as
+ * scale <- scale exp(acceptance - 1/2), clamped to [1e-3, 1].  The run stops
+ * when ln(Z + Lmax X) - ln Z < dlogz or after max_rounds rounds.
+ *   dead_lnl, dead_logwt host [max_dead], dead_u host [max_dead][n_dim]
+ *   (may be NULL; the first min(n_dead - K, max_dead) dead points, in death
+ *   order, without the final live set).
+ * Synchronises the stream before returning. */
+int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+           int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+           double* dead_u, gwl_ns_result* out, void* stream);
+
 /* Size of the fixed device array used by gwl_loglike_static (16 MiB). */
 #define GWL_STATIC_SCRATCH_BYTES (16u << 20)
 

@@ -187,6 +187,7 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     if ((e = dev_alloc(c, &c->d_tab_mixed, n_bins * c->row_floats)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_tab_f64, n_bins * c->row_doubles)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_status, 4)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = cudaMalloc(&c->d_wscal, 64)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = cudaMalloc(&d_strain, sizeof(double) * 2 * n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = cudaMalloc(&d_psd, sizeof(double) * n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     double geom[9 * GWL_MAX_DET];
@@ -313,12 +314,64 @@ int gwl_grad(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, do
 int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, int64_t worst, double lnl_star,
                uint64_t seed, uint64_t counter, int64_t n_chains, int walk_len, double scale, const double* chol,
                double* out_u, double* out_lnl, int32_t* out_nacc, int32_t* out_start, void* stream) {
-  (void)live_u; (void)live_lnl; (void)K; (void)worst; (void)lnl_star; (void)seed; (void)counter;
-  (void)n_chains; (void)walk_len; (void)scale; (void)chol; (void)out_u; (void)out_lnl; (void)out_nacc;
-  (void)out_start; (void)stream;
   int rc = check_ctx(c);
   if (rc) return rc;
-  return fail(GWL_ERR_ARG, "ns_replace: not available in this build");
+  if (K < 2) return fail(GWL_ERR_ARG, "K = %lld < 2", (long long)K);
+  if (worst < 0 || worst >= K) return fail(GWL_ERR_ARG, "worst = %lld outside [0, K)", (long long)worst);
+  if (n_chains < 0 || n_chains > ((int64_t)1 << 31) - 1) return fail(GWL_ERR_ARG, "n_chains out of range");
+  if (walk_len < 0) return fail(GWL_ERR_ARG, "walk_len < 0");
+  if (!(scale > 0.0) || !std::isfinite(scale)) return fail(GWL_ERR_ARG, "scale must be positive");
+  if (n_chains == 0) return GWL_OK;
+  if (!live_u || !live_lnl || !chol || !out_u || !out_lnl || !out_nacc) return fail(GWL_ERR_ARG, "null device pointer");
+  const int D = c->opt.n_dim;
+  if ((rc = ensure_scratch(c, n_chains))) return rc;
+  if ((rc = ensure_bytes(c, (void**)&c->d_walk, &c->walk_cap, (int64_t)sizeof(double) * n_chains * (2 * D + 1))))
+    return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  unsigned char hs[64];
+  gwl::set_walk_scalars(hs, lnl_star, scale, worst, counter);
+  cudaError_t e = cudaMemcpyAsync(c->d_wscal, hs, gwl::walk_scalars_bytes(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ns_replace");
+  double* pu = c->d_walk;
+  double* pth = pu + n_chains * D;
+  double* plnl = pth + n_chains * D;
+  e = gwl::launch_walk(c, live_u, live_lnl, K, c->d_wscal, seed, n_chains, walk_len, chol, out_u, out_lnl, out_nacc,
+                       out_start, pu, pth, plnl, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ns_replace");
+  return GWL_OK;
+}
+
+int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz, int64_t max_rounds,
+           double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt, double* dead_u, gwl_ns_result* out,
+           void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!out) return fail(GWL_ERR_ARG, "out is null");
+  if (K < 2 || n_chains < 1 || walk_len < 1 || max_rounds < 0 || max_dead < 0)
+    return fail(GWL_ERR_ARG, "bad sizes (K >= 2, n_chains >= 1, walk_len >= 1 needed)");
+  if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
+  if (max_dead > 0 && (!dead_lnl || !dead_logwt || !dead_u)) return fail(GWL_ERR_ARG, "null dead-point buffer");
+  const int64_t nb = n_chains > K ? n_chains : K;
+  if ((rc = ensure_scratch(c, nb))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  double res[11];
+  const int r = gwl::ns_run_impl(c, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, max_dead, dead_lnl,
+                                 dead_logwt, dead_u, res, st, 1);
+  if (r != 0) return fail(GWL_ERR_CUDA, "ns_run: %s", cudaGetErrorString(cudaGetLastError()));
+  out->lnZ = res[0];
+  out->lnZ_err = res[1];
+  out->H = res[2];
+  out->n_dead = (int64_t)res[3];
+  out->n_proposals = (int64_t)res[4];
+  out->rounds = (int64_t)res[5];
+  out->scale = res[6];
+  out->acceptance = res[7];
+  out->consumed_per_round = res[8];
+  out->dlogz = res[9];
+  out->n_dead_returned = (int64_t)res[10];
+  return GWL_OK;
 }
 
 int gwl_sync(gwl_ctx* c) {
@@ -405,6 +458,8 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_work, c->work_cap);
   dev_free(c, c->d_status, 4);
   if (c->d_pgrad) cudaFree(c->d_pgrad);
+  if (c->d_walk) cudaFree(c->d_walk);
+  if (c->d_wscal) cudaFree(c->d_wscal);
   if (c->d_gpartials) cudaFree(c->d_gpartials);
   delete c;
 }

@@ -33,6 +33,9 @@ struct gwl_ctx {
   int64_t prop_cap = 0;
   double* d_partials = nullptr;  // [B][n_windows][2 n_det]
   int64_t partials_cap = 0;      // in doubles
+  double* d_walk = nullptr;      // ns_replace proposals: u' [n][D], theta' [n][D], lnL' [n]
+  int64_t walk_cap = 0;          // in doubles
+  void* d_wscal = nullptr;       // walk scalars (L*, scale, worst, counter)
   double* d_io = nullptr;        // staging for the host-buffer entry points
   int64_t io_cap = 0;            // in doubles
   void* d_pgrad = nullptr;       // per-proposal tangents of the gradient prologue
@@ -84,6 +87,17 @@ cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* l
 cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st);
 int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B);
 int64_t prop_grad_bytes(const gwl_ctx* c);
+
+// a7 / a9: random walks and nested sampling
+cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, const void* scalars,
+                        uint64_t seed, int64_t n_chains, int walk_len, const double* chol, double* out_u,
+                        double* out_lnl, int32_t* out_nacc, int32_t* out_start, double* pu, double* pth,
+                        double* plnl, cudaStream_t st);
+size_t walk_scalars_bytes();
+void set_walk_scalars(void* host_buf, double lstar, double scale, int64_t worst, uint64_t counter);
+int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+                double* dead_u, double* res, cudaStream_t st, int use_graph);
 
 // device-path template, for diagnostics and injections
 cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st);

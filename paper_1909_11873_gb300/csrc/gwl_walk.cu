@@ -1,0 +1,661 @@
+// gwl_walk.cu -- constrained random walks (ns_replace) and nested-sampling
+// bookkeeping on the device (Section 3 and Algorithm 1 of the paper).
+//
+// Parallel sampling step: n_chains chains each start at a live point other
+// than the current worst and make walk_len steps u' = u + scale * L z in the
+// unit cube (z standard normal, L a lower-triangular matrix from the live
+// set's covariance); periodic coordinates wrap, a step leaving the cube in any
+// other coordinate is rejected, and a step is accepted iff lnL(theta(u')) >=
+// L* (the worst live value).  Every step of all chains is one batched
+// likelihood evaluation, so the walk is: init, then walk_len times {propose,
+// batched lnL, accept}.
+//
+// Consumption (the replacement loop of Algorithm 1): candidates, in chain
+// order, replace successive worst live points; a candidate whose lnL does not
+// exceed the current worst is discarded (it was drawn above the round's first
+// threshold only), and the round ends when candidates run out.  Dead point i
+// gets the prior-volume weight dX_i = X_{i-1} - X_i with X_i = e^{-i/K}, so
+// lnZ is a log-sum-exp that needs no sequential accumulation.  The final live
+// points enter with equal weights X_N/(K+1).
+#include <cmath>
+
+#include "gwl_internal.h"
+
+namespace gwl {
+
+// ---------------------------------------------------------------- random numbers
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011): 10 rounds of the 4x32
+// S-P network, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key increments
+// 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Normals of walk step `step` of chain `chain` (Box-Muller on word pairs).
+__device__ __forceinline__ void walk_normals(uint64_t seed, uint64_t counter, uint32_t chain, uint32_t step, int D,
+                                             double* z) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int b = 0; 4 * b < D; ++b) {
+    const uint4 w = philox(make_uint4((uint32_t)b, step, chain, (uint32_t)counter), k0, k1);
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double u1 = ((double)ws[2 * h] + 1.0) * 0x1p-32;
+      const double u2 = (double)ws[2 * h + 1] * 0x1p-32;
+      const double r = sqrt(-2.0 * ::log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      const int i0 = 4 * b + 2 * h;
+      if (i0 < D) z[i0] = r * cs;
+      if (i0 + 1 < D) z[i0 + 1] = r * sn;
+    }
+  }
+}
+
+// Unit cube -> parameter (the context's prior of each sampled coordinate).
+struct PriorInfo {
+  int D;
+  int kind[11];
+  double lo[11], hi[11];
+  int periodic[11];
+};
+
+__device__ __forceinline__ double prior_map(int kind, double lo, double hi, double u) {
+  switch (kind) {
+    case GWL_PRIOR_VOLUME: return cbrt(lo * lo * lo + u * (hi * hi * hi - lo * lo * lo));
+    case GWL_PRIOR_SINE: return acos(1.0 - 2.0 * u);
+    case GWL_PRIOR_COSINE: return asin(2.0 * u - 1.0);
+    default: return lo + u * (hi - lo);
+  }
+}
+
+// ---------------------------------------------------------------- walk kernels
+// Device-resident scalars of one walk (written by the host for ns_replace, by
+// the preparation kernel inside ns_run).
+struct WalkScalars {
+  double lstar;
+  double scale;
+  long long worst;
+  unsigned long long counter;
+};
+
+__global__ void k_walk_init(const double* __restrict__ live_u, const double* __restrict__ live_lnl, int64_t K,
+                            int D, const WalkScalars* __restrict__ sc, uint64_t seed, int64_t n_chains,
+                            double* __restrict__ cu, double* __restrict__ cl, int32_t* __restrict__ cn,
+                            int32_t* __restrict__ cstart) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains) return;
+  const uint4 w = philox(make_uint4(0u, 0u, (uint32_t)b, (uint32_t)sc->counter), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+  const int64_t idx = (int64_t)(((uint64_t)w.x * (uint64_t)(K - 1)) >> 32);
+  const int64_t st = idx < sc->worst ? idx : idx + 1;
+  for (int i = 0; i < D; ++i) cu[b * D + i] = live_u[st * D + i];
+  cl[b] = live_lnl[st];
+  cn[b] = 0;
+  if (cstart) cstart[b] = (int32_t)st;
+}
+
+__global__ void k_walk_propose(PriorInfo pr, const WalkScalars* __restrict__ sc, const double* __restrict__ chol,
+                               uint64_t seed, uint32_t step, int64_t n_chains, const double* __restrict__ cu,
+                               double* __restrict__ pu, double* __restrict__ ptheta) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains) return;
+  const int D = pr.D;
+  double z[11];
+  walk_normals(seed, sc->counter, (uint32_t)b, step, D, z);
+  const double scale = sc->scale;
+  bool inside = true;
+  for (int i = 0; i < D; ++i) {
+    double dz = 0.0;
+    for (int k = 0; k <= i; ++k) dz += chol[i * D + k] * z[k];
+    double x = cu[b * D + i] + scale * dz;
+    if (pr.periodic[i]) x -= floor(x);
+    else if (x < 0.0 || x > 1.0) inside = false;
+    pu[b * D + i] = x;
+  }
+  for (int i = 0; i < D; ++i)
+    ptheta[b * D + i] = inside ? prior_map(pr.kind[i], pr.lo[i], pr.hi[i], pu[b * D + i]) : NAN;
+}
+
+__global__ void k_walk_accept(const WalkScalars* __restrict__ sc, int D, int64_t n_chains,
+                              const double* __restrict__ pu, const double* __restrict__ plnl, double* __restrict__ cu,
+                              double* __restrict__ cl, int32_t* __restrict__ cn) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains) return;
+  const double l = plnl[b];
+  if (l >= sc->lstar) {  // NaN rows (steps outside the cube) give -inf and fail
+    for (int i = 0; i < D; ++i) cu[b * D + i] = pu[b * D + i];
+    cl[b] = l;
+    cn[b] += 1;
+  }
+}
+
+// ---------------------------------------------------------------- nested-sampling state kernels
+struct NsDev {
+  // live set
+  double* lu;   // [K][D]
+  double* ll;   // [K]
+  int64_t K;
+  int D;
+  // candidates of the current round (the walk's outputs)
+  double* cu;
+  double* cl;
+  int32_t* cn;
+  int64_t n_chains;
+  // this round's dead points: lnL + ln dX, one per consumed candidate
+  double* rx;   // [n_chains]
+  double* rl;   // [n_chains] lnL
+  // dead points (kept up to cap for posterior samples)
+  double* dl;   // [cap]
+  double* dw;   // [cap] ln dX
+  double* du;   // [cap][D]
+  int64_t cap;
+  // scalars
+  WalkScalars* ws;
+  double* chol;   // [D][D]
+  double* stats;  // see NS_* below
+};
+
+// stats layout
+enum {
+  NS_LNZ = 0,        // ln Z of the dead points so far (m + ln ZS)
+  NS_NDEAD = 1,      // dead points so far (as double)
+  NS_LMAX = 2,       // largest live lnL
+  NS_ROUND = 3,      // rounds done
+  NS_DONE = 4,       // 1 once the stopping rule holds
+  NS_ACC_SUM = 5,    // sum over rounds of the acceptance fraction
+  NS_CONSUMED = 6,   // candidates consumed in total
+  NS_DLOGZ = 7,      // ln(Z + Lmax X) - ln Z after the last round
+  NS_NDEAD_ROUND0 = 8,  // dead count at the start of the round
+  NS_M = 9,          // reference maximum of lnL + ln dX
+  NS_ZS = 10,        // sum exp(lnL + ln dX - m)
+  NS_AS = 11,        // sum exp(lnL + ln dX - m) lnL   (for the information H)
+  NS_H = 12,         // information H = AS/ZS - ln Z
+  NS_NSTATS = 16
+};
+
+__device__ __forceinline__ double logaddexp_d(double a, double b) {
+  if (a == -INFINITY) return b;
+  if (b == -INFINITY) return a;
+  const double m = a > b ? a : b;
+  return m + ::log(::exp(a - m) + ::exp(b - m));
+}
+
+// Round preparation: worst live point and L*, Cholesky factor of the live-set
+// covariance in the unit cube (plain, FP64, one CTA).
+__global__ void __launch_bounds__(256) k_ns_prep(NsDev s) {
+  if (s.stats[NS_DONE] > 0.5) return;  // rounds replayed after the stopping rule held change nothing
+  __shared__ double red_v[256];
+  __shared__ long long red_i[256];
+  __shared__ double mean[11], cov[11 * 11];
+  const int t = threadIdx.x;
+  // argmin of the live lnL
+  double bv = INFINITY;
+  long long bi = 0;
+  for (int64_t k = t; k < s.K; k += blockDim.x) {
+    const double v = s.ll[k];
+    if (v < bv || (v == bv && k < bi)) {
+      bv = v;
+      bi = k;
+    }
+  }
+  red_v[t] = bv;
+  red_i[t] = bi;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (t < off) {
+      const double v = red_v[t + off];
+      const long long i = red_i[t + off];
+      if (v < red_v[t] || (v == red_v[t] && i < red_i[t])) {
+        red_v[t] = v;
+        red_i[t] = i;
+      }
+    }
+    __syncthreads();
+  }
+  const int D = s.D;
+  if (t < D) {
+    double m = 0.0;
+    for (int64_t k = 0; k < s.K; ++k) m += s.lu[k * D + t];
+    mean[t] = m / (double)s.K;
+  }
+  __syncthreads();
+  if (t < D * D) {
+    const int i = t / D, j = t % D;
+    double c = 0.0;
+    for (int64_t k = 0; k < s.K; ++k) c += (s.lu[k * D + i] - mean[i]) * (s.lu[k * D + j] - mean[j]);
+    cov[t] = c / (double)(s.K - 1);
+  }
+  __syncthreads();
+  if (t == 0) {
+    s.ws->lstar = red_v[0];
+    s.ws->worst = red_i[0];
+    s.ws->counter = (unsigned long long)s.stats[NS_ROUND];
+    // Cholesky (lower), diagonal fallback if the covariance is not positive definite
+    double L[11 * 11];
+    bool okc = true;
+    for (int j = 0; j < D && okc; ++j) {
+      double d = cov[j * D + j];
+      for (int k = 0; k < j; ++k) d -= L[j * D + k] * L[j * D + k];
+      if (!(d > 0.0)) {
+        okc = false;
+        break;
+      }
+      L[j * D + j] = sqrt(d);
+      for (int i = j + 1; i < D; ++i) {
+        double x = cov[i * D + j];
+        for (int k = 0; k < j; ++k) x -= L[i * D + k] * L[j * D + k];
+        L[i * D + j] = x / L[j * D + j];
+      }
+      for (int k = j + 1; k < D; ++k) L[j * D + k] = 0.0;
+    }
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j)
+        s.chol[i * D + j] = okc ? L[i * D + j] : (i == j ? sqrt(fmax(cov[i * D + i], 1e-300)) : 0.0);
+    s.stats[NS_NDEAD_ROUND0] = s.stats[NS_NDEAD];
+  }
+}
+
+// Consumption of the round's candidates, one warp: repeatedly find the worst
+// live point (warp argmin), take the next unused candidate with lnL above it,
+// record the dead point and replace it.
+__global__ void __launch_bounds__(32) k_ns_consume(NsDev s) {
+  if (s.stats[NS_DONE] > 0.5) return;
+  const int lane = threadIdx.x;
+  const int D = s.D;
+  int64_t ptr = 0;
+  int64_t nd = (int64_t)s.stats[NS_NDEAD];
+  int64_t consumed = 0;
+  while (true) {
+    double bv = INFINITY;
+    long long bi = 0;
+    for (int64_t k = lane; k < s.K; k += 32) {
+      const double v = s.ll[k];
+      if (v < bv || (v == bv && k < bi)) {
+        bv = v;
+        bi = k;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double v = __shfl_xor_sync(0xffffffffu, bv, off);
+      const long long i = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (v < bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
+      }
+    }
+    while (ptr < s.n_chains && !(s.cl[ptr] > bv)) ++ptr;
+    if (ptr >= s.n_chains) break;
+    ++nd;
+    const double lw = -(double)(nd - 1) / (double)s.K + log1p(-::exp(-1.0 / (double)s.K));  // ln(X_{i-1} - X_i)
+    if (lane == 0) {
+      s.rx[consumed] = bv + lw;
+      s.rl[consumed] = bv;
+    }
+    if (nd <= s.cap) {
+      if (lane == 0) {
+        s.dl[nd - 1] = bv;
+        s.dw[nd - 1] = lw;
+      }
+      for (int i = lane; i < D; i += 32) s.du[(nd - 1) * D + i] = s.lu[bi * D + i];
+    }
+    __syncwarp();
+    for (int i = lane; i < D; i += 32) s.lu[bi * D + i] = s.cu[ptr * D + i];
+    if (lane == 0) s.ll[bi] = s.cl[ptr];
+    __syncwarp();
+    ++ptr;
+    ++consumed;
+  }
+  if (lane == 0) {
+    s.stats[NS_NDEAD] = (double)nd;
+    s.stats[NS_CONSUMED] += (double)consumed;
+  }
+}
+
+// Fold n weighted points x_i = lnL_i + ln dX_i (with lnL_i) into the running
+// sums (m, ZS, AS) of stats; one CTA.
+__device__ void fold_points(double* stats, const double* x, const double* l, int64_t n, double* red) {
+  const int t = threadIdx.x;
+  double m = -INFINITY;
+  for (int64_t i = t; i < n; i += blockDim.x) m = fmax(m, x[i]);
+  red[t] = m;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (t < off) red[t] = fmax(red[t], red[t + off]);
+    __syncthreads();
+  }
+  const double mr = red[0];
+  __syncthreads();
+  const double mref = fmax(stats[NS_M], mr);
+  double zs = 0.0, as = 0.0;
+  if (mref > -INFINITY)
+    for (int64_t i = t; i < n; i += blockDim.x) {
+      const double e = ::exp(x[i] - mref);
+      zs += e;
+      as += e * l[i];
+    }
+  red[t] = zs;
+  red[blockDim.x + t] = as;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (t < off) {
+      red[t] += red[t + off];
+      red[blockDim.x + t] += red[blockDim.x + t + off];
+    }
+    __syncthreads();
+  }
+  if (t == 0 && mref > -INFINITY) {
+    const double r = stats[NS_M] > -INFINITY ? ::exp(stats[NS_M] - mref) : 0.0;
+    stats[NS_ZS] = stats[NS_ZS] * r + red[0];
+    stats[NS_AS] = stats[NS_AS] * r + red[blockDim.x];
+    stats[NS_M] = mref;
+    stats[NS_LNZ] = mref + ::log(stats[NS_ZS]);
+    stats[NS_H] = stats[NS_AS] / stats[NS_ZS] - stats[NS_LNZ];
+  }
+  __syncthreads();
+}
+
+// End of round: ln Z update from the round's dead points, largest live lnL,
+// stopping rule ln(Z + Lmax X) - ln Z < dlogz, acceptance and scale
+// adaptation scale <- scale exp(acc - 1/2) clamped to [1e-3, 1].
+__global__ void __launch_bounds__(256) k_ns_stats(NsDev s, int walk_len, double dlogz) {
+  if (s.stats[NS_DONE] > 0.5) return;
+  __shared__ double red[512];
+  const int t = threadIdx.x;
+  const int64_t nr = (int64_t)(s.stats[NS_NDEAD] - s.stats[NS_NDEAD_ROUND0]);
+  fold_points(s.stats, s.rx, s.rl, nr, red);
+  double lm = -INFINITY;
+  for (int64_t k = t; k < s.K; k += blockDim.x) lm = fmax(lm, s.ll[k]);
+  red[t] = lm;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (t < off) red[t] = fmax(red[t], red[t + off]);
+    __syncthreads();
+  }
+  const double lmax = red[0];
+  __syncthreads();
+  double na = 0.0;
+  for (int64_t b = t; b < s.n_chains; b += blockDim.x) na += (double)s.cn[b];
+  red[t] = na;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (t < off) red[t] += red[t + off];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double lnZ = s.stats[NS_LNZ];
+    s.stats[NS_LMAX] = lmax;
+    const double lnX = -s.stats[NS_NDEAD] / (double)s.K;
+    const double dz = logaddexp_d(lnZ, lmax + lnX) - lnZ;
+    s.stats[NS_DLOGZ] = dz;
+    if (dz < dlogz) s.stats[NS_DONE] = 1.0;
+    const double accf = red[0] / ((double)s.n_chains * (double)walk_len);
+    s.stats[NS_ACC_SUM] += accf;
+    s.ws->scale = fmin(1.0, fmax(1e-3, s.ws->scale * ::exp(accf - 0.5)));
+    s.stats[NS_ROUND] += 1.0;
+  }
+}
+
+// The final live points, each with prior volume X_N / (K + 1).
+__global__ void __launch_bounds__(256) k_ns_final(NsDev s) {
+  __shared__ double red[512];
+  const double lw = -s.stats[NS_NDEAD] / (double)s.K - ::log((double)(s.K + 1));
+  for (int64_t k = threadIdx.x; k < s.K; k += blockDim.x) s.rx[k] = s.ll[k] + lw;
+  __syncthreads();
+  fold_points(s.stats, s.rx, s.ll, s.K, red);
+}
+
+// Initial live points: uniform in the unit cube, Philox words (block, step
+// 0xFFFFFFFF, point k, 0xFFFFFFFF), u = (w + 1/2) 2^-32; theta by the prior map.
+__global__ void k_ns_init(PriorInfo pr, uint64_t seed, int64_t K, double* __restrict__ lu,
+                          double* __restrict__ theta) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const int D = pr.D;
+  for (int b = 0; 4 * b < D; ++b) {
+    const uint4 w = philox(make_uint4((uint32_t)b, 0xFFFFFFFFu, (uint32_t)k, 0xFFFFFFFFu), (uint32_t)seed,
+                           (uint32_t)(seed >> 32));
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    for (int i = 0; i < 4 && 4 * b + i < D; ++i) {
+      const double u = ((double)ws[i] + 0.5) * 0x1p-32;
+      lu[k * D + 4 * b + i] = u;
+      theta[k * D + 4 * b + i] = prior_map(pr.kind[4 * b + i], pr.lo[4 * b + i], pr.hi[4 * b + i], u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+static PriorInfo prior_info(const gwl_ctx* c) {
+  PriorInfo p;
+  p.D = c->opt.n_dim;
+  for (int i = 0; i < 11; ++i) {
+    p.kind[i] = c->opt.prior_kind[i];
+    p.lo[i] = c->opt.prior_lo[i];
+    p.hi[i] = c->opt.prior_hi[i];
+    p.periodic[i] = c->opt.periodic[i];
+  }
+  return p;
+}
+
+// The walk proper: chains start from live points and take walk_len steps.
+cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, const void* scalars,
+                        uint64_t seed, int64_t n_chains, int walk_len, const double* chol, double* out_u,
+                        double* out_lnl, int32_t* out_nacc, int32_t* out_start, double* pu, double* pth,
+                        double* plnl, cudaStream_t st) {
+  const WalkScalars* sc = static_cast<const WalkScalars*>(scalars);
+  const int D = c->opt.n_dim;
+  const unsigned nb = (unsigned)((n_chains + 127) / 128);
+  const PriorInfo pr = prior_info(c);
+  {
+    ProfScope ps(c, GWL_KERNEL_WALK, st);
+    k_walk_init<<<nb, 128, 0, st>>>(live_u, live_lnl, K, D, sc, seed, n_chains, out_u, out_lnl, out_nacc, out_start);
+    c->launches++;
+  }
+  cudaError_t e = cudaGetLastError();
+  for (int s = 1; s <= walk_len && e == cudaSuccess; ++s) {
+    {
+      ProfScope ps(c, GWL_KERNEL_WALK, st);
+      k_walk_propose<<<nb, 128, 0, st>>>(pr, sc, chol, seed, (uint32_t)s, n_chains, out_u, pu, pth);
+      c->launches++;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = launch_loglike(c, pth, n_chains, plnl, st)) != cudaSuccess) break;
+    {
+      ProfScope ps(c, GWL_KERNEL_WALK, st);
+      k_walk_accept<<<nb, 128, 0, st>>>(sc, D, n_chains, pu, plnl, out_u, out_lnl, out_nacc);
+      c->launches++;
+    }
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_ns_init(gwl_ctx* c, uint64_t seed, int64_t K, double* lu, double* theta, cudaStream_t st) {
+  k_ns_init<<<(unsigned)((K + 127) / 128), 128, 0, st>>>(prior_info(c), seed, K, lu, theta);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_round(gwl_ctx* c, const NsDev& s, uint64_t seed, int walk_len, double dlogz, double* pu,
+                            double* pth, double* plnl, cudaStream_t st) {
+  k_ns_prep<<<1, 256, 0, st>>>(s);
+  c->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_walk(c, s.lu, s.ll, s.K, s.ws, seed, s.n_chains, walk_len, s.chol, s.cu, s.cl, s.cn, nullptr, pu, pth,
+                  plnl, st);
+  if (e != cudaSuccess) return e;
+  k_ns_consume<<<1, 32, 0, st>>>(s);
+  k_ns_stats<<<1, 256, 0, st>>>(s, walk_len, dlogz);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+size_t walk_scalars_bytes() { return sizeof(WalkScalars); }
+
+void set_walk_scalars(void* host_buf, double lstar, double scale, int64_t worst, uint64_t counter) {
+  WalkScalars* w = static_cast<WalkScalars*>(host_buf);
+  w->lstar = lstar;
+  w->scale = scale;
+  w->worst = worst;
+  w->counter = counter;
+}
+
+// Static nested sampling run with all state on the device.
+static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                     int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+                     double* dead_u, double* res, cudaStream_t st, int use_graph);
+
+// The run is captured into a CUDA graph, which needs a capturable stream: it
+// runs on a private non-blocking stream after the caller's stream drains.
+int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+                double* dead_u, double* res, cudaStream_t caller, int use_graph) {
+  if (cudaStreamSynchronize(caller) != cudaSuccess) return -2;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -2;
+  const int rc = ns_run_on(c, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, max_dead, dead_lnl, dead_logwt,
+                           dead_u, res, st, use_graph);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  return rc;
+}
+
+static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                     int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+                     double* dead_u, double* res, cudaStream_t st, int use_graph) {
+  const int D = c->opt.n_dim;
+  const int64_t cap = max_dead > 0 ? max_dead : 1;
+  const int64_t rbuf = n_chains > K ? n_chains : K;
+  NsDev s;
+  s.K = K;
+  s.D = D;
+  s.n_chains = n_chains;
+  s.cap = cap;
+  double* pu = nullptr;
+  double* pth = nullptr;
+  double* plnl = nullptr;
+  void* blocks[16] = {nullptr};
+  int nblk = 0;
+  auto alloc = [&](void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 8);
+    if (e == cudaSuccess) blocks[nblk++] = *p;
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = alloc((void**)&s.lu, sizeof(double) * K * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.ll, sizeof(double) * K)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.cu, sizeof(double) * n_chains * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.cl, sizeof(double) * n_chains)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.cn, sizeof(int32_t) * n_chains)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.rx, sizeof(double) * rbuf)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.rl, sizeof(double) * rbuf)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.dl, sizeof(double) * cap)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.dw, sizeof(double) * cap)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.du, sizeof(double) * cap * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.ws, sizeof(WalkScalars))) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.chol, sizeof(double) * D * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&s.stats, sizeof(double) * NS_NSTATS)) != cudaSuccess) break;
+    if ((e = alloc((void**)&pu, sizeof(double) * rbuf * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&pth, sizeof(double) * rbuf * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&plnl, sizeof(double) * rbuf)) != cudaSuccess) break;
+  } while (false);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < nblk; ++i) cudaFree(blocks[i]);
+    return -2;
+  }
+  double st0[NS_NSTATS] = {0};
+  st0[NS_LNZ] = -INFINITY;
+  st0[NS_M] = -INFINITY;
+  st0[NS_LMAX] = -INFINITY;
+  WalkScalars w0;
+  w0.lstar = -INFINITY;
+  w0.scale = scale0;
+  w0.worst = 0;
+  w0.counter = 0;
+  int rc = 0;
+  do {
+    if ((e = cudaMemcpyAsync(s.stats, st0, sizeof(st0), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(s.ws, &w0, sizeof(w0), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = launch_ns_init(c, seed, K, s.lu, pth, st)) != cudaSuccess) break;
+    if ((e = launch_loglike(c, pth, K, s.ll, st)) != cudaSuccess) break;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const bool prof = c->profiling;
+    if (use_graph) {
+      c->profiling = false;
+      if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+      cudaError_t er = launch_ns_round(c, s, seed, walk_len, dlogz, pu, pth, plnl, st);
+      e = cudaStreamEndCapture(st, &graph);
+      c->profiling = prof;
+      if (er != cudaSuccess) e = er;
+      if (e != cudaSuccess) break;
+      if ((e = cudaGraphInstantiate(&gexec, graph, 0)) != cudaSuccess) break;
+    }
+    double stats[NS_NSTATS];
+    int64_t r = 0;
+    const int check = 4;
+    while (r < max_rounds) {
+      const int64_t todo = (max_rounds - r) < check ? (max_rounds - r) : check;
+      for (int64_t i = 0; i < todo && e == cudaSuccess; ++i) {
+        e = use_graph ? cudaGraphLaunch(gexec, st) : launch_ns_round(c, s, seed, walk_len, dlogz, pu, pth, plnl, st);
+        if (e == cudaSuccess) c->launches += use_graph ? (int64_t)(4 + walk_len * 5) : 0;
+      }
+      if (e != cudaSuccess) break;
+      r += todo;
+      if ((e = cudaMemcpyAsync(stats, s.stats, sizeof(stats), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+      if (stats[NS_DONE] > 0.5) break;
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) break;
+    // rounds after the stopping rule held are no-ops only if none ran: the
+    // loop checks every `check` rounds, so report the rounds actually run
+    k_ns_final<<<1, 256, 0, st>>>(s);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(stats, s.stats, sizeof(stats), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    const int64_t nd = (int64_t)stats[NS_NDEAD];
+    const int64_t nk = nd < cap ? nd : cap;
+    if (dead_lnl && max_dead > 0)
+      if ((e = cudaMemcpy(dead_lnl, s.dl, sizeof(double) * nk, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    if (dead_logwt && max_dead > 0)
+      if ((e = cudaMemcpy(dead_logwt, s.dw, sizeof(double) * nk, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    if (dead_u && max_dead > 0)
+      if ((e = cudaMemcpy(dead_u, s.du, sizeof(double) * nk * D, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    const double rounds = stats[NS_ROUND];
+    res[0] = stats[NS_LNZ];
+    res[1] = sqrt(fmax(stats[NS_H], 0.0) / (double)K);
+    res[2] = stats[NS_H];
+    res[3] = (double)nd + (double)K;
+    res[4] = (double)K + rounds * (double)n_chains * (double)walk_len;
+    res[5] = rounds;
+    WalkScalars wl;
+    if ((e = cudaMemcpy(&wl, s.ws, sizeof(wl), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    res[6] = wl.scale;
+    res[7] = rounds > 0 ? stats[NS_ACC_SUM] / rounds : 0.0;
+    res[8] = rounds > 0 ? stats[NS_CONSUMED] / rounds : 0.0;
+    res[9] = stats[NS_DLOGZ];
+    res[10] = (double)nk;
+  } while (false);
+  if (e != cudaSuccess) rc = -2;
+  cudaStreamSynchronize(st);
+  for (int i = 0; i < nblk; ++i) cudaFree(blocks[i]);
+  return rc;
+}
+
+}  // namespace gwl

@@ -23,7 +23,7 @@ N_PARAM = 11
 MAX_DET = 4
 
 # exported symbols declared in include/gwl.h
-EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "gwl_grad", "gwl_waveform", "ns_replace",
+EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "ns_run", "gwl_grad", "gwl_waveform", "ns_replace",
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error")
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
@@ -49,6 +49,12 @@ class GwlOptions(C.Structure):
     ]
 
 
+class GwlNsResult(C.Structure):
+    _fields_ = [("lnZ", C.c_double), ("lnZ_err", C.c_double), ("H", C.c_double), ("n_dead", C.c_int64),
+                ("n_proposals", C.c_int64), ("rounds", C.c_int64), ("scale", C.c_double), ("acceptance", C.c_double),
+                ("consumed_per_round", C.c_double), ("dlogz", C.c_double), ("n_dead_returned", C.c_int64)]
+
+
 class GwlError(RuntimeError):
     pass
 
@@ -71,6 +77,7 @@ def lib() -> C.CDLL:
         L.gwl_grad.argtypes = [P, P, i64, P, P, P]
         L.gwl_waveform.argtypes = [P, P, i64, P, P]
         L.ns_replace.argtypes = [P, P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, P]
+        L.ns_run.argtypes = [P, i64, i64, i32, u64, d, i64, d, i64, P, P, P, C.POINTER(GwlNsResult), P]
         L.gwl_sync.argtypes = [P]
         L.gwl_set_tuning.argtypes = [P, i32, i32, i32]
         L.gwl_profile.argtypes = [P, i32]
@@ -203,6 +210,24 @@ class Context:
                                 int(seed), int(counter), int(n_chains), int(walk_len), float(scale), _ptr(chol),
                                 _ptr(out_u), _ptr(out_lnl), _ptr(out_nacc), _ptr(out_start), _stream(stream)),
                "ns_replace")
+
+    def ns_run(self, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0, max_dead=0,
+               stream=None):
+        """Static parallel nested sampling on the device; returns a dict (plus dead points if max_dead > 0)."""
+        r = GwlNsResult()
+        D = self.n_dim
+        dl = np.zeros(max(max_dead, 1))
+        dw = np.zeros(max(max_dead, 1))
+        du = np.zeros((max(max_dead, 1), D))
+        _check(lib().ns_run(self._h, int(K), int(n_chains), int(walk_len), int(seed), float(dlogz), int(max_rounds),
+                            float(scale0), int(max_dead), dl.ctypes.data if max_dead else None,
+                            dw.ctypes.data if max_dead else None, du.ctypes.data if max_dead else None, C.byref(r),
+                            _stream(stream)), "ns_run")
+        out = {k: getattr(r, k) for k, _ in GwlNsResult._fields_}
+        if max_dead:
+            n = r.n_dead_returned
+            out.update(dead_lnl=dl[:n], dead_logwt=dw[:n], dead_u=du[:n])
+        return out
 
     def gwl_sync(self):
         _check(lib().gwl_sync(self._h), "gwl_sync")
