@@ -129,7 +129,7 @@ def measured_peaks():
         return {}
 
 
-def device_event(ctx, precision):
+def device_event(ctx, precision, name=None):
     """The benchmark event, with the injection made by the device library (no oracle on this leg)."""
     from paper_1909_11873_gb300 import gwl
     import torch
@@ -154,10 +154,60 @@ def device_event(ctx, precision):
         c = zero_ctx(ev)
         return -2.0 * float(gwl.loglike(c, torch.from_numpy(np.ascontiguousarray(th[None])).cuda()).cpu()[0])
 
-    ev = I.make_event(CONFIG, SEED, waveform, snr2)
+    ev = I.make_event(name or CONFIG, SEED, waveform, snr2)
     for c in cache.values():
         c.close()
     return ev
+
+
+GRAD_BATCH = 4096
+NS_K, NS_CHAINS, NS_WALK = 250, 250, 20
+
+
+def run_grad(ev, args, flush, stream):
+    """grad lnL evals/s on the same data (4096 proposals), device-timed, L2 flushed between steps."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    th = I.proposals(ev, GRAD_BATCH, SEED + 7)
+    x = torch.from_numpy(I.reduced(th, ev.sampling)).cuda()
+    ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
+    out = torch.empty(GRAD_BATCH, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(x)
+    for _ in range(args.warmup):
+        ctx.gwl_grad(x, out, g, stream)
+    torch.cuda.synchronize()
+    steps = max(10, args.steps // 2)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        flush.fill_(1.0)
+        e0.record(stream)
+        ctx.gwl_grad(x, out, g, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    ctx.close()
+    return {"value": GRAD_BATCH / (ms * 1e-3), "unit": "grad evals/s", "ms_per_step": ms, "batch": GRAD_BATCH,
+            "steps": steps, "precision": "mixed", "workload": "same 3-det 8 s data, 11-D gradient"}
+
+
+def run_ns(args):
+    """Wall time of a full nested-sampling run on the 1-detector 4 s zero-noise event (4-D)."""
+    from paper_1909_11873_gb300 import gwl
+
+    ev1 = device_event(None, None, name="c1")
+    ctx = gwl.Context.from_event(ev1, gwl.GWL_MIXED)
+    ctx.ns_run(NS_K, NS_CHAINS, NS_WALK, seed=1, dlogz=0.1, max_rounds=2)  # warm-up (graph build, scratch)
+    t0 = time.perf_counter()
+    r = ctx.ns_run(NS_K, NS_CHAINS, NS_WALK, seed=2, dlogz=0.1)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    return {"wall_s": wall, "lnZ": r["lnZ"], "lnZ_err": r["lnZ_err"], "rounds": r["rounds"],
+            "n_proposals": r["n_proposals"], "consumed_per_round": r["consumed_per_round"],
+            "workload": f"1-det 4 s 20-512 Hz zero-noise, 4-D, K={NS_K}, {NS_CHAINS} chains, walk {NS_WALK}, "
+                        "dlogz 0.1, mixed precision"}
 
 
 def run_gwl(args):
@@ -241,6 +291,8 @@ def run_gwl(args):
 
     # end-to-end with host buffers
     ms_e2e, _, _ = timed(mixed, max(5, args.steps // 2), args.warmup, host=True)
+    grad_res = run_grad(ev, args, flush, stream) if rank == 0 else None
+    ns_res = run_ns(args) if rank == 0 else None
 
     # algorithmic work of one launch: in-band (proposal, bin) pairs (ncut from the prologue's f_ISCO)
     eta = theta_full[:, 1] / (1 + theta_full[:, 1]) ** 2
@@ -299,9 +351,12 @@ def run_gwl(args):
                       "combine": prof[gwl.KERNEL_COMBINE][0] / max(prof[gwl.KERNEL_COMBINE][1], 1)},
         "clocks": clk,
         "gpu_launches": int(results[gwl.GWL_MIXED]["launches"]),
+        "grad": grad_res,
+        "ns": ns_res,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(theta_full, args.cpu_seconds, use_device_event=ev)
+        out["cpu_baseline"]["ns_wall_s"] = oracle_ns_wall()
     for c in ctxs.values():
         c.close()
     if rank == 0:
@@ -340,6 +395,23 @@ def cpu_baseline(theta_full, seconds, use_device_event=None):
     return {"value": done / el, "unit": "evals/s", "cores": n, "kind": "oracle",
             "sample": f"{done} evaluations = repeated first 1024 proposals of the 8192-proposal batch "
                       f"(same event, oracle-made injection), {el:.1f} s wall"}
+
+
+def oracle_ns_wall():
+    """The oracle's nested sampler on the same 1-detector event and settings (host cores)."""
+    import oracle
+
+    def wf(ev, th):
+        return oracle.waveform(ev, th)
+
+    def snr2(ev, th):
+        return -2.0 * oracle.loglike(ev.with_strain(np.zeros_like(ev.strain)), th[None])[0]
+
+    ev1 = I.make_event("c1", SEED, wf, snr2)
+    t0 = time.perf_counter()
+    r = oracle.ns_run(ev1, ev1.sampling, NS_K, NS_CHAINS, NS_WALK, seed=2, dlogz=0.1)
+    return {"wall_s": time.perf_counter() - t0, "lnZ": r["lnZ"], "lnZ_err": r["lnZ_err"], "rounds": r["rounds"],
+            "cores": os.cpu_count()}
 
 
 def run_reference(args):

@@ -378,7 +378,10 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   }
   {
     ProfScope ps(c, GWL_KERNEL_GRAD, st);
-    e = launch_pdl(k_window_grad<NDET, MIXED>, dim3(c->num_sms * 2), dim3(256), smem, st, a);
+    int64_t want = ((B + 7) / 8) * nw_total;
+    int grid = c->num_sms * 2;
+    if (want < grid) grid = (int)(want > 0 ? want : 1);
+    e = launch_pdl(k_window_grad<NDET, MIXED>, dim3(grid), dim3(256), smem, st, a);
     c->launches++;
     if (e != cudaSuccess) return e;
   }

@@ -458,7 +458,10 @@ static cudaError_t run_pipeline(gwl_ctx* c, int64_t B, double* lnl, cudaStream_t
   a.work = c->d_work;
   a.status = c->d_status;
   const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double));
-  const int grid = c->num_sms * c->ctas_per_sm;
+  // enough CTAs for every warp of a window to find a proposal, at most a full wave
+  int64_t want = ((B + 7) / 8) * nw_total;
+  int grid = c->num_sms * c->ctas_per_sm;
+  if (want < grid) grid = (int)(want > 0 ? want : 1);
   cudaError_t e = mixed ? run_window<NDET, true>(c, a, grid, smem, st) : run_window<NDET, false>(c, a, grid, smem, st);
   if (e != cudaSuccess) return e;
   {

@@ -49,6 +49,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--entry", default="loglike", choices=["loglike", "grad"])
+    ap.add_argument("--time", action="store_true", help="report device-timed evals/s (L2 flushed between calls)")
     a = ap.parse_args()
     import torch
 
@@ -62,14 +63,29 @@ def main():
     ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED if a.precision == "mixed" else gwl.GWL_FP64)
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(th)
-    for _ in range(a.iters):
+    def call():
         if a.entry == "grad":
             ctx.gwl_grad(th, out, grad)
         else:
             ctx.gwl_loglike(th, out)
+
+    for _ in range(a.iters):
+        call()
     torch.cuda.synchronize()
     ctx.gwl_sync()
-    print(f"{a.config} {a.precision} {a.entry} B={B} iters={a.iters} lnL[0]={out[0].item():.6f}")
+    msg = f"{a.config} {a.precision} {a.entry} B={B} iters={a.iters} lnL[0]={out[0].item():.6f}"
+    if a.time:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record()
+            call()
+            e1.record()
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in evs) / len(evs)
+        msg += f" ms/call={ms:.4f} evals/s={B / (ms * 1e-3):.4e}"
+    print(msg)
 
 
 if __name__ == "__main__":
