@@ -197,6 +197,32 @@ int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t see
            int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
            double* dead_u, gwl_ns_result* out, void* stream);
 
+/* ---- many events in one batch ----
+ * A multi-event context groups n_events contexts (same device, detector
+ * count, precision and sampled dimension; different segment lengths and
+ * priors allowed).  It borrows them: they must outlive it. */
+typedef struct gwl_multi gwl_multi;
+
+int gwl_multi_create(gwl_ctx* const* ctxs, int n_events, gwl_multi** out);
+
+/* Batched lnL of n_per proposals of every event in one launch sequence
+ * (prologue, a persistent bin loop over (event, window) tasks, combination).
+ *   theta_dev dev [n_events][n_per][n_dim], lnl_dev dev [n_events][n_per]. */
+int gwl_multi_loglike(gwl_multi* m, const double* theta_dev, int64_t n_per, double* lnl_dev, void* stream);
+
+/* ns_run for all events at once: every round is one sequence of launches
+ * (CUDA graph) covering all events; each event has its own live set, walk
+ * scale and Philox key seed + e * 0x9E3779B97F4A7C15.  Stops when every
+ * event's stopping rule holds or after max_rounds.  out: [n_events] results
+ * (no dead-point arrays).  Synchronises the stream. */
+int gwl_multi_ns_run(gwl_multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                     int64_t max_rounds, double scale0, gwl_ns_result* out, void* stream);
+
+/* Kernel launches issued by the multi-event context. */
+int64_t gwl_multi_launch_count(const gwl_multi* m);
+
+void gwl_multi_destroy(gwl_multi* m);
+
 /* Size of the fixed device array used by gwl_loglike_static (16 MiB). */
 #define GWL_STATIC_SCRATCH_BYTES (16u << 20)
 

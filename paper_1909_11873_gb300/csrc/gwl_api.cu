@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gwl_internal.h"
 
@@ -352,6 +353,7 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
     return fail(GWL_ERR_ARG, "bad sizes (K >= 2, n_chains >= 1, walk_len >= 1 needed)");
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
   if (max_dead > 0 && (!dead_lnl || !dead_logwt || !dead_u)) return fail(GWL_ERR_ARG, "null dead-point buffer");
+  if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "ns_run supports K <= 4096 and n_chains <= 4096");
   const int64_t nb = n_chains > K ? n_chains : K;
   if ((rc = ensure_scratch(c, nb))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -372,6 +374,82 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
   out->dlogz = res[9];
   out->n_dead_returned = (int64_t)res[10];
   return GWL_OK;
+}
+
+struct gwl_multi {
+  gwl::Multi* m;
+  int E;
+  int device;
+};
+
+int gwl_multi_create(gwl_ctx* const* ctxs, int n_events, gwl_multi** out) {
+  if (!out) return fail(GWL_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!ctxs || n_events < 1) return fail(GWL_ERR_ARG, "need at least one context");
+  for (int e = 0; e < n_events; ++e) {
+    const gwl_ctx* c = ctxs[e];
+    if (!c) return fail(GWL_ERR_ARG, "context %d is null", e);
+    if (c->device != ctxs[0]->device || c->n_det != ctxs[0]->n_det || c->opt.precision != ctxs[0]->opt.precision ||
+        c->opt.n_dim != ctxs[0]->opt.n_dim)
+      return fail(GWL_ERR_ARG, "context %d differs in device, detectors, precision or dimension", e);
+  }
+  int rc = check_ctx(ctxs[0]);
+  if (rc) return rc;
+  gwl_multi* h = new (std::nothrow) gwl_multi();
+  if (!h) return fail(GWL_ERR_NOMEM, "host allocation failed");
+  h->m = gwl::multi_new(ctxs, n_events);
+  h->E = n_events;
+  h->device = ctxs[0]->device;
+  *out = h;
+  return GWL_OK;
+}
+
+int gwl_multi_loglike(gwl_multi* h, const double* theta_dev, int64_t n_per, double* lnl_dev, void* stream) {
+  if (!h) return fail(GWL_ERR_ARG, "null multi-event context");
+  if (n_per < 0) return fail(GWL_ERR_ARG, "n_per < 0");
+  if (n_per == 0) return GWL_OK;
+  if (!theta_dev || !lnl_dev) return fail(GWL_ERR_ARG, "null device pointer");
+  cudaError_t e = gwl::multi_prepare(h->m, n_per);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_multi_loglike");
+  e = gwl::multi_loglike(h->m, theta_dev, n_per, lnl_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_multi_loglike");
+  return GWL_OK;
+}
+
+int gwl_multi_ns_run(gwl_multi* h, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                     int64_t max_rounds, double scale0, gwl_ns_result* out, void* stream) {
+  if (!h || !out) return fail(GWL_ERR_ARG, "null argument");
+  if (K < 2 || n_chains < 1 || walk_len < 1 || max_rounds < 0) return fail(GWL_ERR_ARG, "bad sizes");
+  if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "gwl_multi_ns_run supports K, n_chains <= 4096");
+  if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
+  std::vector<double> res((size_t)11 * h->E);
+  const int r = gwl::multi_ns_run(h->m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res.data(),
+                                  (cudaStream_t)stream);
+  if (r != 0) return fail(GWL_ERR_CUDA, "gwl_multi_ns_run: %s", cudaGetErrorString(cudaGetLastError()));
+  for (int e = 0; e < h->E; ++e) {
+    const double* x = res.data() + 11 * e;
+    gwl_ns_result& o = out[e];
+    o.lnZ = x[0];
+    o.lnZ_err = x[1];
+    o.H = x[2];
+    o.n_dead = (int64_t)x[3];
+    o.n_proposals = (int64_t)x[4];
+    o.rounds = (int64_t)x[5];
+    o.scale = x[6];
+    o.acceptance = x[7];
+    o.consumed_per_round = x[8];
+    o.dlogz = x[9];
+    o.n_dead_returned = 0;
+  }
+  return GWL_OK;
+}
+
+int64_t gwl_multi_launch_count(const gwl_multi* h) { return h ? gwl::multi_launches(h->m) : 0; }
+
+void gwl_multi_destroy(gwl_multi* h) {
+  if (!h) return;
+  gwl::multi_delete(h->m);
+  delete h;
 }
 
 int gwl_sync(gwl_ctx* c) {

@@ -99,6 +99,16 @@ int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t 
                 int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
                 double* dead_u, double* res, cudaStream_t st, int use_graph);
 
+// many events in one batched evaluation
+struct Multi;
+Multi* multi_new(gwl_ctx* const* ctxs, int E);
+void multi_delete(Multi* m);
+cudaError_t multi_prepare(Multi* m, int64_t n_per);
+cudaError_t multi_loglike(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st);
+int64_t multi_launches(const Multi* m);
+int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                 int64_t max_rounds, double scale0, double* res /* [E][11] */, cudaStream_t caller);
+
 // device-path template, for diagnostics and injections
 cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st);
 

@@ -409,5 +409,9 @@ void multi_delete(Multi* m) {
 }
 
 int64_t multi_launches(const Multi* m) { return m ? m->launches : 0; }
+int multi_events(const Multi* m) { return m->E; }
+int multi_dim(const Multi* m) { return m->D; }
+gwl_ctx* multi_ctx(const Multi* m, int e) { return m->ctxs[e]; }
+void multi_count(Multi* m, int64_t n) { m->launches += n; }
 
 }  // namespace gwl

@@ -18,6 +18,7 @@
 // lnZ is a log-sum-exp that needs no sequential accumulation.  The final live
 // points enter with equal weights X_N/(K+1).
 #include <cmath>
+#include <vector>
 
 #include "gwl_internal.h"
 
@@ -193,7 +194,7 @@ __device__ __forceinline__ double logaddexp_d(double a, double b) {
 
 // Round preparation: worst live point and L*, Cholesky factor of the live-set
 // covariance in the unit cube (plain, FP64, one CTA).
-__global__ void __launch_bounds__(256) k_ns_prep(NsDev s) {
+__device__ void ns_prep_body(const NsDev& s) {
   if (s.stats[NS_DONE] > 0.5) return;  // rounds replayed after the stopping rule held change nothing
   __shared__ double red_v[256];
   __shared__ long long red_i[256];
@@ -224,19 +225,52 @@ __global__ void __launch_bounds__(256) k_ns_prep(NsDev s) {
     __syncthreads();
   }
   const int D = s.D;
-  if (t < D) {
+  // mean and covariance of the live set: thread t handles one (dimension or
+  // pair) and one slice of the points; slices are reduced through shared memory
+  __shared__ double part[256];
+  {
+    const int S = blockDim.x / D;
+    const int i = t % D, sl = t / D;
     double m = 0.0;
-    for (int64_t k = 0; k < s.K; ++k) m += s.lu[k * D + t];
-    mean[t] = m / (double)s.K;
+    if (sl < S)
+      for (int64_t k = sl; k < s.K; k += S) m += s.lu[k * D + i];
+    part[t] = sl < S ? m : 0.0;
+    __syncthreads();
+    if (t < D) {
+      double a = 0.0;
+      for (int q = 0; q < S; ++q) a += part[q * D + t];
+      mean[t] = a / (double)s.K;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (t < D * D) {
-    const int i = t / D, j = t % D;
+  {
+    const int P = D * (D + 1) / 2;
+    const int S = blockDim.x / P;
+    const int pr = t % P, sl = t / P;
+    int i = 0, j = pr;
+    while (j >= D - i) {
+      j -= D - i;
+      ++i;
+    }
+    j += i;  // pair index -> (i, j), i <= j
     double c = 0.0;
-    for (int64_t k = 0; k < s.K; ++k) c += (s.lu[k * D + i] - mean[i]) * (s.lu[k * D + j] - mean[j]);
-    cov[t] = c / (double)(s.K - 1);
+    if (sl < S)
+      for (int64_t k = sl; k < s.K; k += S) c += (s.lu[k * D + i] - mean[i]) * (s.lu[k * D + j] - mean[j]);
+    part[t] = sl < S ? c : 0.0;
+    __syncthreads();
+    if (t < P) {
+      double a = 0.0;
+      for (int q = 0; q < S; ++q) a += part[q * P + t];
+      int ii = 0, jj = t;
+      while (jj >= D - ii) {
+        jj -= D - ii;
+        ++ii;
+      }
+      jj += ii;
+      cov[ii * D + jj] = cov[jj * D + ii] = a / (double)(s.K - 1);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (t == 0) {
     s.ws->lstar = red_v[0];
     s.ws->worst = red_i[0];
@@ -266,61 +300,102 @@ __global__ void __launch_bounds__(256) k_ns_prep(NsDev s) {
   }
 }
 
-// Consumption of the round's candidates, one warp: repeatedly find the worst
-// live point (warp argmin), take the next unused candidate with lnL above it,
-// record the dead point and replace it.
-__global__ void __launch_bounds__(32) k_ns_consume(NsDev s) {
+// Consumption of the round's candidates.  The sequential replacement loop
+// (warp 0) touches only shared memory: the live lnL, the candidates' lnL and,
+// per live slot, where its point currently comes from (an original live point
+// or a candidate).  The unit-cube coordinates of dead points and of the
+// replaced slots are then copied by the whole CTA.
+__device__ void ns_consume_body(const NsDev& s) {
   if (s.stats[NS_DONE] > 0.5) return;
-  const int lane = threadIdx.x;
+  extern __shared__ __align__(16) unsigned char smc[];
+  double* ll = reinterpret_cast<double*>(smc);     // [K]
+  double* cl = ll + s.K;                           // [n_chains]
+  int* src = reinterpret_cast<int*>(cl + s.n_chains);  // [K]   -1: original, else candidate index
+  int* rslot = src + s.K;                          // [n_chains] slot replaced at step r
+  int* rsrc = rslot + s.n_chains;                  // [n_chains] source of the dead point at step r
+  __shared__ int sh_nrep;
+  const int t = threadIdx.x, lane = t & 31;
   const int D = s.D;
-  int64_t ptr = 0;
-  int64_t nd = (int64_t)s.stats[NS_NDEAD];
-  int64_t consumed = 0;
-  while (true) {
-    double bv = INFINITY;
-    long long bi = 0;
-    for (int64_t k = lane; k < s.K; k += 32) {
-      const double v = s.ll[k];
-      if (v < bv || (v == bv && k < bi)) {
-        bv = v;
-        bi = k;
+  for (int64_t k = t; k < s.K; k += blockDim.x) {
+    ll[k] = s.ll[k];
+    src[k] = -1;
+  }
+  for (int64_t b = t; b < s.n_chains; b += blockDim.x) cl[b] = s.cl[b];
+  __syncthreads();
+  const int64_t nd0 = (int64_t)s.stats[NS_NDEAD];
+  if (t < 32) {
+    int64_t ptr = 0;
+    int nrep = 0;
+    const double lw1 = log1p(-::exp(-1.0 / (double)s.K));
+    while (true) {
+      double bv = INFINITY;
+      int bi = 0;
+      for (int k = lane; k < s.K; k += 32) {
+        const double v = ll[k];
+        if (v < bv || (v == bv && k < bi)) {
+          bv = v;
+          bi = k;
+        }
       }
-    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double v = __shfl_xor_sync(0xffffffffu, bv, off);
-      const long long i = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (v < bv || (v == bv && i < bi)) {
-        bv = v;
-        bi = i;
+      for (int off = 16; off > 0; off >>= 1) {
+        const double v = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int i = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (v < bv || (v == bv && i < bi)) {
+          bv = v;
+          bi = i;
+        }
       }
-    }
-    while (ptr < s.n_chains && !(s.cl[ptr] > bv)) ++ptr;
-    if (ptr >= s.n_chains) break;
-    ++nd;
-    const double lw = -(double)(nd - 1) / (double)s.K + log1p(-::exp(-1.0 / (double)s.K));  // ln(X_{i-1} - X_i)
-    if (lane == 0) {
-      s.rx[consumed] = bv + lw;
-      s.rl[consumed] = bv;
-    }
-    if (nd <= s.cap) {
+      while (ptr < s.n_chains && !(cl[ptr] > bv)) ++ptr;
+      if (ptr >= s.n_chains) break;
       if (lane == 0) {
-        s.dl[nd - 1] = bv;
-        s.dw[nd - 1] = lw;
+        const int64_t nd = nd0 + nrep + 1;
+        const double lw = -(double)(nd - 1) / (double)s.K + lw1;  // ln(X_{i-1} - X_i)
+        s.rx[nrep] = bv + lw;
+        s.rl[nrep] = bv;
+        if (nd <= s.cap) {
+          s.dl[nd - 1] = bv;
+          s.dw[nd - 1] = lw;
+        }
+        rslot[nrep] = bi;
+        rsrc[nrep] = src[bi];
+        src[bi] = (int)ptr;
+        ll[bi] = cl[ptr];
       }
-      for (int i = lane; i < D; i += 32) s.du[(nd - 1) * D + i] = s.lu[bi * D + i];
+      __syncwarp();
+      ++ptr;
+      ++nrep;
     }
-    __syncwarp();
-    for (int i = lane; i < D; i += 32) s.lu[bi * D + i] = s.cu[ptr * D + i];
-    if (lane == 0) s.ll[bi] = s.cl[ptr];
-    __syncwarp();
-    ++ptr;
-    ++consumed;
+    if (lane == 0) sh_nrep = nrep;
   }
-  if (lane == 0) {
-    s.stats[NS_NDEAD] = (double)nd;
-    s.stats[NS_CONSUMED] += (double)consumed;
+  __syncthreads();
+  const int nrep = sh_nrep;
+  // dead points' coordinates (before any live slot is overwritten)
+  for (int64_t x = t; x < (int64_t)nrep * D; x += blockDim.x) {
+    const int r = (int)(x / D), i = (int)(x % D);
+    const int64_t nd = nd0 + r + 1;
+    if (nd <= s.cap) {
+      const int sr = rsrc[r];
+      s.du[(nd - 1) * D + i] = sr < 0 ? s.lu[(int64_t)rslot[r] * D + i] : s.cu[(int64_t)sr * D + i];
+    }
   }
+  __syncthreads();
+  // live slots that now hold a candidate
+  for (int64_t x = t; x < s.K * D; x += blockDim.x) {
+    const int64_t k = x / D;
+    const int i = (int)(x % D);
+    const int sr = src[k];
+    if (sr >= 0) s.lu[x] = s.cu[(int64_t)sr * D + i];
+  }
+  for (int64_t k = t; k < s.K; k += blockDim.x) s.ll[k] = ll[k];
+  if (t == 0) {
+    s.stats[NS_NDEAD] = (double)(nd0 + nrep);
+    s.stats[NS_CONSUMED] += (double)nrep;
+  }
+}
+
+size_t consume_smem_bytes(int64_t K, int64_t n_chains) {
+  return sizeof(double) * (size_t)(K + n_chains) + sizeof(int) * (size_t)(K + 2 * n_chains);
 }
 
 // Fold n weighted points x_i = lnL_i + ln dX_i (with lnL_i) into the running
@@ -369,7 +444,7 @@ __device__ void fold_points(double* stats, const double* x, const double* l, int
 // End of round: ln Z update from the round's dead points, largest live lnL,
 // stopping rule ln(Z + Lmax X) - ln Z < dlogz, acceptance and scale
 // adaptation scale <- scale exp(acc - 1/2) clamped to [1e-3, 1].
-__global__ void __launch_bounds__(256) k_ns_stats(NsDev s, int walk_len, double dlogz) {
+__device__ void ns_stats_body(const NsDev& s, int walk_len, double dlogz) {
   if (s.stats[NS_DONE] > 0.5) return;
   __shared__ double red[512];
   const int t = threadIdx.x;
@@ -408,12 +483,92 @@ __global__ void __launch_bounds__(256) k_ns_stats(NsDev s, int walk_len, double 
 }
 
 // The final live points, each with prior volume X_N / (K + 1).
-__global__ void __launch_bounds__(256) k_ns_final(NsDev s) {
+__device__ void ns_final_body(const NsDev& s) {
   __shared__ double red[512];
   const double lw = -s.stats[NS_NDEAD] / (double)s.K - ::log((double)(s.K + 1));
   for (int64_t k = threadIdx.x; k < s.K; k += blockDim.x) s.rx[k] = s.ll[k] + lw;
   __syncthreads();
   fold_points(s.stats, s.rx, s.ll, s.K, red);
+}
+
+// One event (parameters by value) or E events (one CTA per event).
+__global__ void __launch_bounds__(256) k_ns_prep(NsDev s) { ns_prep_body(s); }
+__global__ void __launch_bounds__(256) k_ns_consume(NsDev s) { ns_consume_body(s); }
+__global__ void __launch_bounds__(256) k_ns_stats(NsDev s, int walk_len, double dlogz) { ns_stats_body(s, walk_len, dlogz); }
+__global__ void __launch_bounds__(256) k_ns_final(NsDev s) { ns_final_body(s); }
+__global__ void __launch_bounds__(256) k_mns_prep(const NsDev* a) { ns_prep_body(a[blockIdx.x]); }
+__global__ void __launch_bounds__(256) k_mns_consume(const NsDev* a) { ns_consume_body(a[blockIdx.x]); }
+__global__ void __launch_bounds__(256) k_mns_stats(const NsDev* a, int walk_len, double dlogz) {
+  ns_stats_body(a[blockIdx.x], walk_len, dlogz);
+}
+__global__ void __launch_bounds__(256) k_mns_final(const NsDev* a) { ns_final_body(a[blockIdx.x]); }
+
+// Walk kernels over E events x n chains: chain b belongs to event b / n; each
+// event has its own live set, walk scalars, step matrix, prior and Philox key
+// (seed + event * 0x9E3779B97F4A7C15).  Events whose run has stopped propose
+// nothing (NaN rows, which the likelihood flags without bin work).
+__host__ __device__ __forceinline__ uint64_t event_key(uint64_t seed, int e) {
+  return seed + (uint64_t)e * 0x9E3779B97F4A7C15ull;
+}
+
+__global__ void k_mwalk_init(const NsDev* __restrict__ a, int64_t n, int E, uint64_t seed) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * E) return;
+  const int e = (int)(g / n);
+  const int64_t b = g - (int64_t)e * n;
+  const NsDev& s = a[e];
+  const uint64_t key = event_key(seed, e);
+  const uint4 w = philox(make_uint4(0u, 0u, (uint32_t)b, (uint32_t)s.ws->counter), (uint32_t)key,
+                         (uint32_t)(key >> 32));
+  const int64_t idx = (int64_t)(((uint64_t)w.x * (uint64_t)(s.K - 1)) >> 32);
+  const int64_t st = idx < s.ws->worst ? idx : idx + 1;
+  for (int i = 0; i < s.D; ++i) s.cu[b * s.D + i] = s.lu[st * s.D + i];
+  s.cl[b] = s.ll[st];
+  s.cn[b] = 0;
+}
+
+__global__ void k_mwalk_propose(const NsDev* __restrict__ a, const PriorInfo* __restrict__ prs, int64_t n, int E,
+                                uint64_t seed, uint32_t step, double* __restrict__ pu, double* __restrict__ ptheta) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * E) return;
+  const int e = (int)(g / n);
+  const int64_t b = g - (int64_t)e * n;
+  const NsDev& s = a[e];
+  const PriorInfo& pr = prs[e];
+  const int D = pr.D;
+  if (s.stats[NS_DONE] > 0.5) {
+    for (int i = 0; i < D; ++i) ptheta[g * D + i] = NAN;
+    return;
+  }
+  double z[11];
+  walk_normals(event_key(seed, e), s.ws->counter, (uint32_t)b, step, D, z);
+  const double scale = s.ws->scale;
+  bool inside = true;
+  for (int i = 0; i < D; ++i) {
+    double dz = 0.0;
+    for (int k = 0; k <= i; ++k) dz += s.chol[i * D + k] * z[k];
+    double x = s.cu[b * D + i] + scale * dz;
+    if (pr.periodic[i]) x -= floor(x);
+    else if (x < 0.0 || x > 1.0) inside = false;
+    pu[g * D + i] = x;
+  }
+  for (int i = 0; i < D; ++i)
+    ptheta[g * D + i] = inside ? prior_map(pr.kind[i], pr.lo[i], pr.hi[i], pu[g * D + i]) : NAN;
+}
+
+__global__ void k_mwalk_accept(const NsDev* __restrict__ a, int64_t n, int E, const double* __restrict__ pu,
+                               const double* __restrict__ plnl) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n * E) return;
+  const int e = (int)(g / n);
+  const int64_t b = g - (int64_t)e * n;
+  const NsDev& s = a[e];
+  const double l = plnl[g];
+  if (l >= s.ws->lstar) {
+    for (int i = 0; i < s.D; ++i) s.cu[b * s.D + i] = pu[g * s.D + i];
+    s.cl[b] = l;
+    s.cn[b] += 1;
+  }
 }
 
 // Initial live points: uniform in the unit cube, Philox words (block, step
@@ -496,7 +651,14 @@ cudaError_t launch_ns_round(gwl_ctx* c, const NsDev& s, uint64_t seed, int walk_
   e = launch_walk(c, s.lu, s.ll, s.K, s.ws, seed, s.n_chains, walk_len, s.chol, s.cu, s.cl, s.cn, nullptr, pu, pth,
                   plnl, st);
   if (e != cudaSuccess) return e;
-  k_ns_consume<<<1, 32, 0, st>>>(s);
+  const size_t csm = consume_smem_bytes(s.K, s.n_chains);
+  static size_t csm_set = 0;
+  if (csm > 48 * 1024 && csm > csm_set) {
+    e = cudaFuncSetAttribute(k_ns_consume, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+    if (e != cudaSuccess) return e;
+    csm_set = csm;
+  }
+  k_ns_consume<<<1, 256, csm, st>>>(s);
   k_ns_stats<<<1, 256, 0, st>>>(s, walk_len, dlogz);
   c->launches += 2;
   return cudaGetLastError();
@@ -655,6 +817,195 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
   if (e != cudaSuccess) rc = -2;
   cudaStreamSynchronize(st);
   for (int i = 0; i < nblk; ++i) cudaFree(blocks[i]);
+  return rc;
+}
+
+}  // namespace gwl
+
+namespace gwl {
+int multi_events(const Multi* m);
+int multi_dim(const Multi* m);
+gwl_ctx* multi_ctx(const Multi* m, int e);
+void multi_count(Multi* m, int64_t n);
+
+// Nested sampling of E events at once: every round is one sequence of
+// launches covering all events (per-event kernels run one CTA per event; the
+// walk steps evaluate all events' chains in one multi-event batch).
+static int multi_ns_run_on(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                           int64_t max_rounds, double scale0, double* res, cudaStream_t st) {
+  const int E = multi_events(m);
+  const int D = multi_dim(m);
+  const int64_t rbuf = n_chains > K ? n_chains : K;
+  std::vector<void*> blocks;
+  auto alloc = [&](void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 8);
+    if (e == cudaSuccess) blocks.push_back(*p);
+    return e;
+  };
+  double *lu, *ll, *cu, *cl, *rx, *rl, *dl, *dw, *du, *chol, *stats, *pu, *pth, *plnl;
+  int32_t* cn;
+  WalkScalars* ws;
+  NsDev* d_ns;
+  PriorInfo* d_pr;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = alloc((void**)&lu, sizeof(double) * E * K * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&ll, sizeof(double) * E * K)) != cudaSuccess) break;
+    if ((e = alloc((void**)&cu, sizeof(double) * E * n_chains * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&cl, sizeof(double) * E * n_chains)) != cudaSuccess) break;
+    if ((e = alloc((void**)&cn, sizeof(int32_t) * E * n_chains)) != cudaSuccess) break;
+    if ((e = alloc((void**)&rx, sizeof(double) * E * rbuf)) != cudaSuccess) break;
+    if ((e = alloc((void**)&rl, sizeof(double) * E * rbuf)) != cudaSuccess) break;
+    if ((e = alloc((void**)&dl, sizeof(double) * E)) != cudaSuccess) break;
+    if ((e = alloc((void**)&dw, sizeof(double) * E)) != cudaSuccess) break;
+    if ((e = alloc((void**)&du, sizeof(double) * E * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&chol, sizeof(double) * E * D * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&stats, sizeof(double) * E * NS_NSTATS)) != cudaSuccess) break;
+    if ((e = alloc((void**)&ws, sizeof(WalkScalars) * E)) != cudaSuccess) break;
+    if ((e = alloc((void**)&d_ns, sizeof(NsDev) * E)) != cudaSuccess) break;
+    if ((e = alloc((void**)&d_pr, sizeof(PriorInfo) * E)) != cudaSuccess) break;
+    if ((e = alloc((void**)&pu, sizeof(double) * E * rbuf * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&pth, sizeof(double) * E * rbuf * D)) != cudaSuccess) break;
+    if ((e = alloc((void**)&plnl, sizeof(double) * E * rbuf)) != cudaSuccess) break;
+  } while (false);
+  int rc = 0;
+  if (e == cudaSuccess) do {
+    if ((e = multi_prepare(m, rbuf)) != cudaSuccess) break;
+    std::vector<NsDev> hns(E);
+    std::vector<PriorInfo> hpr(E);
+    std::vector<double> st0((size_t)E * NS_NSTATS, 0.0);
+    std::vector<WalkScalars> w0(E);
+    for (int i = 0; i < E; ++i) {
+      NsDev& s = hns[i];
+      s.lu = lu + (int64_t)i * K * D;
+      s.ll = ll + (int64_t)i * K;
+      s.K = K;
+      s.D = D;
+      s.cu = cu + (int64_t)i * n_chains * D;
+      s.cl = cl + (int64_t)i * n_chains;
+      s.cn = cn + (int64_t)i * n_chains;
+      s.n_chains = n_chains;
+      s.rx = rx + (int64_t)i * rbuf;
+      s.rl = rl + (int64_t)i * rbuf;
+      s.dl = dl + i;
+      s.dw = dw + i;
+      s.du = du + (int64_t)i * D;
+      s.cap = 0;  // no dead-point list kept for multi-event runs (lnZ and H are accumulated)
+      s.ws = ws + i;
+      s.chol = chol + (int64_t)i * D * D;
+      s.stats = stats + (int64_t)i * NS_NSTATS;
+      hpr[i] = prior_info(multi_ctx(m, i));
+      st0[(size_t)i * NS_NSTATS + NS_LNZ] = -INFINITY;
+      st0[(size_t)i * NS_NSTATS + NS_M] = -INFINITY;
+      st0[(size_t)i * NS_NSTATS + NS_LMAX] = -INFINITY;
+      w0[i].lstar = -INFINITY;
+      w0[i].scale = scale0;
+      w0[i].worst = 0;
+      w0[i].counter = 0;
+    }
+    if ((e = cudaMemcpyAsync(d_ns, hns.data(), sizeof(NsDev) * E, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(d_pr, hpr.data(), sizeof(PriorInfo) * E, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(stats, st0.data(), sizeof(double) * st0.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(ws, w0.data(), sizeof(WalkScalars) * E, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      break;
+    // initial live points of every event, one batched likelihood call
+    for (int i = 0; i < E && e == cudaSuccess; ++i) {
+      k_ns_init<<<(unsigned)((K + 127) / 128), 128, 0, st>>>(hpr[i], event_key(seed, i), K, hns[i].lu,
+                                                             pth + (int64_t)i * K * D);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) break;
+    if ((e = multi_loglike(m, pth, K, ll, st)) != cudaSuccess) break;
+    // one round, captured
+    const size_t csm = consume_smem_bytes(K, n_chains);
+    if (csm > 48 * 1024) {
+      if ((e = cudaFuncSetAttribute(k_mns_consume, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm)) !=
+          cudaSuccess)
+        break;
+    }
+    const int64_t NC = n_chains * E;
+    const unsigned nb = (unsigned)((NC + 127) / 128);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+    {
+      cudaError_t er = cudaSuccess;
+      k_mns_prep<<<E, 256, 0, st>>>(d_ns);
+      k_mwalk_init<<<nb, 128, 0, st>>>(d_ns, n_chains, E, seed);
+      for (int s2 = 1; s2 <= walk_len && er == cudaSuccess; ++s2) {
+        k_mwalk_propose<<<nb, 128, 0, st>>>(d_ns, d_pr, n_chains, E, seed, (uint32_t)s2, pu, pth);
+        er = multi_loglike(m, pth, n_chains, plnl, st);
+        k_mwalk_accept<<<nb, 128, 0, st>>>(d_ns, n_chains, E, pu, plnl);
+      }
+      k_mns_consume<<<E, 256, csm, st>>>(d_ns);
+      k_mns_stats<<<E, 256, 0, st>>>(d_ns, walk_len, dlogz);
+      cudaError_t ec = cudaStreamEndCapture(st, &graph);
+      e = er != cudaSuccess ? er : ec;
+    }
+    if (e != cudaSuccess) break;
+    if ((e = cudaGraphInstantiate(&gexec, graph, 0)) != cudaSuccess) break;
+    std::vector<double> hst((size_t)E * NS_NSTATS);
+    int64_t r = 0;
+    const int check = 4;
+    while (r < max_rounds && e == cudaSuccess) {
+      const int64_t todo = (max_rounds - r) < check ? (max_rounds - r) : check;
+      for (int64_t i = 0; i < todo && e == cudaSuccess; ++i) {
+        e = cudaGraphLaunch(gexec, st);
+        multi_count(m, 5 + 5 * (int64_t)walk_len);
+      }
+      if (e != cudaSuccess) break;
+      r += todo;
+      if ((e = cudaMemcpyAsync(hst.data(), stats, sizeof(double) * hst.size(), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess)
+        break;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+      bool all = true;
+      for (int i = 0; i < E; ++i) all = all && hst[(size_t)i * NS_NSTATS + NS_DONE] > 0.5;
+      if (all) break;
+    }
+    cudaGraphExecDestroy(gexec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) break;
+    k_mns_final<<<E, 256, 0, st>>>(d_ns);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(hst.data(), stats, sizeof(double) * hst.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      break;
+    std::vector<WalkScalars> wl(E);
+    if ((e = cudaMemcpyAsync(wl.data(), ws, sizeof(WalkScalars) * E, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+    for (int i = 0; i < E; ++i) {
+      const double* x = hst.data() + (size_t)i * NS_NSTATS;
+      double* o = res + 11 * i;
+      const double rounds = x[NS_ROUND];
+      o[0] = x[NS_LNZ];
+      o[1] = sqrt(fmax(x[NS_H], 0.0) / (double)K);
+      o[2] = x[NS_H];
+      o[3] = x[NS_NDEAD] + (double)K;
+      o[4] = (double)K + rounds * (double)n_chains * (double)walk_len;
+      o[5] = rounds;
+      o[6] = wl[i].scale;
+      o[7] = rounds > 0 ? x[NS_ACC_SUM] / rounds : 0.0;
+      o[8] = rounds > 0 ? x[NS_CONSUMED] / rounds : 0.0;
+      o[9] = x[NS_DLOGZ];
+      o[10] = 0.0;
+    }
+  } while (false);
+  if (e != cudaSuccess) rc = -2;
+  cudaStreamSynchronize(st);
+  for (void* b : blocks) cudaFree(b);
+  return rc;
+}
+
+int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                 int64_t max_rounds, double scale0, double* res, cudaStream_t caller) {
+  if (cudaStreamSynchronize(caller) != cudaSuccess) return -2;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -2;
+  const int rc = multi_ns_run_on(m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
   return rc;
 }
 

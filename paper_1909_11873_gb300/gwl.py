@@ -25,7 +25,8 @@ MAX_DET = 4
 # exported symbols declared in include/gwl.h
 EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "ns_run", "gwl_grad", "gwl_waveform", "ns_replace",
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
-           "gwl_launch_count", "gwl_destroy", "gwl_last_error")
+           "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
+           "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy")
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
 
 
@@ -89,6 +90,13 @@ def lib() -> C.CDLL:
         L.gwl_destroy.argtypes = [P]
         L.gwl_destroy.restype = None
         L.gwl_last_error.restype = C.c_char_p
+        L.gwl_multi_create.argtypes = [P, i32, C.POINTER(P)]
+        L.gwl_multi_loglike.argtypes = [P, P, i64, P, P]
+        L.gwl_multi_ns_run.argtypes = [P, i64, i64, i32, u64, d, i64, d, P, P]
+        L.gwl_multi_launch_count.argtypes = [P]
+        L.gwl_multi_launch_count.restype = i64
+        L.gwl_multi_destroy.argtypes = [P]
+        L.gwl_multi_destroy.restype = None
         _lib = L
     return _lib
 
@@ -308,3 +316,42 @@ def GWLogLike():
 
         _GWLogLike = _F
     return _GWLogLike
+
+
+class MultiContext:
+    """Several events evaluated in one batch (wraps a ``gwl_multi*``); keeps its contexts alive."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.handle for c in self.contexts])
+        h = C.c_void_p()
+        _check(lib().gwl_multi_create(arr, len(self.contexts), C.byref(h)), "gwl_multi_create")
+        self._h = h
+        self.E = len(self.contexts)
+        self.n_dim = self.contexts[0].n_dim
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gwl_multi_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def gwl_multi_loglike(self, theta, lnl, stream=None):
+        """theta [E * n_per, n_dim] (event-major), lnl [E * n_per]."""
+        n_per = theta.shape[0] // self.E
+        _check(lib().gwl_multi_loglike(self._h, _ptr(theta), n_per, _ptr(lnl), _stream(stream)), "gwl_multi_loglike")
+
+    def gwl_multi_ns_run(self, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0, stream=None):
+        res = (GwlNsResult * self.E)()
+        _check(lib().gwl_multi_ns_run(self._h, int(K), int(n_chains), int(walk_len), int(seed), float(dlogz),
+                                      int(max_rounds), float(scale0), C.cast(res, C.c_void_p), _stream(stream)),
+               "gwl_multi_ns_run")
+        return [{k: getattr(r, k) for k, _ in GwlNsResult._fields_} for r in res]
+
+    def launch_count(self) -> int:
+        return lib().gwl_multi_launch_count(self._h)

@@ -1,0 +1,78 @@
+"""Many events of uneven durations in one batched evaluation (gwl_multi_*)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import custom_event, tol
+from paper_1909_11873_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1909_11873_gb300 import build
+    build.build()
+
+
+def small_events():
+    cfgs = [(4.0, "bbh"), (8.0, "bns"), (4.0, "bns"), (8.0, "bbh"), (16.0, "bbh")]
+    evs = []
+    for i, (T, src) in enumerate(cfgs):
+        cfg = dict(n_det=3, T=T, f_low=20.0, f_high=1024.0, noise=True, source=src, batch=64, gmst=1.7)
+        evs.append(custom_event(cfg, 100 + i))
+    return evs
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_loglike_equals_single_and_oracle(precision):
+    from paper_1909_11873_gb300 import gwl
+    evs = small_events()
+    n = 96
+    ths = [I.proposals(ev, n, 7 + i) for i, ev in enumerate(evs)]
+    ctxs = [gwl.Context.from_event(ev, precision) for ev in evs]
+    mc = gwl.MultiContext(ctxs)
+    x = torch.from_numpy(np.concatenate([I.reduced(t, ev.sampling) for t, ev in zip(ths, evs)])).cuda()
+    out = torch.empty(x.shape[0], dtype=torch.float64, device="cuda")
+    mc.gwl_multi_loglike(x, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(len(evs), n)
+    for e, (ev, th, ctx) in enumerate(zip(evs, ths, ctxs)):
+        single = gwl.loglike(ctx, torch.from_numpy(I.reduced(th, ev.sampling)).cuda()).cpu().numpy()
+        # same formulas and bin arithmetic; FMA contraction may differ between the two prologue kernels
+        assert np.all(np.abs(got[e] - single) <= 0.1 * tol(precision, single)), e
+        idx = np.arange(0, n, 8)
+        ref = oracle.loglike(ev, th[idx])
+        assert np.all(np.abs(got[e, idx] - ref) <= tol(precision, ref)), e
+
+
+def four_d(ev):
+    """The event with (Mc, q, tc, phic) sampled and the other parameters at the injection.
+    In 11-D the posterior is multimodal and single-ellipsoid random-walk NS with a few hundred live
+    points misses the main mode in a fraction of runs on both sides alike, so lnZ parity is tested
+    where the comparison is well-posed."""
+    th = ev.theta_inj
+    bns = th[0] < 5
+    smp = I.Sampling(np.array([0, 1, 9, 10], dtype=np.int32), th.copy(), np.zeros(4, dtype=np.int32),
+                     np.array([th[0] * (0.995 if bns else 0.97), 0.7 if bns else 0.25, -0.02, 0.0]),
+                     np.array([th[0] * (1.005 if bns else 1.03), 1.0, 0.02, 2 * math.pi]),
+                     np.array([0, 0, 0, 1], dtype=np.int32))
+    import dataclasses
+    return dataclasses.replace(ev, sampling=smp)
+
+
+def test_multi_ns_lnz_matches_oracle_per_event():
+    from paper_1909_11873_gb300 import gwl
+    evs = [four_d(ev) for ev in small_events()[:3]]
+    K, nch, wl = 150, 150, 16
+    mc = gwl.MultiContext([gwl.Context.from_event(ev, 1) for ev in evs])
+    res = mc.gwl_multi_ns_run(K, nch, wl, seed=3, dlogz=0.1)
+    for ev, r in zip(evs, res):
+        o = oracle.ns_run(ev, ev.sampling, K, nch, wl, seed=4, dlogz=0.1)
+        sig = math.hypot(r["lnZ_err"], o["lnZ_err"])
+        assert np.isfinite(r["lnZ"]) and r["rounds"] > 3
+        assert abs(r["lnZ"] - o["lnZ"]) < 4 * sig + 0.2, (r, o)
+        assert r["consumed_per_round"] == pytest.approx(K * math.log(1 + nch / K), rel=0.12)
