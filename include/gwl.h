@@ -190,8 +190,8 @@ typedef struct {
  * scale <- scale exp(acceptance - 1/2), clamped to [1e-3, 1].  The run stops
  * when ln(Z + Lmax X) - ln Z < dlogz or after max_rounds rounds.
  *   dead_lnl, dead_logwt host [max_dead], dead_u host [max_dead][n_dim]
- *   (may be NULL; the first min(n_dead - K, max_dead) dead points, in death
- *   order, without the final live set).
+ *   (may be NULL; the first min(n_dead, max_dead) dead points in death order,
+ *   the final live points last with their equal weights).
  * Synchronises the stream before returning. */
 int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
            int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
@@ -250,6 +250,19 @@ void gwl_multi_destroy(gwl_multi* m);
  *     GPU -- from different streams, threads or contexts -- race on the array
  *     and must be serialised by the caller. */
 int gwl_loglike_static(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, void* stream);
+
+/* Walk used by ns_replace and ns_run. */
+#define GWL_WALK_RANDOM 0   /* Gaussian random walk (default) */
+#define GWL_WALK_GALILEAN 1 /* gradient-informed Galilean walk: chains keep a velocity
+                               v (initially scale * chol z, normals from step word
+                               0x40000000); a step tries x1 = u + v and moves if x1 is in
+                               the cube with lnL >= L*; a step leaving the cube reverses
+                               the offending velocity components; otherwise v is
+                               reflected off the contour, v' = v - 2 (v.n) n with n the
+                               unit gradient of lnL at x1 in the unit cube, and
+                               x2 = x1 + v' is tried (move keeping v', or stay with
+                               v <- -v).  out_nacc counts moves. */
+int gwl_set_walk(gwl_ctx* ctx, int walk_kind);
 
 /* Synchronise the context's last stream and return the latched device
  * status (GWL_OK or GWL_ERR_TIMEOUT); clears the latch. */

@@ -334,6 +334,12 @@ int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t
   gwl::set_walk_scalars(hs, lnl_star, scale, worst, counter);
   cudaError_t e = cudaMemcpyAsync(c->d_wscal, hs, gwl::walk_scalars_bytes(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "ns_replace");
+  if (c->walk_kind == GWL_WALK_GALILEAN) {
+    if ((rc = ensure_bytes(c, (void**)&c->d_gmc, &c->gmc_cap, (int64_t)sizeof(double) * gwl::gmc_scratch_doubles(n_chains, D))))
+      return rc;
+    if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * n_chains))) return rc;
+    if ((rc = ensure_bytes(c, &c->d_gpartials, &c->gpartials_cap, gwl::grad_partials_bytes(c, n_chains)))) return rc;
+  }
   double* pu = c->d_walk;
   double* pth = pu + n_chains * D;
   double* plnl = pth + n_chains * D;
@@ -356,6 +362,13 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
   if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "ns_run supports K <= 4096 and n_chains <= 4096");
   const int64_t nb = n_chains > K ? n_chains : K;
   if ((rc = ensure_scratch(c, nb))) return rc;
+  if (c->walk_kind == GWL_WALK_GALILEAN) {
+    const int D = c->opt.n_dim;
+    if ((rc = ensure_bytes(c, (void**)&c->d_gmc, &c->gmc_cap, (int64_t)sizeof(double) * gwl::gmc_scratch_doubles(n_chains, D))))
+      return rc;
+    if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * nb))) return rc;
+    if ((rc = ensure_bytes(c, &c->d_gpartials, &c->gpartials_cap, gwl::grad_partials_bytes(c, nb)))) return rc;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   double res[11];
@@ -467,6 +480,13 @@ int gwl_sync(gwl_ctx* c) {
   return GWL_OK;
 }
 
+int gwl_set_walk(gwl_ctx* c, int walk_kind) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  if (walk_kind != GWL_WALK_RANDOM && walk_kind != GWL_WALK_GALILEAN) return fail(GWL_ERR_ARG, "bad walk kind");
+  c->walk_kind = walk_kind;
+  return GWL_OK;
+}
+
 int gwl_set_tuning(gwl_ctx* c, int window, int slice, int ctas_per_sm) {
   if (!c) return fail(GWL_ERR_ARG, "null context");
   if (window < 0 || slice < 0 || ctas_per_sm < 0) return fail(GWL_ERR_ARG, "negative tuning value");
@@ -537,6 +557,7 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_status, 4);
   if (c->d_pgrad) cudaFree(c->d_pgrad);
   if (c->d_walk) cudaFree(c->d_walk);
+  if (c->d_gmc) cudaFree(c->d_gmc);
   if (c->d_wscal) cudaFree(c->d_wscal);
   if (c->d_gpartials) cudaFree(c->d_gpartials);
   delete c;

@@ -36,6 +36,9 @@ struct gwl_ctx {
   double* d_walk = nullptr;      // ns_replace proposals: u' [n][D], theta' [n][D], lnL' [n]
   int64_t walk_cap = 0;          // in doubles
   void* d_wscal = nullptr;       // walk scalars (L*, scale, worst, counter)
+  double* d_gmc = nullptr;       // Galilean walk scratch (velocity, reflected points, gradient)
+  int64_t gmc_cap = 0;           // in doubles
+  int walk_kind = GWL_WALK_RANDOM;
   double* d_io = nullptr;        // staging for the host-buffer entry points
   int64_t io_cap = 0;            // in doubles
   void* d_pgrad = nullptr;       // per-proposal tangents of the gradient prologue
@@ -94,6 +97,7 @@ cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl
                         double* out_lnl, int32_t* out_nacc, int32_t* out_start, double* pu, double* pth,
                         double* plnl, cudaStream_t st);
 size_t walk_scalars_bytes();
+size_t gmc_scratch_doubles(int64_t n_chains, int D);
 void set_walk_scalars(void* host_buf, double lstar, double scale, int64_t worst, uint64_t counter);
 int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                 int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,

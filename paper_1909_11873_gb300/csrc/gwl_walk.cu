@@ -141,6 +141,135 @@ __global__ void k_walk_accept(const WalkScalars* __restrict__ sc, int D, int64_t
   }
 }
 
+// ---------------------------------------------------------------- Galilean walk
+// Gradient-informed constrained walk (Galilean Monte Carlo, Skilling 2012):
+// each chain carries a velocity v (initially scale * L z).  A step tries
+// x1 = u + v; if x1 is inside the cube and lnL(x1) >= L* the chain moves.
+// Otherwise, if x1 left the cube, the offending velocity components are
+// reversed and the chain stays; if x1 violated the likelihood constraint, v is
+// reflected off the contour, v' = v - 2 (v.n) n with n the unit gradient of
+// lnL at x1 in the unit cube, and x2 = x1 + v' is tried: the chain moves to x2
+// (keeping v') if it satisfies the constraint, else it stays and v <- -v.
+// Normals for the initial velocity come from step word 0x40000000.
+__device__ __forceinline__ double prior_jac(int kind, double lo, double hi, double th) {
+  switch (kind) {
+    case GWL_PRIOR_VOLUME: return (hi * hi * hi - lo * lo * lo) / (3.0 * th * th);
+    case GWL_PRIOR_SINE: return 2.0 / fmax(sin(th), 1e-300);
+    case GWL_PRIOR_COSINE: return 2.0 / fmax(cos(th), 1e-300);
+    default: return hi - lo;
+  }
+}
+
+__global__ void k_gmc_init(PriorInfo pr, const double* __restrict__ live_u, const double* __restrict__ live_lnl,
+                           int64_t K, const WalkScalars* __restrict__ sc, const double* __restrict__ chol,
+                           uint64_t seed, int64_t n_chains, double* __restrict__ cu, double* __restrict__ cl,
+                           int32_t* __restrict__ cn, int32_t* __restrict__ cstart, double* __restrict__ vel) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains) return;
+  const int D = pr.D;
+  const uint4 w = philox(make_uint4(0u, 0u, (uint32_t)b, (uint32_t)sc->counter), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+  const int64_t idx = (int64_t)(((uint64_t)w.x * (uint64_t)(K - 1)) >> 32);
+  const int64_t st = idx < sc->worst ? idx : idx + 1;
+  for (int i = 0; i < D; ++i) cu[b * D + i] = live_u[st * D + i];
+  cl[b] = live_lnl[st];
+  cn[b] = 0;
+  if (cstart) cstart[b] = (int32_t)st;
+  double z[11];
+  walk_normals(seed, sc->counter, (uint32_t)b, 0x40000000u, D, z);
+  for (int i = 0; i < D; ++i) {
+    double dz = 0.0;
+    for (int k = 0; k <= i; ++k) dz += chol[i * D + k] * z[k];
+    vel[b * D + i] = sc->scale * dz;
+  }
+}
+
+// x1 = u + v; theta1 (NaN rows outside the cube)
+__global__ void k_gmc_step1(PriorInfo pr, int64_t n_chains, const double* __restrict__ cu,
+                            const double* __restrict__ vel, double* __restrict__ x1, double* __restrict__ th1) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains) return;
+  const int D = pr.D;
+  bool inside = true;
+  for (int i = 0; i < D; ++i) {
+    double x = cu[b * D + i] + vel[b * D + i];
+    if (pr.periodic[i]) x -= floor(x);
+    else if (x < 0.0 || x > 1.0) inside = false;
+    x1[b * D + i] = x;
+  }
+  for (int i = 0; i < D; ++i) th1[b * D + i] = inside ? prior_map(pr.kind[i], pr.lo[i], pr.hi[i], x1[b * D + i]) : NAN;
+}
+
+// accept x1, or reflect: writes theta2 for the chains that reflect off the contour (NaN otherwise)
+__global__ void k_gmc_reflect(PriorInfo pr, const WalkScalars* __restrict__ sc, int64_t n_chains,
+                              const double* __restrict__ x1, const double* __restrict__ th1,
+                              const double* __restrict__ l1, const double* __restrict__ g1, double* __restrict__ cu,
+                              double* __restrict__ cl, int32_t* __restrict__ cn, double* __restrict__ vel,
+                              double* __restrict__ x2, double* __restrict__ th2, int32_t* __restrict__ mode) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains) return;
+  const int D = pr.D;
+  bool inside = true;
+  for (int i = 0; i < D; ++i) inside = inside && !isnan(th1[b * D + i]);
+  for (int i = 0; i < D; ++i) th2[b * D + i] = NAN;
+  mode[b] = 0;
+  if (inside && l1[b] >= sc->lstar) {  // move
+    for (int i = 0; i < D; ++i) cu[b * D + i] = x1[b * D + i];
+    cl[b] = l1[b];
+    cn[b] += 1;
+    return;
+  }
+  if (!inside) {  // bounce off the cube walls
+    for (int i = 0; i < D; ++i) {
+      const double x = cu[b * D + i] + vel[b * D + i];
+      if (!pr.periodic[i] && (x < 0.0 || x > 1.0)) vel[b * D + i] = -vel[b * D + i];
+    }
+    return;
+  }
+  // reflect off the likelihood contour at x1
+  double n[11], nn = 0.0;
+  for (int i = 0; i < D; ++i) {
+    n[i] = g1[b * D + i] * prior_jac(pr.kind[i], pr.lo[i], pr.hi[i], th1[b * D + i]);
+    nn += n[i] * n[i];
+  }
+  if (!(nn > 0.0) || !isfinite(nn)) {
+    for (int i = 0; i < D; ++i) vel[b * D + i] = -vel[b * D + i];
+    return;
+  }
+  double vn = 0.0;
+  for (int i = 0; i < D; ++i) vn += vel[b * D + i] * n[i];
+  bool in2 = true;
+  for (int i = 0; i < D; ++i) {
+    const double v2 = vel[b * D + i] - 2.0 * vn * n[i] / nn;
+    double x = x1[b * D + i] + v2;
+    if (pr.periodic[i]) x -= floor(x);
+    else if (x < 0.0 || x > 1.0) in2 = false;
+    x2[b * D + i] = x;
+    vel[b * D + i] = v2;  // tentatively reflected; undone below if x2 fails
+  }
+  if (!in2) {
+    for (int i = 0; i < D; ++i) vel[b * D + i] = -vel[b * D + i];
+    mode[b] = 2;  // the reflected velocity reversed; nothing to evaluate
+    return;
+  }
+  for (int i = 0; i < D; ++i) th2[b * D + i] = prior_map(pr.kind[i], pr.lo[i], pr.hi[i], x2[b * D + i]);
+  mode[b] = 1;
+}
+
+__global__ void k_gmc_step2(int D, const WalkScalars* __restrict__ sc, int64_t n_chains, const double* __restrict__ x2,
+                            const double* __restrict__ l2, const int32_t* __restrict__ mode, double* __restrict__ cu,
+                            double* __restrict__ cl, int32_t* __restrict__ cn, double* __restrict__ vel) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_chains || mode[b] != 1) return;
+  if (l2[b] >= sc->lstar) {
+    for (int i = 0; i < D; ++i) cu[b * D + i] = x2[b * D + i];
+    cl[b] = l2[b];
+    cn[b] += 1;
+  } else {
+    for (int i = 0; i < D; ++i) vel[b * D + i] = -vel[b * D + i];
+  }
+}
+
 // ---------------------------------------------------------------- nested-sampling state kernels
 struct NsDev {
   // live set
@@ -486,7 +615,15 @@ __device__ void ns_stats_body(const NsDev& s, int walk_len, double dlogz) {
 __device__ void ns_final_body(const NsDev& s) {
   __shared__ double red[512];
   const double lw = -s.stats[NS_NDEAD] / (double)s.K - ::log((double)(s.K + 1));
-  for (int64_t k = threadIdx.x; k < s.K; k += blockDim.x) s.rx[k] = s.ll[k] + lw;
+  const int64_t nd = (int64_t)s.stats[NS_NDEAD];
+  for (int64_t k = threadIdx.x; k < s.K; k += blockDim.x) {
+    s.rx[k] = s.ll[k] + lw;
+    if (nd + k < s.cap) {  // the final live points close the dead list
+      s.dl[nd + k] = s.ll[k];
+      s.dw[nd + k] = lw;
+      for (int i = 0; i < s.D; ++i) s.du[(nd + k) * s.D + i] = s.lu[k * s.D + i];
+    }
+  }
   __syncthreads();
   fold_points(s.stats, s.rx, s.ll, s.K, red);
 }
@@ -604,11 +741,54 @@ static PriorInfo prior_info(const gwl_ctx* c) {
 }
 
 // The walk proper: chains start from live points and take walk_len steps.
+static cudaError_t launch_gmc(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K,
+                              const WalkScalars* sc, uint64_t seed, int64_t n_chains, int walk_len, const double* chol,
+                              double* out_u, double* out_lnl, int32_t* out_nacc, int32_t* out_start, double* pu,
+                              double* pth, double* plnl, cudaStream_t st) {
+  const int D = c->opt.n_dim;
+  const unsigned nb = (unsigned)((n_chains + 127) / 128);
+  const PriorInfo pr = prior_info(c);
+  // scratch after the random-walk proposal buffers: velocity, x2, theta2, gradient, l2, mode
+  double* vel = c->d_gmc;
+  double* x2 = vel + n_chains * D;
+  double* th2 = x2 + n_chains * D;
+  double* g1 = th2 + n_chains * D;
+  double* l2 = g1 + n_chains * D;
+  int32_t* mode = reinterpret_cast<int32_t*>(l2 + n_chains);
+  {
+    ProfScope ps(c, GWL_KERNEL_WALK, st);
+    k_gmc_init<<<nb, 128, 0, st>>>(pr, live_u, live_lnl, K, sc, chol, seed, n_chains, out_u, out_lnl, out_nacc,
+                                   out_start, vel);
+    c->launches++;
+  }
+  cudaError_t e = cudaGetLastError();
+  for (int s = 1; s <= walk_len && e == cudaSuccess; ++s) {
+    k_gmc_step1<<<nb, 128, 0, st>>>(pr, n_chains, out_u, vel, pu, pth);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = launch_grad(c, pth, n_chains, plnl, g1, st)) != cudaSuccess) break;
+    k_gmc_reflect<<<nb, 128, 0, st>>>(pr, sc, n_chains, pu, pth, plnl, g1, out_u, out_lnl, out_nacc, vel, x2, th2,
+                                      mode);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = launch_loglike(c, th2, n_chains, l2, st)) != cudaSuccess) break;
+    k_gmc_step2<<<nb, 128, 0, st>>>(D, sc, n_chains, x2, l2, mode, out_u, out_lnl, out_nacc, vel);
+    c->launches++;
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+size_t gmc_scratch_doubles(int64_t n_chains, int D) { return (size_t)n_chains * (4 * D + 2); }
+
 cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, const void* scalars,
                         uint64_t seed, int64_t n_chains, int walk_len, const double* chol, double* out_u,
                         double* out_lnl, int32_t* out_nacc, int32_t* out_start, double* pu, double* pth,
                         double* plnl, cudaStream_t st) {
   const WalkScalars* sc = static_cast<const WalkScalars*>(scalars);
+  if (c->walk_kind == GWL_WALK_GALILEAN)
+    return launch_gmc(c, live_u, live_lnl, K, sc, seed, n_chains, walk_len, chol, out_u, out_lnl, out_nacc,
+                      out_start, pu, pth, plnl, st);
   const int D = c->opt.n_dim;
   const unsigned nb = (unsigned)((n_chains + 127) / 128);
   const PriorInfo pr = prior_info(c);
@@ -753,6 +933,10 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
     if ((e = cudaMemcpyAsync(s.ws, &w0, sizeof(w0), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
     if ((e = launch_ns_init(c, seed, K, s.lu, pth, st)) != cudaSuccess) break;
     if ((e = launch_loglike(c, pth, K, s.ll, st)) != cudaSuccess) break;
+    if (c->walk_kind == GWL_WALK_GALILEAN) {  // warm the gradient path (kernel attributes) before capture
+      const int64_t nw = K < n_chains ? K : n_chains;
+      if ((e = launch_grad(c, pth, nw, plnl, c->d_gmc, st)) != cudaSuccess) break;
+    }
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     const bool prof = c->profiling;
@@ -791,7 +975,7 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(stats, s.stats, sizeof(stats), cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
-    const int64_t nd = (int64_t)stats[NS_NDEAD];
+    const int64_t nd = (int64_t)stats[NS_NDEAD] + K;  // dead points and the final live set
     const int64_t nk = nd < cap ? nd : cap;
     if (dead_lnl && max_dead > 0)
       if ((e = cudaMemcpy(dead_lnl, s.dl, sizeof(double) * nk, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
@@ -803,7 +987,7 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
     res[0] = stats[NS_LNZ];
     res[1] = sqrt(fmax(stats[NS_H], 0.0) / (double)K);
     res[2] = stats[NS_H];
-    res[3] = (double)nd + (double)K;
+    res[3] = (double)nd;
     res[4] = (double)K + rounds * (double)n_chains * (double)walk_len;
     res[5] = rounds;
     WalkScalars wl;

@@ -26,7 +26,9 @@ MAX_DET = 4
 EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "ns_run", "gwl_grad", "gwl_waveform", "ns_replace",
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
-           "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy")
+           "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk")
+GWL_WALK_RANDOM = 0
+GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
 
 
@@ -81,6 +83,7 @@ def lib() -> C.CDLL:
         L.ns_run.argtypes = [P, i64, i64, i32, u64, d, i64, d, i64, P, P, P, C.POINTER(GwlNsResult), P]
         L.gwl_sync.argtypes = [P]
         L.gwl_set_tuning.argtypes = [P, i32, i32, i32]
+        L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
         L.gwl_profile_read.argtypes = [P, i32, C.POINTER(d), C.POINTER(i64)]
         L.gwl_device_bytes.argtypes = [P]
@@ -239,6 +242,9 @@ class Context:
 
     def gwl_sync(self):
         _check(lib().gwl_sync(self._h), "gwl_sync")
+
+    def gwl_set_walk(self, kind: int):
+        _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
 
     def gwl_set_tuning(self, window=0, slice=0, ctas_per_sm=0):
         _check(lib().gwl_set_tuning(self._h, int(window), int(slice), int(ctas_per_sm)), "gwl_set_tuning")

@@ -104,3 +104,45 @@ def test_ns_run_posterior_recovers_injection():
     w = np.exp(g["dead_lnl"] + g["dead_logwt"] - g["lnZ"])
     th = oracle.prior_transform(ev.sampling, g["dead_u"])
     assert abs(np.sum(w * th[:, 0]) / np.sum(w) - 10.0) < 0.05
+
+
+def test_galilean_walk_properties():
+    """Galilean walk: each chain ends at its start or at a point whose oracle lnL >= L* (mixed bar),
+    at most one move per step, and it moves at a useful rate."""
+    from paper_1909_11873_gb300 import gwl
+    ev = event("c2")
+    K = 128
+    u, ll = live_set(ev, K, 6)
+    worst = int(np.argmin(ll))
+    D = ev.sampling.D
+    ctx = gwl.Context.from_event(ev, 1)
+    ctx.gwl_set_walk(gwl.GWL_WALK_GALILEAN)
+    n, wl = 256, 10
+    tu, tl = torch.from_numpy(u).cuda(), torch.from_numpy(ll).cuda()
+    tc = torch.from_numpy(np.diag(np.full(D, 0.03))).cuda()
+    ou = torch.zeros((n, D), dtype=torch.float64, device="cuda")
+    ol = torch.zeros(n, dtype=torch.float64, device="cuda")
+    on = torch.zeros(n, dtype=torch.int32, device="cuda")
+    os_ = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ctx.ns_replace(tu, tl, worst, ll[worst], 5, 2, n, wl, 1.0, tc, ou, ol, on, os_)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    gu, gl, gn, gs = ou.cpu().numpy(), ol.cpu().numpy(), on.cpu().numpy(), os_.cpu().numpy()
+    moved = gn > 0
+    assert np.all((gn >= 0) & (gn <= wl)) and moved.mean() > 0.3
+    assert np.allclose(gu[~moved], u[gs[~moved]])
+    ref = oracle.loglike(ev, oracle.prior_transform(ev.sampling, gu[moved]))
+    assert np.all(np.abs(ref - gl[moved]) <= 1e-3)
+    assert np.all(ref >= ll[worst] - 1e-3)
+
+
+def test_ns_run_galilean_c1_lnz_matches_oracle():
+    from paper_1909_11873_gb300 import gwl
+    ev = event("c1")
+    K, nch, wl = 250, 250, 20
+    ctx = gwl.Context.from_event(ev, 1)
+    ctx.gwl_set_walk(gwl.GWL_WALK_GALILEAN)
+    g = ctx.ns_run(K, nch, wl, seed=21, dlogz=0.1)
+    o = oracle.ns_run(ev, ev.sampling, K, nch, wl, seed=12, dlogz=0.1)
+    sig = math.hypot(g["lnZ_err"], o["lnZ_err"])
+    assert abs(g["lnZ"] - o["lnZ"]) < 4 * sig, (g, o)
