@@ -241,7 +241,7 @@ void gwl_multi_destroy(gwl_multi* m);
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
  *   - A batch needs about (272 + 16 n_det ceil(n_bins / window)) bytes per
- *     proposal, window being the context's bin window (gwl_set_tuning); a
+ *     proposal, window being the context's bin window (gwl_tuning.window); a
  *     batch that does not fit returns GWL_ERR_ARG with the sizes in the error
  *     text and launches nothing.
  *   - All calls on a device share the array and it keeps the previous call's
@@ -268,10 +268,49 @@ int gwl_set_walk(gwl_ctx* ctx, int walk_kind);
  * status (GWL_OK or GWL_ERR_TIMEOUT); clears the latch. */
 int gwl_sync(gwl_ctx* ctx);
 
-/* Tuning knobs (0 keeps the current value): window = bins staged in shared
- * memory per work item; slice = proposals per work item; ctas_per_sm = grid
- * size multiplier over the SM count. */
-int gwl_set_tuning(gwl_ctx* ctx, int window, int slice, int ctas_per_sm);
+/* Launch shape of the bin loops (the tile the hardware sees: a window of
+ * `window` frequency bins staged in shared memory, drained by warps of 32
+ * lanes, one proposal per warp; the grid is sized in CTAs per SM).  The
+ * result of gwl_loglike/gwl_grad depends on the shape only through the FP32
+ * (mixed) or FP64 summation order, within the parity tolerances. */
+typedef struct gwl_tuning {
+  int window;        /* likelihood bin loop: bins per window; 0 keeps (set) */
+  int ctas_per_sm;   /* likelihood bin loop: grid = ctas_per_sm x SMs; 0 keeps */
+  int fused;         /* 1: per-proposal coefficients and window 0 in one
+                        producer/consumer kernel; 0: separate kernels; -1 keeps */
+  int grad_window;   /* gradient bin loop: bins per window; 0 keeps */
+  double ms_loglike; /* gwl_autotune output: best time of one gwl_loglike call
+                        (ms) at the tuned batch; gwl_get_tuning: last tuned value or 0 */
+  double ms_grad;    /* same for gwl_grad */
+  int n_tried;       /* gwl_autotune output: launch shapes timed */
+} gwl_tuning;
+
+/* Set the launch shape (fields as above; the ms/n_tried fields are ignored).
+ * Windows are multiples of 32 bins.  A window that is not, or whose rows
+ * exceed 200 KB of shared memory, a negative value or a ctas_per_sm above 16
+ * returns GWL_ERR_ARG and changes nothing. */
+int gwl_set_tuning(gwl_ctx* ctx, const gwl_tuning* t);
+
+/* Read the context's current launch shape into *out. */
+int gwl_get_tuning(const gwl_ctx* ctx, gwl_tuning* out);
+
+#define GWL_TUNE_LOGLIKE 1
+#define GWL_TUNE_GRAD 2
+
+/* Autotuner: times gwl_loglike (what & GWL_TUNE_LOGLIKE) over every window in
+ * {128, 192, ..., 1536} bins that fits in shared memory (at most the segment),
+ * every ctas_per_sm in {1, 2, 3, 4} and fused in {0, 1}, and gwl_grad
+ * (what & GWL_TUNE_GRAD) over the same windows, on the caller's batch
+ * theta_dev (B x n_dim, device, row-major, read only) on `stream`, and keeps
+ * the fastest shape of each in the context.  Each shape is timed with CUDA
+ * events as the best of two runs of three back-to-back calls after one
+ * warm-up call.  Outputs go to a device buffer the call allocates and frees;
+ * scratch grows to the largest need of the shapes tried and is kept.  The
+ * results are not used; windows whose per-window partial sums would exceed
+ * 2 GB at this batch are skipped.  The call synchronises
+ * the stream.  *out (may be NULL) receives the chosen shape and its times.  On
+ * any error the previous shape is restored. */
+int gwl_autotune(gwl_ctx* ctx, const double* theta_dev, int64_t B, int what, gwl_tuning* out, void* stream);
 
 /* Kernel classes for gwl_profile_read. */
 #define GWL_KERNEL_PROLOGUE 0 /* per-proposal coefficients */

@@ -12,7 +12,7 @@
 
 namespace gwl {
 int64_t partials_needed(const gwl_ctx* c, int64_t B);
-int64_t work_needed(const gwl_ctx* c);
+int64_t work_needed(const gwl_ctx* c, int64_t B);
 }  // namespace gwl
 
 namespace {
@@ -53,6 +53,7 @@ void dev_free(gwl_ctx* c, T*& p, int64_t n) {
 // Grow the per-proposal and partial-sum scratch to hold a batch of B.
 int ensure_scratch(gwl_ctx* c, int64_t B) {
   cudaError_t e;
+
   if (B > c->prop_cap) {
     int64_t cap = B > 2 * c->prop_cap ? B : 2 * c->prop_cap;
     dev_free(c, c->d_pm, c->prop_cap);
@@ -64,7 +65,7 @@ int ensure_scratch(gwl_ctx* c, int64_t B) {
     if ((e = dev_alloc(c, &c->d_pc, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
     c->prop_cap = cap;
   }
-  const int64_t wneed = gwl::work_needed(c);
+  const int64_t wneed = gwl::work_needed(c, B);
   if (wneed > c->work_cap) {
     dev_free(c, c->d_work, c->work_cap);
     c->work_cap = 0;
@@ -182,6 +183,7 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     c->opt = *opt;
     c->row_floats = gwl::mixed_row_floats(n_det);
     c->row_doubles = gwl::f64_row_doubles(n_det);
+    c->window = c->grad_window = opt->precision == GWL_MIXED ? 640 : 384;
     if ((e = dev_alloc(c, &c->d_freqs, n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_geom, 9 * n_det)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_H, (int64_t)n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
@@ -487,16 +489,32 @@ int gwl_set_walk(gwl_ctx* c, int walk_kind) {
   return GWL_OK;
 }
 
-int gwl_set_tuning(gwl_ctx* c, int window, int slice, int ctas_per_sm) {
-  if (!c) return fail(GWL_ERR_ARG, "null context");
-  if (window < 0 || slice < 0 || ctas_per_sm < 0) return fail(GWL_ERR_ARG, "negative tuning value");
-  if (window) {
-    const size_t row = c->opt.precision == GWL_MIXED ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
-    if ((size_t)window * row > 200 * 1024) return fail(GWL_ERR_ARG, "window of %d bins exceeds shared memory", window);
-    if (c->opt.precision == GWL_MIXED) c->window_mixed = window; else c->window_f64 = window;
-  }
-  if (slice) c->slice = slice;
-  if (ctas_per_sm) c->ctas_per_sm = ctas_per_sm;
+int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
+  if (!c || !t) return fail(GWL_ERR_ARG, "null argument");
+  if (t->window < 0 || t->grad_window < 0 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16 || t->fused < -1 ||
+      t->fused > 1)
+    return fail(GWL_ERR_ARG, "bad tuning value");
+  if (t->window % 32 || t->grad_window % 32)
+    return fail(GWL_ERR_ARG, "windows must be multiples of 32 bins (got %d/%d)", t->window, t->grad_window);
+  const size_t row = c->opt.precision == GWL_MIXED ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
+  if ((size_t)t->window * row > 200 * 1024 || (size_t)t->grad_window * row > 200 * 1024)
+    return fail(GWL_ERR_ARG, "window of %d/%d bins exceeds shared memory", t->window, t->grad_window);
+  if (t->window) c->window = t->window;
+  if (t->grad_window) c->grad_window = t->grad_window;
+  if (t->ctas_per_sm) c->ctas_per_sm = t->ctas_per_sm;
+  if (t->fused >= 0) c->fused = t->fused;
+  return GWL_OK;
+}
+
+int gwl_get_tuning(const gwl_ctx* c, gwl_tuning* out) {
+  if (!c || !out) return fail(GWL_ERR_ARG, "null argument");
+  out->window = c->window;
+  out->ctas_per_sm = c->ctas_per_sm;
+  out->fused = c->fused;
+  out->grad_window = c->grad_window;
+  out->ms_loglike = c->tuned_ms[0];
+  out->ms_grad = c->tuned_ms[1];
+  out->n_tried = c->tuned_n;
   return GWL_OK;
 }
 

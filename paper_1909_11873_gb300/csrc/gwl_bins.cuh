@@ -42,13 +42,29 @@ __device__ __forceinline__ void load_row(const double* __restrict__ row, double 
     *reinterpret_cast<double2*>(&v[2 * k]) = reinterpret_cast<const double2*>(row)[k];
 }
 
-// Phase of one bin in float-float arithmetic, reduced to [-1/2, 1/2] cycles,
-// and its sine and cosine: (sn_d, cs_d) = sin/cos 2 pi r_d.
-template <int NDET>
+// Nearest integer of x by the 1.5 * 2^23 shift (exact for |x| < 2^22).  The
+// shift runs on the FMA pipe, whereas a rounding instruction would occupy the
+// narrow conversion pipe.
+__device__ __forceinline__ float nearest_int(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// Phase of one bin in float-float arithmetic, reduced modulo one cycle, and its
+// sine and cosine: (sn_d, cs_d) = sin/cos 2 pi r_d, r_d = S + tau_d f.
+// S = sum_m c_m B_m is summed as an unevaluated float pair (s, lo); tau_d f is
+// formed exactly as p + e (p = fl(tau_hi f_hi), e its error plus the cross
+// terms).  Two reductions:
+//   EXACT_SUM (gradient): t + q = s + p exactly (TwoSum), then
+//     r_d mod 1 = (t - rint t) + (lo + e + q): one final rounding of at most
+//     2^-25 cycles.
+//   otherwise (likelihood): S mod 1 = (s - rint s) + lo once per bin, and per
+//     detector r_d mod 1 = (S mod 1) + (p - rint p) + e (s - rint s and
+//     p - rint p are exact): two roundings of at most 2^-24 cycles each, and
+//     seven fewer FP32 operations per detector.
+template <int NDET, bool EXACT_SUM>
 __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], const float (&ch)[kNBasis],
                                             const float (&cl)[kNBasis], const float (&th)[NDET],
                                             const float (&tl)[NDET], float (&sn)[NDET], float (&cs)[NDET]) {
-  // common phase S = sum_m c_m B_m as an unevaluated float pair (s, lo)
   float s, lo;
   {
     float e;
@@ -65,20 +81,27 @@ __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], con
     lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
   }
   const float fh = v[16], fl = v[17];
+  if constexpr (EXACT_SUM) {
 #pragma unroll
-  for (int d = 0; d < NDET; ++d) {
-    // r_d = S + tau_d f, then its fractional part in [-1/2, 1/2]
-    float p, e, t, q;
-    two_prod(th[d], fh, p, e);
-    e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
-    two_sum(s, p, t, q);
-    const float l = lo + (e + q);
-    // nearest integer of t by the 1.5 * 2^23 shift (exact for |t| < 2^22); the
-    // shift runs on the FMA pipe, whereas a rounding instruction would occupy
-    // the narrow conversion pipe
-    const float n = __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
-    const float fr = __fadd_rn(__fsub_rn(t, n), l);  // t - n is exact
-    __sincosf(6.283185307179586f * fr, &sn[d], &cs[d]);
+    for (int d = 0; d < NDET; ++d) {
+      float p, e, t, q;
+      two_prod(th[d], fh, p, e);
+      e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
+      two_sum(s, p, t, q);
+      const float l = lo + (e + q);
+      const float fr = __fadd_rn(__fsub_rn(t, nearest_int(t)), l);  // t - rint t is exact
+      __sincosf(6.283185307179586f * fr, &sn[d], &cs[d]);
+    }
+  } else {
+    const float sf = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      float p, e;
+      two_prod(th[d], fh, p, e);
+      e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
+      const float fr = __fadd_rn(__fadd_rn(sf, __fsub_rn(p, nearest_int(p))), e);
+      __sincosf(6.283185307179586f * fr, &sn[d], &cs[d]);
+    }
   }
 }
 
@@ -87,7 +110,7 @@ __device__ __forceinline__ void bin_mixed(const float (&v)[RowM<NDET>::n], const
                                           const float (&cl)[kNBasis], const float (&th)[NDET],
                                           const float (&tl)[NDET], float (&U)[NDET], float (&V)[NDET]) {
   float sn[NDET], cs[NDET];
-  phase_mixed<NDET>(v, ch, cl, th, tl, sn, cs);
+  phase_mixed<NDET, false>(v, ch, cl, th, tl, sn, cs);
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     const float gr = v[18 + 2 * d], gi = v[19 + 2 * d];

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "gwl_bins.cuh"
+#include "gwl_sched.cuh"
 
 namespace gwl {
 
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
                                                       PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
                                                       PropCommon* __restrict__ pc,
                                                       PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
-                                                      int* __restrict__ work) {
+                                                      int* __restrict__ work, int* __restrict__ hist, int CH) {
   using G = typename std::conditional<MIXED, float, double>::type;
   using T = Tan<11, G>;
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
     cm.flag = ok ? 0 : 1;
     pc[p] = cm;
   }
+  hist_last_window(ncut, CH, hist);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) ncut = max(ncut, __shfl_xor_sync(0xffffffffu, ncut, off));
   if ((threadIdx.x & 31) == 0 && ncut > 0) atomicMax(&work[0], ncut);
@@ -126,6 +128,7 @@ struct GradArgs {
   const void* prop;
   void* partials;  // [B][nw_total][kAccPerDet * NDET]
   int* work;
+  const int* hist;    // [w] proposals whose last window is w
   int* status;
 };
 
@@ -156,7 +159,7 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
       float v[RowM<NDET>::n];
       load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
       float sn[NDET], cs[NDET];
-      phase_mixed<NDET>(v, ch, cl, th, tl, sn, cs);
+      phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs);
 #pragma unroll
       for (int d = 0; d < NDET; ++d) {
         const float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
@@ -224,23 +227,23 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
   int nw = (maxn + a.CH - 1) / a.CH;
   if (nw > a.nw_total) nw = a.nw_total;
   if (nw < 1) return;
-  const int G = gridDim.x;
-  const int wstep = G >= nw ? nw : G;
-  int w = G >= nw ? (int)(blockIdx.x % nw) : (int)blockIdx.x;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
   }
-  __syncthreads();
+  int n_w = 0;
+  int w = start_window(a.hist, 0, nw, blockIdx.x, gridDim.x, &n_w);
   uint32_t parity = 0;
-  for (; w < nw; w += wstep) {
+  for (; w < nw; ++w) {
     const int j0 = w * a.CH;
     int64_t j1l = (int64_t)j0 + a.CH;
     if (j1l > a.M) j1l = a.M;
     if (j1l > maxn) j1l = maxn;
-    const int j1 = j1l > j0 ? (int)j1l : j0;
-    __syncthreads();
-    if (j1 > j0) {
+    const int j1 = (int)j1l;  // > j0 because w < nw
+    int* ctr = a.work + 1 + w;
+    // every warp is done with the previous window; a window whose proposals are all taken is skipped
+    const bool drained = __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
+    if (!drained) {
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
         const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
@@ -249,26 +252,19 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
       }
       if (!mbar_wait_bounded(&bar, parity, a.status)) return;
       parity ^= 1u;
-    }
-    int* ctr = a.work + 1 + w;
-    while (true) {
-      int pi = 0;
-      if (lane == 0) pi = atomicAdd(ctr, 1);
-      pi = __shfl_sync(0xffffffffu, pi, 0);
-      if (pi >= a.B) break;
-      const int64_t p = pi;
-      const int ncut = a.pc[p].ncut;
-      if (ncut <= j0) continue;
-      Elem A[NDET][kAccPerDet];
-      grad_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, A);
-      // lanes write the per-window sums cooperatively
-      Elem* o = reinterpret_cast<Elem*>(a.partials) + ((int64_t)p * a.nw_total + w) * (kAccPerDet * NDET);
+      drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
+        Elem A[NDET][kAccPerDet];
+        grad_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, A);
+        // lanes write the per-window sums cooperatively
+        Elem* o = reinterpret_cast<Elem*>(a.partials) + (p * a.nw_total + w) * (kAccPerDet * NDET);
 #pragma unroll
-      for (int d = 0; d < NDET; ++d)
+        for (int d = 0; d < NDET; ++d)
 #pragma unroll
-        for (int k = 0; k < kAccPerDet; ++k)
-          if (lane == ((d * kAccPerDet + k) & 31)) o[d * kAccPerDet + k] = A[d][k];
+          for (int k2 = 0; k2 < kAccPerDet; ++k2)
+            if (lane == ((d * kAccPerDet + k2) & 31)) o[d * kAccPerDet + k2] = A[d][k2];
+      });
     }
+    n_w -= __ldcg(&a.hist[w]);
   }
 }
 
@@ -330,7 +326,8 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
 // ---------------------------------------------------------------- launchers
 int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B) {
   const bool mixed = c->opt.precision == GWL_MIXED;
-  int CH = mixed ? c->window_mixed : c->window_f64;
+  (void)mixed;
+  int CH = c->grad_window;
   if (CH > c->M) CH = (int)c->M;
   const int64_t nw = (c->M + CH - 1) / CH;
   return B * nw * kAccPerDet * c->n_det * (int64_t)(mixed ? sizeof(float) : sizeof(double));
@@ -338,21 +335,22 @@ int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B) {
 int64_t prop_grad_bytes(const gwl_ctx* c) {
   return c->opt.precision == GWL_MIXED ? (int64_t)sizeof(PropGrad<float>) : (int64_t)sizeof(PropGrad<double>);
 }
-int64_t work_needed(const gwl_ctx* c);
+int64_t work_needed(const gwl_ctx* c, int64_t B);
+int* window_hist(const gwl_ctx* c);
 
 template <int NDET, bool MIXED>
 static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
   using G = typename std::conditional<MIXED, float, double>::type;
-  int CH = MIXED ? c->window_mixed : c->window_f64;
+  int CH = c->grad_window;
   if (CH > c->M) CH = (int)c->M;
   const int nw_total = (int)((c->M + CH - 1) / CH);
-  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c), st);
+  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
     k_prologue_grad<MIXED><<<(unsigned)((B + 63) / 64), 64, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc,
                                                                       reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
-                                                                      c->d_work);
+                                                                      c->d_work, window_hist(c), CH);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -367,6 +365,7 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   a.prop = MIXED ? (const void*)c->d_pm : (const void*)c->d_pf;
   a.partials = c->d_gpartials;
   a.work = c->d_work;
+  a.hist = window_hist(c);
   a.status = c->d_status;
   const size_t smem = (size_t)CH * a.row_elems * sizeof(G);
   static size_t smem_set = 0;

@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "gwl_bins.cuh"
+#include "gwl_sched.cuh"
 
 namespace gwl {
 
@@ -48,18 +49,33 @@ namespace gwl {
 //   phase 2  warp 0: basis coefficients c_m and the constant PN phase
 //            warp 1: antenna patterns -> complex responses P_d
 //   phase 3  warp 2: K_d, <h|h>, cut; the batch's largest cut
-template <bool MIXED>
-__global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B,
-                                                  PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
-                                                  PropCommon* __restrict__ pc, int* __restrict__ work) {
-  __shared__ double sh_la[32], sh_a13[32], sh_amp[32], sh_ccyc[32];
-  __shared__ double sh_phi[6][32];
-  __shared__ double sh_sky[4][32];   // sin/cos of (ra - gmst), sin/cos of dec
-  __shared__ double sh_ori[3][32];   // sin psi, cos psi, cos iota
-  __shared__ double sh_P[2 * kMaxDet][32];
-  __shared__ int sh_ncut[32];
-  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
-  const int64_t p = (int64_t)blockIdx.x * 32 + lane;
+struct ProSmem {
+  double la[32], a13[32], amp[32], ccyc[32];
+  double phi[6][32];
+  double sky[4][32];  // sin/cos of (ra - gmst), sin/cos of dec
+  double ori[3][32];  // sin psi, cos psi, cos iota
+  double P[2 * kMaxDet][32];
+  int ncut[32];
+};
+
+// The coefficients of rows row0 .. row0+31, computed by four warps (role 0..3);
+// `sync` synchronises exactly those four warps.
+template <bool MIXED, class Sync>
+__device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __restrict__ theta, int64_t B,
+                                              int64_t row0, int role, int lane, ProSmem& sm, Sync sync,
+                                              PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
+                                              PropCommon* __restrict__ pc, int* __restrict__ work,
+                                              int* __restrict__ hist, int CH) {
+  double (&sh_la)[32] = sm.la;
+  double (&sh_a13)[32] = sm.a13;
+  double (&sh_amp)[32] = sm.amp;
+  double (&sh_ccyc)[32] = sm.ccyc;
+  double (&sh_phi)[6][32] = sm.phi;
+  double (&sh_sky)[4][32] = sm.sky;
+  double (&sh_ori)[3][32] = sm.ori;
+  double (&sh_P)[2 * kMaxDet][32] = sm.P;
+  int (&sh_ncut)[32] = sm.ncut;
+  const int64_t p = row0 + lane;
   const bool valid = p < B;
   double th[11];
 #pragma unroll
@@ -112,7 +128,7 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
     sh_ori[1][lane] = cp;
     sh_ori[2][lane] = cos(th[5]);
   }
-  __syncthreads();
+  sync();
 
   // ---- phase 2
   if (role == 0) {
@@ -154,7 +170,7 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
       sh_P[2 * d + 1][lane] = Pi;
     }
   }
-  __syncthreads();
+  sync();
 
   // ---- phase 3
   if (role == 2) {
@@ -194,7 +210,27 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
     if (lane == 0 && nm > 0) atomicMax(&work[0], nm);
+    hist_last_window(valid ? ncut : 0, CH, hist);
   }
+}
+
+struct CtaSync {
+  __device__ void operator()() const { __syncthreads(); }
+};
+// Named barrier for one 4-warp set (ids 1 and 2; 0 is __syncthreads).
+struct SetSync {
+  int id;
+  __device__ void operator()() const { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B,
+                                                  PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
+                                                  PropCommon* __restrict__ pc, int* __restrict__ work,
+                                                  int* __restrict__ hist, int CH) {
+  __shared__ ProSmem sm;
+  prologue_rows<MIXED>(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(),
+                       pm, pf, pc, work, hist, CH);
 }
 
 // ---------------------------------------------------------------- windowed bin loop
@@ -205,10 +241,12 @@ struct WinArgs {
   int CH;         // bins per window
   int64_t B;
   int nw_total;   // ceil(M / CH)
+  int first_w;    // first window handled (1 after the fused kernel did window 0)
   const PropCommon* pc;
   const void* prop;  // PropMixed* or PropF64*
   void* partials;    // [B][nw_total][2 NDET] float (mixed) or double (fp64)
   int* work;         // [0] largest cut, [1 + w] proposal counter of window w
+  const int* hist;   // [w] proposals whose last window is w
   int* status;       // latched error bits
 };
 
@@ -296,26 +334,26 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
   const int maxn = a.work[0];
   int nw = (maxn + a.CH - 1) / a.CH;
   if (nw > a.nw_total) nw = a.nw_total;
-  if (nw < 1) return;  // no proposal has a bin in band
-  const int G = gridDim.x;
-  const int wstep = G >= nw ? nw : G;
-  int w = G >= nw ? (int)(blockIdx.x % nw) : (int)blockIdx.x;
+  if (nw <= a.first_w) return;  // no proposal has a bin in the windows left to this kernel
 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
   }
-  __syncthreads();
+  int n_w = 0;
+  int w = start_window(a.hist, a.first_w, nw, blockIdx.x, gridDim.x, &n_w);
 
   uint32_t parity = 0;
-  for (; w < nw; w += wstep) {
+  for (; w < nw; ++w) {
     const int j0 = w * a.CH;
     int64_t j1l = (int64_t)j0 + a.CH;
     if (j1l > a.M) j1l = a.M;
     if (j1l > maxn) j1l = maxn;
-    const int j1 = j1l > j0 ? (int)j1l : j0;
-    __syncthreads();  // every warp is done with the previous window
-    if (j1 > j0) {
+    const int j1 = (int)j1l;  // > j0 because w < nw
+    int* ctr = a.work + 1 + w;
+    // every warp is done with the previous window; a window whose proposals are all taken is skipped
+    const bool drained = __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
+    if (!drained) {
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
         const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
@@ -324,25 +362,140 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
       }
       if (!mbar_wait_bounded(&bar, parity, a.status)) return;
       parity ^= 1u;
-    }
-    int* ctr = a.work + 1 + w;
-    while (true) {
-      int pi = 0;
-      if (lane == 0) pi = atomicAdd(ctr, 1);
-      pi = __shfl_sync(0xffffffffu, pi, 0);
-      if (pi >= a.B) break;
-      const int64_t p = pi;
-      const int ncut = a.pc[p].ncut;
-      if (ncut <= j0) continue;
-      Acc U[NDET], V[NDET];
-      window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
-      if (lane == 0) {
-        Acc* o = reinterpret_cast<Acc*>(a.partials) + ((int64_t)p * a.nw_total + w) * (2 * NDET);
+      drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
+        Acc U[NDET], V[NDET];
+        window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
+        if (lane == 0) {
+          Acc* o = reinterpret_cast<Acc*>(a.partials) + (p * a.nw_total + w) * (2 * NDET);
 #pragma unroll
-        for (int d = 0; d < NDET; ++d) {
-          o[2 * d] = U[d];
-          o[2 * d + 1] = V[d];
+          for (int d = 0; d < NDET; ++d) {
+            o[2 * d] = U[d];
+            o[2 * d + 1] = V[d];
+          }
         }
+      });
+    }
+    n_w -= __ldcg(&a.hist[w]);
+  }
+}
+
+// ---------------------------------------------------------------- fused prologue + window 0
+// Every CTA first produces: it takes groups of 64 rows from an atomic counter
+// and computes their coefficients (two 4-warp sets, one per 32 rows, FP64),
+// then publishes one ready flag per 32 rows.  When no group is left it
+// consumes: it stages window 0 of the table (bulk copy, bounded wait) into the
+// same shared memory and takes proposals in order from a second counter,
+// waiting (bounded spin) until the proposal's rows are published.  The FP64
+// prologue of late groups thus overlaps the FP32 bin loop of early ones.  No
+// consumer waits for rows that no running CTA holds: a group is only taken by
+// a CTA that is executing, and it publishes before it consumes.
+struct FusedArgs {
+  SegInfo s;
+  const double* theta;
+  int64_t B;
+  const void* tab;
+  int row_elems;
+  int CH;
+  int nw_total;
+  PropMixed* pm;
+  PropF64* pf;
+  PropCommon* pc;
+  void* partials;
+  int* work;  // [0] largest cut, [1 + w] window counters (used by the later kernel)
+  int* hist;  // [w] proposals whose last window is w
+  int* fctr;  // [0] group counter, [1] proposal counter, [2 + r] ready flag of rows 32r .. 32r+31
+  int* status;
+};
+
+template <int NDET, bool MIXED>
+__global__ void __launch_bounds__(256, 3) k_fused(FusedArgs a) {
+  using Elem = typename std::conditional<MIXED, float, double>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int sh_group;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int set = warp >> 2, role = warp & 3;
+  ProSmem* psm = reinterpret_cast<ProSmem*>(smem_raw) + set;  // two sets, aliased with the window later
+  const int64_t n_groups = (a.B + 63) / 64;
+  // ---- produce
+  while (true) {
+    if (threadIdx.x == 0) sh_group = atomicAdd(&a.fctr[0], 1);
+    __syncthreads();
+    const int64_t g = sh_group;
+    __syncthreads();
+    if (g >= n_groups) break;
+    const int64_t row0 = g * 64 + set * 32;
+    if (row0 < a.B)
+      prologue_rows<MIXED>(a.s, a.theta, a.B, row0, role, lane, *psm, SetSync{1 + set}, a.pm, a.pf, a.pc, a.work,
+                           a.hist, a.CH);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(&a.fctr[2 + 2 * g], 1);
+      atomicExch(&a.fctr[3 + 2 * g], 1);
+    }
+  }
+  // ---- consume window 0
+  Elem* sm = reinterpret_cast<Elem*>(smem_raw);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int j1 = a.CH < a.s.M ? a.CH : (int)a.s.M;
+  if (threadIdx.x == 0) {
+    fence_proxy_async_smem();
+    const uint32_t bytes = (uint32_t)j1 * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(sm, a.tab, bytes, &bar);
+  }
+  if (!mbar_wait_bounded(&bar, 0, a.status)) return;
+  WinArgs wa;
+  wa.tab = a.tab;
+  wa.row_elems = a.row_elems;
+  wa.M = a.s.M;
+  wa.CH = a.CH;
+  wa.B = a.B;
+  wa.nw_total = a.nw_total;
+  wa.first_w = 0;
+  wa.pc = a.pc;
+  wa.prop = MIXED ? (const void*)a.pm : (const void*)a.pf;
+  wa.partials = a.partials;
+  wa.work = a.work;
+  wa.hist = a.hist;
+  wa.status = a.status;
+  while (true) {
+    int pi = 0;
+    if (lane == 0) {
+      pi = atomicAdd(&a.fctr[1], 1);
+      if (pi < a.B) {  // wait until the proposal's rows are published (bounded)
+        const volatile int* flag = &a.fctr[2 + pi / 32];
+        const long long t0 = clock64();
+        while (*flag == 0) {
+          if (clock64() - t0 > 2000000000LL) {
+            atomicOr(a.status, kStatusTimeout);
+            pi = -1;
+            break;
+          }
+          __nanosleep(256);
+        }
+        __threadfence();
+      }
+    }
+    pi = __shfl_sync(0xffffffffu, pi, 0);
+    if (pi < 0) return;
+    if (pi >= a.B) break;
+    const int64_t p = pi;
+    const int ncut = __ldcg(&a.pc[p].ncut);
+    if (ncut <= 0) continue;
+    Elem U[NDET], V[NDET];
+    window_sums<NDET, MIXED>(wa, sm, p, 0, ncut < j1 ? ncut : j1, lane, U, V);
+    if (lane == 0) {
+      Elem* o = reinterpret_cast<Elem*>(a.partials) + (int64_t)p * a.nw_total * (2 * NDET);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        o[2 * d] = U[d];
+        o[2 * d + 1] = V[d];
       }
     }
   }
@@ -410,8 +563,8 @@ __global__ void k_waveform(SegInfo s, const PropF64* __restrict__ pf, const Prop
 
 // ---------------------------------------------------------------- launchers
 static int window_of(const gwl_ctx* c, int precision) {
-  int CH = precision == GWL_MIXED ? c->window_mixed : c->window_f64;
-  return CH > c->M ? (int)c->M : CH;
+  (void)precision;
+  return c->window > c->M ? (int)c->M : c->window;
 }
 
 int64_t partials_needed(const gwl_ctx* c, int64_t B) {
@@ -420,10 +573,19 @@ int64_t partials_needed(const gwl_ctx* c, int64_t B) {
   return B * nw * 2 * c->n_det;
 }
 
-int64_t work_needed(const gwl_ctx* c) {
-  const int CH = window_of(c, c->opt.precision);
-  return 1 + (c->M + CH - 1) / CH;
+// Windows of the likelihood or the gradient bin loop, whichever has more.
+static int64_t nw_max(const gwl_ctx* c) {
+  int CH = window_of(c, c->opt.precision);
+  const int CHg = c->grad_window > c->M ? (int)c->M : c->grad_window;
+  if (CHg < CH) CH = CHg;
+  return (c->M + CH - 1) / CH;
 }
+// [0] largest cut, [1 + w] proposal counter of window w, [1 + nw_max + w]
+// histogram of last windows, then the fused kernel's group and proposal
+// counters and one ready flag per 32 rows.
+int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + 2 + 2 * ((B + 63) / 64); }
+int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
+static int* fused_counters(const gwl_ctx* c) { return c->d_work + 1 + 2 * nw_max(c); }
 
 template <int NDET, bool MIXED>
 static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, cudaStream_t st) {
@@ -440,11 +602,57 @@ static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t sme
   return e;
 }
 
+cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int precision, cudaStream_t st);
+
 template <int NDET>
-static cudaError_t run_pipeline(gwl_ctx* c, int64_t B, double* lnl, cudaStream_t st) {
+static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
   const bool mixed = c->opt.precision == GWL_MIXED;
   const int CH = window_of(c, c->opt.precision);
   const int nw_total = (int)((c->M + CH - 1) / CH);
+  const bool fused = c->fused != 0;
+  cudaError_t e = cudaSuccess;
+  if (fused) {
+    e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
+    if (e != cudaSuccess) return e;
+    FusedArgs f;
+    f.s = c->seg;
+    f.theta = theta;
+    f.B = B;
+    f.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
+    f.row_elems = mixed ? c->row_floats : c->row_doubles;
+    f.CH = CH;
+    f.nw_total = nw_total;
+    f.pm = c->d_pm;
+    f.pf = c->d_pf;
+    f.pc = c->d_pc;
+    f.partials = c->d_partials;
+    f.work = c->d_work;
+    f.fctr = fused_counters(c);
+    f.hist = window_hist(c);
+    f.status = c->d_status;
+    size_t smem = (size_t)CH * f.row_elems * (mixed ? sizeof(float) : sizeof(double));
+    if (smem < 2 * sizeof(ProSmem)) smem = 2 * sizeof(ProSmem);
+    static size_t smem_set[2] = {0, 0};
+    if (smem > smem_set[mixed]) {
+      e = mixed ? cudaFuncSetAttribute(k_fused<NDET, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                : cudaFuncSetAttribute(k_fused<NDET, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      smem_set[mixed] = smem;
+    }
+    int64_t want = (B + 7) / 8;
+    int grid = c->num_sms * c->ctas_per_sm;
+    if (want < grid) grid = (int)(want > 0 ? want : 1);
+    {
+      ProfScope ps(c, GWL_KERNEL_BINS, st);
+      if (mixed) k_fused<NDET, true><<<grid, 256, smem, st>>>(f);
+      else k_fused<NDET, false><<<grid, 256, smem, st>>>(f);
+    }
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    e = launch_prologue(c, theta, B, c->opt.precision, st);
+    if (e != cudaSuccess) return e;
+  }
   WinArgs a;
   a.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
   a.row_elems = mixed ? c->row_floats : c->row_doubles;
@@ -452,17 +660,19 @@ static cudaError_t run_pipeline(gwl_ctx* c, int64_t B, double* lnl, cudaStream_t
   a.CH = CH;
   a.B = B;
   a.nw_total = nw_total;
+  a.first_w = fused ? 1 : 0;
   a.pc = c->d_pc;
   a.prop = mixed ? (const void*)c->d_pm : (const void*)c->d_pf;
   a.partials = c->d_partials;
   a.work = c->d_work;
+  a.hist = window_hist(c);
   a.status = c->d_status;
   const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double));
   // enough CTAs for every warp of a window to find a proposal, at most a full wave
-  int64_t want = ((B + 7) / 8) * nw_total;
+  int64_t want = ((B + 7) / 8) * (nw_total - a.first_w > 0 ? nw_total - a.first_w : 1);
   int grid = c->num_sms * c->ctas_per_sm;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
-  cudaError_t e = mixed ? run_window<NDET, true>(c, a, grid, smem, st) : run_window<NDET, false>(c, a, grid, smem, st);
+  e = mixed ? run_window<NDET, true>(c, a, grid, smem, st) : run_window<NDET, false>(c, a, grid, smem, st);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_COMBINE, st);
@@ -479,28 +689,28 @@ static cudaError_t run_pipeline(gwl_ctx* c, int64_t B, double* lnl, cudaStream_t
 }
 
 cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int precision, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c), st);
+  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
     const unsigned nb = (unsigned)((B + 31) / 32);
     if (precision == GWL_MIXED)
-      k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work);
+      k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work, window_hist(c),
+                                           window_of(c, precision));
     else
-      k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work);
+      k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work, window_hist(c),
+                                            window_of(c, precision));
   }
   c->launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
-  cudaError_t e = launch_prologue(c, theta, B, c->opt.precision, st);
-  if (e != cudaSuccess) return e;
   switch (c->n_det) {
-    case 1: return run_pipeline<1>(c, B, lnl, st);
-    case 2: return run_pipeline<2>(c, B, lnl, st);
-    case 3: return run_pipeline<3>(c, B, lnl, st);
-    default: return run_pipeline<4>(c, B, lnl, st);
+    case 1: return run_pipeline<1>(c, theta, B, lnl, st);
+    case 2: return run_pipeline<2>(c, theta, B, lnl, st);
+    case 3: return run_pipeline<3>(c, theta, B, lnl, st);
+    default: return run_pipeline<4>(c, theta, B, lnl, st);
   }
 }
 

@@ -311,7 +311,7 @@ cudaError_t multi_prepare(Multi* m, int64_t n_per) {
     d.seg = c->seg;
     d.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
     d.row_elems = mixed ? c->row_floats : c->row_doubles;
-    int CH = mixed ? c->window_mixed : c->window_f64;
+    int CH = c->window;
     if (CH > c->M) CH = (int)c->M;
     d.CH = CH;
     d.nw_total = (int)((c->M + CH - 1) / CH);

@@ -16,7 +16,7 @@
 
 namespace gwl {
 int64_t partials_needed(const gwl_ctx* c, int64_t B);
-int64_t work_needed(const gwl_ctx* c);
+int64_t work_needed(const gwl_ctx* c, int64_t B);
 int set_error(int code, const char* fmt, ...);
 }  // namespace gwl
 
@@ -38,7 +38,7 @@ size_t static_bytes_needed(const gwl_ctx* c, int64_t B) {
   n += align256(sizeof(gwl::PropF64) * (size_t)B);
   n += align256(sizeof(gwl::PropCommon) * (size_t)B);
   n += align256(sizeof(double) * (size_t)gwl::partials_needed(c, B));
-  n += align256(sizeof(int) * (size_t)gwl::work_needed(c));
+  n += align256(sizeof(int) * (size_t)gwl::work_needed(c, B));
   return n;
 }
 

@@ -1,0 +1,147 @@
+// gwl_tune.cu -- the autotuner of the bin-loop launch shape (gwl_autotune).
+//
+// The bin loops are tiled by a window of frequency bins staged in shared
+// memory and a grid sized in CTAs per SM; the likelihood can also run its
+// per-proposal coefficients and first window in one producer/consumer kernel.
+// Which shape is fastest depends on the segment length (bins), the detector
+// count (row size) and the batch, so the library times the candidates on the
+// caller's own batch and keeps the fastest.  Only public entry points are
+// called; every launch goes through gwl_loglike / gwl_grad.
+#include <string>
+#include <vector>
+
+#include "gwl_internal.h"
+
+namespace gwl {
+int set_error(int code, const char* fmt, ...);
+}
+
+namespace {
+
+struct Timer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t init() {
+    cudaError_t e = cudaEventCreate(&e0);
+    return e == cudaSuccess ? cudaEventCreate(&e1) : e;
+  }
+  ~Timer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+// Best time (ms per call) of two runs of `reps` back-to-back calls after one
+// warm-up call; returns a GWL_* code.
+template <class F>
+int time_calls(Timer& t, cudaStream_t st, F call, double* ms_out) {
+  const int reps = 3;
+  int rc = call();
+  if (rc) return rc;
+  double best = 1e30;
+  for (int r = 0; r < 2; ++r) {
+    cudaError_t e = cudaEventRecord(t.e0, st);
+    if (e != cudaSuccess) return gwl::set_error(GWL_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    for (int k = 0; k < reps; ++k)
+      if ((rc = call())) return rc;
+    if ((e = cudaEventRecord(t.e1, st)) != cudaSuccess || (e = cudaEventSynchronize(t.e1)) != cudaSuccess)
+      return gwl::set_error(GWL_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, t.e0, t.e1)) != cudaSuccess)
+      return gwl::set_error(GWL_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    if (ms / reps < best) best = ms / reps;
+  }
+  *ms_out = best;
+  return GWL_OK;
+}
+
+}  // namespace
+
+extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int what, gwl_tuning* out,
+                            void* stream) {
+  if (!c) return gwl::set_error(GWL_ERR_ARG, "null context");
+  if (B < 1 || !theta_dev) return gwl::set_error(GWL_ERR_ARG, "autotune needs a non-empty device batch");
+  if (what < 1 || what > 3) return gwl::set_error(GWL_ERR_ARG, "bad autotune selector %d", what);
+  cudaStream_t st = (cudaStream_t)stream;
+  gwl_tuning saved;
+  int rc = gwl_get_tuning(c, &saved);
+  if (rc) return rc;
+  saved.ms_loglike = saved.ms_grad = 0.0;
+
+  const size_t row = c->opt.precision == GWL_MIXED ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
+  std::vector<int> windows;
+  for (int w = 128; w <= 1536; w += 64) {
+    if ((size_t)w * row > 200 * 1024) break;
+    // windows at least as long as the segment are all the same shape
+    if (w >= c->M) {
+      windows.push_back(w);
+      break;
+    }
+    // keep the per-window partial sums within 2 GB
+    const int64_t nw = (c->M + w - 1) / w;
+    if (B * nw * 2 * c->n_det * (int64_t)sizeof(double) > ((int64_t)2 << 30)) continue;
+    windows.push_back(w);
+  }
+  if (windows.empty()) return gwl::set_error(GWL_ERR_ARG, "autotune: no window fits");
+
+  double* d_out = nullptr;
+  const int64_t n_out = B * (1 + c->opt.n_dim);
+  cudaError_t e = cudaMalloc(&d_out, sizeof(double) * (size_t)n_out);
+  if (e != cudaSuccess) return gwl::set_error(GWL_ERR_NOMEM, "autotune: %s", cudaGetErrorString(e));
+  Timer t;
+  if ((e = t.init()) != cudaSuccess) {
+    cudaFree(d_out);
+    return gwl::set_error(GWL_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  }
+
+  gwl_tuning best = saved;
+  double best_l = 1e30, best_g = 1e30;
+  int tried = 0;
+  if (what & GWL_TUNE_LOGLIKE) {
+    for (int fused = 0; fused <= 1 && !rc; ++fused)
+      for (int ctas = 1; ctas <= 4 && !rc; ++ctas)
+        for (int w : windows) {
+          gwl_tuning s = saved;
+          s.window = w;
+          s.ctas_per_sm = ctas;
+          s.fused = fused;
+          if ((rc = gwl_set_tuning(c, &s))) break;
+          double ms = 0.0;
+          rc = time_calls(t, st, [&] { return gwl_loglike(c, theta_dev, B, d_out, stream); }, &ms);
+          if (rc) break;
+          ++tried;
+          if (ms < best_l) {
+            best_l = ms;
+            best.window = w;
+            best.ctas_per_sm = ctas;
+            best.fused = fused;
+          }
+        }
+  }
+  if (!rc && (what & GWL_TUNE_GRAD)) {
+    for (int w : windows) {
+      gwl_tuning s = saved;
+      s.grad_window = w;
+      if ((rc = gwl_set_tuning(c, &s))) break;
+      double ms = 0.0;
+      rc = time_calls(t, st, [&] { return gwl_grad(c, theta_dev, B, d_out, d_out + B, stream); }, &ms);
+      if (rc) break;
+      ++tried;
+      if (ms < best_g) {
+        best_g = ms;
+        best.grad_window = w;
+      }
+    }
+  }
+  if (!rc) rc = gwl_sync(c);  // a bounded wait that ran out during tuning fails the tuning
+  cudaFree(d_out);
+  if (rc) {
+    const std::string msg = gwl_last_error();
+    gwl_set_tuning(c, &saved);
+    return gwl::set_error(rc, "%s", msg.c_str());
+  }
+  if ((rc = gwl_set_tuning(c, &best))) return rc;
+  if (what & GWL_TUNE_LOGLIKE) c->tuned_ms[0] = best_l;
+  if (what & GWL_TUNE_GRAD) c->tuned_ms[1] = best_g;
+  c->tuned_n = tried;
+  return out ? gwl_get_tuning(c, out) : GWL_OK;
+}

@@ -26,10 +26,13 @@ MAX_DET = 4
 EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "ns_run", "gwl_grad", "gwl_waveform", "ns_replace",
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
-           "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk")
+           "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
+           "gwl_get_tuning", "gwl_autotune")
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
+GWL_TUNE_LOGLIKE = 1
+GWL_TUNE_GRAD = 2
 
 
 class GwlDetector(C.Structure):
@@ -58,6 +61,14 @@ class GwlNsResult(C.Structure):
                 ("consumed_per_round", C.c_double), ("dlogz", C.c_double), ("n_dead_returned", C.c_int64)]
 
 
+class GwlTuning(C.Structure):
+    _fields_ = [("window", C.c_int), ("ctas_per_sm", C.c_int), ("fused", C.c_int), ("grad_window", C.c_int),
+                ("ms_loglike", C.c_double), ("ms_grad", C.c_double), ("n_tried", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GwlError(RuntimeError):
     pass
 
@@ -82,7 +93,9 @@ def lib() -> C.CDLL:
         L.ns_replace.argtypes = [P, P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, P]
         L.ns_run.argtypes = [P, i64, i64, i32, u64, d, i64, d, i64, P, P, P, C.POINTER(GwlNsResult), P]
         L.gwl_sync.argtypes = [P]
-        L.gwl_set_tuning.argtypes = [P, i32, i32, i32]
+        L.gwl_set_tuning.argtypes = [P, C.POINTER(GwlTuning)]
+        L.gwl_get_tuning.argtypes = [P, C.POINTER(GwlTuning)]
+        L.gwl_autotune.argtypes = [P, P, i64, i32, C.POINTER(GwlTuning), P]
         L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
         L.gwl_profile_read.argtypes = [P, i32, C.POINTER(d), C.POINTER(i64)]
@@ -246,8 +259,21 @@ class Context:
     def gwl_set_walk(self, kind: int):
         _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
 
-    def gwl_set_tuning(self, window=0, slice=0, ctas_per_sm=0):
-        _check(lib().gwl_set_tuning(self._h, int(window), int(slice), int(ctas_per_sm)), "gwl_set_tuning")
+    def gwl_set_tuning(self, window=0, ctas_per_sm=0, fused=-1, grad_window=0):
+        t = GwlTuning(int(window), int(ctas_per_sm), int(fused), int(grad_window), 0.0, 0.0, 0)
+        _check(lib().gwl_set_tuning(self._h, C.byref(t)), "gwl_set_tuning")
+
+    def gwl_get_tuning(self) -> dict:
+        t = GwlTuning()
+        _check(lib().gwl_get_tuning(self._h, C.byref(t)), "gwl_get_tuning")
+        return t.as_dict()
+
+    def gwl_autotune(self, theta, what=GWL_TUNE_LOGLIKE | GWL_TUNE_GRAD, stream=None) -> dict:
+        """Time the bin-loop launch shapes on this batch (B x n_dim, float64, on the device); keep the fastest."""
+        t = GwlTuning()
+        _check(lib().gwl_autotune(self._h, _ptr(theta), theta.shape[0], int(what), C.byref(t), _stream(stream)),
+               "gwl_autotune")
+        return t.as_dict()
 
     def gwl_profile(self, enable: bool):
         _check(lib().gwl_profile(self._h, int(bool(enable))), "gwl_profile")

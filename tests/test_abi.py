@@ -54,4 +54,7 @@ def test_argument_errors_are_synchronous(L):
     opt.precision = 7
     assert L.gwl_create(f.ctypes.data, 16, s.ctypes.data, p.ctypes.data, dets, 1, C.byref(opt), C.byref(out)) == -1
     assert L.gwl_loglike(None, None, 1, None, None) == -1
+    assert L.gwl_autotune(None, None, 1, 1, None, None) == -1
+    assert L.gwl_set_tuning(None, None) == -1
+    assert L.gwl_get_tuning(None, None) == -1
     assert out.value is None
