@@ -309,7 +309,7 @@ def run_gwl(args):
     fisco = 1.0 / (6 ** 1.5 * math.pi * theta_full[:, 0] * eta ** -0.6 * 4.925490947e-6)
     ncut = np.searchsorted(ev.freqs, fisco, side="right")
     pairs = float(ncut.sum())
-    # the bin loop of one call: one launch, or two with the fused producer/consumer shape
+    # the bin loop of one call (one launch; it also forms lnL)
     bins_ms, bins_n = prof[gwl.KERNEL_BINS]
     per_launch_s = bins_ms / args.steps * 1e-3
     peaks = measured_peaks()
@@ -352,8 +352,7 @@ def run_gwl(args):
                 "d2h_bytes_per_step": int(BATCH * 8)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": ("k_fused<3,mixed> + k_window<3,mixed> (bin loop, fused shape)"
-                                if tuning["mixed"]["fused"] else "k_window<3,mixed> (windowed bin loop)"),
+                     "kernel": "k_window<3,mixed> (windowed bin loop and lnL combination)",
                      "peak_basis": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 flop x {fclk / 1e6:.0f} MHz (derived)",
                      "flops_per_pair": FLOPS_PER_BIN_MIXED, "pairs_per_launch": int(pairs),
                      "kernel_ms": per_launch_s * 1e3,
@@ -361,7 +360,7 @@ def run_gwl(args):
         "kernel_ms": {"prologue": prof[gwl.KERNEL_PROLOGUE][0] / args.steps,
                       "bins": bins_ms / args.steps,
                       "combine": prof[gwl.KERNEL_COMBINE][0] / args.steps},
-        "tuning": {k: {f: v[f] for f in ("window", "ctas_per_sm", "fused", "ms_loglike", "n_tried")}
+        "tuning": {k: {f: v[f] for f in ("window", "ctas_per_sm", "ms_loglike", "n_tried")}
                    for k, v in tuning.items()},
         "clocks": clk,
         "gpu_launches": int(results[gwl.GWL_MIXED]["launches"]),

@@ -276,8 +276,6 @@ int gwl_sync(gwl_ctx* ctx);
 typedef struct gwl_tuning {
   int window;        /* likelihood bin loop: bins per window; 0 keeps (set) */
   int ctas_per_sm;   /* likelihood bin loop: grid = ctas_per_sm x SMs; 0 keeps */
-  int fused;         /* 1: per-proposal coefficients and window 0 in one
-                        producer/consumer kernel; 0: separate kernels; -1 keeps */
   int grad_window;   /* gradient bin loop: bins per window; 0 keeps */
   double ms_loglike; /* gwl_autotune output: best time of one gwl_loglike call
                         (ms) at the tuned batch; gwl_get_tuning: last tuned value or 0 */
@@ -299,7 +297,7 @@ int gwl_get_tuning(const gwl_ctx* ctx, gwl_tuning* out);
 
 /* Autotuner: times gwl_loglike (what & GWL_TUNE_LOGLIKE) over every window in
  * {128, 192, ..., 1536} bins that fits in shared memory (at most the segment),
- * every ctas_per_sm in {1, 2, 3, 4} and fused in {0, 1}, and gwl_grad
+ * and every ctas_per_sm in {1, 2, 3, 4}, and gwl_grad
  * (what & GWL_TUNE_GRAD) over the same windows, on the caller's batch
  * theta_dev (B x n_dim, device, row-major, read only) on `stream`, and keeps
  * the fastest shape of each in the context.  Each shape is timed with CUDA

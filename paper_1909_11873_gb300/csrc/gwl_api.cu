@@ -491,8 +491,7 @@ int gwl_set_walk(gwl_ctx* c, int walk_kind) {
 
 int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
   if (!c || !t) return fail(GWL_ERR_ARG, "null argument");
-  if (t->window < 0 || t->grad_window < 0 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16 || t->fused < -1 ||
-      t->fused > 1)
+  if (t->window < 0 || t->grad_window < 0 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16)
     return fail(GWL_ERR_ARG, "bad tuning value");
   if (t->window % 32 || t->grad_window % 32)
     return fail(GWL_ERR_ARG, "windows must be multiples of 32 bins (got %d/%d)", t->window, t->grad_window);
@@ -502,7 +501,6 @@ int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
   if (t->window) c->window = t->window;
   if (t->grad_window) c->grad_window = t->grad_window;
   if (t->ctas_per_sm) c->ctas_per_sm = t->ctas_per_sm;
-  if (t->fused >= 0) c->fused = t->fused;
   return GWL_OK;
 }
 
@@ -510,7 +508,6 @@ int gwl_get_tuning(const gwl_ctx* c, gwl_tuning* out) {
   if (!c || !out) return fail(GWL_ERR_ARG, "null argument");
   out->window = c->window;
   out->ctas_per_sm = c->ctas_per_sm;
-  out->fused = c->fused;
   out->grad_window = c->grad_window;
   out->ms_loglike = c->tuned_ms[0];
   out->ms_grad = c->tuned_ms[1];

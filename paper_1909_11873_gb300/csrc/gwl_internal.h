@@ -54,7 +54,6 @@ struct gwl_ctx {
   int window = 0;       // likelihood bin loop: bins per staged window
   int grad_window = 0;  // gradient bin loop: bins per staged window
   int ctas_per_sm = 3;  // likelihood bin loop grid: CTAs per SM
-  int fused = 0;        // 1: prologue and window 0 in one producer/consumer kernel
   double tuned_ms[2] = {0.0, 0.0};  // autotuner: best gwl_loglike / gwl_grad time (ms)
   int tuned_n = 0;                  // autotuner: shapes timed
 

@@ -65,7 +65,7 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
                                               int64_t row0, int role, int lane, ProSmem& sm, Sync sync,
                                               PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
                                               PropCommon* __restrict__ pc, int* __restrict__ work,
-                                              int* __restrict__ hist, int CH) {
+                                              int* __restrict__ hist, int CH, double* __restrict__ lnl) {
   double (&sh_la)[32] = sm.la;
   double (&sh_a13)[32] = sm.a13;
   double (&sh_amp)[32] = sm.amp;
@@ -204,6 +204,8 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
       cm.ncut = ncut;
       cm.flag = ok ? 0 : 1;
       pc[p] = cm;
+      // rows that no bin loop visits: unphysical (-inf) or without an in-band bin (lnL = 0)
+      if (lnl && ncut == 0) lnl[p] = ok ? 0.0 : -INFINITY;
     }
     // largest cut of the batch: one atomic per warp
     int nm = valid ? ncut : 0;
@@ -217,20 +219,15 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
 struct CtaSync {
   __device__ void operator()() const { __syncthreads(); }
 };
-// Named barrier for one 4-warp set (ids 1 and 2; 0 is __syncthreads).
-struct SetSync {
-  int id;
-  __device__ void operator()() const { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
-};
 
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B,
                                                   PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
                                                   PropCommon* __restrict__ pc, int* __restrict__ work,
-                                                  int* __restrict__ hist, int CH) {
+                                                  int* __restrict__ hist, int CH, double* __restrict__ lnl) {
   __shared__ ProSmem sm;
   prologue_rows<MIXED>(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(),
-                       pm, pf, pc, work, hist, CH);
+                       pm, pf, pc, work, hist, CH, lnl);
 }
 
 // ---------------------------------------------------------------- windowed bin loop
@@ -241,14 +238,26 @@ struct WinArgs {
   int CH;         // bins per window
   int64_t B;
   int nw_total;   // ceil(M / CH)
-  int first_w;    // first window handled (1 after the fused kernel did window 0)
   const PropCommon* pc;
   const void* prop;  // PropMixed* or PropF64*
   void* partials;    // [B][nw_total][2 NDET] float (mixed) or double (fp64)
   int* work;         // [0] largest cut, [1 + w] proposal counter of window w
   const int* hist;   // [w] proposals whose last window is w
+  int* pdone;        // [p] windows of proposal p already summed
+  double* lnl;       // [B] output
   int* status;       // latched error bits
 };
+
+// lnL_p = sum_d [Re K_d U_d - Im K_d V_d] - <h|h>/2 (FP64), U_d + i V_d the
+// proposal's data-template sums over all its windows.
+template <int NDET, typename T>
+__device__ __forceinline__ double combine_lnl(const PropCommon* __restrict__ c, const T (&U)[NDET],
+                                              const T (&V)[NDET]) {
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) acc += c->Kr[d] * (double)U[d] - c->Ki[d] * (double)V[d];
+  return acc - 0.5 * c->hh;
+}
 
 template <int NDET, bool MIXED, typename Acc>
 __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __restrict__ smv, int64_t p, int j0,
@@ -334,14 +343,14 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
   const int maxn = a.work[0];
   int nw = (maxn + a.CH - 1) / a.CH;
   if (nw > a.nw_total) nw = a.nw_total;
-  if (nw <= a.first_w) return;  // no proposal has a bin in the windows left to this kernel
+  if (nw < 1) return;  // no proposal has a bin in band
 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
   }
   int n_w = 0;
-  int w = start_window(a.hist, a.first_w, nw, blockIdx.x, gridDim.x, &n_w);
+  int w = start_window(a.hist, 0, nw, blockIdx.x, gridDim.x, &n_w);
 
   uint32_t parity = 0;
   for (; w < nw; ++w) {
@@ -365,6 +374,13 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
         Acc U[NDET], V[NDET];
         window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
+        const int nwp = (ncut + a.CH - 1) / a.CH;
+        if (nwp == 1) {  // the proposal's only window: combine now
+          if (lane == 0) a.lnl[p] = combine_lnl<NDET>(a.pc + p, U, V);
+          return;
+        }
+        // several windows: publish this one; the warp that closes the last one combines
+        int done = 0;
         if (lane == 0) {
           Acc* o = reinterpret_cast<Acc*>(a.partials) + (p * a.nw_total + w) * (2 * NDET);
 #pragma unroll
@@ -372,163 +388,38 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
             o[2 * d] = U[d];
             o[2 * d + 1] = V[d];
           }
+          __threadfence();
+          done = atomicAdd(&a.pdone[p], 1);
         }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done != nwp - 1) return;
+        __threadfence();
+        // lanes take windows lane, lane + 32, ...; a fixed shuffle tree then sums
+        // the lanes (FP64, the same order whichever warp closes the proposal)
+        const Acc* q = reinterpret_cast<const Acc*>(a.partials) + p * a.nw_total * (2 * NDET);
+        double Ud[NDET], Vd[NDET];
+#pragma unroll
+        for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = 0.0;
+        for (int v = lane; v < nwp; v += 32)
+#pragma unroll
+          for (int d = 0; d < NDET; ++d) {
+            Ud[d] += (double)__ldcg(&q[v * (2 * NDET) + 2 * d]);
+            Vd[d] += (double)__ldcg(&q[v * (2 * NDET) + 2 * d + 1]);
+          }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+          for (int d = 0; d < NDET; ++d) {
+            Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
+            Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
+          }
+        if (lane == 0) a.lnl[p] = combine_lnl<NDET>(a.pc + p, Ud, Vd);
       });
     }
     n_w -= __ldcg(&a.hist[w]);
   }
 }
 
-// ---------------------------------------------------------------- fused prologue + window 0
-// Every CTA first produces: it takes groups of 64 rows from an atomic counter
-// and computes their coefficients (two 4-warp sets, one per 32 rows, FP64),
-// then publishes one ready flag per 32 rows.  When no group is left it
-// consumes: it stages window 0 of the table (bulk copy, bounded wait) into the
-// same shared memory and takes proposals in order from a second counter,
-// waiting (bounded spin) until the proposal's rows are published.  The FP64
-// prologue of late groups thus overlaps the FP32 bin loop of early ones.  No
-// consumer waits for rows that no running CTA holds: a group is only taken by
-// a CTA that is executing, and it publishes before it consumes.
-struct FusedArgs {
-  SegInfo s;
-  const double* theta;
-  int64_t B;
-  const void* tab;
-  int row_elems;
-  int CH;
-  int nw_total;
-  PropMixed* pm;
-  PropF64* pf;
-  PropCommon* pc;
-  void* partials;
-  int* work;  // [0] largest cut, [1 + w] window counters (used by the later kernel)
-  int* hist;  // [w] proposals whose last window is w
-  int* fctr;  // [0] group counter, [1] proposal counter, [2 + r] ready flag of rows 32r .. 32r+31
-  int* status;
-};
-
-template <int NDET, bool MIXED>
-__global__ void __launch_bounds__(256, 3) k_fused(FusedArgs a) {
-  using Elem = typename std::conditional<MIXED, float, double>::type;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int sh_group;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int set = warp >> 2, role = warp & 3;
-  ProSmem* psm = reinterpret_cast<ProSmem*>(smem_raw) + set;  // two sets, aliased with the window later
-  const int64_t n_groups = (a.B + 63) / 64;
-  // ---- produce
-  while (true) {
-    if (threadIdx.x == 0) sh_group = atomicAdd(&a.fctr[0], 1);
-    __syncthreads();
-    const int64_t g = sh_group;
-    __syncthreads();
-    if (g >= n_groups) break;
-    const int64_t row0 = g * 64 + set * 32;
-    if (row0 < a.B)
-      prologue_rows<MIXED>(a.s, a.theta, a.B, row0, role, lane, *psm, SetSync{1 + set}, a.pm, a.pf, a.pc, a.work,
-                           a.hist, a.CH);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      atomicExch(&a.fctr[2 + 2 * g], 1);
-      atomicExch(&a.fctr[3 + 2 * g], 1);
-    }
-  }
-  // ---- consume window 0
-  Elem* sm = reinterpret_cast<Elem*>(smem_raw);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  const int j1 = a.CH < a.s.M ? a.CH : (int)a.s.M;
-  if (threadIdx.x == 0) {
-    fence_proxy_async_smem();
-    const uint32_t bytes = (uint32_t)j1 * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_g2s(sm, a.tab, bytes, &bar);
-  }
-  if (!mbar_wait_bounded(&bar, 0, a.status)) return;
-  WinArgs wa;
-  wa.tab = a.tab;
-  wa.row_elems = a.row_elems;
-  wa.M = a.s.M;
-  wa.CH = a.CH;
-  wa.B = a.B;
-  wa.nw_total = a.nw_total;
-  wa.first_w = 0;
-  wa.pc = a.pc;
-  wa.prop = MIXED ? (const void*)a.pm : (const void*)a.pf;
-  wa.partials = a.partials;
-  wa.work = a.work;
-  wa.hist = a.hist;
-  wa.status = a.status;
-  while (true) {
-    int pi = 0;
-    if (lane == 0) {
-      pi = atomicAdd(&a.fctr[1], 1);
-      if (pi < a.B) {  // wait until the proposal's rows are published (bounded)
-        const volatile int* flag = &a.fctr[2 + pi / 32];
-        const long long t0 = clock64();
-        while (*flag == 0) {
-          if (clock64() - t0 > 2000000000LL) {
-            atomicOr(a.status, kStatusTimeout);
-            pi = -1;
-            break;
-          }
-          __nanosleep(256);
-        }
-        __threadfence();
-      }
-    }
-    pi = __shfl_sync(0xffffffffu, pi, 0);
-    if (pi < 0) return;
-    if (pi >= a.B) break;
-    const int64_t p = pi;
-    const int ncut = __ldcg(&a.pc[p].ncut);
-    if (ncut <= 0) continue;
-    Elem U[NDET], V[NDET];
-    window_sums<NDET, MIXED>(wa, sm, p, 0, ncut < j1 ? ncut : j1, lane, U, V);
-    if (lane == 0) {
-      Elem* o = reinterpret_cast<Elem*>(a.partials) + (int64_t)p * a.nw_total * (2 * NDET);
-#pragma unroll
-      for (int d = 0; d < NDET; ++d) {
-        o[2 * d] = U[d];
-        o[2 * d + 1] = V[d];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------- combination
-// lnL_p = sum_d [Re K_d U_d - Im K_d V_d] - <h|h>/2, with U, V summed over the
-// proposal's windows in window order (FP64).
-template <int NDET, typename Acc>
-__global__ void k_finalize(const PropCommon* __restrict__ pc, const Acc* __restrict__ partials, int64_t B, int CH,
-                           int nw_total, double* __restrict__ lnl) {
-  cudaGridDependencySynchronize();
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= B) return;
-  const PropCommon c = pc[p];
-  if (c.flag) {
-    lnl[p] = -INFINITY;
-    return;
-  }
-  const int nwp = (c.ncut + CH - 1) / CH;
-  const Acc* q = partials + (int64_t)p * nw_total * (2 * NDET);
-  double acc = 0.0;
-#pragma unroll
-  for (int d = 0; d < NDET; ++d) {
-    double U = 0.0, V = 0.0;
-    for (int w = 0; w < nwp; ++w) {
-      U += (double)q[w * (2 * NDET) + 2 * d];
-      V += (double)q[w * (2 * NDET) + 2 * d + 1];
-    }
-    acc += c.Kr[d] * U - c.Ki[d] * V;
-  }
-  lnl[p] = acc - 0.5 * c.hh;
-}
 
 // ---------------------------------------------------------------- waveform (FP64)
 __global__ void k_waveform(SegInfo s, const PropF64* __restrict__ pf, const PropCommon* __restrict__ pc,
@@ -581,14 +472,12 @@ static int64_t nw_max(const gwl_ctx* c) {
   return (c->M + CH - 1) / CH;
 }
 // [0] largest cut, [1 + w] proposal counter of window w, [1 + nw_max + w]
-// histogram of last windows, then the fused kernel's group and proposal
-// counters and one ready flag per 32 rows.
-int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + 2 + 2 * ((B + 63) / 64); }
+// histogram of last windows, [1 + 2 nw_max + p] windows of proposal p summed.
+int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + B; }
 int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
-static int* fused_counters(const gwl_ctx* c) { return c->d_work + 1 + 2 * nw_max(c); }
 
 template <int NDET, bool MIXED>
-static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, cudaStream_t st) {
+static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, bool pdl, cudaStream_t st) {
   static size_t smem_set = 0;  // per template instance: raise the dynamic shared-memory limit when it grows
   if (smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(k_window<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -597,62 +486,42 @@ static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t sme
     smem_set = smem;
   }
   ProfScope ps(c, GWL_KERNEL_BINS, st);
-  cudaError_t e = launch_pdl(k_window<NDET, MIXED>, dim3(grid), dim3(256), smem, st, a);
+  cudaError_t e;
+  if (pdl) {
+    e = launch_pdl(k_window<NDET, MIXED>, dim3(grid), dim3(256), smem, st, a);
+  } else {
+    k_window<NDET, MIXED><<<grid, 256, smem, st>>>(a);
+    e = cudaGetLastError();
+  }
   c->launches++;
   return e;
 }
 
-cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int precision, cudaStream_t st);
+// Prologue of rows [0, B) of theta into the coefficient arrays at row offset
+// `off`, with `work` the counter region (zeroed by the caller).
+static cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int64_t off, int precision,
+                                   double* lnl, int* work, cudaStream_t st) {
+  ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
+  const unsigned nb = (unsigned)((B + 31) / 32);
+  int* hist = work + 1 + nw_max(c);
+  const int CH = window_of(c, precision);
+  if (precision == GWL_MIXED)
+    k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm + off, c->d_pf + off, c->d_pc + off, work, hist,
+                                         CH, lnl);
+  else
+    k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm + off, c->d_pf + off, c->d_pc + off, work, hist,
+                                          CH, lnl);
+  c->launches++;
+  return cudaGetLastError();
+}
 
+// The bin loop (which also forms lnL) of rows [off, off + B) of the batch.
 template <int NDET>
-static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
+static cudaError_t launch_bins(gwl_ctx* c, int64_t B, int64_t off, double* lnl, int* work, bool pdl,
+                               cudaStream_t st) {
   const bool mixed = c->opt.precision == GWL_MIXED;
   const int CH = window_of(c, c->opt.precision);
   const int nw_total = (int)((c->M + CH - 1) / CH);
-  const bool fused = c->fused != 0;
-  cudaError_t e = cudaSuccess;
-  if (fused) {
-    e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
-    if (e != cudaSuccess) return e;
-    FusedArgs f;
-    f.s = c->seg;
-    f.theta = theta;
-    f.B = B;
-    f.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
-    f.row_elems = mixed ? c->row_floats : c->row_doubles;
-    f.CH = CH;
-    f.nw_total = nw_total;
-    f.pm = c->d_pm;
-    f.pf = c->d_pf;
-    f.pc = c->d_pc;
-    f.partials = c->d_partials;
-    f.work = c->d_work;
-    f.fctr = fused_counters(c);
-    f.hist = window_hist(c);
-    f.status = c->d_status;
-    size_t smem = (size_t)CH * f.row_elems * (mixed ? sizeof(float) : sizeof(double));
-    if (smem < 2 * sizeof(ProSmem)) smem = 2 * sizeof(ProSmem);
-    static size_t smem_set[2] = {0, 0};
-    if (smem > smem_set[mixed]) {
-      e = mixed ? cudaFuncSetAttribute(k_fused<NDET, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                : cudaFuncSetAttribute(k_fused<NDET, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      smem_set[mixed] = smem;
-    }
-    int64_t want = (B + 7) / 8;
-    int grid = c->num_sms * c->ctas_per_sm;
-    if (want < grid) grid = (int)(want > 0 ? want : 1);
-    {
-      ProfScope ps(c, GWL_KERNEL_BINS, st);
-      if (mixed) k_fused<NDET, true><<<grid, 256, smem, st>>>(f);
-      else k_fused<NDET, false><<<grid, 256, smem, st>>>(f);
-    }
-    c->launches++;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  } else {
-    e = launch_prologue(c, theta, B, c->opt.precision, st);
-    if (e != cudaSuccess) return e;
-  }
   WinArgs a;
   a.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
   a.row_elems = mixed ? c->row_floats : c->row_doubles;
@@ -660,49 +529,32 @@ static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, doub
   a.CH = CH;
   a.B = B;
   a.nw_total = nw_total;
-  a.first_w = fused ? 1 : 0;
-  a.pc = c->d_pc;
-  a.prop = mixed ? (const void*)c->d_pm : (const void*)c->d_pf;
-  a.partials = c->d_partials;
-  a.work = c->d_work;
-  a.hist = window_hist(c);
+  a.pc = c->d_pc + off;
+  a.prop = mixed ? (const void*)(c->d_pm + off) : (const void*)(c->d_pf + off);
+  a.partials = reinterpret_cast<char*>(c->d_partials) +
+               off * nw_total * 2 * NDET * (int64_t)(mixed ? sizeof(float) : sizeof(double));
+  a.work = work;
+  a.hist = work + 1 + nw_max(c);
+  a.pdone = work + 1 + 2 * nw_max(c);
+  a.lnl = lnl;
   a.status = c->d_status;
   const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double));
   // enough CTAs for every warp of a window to find a proposal, at most a full wave
-  int64_t want = ((B + 7) / 8) * (nw_total - a.first_w > 0 ? nw_total - a.first_w : 1);
+  const int64_t want = ((B + 7) / 8) * nw_total;
   int grid = c->num_sms * c->ctas_per_sm;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
-  e = mixed ? run_window<NDET, true>(c, a, grid, smem, st) : run_window<NDET, false>(c, a, grid, smem, st);
-  if (e != cudaSuccess) return e;
-  {
-    ProfScope ps(c, GWL_KERNEL_COMBINE, st);
-    const dim3 g((unsigned)((B + 63) / 64)), b(64);  // small CTAs: the combination is FP64 latency-bound
-    if (mixed)
-      e = launch_pdl(k_finalize<NDET, float>, g, b, 0, st, (const PropCommon*)c->d_pc,
-                     (const float*)c->d_partials, B, CH, nw_total, lnl);
-    else
-      e = launch_pdl(k_finalize<NDET, double>, g, b, 0, st, (const PropCommon*)c->d_pc,
-                     (const double*)c->d_partials, B, CH, nw_total, lnl);
-  }
-  c->launches++;
-  return e;
+  return mixed ? run_window<NDET, true>(c, a, grid, smem, pdl, st) : run_window<NDET, false>(c, a, grid, smem, pdl, st);
 }
 
-cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int precision, cudaStream_t st) {
+// Prologue (per-proposal coefficients, FP64) then the windowed bin loop, which
+// also forms lnL (programmatic dependent launch: its CTAs start while the
+// prologue drains and wait for its results).
+template <int NDET>
+static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
-  if (e != cudaSuccess) return e;
-  {
-    ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
-    const unsigned nb = (unsigned)((B + 31) / 32);
-    if (precision == GWL_MIXED)
-      k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work, window_hist(c),
-                                           window_of(c, precision));
-    else
-      k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc, c->d_work, window_hist(c),
-                                            window_of(c, precision));
-  }
-  c->launches++;
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st);
+  if (e == cudaSuccess) e = launch_bins<NDET>(c, B, 0, lnl, c->d_work, true, st);
+  return e;
 }
 
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
@@ -716,7 +568,8 @@ cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* l
 
 cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st) {
   // the waveform is always produced in FP64
-  cudaError_t e = launch_prologue(c, theta, B, GWL_FP64, st);
+  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
+  if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, GWL_FP64, nullptr, c->d_work, st);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((c->M + 255) / 256), (unsigned)B);
   k_waveform<<<grid, 256, 0, st>>>(c->seg, c->d_pf, c->d_pc, c->d_tab_f64, c->row_doubles, h);

@@ -1,8 +1,7 @@
 // gwl_tune.cu -- the autotuner of the bin-loop launch shape (gwl_autotune).
 //
 // The bin loops are tiled by a window of frequency bins staged in shared
-// memory and a grid sized in CTAs per SM; the likelihood can also run its
-// per-proposal coefficients and first window in one producer/consumer kernel.
+// memory and a grid sized in CTAs per SM.
 // Which shape is fastest depends on the segment length (bins), the detector
 // count (row size) and the batch, so the library times the candidates on the
 // caller's own batch and keeps the fastest.  Only public entry points are
@@ -97,25 +96,22 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
   double best_l = 1e30, best_g = 1e30;
   int tried = 0;
   if (what & GWL_TUNE_LOGLIKE) {
-    for (int fused = 0; fused <= 1 && !rc; ++fused)
-      for (int ctas = 1; ctas <= 4 && !rc; ++ctas)
-        for (int w : windows) {
-          gwl_tuning s = saved;
-          s.window = w;
-          s.ctas_per_sm = ctas;
-          s.fused = fused;
-          if ((rc = gwl_set_tuning(c, &s))) break;
-          double ms = 0.0;
-          rc = time_calls(t, st, [&] { return gwl_loglike(c, theta_dev, B, d_out, stream); }, &ms);
-          if (rc) break;
-          ++tried;
-          if (ms < best_l) {
-            best_l = ms;
-            best.window = w;
-            best.ctas_per_sm = ctas;
-            best.fused = fused;
-          }
+    for (int ctas = 1; ctas <= 4 && !rc; ++ctas)
+      for (int w : windows) {
+        gwl_tuning s = saved;
+        s.window = w;
+        s.ctas_per_sm = ctas;
+        if ((rc = gwl_set_tuning(c, &s))) break;
+        double ms = 0.0;
+        rc = time_calls(t, st, [&] { return gwl_loglike(c, theta_dev, B, d_out, stream); }, &ms);
+        if (rc) break;
+        ++tried;
+        if (ms < best_l) {
+          best_l = ms;
+          best.window = w;
+          best.ctas_per_sm = ctas;
         }
+      }
   }
   if (!rc && (what & GWL_TUNE_GRAD)) {
     for (int w : windows) {

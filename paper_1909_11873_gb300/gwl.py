@@ -62,7 +62,7 @@ class GwlNsResult(C.Structure):
 
 
 class GwlTuning(C.Structure):
-    _fields_ = [("window", C.c_int), ("ctas_per_sm", C.c_int), ("fused", C.c_int), ("grad_window", C.c_int),
+    _fields_ = [("window", C.c_int), ("ctas_per_sm", C.c_int), ("grad_window", C.c_int),
                 ("ms_loglike", C.c_double), ("ms_grad", C.c_double), ("n_tried", C.c_int)]
 
     def as_dict(self):
@@ -259,8 +259,8 @@ class Context:
     def gwl_set_walk(self, kind: int):
         _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
 
-    def gwl_set_tuning(self, window=0, ctas_per_sm=0, fused=-1, grad_window=0):
-        t = GwlTuning(int(window), int(ctas_per_sm), int(fused), int(grad_window), 0.0, 0.0, 0)
+    def gwl_set_tuning(self, window=0, ctas_per_sm=0, grad_window=0):
+        t = GwlTuning(int(window), int(ctas_per_sm), int(grad_window), 0.0, 0.0, 0)
         _check(lib().gwl_set_tuning(self._h, C.byref(t)), "gwl_set_tuning")
 
     def gwl_get_tuning(self) -> dict:

@@ -50,7 +50,6 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--entry", default="loglike", choices=["loglike", "grad"])
     ap.add_argument("--time", action="store_true", help="report device-timed evals/s (L2 flushed between calls)")
-    ap.add_argument("--fused", type=int, default=-1, help="1/0: coefficients and first window fused or not")
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     a = ap.parse_args()
@@ -64,7 +63,7 @@ def main():
     B = a.batch or I.CONFIGS[a.config]["batch"]
     th = torch.from_numpy(I.reduced(I.proposals(ev, B, a.seed), ev.sampling)).cuda()
     ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED if a.precision == "mixed" else gwl.GWL_FP64)
-    ctx.gwl_set_tuning(window=a.window, ctas_per_sm=a.ctas, fused=a.fused)
+    ctx.gwl_set_tuning(window=a.window, ctas_per_sm=a.ctas)
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(th)
     def call():
@@ -77,7 +76,7 @@ def main():
         call()
     torch.cuda.synchronize()
     ctx.gwl_sync()
-    msg = (f"{a.config} {a.precision} {a.entry} B={B} fused={a.fused} window={a.window} ctas={a.ctas} "
+    msg = (f"{a.config} {a.precision} {a.entry} B={B} window={a.window} ctas={a.ctas} "
            f"iters={a.iters} lnL[0]={out[0].item():.6f}")
     if a.time:
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")

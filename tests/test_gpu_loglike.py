@@ -82,13 +82,13 @@ def test_c3_long_segment_sampled(precision):
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("fcut_mode", [0, 1])
 def test_several_windows_and_ragged_tails(precision, fcut_mode):
-    """3001 bins in windows of 992 and 512 bins, 333 proposals (ragged everywhere), with and without fusion."""
+    """3001 bins in windows of 992, 512 and 128 bins, 333 proposals (ragged everywhere)."""
     cfg = dict(n_det=3, T=8.0, f_low=20.0, f_high=395.0, noise=True, source="bbh", batch=333, gmst=0.9)
     ev = custom_event(cfg, 5, fcut_mode=fcut_mode)
     th = I.proposals(ev, 333, 5)
     ref = oracle.loglike(ev, th)
-    for window, fused in ((992, 1), (512, 1), (512, 0), (992, 0)):
-        got = run_gpu(ev, th, precision, window=window, fused=fused)
+    for window, ctas in ((992, 3), (512, 2), (128, 4)):
+        got = run_gpu(ev, th, precision, window=window, ctas_per_sm=ctas)
         assert np.all(np.abs(got - ref) <= tol(precision, ref)), report(got, ref, precision)
 
 
