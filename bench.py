@@ -68,6 +68,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of a replica's proposal batch: every rank evaluates its own proposals."""
+    return SEED + 1000 * rank
+
+
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest replica sets the time)."""
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() \
+            and torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units processed by all replicas per second, over the slowest replica's time per step."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -226,7 +247,7 @@ def run_gwl(args):
     if not os.path.exists(gwl.LIB_PATH):
         build.build()
     ev = device_event(None, None)
-    theta_full = I.proposals(ev, BATCH, SEED + 1000 * rank)
+    theta_full = I.proposals(ev, BATCH, rank_seed(rank))
     theta_np = np.ascontiguousarray(I.reduced(theta_full, ev.sampling))
     theta = torch.from_numpy(theta_np).cuda()
     lnl = torch.empty(BATCH, dtype=torch.float64, device="cuda")
@@ -320,14 +341,8 @@ def run_gwl(args):
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * fclk / 1e12
     achieved = FLOPS_PER_BIN_MIXED * pairs / per_launch_s / 1e12
 
-    ms = torch.tensor([results[gwl.GWL_MIXED]["ms"]], device="cuda")
-    ms64 = torch.tensor([results[gwl.GWL_FP64]["ms"]], device="cuda")
-    mse = torch.tensor([ms_e2e], device="cuda")
-    if world > 1:
-        for t in (ms, ms64, mse):
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, ms64, mse = ms.item(), ms64.item(), mse.item()
-    value = world * BATCH / (ms * 1e-3)
+    ms, ms64, mse = max_over_ranks([results[gwl.GWL_MIXED]["ms"], results[gwl.GWL_FP64]["ms"], ms_e2e], "cuda")
+    value = whole_job_rate(BATCH, world, ms)
 
     out = {
         "metric": METRIC,
@@ -346,9 +361,9 @@ def run_gwl(args):
                    "global_batch": BATCH * world, "bins_per_det": int(ev.M), "n_det": int(ev.n_det),
                    "in_band_pairs_per_batch": int(pairs), "precision": "mixed",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "fp64_path": {"value": world * BATCH / (ms64 * 1e-3), "ms_per_step": ms64, "steps": results[gwl.GWL_FP64]["steps"],
+        "fp64_path": {"value": whole_job_rate(BATCH, world, ms64), "ms_per_step": ms64, "steps": results[gwl.GWL_FP64]["steps"],
                       "speedup_mixed_over_fp64": ms64 / ms},
-        "e2e": {"value": world * BATCH / (mse * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": int(theta_np.nbytes),
+        "e2e": {"value": whole_job_rate(BATCH, world, mse), "unit": "evals/s", "h2d_bytes_per_step": int(theta_np.nbytes),
                 "d2h_bytes_per_step": int(BATCH * 8)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,

@@ -240,7 +240,7 @@ void gwl_multi_destroy(gwl_multi* m);
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
- *   - A batch needs about (272 + 16 n_det ceil(n_bins / window)) bytes per
+ *   - A batch needs about (276 + 16 n_det ceil(n_bins / window)) bytes per
  *     proposal, window being the context's bin window (gwl_tuning.window); a
  *     batch that does not fit returns GWL_ERR_ARG with the sizes in the error
  *     text and launches nothing.

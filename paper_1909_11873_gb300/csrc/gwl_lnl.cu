@@ -249,14 +249,26 @@ struct WinArgs {
 };
 
 // lnL_p = sum_d [Re K_d U_d - Im K_d V_d] - <h|h>/2 (FP64), U_d + i V_d the
-// proposal's data-template sums over all its windows.
+// proposal's data-template sums over all its windows.  Warp-level: lane d
+// (d < NDET) forms detector d's term and a fixed shuffle tree adds them, so
+// the FP64 pipe sees a handful of warp instructions per proposal; the result
+// is valid on lane 0.
 template <int NDET, typename T>
 __device__ __forceinline__ double combine_lnl(const PropCommon* __restrict__ c, const T (&U)[NDET],
-                                              const T (&V)[NDET]) {
-  double acc = 0.0;
+                                              const T (&V)[NDET], int lane) {
+  static_assert(NDET <= 4, "at most four detectors");
+  T u = (T)0, v = (T)0;
 #pragma unroll
-  for (int d = 0; d < NDET; ++d) acc += c->Kr[d] * (double)U[d] - c->Ki[d] * (double)V[d];
-  return acc - 0.5 * c->hh;
+  for (int d = 0; d < NDET; ++d)
+    if (lane == d) {
+      u = U[d];
+      v = V[d];
+    }
+  double t = 0.0;
+  if (lane < NDET) t = c->Kr[lane] * (double)u - c->Ki[lane] * (double)v;
+  t += __shfl_down_sync(0xffffffffu, t, 2);
+  t += __shfl_down_sync(0xffffffffu, t, 1);
+  return t - 0.5 * c->hh;
 }
 
 template <int NDET, bool MIXED, typename Acc>
@@ -376,7 +388,8 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
         window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
         const int nwp = (ncut + a.CH - 1) / a.CH;
         if (nwp == 1) {  // the proposal's only window: combine now
-          if (lane == 0) a.lnl[p] = combine_lnl<NDET>(a.pc + p, U, V);
+          const double l = combine_lnl<NDET>(a.pc + p, U, V, lane);
+          if (lane == 0) a.lnl[p] = l;
           return;
         }
         // several windows: publish this one; the warp that closes the last one combines
@@ -413,7 +426,8 @@ __global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
             Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
             Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
           }
-        if (lane == 0) a.lnl[p] = combine_lnl<NDET>(a.pc + p, Ud, Vd);
+        const double l = combine_lnl<NDET>(a.pc + p, Ud, Vd, lane);
+        if (lane == 0) a.lnl[p] = l;
       });
     }
     n_w -= __ldcg(&a.hist[w]);
