@@ -42,7 +42,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_replicas_max_over_ranks_and_weak_scaling():
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, start_method="spawn",
                            join=True)
