@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
                                                       PropCommon* __restrict__ pc,
                                                       PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
                                                       int* __restrict__ work, int* __restrict__ hist, int CH) {
+  // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
+  cudaTriggerProgrammaticLaunchCompletion();
   using G = typename std::conditional<MIXED, float, double>::type;
   using T = Tan<11, G>;
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,24 +218,28 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
 
 template <int NDET, bool MIXED>
 __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
-  cudaGridDependencySynchronize();
   using Elem = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
   const int lane = threadIdx.x & 31;
-  const int maxn = a.work[0];
-  int nw = (maxn + a.CH - 1) / a.CH;
-  if (nw > a.nw_total) nw = a.nw_total;
-  if (nw < 1) return;
+  // window 0 of the table is copied while the prologue finishes (see k_window)
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
+    const uint32_t bytes = (uint32_t)(a.CH < a.M ? a.CH : a.M) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(sm, tab, bytes, &bar);
   }
-  int n_w = 0;
-  int w = start_window(a.hist, 0, nw, blockIdx.x, gridDim.x, &n_w);
+  bool w0_pending = true;
   uint32_t parity = 0;
+  cudaGridDependencySynchronize();
+  const int maxn = a.work[0];
+  int nw = (maxn + a.CH - 1) / a.CH;
+  if (nw > a.nw_total) nw = a.nw_total;
+  int n_w = 0;
+  int w = nw < 1 ? 0 : start_window(a.hist, 0, nw, blockIdx.x, gridDim.x, &n_w);
   for (; w < nw; ++w) {
     const int j0 = w * a.CH;
     int64_t j1l = (int64_t)j0 + a.CH;
@@ -244,14 +250,22 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
     // every warp is done with the previous window; a window whose proposals are all taken is skipped
     const bool drained = __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
     if (!drained) {
-      if (threadIdx.x == 0) {
-        fence_proxy_async_smem();
-        const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
-        mbar_arrive_expect_tx(&bar, bytes);
-        bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, &bar);
+      if (w0_pending) {
+        if (!mbar_wait_bounded(&bar, parity, a.status)) return;
+        parity ^= 1u;
+        w0_pending = false;
+        if (w != 0) __syncthreads();  // every thread has seen the copy land before the barrier is armed again
       }
-      if (!mbar_wait_bounded(&bar, parity, a.status)) return;
-      parity ^= 1u;
+      if (w != 0) {
+        if (threadIdx.x == 0) {
+          fence_proxy_async_smem();
+          const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+          mbar_arrive_expect_tx(&bar, bytes);
+          bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, &bar);
+        }
+        if (!mbar_wait_bounded(&bar, parity, a.status)) return;
+        parity ^= 1u;
+      }
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
         Elem A[NDET][kAccPerDet];
         grad_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, A);
@@ -266,6 +280,7 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
     }
     n_w -= __ldcg(&a.hist[w]);
   }
+  if (w0_pending) mbar_wait_bounded(&bar, parity, a.status);  // no copy may outlive the CTA
 }
 
 // ---------------------------------------------------------------- combination
