@@ -46,6 +46,9 @@ SEED = 2
 # 27 (phase completion, reduction to [-1/2, 1/2], argument scaling, 4 FMA of
 # the accumulation) -> 112 + 3 * 27 = 193; plus 6 MUFU sin/cos (separate pipe).
 FLOPS_PER_BIN_MIXED = 193
+# The gradient's bin loop adds, per detector, the nine basis-weighted sums
+# W_d,m (real and imaginary: 18 FMA = 36 flop) -> 193 + 3 * 36 = 301.
+FLOPS_PER_BIN_GRAD = 301
 FP32_LANES_PER_SM = 128
 
 
@@ -185,7 +188,14 @@ GRAD_BATCH = 4096
 NS_K, NS_CHAINS, NS_WALK = 250, 250, 20
 
 
-def run_grad(ev, args, flush, stream):
+def in_band_pairs(ev, theta_full):
+    """Sum over proposals of the in-band bin count (the ISCO cut from the proposal's total mass)."""
+    eta = theta_full[:, 1] / (1 + theta_full[:, 1]) ** 2
+    fisco = 1.0 / (6 ** 1.5 * math.pi * theta_full[:, 0] * eta ** -0.6 * 4.925490947e-6)
+    return float(np.searchsorted(ev.freqs, fisco, side="right").sum())
+
+
+def run_grad(ev, args, flush, stream, peak_tflops):
     """grad lnL evals/s on the same data (4096 proposals), device-timed, L2 flushed between steps."""
     import torch
 
@@ -210,10 +220,24 @@ def run_grad(ev, args, flush, stream):
     torch.cuda.synchronize()
     ctx.gwl_sync()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    # the gradient bin loop's own time (library CUDA events on the launch stream)
+    ctx.gwl_profile(True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        ctx.gwl_grad(x, out, g, stream)
+    torch.cuda.synchronize()
+    kms, kn = ctx.gwl_profile_read(gwl.KERNEL_GRAD)
+    ctx.gwl_profile(False)
     ctx.close()
+    pairs = in_band_pairs(ev, th)
+    achieved = FLOPS_PER_BIN_GRAD * pairs / (kms / kn * 1e-3) / 1e12
     return {"value": GRAD_BATCH / (ms * 1e-3), "unit": "grad evals/s", "ms_per_step": ms, "batch": GRAD_BATCH,
             "steps": steps, "precision": "mixed", "workload": "same 3-det 8 s data, 11-D gradient",
-            "grad_window": tuning["grad_window"]}
+            "grad_window": tuning["grad_window"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "kernel": "k_window_grad<3,mixed>",
+                         "flops_per_pair": FLOPS_PER_BIN_GRAD, "pairs_per_launch": int(pairs),
+                         "kernel_ms": kms / kn}}
 
 
 def run_ns(args):
@@ -322,14 +346,8 @@ def run_gwl(args):
 
     # end-to-end with host buffers
     ms_e2e, _, _ = timed(mixed, max(5, args.steps // 2), args.warmup, host=True)
-    grad_res = run_grad(ev, args, flush, stream) if rank == 0 else None
-    ns_res = run_ns(args) if rank == 0 else None
-
     # algorithmic work of one launch: in-band (proposal, bin) pairs (ncut from the prologue's f_ISCO)
-    eta = theta_full[:, 1] / (1 + theta_full[:, 1]) ** 2
-    fisco = 1.0 / (6 ** 1.5 * math.pi * theta_full[:, 0] * eta ** -0.6 * 4.925490947e-6)
-    ncut = np.searchsorted(ev.freqs, fisco, side="right")
-    pairs = float(ncut.sum())
+    pairs = in_band_pairs(ev, theta_full)
     # the bin loop of one call (one launch; it also forms lnL)
     bins_ms, bins_n = prof[gwl.KERNEL_BINS]
     per_launch_s = bins_ms / args.steps * 1e-3
@@ -340,6 +358,8 @@ def run_gwl(args):
     n_sm = _t.cuda.get_device_properties(local).multi_processor_count
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * fclk / 1e12
     achieved = FLOPS_PER_BIN_MIXED * pairs / per_launch_s / 1e12
+    grad_res = run_grad(ev, args, flush, stream, peak_tflops) if rank == 0 else None
+    ns_res = run_ns(args) if rank == 0 else None
 
     ms, ms64, mse = max_over_ranks([results[gwl.GWL_MIXED]["ms"], results[gwl.GWL_FP64]["ms"], ms_e2e], "cuda")
     value = whole_job_rate(BATCH, world, ms)
@@ -384,6 +404,7 @@ def run_gwl(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(theta_full, args.cpu_seconds, use_device_event=ev)
+        out["accuracy"] = out["cpu_baseline"].pop("accuracy")
         out["cpu_baseline"]["ns_wall_s"] = oracle_ns_wall()
     for c in ctxs.values():
         c.close()
@@ -422,7 +443,26 @@ def cpu_baseline(theta_full, seconds, use_device_event=None):
     el = time.perf_counter() - t0
     return {"value": done / el, "unit": "evals/s", "cores": n, "kind": "oracle",
             "sample": f"{done} evaluations = repeated first 1024 proposals of the 8192-proposal batch "
-                      f"(same event, oracle-made injection), {el:.1f} s wall"}
+                      f"(same event, oracle-made injection), {el:.1f} s wall",
+            "accuracy": device_accuracy(ev, sample, oracle.loglike(ev, sample, n_threads=n))}
+
+
+def device_accuracy(ev, theta_full, ref):
+    """max |lnL_device - lnL_oracle| of both device paths on the oracle's own event (bars 1e-6 / 1e-3)."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    x = torch.from_numpy(np.ascontiguousarray(I.reduced(theta_full, ev.sampling))).cuda()
+    out = {"rows": int(theta_full.shape[0]), "max_abs_lnL": float(np.max(np.abs(ref)))}
+    for name, prec in (("fp64", gwl.GWL_FP64), ("mixed", gwl.GWL_MIXED)):
+        ctx = gwl.Context.from_event(ev, prec)
+        got = gwl.loglike(ctx, x).cpu().numpy()
+        ctx.gwl_sync()
+        ctx.close()
+        out[f"{name}_max_abs_err"] = float(np.max(np.abs(got - ref)))
+    out["bars"] = {"fp64": 1e-6, "mixed": 1e-3}
+    return out
 
 
 def oracle_ns_wall():

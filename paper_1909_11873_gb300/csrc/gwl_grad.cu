@@ -32,17 +32,27 @@ struct PropGrad {
 };
 
 // ---------------------------------------------------------------- tangent prologue
+// The sampled directions are split into groups of kTanGroup; thread t takes
+// row t / ngrp and directions [kTanGroup g, kTanGroup g + kTanGroup), g = t % ngrp.
+// Every thread of a row runs the FP64 value path (the FP64 pipe has room for
+// it); the group-0 thread writes the values.  Four tangents per thread keep
+// the code and register footprint small and give each row ngrp threads.
+constexpr int kTanGroup = 4;
+
 template <bool MIXED>
-__global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* __restrict__ theta, int64_t B,
-                                                      PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
-                                                      PropCommon* __restrict__ pc,
-                                                      PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
-                                                      int* __restrict__ work, int* __restrict__ hist, int CH) {
+__global__ void __launch_bounds__(128) k_prologue_grad(SegInfo s, const double* __restrict__ theta, int64_t B,
+                                                       int ngrp, PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
+                                                       PropCommon* __restrict__ pc,
+                                                       PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
+                                                       int* __restrict__ work, int* __restrict__ hist, int CH) {
   // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
   cudaTriggerProgrammaticLaunchCompletion();
   using G = typename std::conditional<MIXED, float, double>::type;
-  using T = Tan<11, G>;
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  using T = Tan<kTanGroup, G>;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p = t / ngrp;
+  const int i0 = (int)(t % ngrp) * kTanGroup;
+  const bool lead = i0 == 0;
   int ncut = 0;
   if (p < B) {
     double th[11];
@@ -55,8 +65,9 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
     }
     T x[11];
 #pragma unroll
-    for (int k = 0; k < 11; ++k) x[k] = tan_const<11, G>(th[k]);
-    for (int i = 0; i < s.n_dim; ++i) x[s.param_map[i]].d[i] = (G)1;
+    for (int k = 0; k < 11; ++k) x[k] = tan_const<kTanGroup, G>(th[k]);
+    for (int j = 0; j < kTanGroup; ++j)
+      if (i0 + j < s.n_dim) x[s.param_map[i0 + j]].d[j] = (G)1;
 
     const PNCoeffs<T> P = pn_coeffs(x[1], x[2], x[3]);
     const Scale<T> S = mass_scale(x[0], P.eta, x[4], s.amp_scale);
@@ -77,14 +88,17 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
 #pragma unroll
     for (int m = 0; m < kNBasis; ++m) {
 #pragma unroll
-      for (int i = 0; i < 11; ++i) g.dc[m][i] = ok ? c[m].d[i] : (G)0;
-      if (MIXED) split_f64(ok ? c[m].v : 0.0, pm[p].ch[m], pm[p].cl[m]);
-      else pf[p].c[m] = ok ? c[m].v : 0.0;
+      for (int j = 0; j < kTanGroup; ++j)
+        if (i0 + j < 11) g.dc[m][i0 + j] = ok ? c[m].d[j] : (G)0;
+      if (lead) {
+        if (MIXED) split_f64(ok ? c[m].v : 0.0, pm[p].ch[m], pm[p].cl[m]);
+        else pf[p].c[m] = ok ? c[m].v : 0.0;
+      }
     }
-    T hh = tan_const<11, G>(0.0);
+    T hh = tan_const<kTanGroup, G>(0.0);
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
-      T tau = tan_const<11, G>(0.0), Kr = tau, Ki = tau;
+      T tau = tan_const<kTanGroup, G>(0.0), Kr = tau, Ki = tau;
       if (d < s.n_det && ok) {
         const double* gd = s.geom + 9 * d;
         tau = delay(x[9], k, gd);
@@ -95,24 +109,28 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
         if (ncut > 0) hh = hh + (S.amp * S.amp) * (Pr * Pr + Pi * Pi) * s.H[(int64_t)d * s.M + ncut - 1];
       }
 #pragma unroll
-      for (int i = 0; i < 11; ++i) {
-        g.dtau[d][i] = tau.d[i];
-        g.dKr[d][i] = Kr.d[i];
-        g.dKi[d][i] = Ki.d[i];
+      for (int j = 0; j < kTanGroup; ++j)
+        if (i0 + j < 11) {
+          g.dtau[d][i0 + j] = tau.d[j];
+          g.dKr[d][i0 + j] = Kr.d[j];
+          g.dKi[d][i0 + j] = Ki.d[j];
+        }
+      if (lead) {
+        if (MIXED) split_f64(tau.v, pm[p].th[d], pm[p].tl[d]);
+        else pf[p].tau[d] = tau.v;
       }
-      if (MIXED) split_f64(tau.v, pm[p].th[d], pm[p].tl[d]);
-      else pf[p].tau[d] = tau.v;
       cm.Kr[d] = Kr.v;
       cm.Ki[d] = Ki.v;
     }
 #pragma unroll
-    for (int i = 0; i < 11; ++i) g.dhh[i] = hh.d[i];
+    for (int j = 0; j < kTanGroup; ++j)
+      if (i0 + j < 11) g.dhh[i0 + j] = hh.d[j];
     cm.hh = hh.v;
     cm.ncut = ncut;
     cm.flag = ok ? 0 : 1;
-    pc[p] = cm;
+    if (lead) pc[p] = cm;
   }
-  hist_last_window(ncut, CH, hist);
+  hist_last_window(lead ? ncut : 0, CH, hist);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) ncut = max(ncut, __shfl_xor_sync(0xffffffffu, ncut, off));
   if ((threadIdx.x & 31) == 0 && ncut > 0) atomicMax(&work[0], ncut);
@@ -291,12 +309,16 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
                                 double* __restrict__ lnl, double* __restrict__ grad) {
   cudaGridDependencySynchronize();
   using G = typename std::conditional<MIXED, float, double>::type;
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // thread per (proposal, sampled direction): the n_dim threads of a proposal
+  // are adjacent, so their loads of its window sums coincide
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p = t / n_dim;
+  const int i = (int)(t % n_dim);
   if (p >= B) return;
   const PropCommon c = pc[p];
   if (c.flag) {
-    lnl[p] = -INFINITY;
-    for (int i = 0; i < n_dim; ++i) grad[p * n_dim + i] = 0.0;
+    if (i == 0) lnl[p] = -INFINITY;
+    grad[p * n_dim + i] = 0.0;
     return;
   }
   const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
@@ -316,13 +338,15 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
 #pragma unroll
     for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)acc[2 + k];
   }
-  double l = -0.5 * c.hh;
+  if (i == 0) {
+    double l = -0.5 * c.hh;
 #pragma unroll
-  for (int d = 0; d < NDET; ++d) l += c.Kr[d] * Z[d][0] - c.Ki[d] * Z[d][1];
-  lnl[p] = l;
+    for (int d = 0; d < NDET; ++d) l += c.Kr[d] * Z[d][0] - c.Ki[d] * Z[d][1];
+    lnl[p] = l;
+  }
   const PropGrad<G>& g = pg[p];
   const G twopi = (G)(2.0 * kPi);
-  for (int i = 0; i < n_dim; ++i) {
+  {
     G acc = (G)(-0.5) * g.dhh[i];
 #pragma unroll
     for (int d = 0; d < NDET; ++d) {
@@ -363,9 +387,12 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
-    k_prologue_grad<MIXED><<<(unsigned)((B + 63) / 64), 64, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pf, c->d_pc,
-                                                                      reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
-                                                                      c->d_work, window_hist(c), CH);
+    const int ngrp = (c->opt.n_dim + kTanGroup - 1) / kTanGroup;
+    const int64_t nt = B * ngrp;
+    k_prologue_grad<MIXED><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->seg, theta, B, ngrp, c->d_pm, c->d_pf,
+                                                                          c->d_pc,
+                                                                          reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
+                                                                          c->d_work, window_hist(c), CH);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -401,7 +428,8 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   }
   {
     ProfScope ps(c, GWL_KERNEL_COMBINE, st);
-    e = launch_pdl(k_finalize_grad<NDET, MIXED>, dim3((unsigned)((B + 63) / 64)), dim3(64), 0, st,
+    const int64_t nt = B * c->opt.n_dim;
+    e = launch_pdl(k_finalize_grad<NDET, MIXED>, dim3((unsigned)((nt + 63) / 64)), dim3(64), 0, st,
                    (const PropCommon*)c->d_pc, (const PropGrad<G>*)c->d_pgrad, (const void*)c->d_gpartials, B, CH,
                    nw_total, c->opt.n_dim, lnl, grad);
     c->launches++;
