@@ -40,7 +40,7 @@ struct PropGrad {
 constexpr int kTanGroup = 4;
 
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_prologue_grad(SegInfo s, const double* __restrict__ theta, int64_t B,
+__global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* __restrict__ theta, int64_t B,
                                                        int ngrp, PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
                                                        PropCommon* __restrict__ pc,
                                                        PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
@@ -325,18 +325,22 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
   const int nwp = (c.ncut + CH - 1) / CH;
   double Z[NDET][2];
   G W[NDET][2 * kNW];
+  // Z (enters lnL) is summed over windows in FP64; the basis-weighted W enter
+  // the gradient in G precision and are summed in it
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    double acc[kAccPerDet];
+    double z0 = 0.0, z1 = 0.0;
 #pragma unroll
-    for (int k = 0; k < kAccPerDet; ++k) acc[k] = 0.0;
-    for (int w = 0; w < nwp; ++w)
+    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)0;
+    for (int w = 0; w < nwp; ++w) {
+      const G* qw = q + w * (kAccPerDet * NDET) + d * kAccPerDet;
+      z0 += (double)qw[0];
+      z1 += (double)qw[1];
 #pragma unroll
-      for (int k = 0; k < kAccPerDet; ++k) acc[k] += (double)q[w * (kAccPerDet * NDET) + d * kAccPerDet + k];
-    Z[d][0] = acc[0];
-    Z[d][1] = acc[1];
-#pragma unroll
-    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)acc[2 + k];
+      for (int k = 0; k < 2 * kNW; ++k) W[d][k] += qw[2 + k];
+    }
+    Z[d][0] = z0;
+    Z[d][1] = z1;
   }
   if (i == 0) {
     double l = -0.5 * c.hh;
@@ -389,7 +393,7 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
     const int ngrp = (c->opt.n_dim + kTanGroup - 1) / kTanGroup;
     const int64_t nt = B * ngrp;
-    k_prologue_grad<MIXED><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->seg, theta, B, ngrp, c->d_pm, c->d_pf,
+    k_prologue_grad<MIXED><<<(unsigned)((nt + 63) / 64), 64, 0, st>>>(c->seg, theta, B, ngrp, c->d_pm, c->d_pf,
                                                                           c->d_pc,
                                                                           reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
                                                                           c->d_work, window_hist(c), CH);
