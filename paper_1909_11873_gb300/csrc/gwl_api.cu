@@ -182,12 +182,16 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     c->df = df;
     c->opt = *opt;
     c->row_floats = gwl::mixed_row_floats(n_det);
+    c->row_delta = gwl::delta_row_floats(n_det);
     c->row_doubles = gwl::f64_row_doubles(n_det);
     c->window = c->grad_window = opt->precision == GWL_MIXED ? 640 : 384;
     if ((e = dev_alloc(c, &c->d_freqs, n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_geom, 9 * n_det)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_H, (int64_t)n_det * n_bins)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_tab_mixed, n_bins * c->row_floats)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_tab_delta, n_bins * c->row_delta)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
+    if ((e = dev_alloc(c, &c->d_anchor, (n_bins + gwl::kAnchor - 1) / gwl::kAnchor * gwl::kAnchorRowFloats)) !=
+        cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_tab_f64, n_bins * c->row_doubles)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = dev_alloc(c, &c->d_status, 4)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
     if ((e = cudaMalloc(&c->d_wscal, 64)) != cudaSuccess) { rc = cuda_fail(e, "alloc"); break; }
@@ -495,8 +499,11 @@ int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
     return fail(GWL_ERR_ARG, "bad tuning value");
   if (t->window % 32 || t->grad_window % 32)
     return fail(GWL_ERR_ARG, "windows must be multiples of 32 bins (got %d/%d)", t->window, t->grad_window);
-  const size_t row = c->opt.precision == GWL_MIXED ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
-  if ((size_t)t->window * row > 200 * 1024 || (size_t)t->grad_window * row > 200 * 1024)
+  // likelihood rows: the delta table (mixed) or the FP64 table; gradient rows: the mixed or FP64 table
+  const bool mixed = c->opt.precision == GWL_MIXED;
+  const size_t row = mixed ? sizeof(float) * c->row_delta : sizeof(double) * c->row_doubles;
+  const size_t grow = mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
+  if ((size_t)t->window * row > 200 * 1024 || (size_t)t->grad_window * grow > 200 * 1024)
     return fail(GWL_ERR_ARG, "window of %d/%d bins exceeds shared memory", t->window, t->grad_window);
   if (t->window) c->window = t->window;
   if (t->grad_window) c->grad_window = t->grad_window;
@@ -562,6 +569,8 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_geom, 9 * c->n_det);
   dev_free(c, c->d_H, (int64_t)c->n_det * c->M);
   dev_free(c, c->d_tab_mixed, c->M * c->row_floats);
+  dev_free(c, c->d_tab_delta, c->M * c->row_delta);
+  dev_free(c, c->d_anchor, (c->M + gwl::kAnchor - 1) / gwl::kAnchor * gwl::kAnchorRowFloats);
   dev_free(c, c->d_tab_f64, c->M * c->row_doubles);
   dev_free(c, c->d_pm, c->prop_cap);
   dev_free(c, c->d_pf, c->prop_cap);

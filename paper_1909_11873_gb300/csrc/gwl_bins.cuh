@@ -120,6 +120,196 @@ __device__ __forceinline__ void bin_mixed(const float (&v)[RowM<NDET>::n], const
   }
 }
 
+// ---------------------------------------------------------------- anchored phase (likelihood, mixed path)
+// For the block of kAnchor bins starting at anchor bin a, the phase is
+//   r_d,j = [S(f_a) + tau_d f_a] + dS_j + tau_d (f_j - f_a),  dS_j = sum_m c_m dB_m(f_j).
+// The anchor term is formed once per block in float-float arithmetic and
+// reduced modulo one cycle.  |dS_j| is at most sum_m |c_m| max|dB_m| over the
+// block (the chirp's duration times the block's width in frequency): where
+// that bound is below kFastBound cycles, dS_j runs in plain FP32 (8 FMA), is
+// reduced exactly (dS - rint dS), and the small anchor and lane-offset terms
+// are added (three roundings of at most 2^-24 cycles plus the FP32 error of
+// dS, at most ~8 2^-24 kFastBound and ~1e-7 cycles rms on the workloads here,
+// about the error of the hardware sine); otherwise dS_j runs in float-float
+// arithmetic like the unanchored phase.  The choice is made per block, so it
+// is uniform over the warp.
+constexpr float kFastBound = 4.0f;
+
+// Anchor term of one block: (S(f_a) + tau_d f_a) mod 1 per detector, from the
+// anchor row (B_m(f_a), f_a as float pairs); returns whether the block may use
+// the FP32 delta.
+template <int NDET>
+__device__ __forceinline__ bool anchor_terms(const float* __restrict__ ra, const float (&ch)[kNBasis],
+                                             const float (&cl)[kNBasis], const float (&th)[NDET],
+                                             const float (&tl)[NDET], float (&an)[NDET]) {
+  float v[kAnchorRowFloats];
+#pragma unroll
+  for (int k = 0; k < kAnchorRowFloats / 4; ++k)
+    *reinterpret_cast<float4*>(&v[4 * k]) = __ldg(reinterpret_cast<const float4*>(ra) + k);
+  float bound = 0.0f;
+#pragma unroll
+  for (int m = 0; m < kNBasis; ++m) bound = fmaf(fabsf(ch[m]), v[18 + m], bound);
+  float s, lo;
+  {
+    float e;
+    two_prod(ch[0], v[0], s, e);
+    lo = __fmaf_rn(cl[0], v[0], __fmaf_rn(ch[0], v[kNBasis], e));
+  }
+#pragma unroll
+  for (int m = 1; m < kNBasis; ++m) {
+    const float bh = v[m], bl = v[kNBasis + m];
+    float p, e, t, q;
+    two_prod(ch[m], bh, p, e);
+    two_sum(s, p, t, q);
+    s = t;
+    lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
+  }
+  const float sf = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);
+  const float fh = v[16], fl = v[17];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    float p, e;
+    two_prod(th[d], fh, p, e);
+    e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
+    const float x = __fadd_rn(__fadd_rn(sf, __fsub_rn(p, nearest_int(p))), e);
+    an[d] = __fsub_rn(x, nearest_int(x));
+  }
+  return bound < kFastBound;
+}
+
+// One bin of the anchored path with an FP32 delta: v = the first part of the
+// delta row (dB_m high parts, G_d), ad[d] = the block's anchor term plus this
+// lane's tau_d (f_j - f_a).
+template <int NDET>
+__device__ __forceinline__ void bin_anchor(const float (&v)[4 * ((kNBasis + 2 * NDET + 3) / 4)],
+                                           const float (&ch)[kNBasis], const float (&ad)[NDET], float (&U)[NDET],
+                                           float (&V)[NDET]) {
+  float ds = __fmul_rn(ch[0], v[0]);
+#pragma unroll
+  for (int m = 1; m < kNBasis; ++m) ds = __fmaf_rn(ch[m], v[m], ds);
+  ds = __fsub_rn(ds, nearest_int(ds));  // exact
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    const float x = __fadd_rn(ds, ad[d]);
+    const float fr = __fsub_rn(x, nearest_int(x));
+    float sn, cs;
+    __sincosf(6.283185307179586f * fr, &sn, &cs);
+    const float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
+    U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
+    V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
+  }
+}
+
+// One bin of the anchored path with a float-float delta: v = the whole delta
+// row, dB_m = (v[m], v[kNBasis + 2 NDET + m]).
+template <int NDET>
+__device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBasis + 2 * NDET + 3) / 4)],
+                                                 const float (&ch)[kNBasis], const float (&cl)[kNBasis],
+                                                 const float (&ad)[NDET], float (&U)[NDET], float (&V)[NDET]) {
+  constexpr int LO = kNBasis + 2 * NDET;
+  float s, lo;
+  {
+    float e;
+    two_prod(ch[0], v[0], s, e);
+    lo = __fmaf_rn(cl[0], v[0], __fmaf_rn(ch[0], v[LO], e));
+  }
+#pragma unroll
+  for (int m = 1; m < kNBasis; ++m) {
+    const float bh = v[m], bl = v[LO + m];
+    float p, e, t, q;
+    two_prod(ch[m], bh, p, e);
+    two_sum(s, p, t, q);
+    s = t;
+    lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
+  }
+  const float ds = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    const float x = __fadd_rn(ds, ad[d]);
+    const float fr = __fsub_rn(x, nearest_int(x));
+    float sn, cs;
+    __sincosf(6.283185307179586f * fr, &sn, &cs);
+    const float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
+    U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
+    V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
+  }
+}
+
+// Window sums U_d + i V_d of one proposal over bins [j0, jend) of a staged
+// window of delta rows (sm, row_elems floats per row; j0 on an anchor), by the
+// anchored phase; the result is per lane (the caller reduces over the warp).
+template <int NDET>
+__device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int row_elems,
+                                              const float* __restrict__ anchor, float df,
+                                              const PropMixed* __restrict__ P, int j0, int jend, int lane,
+                                              float (&U)[NDET], float (&V)[NDET]) {
+  // anchored phase: the window starts on an anchor (windows are multiples of
+  // kAnchor bins); lane l forms the anchor terms of block l of each batch of
+  // 32 blocks and the warp shares them by shuffles
+  constexpr int RX = 4 * ((kNBasis + 2 * NDET + 3) / 4);       // floats the FP32-delta bin reads
+  constexpr int RXF = 4 * ((2 * kNBasis + 2 * NDET + 3) / 4);  // floats the float-float-delta bin reads
+  float ch[kNBasis], cl[kNBasis], th[NDET], tl[NDET];
+#pragma unroll
+  for (int m = 0; m < kNBasis; ++m) {
+    ch[m] = P->ch[m];
+    cl[m] = P->cl[m];
+  }
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    th[d] = P->th[d];
+    tl[d] = P->tl[d];
+  }
+  // tau_d (f_j - f_a) = tau_d lane df (|.| < 1 cycle)
+  float dtl[NDET];
+  const float lane_df = (float)lane * df;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) dtl[d] = __fmul_rn(th[d], lane_df);
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
+  const int nblk = (jend - j0 + kAnchor - 1) / kAnchor;
+  const float* anc0 = anchor + (int64_t)(j0 / kAnchor) * kAnchorRowFloats;
+  for (int b0 = 0; b0 < nblk; b0 += 32) {
+    float an[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) an[d] = 0.0f;
+    bool fast = false;
+    if (b0 + lane < nblk)
+      fast = anchor_terms<NDET>(anc0 + (int64_t)(b0 + lane) * kAnchorRowFloats, ch, cl, th, tl, an);
+    const unsigned fast_mask = __ballot_sync(0xffffffffu, fast);
+    const int nb = nblk - b0 < 32 ? nblk - b0 : 32;
+    for (int it = 0; it < nb; it += 2) {
+      float ad0[NDET], ad1[NDET];
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        ad0[d] = __fadd_rn(__shfl_sync(0xffffffffu, an[d], it), dtl[d]);
+        ad1[d] = __fadd_rn(__shfl_sync(0xffffffffu, an[d], (it + 1) & 31), dtl[d]);
+      }
+      const int j = j0 + (b0 + it) * kAnchor + lane;
+      // two blocks per iteration (independent chains); each block takes the
+      // FP32 or the float-float delta, uniformly over the warp
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (it + h >= nb) break;
+        const int jj = j + h * kAnchor;
+        const float* row = sm + (int64_t)(jj - j0) * row_elems;
+        if ((fast_mask >> (it + h)) & 1u) {
+          if (jj < jend) {
+            float v[RX];
+#pragma unroll
+            for (int k = 0; k < RX / 4; ++k) *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
+            bin_anchor<NDET>(v, ch, h ? ad1 : ad0, U, V);
+          }
+        } else if (jj < jend) {
+          float v[RXF];
+#pragma unroll
+          for (int k = 0; k < RXF / 4; ++k) *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
+          bin_anchor_exact<NDET>(v, ch, cl, h ? ad1 : ad0, U, V);
+        }
+      }
+    }
+  }
+}
+
 template <int NDET>
 __device__ __forceinline__ void phase_f64(const double (&v)[RowD<NDET>::n], const double (&c)[kNBasis],
                                           const double (&tau)[NDET], double (&sn)[NDET], double (&cs)[NDET]) {

@@ -41,6 +41,14 @@ constexpr int kStatusTimeout = 1;
 __host__ __device__ constexpr int odd_units(int units) { return (units % 2) ? units : units + 1; }
 __host__ __device__ constexpr int mixed_row_floats(int ndet) { return 4 * odd_units((18 + 2 * ndet + 3) / 4); }
 __host__ __device__ constexpr int f64_row_doubles(int ndet) { return 2 * odd_units((9 + 2 * ndet + 1) / 2); }
+// Anchored phase (likelihood, mixed path): bins are grouped in blocks of
+// kAnchor; a delta row holds dB_m(f_j) = B_m(f_j) - B_m(f_a) (a = the block's
+// first bin) as a float pair and G_d,j, laid out [dB_hi 0..7][G_d][dB_lo 0..7];
+// an anchor row holds B_m(f_a) and f_a as float pairs and the block's largest
+// |dB_m|: [bh 0..7][bl 0..7][fh, fl][dmax 0..7][pad 2] (seven 16-byte units).
+constexpr int kAnchor = 32;
+__host__ __device__ constexpr int delta_row_floats(int ndet) { return 4 * odd_units((16 + 2 * ndet + 3) / 4); }
+constexpr int kAnchorRowFloats = 28;
 
 // Per-proposal coefficients read warp-uniformly by the bin loop.
 struct alignas(16) PropMixed {

@@ -23,6 +23,9 @@ struct gwl_ctx {
   double* d_geom = nullptr;    // [n_det][9]
   double* d_H = nullptr;       // [n_det][M]
   float* d_tab_mixed = nullptr;  // [M][mixed_row_floats]
+  float* d_tab_delta = nullptr;  // [M][delta_row_floats]: basis deltas from the block anchor, G_d
+  float* d_anchor = nullptr;     // [ceil(M / kAnchor)][kAnchorRowFloats]
+  int row_delta = 0;
   double* d_tab_f64 = nullptr;   // [M][f64_row_doubles]
   int row_floats = 0, row_doubles = 0;
 

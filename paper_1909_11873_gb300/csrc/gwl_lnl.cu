@@ -245,6 +245,8 @@ struct WinArgs {
   void* partials;    // [B][nw_total][2 NDET] float (mixed) or double (fp64)
   int* work;         // [0] largest cut, [1 + w] proposal counter of window w
   const int* hist;   // [w] proposals whose last window is w
+  const float* anchor;  // mixed: anchor rows, one per kAnchor bins
+  float df;          // bin spacing [Hz]
   int* pdone;        // [p] windows of proposal p already summed
   double* lnl;       // [B] output
   int* status;       // latched error bits
@@ -277,35 +279,9 @@ template <int NDET, bool MIXED, typename Acc>
 __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __restrict__ smv, int64_t p, int j0,
                                             int jend, int lane, Acc (&Ud)[NDET], Acc (&Vd)[NDET]) {
   if constexpr (MIXED) {
-    const float* sm = reinterpret_cast<const float*>(smv);
-    const PropMixed* P = reinterpret_cast<const PropMixed*>(a.prop) + p;
-    float ch[kNBasis], cl[kNBasis], th[NDET], tl[NDET];
-#pragma unroll
-    for (int m = 0; m < kNBasis; ++m) {
-      ch[m] = P->ch[m];
-      cl[m] = P->cl[m];
-    }
-#pragma unroll
-    for (int d = 0; d < NDET; ++d) {
-      th[d] = P->th[d];
-      tl[d] = P->tl[d];
-    }
     float U[NDET], V[NDET];
-#pragma unroll
-    for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
-    int j = j0 + lane;
-    for (; j + 32 < jend; j += 64) {
-      float v0[RowM<NDET>::n], v1[RowM<NDET>::n];
-      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v0);
-      load_row<NDET>(sm + (int64_t)(j + 32 - j0) * a.row_elems, v1);
-      bin_mixed<NDET>(v0, ch, cl, th, tl, U, V);
-      bin_mixed<NDET>(v1, ch, cl, th, tl, U, V);
-    }
-    if (j < jend) {
-      float v0[RowM<NDET>::n];
-      load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v0);
-      bin_mixed<NDET>(v0, ch, cl, th, tl, U, V);
-    }
+    anchored_sums<NDET>(reinterpret_cast<const float*>(smv), a.row_elems, a.anchor, a.df,
+                        reinterpret_cast<const PropMixed*>(a.prop) + p, j0, jend, lane, U, V);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -344,7 +320,7 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
 }
 
 template <int NDET, bool MIXED>
-__global__ void __launch_bounds__(256, 3) k_window(WinArgs a) {
+__global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -554,8 +530,10 @@ static cudaError_t launch_bins(gwl_ctx* c, int64_t B, int64_t off, double* lnl, 
   const int CH = window_of(c, c->opt.precision);
   const int nw_total = (int)((c->M + CH - 1) / CH);
   WinArgs a;
-  a.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
-  a.row_elems = mixed ? c->row_floats : c->row_doubles;
+  a.tab = mixed ? (const void*)c->d_tab_delta : (const void*)c->d_tab_f64;
+  a.row_elems = mixed ? c->row_delta : c->row_doubles;
+  a.anchor = c->d_anchor;
+  a.df = (float)c->df;
   a.M = c->M;
   a.CH = CH;
   a.B = B;

@@ -20,7 +20,9 @@ namespace gwl {
 
 struct EvDesc {
   SegInfo seg;
-  const void* tab;     // mixed or FP64 table of this event
+  const void* tab;     // delta table (mixed) or FP64 table of this event
+  const float* anchor; // anchor rows (mixed)
+  float df;
   int row_elems;
   int CH;              // window (bins)
   int nw_total;        // ceil(M / CH)
@@ -172,31 +174,8 @@ __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
 #pragma unroll
       for (int q = 0; q < NDET; ++q) U[q] = V[q] = (Elem)0;
       if constexpr (MIXED) {
-        const PropMixed* P = reinterpret_cast<const PropMixed*>(a.prop) + p;
-        float ch[kNBasis], cl[kNBasis], th[NDET], tl[NDET];
-#pragma unroll
-        for (int m = 0; m < kNBasis; ++m) {
-          ch[m] = P->ch[m];
-          cl[m] = P->cl[m];
-        }
-#pragma unroll
-        for (int q = 0; q < NDET; ++q) {
-          th[q] = P->th[q];
-          tl[q] = P->tl[q];
-        }
-        int j = j0 + lane;
-        for (; j + 32 < jend; j += 64) {
-          float v0[RowM<NDET>::n], v1[RowM<NDET>::n];
-          load_row<NDET>(sm + (int64_t)(j - j0) * d.row_elems, v0);
-          load_row<NDET>(sm + (int64_t)(j + 32 - j0) * d.row_elems, v1);
-          bin_mixed<NDET>(v0, ch, cl, th, tl, U, V);
-          bin_mixed<NDET>(v1, ch, cl, th, tl, U, V);
-        }
-        if (j < jend) {
-          float v0[RowM<NDET>::n];
-          load_row<NDET>(sm + (int64_t)(j - j0) * d.row_elems, v0);
-          bin_mixed<NDET>(v0, ch, cl, th, tl, U, V);
-        }
+        anchored_sums<NDET>(sm, d.row_elems, d.anchor, d.df, reinterpret_cast<const PropMixed*>(a.prop) + p, j0,
+                            jend, lane, U, V);
       } else {
         const PropF64* P = reinterpret_cast<const PropF64*>(a.prop) + p;
         double c[kNBasis], tau[NDET];
@@ -309,8 +288,10 @@ cudaError_t multi_prepare(Multi* m, int64_t n_per) {
     gwl_ctx* c = m->ctxs[e];
     EvDesc& d = m->host_ev[e];
     d.seg = c->seg;
-    d.tab = mixed ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
-    d.row_elems = mixed ? c->row_floats : c->row_doubles;
+    d.tab = mixed ? (const void*)c->d_tab_delta : (const void*)c->d_tab_f64;
+    d.anchor = c->d_anchor;
+    d.df = (float)c->df;
+    d.row_elems = mixed ? c->row_delta : c->row_doubles;
     int CH = c->window;
     if (CH > c->M) CH = (int)c->M;
     d.CH = CH;

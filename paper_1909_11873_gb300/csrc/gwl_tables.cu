@@ -7,20 +7,17 @@
 // so that, with r_d,j = sum_m c_m B_m(f_j) + tau_d f_j in cycles,
 //   <d|h>_d = Re[K_d sum_j G_d,j e^{-2 pi i r_d,j}],   <h|h>_d = |K_d|^2 H_d[ncut - 1]
 // (Eq. 2 of the paper, split into a data-dependent and a template-dependent part).
+// The mixed likelihood also gets a delta table, dB_m(f_j) = B_m(f_j) - B_m(f_a)
+// with a = kAnchor floor(j / kAnchor) (FP64 difference, as a float pair), and
+// an anchor table with B_m(f_a) and f_a as float pairs and the largest |dB_m|
+// of the block (the last bin's: every B_m is monotonic in f for f > 1 Hz).
 #include "gwl_internal.h"
 
 namespace gwl {
 
-__global__ void k_table_rows(const double* __restrict__ freqs, const double* __restrict__ strain,
-                             const double* __restrict__ psd, int64_t M, int n_det, double df, double t_ref,
-                             float* __restrict__ tab_m, int row_f, double* __restrict__ tab_d, int row_d,
-                             double* __restrict__ hterm) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  const double f = freqs[j];
+__device__ __forceinline__ void basis_values(double f, double (&b)[kNBasis]) {
   const double c1 = cbrt(f);
   const double lf = log(f);
-  double b[kNBasis];
   b[0] = 1.0 / (f * c1 * c1);
   b[1] = 1.0 / f;
   b[2] = 1.0 / (c1 * c1);
@@ -29,6 +26,37 @@ __global__ void k_table_rows(const double* __restrict__ freqs, const double* __r
   b[5] = c1;
   b[6] = c1 * lf;
   b[7] = c1 * c1;
+}
+
+__global__ void k_table_rows(const double* __restrict__ freqs, const double* __restrict__ strain,
+                             const double* __restrict__ psd, int64_t M, int n_det, double df, double t_ref,
+                             float* __restrict__ tab_m, int row_f, double* __restrict__ tab_d, int row_d,
+                             float* __restrict__ tab_x, int row_x, float* __restrict__ anc,
+                             double* __restrict__ hterm) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double f = freqs[j];
+  double b[kNBasis], ba[kNBasis];
+  basis_values(f, b);
+  const int64_t ja = j - j % kAnchor;
+  basis_values(freqs[ja], ba);
+  float* rx = tab_x + j * row_x;
+  const int lo_off = kNBasis + 2 * n_det;  // low parts after G
+  for (int k = lo_off + kNBasis; k < row_x; ++k) rx[k] = 0.0f;
+#pragma unroll
+  for (int m = 0; m < kNBasis; ++m) split_f64(b[m] - ba[m], rx[m], rx[lo_off + m]);
+  if (j == ja) {
+    float* ra = anc + (j / kAnchor) * kAnchorRowFloats;
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) split_f64(b[m], ra[m], ra[kNBasis + m]);
+    split_f64(f, ra[16], ra[17]);
+    const int64_t jl = (j + kAnchor - 1 < M ? j + kAnchor - 1 : M - 1);
+    double bl[kNBasis];
+    basis_values(freqs[jl], bl);
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) ra[18 + m] = (float)fabs(bl[m] - b[m]) * 1.0000001f;
+    ra[26] = ra[27] = 0.0f;
+  }
   float* rm = tab_m + j * row_f;
   double* rd = tab_d + j * row_d;
 #pragma unroll
@@ -61,6 +89,8 @@ __global__ void k_table_rows(const double* __restrict__ freqs, const double* __r
     rd[10 + 2 * d] = gi;
     rm[18 + 2 * d] = (float)gr;
     rm[19 + 2 * d] = (float)gi;
+    rx[kNBasis + 2 * d] = (float)gr;
+    rx[kNBasis + 2 * d + 1] = (float)gi;
     hterm[(int64_t)d * M + j] = 4.0 * df * f76 * f76 / S;
   }
   for (int k = 18 + 2 * n_det; k < row_f; ++k) rm[k] = 0.0f;
@@ -99,7 +129,8 @@ __global__ void k_prefix_scan(double* __restrict__ H, int64_t M) {
 
 // Multiply the data weights by 2^-e and the prefix sums by 2^-2e (exact).
 __global__ void k_scale_tables(int64_t M, int n_det, double sg, float* __restrict__ tab_m, int row_f,
-                               double* __restrict__ tab_d, int row_d, double* __restrict__ H) {
+                               double* __restrict__ tab_d, int row_d, float* __restrict__ tab_x, int row_x,
+                               double* __restrict__ H) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   for (int d = 0; d < n_det; ++d) {
@@ -107,6 +138,8 @@ __global__ void k_scale_tables(int64_t M, int n_det, double sg, float* __restric
     tab_d[j * row_d + 10 + 2 * d] *= sg;
     tab_m[j * row_f + 18 + 2 * d] = (float)tab_d[j * row_d + 9 + 2 * d];
     tab_m[j * row_f + 19 + 2 * d] = (float)tab_d[j * row_d + 10 + 2 * d];
+    tab_x[j * row_x + kNBasis + 2 * d] = tab_m[j * row_f + 18 + 2 * d];
+    tab_x[j * row_x + kNBasis + 2 * d + 1] = tab_m[j * row_f + 19 + 2 * d];
     H[(int64_t)d * M + j] *= sg * sg;
   }
 }
@@ -114,7 +147,8 @@ __global__ void k_scale_tables(int64_t M, int n_det, double sg, float* __restric
 cudaError_t launch_scale_tables(gwl_ctx* c, double sg, cudaStream_t st) {
   const int T = 256;
   k_scale_tables<<<(unsigned)((c->M + T - 1) / T), T, 0, st>>>(c->M, c->n_det, sg, c->d_tab_mixed, c->row_floats,
-                                                                c->d_tab_f64, c->row_doubles, c->d_H);
+                                                                c->d_tab_f64, c->row_doubles, c->d_tab_delta,
+                                                                c->row_delta, c->d_H);
   c->launches++;
   return cudaGetLastError();
 }
@@ -123,7 +157,8 @@ cudaError_t launch_build_tables(gwl_ctx* c, const double* d_strain, const double
   const int T = 256;
   const int64_t nb = (c->M + T - 1) / T;
   k_table_rows<<<(unsigned)nb, T, 0, st>>>(c->d_freqs, d_strain, d_psd, c->M, c->n_det, c->df, c->opt.t_ref,
-                                            c->d_tab_mixed, c->row_floats, c->d_tab_f64, c->row_doubles, c->d_H);
+                                            c->d_tab_mixed, c->row_floats, c->d_tab_f64, c->row_doubles,
+                                            c->d_tab_delta, c->row_delta, c->d_anchor, c->d_H);
   c->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

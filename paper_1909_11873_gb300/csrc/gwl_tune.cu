@@ -66,21 +66,28 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
   if (rc) return rc;
   saved.ms_loglike = saved.ms_grad = 0.0;
 
-  const size_t row = c->opt.precision == GWL_MIXED ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
-  std::vector<int> windows;
-  for (int w = 128; w <= 1536; w += 64) {
-    if ((size_t)w * row > 200 * 1024) break;
-    // windows at least as long as the segment are all the same shape
-    if (w >= c->M) {
-      windows.push_back(w);
-      break;
+  // candidate windows for a row size (bytes): multiples of 64 bins that fit in
+  // shared memory, at most the segment, partial sums within 2 GB
+  auto candidates = [&](size_t row) {
+    std::vector<int> ws;
+    for (int w = 128; w <= 1536; w += 64) {
+      if ((size_t)w * row > 200 * 1024) break;
+      if (w >= c->M) {  // windows at least as long as the segment are all the same shape
+        ws.push_back(w);
+        break;
+      }
+      const int64_t nw = (c->M + w - 1) / w;
+      if (B * nw * 2 * c->n_det * (int64_t)sizeof(double) > ((int64_t)2 << 30)) continue;
+      ws.push_back(w);
     }
-    // keep the per-window partial sums within 2 GB
-    const int64_t nw = (c->M + w - 1) / w;
-    if (B * nw * 2 * c->n_det * (int64_t)sizeof(double) > ((int64_t)2 << 30)) continue;
-    windows.push_back(w);
-  }
-  if (windows.empty()) return gwl::set_error(GWL_ERR_ARG, "autotune: no window fits");
+    return ws;
+  };
+  const bool mixed = c->opt.precision == GWL_MIXED;
+  const std::vector<int> windows =
+      candidates(mixed ? sizeof(float) * c->row_delta : sizeof(double) * c->row_doubles);
+  const std::vector<int> gwindows =
+      candidates(mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles);
+  if (windows.empty() || gwindows.empty()) return gwl::set_error(GWL_ERR_ARG, "autotune: no window fits");
 
   double* d_out = nullptr;
   const int64_t n_out = B * (1 + c->opt.n_dim);
@@ -114,7 +121,7 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
       }
   }
   if (!rc && (what & GWL_TUNE_GRAD)) {
-    for (int w : windows) {
+    for (int w : gwindows) {
       gwl_tuning s = saved;
       s.grad_window = w;
       if ((rc = gwl_set_tuning(c, &s))) break;
