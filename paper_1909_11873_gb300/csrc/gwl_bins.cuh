@@ -133,7 +133,7 @@ __device__ __forceinline__ void bin_mixed(const float (&v)[RowM<NDET>::n], const
 // about the error of the hardware sine); otherwise dS_j runs in float-float
 // arithmetic like the unanchored phase.  The choice is made per block, so it
 // is uniform over the warp.
-constexpr float kFastBound = 4.0f;
+constexpr float kFastBound = 16.0f;
 
 // Anchor term of one block: (S(f_a) + tau_d f_a) mod 1 per detector, from the
 // anchor row (B_m(f_a), f_a as float pairs); returns whether the block may use
