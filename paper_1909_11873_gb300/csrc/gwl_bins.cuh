@@ -145,7 +145,7 @@ __device__ __forceinline__ bool anchor_terms(const float* __restrict__ ra, const
   float v[kAnchorRowFloats];
 #pragma unroll
   for (int k = 0; k < kAnchorRowFloats / 4; ++k)
-    *reinterpret_cast<float4*>(&v[4 * k]) = __ldg(reinterpret_cast<const float4*>(ra) + k);
+    *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(ra)[k];
   float bound = 0.0f;
 #pragma unroll
   for (int m = 0; m < kNBasis; ++m) bound = fmaf(fabsf(ch[m]), v[18 + m], bound);
@@ -237,10 +237,11 @@ __device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBa
 
 // Window sums U_d + i V_d of one proposal over bins [j0, jend) of a staged
 // window of delta rows (sm, row_elems floats per row; j0 on an anchor), by the
-// anchored phase; the result is per lane (the caller reduces over the warp).
+// anchored phase; anc0 = the anchor row of bin j0 (shared or global memory).
+// The result is per lane (the caller reduces over the warp).
 template <int NDET>
 __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int row_elems,
-                                              const float* __restrict__ anchor, float df,
+                                              const float* __restrict__ anc0, float df,
                                               const PropMixed* __restrict__ P, int j0, int jend, int lane,
                                               float (&U)[NDET], float (&V)[NDET]) {
   // anchored phase: the window starts on an anchor (windows are multiples of
@@ -267,7 +268,6 @@ __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int 
 #pragma unroll
   for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
   const int nblk = (jend - j0 + kAnchor - 1) / kAnchor;
-  const float* anc0 = anchor + (int64_t)(j0 / kAnchor) * kAnchorRowFloats;
   for (int b0 = 0; b0 < nblk; b0 += 32) {
     float an[NDET];
 #pragma unroll
@@ -285,8 +285,24 @@ __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int 
         ad1[d] = __fadd_rn(__shfl_sync(0xffffffffu, an[d], (it + 1) & 31), dtl[d]);
       }
       const int j = j0 + (b0 + it) * kAnchor + lane;
-      // two blocks per iteration (independent chains); each block takes the
-      // FP32 or the float-float delta, uniformly over the warp
+      const int jb = j - lane;  // first bin of block it
+      if (it + 1 < nb && ((fast_mask >> it) & 3u) == 3u && jb + 2 * kAnchor <= jend) {
+        // the common case, two complete blocks with FP32 deltas: straight-line
+        // code so that the two bins' chains interleave
+        float v0[RX], v1[RX];
+        const float* r0 = sm + (int64_t)(j - j0) * row_elems;
+        const float* r1 = r0 + (int64_t)kAnchor * row_elems;
+#pragma unroll
+        for (int k = 0; k < RX / 4; ++k) {
+          *reinterpret_cast<float4*>(&v0[4 * k]) = reinterpret_cast<const float4*>(r0)[k];
+          *reinterpret_cast<float4*>(&v1[4 * k]) = reinterpret_cast<const float4*>(r1)[k];
+        }
+        bin_anchor<NDET>(v0, ch, ad0, U, V);
+        bin_anchor<NDET>(v1, ch, ad1, U, V);
+        continue;
+      }
+      // otherwise block by block: each takes the FP32 or the float-float delta,
+      // uniformly over the warp, and lanes past the cut sit out
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (it + h >= nb) break;

@@ -280,7 +280,9 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
                                             int jend, int lane, Acc (&Ud)[NDET], Acc (&Vd)[NDET]) {
   if constexpr (MIXED) {
     float U[NDET], V[NDET];
-    anchored_sums<NDET>(reinterpret_cast<const float*>(smv), a.row_elems, a.anchor, a.df,
+    // the window's anchor rows follow its delta rows in shared memory
+    const float* sa = reinterpret_cast<const float*>(smv) + (int64_t)a.CH * a.row_elems;
+    anchored_sums<NDET>(reinterpret_cast<const float*>(smv), a.row_elems, sa, a.df,
                         reinterpret_cast<const PropMixed*>(a.prop) + p, j0, jend, lane, U, V);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -319,13 +321,33 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
   }
 }
 
+// One thread: copy bins [j0, j1) of the table into shared memory (bulk copy
+// completing on bar); in the mixed path the window's anchor rows follow the
+// delta rows (after CH rows).
+template <bool MIXED>
+__device__ __forceinline__ void stage_window(const WinArgs& a, void* sm, int j0, int j1, uint64_t* bar) {
+  using Elem = typename std::conditional<MIXED, float, double>::type;
+  const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
+  const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+  if constexpr (MIXED) {
+    const int a0 = j0 / kAnchor, a1 = (j1 + kAnchor - 1) / kAnchor;
+    const uint32_t abytes = (uint32_t)(a1 - a0) * (uint32_t)(kAnchorRowFloats * sizeof(float));
+    mbar_arrive_expect_tx(bar, bytes + abytes);
+    bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
+    bulk_g2s(reinterpret_cast<float*>(sm) + (int64_t)a.CH * a.row_elems, a.anchor + (int64_t)a0 * kAnchorRowFloats,
+             abytes, bar);
+  } else {
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
+  }
+}
+
 template <int NDET, bool MIXED>
 __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
-  const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
   const int lane = threadIdx.x & 31;
   using Acc = Elem;  // per-window partial sums: FP32 (mixed) or FP64
 
@@ -335,9 +357,7 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
-    const uint32_t bytes = (uint32_t)(a.CH < a.M ? a.CH : a.M) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_g2s(sm, tab, bytes, &bar);
+    stage_window<MIXED>(a, sm, 0, a.CH < a.M ? (int)a.CH : (int)a.M, &bar);
   }
   bool w0_pending = true;  // the copy of window 0 (phase 0 of the barrier) is in flight
   uint32_t parity = 0;
@@ -368,9 +388,7 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
       if (w != 0) {
         if (threadIdx.x == 0) {
           fence_proxy_async_smem();
-          const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
-          mbar_arrive_expect_tx(&bar, bytes);
-          bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, &bar);
+          stage_window<MIXED>(a, sm, j0, j1, &bar);
         }
         if (!mbar_wait_bounded(&bar, parity, a.status)) return;
         parity ^= 1u;
@@ -547,7 +565,8 @@ static cudaError_t launch_bins(gwl_ctx* c, int64_t B, int64_t off, double* lnl, 
   a.pdone = work + 1 + 2 * nw_max(c);
   a.lnl = lnl;
   a.status = c->d_status;
-  const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double));
+  const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double)) +
+                      (mixed ? (size_t)((CH + kAnchor - 1) / kAnchor) * kAnchorRowFloats * sizeof(float) : 0);
   // enough CTAs for every warp of a window to find a proposal, at most a full wave
   const int64_t want = ((B + 7) / 8) * nw_total;
   int grid = c->num_sms * c->ctas_per_sm;

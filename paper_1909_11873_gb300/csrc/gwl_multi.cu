@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
 #pragma unroll
       for (int q = 0; q < NDET; ++q) U[q] = V[q] = (Elem)0;
       if constexpr (MIXED) {
-        anchored_sums<NDET>(sm, d.row_elems, d.anchor, d.df, reinterpret_cast<const PropMixed*>(a.prop) + p, j0,
-                            jend, lane, U, V);
+        anchored_sums<NDET>(sm, d.row_elems, d.anchor + (int64_t)(j0 / kAnchor) * kAnchorRowFloats, d.df,
+                            reinterpret_cast<const PropMixed*>(a.prop) + p, j0, jend, lane, U, V);
       } else {
         const PropF64* P = reinterpret_cast<const PropF64*>(a.prop) + p;
         double c[kNBasis], tau[NDET];
