@@ -321,6 +321,35 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
   }
 }
 
+// Proposals whose only window a CTA has summed wait in shared memory and are
+// combined by all the CTA's threads together at the next window boundary: an
+// FP64 warp instruction costs the pipe the same whether one lane or 32 are
+// active, so one proposal per lane keeps the FP64 work off the bin loop.
+template <int NDET, typename Acc>
+struct Pending {
+  int64_t p;
+  Acc U[NDET], V[NDET];
+};
+constexpr int kPendCap = 128;
+
+// All threads of the CTA, after a CTA barrier: lnL of the waiting proposals.
+template <int NDET, typename Acc>
+__device__ __forceinline__ void flush_pending(const Pending<NDET, Acc>* pend, int* npend,
+                                              const PropCommon* __restrict__ pc, double* __restrict__ lnl) {
+  const int n = *npend < kPendCap ? *npend : kPendCap;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const Pending<NDET, Acc>& q = pend[e];
+    const PropCommon* c = pc + q.p;
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) acc += c->Kr[d] * (double)q.U[d] - c->Ki[d] * (double)q.V[d];
+    lnl[q.p] = acc - 0.5 * c->hh;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *npend = 0;
+  __syncthreads();
+}
+
 // One thread: copy bins [j0, j1) of the table into shared memory (bulk copy
 // completing on bar); in the mixed path the window's anchor rows follow the
 // delta rows (after CH rows).
@@ -350,11 +379,14 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const int lane = threadIdx.x & 31;
   using Acc = Elem;  // per-window partial sums: FP32 (mixed) or FP64
+  __shared__ Pending<NDET, Acc> s_pend[kPendCap];
+  __shared__ int s_npend;
 
   // Window 0 of the table does not depend on the prologue: its copy starts
   // before the wait (the prologue lets this grid launch early), and most CTAs
   // start there.  A CTA that starts elsewhere retires the copy first.
   if (threadIdx.x == 0) {
+    s_npend = 0;
     mbar_init(&bar, 1);
     fence_mbar_init();
     stage_window<MIXED>(a, sm, 0, a.CH < a.M ? (int)a.CH : (int)a.M, &bar);
@@ -378,6 +410,7 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
     int* ctr = a.work + 1 + w;
     // every warp is done with the previous window; a window whose proposals are all taken is skipped
     const bool drained = __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
+    if (s_npend > 0) flush_pending<NDET, Acc>(s_pend, &s_npend, a.pc, a.lnl);
     if (!drained) {
       if (w0_pending) {  // window 0's copy: use it, or let it land before staging another window
         if (!mbar_wait_bounded(&bar, parity, a.status)) return;
@@ -397,9 +430,23 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
         Acc U[NDET], V[NDET];
         window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
         const int nwp = (ncut + a.CH - 1) / a.CH;
-        if (nwp == 1) {  // the proposal's only window: combine now
-          const double l = combine_lnl<NDET>(a.pc + p, U, V, lane);
-          if (lane == 0) a.lnl[p] = l;
+        if (nwp == 1) {  // the proposal's only window: queue it for the CTA's next combination
+          int slot = 0;
+          if (lane == 0) slot = atomicAdd(&s_npend, 1);
+          slot = __shfl_sync(0xffffffffu, slot, 0);
+          if (slot < kPendCap) {
+            if (lane == 0) {
+              s_pend[slot].p = p;
+#pragma unroll
+              for (int d = 0; d < NDET; ++d) {
+                s_pend[slot].U[d] = U[d];
+                s_pend[slot].V[d] = V[d];
+              }
+            }
+          } else {  // queue full: combine here
+            const double l = combine_lnl<NDET>(a.pc + p, U, V, lane);
+            if (lane == 0) a.lnl[p] = l;
+          }
           return;
         }
         // several windows: publish this one; the warp that closes the last one combines
@@ -442,6 +489,8 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
     }
     n_w -= __ldcg(&a.hist[w]);
   }
+  __syncthreads();
+  if (s_npend > 0) flush_pending<NDET, Acc>(s_pend, &s_npend, a.pc, a.lnl);
   if (w0_pending) mbar_wait_bounded(&bar, parity, a.status);  // no copy may outlive the CTA
 }
 
