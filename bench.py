@@ -41,14 +41,16 @@ METRIC = "lnL evals/s (BBH 3-det 8s, 11-D)"
 CONFIG = "c2"
 BATCH = 8192
 SEED = 2
-# Algorithmic FP32 operations per in-band (proposal, bin) of the mixed path
-# with 3 detectors (flops, FMA = 2): float-float common phase 112, per detector
-# 27 (phase completion, reduction to [-1/2, 1/2], argument scaling, 4 FMA of
-# the accumulation) -> 112 + 3 * 27 = 193; plus 6 MUFU sin/cos (separate pipe).
-FLOPS_PER_BIN_MIXED = 193
-# The gradient's bin loop adds, per detector, the nine basis-weighted sums
-# W_d,m (real and imaginary: 18 FMA = 36 flop) -> 193 + 3 * 36 = 301.
-FLOPS_PER_BIN_GRAD = 301
+# Algorithmic work per in-band (proposal, bin) pair with 3 detectors (flops,
+# FMA = 2), counted from what the method must compute, not from the kernel's
+# instructions: the phase, 9 basis terms (9 FMA = 18 flop) and per detector
+# the delay term, nearest integer and subtraction (3 x 4 = 12 flop); the
+# inner-product accumulation, 4 FMA per detector (24 flop), and its
+# compensation (24 flop) -> 78 flop, plus 6 sine/cosine (MUFU, separate pipe).
+FLOPS_PER_BIN_MIXED = 78
+# The gradient adds per bin the combination of the three detectors' terms
+# (3 x 4 FMA) and the basis-weighted sums (10 FMA): 22 FMA = 44 flop -> 122.
+FLOPS_PER_BIN_GRAD = 122
 FP32_LANES_PER_SM = 128
 
 
