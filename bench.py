@@ -52,6 +52,10 @@ FLOPS_PER_BIN_MIXED = 78
 # (3 x 4 FMA) and the basis-weighted sums (10 FMA): 22 FMA = 44 flop -> 122.
 FLOPS_PER_BIN_GRAD = 122
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one bin-loop launch on this workload, from the
+# ncu capture summarised in profiles/k_window_mixed_c2.md; None whenever the
+# kernel has changed since that capture.
+KWINDOW_DRAM_BYTES = 1581824 + 256
 
 
 def parse():
@@ -63,6 +67,9 @@ def parse():
     ap.add_argument("--impl", default="gwl", choices=["gwl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--shape", default="",
+                    help="W,C: fixed likelihood launch shape (window bins, CTAs per SM) instead of the autotuner; "
+                         "for profiler runs, whose timing would mislead the autotuner")
     return ap.parse_args()
 
 
@@ -327,8 +334,14 @@ def run_gwl(args):
     for prec in (gwl.GWL_FP64, gwl.GWL_MIXED):
         ctx = gwl.Context.from_event(ev, prec)
         ctxs[prec] = ctx
-        # launch shape from the library's autotuner on this batch (untimed)
-        tuning["mixed" if prec == gwl.GWL_MIXED else "fp64"] = ctx.gwl_autotune(theta, gwl.GWL_TUNE_LOGLIKE, stream)
+        # launch shape from the library's autotuner on this batch (untimed), or fixed by --shape
+        if args.shape and prec == gwl.GWL_MIXED:
+            w, c = (int(v) for v in args.shape.split(","))
+            ctx.gwl_set_tuning(window=w, ctas_per_sm=c)
+            tuning["mixed"] = dict(ctx.gwl_get_tuning(), fixed=True)
+        else:
+            tuning["mixed" if prec == gwl.GWL_MIXED else "fp64"] = ctx.gwl_autotune(theta, gwl.GWL_TUNE_LOGLIKE,
+                                                                                    stream)
         steps = args.steps if prec == gwl.GWL_MIXED else max(3, args.steps // 5)
         with ClockSampler(local) as clk:
             ms, launches, wall = timed(ctx, steps, args.warmup, soak=args.soak_seconds,
@@ -388,7 +401,9 @@ def run_gwl(args):
         "e2e": {"value": whole_job_rate(BATCH, world, mse), "unit": "evals/s", "h2d_bytes_per_step": int(theta_np.nbytes),
                 "d2h_bytes_per_step": int(BATCH * 8)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops, "traffic": KWINDOW_DRAM_BYTES,
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_window<3,mixed> "
+                                      "launch (640-bin windows, 2 CTAs/SM; profiles/k_window_mixed_c2.md)",
                      "kernel": "k_window<3,mixed> (windowed bin loop and lnL combination)",
                      "peak_basis": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 flop x {fclk / 1e6:.0f} MHz (derived)",
                      "flops_per_pair": FLOPS_PER_BIN_MIXED, "pairs_per_launch": int(pairs),
