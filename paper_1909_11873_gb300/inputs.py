@@ -229,6 +229,34 @@ def make_event(name: str, seed: int, waveform: WaveformFn, snr2: Snr2Fn, cfg: di
     return ev.with_strain(n + h)
 
 
+# Probability-probability (PP) coverage test: a fixed 4-D prior (Mc, q, tc,
+# phic), injections drawn from it, the other parameters fixed; c2's network,
+# segment and noise recipe.  Chosen so that the posterior is unimodal and the
+# sampled prior is exactly the one the injections come from.
+PP_FIXED = np.array([30.0, 0.7, 0.0, 0.0, 800.0, 0.4, 0.3, 2.7, 0.2, 0.0, 1.0])
+PP_LO = np.array([25.0, 0.4, -0.05, 0.0])
+PP_HI = np.array([35.0, 1.0, 0.05, 2.0 * math.pi])
+
+
+def sampling_pp() -> Sampling:
+    return Sampling(np.array([IDX["mc"], IDX["q"], IDX["tc"], IDX["phic"]], dtype=np.int32), PP_FIXED.copy(),
+                    np.zeros(4, dtype=np.int32), PP_LO.copy(), PP_HI.copy(), np.array([0, 0, 0, 1], dtype=np.int32))
+
+
+def make_pp_event(seed: int, waveform: WaveformFn) -> Event:
+    """One PP injection: (Mc, q, tc, phic) drawn from the PP prior, c2's network, coloured noise."""
+    cfg = dict(CONFIGS["c2"])
+    rng = np.random.default_rng(10_000 + seed)
+    freqs = grid(cfg["T"], cfg["f_low"], cfg["f_high"])
+    psd = np.tile(psd_aligo(freqs), (3, 1))
+    geom = np.stack([site_geometry(*SITES[s]) for s in ("H", "L", "V")])
+    th = PP_FIXED.copy()
+    th[[IDX["mc"], IDX["q"], IDX["tc"], IDX["phic"]]] = PP_LO + (PP_HI - PP_LO) * rng.uniform(0.0, 1.0, 4)
+    ev = _skeleton("pp", cfg, geom, freqs, psd, th, 0.0, 0, sampling_pp())
+    h = waveform(ev, th)
+    return ev.with_strain(gaussian_noise(psd, cfg["T"], rng) + h)
+
+
 def proposals(ev: Event, n: int, seed: int, local_fraction: float = 0.5, local_sigma: float = 1e-3) -> np.ndarray:
     """A batch of n full 11-D parameter vectors for lnL throughput runs.
 

@@ -451,3 +451,4 @@ def test_ns_replace_semantics(c1):
     assert np.array_equal(oracle.loglike(c1, oracle.prior_transform(smp, ou)), ol)
     out2 = oracle.ns_replace(c1, smp, u, ll, worst, ll[worst], 42, 3, 96, 10, 1.0, chol)
     assert all(np.array_equal(a, b) for a, b in zip(out, out2))
+
