@@ -2,7 +2,8 @@
 
 Python access (ctypes) to ``gwl_oracle.cpp``: the plain per-bin definition of
 the frequency-domain Gaussian-noise log-likelihood (Eq. 2 of Smith et al.
-2020, read as the log-likelihood ratio), its dual-number gradient, and a plain
+2020, read as the log-likelihood ratio), the same with the per-detector
+calibration model of Section 2.2, its dual-number gradient, and a plain
 static parallel nested sampler (Section 3, Algorithm 1).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -58,6 +59,8 @@ def _L():
             _lib.oracle_pn_psi.restype = d
             _lib.oracle_loglike.argtypes = [P, i64, P, P, P, i32, d, d, i32, P, i64, P, i32]
             _lib.oracle_grad.argtypes = [P, i64, P, P, P, i32, d, d, i32, P, i64, P, P, i32]
+            _lib.oracle_loglike_cal.argtypes = [P, i64, P, P, P, i32, d, d, i32, i32, P, P, i64, P, i32]
+            _lib.oracle_cal_spline.argtypes = [i32, P, P, i64, P, P]
             _lib.oracle_philox.argtypes = [P, P, P]
             _lib.oracle_prior_transform.argtypes = [i32, P, P, P, P, P, P, P, i64, P]
             _lib.oracle_ns_replace.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
@@ -146,6 +149,34 @@ def grad(ev, theta, n_threads: int | None = None):
     keep, a = _ev_args(ev)
     _L().oracle_grad(*a, _p(th), th.shape[0], _p(out), _p(g), n_threads or default_threads())
     return out, g
+
+
+def loglike_cal(ev, node_freqs, theta, n_threads: int | None = None) -> np.ndarray:
+    """lnL with the calibration model for theta[B, 11 + 2 n_nodes n_det] -> [B].
+
+    After the 11 source parameters each row holds, per detector, the amplitude
+    corrections dA at the nodes and then the phase corrections dphi [rad]; the
+    template of detector d is multiplied by (1 + dA_d(f)) exp(i dphi_d(f)),
+    both natural cubic splines in ln f through the nodes (Section 2.2's
+    calibration model, in the reading stated in gwl_oracle.cpp).
+    """
+    nf = _f64(node_freqs)
+    n_det = np.asarray(ev.geom).shape[0]
+    th = _f64(theta).reshape(-1, N_PARAM + 2 * nf.size * n_det)
+    out = np.zeros(th.shape[0])
+    keep, a = _ev_args(ev)
+    rc = _L().oracle_loglike_cal(*a, nf.size, _p(nf), _p(th), th.shape[0], _p(out), n_threads or default_threads())
+    if rc:
+        raise ValueError("calibration needs at least two nodes")
+    return out
+
+
+def cal_spline(x, y, xq) -> np.ndarray:
+    """The oracle's natural cubic spline through (x, y) evaluated at xq."""
+    xx, yy, qq = _f64(x), _f64(y), _f64(xq)
+    out = np.zeros(qq.size)
+    _L().oracle_cal_spline(xx.size, _p(xx), _p(yy), qq.size, _p(qq), _p(out))
+    return out
 
 
 def philox(ctr, key) -> np.ndarray:

@@ -312,3 +312,34 @@ def c4_events(seed: int, n_events: int = 64):
         out.append(dict(n_det=3, T=T, f_low=20.0, f_high=1024.0, noise=True, source=src, batch=1000,
                         gmst=1.7, seed=int(rng.integers(1 << 31))))
     return out
+
+
+# ---------------------------------------------------------------- calibration model
+# Section 2.2: ten amplitude and ten phase nodes per interferometer.  Nodes are
+# log-spaced over the analysed band; the per-node corrections are drawn from
+# zero-mean Gaussians of 10 % in amplitude and 0.1 rad (about 6 degrees) in
+# phase, the order of the calibration uncertainty of the LIGO detectors.
+CAL_NODES = 10
+CAL_SIGMA_AMP = 0.1
+CAL_SIGMA_PHASE = 0.1
+
+
+def cal_node_freqs(f_low: float, f_high: float, n: int = CAL_NODES) -> np.ndarray:
+    """n node frequencies, log-spaced from f_low to f_high inclusive."""
+    return np.geomspace(f_low, f_high, n)
+
+
+def draw_calibration(rng: np.random.Generator, n: int, n_det: int, n_nodes: int = CAL_NODES,
+                     sigma_amp: float = CAL_SIGMA_AMP, sigma_phase: float = CAL_SIGMA_PHASE) -> np.ndarray:
+    """[n, 2 n_nodes n_det] calibration parameters: per detector dA at the nodes, then dphi [rad]."""
+    out = np.empty((n, n_det, 2, n_nodes))
+    out[:, :, 0, :] = sigma_amp * rng.standard_normal((n, n_det, n_nodes))
+    out[:, :, 1, :] = sigma_phase * rng.standard_normal((n, n_det, n_nodes))
+    return out.reshape(n, 2 * n_nodes * n_det)
+
+
+def calibrated_proposals(ev: Event, n: int, seed: int, n_nodes: int = CAL_NODES) -> np.ndarray:
+    """[n, 11 + 2 n_nodes n_det]: lnL throughput proposals with calibration parameters appended."""
+    th = proposals(ev, n, seed)
+    cal = draw_calibration(np.random.default_rng(seed + 7), n, ev.geom.shape[0], n_nodes)
+    return np.ascontiguousarray(np.concatenate([th, cal], axis=1))

@@ -452,3 +452,75 @@ def test_ns_replace_semantics(c1):
     out2 = oracle.ns_replace(c1, smp, u, ll, worst, ll[worst], 42, 3, 96, 10, 1.0, chol)
     assert all(np.array_equal(a, b) for a, b in zip(out, out2))
 
+
+
+# ---------------------------------------------------------------- calibration model
+def _cal_theta(ev, th11, dA, dphi):
+    """Row [11 + 2 n_nodes n_det] from per-detector node arrays dA, dphi [n_det, n_nodes]."""
+    n_det = ev.geom.shape[0]
+    cal = np.concatenate([np.concatenate([dA[d], dphi[d]]) for d in range(n_det)])
+    return np.concatenate([th11, cal])
+
+
+def test_cal_spline_is_scipy_natural_cubic_spline():
+    """The oracle's spline equals scipy's natural CubicSpline, inside and outside the nodes."""
+    from scipy.interpolate import CubicSpline
+    rng = np.random.default_rng(5)
+    for n in (2, 3, 4, 10, 16):
+        x = np.sort(rng.uniform(2.5, 7.5, n))
+        x[1:] = np.maximum(x[1:], x[:-1] + 0.05)
+        y = rng.normal(size=n)
+        q = np.linspace(x[0] - 0.7, x[-1] + 0.7, 777)
+        ref = CubicSpline(x, y, bc_type="natural")(q)
+        assert np.abs(oracle.cal_spline(x, y, q) - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_cal_zero_corrections_reduce_to_uncalibrated(c2):
+    nodes = I.cal_node_freqs(20.0, 1024.0)
+    th = I.proposals(c2, 8, 3)
+    rows = np.stack([_cal_theta(c2, t, np.zeros((3, 10)), np.zeros((3, 10))) for t in th])
+    np.testing.assert_allclose(oracle.loglike_cal(c2, nodes, rows), oracle.loglike(c2, th), rtol=1e-13, atol=1e-12)
+
+
+def test_cal_constant_amplitude_is_a_distance_rescale(c2):
+    """dA = a at every node: C h = (1 + a) h, the template of distance d_L / (1 + a)."""
+    nodes = I.cal_node_freqs(20.0, 1024.0)
+    th = I.proposals(c2, 6, 4)
+    for a in (-0.2, 0.07, 0.3):
+        rows = np.stack([_cal_theta(c2, t, np.full((3, 10), a), np.zeros((3, 10))) for t in th])
+        ref_th = th.copy()
+        ref_th[:, I.IDX["dl"]] /= 1.0 + a
+        np.testing.assert_allclose(oracle.loglike_cal(c2, nodes, rows), oracle.loglike(c2, ref_th),
+                                   rtol=1e-11, atol=1e-9)
+
+
+def test_cal_constant_phase_is_a_coalescence_phase_shift(c2):
+    """dphi = p0 at every node: C h = e^{i p0} h, the template with phi_c + p0."""
+    nodes = I.cal_node_freqs(20.0, 1024.0)
+    th = I.proposals(c2, 6, 5)
+    for p0 in (-0.4, 0.15, 1.0):
+        rows = np.stack([_cal_theta(c2, t, np.zeros((3, 10)), np.full((3, 10), p0)) for t in th])
+        ref_th = th.copy()
+        ref_th[:, I.IDX["phic"]] += p0
+        np.testing.assert_allclose(oracle.loglike_cal(c2, nodes, rows), oracle.loglike(c2, ref_th),
+                                   rtol=1e-11, atol=1e-9)
+
+
+def test_cal_loglike_brute_force_with_scipy_splines(c2):
+    """Different corrections per detector: lnL = <d|C h> - <C h|C h>/2 from the oracle's
+    waveform, scipy's natural splines in ln f and a numpy inner product."""
+    from scipy.interpolate import CubicSpline
+    nodes = I.cal_node_freqs(20.0, 1024.0)
+    rng = np.random.default_rng(9)
+    th = I.proposals(c2, 4, 6)
+    x = np.log(c2.freqs)
+    for t in th:
+        dA = 0.1 * rng.standard_normal((3, 10))
+        dphi = 0.1 * rng.standard_normal((3, 10))
+        h = oracle.waveform(c2, t)
+        C = np.stack([(1.0 + CubicSpline(np.log(nodes), dA[d], bc_type="natural")(x))
+                      * np.exp(1j * CubicSpline(np.log(nodes), dphi[d], bc_type="natural")(x)) for d in range(3)])
+        ch = C * h
+        ref = inner(c2, c2.strain, ch) - 0.5 * inner(c2, ch, ch)
+        got = oracle.loglike_cal(c2, nodes, _cal_theta(c2, t, dA, dphi)[None])[0]
+        assert got == pytest.approx(ref, rel=1e-10, abs=1e-8)
