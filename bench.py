@@ -51,11 +51,15 @@ FLOPS_PER_BIN_MIXED = 78
 # The gradient adds per bin the combination of the three detectors' terms
 # (3 x 4 FMA) and the basis-weighted sums (10 FMA): 22 FMA = 44 flop -> 122.
 FLOPS_PER_BIN_GRAD = 122
+# Calibration model (Section 2.2), per bin and detector on top of the plain
+# likelihood: two spline values (4 FMA each, 16 flop), the phase shift (1),
+# the amplitude factor (1 + 2) and the <h|h> correction (4): 24 flop.
+FLOPS_PER_BIN_CAL = FLOPS_PER_BIN_MIXED + 3 * 24
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one bin-loop launch on this workload, from the
 # ncu capture summarised in profiles/k_window_mixed_c2.md; None whenever the
 # kernel has changed since that capture.
-KWINDOW_DRAM_BYTES = 1581824 + 256
+KWINDOW_DRAM_BYTES = None
 
 
 def parse():
@@ -249,6 +253,53 @@ def run_grad(ev, args, flush, stream, peak_tflops):
                          "kernel_ms": kms / kn}}
 
 
+def run_cal(ev, args, flush, stream, peak_tflops):
+    """lnL evals/s with the calibration model (ten amplitude and ten phase nodes per detector, 71 parameters
+    per row) on the same data and batch, device-timed, L2 flushed between steps."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    th = I.calibrated_proposals(ev, BATCH, SEED + 11)
+    rows = np.ascontiguousarray(np.concatenate([I.reduced(th[:, :11], ev.sampling), th[:, 11:]], axis=1))
+    x = torch.from_numpy(rows).cuda()
+    ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
+    ctx.gwl_set_calibration(I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1])))
+    tuning = ctx.gwl_autotune(x, gwl.GWL_TUNE_LOGLIKE, stream)
+    out = torch.empty(BATCH, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.gwl_loglike(x, out, stream)
+    torch.cuda.synchronize()
+    steps = max(10, args.steps // 2)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        flush.fill_(1.0)
+        e0.record(stream)
+        ctx.gwl_loglike(x, out, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    ctx.gwl_profile(True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        ctx.gwl_loglike(x, out, stream)
+    torch.cuda.synchronize()
+    kms, kn = ctx.gwl_profile_read(gwl.KERNEL_BINS)
+    ctx.gwl_profile(False)
+    ctx.close()
+    pairs = in_band_pairs(ev, th[:, :11])
+    achieved = FLOPS_PER_BIN_CAL * pairs / (kms / kn * 1e-3) / 1e12
+    return {"value": BATCH / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms, "batch": BATCH, "steps": steps,
+            "precision": "mixed", "dim": int(rows.shape[1]),
+            "workload": "same 3-det 8 s data, 11 source + 60 calibration parameters (10 nodes per detector)",
+            "window": tuning["window"], "ctas_per_sm": tuning["ctas_per_sm"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "kernel": "k_window<3,mixed,calibrated>",
+                         "flops_per_pair": FLOPS_PER_BIN_CAL, "pairs_per_launch": int(pairs),
+                         "kernel_ms": kms / kn}}
+
+
 def run_ns(args):
     """Wall time of a full nested-sampling run on the 1-detector 4 s zero-noise event (4-D)."""
     from paper_1909_11873_gb300 import gwl
@@ -374,6 +425,7 @@ def run_gwl(args):
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * fclk / 1e12
     achieved = FLOPS_PER_BIN_MIXED * pairs / per_launch_s / 1e12
     grad_res = run_grad(ev, args, flush, stream, peak_tflops) if rank == 0 else None
+    cal_res = run_cal(ev, args, flush, stream, peak_tflops) if rank == 0 else None
     ns_res = run_ns(args) if rank == 0 else None
 
     ms, ms64, mse = max_over_ranks([results[gwl.GWL_MIXED]["ms"], results[gwl.GWL_FP64]["ms"], ms_e2e], "cuda")
@@ -417,6 +469,7 @@ def run_gwl(args):
         "clocks": clk,
         "gpu_launches": int(results[gwl.GWL_MIXED]["launches"]),
         "grad": grad_res,
+        "calibrated": cal_res,
         "ns": ns_res,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

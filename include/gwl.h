@@ -117,7 +117,8 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
                const gwl_detector* dets, int n_det, const gwl_options* opt, gwl_ctx** out);
 
 /* Batched log-likelihood (Eq. 2 as the log-likelihood ratio).
- *   theta_dev dev [B][n_dim] FP64 sampled coordinates
+ *   theta_dev dev [B][n_dim] FP64 sampled coordinates (with the calibration
+ *             model: [B][n_dim + 2 n_nodes n_det], see gwl_set_calibration)
  *   lnl_dev   dev [B]        FP64 output
  * B >= 0 (B = 0 is a no-op). */
 int gwl_loglike(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, void* stream);
@@ -126,6 +127,35 @@ int gwl_loglike(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_de
  * copies lnL back and synchronises the stream before returning. */
 int gwl_loglike_host(gwl_ctx* ctx, const double* theta_host, int64_t B, double* lnl_host,
                      void* stream);
+
+/* Calibration model (Section 2.2 of the paper: the calibration uncertainty
+ * of each interferometer's data is modelled by amplitude and phase
+ * corrections at frequency nodes, ten nodes and twenty parameters per
+ * detector in the paper's analyses).  With n_nodes > 0 the template of
+ * detector d is multiplied bin by bin by
+ *   C_d(f) = (1 + dA_d(f)) exp(i dphi_d(f)),
+ * dA_d and dphi_d [rad] natural cubic splines in ln f through the node values
+ * (the end cubics continued outside the nodes), and each row of theta for
+ * gwl_loglike, gwl_loglike_host and gwl_loglike_static holds
+ * n_dim + 2 n_nodes n_det doubles: the n_dim sampled coordinates, then for
+ * each detector d (gwl_create's order) dA at the nodes followed by dphi at
+ * the nodes.
+ *   n_nodes     0 (off, the default) or 2 .. GWL_MAX_CAL_NODES
+ *   node_freqs  host [n_nodes] positive, strictly increasing [Hz]; copied
+ * A set-up call like gwl_create: it synchronises the device and builds
+ * per-bin tables there (128 bytes per bin).  gwl_grad, ns_replace, ns_run,
+ * gwl_autotune with GWL_TUNE_GRAD and gwl_multi_create / gwl_multi_loglike /
+ * gwl_multi_ns_run refuse a calibrated context with GWL_ERR_ARG;
+ * gwl_waveform returns the template without the calibration factor.  A
+ * non-finite calibration parameter gives a non-finite lnL.  The likelihood
+ * window (gwl_tuning.window) shrinks, if needed, so that the calibration rows
+ * fit in shared memory. */
+#define GWL_MAX_CAL_NODES 16
+int gwl_set_calibration(gwl_ctx* ctx, int n_nodes, const double* node_freqs);
+
+/* The context's calibration nodes (0: off) and doubles per row of theta
+ * (either pointer may be null). */
+int gwl_get_calibration(const gwl_ctx* ctx, int* n_nodes, int64_t* theta_stride);
 
 /* Log-likelihood and its gradient with respect to the n_dim sampled
  * coordinates (adjoint accumulation over bins; the ISCO cut index is held
@@ -241,7 +271,8 @@ void gwl_multi_destroy(gwl_multi* m);
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
  *   - A batch needs about (276 + 16 n_det ceil(n_bins / window)) bytes per
- *     proposal, window being the context's bin window (gwl_tuning.window); a
+ *     proposal (24 n_det with the calibration model), window being the
+ *     context's bin window (gwl_tuning.window); a
  *     batch that does not fit returns GWL_ERR_ARG with the sizes in the error
  *     text and launches nothing.
  *   - All calls on a device share the array and it keeps the previous call's

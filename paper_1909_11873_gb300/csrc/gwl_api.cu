@@ -109,6 +109,56 @@ int ensure_io(gwl_ctx* c, int64_t n) {
   return GWL_OK;
 }
 
+// m = Q y: the second derivatives at the nodes of the natural cubic spline
+// through (x_k, y_k), as a fixed matrix of the node layout.  Interior rows
+// k = 1 .. n-2 of  h_{k-1} m_{k-1} + 2 (h_{k-1} + h_k) m_k + h_k m_{k+1}
+// = 6 [(y_{k+1} - y_k)/h_k - (y_k - y_{k-1})/h_{k-1}], m_0 = m_{n-1} = 0, are
+// solved for all n right-hand sides at once by Gauss-Jordan elimination.
+std::vector<double> natural_spline_matrix(int n, const double* x) {
+  std::vector<double> Q((size_t)n * n, 0.0);
+  const int ni = n - 2;
+  if (ni <= 0) return Q;
+  std::vector<double> A((size_t)ni * ni, 0.0), R((size_t)ni * n, 0.0);
+  for (int i = 0; i < ni; ++i) {
+    const int k = i + 1;
+    const double hl = x[k] - x[k - 1], hr = x[k + 1] - x[k];
+    if (i > 0) A[(size_t)i * ni + i - 1] = hl;
+    A[(size_t)i * ni + i] = 2.0 * (hl + hr);
+    if (i + 1 < ni) A[(size_t)i * ni + i + 1] = hr;
+    R[(size_t)i * n + k - 1] += 6.0 / hl;
+    R[(size_t)i * n + k] -= 6.0 / hl + 6.0 / hr;
+    R[(size_t)i * n + k + 1] += 6.0 / hr;
+  }
+  for (int col = 0; col < ni; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < ni; ++r)
+      if (std::fabs(A[(size_t)r * ni + col]) > std::fabs(A[(size_t)piv * ni + col])) piv = r;
+    if (piv != col) {
+      for (int c2 = 0; c2 < ni; ++c2) std::swap(A[(size_t)col * ni + c2], A[(size_t)piv * ni + c2]);
+      for (int c2 = 0; c2 < n; ++c2) std::swap(R[(size_t)col * n + c2], R[(size_t)piv * n + c2]);
+    }
+    const double inv = 1.0 / A[(size_t)col * ni + col];
+    for (int c2 = 0; c2 < ni; ++c2) A[(size_t)col * ni + c2] *= inv;
+    for (int c2 = 0; c2 < n; ++c2) R[(size_t)col * n + c2] *= inv;
+    for (int r = 0; r < ni; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * ni + col];
+      if (f == 0.0) continue;
+      for (int c2 = 0; c2 < ni; ++c2) A[(size_t)r * ni + c2] -= f * A[(size_t)col * ni + c2];
+      for (int c2 = 0; c2 < n; ++c2) R[(size_t)r * n + c2] -= f * R[(size_t)col * n + c2];
+    }
+  }
+  for (int i = 0; i < ni; ++i)
+    for (int c2 = 0; c2 < n; ++c2) Q[(size_t)(i + 1) * n + c2] = R[(size_t)i * n + c2];
+  return Q;
+}
+
+// The compute entry points that do not model calibration refuse a calibrated context.
+int no_calibration(const gwl_ctx* c, const char* what) {
+  if (c->n_cal_nodes) return fail(GWL_ERR_ARG, "%s is not available with the calibration model", what);
+  return GWL_OK;
+}
+
 int check_ctx(const gwl_ctx* c) {
   if (!c) return fail(GWL_ERR_ARG, "null context");
   int dev = -1;
@@ -240,6 +290,7 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     s.gmst = opt->gmst;
     s.t_ref = opt->t_ref;
     s.n_dim = opt->n_dim;
+    s.stride = opt->n_dim;
     for (int k = 0; k < GWL_N_PARAM; ++k) {
       s.fixed[k] = opt->fixed_theta[k];
       s.param_map[k] = k < opt->n_dim ? opt->param_map[k] : 0;
@@ -275,7 +326,7 @@ int gwl_loglike_host(gwl_ctx* c, const double* theta_host, int64_t B, double* ln
   if (B < 0) return fail(GWL_ERR_ARG, "B < 0");
   if (B == 0) return GWL_OK;
   if (!theta_host || !lnl_host) return fail(GWL_ERR_ARG, "null host pointer");
-  const int64_t nt = B * c->opt.n_dim;
+  const int64_t nt = B * gwl::theta_stride(c);
   if ((rc = ensure_io(c, nt + B))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(c->d_io, theta_host, sizeof(double) * nt, cudaMemcpyHostToDevice, st);
@@ -308,6 +359,7 @@ int gwl_grad(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, do
   if (B < 0) return fail(GWL_ERR_ARG, "B < 0");
   if (B == 0) return GWL_OK;
   if (!theta_dev || !lnl_dev || !grad_dev) return fail(GWL_ERR_ARG, "null device pointer");
+  if ((rc = no_calibration(c, "gwl_grad"))) return rc;
   if ((rc = ensure_scratch(c, B))) return rc;
   if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * B))) return rc;
   if ((rc = ensure_bytes(c, &c->d_gpartials, &c->gpartials_cap, gwl::grad_partials_bytes(c, B)))) return rc;
@@ -328,6 +380,7 @@ int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t
   if (n_chains < 0 || n_chains > ((int64_t)1 << 31) - 1) return fail(GWL_ERR_ARG, "n_chains out of range");
   if (walk_len < 0) return fail(GWL_ERR_ARG, "walk_len < 0");
   if (!(scale > 0.0) || !std::isfinite(scale)) return fail(GWL_ERR_ARG, "scale must be positive");
+  if ((rc = no_calibration(c, "ns_replace"))) return rc;
   if (n_chains == 0) return GWL_OK;
   if (!live_u || !live_lnl || !chol || !out_u || !out_lnl || !out_nacc) return fail(GWL_ERR_ARG, "null device pointer");
   const int D = c->opt.n_dim;
@@ -366,6 +419,7 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
   if (max_dead > 0 && (!dead_lnl || !dead_logwt || !dead_u)) return fail(GWL_ERR_ARG, "null dead-point buffer");
   if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "ns_run supports K <= 4096 and n_chains <= 4096");
+  if ((rc = no_calibration(c, "ns_run"))) return rc;
   const int64_t nb = n_chains > K ? n_chains : K;
   if ((rc = ensure_scratch(c, nb))) return rc;
   if (c->walk_kind == GWL_WALK_GALILEAN) {
@@ -411,6 +465,7 @@ int gwl_multi_create(gwl_ctx* const* ctxs, int n_events, gwl_multi** out) {
     if (c->device != ctxs[0]->device || c->n_det != ctxs[0]->n_det || c->opt.precision != ctxs[0]->opt.precision ||
         c->opt.n_dim != ctxs[0]->opt.n_dim)
       return fail(GWL_ERR_ARG, "context %d differs in device, detectors, precision or dimension", e);
+    if (c->n_cal_nodes) return fail(GWL_ERR_ARG, "context %d has the calibration model (not batched)", e);
   }
   int rc = check_ctx(ctxs[0]);
   if (rc) return rc;
@@ -428,6 +483,7 @@ int gwl_multi_loglike(gwl_multi* h, const double* theta_dev, int64_t n_per, doub
   if (n_per < 0) return fail(GWL_ERR_ARG, "n_per < 0");
   if (n_per == 0) return GWL_OK;
   if (!theta_dev || !lnl_dev) return fail(GWL_ERR_ARG, "null device pointer");
+  if (gwl::multi_has_calibration(h->m)) return fail(GWL_ERR_ARG, "a context of the batch has the calibration model");
   cudaError_t e = gwl::multi_prepare(h->m, n_per);
   if (e != cudaSuccess) return cuda_fail(e, "gwl_multi_loglike");
   e = gwl::multi_loglike(h->m, theta_dev, n_per, lnl_dev, (cudaStream_t)stream);
@@ -441,6 +497,7 @@ int gwl_multi_ns_run(gwl_multi* h, int64_t K, int64_t n_chains, int walk_len, ui
   if (K < 2 || n_chains < 1 || walk_len < 1 || max_rounds < 0) return fail(GWL_ERR_ARG, "bad sizes");
   if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "gwl_multi_ns_run supports K, n_chains <= 4096");
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
+  if (gwl::multi_has_calibration(h->m)) return fail(GWL_ERR_ARG, "a context of the batch has the calibration model");
   std::vector<double> res((size_t)11 * h->E);
   const int r = gwl::multi_ns_run(h->m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res.data(),
                                   (cudaStream_t)stream);
@@ -501,9 +558,9 @@ int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
     return fail(GWL_ERR_ARG, "windows must be multiples of 32 bins (got %d/%d)", t->window, t->grad_window);
   // likelihood rows: the delta table (mixed) or the FP64 table; gradient rows: the mixed or FP64 table
   const bool mixed = c->opt.precision == GWL_MIXED;
-  const size_t row = mixed ? sizeof(float) * c->row_delta : sizeof(double) * c->row_doubles;
+  const size_t row = gwl::lnl_row_bytes(c);
   const size_t grow = mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
-  if ((size_t)t->window * row > 200 * 1024 || (size_t)t->grad_window * grow > 200 * 1024)
+  if ((size_t)t->window * row > gwl::kWindowSmemMax || (size_t)t->grad_window * grow > gwl::kWindowSmemMax)
     return fail(GWL_ERR_ARG, "window of %d/%d bins exceeds shared memory", t->window, t->grad_window);
   if (t->window) c->window = t->window;
   if (t->grad_window) c->grad_window = t->grad_window;
@@ -519,6 +576,68 @@ int gwl_get_tuning(const gwl_ctx* c, gwl_tuning* out) {
   out->ms_loglike = c->tuned_ms[0];
   out->ms_grad = c->tuned_ms[1];
   out->n_tried = c->tuned_n;
+  return GWL_OK;
+}
+
+int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n_nodes != 0 && (n_nodes < 2 || n_nodes > GWL_MAX_CAL_NODES))
+    return fail(GWL_ERR_ARG, "n_nodes=%d outside {0} and [2, %d]", n_nodes, GWL_MAX_CAL_NODES);
+  if (n_nodes && !node_freqs) return fail(GWL_ERR_ARG, "node_freqs is null");
+  for (int k = 0; k < n_nodes; ++k) {
+    if (!(node_freqs[k] > 0.0) || !std::isfinite(node_freqs[k]))
+      return fail(GWL_ERR_ARG, "node_freqs[%d] not positive", k);
+    if (k > 0 && !(std::log(node_freqs[k]) > std::log(node_freqs[k - 1])))
+      return fail(GWL_ERR_ARG, "node_freqs must increase strictly (at %d)", k);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError(), "gwl_set_calibration");
+  dev_free(c, c->d_cal_f, c->M * c->row_cal_f);
+  dev_free(c, c->d_cal_d, c->M * c->row_cal_d);
+  dev_free(c, c->d_calQ_f, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
+  dev_free(c, c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
+  c->n_cal_nodes = 0;
+  c->seg.stride = c->opt.n_dim;
+  if (n_nodes == 0) return GWL_OK;
+
+  std::vector<double> x(n_nodes);
+  for (int k = 0; k < n_nodes; ++k) x[k] = std::log(node_freqs[k]);
+  const std::vector<double> Q = natural_spline_matrix(n_nodes, x.data());
+  std::vector<float> Qf(Q.size());
+  for (size_t i = 0; i < Q.size(); ++i) Qf[i] = (float)Q[i];
+  c->row_cal_f = gwl::cal_row_floats(c->n_det);
+  c->row_cal_d = gwl::cal_row_doubles(c->n_det);
+  double* d_x = nullptr;
+  cudaError_t e;
+  do {
+    if ((e = dev_alloc(c, &c->d_cal_f, c->M * c->row_cal_f)) != cudaSuccess) break;
+    if ((e = dev_alloc(c, &c->d_cal_d, c->M * c->row_cal_d)) != cudaSuccess) break;
+    if ((e = dev_alloc(c, &c->d_calQ_f, gwl::kMaxCalNodes * gwl::kMaxCalNodes)) != cudaSuccess) break;
+    if ((e = dev_alloc(c, &c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&d_x, sizeof(double) * n_nodes)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(d_x, x.data(), sizeof(double) * n_nodes, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(c->d_calQ_d, Q.data(), sizeof(double) * Q.size(), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(c->d_calQ_f, Qf.data(), sizeof(float) * Qf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    c->n_cal_nodes = n_nodes;
+    if ((e = gwl::launch_cal_tables(c, d_x, 0)) != cudaSuccess) break;
+    e = cudaDeviceSynchronize();
+  } while (false);
+  if (d_x) cudaFree(d_x);
+  if (e != cudaSuccess) {
+    c->n_cal_nodes = 0;
+    return cuda_fail(e, "gwl_set_calibration");
+  }
+  c->seg.stride = c->opt.n_dim + 2 * n_nodes * c->n_det;
+  // the likelihood window must still fit shared memory with the calibration rows
+  const size_t row = gwl::lnl_row_bytes(c);
+  while (c->window > 32 && (size_t)c->window * row > gwl::kWindowSmemMax) c->window -= 32;
+  return GWL_OK;
+}
+
+int gwl_get_calibration(const gwl_ctx* c, int* n_nodes, int64_t* theta_stride) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  if (n_nodes) *n_nodes = c->n_cal_nodes;
+  if (theta_stride) *theta_stride = c->seg.stride;
   return GWL_OK;
 }
 
@@ -572,6 +691,10 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_tab_delta, c->M * c->row_delta);
   dev_free(c, c->d_anchor, (c->M + gwl::kAnchor - 1) / gwl::kAnchor * gwl::kAnchorRowFloats);
   dev_free(c, c->d_tab_f64, c->M * c->row_doubles);
+  dev_free(c, c->d_cal_f, c->M * c->row_cal_f);
+  dev_free(c, c->d_cal_d, c->M * c->row_cal_d);
+  dev_free(c, c->d_calQ_f, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
+  dev_free(c, c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
   dev_free(c, c->d_pm, c->prop_cap);
   dev_free(c, c->d_pf, c->prop_cap);
   dev_free(c, c->d_pc, c->prop_cap);

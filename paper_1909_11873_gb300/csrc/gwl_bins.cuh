@@ -120,6 +120,63 @@ __device__ __forceinline__ void bin_mixed(const float (&v)[RowM<NDET>::n], const
   }
 }
 
+// ---------------------------------------------------------------- calibration model (Section 2.2)
+// With calibration the template of detector d at bin j is multiplied by
+// (1 + dA_d,j) e^{i dphi_d,j}: with dphi in cycles the bin's term becomes
+//   (1 + dA) G_d,j e^{-2 pi i (r_d,j - dphi)},
+// and <h|h>_d = |K_d|^2 (H_d[ncut - 1] + X_d) with X_d = sum_j dA (2 + dA) dH_d,j.
+// dA and dphi come from the bin's calibration row (spline weights, interval k)
+// and the warp's node data of the proposal (see gwl_device.cuh).
+template <int NDET, typename T>
+struct CalBin {
+  T A[NDET], P[NDET], H[NDET];
+};
+
+template <int NDET>
+__device__ __forceinline__ void cal_eval(const float* __restrict__ crow, const float4* __restrict__ nodes,
+                                         CalBin<NDET, float>& cb) {
+  const float4 w = reinterpret_cast<const float4*>(crow)[0];
+  const float4 r1 = reinterpret_cast<const float4*>(crow)[1];
+  const int k = __float_as_int(r1.x);
+  float hx[4] = {r1.y, r1.z, r1.w, 0.0f};
+  if constexpr (NDET > 3) hx[3] = crow[8];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    const float4 n0 = nodes[d * kMaxCalNodes + k], n1 = nodes[d * kMaxCalNodes + k + 1];
+    cb.A[d] = fmaf(w.x, n0.x, fmaf(w.y, n1.x, fmaf(w.z, n0.y, w.w * n1.y)));
+    cb.P[d] = fmaf(w.x, n0.z, fmaf(w.y, n1.z, fmaf(w.z, n0.w, w.w * n1.w)));
+    cb.H[d] = hx[d];
+  }
+}
+
+template <int NDET>
+__device__ __forceinline__ void cal_eval(const double* __restrict__ crow, const CalNodeD* __restrict__ nodes,
+                                         CalBin<NDET, double>& cb) {
+  const double2 w01 = reinterpret_cast<const double2*>(crow)[0];
+  const double2 w23 = reinterpret_cast<const double2*>(crow)[1];
+  const int k = (int)crow[4];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    const CalNodeD& n0 = nodes[d * kMaxCalNodes + k];
+    const CalNodeD& n1 = nodes[d * kMaxCalNodes + k + 1];
+    cb.A[d] = fma(w01.x, n0.v[0], fma(w01.y, n1.v[0], fma(w23.x, n0.v[1], w23.y * n1.v[1])));
+    cb.P[d] = fma(w01.x, n0.v[2], fma(w01.y, n1.v[2], fma(w23.x, n0.v[3], w23.y * n1.v[3])));
+    cb.H[d] = crow[5 + d];
+  }
+}
+
+// One detector's term of a bin: reduced phase fr [cycles], data weight (gr, gi).
+template <bool CAL, typename T>
+__device__ __forceinline__ void cal_apply(T& fr, T& gr, T& gi, T A, T P, T H, T& X) {
+  if constexpr (CAL) {
+    fr = fr - P;
+    const T a1 = (T)1 + A;
+    gr *= a1;
+    gi *= a1;
+    X = fma(A * ((T)2 + A), H, X);
+  }
+}
+
 // ---------------------------------------------------------------- anchored phase (likelihood, mixed path)
 // For the block of kAnchor bins starting at anchor bin a, the phase is
 //   r_d,j = [S(f_a) + tau_d f_a] + dS_j + tau_d (f_j - f_a),  dS_j = sum_m c_m dB_m(f_j).
@@ -180,10 +237,10 @@ __device__ __forceinline__ bool anchor_terms(const float* __restrict__ ra, const
 // One bin of the anchored path with an FP32 delta: v = the first part of the
 // delta row (dB_m high parts, G_d), ad[d] = the block's anchor term plus this
 // lane's tau_d (f_j - f_a).
-template <int NDET>
+template <int NDET, bool CAL>
 __device__ __forceinline__ void bin_anchor(const float (&v)[4 * ((kNBasis + 2 * NDET + 3) / 4)],
                                            const float (&ch)[kNBasis], const float (&ad)[NDET], float (&U)[NDET],
-                                           float (&V)[NDET]) {
+                                           float (&V)[NDET], const CalBin<NDET, float>& cb, float (&X)[NDET]) {
   float ds = __fmul_rn(ch[0], v[0]);
 #pragma unroll
   for (int m = 1; m < kNBasis; ++m) ds = __fmaf_rn(ch[m], v[m], ds);
@@ -191,10 +248,11 @@ __device__ __forceinline__ void bin_anchor(const float (&v)[4 * ((kNBasis + 2 * 
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     const float x = __fadd_rn(ds, ad[d]);
-    const float fr = __fsub_rn(x, nearest_int(x));
+    float fr = __fsub_rn(x, nearest_int(x));
+    float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
+    cal_apply<CAL>(fr, gr, gi, cb.A[d], cb.P[d], cb.H[d], X[d]);
     float sn, cs;
     __sincosf(6.283185307179586f * fr, &sn, &cs);
-    const float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
     U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
     V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
   }
@@ -202,10 +260,11 @@ __device__ __forceinline__ void bin_anchor(const float (&v)[4 * ((kNBasis + 2 * 
 
 // One bin of the anchored path with a float-float delta: v = the whole delta
 // row, dB_m = (v[m], v[kNBasis + 2 NDET + m]).
-template <int NDET>
+template <int NDET, bool CAL>
 __device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBasis + 2 * NDET + 3) / 4)],
                                                  const float (&ch)[kNBasis], const float (&cl)[kNBasis],
-                                                 const float (&ad)[NDET], float (&U)[NDET], float (&V)[NDET]) {
+                                                 const float (&ad)[NDET], float (&U)[NDET], float (&V)[NDET],
+                                                 const CalBin<NDET, float>& cb, float (&X)[NDET]) {
   constexpr int LO = kNBasis + 2 * NDET;
   float s, lo;
   {
@@ -226,10 +285,11 @@ __device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBa
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     const float x = __fadd_rn(ds, ad[d]);
-    const float fr = __fsub_rn(x, nearest_int(x));
+    float fr = __fsub_rn(x, nearest_int(x));
+    float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
+    cal_apply<CAL>(fr, gr, gi, cb.A[d], cb.P[d], cb.H[d], X[d]);
     float sn, cs;
     __sincosf(6.283185307179586f * fr, &sn, &cs);
-    const float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
     U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
     V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
   }
@@ -238,12 +298,16 @@ __device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBa
 // Window sums U_d + i V_d of one proposal over bins [j0, jend) of a staged
 // window of delta rows (sm, row_elems floats per row; j0 on an anchor), by the
 // anchored phase; anc0 = the anchor row of bin j0 (shared or global memory).
+// With CAL, cal_sm holds the window's calibration rows (cal_row floats each),
+// nodes the proposal's node data, and X_d collects the <h|h> correction.
 // The result is per lane (the caller reduces over the warp).
-template <int NDET>
-__device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int row_elems,
-                                              const float* __restrict__ anc0, float df,
-                                              const PropMixed* __restrict__ P, int j0, int jend, int lane,
-                                              float (&U)[NDET], float (&V)[NDET]) {
+template <int NDET, bool CAL>
+__device__ __forceinline__ void anchored_sums_cal(const float* __restrict__ sm, int row_elems,
+                                                  const float* __restrict__ anc0, float df,
+                                                  const PropMixed* __restrict__ P, int j0, int jend, int lane,
+                                                  float (&U)[NDET], float (&V)[NDET],
+                                                  const float* __restrict__ cal_sm, int cal_row,
+                                                  const float4* __restrict__ nodes, float (&X)[NDET]) {
   // anchored phase: the window starts on an anchor (windows are multiples of
   // kAnchor bins); lane l forms the anchor terms of block l of each batch of
   // 32 blocks and the warp shares them by shuffles
@@ -266,7 +330,8 @@ __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int 
 #pragma unroll
   for (int d = 0; d < NDET; ++d) dtl[d] = __fmul_rn(th[d], lane_df);
 #pragma unroll
-  for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
+  for (int d = 0; d < NDET; ++d) U[d] = V[d] = X[d] = 0.0f;
+  CalBin<NDET, float> cb0, cb1;
   const int nblk = (jend - j0 + kAnchor - 1) / kAnchor;
   for (int b0 = 0; b0 < nblk; b0 += 32) {
     float an[NDET];
@@ -297,8 +362,13 @@ __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int 
           *reinterpret_cast<float4*>(&v0[4 * k]) = reinterpret_cast<const float4*>(r0)[k];
           *reinterpret_cast<float4*>(&v1[4 * k]) = reinterpret_cast<const float4*>(r1)[k];
         }
-        bin_anchor<NDET>(v0, ch, ad0, U, V);
-        bin_anchor<NDET>(v1, ch, ad1, U, V);
+        if constexpr (CAL) {
+          const float* c0 = cal_sm + (int64_t)(j - j0) * cal_row;
+          cal_eval<NDET>(c0, nodes, cb0);
+          cal_eval<NDET>(c0 + (int64_t)kAnchor * cal_row, nodes, cb1);
+        }
+        bin_anchor<NDET, CAL>(v0, ch, ad0, U, V, cb0, X);
+        bin_anchor<NDET, CAL>(v1, ch, ad1, U, V, cb1, X);
         continue;
       }
       // otherwise block by block: each takes the FP32 or the float-float delta,
@@ -308,22 +378,35 @@ __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int 
         if (it + h >= nb) break;
         const int jj = j + h * kAnchor;
         const float* row = sm + (int64_t)(jj - j0) * row_elems;
+        if (jj < jend) {
+          if constexpr (CAL) cal_eval<NDET>(cal_sm + (int64_t)(jj - j0) * cal_row, nodes, cb0);
+        }
         if ((fast_mask >> (it + h)) & 1u) {
           if (jj < jend) {
             float v[RX];
 #pragma unroll
             for (int k = 0; k < RX / 4; ++k) *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
-            bin_anchor<NDET>(v, ch, h ? ad1 : ad0, U, V);
+            bin_anchor<NDET, CAL>(v, ch, h ? ad1 : ad0, U, V, cb0, X);
           }
         } else if (jj < jend) {
           float v[RXF];
 #pragma unroll
           for (int k = 0; k < RXF / 4; ++k) *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
-          bin_anchor_exact<NDET>(v, ch, cl, h ? ad1 : ad0, U, V);
+          bin_anchor_exact<NDET, CAL>(v, ch, cl, h ? ad1 : ad0, U, V, cb0, X);
         }
       }
     }
   }
+}
+
+// The same without calibration.
+template <int NDET>
+__device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int row_elems,
+                                              const float* __restrict__ anc0, float df,
+                                              const PropMixed* __restrict__ P, int j0, int jend, int lane,
+                                              float (&U)[NDET], float (&V)[NDET]) {
+  float X[NDET];
+  anchored_sums_cal<NDET, false>(sm, row_elems, anc0, df, P, j0, jend, lane, U, V, nullptr, 0, nullptr, X);
 }
 
 template <int NDET>
@@ -347,6 +430,27 @@ __device__ __forceinline__ void bin_f64(const double (&v)[RowD<NDET>::n], const 
     const double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
     U[d] = fma(gr, cs[d], fma(gi, sn[d], U[d]));
     V[d] = fma(gi, cs[d], fma(-gr, sn[d], V[d]));
+  }
+}
+
+// FP64 bin with the calibration factor (phase correction in cycles).
+template <int NDET>
+__device__ __forceinline__ void bin_f64_cal(const double (&v)[RowD<NDET>::n], const double (&c)[kNBasis],
+                                            const double (&tau)[NDET], const CalBin<NDET, double>& cb,
+                                            double (&U)[NDET], double (&V)[NDET], double (&X)[NDET]) {
+  double r = c[0] * v[0];
+#pragma unroll
+  for (int m = 1; m < kNBasis; ++m) r = fma(c[m], v[m], r);
+  const double f = v[8];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    double ph = fma(tau[d], f, r);
+    double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
+    cal_apply<true>(ph, gr, gi, cb.A[d], cb.P[d], cb.H[d], X[d]);
+    double sn, cs;
+    sincospi(2.0 * ph, &sn, &cs);
+    U[d] = fma(gr, cs, fma(gi, sn, U[d]));
+    V[d] = fma(gi, cs, fma(-gr, sn, V[d]));
   }
 }
 

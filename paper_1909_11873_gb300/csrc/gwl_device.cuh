@@ -50,6 +50,27 @@ constexpr int kAnchor = 32;
 __host__ __device__ constexpr int delta_row_floats(int ndet) { return 4 * odd_units((16 + 2 * ndet + 3) / 4); }
 constexpr int kAnchorRowFloats = 28;
 
+// Calibration model (Section 2.2 of the paper): per detector, amplitude and
+// phase corrections at n_nodes frequency nodes, natural cubic splines in
+// x = ln f.  On interval [x_k, x_{k+1}] (h = x_{k+1} - x_k, t = (x - x_k)/h,
+// the end intervals continued beyond the nodes) a spline with node values y
+// and second derivatives m is
+//   S(x) = (1 - t) y_k + t y_{k+1} + w_c m_k + w_e m_{k+1},
+//   w_c = h^2/6 ((1 - t)^3 - (1 - t)),  w_e = h^2/6 (t^3 - t),
+// so a bin needs four weights and k, shared by every spline, and a proposal
+// needs (y, m) per node, with m = Q y for a fixed n_nodes x n_nodes matrix Q
+// of the node layout.  Calibration rows: [1 - t, t, w_c, w_e, k, dH_d x n_det]
+// (dH_d,j = H_d[j] - H_d[j-1], the bin's <h|h> weight), float or double,
+// padded to an odd number of 16-byte units like the other tables.
+constexpr int kMaxCalNodes = 16;
+__host__ __device__ constexpr int cal_row_floats(int ndet) { return 4 * odd_units((5 + ndet + 3) / 4); }
+__host__ __device__ constexpr int cal_row_doubles(int ndet) { return 2 * odd_units((5 + ndet + 1) / 2); }
+// Per-warp node data of the proposal being summed: (dA_k, m^A_k, dphi_k,
+// m^phi_k) per detector and node, the phase values in cycles.
+struct alignas(32) CalNodeD {
+  double v[4];
+};
+
 // Per-proposal coefficients read warp-uniformly by the bin loop.
 struct alignas(16) PropMixed {
   float ch[kNBasis], cl[kNBasis];  // c_m as float pairs [cycles per basis unit]
@@ -81,8 +102,10 @@ struct SegInfo {
   // the amplitude by amp_scale, so that every quantity is O(1) -- well inside
   // the FP32 range used by the mixed path and the FP32 tangents.
   double amp_scale;
-  // sampled-parameter map
+  // sampled-parameter map; rows of theta hold n_dim sampled coordinates, then
+  // (with calibration) 2 n_nodes n_det calibration parameters: stride doubles
   int n_dim;
+  int stride;
   int param_map[11];
   double fixed[11];
 };

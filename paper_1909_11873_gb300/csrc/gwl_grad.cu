@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
   int ncut = 0;
   if (p < B) {
     double th[11];
-    expand_theta(s, theta + p * s.n_dim, th);
+    expand_theta(s, theta + p * s.stride, th);
     const bool ok = physical(th);
     if (!ok) {
       th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;

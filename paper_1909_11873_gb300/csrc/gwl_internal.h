@@ -29,6 +29,14 @@ struct gwl_ctx {
   double* d_tab_f64 = nullptr;   // [M][f64_row_doubles]
   int row_floats = 0, row_doubles = 0;
 
+  // calibration model (gwl_set_calibration); n_cal_nodes == 0: off
+  int n_cal_nodes = 0;
+  float* d_cal_f = nullptr;      // [M][cal_row_floats]: spline weights, interval, dH_d
+  double* d_cal_d = nullptr;     // [M][cal_row_doubles]
+  float* d_calQ_f = nullptr;     // [n_nodes][n_nodes]: m = Q y (natural-spline curvatures)
+  double* d_calQ_d = nullptr;
+  int row_cal_f = 0, row_cal_d = 0;
+
   // device scratch (owned, grown on demand)
   gwl::PropMixed* d_pm = nullptr;
   gwl::PropF64* d_pf = nullptr;
@@ -73,6 +81,22 @@ struct gwl_ctx {
 };
 
 namespace gwl {
+// Largest staged window of a bin loop (bytes of dynamic shared memory), so
+// that with the kernels' static shared memory a CTA stays within 227 KB.
+constexpr size_t kWindowSmemMax = 192 * 1024;
+// Doubles per row of theta: the sampled coordinates, then the calibration parameters.
+inline int64_t theta_stride(const gwl_ctx* c) { return c->seg.stride; }
+// Bytes of shared memory per bin of the likelihood bin loop's window.
+inline size_t lnl_row_bytes(const gwl_ctx* c) {
+  const bool mixed = c->opt.precision == GWL_MIXED;
+  size_t b = mixed ? sizeof(float) * (size_t)c->row_delta : sizeof(double) * (size_t)c->row_doubles;
+  if (c->n_cal_nodes) b += mixed ? sizeof(float) * (size_t)c->row_cal_f : sizeof(double) * (size_t)c->row_cal_d;
+  return b;
+}
+// Per-detector sums a bin loop keeps per (proposal, window): U, V (and the
+// calibrated <h|h> correction X).
+inline int sums_per_det(const gwl_ctx* c) { return c->n_cal_nodes ? 3 : 2; }
+
 // Records a start event now and a stop event when it goes out of scope, on
 // the launch stream, if the context has profiling enabled.
 struct ProfScope {
@@ -90,6 +114,7 @@ namespace gwl {
 // a1: tables
 cudaError_t launch_build_tables(gwl_ctx* c, const double* d_strain, const double* d_psd, cudaStream_t st);
 cudaError_t launch_scale_tables(gwl_ctx* c, double sg, cudaStream_t st);
+cudaError_t launch_cal_tables(gwl_ctx* c, const double* d_xnode, cudaStream_t st);
 
 // a2-a6: batched log-likelihood
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st);
@@ -118,6 +143,7 @@ void multi_delete(Multi* m);
 cudaError_t multi_prepare(Multi* m, int64_t n_per);
 cudaError_t multi_loglike(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st);
 int64_t multi_launches(const Multi* m);
+bool multi_has_calibration(const Multi* m);
 int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                  int64_t max_rounds, double scale0, double* res /* [E][11] */, cudaStream_t caller);
 

@@ -80,7 +80,7 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
   double th[11];
 #pragma unroll
   for (int k = 0; k < 11; ++k) th[k] = 1.0;
-  if (valid) expand_theta(s, theta + p * s.n_dim, th);
+  if (valid) expand_theta(s, theta + p * s.stride, th);
   const bool ok = valid && physical(th);
   if (!ok) {  // keep every transcendental below on a harmless argument
     th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
@@ -242,7 +242,7 @@ struct WinArgs {
   int nw_total;   // ceil(M / CH)
   const PropCommon* pc;
   const void* prop;  // PropMixed* or PropF64*
-  void* partials;    // [B][nw_total][2 NDET] float (mixed) or double (fp64)
+  void* partials;    // [B][nw_total][S NDET] float (mixed) or double (fp64), S = 2 (3 with calibration)
   int* work;         // [0] largest cut, [1 + w] proposal counter of window w
   const int* hist;   // [w] proposals whose last window is w
   const float* anchor;  // mixed: anchor rows, one per kAnchor bins
@@ -250,51 +250,95 @@ struct WinArgs {
   int* pdone;        // [p] windows of proposal p already summed
   double* lnl;       // [B] output
   int* status;       // latched error bits
+  // calibration model (instances with CAL only)
+  const void* cal;       // [M][cal_row] calibration rows, float (mixed) or double
+  int cal_row;           // elements per calibration row
+  int cal_smem;          // offset of the window's calibration rows in shared memory (elements)
+  const double* theta;   // [B][stride] parameter rows
+  int64_t stride;        // doubles per row of theta
+  int cal_par;           // first calibration parameter of a row
+  int nn;                // calibration nodes
+  const void* calQ;      // [nn][nn] natural-spline matrix m = Q y, float (mixed) or double
 };
 
-// lnL_p = sum_d [Re K_d U_d - Im K_d V_d] - <h|h>/2 (FP64), U_d + i V_d the
-// proposal's data-template sums over all its windows.  Warp-level: lane d
+// lnL_p = sum_d [Re K_d U_d - Im K_d V_d - |K_d|^2 X_d / 2] - <h|h>/2 (FP64),
+// U_d + i V_d the proposal's data-template sums over all its windows and X_d
+// the calibration's <h|h> correction (CAL only).  Warp-level: lane d
 // (d < NDET) forms detector d's term and a fixed shuffle tree adds them, so
 // the FP64 pipe sees a handful of warp instructions per proposal; the result
 // is valid on lane 0.
-template <int NDET, typename T>
+template <int NDET, bool CAL, typename T>
 __device__ __forceinline__ double combine_lnl(const PropCommon* __restrict__ c, const T (&U)[NDET],
-                                              const T (&V)[NDET], int lane) {
+                                              const T (&V)[NDET], const T (&X)[NDET], int lane) {
   static_assert(NDET <= 4, "at most four detectors");
-  T u = (T)0, v = (T)0;
+  T u = (T)0, v = (T)0, x = (T)0;
 #pragma unroll
   for (int d = 0; d < NDET; ++d)
     if (lane == d) {
       u = U[d];
       v = V[d];
+      if (CAL) x = X[d];
     }
   double t = 0.0;
-  if (lane < NDET) t = c->Kr[lane] * (double)u - c->Ki[lane] * (double)v;
+  if (lane < NDET) {
+    const double kr = c->Kr[lane], ki = c->Ki[lane];
+    t = kr * (double)u - ki * (double)v;
+    if (CAL) t -= 0.5 * (kr * kr + ki * ki) * (double)x;
+  }
   t += __shfl_down_sync(0xffffffffu, t, 2);
   t += __shfl_down_sync(0xffffffffu, t, 1);
   return t - 0.5 * c->hh;
 }
 
-template <int NDET, bool MIXED, typename Acc>
-__device__ __forceinline__ void window_sums(const WinArgs& a, const void* __restrict__ smv, int64_t p, int j0,
-                                            int jend, int lane, Acc (&Ud)[NDET], Acc (&Vd)[NDET]) {
+// Node data of proposal p for the warp's calibration splines: lane o of the
+// 2 NDET nn outputs (spline s = 2 d + q, q = 0 amplitude, 1 phase; node k)
+// forms m_k = sum_i Q_ki y_i and stores (y_k, m_k), the phase scaled to cycles.
+template <int NDET, bool MIXED, typename Node>
+__device__ __forceinline__ void cal_nodes(const WinArgs& a, int64_t p, int lane, Node* __restrict__ nd) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  const double* y = a.theta + p * a.stride + a.cal_par;
+  const T* Q = reinterpret_cast<const T*>(a.calQ);
+  const int nn = a.nn;
+  __syncwarp();  // the warp is done with the previous proposal's node data
+  for (int o = lane; o < 2 * NDET * nn; o += 32) {
+    const int sp = o / nn, k = o - sp * nn;
+    const double* ys = y + (int64_t)sp * nn;
+    T m = (T)0;
+    for (int i = 0; i < nn; ++i) m = fma(Q[k * nn + i], (T)__ldg(ys + i), m);
+    const T sc = (sp & 1) ? (T)(0.5 / kPi) : (T)1;
+    T* e = reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k]) + 2 * (sp & 1);
+    e[0] = (T)__ldg(ys + k) * sc;
+    e[1] = m * sc;
+  }
+  __syncwarp();
+}
+
+template <int NDET, bool MIXED, bool CAL, typename Acc, typename Node>
+__device__ __forceinline__ void window_sums(const WinArgs& a, const void* __restrict__ smv, const Node* nodes,
+                                            int64_t p, int j0, int jend, int lane, Acc (&Ud)[NDET],
+                                            Acc (&Vd)[NDET], Acc (&Xd)[NDET]) {
   if constexpr (MIXED) {
-    float U[NDET], V[NDET];
-    // the window's anchor rows follow its delta rows in shared memory
-    const float* sa = reinterpret_cast<const float*>(smv) + (int64_t)a.CH * a.row_elems;
-    anchored_sums<NDET>(reinterpret_cast<const float*>(smv), a.row_elems, sa, a.df,
-                        reinterpret_cast<const PropMixed*>(a.prop) + p, j0, jend, lane, U, V);
+    float U[NDET], V[NDET], X[NDET];
+    // the window's anchor rows follow its delta rows in shared memory, its
+    // calibration rows follow the anchor rows
+    const float* smf = reinterpret_cast<const float*>(smv);
+    const float* sa = smf + (int64_t)a.CH * a.row_elems;
+    anchored_sums_cal<NDET, CAL>(smf, a.row_elems, sa, a.df, reinterpret_cast<const PropMixed*>(a.prop) + p, j0,
+                                 jend, lane, U, V, smf + a.cal_smem, a.cal_row,
+                                 reinterpret_cast<const float4*>(nodes), X);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
       for (int d = 0; d < NDET; ++d) {
         U[d] += __shfl_xor_sync(0xffffffffu, U[d], off);
         V[d] += __shfl_xor_sync(0xffffffffu, V[d], off);
+        if (CAL) X[d] += __shfl_xor_sync(0xffffffffu, X[d], off);
       }
 #pragma unroll
     for (int d = 0; d < NDET; ++d) {
       Ud[d] = U[d];
       Vd[d] = V[d];
+      Xd[d] = CAL ? X[d] : 0.0f;
     }
   } else {
     const double* sm = reinterpret_cast<const double*>(smv);
@@ -305,11 +349,18 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
 #pragma unroll
     for (int d = 0; d < NDET; ++d) tau[d] = P->tau[d];
 #pragma unroll
-    for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = 0.0;
+    for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = Xd[d] = 0.0;
     for (int j = j0 + lane; j < jend; j += 32) {
       double v[RowD<NDET>::n];
       load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
-      bin_f64<NDET>(v, c, tau, Ud, Vd);
+      if constexpr (CAL) {
+        CalBin<NDET, double> cb;
+        cal_eval<NDET>(sm + a.cal_smem + (int64_t)(j - j0) * a.cal_row, reinterpret_cast<const CalNodeD*>(nodes),
+                       cb);
+        bin_f64_cal<NDET>(v, c, tau, cb, Ud, Vd, Xd);
+      } else {
+        bin_f64<NDET>(v, c, tau, Ud, Vd);
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -317,6 +368,7 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
       for (int d = 0; d < NDET; ++d) {
         Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
         Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
+        if (CAL) Xd[d] += __shfl_xor_sync(0xffffffffu, Xd[d], off);
       }
   }
 }
@@ -325,24 +377,28 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
 // combined by all the CTA's threads together at the next window boundary: an
 // FP64 warp instruction costs the pipe the same whether one lane or 32 are
 // active, so one proposal per lane keeps the FP64 work off the bin loop.
-template <int NDET, typename Acc>
+template <int NDET, typename Acc, bool CAL>
 struct Pending {
   int64_t p;
-  Acc U[NDET], V[NDET];
+  Acc U[NDET], V[NDET], X[CAL ? NDET : 1];
 };
 constexpr int kPendCap = 128;
 
 // All threads of the CTA, after a CTA barrier: lnL of the waiting proposals.
-template <int NDET, typename Acc>
-__device__ __forceinline__ void flush_pending(const Pending<NDET, Acc>* pend, int* npend,
+template <int NDET, typename Acc, bool CAL>
+__device__ __forceinline__ void flush_pending(const Pending<NDET, Acc, CAL>* pend, int* npend,
                                               const PropCommon* __restrict__ pc, double* __restrict__ lnl) {
   const int n = *npend < kPendCap ? *npend : kPendCap;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const Pending<NDET, Acc>& q = pend[e];
+    const Pending<NDET, Acc, CAL>& q = pend[e];
     const PropCommon* c = pc + q.p;
     double acc = 0.0;
 #pragma unroll
-    for (int d = 0; d < NDET; ++d) acc += c->Kr[d] * (double)q.U[d] - c->Ki[d] * (double)q.V[d];
+    for (int d = 0; d < NDET; ++d) {
+      const double kr = c->Kr[d], ki = c->Ki[d];
+      acc += kr * (double)q.U[d] - ki * (double)q.V[d];
+      if constexpr (CAL) acc -= 0.5 * (kr * kr + ki * ki) * (double)q.X[d];
+    }
     lnl[q.p] = acc - 0.5 * c->hh;
   }
   __syncthreads();
@@ -352,35 +408,45 @@ __device__ __forceinline__ void flush_pending(const Pending<NDET, Acc>* pend, in
 
 // One thread: copy bins [j0, j1) of the table into shared memory (bulk copy
 // completing on bar); in the mixed path the window's anchor rows follow the
-// delta rows (after CH rows).
-template <bool MIXED>
+// delta rows (after CH rows); with calibration the window's calibration rows
+// follow at element offset cal_smem.
+template <bool MIXED, bool CAL>
 __device__ __forceinline__ void stage_window(const WinArgs& a, void* sm, int j0, int j1, uint64_t* bar) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
   const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
   const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+  uint32_t abytes = 0, cbytes = 0;
+  int a0 = 0;
   if constexpr (MIXED) {
-    const int a0 = j0 / kAnchor, a1 = (j1 + kAnchor - 1) / kAnchor;
-    const uint32_t abytes = (uint32_t)(a1 - a0) * (uint32_t)(kAnchorRowFloats * sizeof(float));
-    mbar_arrive_expect_tx(bar, bytes + abytes);
-    bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
+    a0 = j0 / kAnchor;
+    const int a1 = (j1 + kAnchor - 1) / kAnchor;
+    abytes = (uint32_t)(a1 - a0) * (uint32_t)(kAnchorRowFloats * sizeof(float));
+  }
+  if constexpr (CAL) cbytes = (uint32_t)(j1 - j0) * (uint32_t)a.cal_row * (uint32_t)sizeof(Elem);
+  mbar_arrive_expect_tx(bar, bytes + abytes + cbytes);
+  bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
+  if constexpr (MIXED)
     bulk_g2s(reinterpret_cast<float*>(sm) + (int64_t)a.CH * a.row_elems, a.anchor + (int64_t)a0 * kAnchorRowFloats,
              abytes, bar);
-  } else {
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
-  }
+  if constexpr (CAL)
+    bulk_g2s(reinterpret_cast<Elem*>(sm) + a.cal_smem,
+             reinterpret_cast<const Elem*>(a.cal) + (int64_t)j0 * a.cal_row, cbytes, bar);
 }
 
-template <int NDET, bool MIXED>
+template <int NDET, bool MIXED, bool CAL>
 __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
+  using Node = typename std::conditional<MIXED, float4, CalNodeD>::type;
+  constexpr int S = CAL ? 3 : 2;  // sums per detector in a partial
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const int lane = threadIdx.x & 31;
   using Acc = Elem;  // per-window partial sums: FP32 (mixed) or FP64
-  __shared__ Pending<NDET, Acc> s_pend[kPendCap];
+  __shared__ Pending<NDET, Acc, CAL> s_pend[kPendCap];
   __shared__ int s_npend;
+  __shared__ __align__(32) Node s_nodes[CAL ? 8 * NDET * kMaxCalNodes : 1];
+  Node* nodes = s_nodes + (CAL ? (threadIdx.x >> 5) * NDET * kMaxCalNodes : 0);
 
   // Window 0 of the table does not depend on the prologue: its copy starts
   // before the wait (the prologue lets this grid launch early), and most CTAs
@@ -389,7 +455,7 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
     s_npend = 0;
     mbar_init(&bar, 1);
     fence_mbar_init();
-    stage_window<MIXED>(a, sm, 0, a.CH < a.M ? (int)a.CH : (int)a.M, &bar);
+    stage_window<MIXED, CAL>(a, sm, 0, a.CH < a.M ? (int)a.CH : (int)a.M, &bar);
   }
   bool w0_pending = true;  // the copy of window 0 (phase 0 of the barrier) is in flight
   uint32_t parity = 0;
@@ -410,7 +476,7 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
     int* ctr = a.work + 1 + w;
     // every warp is done with the previous window; a window whose proposals are all taken is skipped
     const bool drained = __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
-    if (s_npend > 0) flush_pending<NDET, Acc>(s_pend, &s_npend, a.pc, a.lnl);
+    if (s_npend > 0) flush_pending<NDET, Acc, CAL>(s_pend, &s_npend, a.pc, a.lnl);
     if (!drained) {
       if (w0_pending) {  // window 0's copy: use it, or let it land before staging another window
         if (!mbar_wait_bounded(&bar, parity, a.status)) return;
@@ -421,14 +487,15 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
       if (w != 0) {
         if (threadIdx.x == 0) {
           fence_proxy_async_smem();
-          stage_window<MIXED>(a, sm, j0, j1, &bar);
+          stage_window<MIXED, CAL>(a, sm, j0, j1, &bar);
         }
         if (!mbar_wait_bounded(&bar, parity, a.status)) return;
         parity ^= 1u;
       }
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
-        Acc U[NDET], V[NDET];
-        window_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, U, V);
+        Acc U[NDET], V[NDET], X[NDET];
+        if constexpr (CAL) cal_nodes<NDET, MIXED>(a, p, lane, nodes);
+        window_sums<NDET, MIXED, CAL>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, U, V, X);
         const int nwp = (ncut + a.CH - 1) / a.CH;
         if (nwp == 1) {  // the proposal's only window: queue it for the CTA's next combination
           int slot = 0;
@@ -441,10 +508,11 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
               for (int d = 0; d < NDET; ++d) {
                 s_pend[slot].U[d] = U[d];
                 s_pend[slot].V[d] = V[d];
+                if constexpr (CAL) s_pend[slot].X[d] = X[d];
               }
             }
           } else {  // queue full: combine here
-            const double l = combine_lnl<NDET>(a.pc + p, U, V, lane);
+            const double l = combine_lnl<NDET, CAL>(a.pc + p, U, V, X, lane);
             if (lane == 0) a.lnl[p] = l;
           }
           return;
@@ -452,11 +520,12 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
         // several windows: publish this one; the warp that closes the last one combines
         int done = 0;
         if (lane == 0) {
-          Acc* o = reinterpret_cast<Acc*>(a.partials) + (p * a.nw_total + w) * (2 * NDET);
+          Acc* o = reinterpret_cast<Acc*>(a.partials) + (p * a.nw_total + w) * (S * NDET);
 #pragma unroll
           for (int d = 0; d < NDET; ++d) {
-            o[2 * d] = U[d];
-            o[2 * d + 1] = V[d];
+            o[S * d] = U[d];
+            o[S * d + 1] = V[d];
+            if constexpr (CAL) o[S * d + 2] = X[d];
           }
           __threadfence();
           done = atomicAdd(&a.pdone[p], 1);
@@ -466,15 +535,16 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
         __threadfence();
         // lanes take windows lane, lane + 32, ...; a fixed shuffle tree then sums
         // the lanes (FP64, the same order whichever warp closes the proposal)
-        const Acc* q = reinterpret_cast<const Acc*>(a.partials) + p * a.nw_total * (2 * NDET);
-        double Ud[NDET], Vd[NDET];
+        const Acc* q = reinterpret_cast<const Acc*>(a.partials) + p * a.nw_total * (S * NDET);
+        double Ud[NDET], Vd[NDET], Xd[NDET];
 #pragma unroll
-        for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = 0.0;
+        for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = Xd[d] = 0.0;
         for (int v = lane; v < nwp; v += 32)
 #pragma unroll
           for (int d = 0; d < NDET; ++d) {
-            Ud[d] += (double)__ldcg(&q[v * (2 * NDET) + 2 * d]);
-            Vd[d] += (double)__ldcg(&q[v * (2 * NDET) + 2 * d + 1]);
+            Ud[d] += (double)__ldcg(&q[v * (S * NDET) + S * d]);
+            Vd[d] += (double)__ldcg(&q[v * (S * NDET) + S * d + 1]);
+            if constexpr (CAL) Xd[d] += (double)__ldcg(&q[v * (S * NDET) + S * d + 2]);
           }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
@@ -482,15 +552,16 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
           for (int d = 0; d < NDET; ++d) {
             Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
             Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
+            if constexpr (CAL) Xd[d] += __shfl_xor_sync(0xffffffffu, Xd[d], off);
           }
-        const double l = combine_lnl<NDET>(a.pc + p, Ud, Vd, lane);
+        const double l = combine_lnl<NDET, CAL>(a.pc + p, Ud, Vd, Xd, lane);
         if (lane == 0) a.lnl[p] = l;
       });
     }
     n_w -= __ldcg(&a.hist[w]);
   }
   __syncthreads();
-  if (s_npend > 0) flush_pending<NDET, Acc>(s_pend, &s_npend, a.pc, a.lnl);
+  if (s_npend > 0) flush_pending<NDET, Acc, CAL>(s_pend, &s_npend, a.pc, a.lnl);
   if (w0_pending) mbar_wait_bounded(&bar, parity, a.status);  // no copy may outlive the CTA
 }
 
@@ -535,7 +606,7 @@ static int window_of(const gwl_ctx* c, int precision) {
 int64_t partials_needed(const gwl_ctx* c, int64_t B) {
   const int CH = window_of(c, c->opt.precision);
   const int64_t nw = (c->M + CH - 1) / CH;
-  return B * nw * 2 * c->n_det;
+  return B * nw * sums_per_det(c) * c->n_det;
 }
 
 // Windows of the likelihood or the gradient bin loop, whichever has more.
@@ -550,11 +621,11 @@ static int64_t nw_max(const gwl_ctx* c) {
 int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + B; }
 int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
 
-template <int NDET, bool MIXED>
+template <int NDET, bool MIXED, bool CAL>
 static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, bool pdl, cudaStream_t st) {
   static size_t smem_set = 0;  // per template instance: raise the dynamic shared-memory limit when it grows
   if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_window<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_window<NDET, MIXED, CAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     smem_set = smem;
@@ -562,9 +633,9 @@ static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t sme
   ProfScope ps(c, GWL_KERNEL_BINS, st);
   cudaError_t e;
   if (pdl) {
-    e = launch_pdl(k_window<NDET, MIXED>, dim3(grid), dim3(256), smem, st, a);
+    e = launch_pdl(k_window<NDET, MIXED, CAL>, dim3(grid), dim3(256), smem, st, a);
   } else {
-    k_window<NDET, MIXED><<<grid, 256, smem, st>>>(a);
+    k_window<NDET, MIXED, CAL><<<grid, 256, smem, st>>>(a);
     e = cudaGetLastError();
   }
   c->launches++;
@@ -591,8 +662,8 @@ static cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, i
 
 // The bin loop (which also forms lnL) of rows [off, off + B) of the batch.
 template <int NDET>
-static cudaError_t launch_bins(gwl_ctx* c, int64_t B, int64_t off, double* lnl, int* work, bool pdl,
-                               cudaStream_t st) {
+static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64_t off, double* lnl, int* work,
+                               bool pdl, cudaStream_t st) {
   const bool mixed = c->opt.precision == GWL_MIXED;
   const int CH = window_of(c, c->opt.precision);
   const int nw_total = (int)((c->M + CH - 1) / CH);
@@ -607,20 +678,42 @@ static cudaError_t launch_bins(gwl_ctx* c, int64_t B, int64_t off, double* lnl, 
   a.nw_total = nw_total;
   a.pc = c->d_pc + off;
   a.prop = mixed ? (const void*)(c->d_pm + off) : (const void*)(c->d_pf + off);
+  const bool cal = c->n_cal_nodes > 0;
   a.partials = reinterpret_cast<char*>(c->d_partials) +
-               off * nw_total * 2 * NDET * (int64_t)(mixed ? sizeof(float) : sizeof(double));
+               off * nw_total * sums_per_det(c) * NDET * (int64_t)(mixed ? sizeof(float) : sizeof(double));
   a.work = work;
   a.hist = work + 1 + nw_max(c);
   a.pdone = work + 1 + 2 * nw_max(c);
   a.lnl = lnl;
   a.status = c->d_status;
-  const size_t smem = (size_t)CH * a.row_elems * (mixed ? sizeof(float) : sizeof(double)) +
-                      (mixed ? (size_t)((CH + kAnchor - 1) / kAnchor) * kAnchorRowFloats * sizeof(float) : 0);
+  // shared memory (elements): the window's rows, [mixed] its anchor rows, [calibration] its calibration rows
+  int64_t elems = (int64_t)CH * a.row_elems;
+  if (mixed) elems += (int64_t)((CH + kAnchor - 1) / kAnchor) * kAnchorRowFloats;
+  a.cal = nullptr;
+  a.cal_row = 0;
+  a.cal_smem = (int)elems;
+  a.theta = nullptr;
+  a.stride = theta_stride(c);
+  a.cal_par = c->opt.n_dim;
+  a.nn = c->n_cal_nodes;
+  a.calQ = nullptr;
+  if (cal) {
+    a.cal = mixed ? (const void*)c->d_cal_f : (const void*)c->d_cal_d;
+    a.cal_row = mixed ? c->row_cal_f : c->row_cal_d;
+    a.theta = theta;
+    a.calQ = mixed ? (const void*)c->d_calQ_f : (const void*)c->d_calQ_d;
+    elems += (int64_t)CH * a.cal_row;
+  }
+  const size_t smem = (size_t)elems * (mixed ? sizeof(float) : sizeof(double));
   // enough CTAs for every warp of a window to find a proposal, at most a full wave
   const int64_t want = ((B + 7) / 8) * nw_total;
   int grid = c->num_sms * c->ctas_per_sm;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
-  return mixed ? run_window<NDET, true>(c, a, grid, smem, pdl, st) : run_window<NDET, false>(c, a, grid, smem, pdl, st);
+  if (cal)
+    return mixed ? run_window<NDET, true, true>(c, a, grid, smem, pdl, st)
+                 : run_window<NDET, false, true>(c, a, grid, smem, pdl, st);
+  return mixed ? run_window<NDET, true, false>(c, a, grid, smem, pdl, st)
+               : run_window<NDET, false, false>(c, a, grid, smem, pdl, st);
 }
 
 // Prologue (per-proposal coefficients, FP64) then the windowed bin loop, which
@@ -630,7 +723,7 @@ template <int NDET>
 static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
   if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st);
-  if (e == cudaSuccess) e = launch_bins<NDET>(c, B, 0, lnl, c->d_work, true, st);
+  if (e == cudaSuccess) e = launch_bins<NDET>(c, theta, B, 0, lnl, c->d_work, true, st);
   return e;
 }
 

@@ -390,6 +390,12 @@ void multi_delete(Multi* m) {
 }
 
 int64_t multi_launches(const Multi* m) { return m ? m->launches : 0; }
+bool multi_has_calibration(const Multi* m) {
+  if (!m) return false;
+  for (int e = 0; e < m->E; ++e)
+    if (m->ctxs[e]->n_cal_nodes) return true;
+  return false;
+}
 int multi_events(const Multi* m) { return m->E; }
 int multi_dim(const Multi* m) { return m->D; }
 gwl_ctx* multi_ctx(const Multi* m, int e) { return m->ctxs[e]; }

@@ -71,20 +71,21 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
   auto candidates = [&](size_t row) {
     std::vector<int> ws;
     for (int w = 128; w <= 1536; w += 64) {
-      if ((size_t)w * row > 200 * 1024) break;
+      if ((size_t)w * row > gwl::kWindowSmemMax) break;
       if (w >= c->M) {  // windows at least as long as the segment are all the same shape
         ws.push_back(w);
         break;
       }
       const int64_t nw = (c->M + w - 1) / w;
-      if (B * nw * 2 * c->n_det * (int64_t)sizeof(double) > ((int64_t)2 << 30)) continue;
+      if (B * nw * gwl::sums_per_det(c) * c->n_det * (int64_t)sizeof(double) > ((int64_t)2 << 30)) continue;
       ws.push_back(w);
     }
     return ws;
   };
   const bool mixed = c->opt.precision == GWL_MIXED;
-  const std::vector<int> windows =
-      candidates(mixed ? sizeof(float) * c->row_delta : sizeof(double) * c->row_doubles);
+  if ((what & GWL_TUNE_GRAD) && c->n_cal_nodes)
+    return gwl::set_error(GWL_ERR_ARG, "autotune: gwl_grad is not available with the calibration model");
+  const std::vector<int> windows = candidates(gwl::lnl_row_bytes(c));
   const std::vector<int> gwindows =
       candidates(mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles);
   if (windows.empty() || gwindows.empty()) return gwl::set_error(GWL_ERR_ARG, "autotune: no window fits");

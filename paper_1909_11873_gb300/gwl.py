@@ -27,7 +27,7 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
            "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
-           "gwl_get_tuning", "gwl_autotune")
+           "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration")
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
         L.gwl_set_tuning.argtypes = [P, C.POINTER(GwlTuning)]
         L.gwl_get_tuning.argtypes = [P, C.POINTER(GwlTuning)]
         L.gwl_autotune.argtypes = [P, P, i64, i32, C.POINTER(GwlTuning), P]
+        L.gwl_set_calibration.argtypes = [P, i32, P]
+        L.gwl_get_calibration.argtypes = [P, C.POINTER(i32), C.POINTER(i64)]
         L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
         L.gwl_profile_read.argtypes = [P, i32, C.POINTER(d), C.POINTER(i64)]
@@ -274,6 +276,24 @@ class Context:
         _check(lib().gwl_autotune(self._h, _ptr(theta), theta.shape[0], int(what), C.byref(t), _stream(stream)),
                "gwl_autotune")
         return t.as_dict()
+
+    def gwl_set_calibration(self, node_freqs):
+        """Calibration model at these node frequencies [Hz] (empty: off); rows of theta then hold
+        n_dim + 2 n_nodes n_det values (per detector dA at the nodes, then dphi)."""
+        nf = np.ascontiguousarray(node_freqs, dtype=np.float64).ravel()
+        _check(lib().gwl_set_calibration(self._h, nf.size, nf.ctypes.data if nf.size else None),
+               "gwl_set_calibration")
+
+    def gwl_get_calibration(self):
+        """(calibration nodes, doubles per row of theta)."""
+        n = C.c_int()
+        st = C.c_int64()
+        _check(lib().gwl_get_calibration(self._h, C.byref(n), C.byref(st)), "gwl_get_calibration")
+        return n.value, st.value
+
+    @property
+    def theta_stride(self) -> int:
+        return self.gwl_get_calibration()[1]
 
     def gwl_profile(self, enable: bool):
         _check(lib().gwl_profile(self._h, int(bool(enable))), "gwl_profile")
