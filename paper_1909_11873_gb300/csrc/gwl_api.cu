@@ -592,8 +592,8 @@ int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs) {
       return fail(GWL_ERR_ARG, "node_freqs must increase strictly (at %d)", k);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError(), "gwl_set_calibration");
-  dev_free(c, c->d_cal_f, c->M * c->row_cal_f);
-  dev_free(c, c->d_cal_d, c->M * c->row_cal_d);
+  dev_free(c, c->d_cal_f, (c->M + 1) * c->row_cal_f);
+  dev_free(c, c->d_cal_d, (c->M + 1) * c->row_cal_d);
   dev_free(c, c->d_calQ_f, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
   dev_free(c, c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
   c->n_cal_nodes = 0;
@@ -610,8 +610,8 @@ int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs) {
   double* d_x = nullptr;
   cudaError_t e;
   do {
-    if ((e = dev_alloc(c, &c->d_cal_f, c->M * c->row_cal_f)) != cudaSuccess) break;
-    if ((e = dev_alloc(c, &c->d_cal_d, c->M * c->row_cal_d)) != cudaSuccess) break;
+    if ((e = dev_alloc(c, &c->d_cal_f, (c->M + 1) * c->row_cal_f)) != cudaSuccess) break;
+    if ((e = dev_alloc(c, &c->d_cal_d, (c->M + 1) * c->row_cal_d)) != cudaSuccess) break;
     if ((e = dev_alloc(c, &c->d_calQ_f, gwl::kMaxCalNodes * gwl::kMaxCalNodes)) != cudaSuccess) break;
     if ((e = dev_alloc(c, &c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes)) != cudaSuccess) break;
     if ((e = cudaMalloc(&d_x, sizeof(double) * n_nodes)) != cudaSuccess) break;
@@ -691,8 +691,8 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_tab_delta, c->M * c->row_delta);
   dev_free(c, c->d_anchor, (c->M + gwl::kAnchor - 1) / gwl::kAnchor * gwl::kAnchorRowFloats);
   dev_free(c, c->d_tab_f64, c->M * c->row_doubles);
-  dev_free(c, c->d_cal_f, c->M * c->row_cal_f);
-  dev_free(c, c->d_cal_d, c->M * c->row_cal_d);
+  dev_free(c, c->d_cal_f, (c->M + 1) * c->row_cal_f);
+  dev_free(c, c->d_cal_d, (c->M + 1) * c->row_cal_d);
   dev_free(c, c->d_calQ_f, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
   dev_free(c, c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
   dev_free(c, c->d_pm, c->prop_cap);

@@ -132,36 +132,51 @@ struct CalBin {
   T A[NDET], P[NDET], H[NDET];
 };
 
+// Spline weights of a bin from its row [t, h^2/6, k, dH_d ...]:
+//   (1 - t, t, h^2/6 (1 - t)((1 - t)^2 - 1), h^2/6 t (t^2 - 1)).
+template <int NDET, typename T>
+__device__ __forceinline__ void cal_weights(const T (&r)[2 * ((3 + NDET + 1) / 2)], T (&w)[4]) {
+  const T t = r[0], h6 = r[1], a = (T)1 - t;
+  w[0] = a;
+  w[1] = t;
+  w[2] = h6 * a * fma(a, a, (T)-1);
+  w[3] = h6 * t * fma(t, t, (T)-1);
+}
+
 template <int NDET>
 __device__ __forceinline__ void cal_eval(const float* __restrict__ crow, const float4* __restrict__ nodes,
                                          CalBin<NDET, float>& cb) {
-  const float4 w = reinterpret_cast<const float4*>(crow)[0];
-  const float4 r1 = reinterpret_cast<const float4*>(crow)[1];
-  const int k = __float_as_int(r1.x);
-  float hx[4] = {r1.y, r1.z, r1.w, 0.0f};
-  if constexpr (NDET > 3) hx[3] = crow[8];
+  constexpr int NP = (3 + NDET + 1) / 2;  // 8-byte pairs per row
+  float r[2 * NP], w[4];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) *reinterpret_cast<float2*>(&r[2 * i]) = reinterpret_cast<const float2*>(crow)[i];
+  cal_weights<NDET>(r, w);
+  const int k = __float_as_int(r[2]);
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     const float4 n0 = nodes[d * kMaxCalNodes + k], n1 = nodes[d * kMaxCalNodes + k + 1];
-    cb.A[d] = fmaf(w.x, n0.x, fmaf(w.y, n1.x, fmaf(w.z, n0.y, w.w * n1.y)));
-    cb.P[d] = fmaf(w.x, n0.z, fmaf(w.y, n1.z, fmaf(w.z, n0.w, w.w * n1.w)));
-    cb.H[d] = hx[d];
+    cb.A[d] = fmaf(w[0], n0.x, fmaf(w[1], n1.x, fmaf(w[2], n0.y, w[3] * n1.y)));
+    cb.P[d] = fmaf(w[0], n0.z, fmaf(w[1], n1.z, fmaf(w[2], n0.w, w[3] * n1.w)));
+    cb.H[d] = r[3 + d];
   }
 }
 
 template <int NDET>
 __device__ __forceinline__ void cal_eval(const double* __restrict__ crow, const CalNodeD* __restrict__ nodes,
                                          CalBin<NDET, double>& cb) {
-  const double2 w01 = reinterpret_cast<const double2*>(crow)[0];
-  const double2 w23 = reinterpret_cast<const double2*>(crow)[1];
-  const int k = (int)crow[4];
+  constexpr int NP = (3 + NDET + 1) / 2;
+  double r[2 * NP], w[4];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) *reinterpret_cast<double2*>(&r[2 * i]) = reinterpret_cast<const double2*>(crow)[i];
+  cal_weights<NDET>(r, w);
+  const int k = (int)r[2];
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
     const CalNodeD& n0 = nodes[d * kMaxCalNodes + k];
     const CalNodeD& n1 = nodes[d * kMaxCalNodes + k + 1];
-    cb.A[d] = fma(w01.x, n0.v[0], fma(w01.y, n1.v[0], fma(w23.x, n0.v[1], w23.y * n1.v[1])));
-    cb.P[d] = fma(w01.x, n0.v[2], fma(w01.y, n1.v[2], fma(w23.x, n0.v[3], w23.y * n1.v[3])));
-    cb.H[d] = crow[5 + d];
+    cb.A[d] = fma(w[0], n0.v[0], fma(w[1], n1.v[0], fma(w[2], n0.v[1], w[3] * n1.v[1])));
+    cb.P[d] = fma(w[0], n0.v[2], fma(w[1], n1.v[2], fma(w[2], n0.v[3], w[3] * n1.v[3])));
+    cb.H[d] = r[3 + d];
   }
 }
 

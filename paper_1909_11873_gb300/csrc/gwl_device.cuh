@@ -57,14 +57,17 @@ constexpr int kAnchorRowFloats = 28;
 // and second derivatives m is
 //   S(x) = (1 - t) y_k + t y_{k+1} + w_c m_k + w_e m_{k+1},
 //   w_c = h^2/6 ((1 - t)^3 - (1 - t)),  w_e = h^2/6 (t^3 - t),
-// so a bin needs four weights and k, shared by every spline, and a proposal
+// so a bin needs t, h^2/6 and k, shared by every spline, and a proposal
 // needs (y, m) per node, with m = Q y for a fixed n_nodes x n_nodes matrix Q
-// of the node layout.  Calibration rows: [1 - t, t, w_c, w_e, k, dH_d x n_det]
-// (dH_d,j = H_d[j] - H_d[j-1], the bin's <h|h> weight), float or double,
-// padded to an odd number of 16-byte units like the other tables.
+// of the node layout.  Calibration rows: [t, h^2/6, k, dH_d x n_det]
+// (dH_d,j = H_d[j] - H_d[j-1], the bin's <h|h> weight), float rows in whole
+// 8-byte pairs (24 bytes for 2-3 detectors: three 64-bit loads per bin without
+// bank conflicts), double rows padded to an odd number of 16-byte units.  A
+// table holds one zero row past the last bin, because float rows are staged in
+// pairs (a bulk copy moves whole 16-byte units).
 constexpr int kMaxCalNodes = 16;
-__host__ __device__ constexpr int cal_row_floats(int ndet) { return 4 * odd_units((5 + ndet + 3) / 4); }
-__host__ __device__ constexpr int cal_row_doubles(int ndet) { return 2 * odd_units((5 + ndet + 1) / 2); }
+__host__ __device__ constexpr int cal_row_floats(int ndet) { return 2 * ((3 + ndet + 1) / 2); }
+__host__ __device__ constexpr int cal_row_doubles(int ndet) { return 2 * odd_units((3 + ndet + 1) / 2); }
 // Per-warp node data of the proposal being summed: (dA_k, m^A_k, dphi_k,
 // m^phi_k) per detector and node, the phase values in cycles.
 struct alignas(32) CalNodeD {

@@ -422,7 +422,8 @@ __device__ __forceinline__ void stage_window(const WinArgs& a, void* sm, int j0,
     const int a1 = (j1 + kAnchor - 1) / kAnchor;
     abytes = (uint32_t)(a1 - a0) * (uint32_t)(kAnchorRowFloats * sizeof(float));
   }
-  if constexpr (CAL) cbytes = (uint32_t)(j1 - j0) * (uint32_t)a.cal_row * (uint32_t)sizeof(Elem);
+  // calibration rows in pairs: a bulk copy moves whole 16-byte units (the table has a row past the last bin)
+  if constexpr (CAL) cbytes = (uint32_t)((j1 - j0 + 1) & ~1) * (uint32_t)a.cal_row * (uint32_t)sizeof(Elem);
   mbar_arrive_expect_tx(bar, bytes + abytes + cbytes);
   bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
   if constexpr (MIXED)
@@ -702,7 +703,7 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
     a.cal_row = mixed ? c->row_cal_f : c->row_cal_d;
     a.theta = theta;
     a.calQ = mixed ? (const void*)c->d_calQ_f : (const void*)c->d_calQ_d;
-    elems += (int64_t)CH * a.cal_row;
+    elems += (int64_t)(CH + 1) * a.cal_row;  // rows are staged in pairs
   }
   const size_t smem = (size_t)elems * (mixed ? sizeof(float) : sizeof(double));
   // enough CTAs for every warp of a window to find a proposal, at most a full wave

@@ -154,8 +154,9 @@ cudaError_t launch_scale_tables(gwl_ctx* c, double sg, cudaStream_t st) {
 }
 
 // Calibration rows (layout in gwl_device.cuh): bin j's interval k of the
-// nodes xn (ln f_k) -- the first or last interval outside them -- its spline
-// weights and the per-detector <h|h> weights dH_d,j of the (scaled) prefix sums.
+// nodes xn (ln f_k) -- the first or last interval outside them -- its local
+// coordinate t and h^2/6, and the per-detector <h|h> weights dH_d,j of the
+// (scaled) prefix sums.
 __global__ void k_cal_rows(const double* __restrict__ freqs, const double* __restrict__ H, int64_t M, int n_det,
                            const double* __restrict__ xn, int nn, float* __restrict__ cf, int row_f,
                            double* __restrict__ cd, int row_d) {
@@ -165,28 +166,31 @@ __global__ void k_cal_rows(const double* __restrict__ freqs, const double* __res
   int k = 0;
   while (k < nn - 2 && x >= xn[k + 1]) ++k;
   const double h = xn[k + 1] - xn[k];
-  const double a = (xn[k + 1] - x) / h, t = (x - xn[k]) / h;
+  const double t = (x - xn[k]) / h;
   const double h6 = h * h / 6.0;
-  const double w[4] = {a, t, h6 * (a * a * a - a), h6 * (t * t * t - t)};
   double* rd = cd + j * row_d;
   float* rf = cf + j * row_f;
-  for (int i = 0; i < 4; ++i) {
-    rd[i] = w[i];
-    rf[i] = (float)w[i];
-  }
-  rd[4] = (double)k;
-  rf[4] = __int_as_float(k);
+  rd[0] = t;
+  rd[1] = h6;
+  rd[2] = (double)k;
+  rf[0] = (float)t;
+  rf[1] = (float)h6;
+  rf[2] = __int_as_float(k);
   for (int d = 0; d < n_det; ++d) {
     const double dh = H[(int64_t)d * M + j] - (j > 0 ? H[(int64_t)d * M + j - 1] : 0.0);
-    rd[5 + d] = dh;
-    rf[5 + d] = (float)dh;
+    rd[3 + d] = dh;
+    rf[3 + d] = (float)dh;
   }
-  for (int i = 5 + n_det; i < row_d; ++i) rd[i] = 0.0;
-  for (int i = 5 + n_det; i < row_f; ++i) rf[i] = 0.0f;
+  for (int i = 3 + n_det; i < row_d; ++i) rd[i] = 0.0;
+  for (int i = 3 + n_det; i < row_f; ++i) rf[i] = 0.0f;
 }
 
 cudaError_t launch_cal_tables(gwl_ctx* c, const double* d_xnode, cudaStream_t st) {
   const int T = 256;
+  // the zero row past the last bin
+  cudaError_t e = cudaMemsetAsync(c->d_cal_f + c->M * c->row_cal_f, 0, sizeof(float) * c->row_cal_f, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_cal_d + c->M * c->row_cal_d, 0, sizeof(double) * c->row_cal_d, st);
+  if (e != cudaSuccess) return e;
   k_cal_rows<<<(unsigned)((c->M + T - 1) / T), T, 0, st>>>(c->d_freqs, c->d_H, c->M, c->n_det, d_xnode,
                                                             c->n_cal_nodes, c->d_cal_f, c->row_cal_f, c->d_cal_d,
                                                             c->row_cal_d);

@@ -1,6 +1,7 @@
 """Run one workload through the library a fixed number of times (for profilers such as ncu).
 
   python -m paper_1909_11873_gb300.profile_run --config c2 --precision mixed --iters 5 [--entry loglike|grad]
+      [--cal N]   (likelihood with the calibration model, N nodes per detector over the band)
 
 The event is synthetic and seeded; its injection is produced by the library's
 own template, so no test infrastructure is involved.
@@ -52,6 +53,7 @@ def main():
     ap.add_argument("--time", action="store_true", help="report device-timed evals/s (L2 flushed between calls)")
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--cal", type=int, default=0, help="calibration nodes per detector (0: off)")
     a = ap.parse_args()
     import torch
 
@@ -61,8 +63,14 @@ def main():
     build.build()
     ev = device_event(a.config, a.seed)
     B = a.batch or I.CONFIGS[a.config]["batch"]
-    th = torch.from_numpy(I.reduced(I.proposals(ev, B, a.seed), ev.sampling)).cuda()
     ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED if a.precision == "mixed" else gwl.GWL_FP64)
+    if a.cal:
+        full = I.calibrated_proposals(ev, B, a.seed, n_nodes=a.cal)
+        rows = np.concatenate([I.reduced(full[:, :11], ev.sampling), full[:, 11:]], axis=1)
+        ctx.gwl_set_calibration(I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1]), a.cal))
+    else:
+        rows = I.reduced(I.proposals(ev, B, a.seed), ev.sampling)
+    th = torch.from_numpy(np.ascontiguousarray(rows)).cuda()
     ctx.gwl_set_tuning(window=a.window, ctas_per_sm=a.ctas)
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     grad = torch.empty_like(th)
@@ -76,7 +84,7 @@ def main():
         call()
     torch.cuda.synchronize()
     ctx.gwl_sync()
-    msg = (f"{a.config} {a.precision} {a.entry} B={B} window={a.window} ctas={a.ctas} "
+    msg = (f"{a.config} {a.precision} {a.entry} cal={a.cal} B={B} window={a.window} ctas={a.ctas} "
            f"iters={a.iters} lnL[0]={out[0].item():.6f}")
     if a.time:
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")

@@ -40,6 +40,23 @@ def main():
             line.append(f"{'fp64' if prec == 0 else 'mixed'} max {d.max():.2e} median {np.median(d):.2e} "
                         f"max rel {np.max(d / np.maximum(np.abs(ref), 1.0)):.2e}")
         print("; ".join(line), flush=True)
+    # the calibration model (ten nodes per detector over the band)
+    for name, (B, n) in {"c1": (1024, 1024), "c2": (8192, 1024), "c3": (2048, 24)}.items():
+        ev = event(name)
+        th = I.calibrated_proposals(ev, B, 4)
+        nodes = I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1]))
+        idx = np.random.default_rng(1).choice(B, n, replace=False)
+        ref = oracle.loglike_cal(ev, nodes, th[idx])
+        rows_dev = np.ascontiguousarray(np.concatenate([I.reduced(th[:, :11], ev.sampling), th[:, 11:]], axis=1))
+        line = [f"{name} calibrated ({rows_dev.shape[1]} parameters per row): B={B}, rows compared {n}"]
+        for prec in (0, 1):
+            ctx = gwl.Context.from_event(ev, prec)
+            ctx.gwl_set_calibration(nodes)
+            got = gwl.loglike(ctx, torch.from_numpy(rows_dev).cuda()).cpu().numpy()[idx]
+            ctx.gwl_sync()
+            d = np.abs(got - ref)
+            line.append(f"{'fp64' if prec == 0 else 'mixed'} max {d.max():.2e} median {np.median(d):.2e}")
+        print("; ".join(line), flush=True)
 
 
 if __name__ == "__main__":
