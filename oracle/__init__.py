@@ -61,6 +61,12 @@ def _L():
             _lib.oracle_grad.argtypes = [P, i64, P, P, P, i32, d, d, i32, P, i64, P, P, i32]
             _lib.oracle_loglike_cal.argtypes = [P, i64, P, P, P, i32, d, d, i32, i32, P, P, i64, P, i32]
             _lib.oracle_cal_spline.argtypes = [i32, P, P, i64, P, P]
+            _lib.oracle_inv_normal_cdf.argtypes = [i64, P, P]
+            _lib.oracle_ns_replace_cal.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
+                                                   + [i32, P, P]
+                                                   + [P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, i32])
+            _lib.oracle_ns_run_cal.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
+                                               + [i32, P, P, i64, i64, i32, u64, d, i64, d, P, i32])
             _lib.oracle_philox.argtypes = [P, P, P]
             _lib.oracle_prior_transform.argtypes = [i32, P, P, P, P, P, P, P, i64, P]
             _lib.oracle_ns_replace.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
@@ -241,6 +247,57 @@ def ns_run(ev, smp, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, s
         n = min(int(res[3]), max_dead)
         out.update(dead_lnl=dl[:n], dead_logwt=dw[:n], dead_u=du[:n])
     return out
+
+
+def inv_normal_cdf(u) -> np.ndarray:
+    """The oracle's standard normal quantile Phi^{-1}(u)."""
+    uu = _f64(u).ravel()
+    out = np.zeros(uu.size)
+    _L().oracle_inv_normal_cdf(uu.size, _p(uu), _p(out))
+    return out
+
+
+def _cal_args(ev, cal):
+    """cal = (node_freqs, sigma_amp, sigma_phase) -> (keep, args, calibration coordinates)."""
+    nf = _f64(cal[0])
+    sig = _f64([cal[1], cal[2]])
+    n_det = np.asarray(ev.geom).shape[0]
+    return (nf, sig), [nf.size, _p(nf), _p(sig)], 2 * nf.size * n_det
+
+
+def ns_replace_cal(ev, smp, cal, live_u, live_lnl, worst, lnl_star, seed, counter, n_chains, walk_len, scale, chol,
+                   n_threads: int | None = None):
+    """ns_replace with the calibration model: walk coordinates are the sampled source coordinates followed by
+    the calibration parameters (zero-mean Gaussian priors); cal = (node_freqs, sigma_amp, sigma_phase)."""
+    k3, c, nc = _cal_args(ev, cal)
+    D = len(smp.param_map) + nc
+    lu = _f64(live_u).reshape(-1, D)
+    ll = _f64(live_lnl)
+    ch = _f64(chol).reshape(D, D)
+    ou = np.zeros((n_chains, D))
+    ol = np.zeros(n_chains)
+    on = np.zeros(n_chains, dtype=np.int32)
+    os_ = np.zeros(n_chains, dtype=np.int32)
+    k1, a = _ev_args(ev)
+    k2, b = _smp_args(smp)
+    rc = _L().oracle_ns_replace_cal(*a, *b, *c, _p(lu), _p(ll), lu.shape[0], int(worst), float(lnl_star),
+                                    int(seed), int(counter), int(n_chains), int(walk_len), float(scale), _p(ch),
+                                    _p(ou), _p(ol), _p(on), _p(os_), n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_ns_replace_cal: bad arguments")
+    return ou, ol, on, os_
+
+
+def ns_run_cal(ev, smp, cal, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0,
+               n_threads: int | None = None):
+    """Plain static parallel nested sampling on the calibrated GW likelihood."""
+    res = np.zeros(9)
+    k3, c, nc = _cal_args(ev, cal)
+    k1, a = _ev_args(ev)
+    k2, b = _smp_args(smp)
+    _L().oracle_ns_run_cal(*a, *b, *c, int(K), int(n_chains), int(walk_len), int(seed), float(dlogz),
+                           int(max_rounds), float(scale0), _p(res), n_threads or default_threads())
+    return dict(zip(NS_KEYS, res.tolist()))
 
 
 def ns_run_gauss(D, mu, sigma, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0,

@@ -795,6 +795,60 @@ UnitLike gauss_like(int D, const double* mu, double sigma) {
   };
 }
 
+// Phi^{-1}(u) for the standard normal: the root of Phi(x) = u, bracketed by
+// bisection and polished by Newton steps x <- x - F(x) / phi(x) until they
+// stop shrinking.  u > 1/2 uses Phi^{-1}(u) = -Phi^{-1}(1 - u) (1 - u is exact
+// there), so the root is negative; F is written so that it has no rounding
+// floor near the root: F(x) = erfc(-x / sqrt 2) / 2 - p in the tail (p < 1/4),
+// and F(x) = erf(x / sqrt 2) / 2 - (p - 1/2) near the centre (p - 1/2 is
+// exact for p >= 1/4, and erf is accurate relative to its small values).
+double inv_normal_cdf(double u) {
+  if (!(u > 0.0)) return -std::numeric_limits<double>::infinity();
+  if (!(u < 1.0)) return std::numeric_limits<double>::infinity();
+  if (u == 0.5) return 0.0;
+  const bool upper = u > 0.5;
+  const double p = upper ? 1.0 - u : u;  // in (0, 1/2): the root is negative
+  const bool centre = p >= 0.25;
+  const double pc = p - 0.5;
+  auto F = [centre, p, pc](double x) {
+    return centre ? 0.5 * std::erf(x / std::sqrt(2.0)) - pc : 0.5 * std::erfc(-x / std::sqrt(2.0)) - p;
+  };
+  double a = -40.0, b = 0.0;
+  for (int i = 0; i < 40; ++i) {
+    const double m = 0.5 * (a + b);
+    if (F(m) < 0.0) a = m;
+    else b = m;
+  }
+  double x = 0.5 * (a + b), step = 1.0;
+  for (int i = 0; i < 50; ++i) {
+    const double phi = std::exp(-0.5 * x * x) / std::sqrt(2.0 * kPi);
+    const double nx = x - F(x) / phi;
+    const double ns = std::fabs(nx - x);
+    if (!(ns < step)) break;  // no longer converging: at the rounding floor
+    step = ns;
+    x = nx;
+    if (ns == 0.0) break;
+  }
+  return upper ? -x : x;
+}
+
+// The calibrated likelihood of unit-cube points: the first s.D coordinates
+// through the source prior, the next 2 nn n_det through zero-mean Gaussian
+// priors of width sig[0] (amplitude) and sig[1] (phase), per detector nn
+// amplitude then nn phase corrections.
+UnitLike cal_like(const Event& ev, const Sampling& s, int nn, const double* node_f, const double* sig) {
+  std::vector<double> xn(nn);
+  for (int k = 0; k < nn; ++k) xn[k] = std::log(node_f[k]);
+  const int nc = 2 * nn * ev.n_det;
+  const double sa = sig[0], sp = sig[1];
+  return [ev, s, nn, xn, nc, sa, sp](const double* u) {
+    std::vector<double> th(P_N + nc);
+    unit_to_theta(s, u, th.data());
+    for (int c = 0; c < nc; ++c) th[P_N + c] = ((c / nn) % 2 ? sp : sa) * inv_normal_cdf(u[s.D + c]);
+    return loglike_cal_one(ev, th.data(), nn, xn.data());
+  };
+}
+
 UnitLike gw_like(const Event& ev, const Sampling& s) {
   return [ev, s](const double* u) { return loglike_unit(ev, s, u); };
 }
@@ -835,6 +889,53 @@ int oracle_ns_run(const double* freqs, int64_t M, const double* strain, const do
   ns_run_impl(gw_like(ev, s), D, periodic, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0,
               res, dead_lnl, dead_logwt, dead_u, max_dead, n_threads);
   return 0;
+}
+
+// ns_replace / ns_run with the calibration model: the walk coordinates are the
+// D sampled source coordinates followed by 2 n_nodes n_det calibration
+// coordinates (Gaussian priors of widths sig[2]); live_u, chol and out_u use
+// that dimension.
+int oracle_ns_replace_cal(const double* freqs, int64_t M, const double* strain, const double* psd,
+                          const double* geom, int n_det, double gmst, double t_ref, int fcut_mode,
+                          int D, const int* param_map, const double* fixed, const int* kind,
+                          const double* lo, const double* hi, const int* periodic, int n_nodes,
+                          const double* node_f, const double* sig, const double* live_u,
+                          const double* live_lnl, int64_t K, int64_t worst, double lnl_star,
+                          uint64_t seed, uint64_t counter, int64_t n_chains, int walk_len,
+                          double scale, const double* chol, double* out_u, double* out_lnl,
+                          int32_t* out_nacc, int32_t* out_start, int n_threads) {
+  if (K < 2 || worst < 0 || worst >= K || n_nodes < 2) return -1;
+  Event ev{freqs, M, strain, psd, geom, n_det, gmst, t_ref, fcut_mode};
+  Sampling s{D, param_map, fixed, kind, lo, hi, periodic};
+  const int Dw = D + 2 * n_nodes * n_det;
+  std::vector<int> per(Dw, 0);
+  for (int i = 0; i < D; ++i) per[i] = periodic[i];
+  ns_replace_impl(cal_like(ev, s, n_nodes, node_f, sig), Dw, per.data(), live_u, live_lnl, K, worst,
+                  lnl_star, seed, counter, n_chains, walk_len, scale, chol, out_u, out_lnl, out_nacc,
+                  out_start, n_threads);
+  return 0;
+}
+
+int oracle_ns_run_cal(const double* freqs, int64_t M, const double* strain, const double* psd,
+                      const double* geom, int n_det, double gmst, double t_ref, int fcut_mode, int D,
+                      const int* param_map, const double* fixed, const int* kind, const double* lo,
+                      const double* hi, const int* periodic, int n_nodes, const double* node_f,
+                      const double* sig, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
+                      double dlogz, int64_t max_rounds, double scale0, double* res, int n_threads) {
+  if (K < 2 || D < 1 || n_nodes < 2) return -1;
+  Event ev{freqs, M, strain, psd, geom, n_det, gmst, t_ref, fcut_mode};
+  Sampling s{D, param_map, fixed, kind, lo, hi, periodic};
+  const int Dw = D + 2 * n_nodes * n_det;
+  std::vector<int> per(Dw, 0);
+  for (int i = 0; i < D; ++i) per[i] = periodic[i];
+  ns_run_impl(cal_like(ev, s, n_nodes, node_f, sig), Dw, per.data(), K, n_chains, walk_len, seed, dlogz,
+              max_rounds, scale0, res, nullptr, nullptr, nullptr, 0, n_threads);
+  return 0;
+}
+
+// Phi^{-1} of n values (test hook).
+void oracle_inv_normal_cdf(int64_t n, const double* u, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = inv_normal_cdf(u[i]);
 }
 
 // Nested sampling of the analytic Gaussian-in-a-box likelihood (test pin).

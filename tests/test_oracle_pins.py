@@ -524,3 +524,26 @@ def test_cal_loglike_brute_force_with_scipy_splines(c2):
         ref = inner(c2, c2.strain, ch) - 0.5 * inner(c2, ch, ch)
         got = oracle.loglike_cal(c2, nodes, _cal_theta(c2, t, dA, dphi)[None])[0]
         assert got == pytest.approx(ref, rel=1e-10, abs=1e-8)
+
+
+def test_inverse_normal_cdf_is_scipy_ndtri():
+    """The oracle's Phi^{-1} (calibration priors) equals scipy's ndtri from the far tails to the centre."""
+    u = np.concatenate([np.geomspace(1e-300, 0.5, 400), 1.0 - np.geomspace(1e-16, 0.5, 400),
+                        np.random.default_rng(0).uniform(size=2000)])
+    got, ref = oracle.inv_normal_cdf(u), special.ndtri(u)
+    assert np.all(np.abs(got - ref) <= 2e-15 * np.maximum(1.0, np.abs(ref)))
+    nz = np.abs(ref) > 1e-3
+    assert np.all(np.abs(got[nz] - ref[nz]) <= 4e-15 * np.abs(ref[nz]))
+    assert list(oracle.inv_normal_cdf([0.0, 0.5, 1.0])) == [-np.inf, 0.0, np.inf]
+
+
+@pytest.mark.slow
+def test_ns_with_vanishing_calibration_priors_reproduces_lnz(c1):
+    """Calibrated NS whose calibration priors are 1e-9 wide (8 extra walk coordinates that change no
+    likelihood) gives the uncalibrated evidence within the sampling error."""
+    nodes = np.geomspace(20.0, 512.0, 4)
+    kw = dict(K=150, n_chains=150, walk_len=20, dlogz=0.1)
+    ref = oracle.ns_run(c1, c1.sampling, seed=5, **kw)
+    got = oracle.ns_run_cal(c1, c1.sampling, (nodes, 1e-9, 1e-9), seed=6, **kw)
+    sig = math.hypot(ref["lnZ_err"], got["lnZ_err"])
+    assert abs(got["lnZ"] - ref["lnZ"]) < 4 * sig, (got, ref)
