@@ -142,16 +142,23 @@ int gwl_loglike_host(gwl_ctx* ctx, const double* theta_host, int64_t B, double* 
  * the nodes.
  *   n_nodes     0 (off, the default) or 2 .. GWL_MAX_CAL_NODES
  *   node_freqs  host [n_nodes] positive, strictly increasing [Hz]; copied
+ *   sigma_amp, sigma_phase  > 0: widths of the zero-mean Gaussian priors of
+ *               the amplitude and phase [rad] corrections, used where
+ *               ns_replace / ns_run map unit-cube coordinates to parameters
+ *               (theta = sigma Phi^{-1}(u); never periodic)
  * A set-up call like gwl_create: it synchronises the device and builds
- * per-bin tables there (128 bytes per bin).  gwl_grad, ns_replace, ns_run,
- * gwl_autotune with GWL_TUNE_GRAD and gwl_multi_create / gwl_multi_loglike /
- * gwl_multi_ns_run refuse a calibrated context with GWL_ERR_ARG;
- * gwl_waveform returns the template without the calibration factor.  A
- * non-finite calibration parameter gives a non-finite lnL.  The likelihood
- * window (gwl_tuning.window) shrinks, if needed, so that the calibration rows
- * fit in shared memory. */
+ * per-bin tables there (about 70 bytes per bin).  ns_replace and ns_run walk
+ * in the n_dim + 2 n_nodes n_det coordinates (random walk only).  gwl_grad,
+ * the Galilean walk, gwl_autotune with GWL_TUNE_GRAD and gwl_multi_create /
+ * gwl_multi_loglike / gwl_multi_ns_run refuse a calibrated context with
+ * GWL_ERR_ARG; gwl_waveform returns the template without the calibration
+ * factor.  A non-finite calibration parameter gives a non-finite lnL.  The
+ * likelihood window (gwl_tuning.window) shrinks, if needed, so that the
+ * calibration rows fit in shared memory.  An argument error leaves the
+ * context unchanged. */
 #define GWL_MAX_CAL_NODES 16
-int gwl_set_calibration(gwl_ctx* ctx, int n_nodes, const double* node_freqs);
+int gwl_set_calibration(gwl_ctx* ctx, int n_nodes, const double* node_freqs, double sigma_amp,
+                        double sigma_phase);
 
 /* The context's calibration nodes (0: off) and doubles per row of theta
  * (either pointer may be null). */
@@ -174,11 +181,12 @@ int gwl_waveform(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* h_dev
  * point chosen uniformly among the K - 1 points other than `worst`, then makes
  * walk_len steps u' = u + scale * chol z in the unit cube (z standard normal);
  * periodic coordinates wrap, any other coordinate outside [0,1] rejects the
- * step; a step is accepted iff lnL(theta(u')) >= lnl_star.
- *   live_u   dev [K][n_dim]      unit-cube coordinates of the live points
+ * step; a step is accepted iff lnL(theta(u')) >= lnl_star.  D below is the
+ * walk dimension: n_dim, plus 2 n_nodes n_det with the calibration model.
+ *   live_u   dev [K][D]          unit-cube coordinates of the live points
  *   live_lnl dev [K]             their lnL
- *   chol     dev [n_dim][n_dim]  lower-triangular step matrix (row-major)
- *   out_u    dev [n_chains][n_dim], out_lnl dev [n_chains],
+ *   chol     dev [D][D]          lower-triangular step matrix (row-major)
+ *   out_u    dev [n_chains][D], out_lnl dev [n_chains],
  *   out_nacc dev [n_chains] int32 accepted steps (0 = the chain returns its
  *            start point), out_start dev [n_chains] int32 (may be NULL).
  * Random numbers: Philox4x32-10 (Salmon et al. 2011) with key = (seed low,
@@ -219,7 +227,7 @@ typedef struct {
  * final live points enter with X_N/(K+1) each.  The walk scale adapts as
  * scale <- scale exp(acceptance - 1/2), clamped to [1e-3, 1].  The run stops
  * when ln(Z + Lmax X) - ln Z < dlogz or after max_rounds rounds.
- *   dead_lnl, dead_logwt host [max_dead], dead_u host [max_dead][n_dim]
+ *   dead_lnl, dead_logwt host [max_dead], dead_u host [max_dead][D] (D as for ns_replace)
  *   (may be NULL; the first min(n_dead, max_dead) dead points in death order,
  *   the final live points last with their equal weights).
  * Synchronises the stream before returning. */

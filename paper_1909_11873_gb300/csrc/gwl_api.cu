@@ -158,6 +158,12 @@ int no_calibration(const gwl_ctx* c, const char* what) {
   if (c->n_cal_nodes) return fail(GWL_ERR_ARG, "%s is not available with the calibration model", what);
   return GWL_OK;
 }
+// The Galilean walk needs gwl_grad, which does not model calibration.
+int walk_supported(const gwl_ctx* c, const char* what) {
+  if (c->n_cal_nodes && c->walk_kind == GWL_WALK_GALILEAN)
+    return fail(GWL_ERR_ARG, "%s: the Galilean walk is not available with the calibration model", what);
+  return GWL_OK;
+}
 
 int check_ctx(const gwl_ctx* c) {
   if (!c) return fail(GWL_ERR_ARG, "null context");
@@ -380,10 +386,10 @@ int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t
   if (n_chains < 0 || n_chains > ((int64_t)1 << 31) - 1) return fail(GWL_ERR_ARG, "n_chains out of range");
   if (walk_len < 0) return fail(GWL_ERR_ARG, "walk_len < 0");
   if (!(scale > 0.0) || !std::isfinite(scale)) return fail(GWL_ERR_ARG, "scale must be positive");
-  if ((rc = no_calibration(c, "ns_replace"))) return rc;
+  if ((rc = walk_supported(c, "ns_replace"))) return rc;
   if (n_chains == 0) return GWL_OK;
   if (!live_u || !live_lnl || !chol || !out_u || !out_lnl || !out_nacc) return fail(GWL_ERR_ARG, "null device pointer");
-  const int D = c->opt.n_dim;
+  const int D = (int)gwl::theta_stride(c);
   if ((rc = ensure_scratch(c, n_chains))) return rc;
   if ((rc = ensure_bytes(c, (void**)&c->d_walk, &c->walk_cap, (int64_t)sizeof(double) * n_chains * (2 * D + 1))))
     return rc;
@@ -419,7 +425,7 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
   if (max_dead > 0 && (!dead_lnl || !dead_logwt || !dead_u)) return fail(GWL_ERR_ARG, "null dead-point buffer");
   if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "ns_run supports K <= 4096 and n_chains <= 4096");
-  if ((rc = no_calibration(c, "ns_run"))) return rc;
+  if ((rc = walk_supported(c, "ns_run"))) return rc;
   const int64_t nb = n_chains > K ? n_chains : K;
   if ((rc = ensure_scratch(c, nb))) return rc;
   if (c->walk_kind == GWL_WALK_GALILEAN) {
@@ -579,12 +585,15 @@ int gwl_get_tuning(const gwl_ctx* c, gwl_tuning* out) {
   return GWL_OK;
 }
 
-int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs) {
+int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs, double sigma_amp, double sigma_phase) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (n_nodes != 0 && (n_nodes < 2 || n_nodes > GWL_MAX_CAL_NODES))
     return fail(GWL_ERR_ARG, "n_nodes=%d outside {0} and [2, %d]", n_nodes, GWL_MAX_CAL_NODES);
   if (n_nodes && !node_freqs) return fail(GWL_ERR_ARG, "node_freqs is null");
+  if (n_nodes && (!(sigma_amp > 0.0) || !(sigma_phase > 0.0) || !std::isfinite(sigma_amp) ||
+                  !std::isfinite(sigma_phase)))
+    return fail(GWL_ERR_ARG, "calibration prior widths must be positive");
   for (int k = 0; k < n_nodes; ++k) {
     if (!(node_freqs[k] > 0.0) || !std::isfinite(node_freqs[k]))
       return fail(GWL_ERR_ARG, "node_freqs[%d] not positive", k);
@@ -628,6 +637,8 @@ int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs) {
     return cuda_fail(e, "gwl_set_calibration");
   }
   c->seg.stride = c->opt.n_dim + 2 * n_nodes * c->n_det;
+  c->cal_sigma[0] = sigma_amp;
+  c->cal_sigma[1] = sigma_phase;
   // the likelihood window must still fit shared memory with the calibration rows
   const size_t row = gwl::lnl_row_bytes(c);
   while (c->window > 32 && (size_t)c->window * row > gwl::kWindowSmemMax) c->window -= 32;

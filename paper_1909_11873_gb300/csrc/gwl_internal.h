@@ -36,6 +36,7 @@ struct gwl_ctx {
   float* d_calQ_f = nullptr;     // [n_nodes][n_nodes]: m = Q y (natural-spline curvatures)
   double* d_calQ_d = nullptr;
   int row_cal_f = 0, row_cal_d = 0;
+  double cal_sigma[2] = {0.1, 0.1};  // prior widths of the amplitude and phase corrections (ns_replace, ns_run)
 
   // device scratch (owned, grown on demand)
   gwl::PropMixed* d_pm = nullptr;

@@ -63,12 +63,20 @@ __device__ __forceinline__ void walk_normals(uint64_t seed, uint64_t counter, ui
   }
 }
 
-// Unit cube -> parameter (the context's prior of each sampled coordinate).
+// Unit cube -> parameter.  A walk coordinate is one of the n_src sampled
+// source coordinates (the context's prior of each) or, with the calibration
+// model, one of the 2 nn n_det calibration parameters that follow them (per
+// detector nn amplitude then nn phase corrections), each with a zero-mean
+// Gaussian prior: theta = sigma Phi^{-1}(u).
+constexpr int kMaxWalkDim = GWL_N_PARAM + 2 * kMaxCalNodes * kMaxDet;
 struct PriorInfo {
-  int D;
+  int D;      // walk dimension
+  int n_src;  // sampled source coordinates
   int kind[11];
   double lo[11], hi[11];
   int periodic[11];
+  int nn;               // calibration nodes (0: none)
+  double cal_sigma[2];  // prior widths of the amplitude and the phase [rad] corrections
 };
 
 __device__ __forceinline__ double prior_map(int kind, double lo, double hi, double u) {
@@ -78,6 +86,14 @@ __device__ __forceinline__ double prior_map(int kind, double lo, double hi, doub
     case GWL_PRIOR_COSINE: return asin(2.0 * u - 1.0);
     default: return lo + u * (hi - lo);
   }
+}
+
+__device__ __forceinline__ bool coord_periodic(const PriorInfo& pr, int i) { return i < pr.n_src && pr.periodic[i]; }
+
+__device__ __forceinline__ double coord_map(const PriorInfo& pr, int i, double u) {
+  if (i < pr.n_src) return prior_map(pr.kind[i], pr.lo[i], pr.hi[i], u);
+  const int c = i - pr.n_src;
+  return pr.cal_sigma[(c / pr.nn) & 1] * normcdfinv(u);
 }
 
 // ---------------------------------------------------------------- walk kernels
@@ -112,7 +128,7 @@ __global__ void k_walk_propose(PriorInfo pr, const WalkScalars* __restrict__ sc,
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_chains) return;
   const int D = pr.D;
-  double z[11];
+  double z[kMaxWalkDim];
   walk_normals(seed, sc->counter, (uint32_t)b, step, D, z);
   const double scale = sc->scale;
   bool inside = true;
@@ -120,12 +136,11 @@ __global__ void k_walk_propose(PriorInfo pr, const WalkScalars* __restrict__ sc,
     double dz = 0.0;
     for (int k = 0; k <= i; ++k) dz += chol[i * D + k] * z[k];
     double x = cu[b * D + i] + scale * dz;
-    if (pr.periodic[i]) x -= floor(x);
+    if (coord_periodic(pr, i)) x -= floor(x);
     else if (x < 0.0 || x > 1.0) inside = false;
     pu[b * D + i] = x;
   }
-  for (int i = 0; i < D; ++i)
-    ptheta[b * D + i] = inside ? prior_map(pr.kind[i], pr.lo[i], pr.hi[i], pu[b * D + i]) : NAN;
+  for (int i = 0; i < D; ++i) ptheta[b * D + i] = inside ? coord_map(pr, i, pu[b * D + i]) : NAN;
 }
 
 __global__ void k_walk_accept(const WalkScalars* __restrict__ sc, int D, int64_t n_chains,
@@ -327,7 +342,6 @@ __device__ void ns_prep_body(const NsDev& s) {
   if (s.stats[NS_DONE] > 0.5) return;  // rounds replayed after the stopping rule held change nothing
   __shared__ double red_v[256];
   __shared__ long long red_i[256];
-  __shared__ double mean[11], cov[11 * 11];
   const int t = threadIdx.x;
   // argmin of the live lnL
   double bv = INFINITY;
@@ -355,10 +369,12 @@ __device__ void ns_prep_body(const NsDev& s) {
   }
   const int D = s.D;
   // mean and covariance of the live set: thread t handles one (dimension or
-  // pair) and one slice of the points; slices are reduced through shared memory
+  // pair) and one slice of the points; slices are reduced through shared
+  // memory (with more pairs than threads, each thread takes whole pairs)
   __shared__ double part[256];
+  __shared__ double mean[kMaxWalkDim], diag[kMaxWalkDim];
   {
-    const int S = blockDim.x / D;
+    const int S = blockDim.x / D;  // D <= kMaxWalkDim < blockDim
     const int i = t % D, sl = t / D;
     double m = 0.0;
     if (sl < S)
@@ -372,59 +388,80 @@ __device__ void ns_prep_body(const NsDev& s) {
     }
     __syncthreads();
   }
+  double* A = s.chol;  // the covariance, then (in place) its Cholesky factor
   {
     const int P = D * (D + 1) / 2;
-    const int S = blockDim.x / P;
-    const int pr = t % P, sl = t / P;
-    int i = 0, j = pr;
-    while (j >= D - i) {
-      j -= D - i;
-      ++i;
-    }
-    j += i;  // pair index -> (i, j), i <= j
-    double c = 0.0;
-    if (sl < S)
-      for (int64_t k = sl; k < s.K; k += S) c += (s.lu[k * D + i] - mean[i]) * (s.lu[k * D + j] - mean[j]);
-    part[t] = sl < S ? c : 0.0;
-    __syncthreads();
-    if (t < P) {
-      double a = 0.0;
-      for (int q = 0; q < S; ++q) a += part[q * P + t];
-      int ii = 0, jj = t;
-      while (jj >= D - ii) {
-        jj -= D - ii;
-        ++ii;
+    auto pair = [D](int pr, int& i, int& j) {  // pair index -> (i, j), i <= j
+      i = 0;
+      j = pr;
+      while (j >= D - i) {
+        j -= D - i;
+        ++i;
       }
-      jj += ii;
-      cov[ii * D + jj] = cov[jj * D + ii] = a / (double)(s.K - 1);
+      j += i;
+    };
+    if (P <= (int)blockDim.x) {
+      const int S = blockDim.x / P;
+      const int pr = t % P, sl = t / P;
+      int i, j;
+      pair(pr, i, j);
+      double c = 0.0;
+      if (sl < S)
+        for (int64_t k = sl; k < s.K; k += S) c += (s.lu[k * D + i] - mean[i]) * (s.lu[k * D + j] - mean[j]);
+      part[t] = sl < S ? c : 0.0;
+      __syncthreads();
+      if (t < P) {
+        double a = 0.0;
+        for (int q = 0; q < S; ++q) a += part[q * P + t];
+        int ii, jj;
+        pair(t, ii, jj);
+        A[ii * D + jj] = A[jj * D + ii] = a / (double)(s.K - 1);
+      }
+    } else {
+      for (int pr = t; pr < P; pr += blockDim.x) {
+        int i, j;
+        pair(pr, i, j);
+        double c = 0.0;
+        for (int64_t k = 0; k < s.K; ++k) c += (s.lu[k * D + i] - mean[i]) * (s.lu[k * D + j] - mean[j]);
+        A[i * D + j] = A[j * D + i] = c / (double)(s.K - 1);
+      }
     }
     __syncthreads();
+  }
+  // Cholesky factor (lower), left-looking, in place: column j's diagonal on
+  // thread 0, its rows below in parallel, one barrier per column; a diagonal
+  // factor of the covariance if it is not positive definite
+  __shared__ int s_ok;
+  for (int i = t; i < D; i += blockDim.x) diag[i] = A[i * D + i];
+  if (t == 0) s_ok = 1;
+  __syncthreads();
+  for (int j = 0; j < D; ++j) {
+    if (t == 0) {
+      double d = A[j * D + j];
+      for (int k = 0; k < j; ++k) d -= A[j * D + k] * A[j * D + k];
+      if (d > 0.0) A[j * D + j] = sqrt(d);
+      else s_ok = 0;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const double ljj = A[j * D + j];
+    for (int i = j + 1 + t; i < D; i += blockDim.x) {
+      double x = A[i * D + j];
+      for (int k = 0; k < j; ++k) x -= A[i * D + k] * A[j * D + k];
+      A[i * D + j] = x / ljj;
+    }
+    __syncthreads();
+  }
+  const bool okc = s_ok != 0;
+  for (int x = t; x < D * D; x += blockDim.x) {
+    const int i = x / D, j = x % D;
+    if (!okc) A[x] = i == j ? sqrt(fmax(diag[i], 1e-300)) : 0.0;
+    else if (j > i) A[x] = 0.0;
   }
   if (t == 0) {
     s.ws->lstar = red_v[0];
     s.ws->worst = red_i[0];
     s.ws->counter = (unsigned long long)s.stats[NS_ROUND];
-    // Cholesky (lower), diagonal fallback if the covariance is not positive definite
-    double L[11 * 11];
-    bool okc = true;
-    for (int j = 0; j < D && okc; ++j) {
-      double d = cov[j * D + j];
-      for (int k = 0; k < j; ++k) d -= L[j * D + k] * L[j * D + k];
-      if (!(d > 0.0)) {
-        okc = false;
-        break;
-      }
-      L[j * D + j] = sqrt(d);
-      for (int i = j + 1; i < D; ++i) {
-        double x = cov[i * D + j];
-        for (int k = 0; k < j; ++k) x -= L[i * D + k] * L[j * D + k];
-        L[i * D + j] = x / L[j * D + j];
-      }
-      for (int k = j + 1; k < D; ++k) L[j * D + k] = 0.0;
-    }
-    for (int i = 0; i < D; ++i)
-      for (int j = 0; j < D; ++j)
-        s.chol[i * D + j] = okc ? L[i * D + j] : (i == j ? sqrt(fmax(cov[i * D + i], 1e-300)) : 0.0);
     s.stats[NS_NDEAD_ROUND0] = s.stats[NS_NDEAD];
   }
 }
@@ -677,7 +714,7 @@ __global__ void k_mwalk_propose(const NsDev* __restrict__ a, const PriorInfo* __
     for (int i = 0; i < D; ++i) ptheta[g * D + i] = NAN;
     return;
   }
-  double z[11];
+  double z[kMaxWalkDim];
   walk_normals(event_key(seed, e), s.ws->counter, (uint32_t)b, step, D, z);
   const double scale = s.ws->scale;
   bool inside = true;
@@ -685,12 +722,11 @@ __global__ void k_mwalk_propose(const NsDev* __restrict__ a, const PriorInfo* __
     double dz = 0.0;
     for (int k = 0; k <= i; ++k) dz += s.chol[i * D + k] * z[k];
     double x = s.cu[b * D + i] + scale * dz;
-    if (pr.periodic[i]) x -= floor(x);
+    if (coord_periodic(pr, i)) x -= floor(x);
     else if (x < 0.0 || x > 1.0) inside = false;
     pu[g * D + i] = x;
   }
-  for (int i = 0; i < D; ++i)
-    ptheta[g * D + i] = inside ? prior_map(pr.kind[i], pr.lo[i], pr.hi[i], pu[g * D + i]) : NAN;
+  for (int i = 0; i < D; ++i) ptheta[g * D + i] = inside ? coord_map(pr, i, pu[g * D + i]) : NAN;
 }
 
 __global__ void k_mwalk_accept(const NsDev* __restrict__ a, int64_t n, int E, const double* __restrict__ pu,
@@ -722,7 +758,7 @@ __global__ void k_ns_init(PriorInfo pr, uint64_t seed, int64_t K, double* __rest
     for (int i = 0; i < 4 && 4 * b + i < D; ++i) {
       const double u = ((double)ws[i] + 0.5) * 0x1p-32;
       lu[k * D + 4 * b + i] = u;
-      theta[k * D + 4 * b + i] = prior_map(pr.kind[4 * b + i], pr.lo[4 * b + i], pr.hi[4 * b + i], u);
+      theta[k * D + 4 * b + i] = coord_map(pr, 4 * b + i, u);
     }
   }
 }
@@ -730,13 +766,17 @@ __global__ void k_ns_init(PriorInfo pr, uint64_t seed, int64_t K, double* __rest
 // ---------------------------------------------------------------- host side
 static PriorInfo prior_info(const gwl_ctx* c) {
   PriorInfo p;
-  p.D = c->opt.n_dim;
+  p.D = (int)theta_stride(c);
+  p.n_src = c->opt.n_dim;
   for (int i = 0; i < 11; ++i) {
     p.kind[i] = c->opt.prior_kind[i];
     p.lo[i] = c->opt.prior_lo[i];
     p.hi[i] = c->opt.prior_hi[i];
     p.periodic[i] = c->opt.periodic[i];
   }
+  p.nn = c->n_cal_nodes > 0 ? c->n_cal_nodes : 1;
+  p.cal_sigma[0] = c->cal_sigma[0];
+  p.cal_sigma[1] = c->cal_sigma[1];
   return p;
 }
 
@@ -745,7 +785,7 @@ static cudaError_t launch_gmc(gwl_ctx* c, const double* live_u, const double* li
                               const WalkScalars* sc, uint64_t seed, int64_t n_chains, int walk_len, const double* chol,
                               double* out_u, double* out_lnl, int32_t* out_nacc, int32_t* out_start, double* pu,
                               double* pth, double* plnl, cudaStream_t st) {
-  const int D = c->opt.n_dim;
+  const int D = (int)theta_stride(c);
   const unsigned nb = (unsigned)((n_chains + 127) / 128);
   const PriorInfo pr = prior_info(c);
   // scratch after the random-walk proposal buffers: velocity, x2, theta2, gradient, l2, mode
@@ -789,7 +829,7 @@ cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl
   if (c->walk_kind == GWL_WALK_GALILEAN)
     return launch_gmc(c, live_u, live_lnl, K, sc, seed, n_chains, walk_len, chol, out_u, out_lnl, out_nacc,
                       out_start, pu, pth, plnl, st);
-  const int D = c->opt.n_dim;
+  const int D = (int)theta_stride(c);
   const unsigned nb = (unsigned)((n_chains + 127) / 128);
   const PriorInfo pr = prior_info(c);
   {
@@ -877,7 +917,7 @@ int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t 
 static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                      int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
                      double* dead_u, double* res, cudaStream_t st, int use_graph) {
-  const int D = c->opt.n_dim;
+  const int D = (int)theta_stride(c);
   const int64_t cap = max_dead > 0 ? max_dead : 1;
   const int64_t rbuf = n_chains > K ? n_chains : K;
   NsDev s;

@@ -96,7 +96,7 @@ def lib() -> C.CDLL:
         L.gwl_set_tuning.argtypes = [P, C.POINTER(GwlTuning)]
         L.gwl_get_tuning.argtypes = [P, C.POINTER(GwlTuning)]
         L.gwl_autotune.argtypes = [P, P, i64, i32, C.POINTER(GwlTuning), P]
-        L.gwl_set_calibration.argtypes = [P, i32, P]
+        L.gwl_set_calibration.argtypes = [P, i32, P, d, d]
         L.gwl_get_calibration.argtypes = [P, C.POINTER(i32), C.POINTER(i64)]
         L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
@@ -241,7 +241,7 @@ class Context:
                stream=None):
         """Static parallel nested sampling on the device; returns a dict (plus dead points if max_dead > 0)."""
         r = GwlNsResult()
-        D = self.n_dim
+        D = self.theta_stride
         dl = np.zeros(max(max_dead, 1))
         dw = np.zeros(max(max_dead, 1))
         du = np.zeros((max(max_dead, 1), D))
@@ -277,12 +277,13 @@ class Context:
                "gwl_autotune")
         return t.as_dict()
 
-    def gwl_set_calibration(self, node_freqs):
+    def gwl_set_calibration(self, node_freqs, sigma_amp=0.1, sigma_phase=0.1):
         """Calibration model at these node frequencies [Hz] (empty: off); rows of theta then hold
-        n_dim + 2 n_nodes n_det values (per detector dA at the nodes, then dphi)."""
+        n_dim + 2 n_nodes n_det values (per detector dA at the nodes, then dphi), and ns_replace /
+        ns_run sample them under zero-mean Gaussian priors of these widths."""
         nf = np.ascontiguousarray(node_freqs, dtype=np.float64).ravel()
-        _check(lib().gwl_set_calibration(self._h, nf.size, nf.ctypes.data if nf.size else None),
-               "gwl_set_calibration")
+        _check(lib().gwl_set_calibration(self._h, nf.size, nf.ctypes.data if nf.size else None, float(sigma_amp),
+                                         float(sigma_phase)), "gwl_set_calibration")
 
     def gwl_get_calibration(self):
         """(calibration nodes, doubles per row of theta)."""

@@ -57,6 +57,6 @@ def test_argument_errors_are_synchronous(L):
     assert L.gwl_autotune(None, None, 1, 1, None, None) == -1
     assert L.gwl_set_tuning(None, None) == -1
     assert L.gwl_get_tuning(None, None) == -1
-    assert L.gwl_set_calibration(None, 10, f.ctypes.data) == -1
+    assert L.gwl_set_calibration(None, 10, f.ctypes.data, 0.1, 0.1) == -1
     assert L.gwl_get_calibration(None, None, None) == -1
     assert out.value is None

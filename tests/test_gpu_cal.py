@@ -163,19 +163,24 @@ def test_calibration_edge_rows_and_entry_points(precision):
 
 
 def test_calibration_refused_where_not_modelled():
-    """gwl_grad, ns_run and multi-event batches refuse a calibrated context (GWL_ERR_ARG);
-    invalid node sets are refused."""
+    """gwl_grad, the Galilean walk and multi-event batches refuse a calibrated context (GWL_ERR_ARG);
+    invalid node sets and prior widths are refused."""
     g = gwl()
     ev = event("c2")
     ctx = cal_context(ev, I.cal_node_freqs(20.0, 1024.0), 1)
     th = torch.zeros((4, ctx.theta_stride), dtype=torch.float64, device="cuda")
     with pytest.raises(g.GwlError, match="calibration"):
         g.grad(ctx, th)
+    ctx.gwl_set_walk(g.GWL_WALK_GALILEAN)
     with pytest.raises(g.GwlError, match="calibration"):
         ctx.ns_run(64, 64, 4, 1)
+    ctx.gwl_set_walk(g.GWL_WALK_RANDOM)
     with pytest.raises(g.GwlError, match="calibration"):
         g.MultiContext([ctx])
     for bad in ([20.0], [20.0, 20.0, 30.0], [-1.0, 30.0], np.geomspace(20, 1024, 17)):
         with pytest.raises(g.GwlError):
             ctx.gwl_set_calibration(bad)
+    for sa, sp in ((0.0, 0.1), (0.1, -1.0), (np.inf, 0.1)):
+        with pytest.raises(g.GwlError):
+            ctx.gwl_set_calibration(I.cal_node_freqs(20.0, 1024.0), sa, sp)
     assert ctx.gwl_get_calibration()[0] == 10  # a refused set leaves the context as it was
