@@ -235,6 +235,21 @@ int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t see
            int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
            double* dead_u, gwl_ns_result* out, void* stream);
 
+/* Diagnostic: the float-float elementary functions of the mixed prologue
+ * (about 48 significant bits on the FP32 pipe) on n arguments, for checking
+ * their accuracy against FP64 references.  (An interface addition without a
+ * counterpart in the paper.)
+ *   x_dev   dev [n] FP64 arguments (split into float pairs first);
+ *           GWL_FF_LOG needs x > 0; arguments of moderate size (|x| < 2^20)
+ *   fn      GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN or GWL_FF_COS
+ *   out_dev dev [n] FP64 results (the float pair summed in FP64)
+ * Enqueues one kernel on the stream and returns. */
+#define GWL_FF_EXP 0
+#define GWL_FF_LOG 1
+#define GWL_FF_SIN 2
+#define GWL_FF_COS 3
+int gwl_ff_eval(const double* x_dev, int64_t n, int fn, double* out_dev, void* stream);
+
 /* ---- many events in one batch ----
  * A multi-event context groups n_events contexts (same device, detector
  * count, precision and sampled dimension; different segment lengths and

@@ -285,6 +285,12 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "normalise tables"); break; }
     c->seg.amp_scale = scale;
     gwl::SegInfo& s = c->seg;
+    gwl::split_f64(gwl::kAmpConst * gwl::kC / gwl::kMpc * scale, s.amp_c_ff.hi, s.amp_c_ff.lo);
+    for (int d = 0; d < GWL_MAX_DET; ++d) {
+      for (int k = 0; k < 9; ++k) gwl::split_f64(d < n_det ? geom[9 * d + k] : 0.0, s.geom_ff[d][k].hi, s.geom_ff[d][k].lo);
+      for (int k = 0; k < 3; ++k)
+        gwl::split_f64(d < n_det ? geom[9 * d + k] / gwl::kC : 0.0, s.vtx_c_ff[d][k].hi, s.vtx_c_ff[d][k].lo);
+    }
     s.freqs = c->d_freqs;
     s.H = c->d_H;
     s.geom = c->d_geom;

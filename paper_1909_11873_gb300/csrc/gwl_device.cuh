@@ -92,6 +92,12 @@ struct alignas(16) PropCommon {
 };
 
 // Everything the prologue needs about the data segment.
+// An unevaluated float pair x = hi + lo with |lo| <= ulp(hi)/2: about 48
+// significant bits, computed on the FP32 pipe (arithmetic in gwl_ff.cuh).
+struct FF {
+  float hi, lo;
+};
+
 struct SegInfo {
   const double* freqs;  // [M]
   const double* H;      // [n_det][M] inclusive prefix of 4 df f^{-7/3} / S
@@ -111,6 +117,12 @@ struct SegInfo {
   int stride;
   int param_map[11];
   double fixed[11];
+  // float-float copies for the mixed prologue: the detector geometry, the
+  // vertex over c (delays) and the amplitude constant
+  // sqrt(5/24) pi^{-2/3} c / Mpc * amp_scale
+  FF geom_ff[kMaxDet][9];
+  FF vtx_c_ff[kMaxDet][3];
+  FF amp_c_ff;
 };
 
 // ------------------------------------------------------------- float-float
@@ -461,8 +473,8 @@ __device__ __forceinline__ T delay(const T& tc, const Sky<T>& k, const double* g
 // axes X = cos psi e_E + sin psi e_N, Y = -sin psi e_E + cos psi e_N,
 // e_E = (-sin lam, cos lam, 0), e_N = (-sin dec cos lam, -sin dec sin lam, cos dec),
 // F+ = D:(XX - YY), Fx = D:(XY + YX), D = (xx - yy)/2.
-template <class T>
-__device__ __forceinline__ void response(const Sky<T>& k, const T& sp, const T& cp, const T& ci, const double* g,
+template <class T, class G>
+__device__ __forceinline__ void response(const Sky<T>& k, const T& sp, const T& cp, const T& ci, const G* g,
                                          T& Pr, T& Pi) {
   const T X0 = -(cp * k.sl) - sp * k.sd * k.cl, X1 = cp * k.cl - sp * k.sd * k.sl, X2 = sp * k.cd;
   const T Y0 = sp * k.sl - cp * k.sd * k.cl, Y1 = -(sp * k.cl) - cp * k.sd * k.sl, Y2 = cp * k.cd;

@@ -1,0 +1,154 @@
+// gwl_ff.cuh -- float-float arithmetic and elementary functions on the FP32 pipe.
+//
+// GB300 issues FP64 instructions at about 1/60 of its FP32 rate (measured:
+// 1.9 DFMA against 116 FFMA per clock per SM), so the mixed prologue keeps
+// FP64-class precision (~48 significant bits, relative error ~1e-14) with
+// unevaluated float pairs built from error-free transformations (Dekker 1971;
+// Knuth's TwoSum; FMA-based TwoProduct).  A float-float add or multiply costs
+// 7-11 FP32 instructions, several times less pipe time than one FP64
+// instruction, and the elementary functions below are written from their
+// series:
+//   exp x   = 2^k e^r, k = rint(x / ln 2), |r| <= ln 2 / 2, e^r by its Taylor
+//             series to r^13 / 13! (truncation < 4e-18);
+//   ln x    = y0 + ln(1 + t), y0 = the FP32 logarithm of the high part,
+//             1 + t = x e^{-y0} (|t| ~ 1e-7), ln(1 + t) = t - t^2/2 (+ O(t^3));
+//   sin/cos = reduction x = k pi/2 + r with |r| <= pi/4, the Taylor series of
+//             sin r to r^15 / 15! and cos r to r^16 / 16! (truncation < 5e-17),
+//             the quadrant k mod 4 selecting and signing them.
+// The series coefficients are the reciprocal factorials.  The reductions
+// subtract k c with c = ln 2 or pi/2 split into three floats (Cody & Waite
+// 1980): c1 with 12 significant bits (k c1 exact for |k| < 2^12), c2 and c3
+// the next 24 bits each (derived here from 50-digit values; the remainder is
+// below 1e-19).  Inputs of the elementary functions are small (|x| < 2^11).
+#pragma once
+
+#include "gwl_bins.cuh"
+
+namespace gwl {
+
+// A double constant as a float pair (folded at compile time for literals).
+__host__ __device__ constexpr FF ffc(double x) { return FF{(float)x, (float)(x - (double)(float)x)}; }
+__device__ __forceinline__ FF ff(float x) { return FF{x, 0.0f}; }
+// A run-time double as a float pair, and back (f32<->f64 conversions: keep them few).
+__device__ __forceinline__ FF ff_from(double x) {
+  FF r;
+  split_f64(x, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+
+// s + e renormalised, for |e| <= |s| or s == 0 (Fast2Sum).
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ FF operator+(const FF& a, const FF& b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ FF operator-(const FF& a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ FF operator-(const FF& a, const FF& b) { return a + (-b); }
+__device__ __forceinline__ FF operator*(const FF& a, const FF& b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  return ff_norm(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+// a / b: the FP32 quotient of the high parts, corrected by the quotient of the remainder.
+__device__ __forceinline__ FF operator/(const FF& a, const FF& b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const FF r = a - b * ff(q1);
+  return ff_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ FF operator+(const FF& a, double c) { return a + ffc(c); }
+__device__ __forceinline__ FF operator+(double c, const FF& a) { return a + ffc(c); }
+__device__ __forceinline__ FF operator-(const FF& a, double c) { return a + ffc(-c); }
+__device__ __forceinline__ FF operator-(double c, const FF& a) { return ffc(c) - a; }
+__device__ __forceinline__ FF operator*(const FF& a, double c) { return a * ffc(c); }
+__device__ __forceinline__ FF operator*(double c, const FF& a) { return a * ffc(c); }
+__device__ __forceinline__ FF operator/(const FF& a, double c) { return a / ffc(c); }
+__device__ __forceinline__ FF operator/(double c, const FF& a) { return ffc(c) / a; }
+
+// a - rint(a) for |a| < 2^22 (the high part's nearest integer; hi - r is exact).
+__device__ __forceinline__ FF frac_near(const FF& a) {
+  const float r = nearest_int(a.hi);
+  float s, e;
+  two_sum(__fsub_rn(a.hi, r), a.lo, s, e);
+  return FF{s, e};
+}
+
+// Series coefficients as float pairs (constant memory; indexed with
+// compile-time indices they become instruction operands):
+//   exp:  1/n!                    n = 0..13
+//   sin:  (-1)^n / (2n+1)!        n = 0..7   (sin r = r sum_n c_n r^{2n})
+//   cos:  (-1)^n / (2n)!          n = 0..8
+static __constant__ FF kExpCoef[14] = {ffc(1.0), ffc(1.0), ffc(1.0 / 2.0), ffc(1.0 / 6.0), ffc(1.0 / 24.0),
+                                       ffc(1.0 / 120.0), ffc(1.0 / 720.0), ffc(1.0 / 5040.0), ffc(1.0 / 40320.0),
+                                       ffc(1.0 / 362880.0), ffc(1.0 / 3628800.0), ffc(1.0 / 39916800.0),
+                                       ffc(1.0 / 479001600.0), ffc(1.0 / 6227020800.0)};
+static __constant__ FF kSinCoef[8] = {ffc(1.0), ffc(-1.0 / 6.0), ffc(1.0 / 120.0), ffc(-1.0 / 5040.0),
+                                      ffc(1.0 / 362880.0), ffc(-1.0 / 39916800.0), ffc(1.0 / 6227020800.0),
+                                      ffc(-1.0 / 1307674368000.0)};
+static __constant__ FF kCosCoef[9] = {ffc(1.0), ffc(-1.0 / 2.0), ffc(1.0 / 24.0), ffc(-1.0 / 720.0),
+                                      ffc(1.0 / 40320.0), ffc(-1.0 / 3628800.0), ffc(1.0 / 479001600.0),
+                                      ffc(-1.0 / 87178291200.0), ffc(1.0 / 20922789888000.0)};
+// x - k (c1 + c2 + c3): k c1 exact, k c2 exact as a float pair (TwoProduct),
+// k c3 below the float-float rounding.
+__device__ __forceinline__ FF ff_reduce(const FF& x, float k, float c1, float c2, float c3) {
+  FF t = x - ff(__fmul_rn(k, c1));
+  float p, e;
+  two_prod(k, c2, p, e);
+  t = t - FF{p, e};
+  return t - ff(__fmul_rn(k, c3));
+}
+
+// The elementary functions are out of line: each is a few hundred
+// instructions, called from several places, and one copy of each keeps the
+// prologue's code within the instruction cache.
+static __device__ __noinline__ FF ff_exp(const FF& x) {
+  const float k = nearest_int(__fmul_rn(x.hi, 1.44269504088896341f));
+  const FF r = ff_reduce(x, k, 0x1.62e000p-1f, 0x1.0bfbe8p-15f, 0x1.cf79acp-40f);  // ln 2
+  FF p = kExpCoef[13];
+#pragma unroll 1
+  for (int n = 12; n >= 0; --n) p = p * r + kExpCoef[n];
+  const float s = __int_as_float((127 + (int)k) << 23);  // 2^k (|k| < 127 for these inputs)
+  return FF{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)};
+}
+
+static __device__ __noinline__ FF ff_log(const FF& x) {
+  const float y0 = logf(x.hi);
+  const FF t = x * ff_exp(ff(-y0)) - 1.0;
+  return ff(y0) + (t - t * t * 0.5);
+}
+
+static __device__ __noinline__ void ff_sincos(const FF& x, FF* sn, FF* cs) {
+  const float k = nearest_int(__fmul_rn(x.hi, 0.636619772367581343f));
+  const FF r = ff_reduce(x, k, 0x1.920000p+0f, 0x1.fb5444p-12f, 0x1.68c234p-39f);  // pi / 2
+  const FF r2 = r * r;
+  FF ps = kSinCoef[7], pc = kCosCoef[8];
+#pragma unroll 1
+  for (int n = 7; n >= 0; --n) {  // the two series interleaved
+    if (n < 7) ps = ps * r2 + kSinCoef[n];
+    pc = pc * r2 + kCosCoef[n];
+  }
+  const FF s = r * ps, c = pc;
+  switch ((int)k & 3) {
+    case 0: *sn = s; *cs = c; break;
+    case 1: *sn = c; *cs = -s; break;
+    case 2: *sn = -s; *cs = -c; break;
+    default: *sn = -c; *cs = s; break;
+  }
+}
+
+// Overloads used by the templated model code (gwl_device.cuh).
+__device__ __forceinline__ FF exp(const FF& x) { return ff_exp(x); }
+__device__ __forceinline__ FF log(const FF& x) { return ff_log(x); }
+__device__ __forceinline__ void sincos(const FF& x, FF* s, FF* c) { ff_sincos(x, s, c); }
+__device__ __forceinline__ FF cos(const FF& x) {
+  FF s, c;
+  ff_sincos(x, &s, &c);
+  return c;
+}
+
+}  // namespace gwl

@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "gwl_bins.cuh"
+#include "gwl_ff.cuh"
 #include "gwl_sched.cuh"
 
 namespace gwl {
@@ -220,6 +221,163 @@ struct CtaSync {
   __device__ void operator()() const { __syncthreads(); }
 };
 
+// The mixed path's prologue: the same quantities, roles and phases in
+// float-float arithmetic on the FP32 pipe (gwl_ff.cuh, ~1e-14 relative), so
+// that FP64 is left only for reading theta, the cut frequency's bin count and
+// the double outputs K_d, <h|h>.  The phase of K_d also gets the float-float
+// sine and cosine.
+struct ProSmemFF {
+  FF lmc[32], leta[32], a13[32], amp[32], ccyc[32], eta[32];
+  FF phi[6][32];
+  FF sky[4][32];
+  FF ori[3][32];
+  FF P[2 * kMaxDet][32];
+  int ncut[32];
+};
+
+__device__ __forceinline__ FF delay_ff(const FF& tc, const Sky<FF>& k, const FF* vc) {
+  return tc - ((k.cd * k.cl) * vc[0] + (k.cd * k.sl) * vc[1] + k.sd * vc[2]);
+}
+
+__device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double* __restrict__ theta, int64_t B,
+                                                 int64_t row0, int role, int lane, ProSmemFF& sm,
+                                                 PropMixed* __restrict__ pm, PropCommon* __restrict__ pc,
+                                                 int* __restrict__ work, int* __restrict__ hist, int CH,
+                                                 double* __restrict__ lnl) {
+  const int64_t p = row0 + lane;
+  const bool valid = p < B;
+  double th[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) th[k] = 1.0;
+  if (valid) expand_theta(s, theta + p * s.stride, th);
+  const bool ok = valid && physical(th);
+  if (!ok) {  // keep every function below on a harmless argument
+    th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
+#pragma unroll
+    for (int k = 5; k < 11; ++k) th[k] = 0.0;
+  }
+
+  // ---- phase 1 (the mass scale is split over two warps: ln(pi Mc T_sun) and
+  // the amplitude on warp 0, ln eta beside the PN coefficients on warp 1)
+  if (role == 0) {
+    const FF lmc = log(ff_from(th[0]) * (kPi * kTsun));  // ln(pi Mc T_sun)
+    sm.lmc[lane] = lmc;
+    sm.amp[lane] = exp((lmc - kLnPi) * (5.0 / 6.0)) * s.amp_c_ff / ff_from(th[4]);
+  } else if (role == 1) {
+    const PNCoeffs<FF> P = pn_coeffs(ff_from(th[1]), ff_from(th[2]), ff_from(th[3]));
+    sm.leta[lane] = log(P.eta);
+    sm.eta[lane] = P.eta;
+    sm.phi[0][lane] = P.p2;
+    sm.phi[1][lane] = P.p3;
+    sm.phi[2][lane] = P.p4;
+    sm.phi[3][lane] = P.p5c;
+    sm.phi[4][lane] = P.p6c;
+    sm.phi[5][lane] = P.p7;
+  } else if (role == 2) {
+    const Sky<FF> k = sky_trig(ff_from(th[7]), ff_from(th[8]), s.gmst);
+    sm.sky[0][lane] = k.sl;
+    sm.sky[1][lane] = k.cl;
+    sm.sky[2][lane] = k.sd;
+    sm.sky[3][lane] = k.cd;
+    if (valid) {
+      const FF tc = ff_from(th[9]);
+#pragma unroll
+      for (int d = 0; d < kMaxDet; ++d) {
+        const FF tau = (d < s.n_det && ok) ? delay_ff(tc, k, s.vtx_c_ff[d]) : ff(0.0f);
+        pm[p].th[d] = tau.hi;
+        pm[p].tl[d] = tau.lo;
+      }
+    }
+  } else {
+    FF sp, cp;
+    sincos(ff_from(th[6]), &sp, &cp);
+    sm.ori[0][lane] = sp;
+    sm.ori[1][lane] = cp;
+    sm.ori[2][lane] = cos(ff_from(th[5]));
+  }
+  __syncthreads();
+
+  // ---- phase 2
+  if (role == 0) {
+    Scale<FF> S;
+    S.la = sm.lmc[lane] - 0.6 * sm.leta[lane];
+    S.a13 = exp(S.la * (1.0 / 3.0));
+    S.amp = sm.amp[lane];
+    sm.a13[lane] = S.a13;
+    int ncut = (int)s.M;
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, ff_to_double(1.0 / (kSix32 * (S.a13 * S.a13 * S.a13))));
+    sm.ncut[lane] = ok ? ncut : 0;
+    PNCoeffs<FF> P;
+    P.eta = sm.eta[lane];
+    P.p2 = sm.phi[0][lane];
+    P.p3 = sm.phi[1][lane];
+    P.p4 = sm.phi[2][lane];
+    P.p5c = sm.phi[3][lane];
+    P.p6c = sm.phi[4][lane];
+    P.p7 = sm.phi[5][lane];
+    FF c[kNBasis], ccyc;
+    basis_coeffs(P, S, c, ccyc);
+    sm.ccyc[lane] = ccyc;
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < kNBasis; ++m) {
+        pm[p].ch[m] = ok ? c[m].hi : 0.0f;
+        pm[p].cl[m] = ok ? c[m].lo : 0.0f;
+      }
+    }
+  } else if (role == 1) {
+    Sky<FF> k;
+    k.sl = sm.sky[0][lane];
+    k.cl = sm.sky[1][lane];
+    k.sd = sm.sky[2][lane];
+    k.cd = sm.sky[3][lane];
+    const FF sp = sm.ori[0][lane], cp = sm.ori[1][lane], ci = sm.ori[2][lane];
+#pragma unroll 1
+    for (int d = 0; d < kMaxDet; ++d) {
+      FF Pr = ff(0.0f), Pi = ff(0.0f);
+      if (d < s.n_det) response(k, sp, cp, ci, s.geom_ff[d], Pr, Pi);
+      sm.P[2 * d][lane] = Pr;
+      sm.P[2 * d + 1][lane] = Pi;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 3
+  if (role == 2) {
+    const int ncut = sm.ncut[lane];
+    if (valid) {
+      PropCommon cm;
+#pragma unroll
+      for (int d = 0; d < kMaxDet; ++d) cm.Kr[d] = cm.Ki[d] = 0.0;
+      FF hh = ff(0.0f);
+      if (ok) {
+        const FF amp = sm.amp[lane];
+        FF sa, ca;
+        sincos(ff_from(th[10]) + 0.25 * kPi - (2.0 * kPi) * frac_near(sm.ccyc[lane]), &sa, &ca);
+        for (int d = 0; d < s.n_det; ++d) {
+          const FF Pr = sm.P[2 * d][lane], Pi = sm.P[2 * d + 1][lane];
+          const FF kr = amp * (Pr * ca - Pi * sa), ki = amp * (Pr * sa + Pi * ca);
+          cm.Kr[d] = ff_to_double(kr);
+          cm.Ki[d] = ff_to_double(ki);
+          if (ncut > 0) hh = hh + (kr * kr + ki * ki) * ff_from(s.H[(int64_t)d * s.M + ncut - 1]);
+        }
+      }
+      cm.hh = ff_to_double(hh);
+      cm.ncut = ncut;
+      cm.flag = ok ? 0 : 1;
+      pc[p] = cm;
+      // rows that no bin loop visits: unphysical (-inf) or without an in-band bin (lnL = 0)
+      if (lnl && ncut == 0) lnl[p] = ok ? 0.0 : -INFINITY;
+    }
+    // largest cut of the batch: one atomic per warp
+    int nm = valid ? ncut : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
+    if (lane == 0 && nm > 0) atomicMax(&work[0], nm);
+    hist_last_window(valid ? ncut : 0, CH, hist);
+  }
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B,
                                                   PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
@@ -227,9 +385,15 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
                                                   int* __restrict__ hist, int CH, double* __restrict__ lnl) {
   // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
   cudaTriggerProgrammaticLaunchCompletion();
-  __shared__ ProSmem sm;
-  prologue_rows<MIXED>(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(),
-                       pm, pf, pc, work, hist, CH, lnl);
+  if constexpr (MIXED) {
+    __shared__ ProSmemFF sm;
+    prologue_rows_ff(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, pm, pc, work,
+                     hist, CH, lnl);
+  } else {
+    __shared__ ProSmem sm;
+    prologue_rows<false>(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(),
+                         pm, pf, pc, work, hist, CH, lnl);
+  }
 }
 
 // ---------------------------------------------------------------- windowed bin loop

@@ -27,7 +27,7 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
            "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
-           "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration")
+           "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval")
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
         L.gwl_get_tuning.argtypes = [P, C.POINTER(GwlTuning)]
         L.gwl_autotune.argtypes = [P, P, i64, i32, C.POINTER(GwlTuning), P]
         L.gwl_set_calibration.argtypes = [P, i32, P, d, d]
+        L.gwl_ff_eval.argtypes = [P, i64, i32, P, P]
         L.gwl_get_calibration.argtypes = [P, C.POINTER(i32), C.POINTER(i64)]
         L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
@@ -311,6 +312,17 @@ class Context:
 
     def launch_count(self) -> int:
         return lib().gwl_launch_count(self._h)
+
+
+GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN, GWL_FF_COS = range(4)
+
+
+def ff_eval(x, fn, stream=None):
+    """The library's float-float exp / log / sin / cos (GWL_FF_*) of a float64 CUDA tensor."""
+    import torch
+    out = torch.empty_like(x)
+    _check(lib().gwl_ff_eval(_ptr(x), x.numel(), int(fn), _ptr(out), _stream(stream)), "gwl_ff_eval")
+    return out
 
 
 # ---- convenience wrappers used by tests and the benchmark (torch tensors in, torch tensors out)

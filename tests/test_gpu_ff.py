@@ -1,0 +1,47 @@
+"""Accuracy of the float-float elementary functions that the mixed prologue computes on the FP32 pipe
+(gwl_ff_eval through the C ABI) against numpy's FP64 functions (correctly rounded to within 1 ulp)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1909_11873_gb300 import build, gwl
+    build.build()
+    return gwl
+
+
+def run(g, x, fn):
+    out = g.ff_eval(torch.from_numpy(np.ascontiguousarray(x)).cuda(), fn)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_ff_exp(g):
+    x = np.concatenate([np.linspace(-20.0, 20.0, 20001), np.random.default_rng(0).uniform(-12, 3, 20000),
+                        [0.0, -0.0, 1e-12, -1e-12]])
+    ref = np.exp(x)
+    assert np.max(np.abs(run(g, x, g.GWL_FF_EXP) - ref) / ref) < 6e-14
+
+
+def test_ff_log(g):
+    x = np.concatenate([np.geomspace(1e-8, 1e8, 20001), np.random.default_rng(1).uniform(0.01, 2.0, 20000),
+                        1.0 + np.linspace(-1e-6, 1e-6, 101)])
+    ref = np.log(x)
+    assert np.max(np.abs(run(g, x, g.GWL_FF_LOG) - ref) / np.maximum(np.abs(ref), 1.0)) < 6e-14
+
+
+@pytest.mark.parametrize("fn", ["sin", "cos"])
+def test_ff_sin_cos(g, fn):
+    """Absolute error over [-4 pi, 4 pi] (the prologue's angles lie in [-2 pi, 3 pi]), including quadrant
+    boundaries (multiples of pi/4) and zeros."""
+    k = np.arange(-16, 17)
+    x = np.concatenate([np.linspace(-4 * np.pi, 4 * np.pi, 40001), k * np.pi / 4,
+                        k * np.pi / 4 + 1e-9, k * np.pi / 4 - 1e-9,
+                        np.random.default_rng(2).uniform(-7.0, 7.0, 20000)])
+    code = g.GWL_FF_SIN if fn == "sin" else g.GWL_FF_COS
+    ref = np.sin(x) if fn == "sin" else np.cos(x)
+    assert np.max(np.abs(run(g, x, code) - ref)) < 6e-14
