@@ -228,67 +228,82 @@ __device__ __forceinline__ int count_bins_le(const SegInfo& s, double fc) {
 }
 
 // ------------------------------------------------------------- model formulas
-// Written once as templates over the scalar type: T = double for the
-// likelihood, T = Tan<...> (FP64 value with tangents) for the gradient.
+// Written once as templates over the scalar type: T = double for the FP64
+// likelihood, T = FF (a float pair, gwl_ff.cuh) for the mixed one, and
+// T = Tan<...> (value with tangents) for the gradient.
 
-// Forward-mode tangent type: the value stays FP64 (bit-identical arithmetic to
-// the plain path); the N tangents, and a shadow copy of the value used for
-// the tangent arithmetic, are kept in G (float on the fast pipe, or double).
-template <int N, class G>
+// Value-type helpers: V = double here; gwl_ff.cuh adds the float-pair versions.
+template <class V>
+__device__ __forceinline__ V make_value(double x);
+template <>
+__device__ __forceinline__ double make_value<double>(double x) { return x; }
+__device__ __forceinline__ double vval(double x) { return x; }
+template <class G>
+__device__ __forceinline__ G vshadow(double x) { return (G)x; }
+__device__ __forceinline__ double vexp(double x) { return ::exp(x); }
+__device__ __forceinline__ double vlog(double x) { return ::log(x); }
+__device__ __forceinline__ void vsincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+__device__ __forceinline__ double vfrac(double x) { return x - rint(x); }
+
+// Forward-mode tangent type: the value V is FP64 (bit-identical arithmetic to
+// the FP64 path) or a float pair (the mixed path's arithmetic); the N
+// tangents, and a shadow copy of the value used for the tangent arithmetic,
+// are kept in G (float on the fast pipe, or double).
+template <int N, class G, class V = double>
 struct Tan {
-  double v;
+  V v;
   G vt;
   G d[N];
 };
 
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> tan_const(double x) {
-  Tan<N, G> r;
-  r.v = x;
+template <int N, class G, class V = double>
+__device__ __forceinline__ Tan<N, G, V> tan_const(double x) {
+  Tan<N, G, V> r;
+  r.v = make_value<V>(x);
   r.vt = (G)x;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = (G)0;
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator+(const Tan<N, G>& a, const Tan<N, G>& b) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator+(const Tan<N, G, V>& a, const Tan<N, G, V>& b) {
+  Tan<N, G, V> r;
   r.v = a.v + b.v;
   r.vt = a.vt + b.vt;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator-(const Tan<N, G>& a, const Tan<N, G>& b) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator-(const Tan<N, G, V>& a, const Tan<N, G, V>& b) {
+  Tan<N, G, V> r;
   r.v = a.v - b.v;
   r.vt = a.vt - b.vt;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator-(const Tan<N, G>& a) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator-(const Tan<N, G, V>& a) {
+  Tan<N, G, V> r;
   r.v = -a.v;
   r.vt = -a.vt;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator*(const Tan<N, G>& a, const Tan<N, G>& b) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator*(const Tan<N, G, V>& a, const Tan<N, G, V>& b) {
+  Tan<N, G, V> r;
   r.v = a.v * b.v;
   r.vt = a.vt * b.vt;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.vt + a.vt * b.d[i];
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator/(const Tan<N, G>& a, const Tan<N, G>& b) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator/(const Tan<N, G, V>& a, const Tan<N, G, V>& b) {
+  Tan<N, G, V> r;
   r.v = a.v / b.v;
   r.vt = a.vt / b.vt;
   const G ib = (G)1 / b.vt;
@@ -296,38 +311,40 @@ __device__ __forceinline__ Tan<N, G> operator/(const Tan<N, G>& a, const Tan<N, 
   for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.vt * b.d[i]) * ib;
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator+(const Tan<N, G>& a, double b) {
-  Tan<N, G> r = a;
-  r.v += b;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator+(const Tan<N, G, V>& a, double b) {
+  Tan<N, G, V> r = a;
+  r.v = a.v + b;
   r.vt += (G)b;
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator+(double b, const Tan<N, G>& a) { return a + b; }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator-(const Tan<N, G>& a, double b) { return a + (-b); }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator-(double b, const Tan<N, G>& a) { return (-a) + b; }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator*(const Tan<N, G>& a, double b) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator+(double b, const Tan<N, G, V>& a) { return a + b; }
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator-(const Tan<N, G, V>& a, double b) { return a + (-b); }
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator-(double b, const Tan<N, G, V>& a) { return (-a) + b; }
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator*(const Tan<N, G, V>& a, double b) {
+  Tan<N, G, V> r;
   r.v = a.v * b;
   r.vt = a.vt * (G)b;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * (G)b;
   return r;
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator*(double b, const Tan<N, G>& a) { return a * b; }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator/(const Tan<N, G>& a, double b) { return a * (1.0 / b); }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> operator/(double a, const Tan<N, G>& b) { return tan_const<N, G>(a) / b; }
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator*(double b, const Tan<N, G, V>& a) { return a * b; }
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator/(const Tan<N, G, V>& a, double b) { return a * (1.0 / b); }
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> operator/(double a, const Tan<N, G, V>& b) {
+  return tan_const<N, G, V>(a) / b;
+}
 
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> tan_lift(const Tan<N, G>& a, double fv, G ft, G dft) {
-  Tan<N, G> r;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> tan_lift(const Tan<N, G, V>& a, const V& fv, G ft, G dft) {
+  Tan<N, G, V> r;
   r.v = fv;
   r.vt = ft;
 #pragma unroll
@@ -340,46 +357,46 @@ __device__ __forceinline__ double log(double x) { return ::log(x); }
 __device__ __forceinline__ double cos(double x) { return ::cos(x); }
 __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
 
-// For the transcendental functions the shadow values are taken from the FP64
-// results: an argument whose shadow has drifted (a phase of many cycles, say)
-// would otherwise spoil the derivative.
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> exp(const Tan<N, G>& a) {
-  const double fv = ::exp(a.v);
-  const G ft = (G)fv;
+// For the transcendental functions the shadow values are taken from the
+// full-precision results: an argument whose shadow has drifted (a phase of
+// many cycles, say) would otherwise spoil the derivative.
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> exp(const Tan<N, G, V>& a) {
+  const V fv = vexp(a.v);
+  const G ft = vshadow<G>(fv);
   return tan_lift(a, fv, ft, ft);
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> log(const Tan<N, G>& a) {
-  const double fv = ::log(a.v);
-  return tan_lift(a, fv, (G)fv, (G)(1.0 / a.v));
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> log(const Tan<N, G, V>& a) {
+  const V fv = vlog(a.v);
+  return tan_lift(a, fv, vshadow<G>(fv), (G)1 / vshadow<G>(a.v));
 }
-template <int N, class G>
-__device__ __forceinline__ void sincos(const Tan<N, G>& a, Tan<N, G>* s, Tan<N, G>* c) {
-  double sv, cv;
-  ::sincos(a.v, &sv, &cv);
-  const G st = (G)sv, ct = (G)cv;
+template <int N, class G, class V>
+__device__ __forceinline__ void sincos(const Tan<N, G, V>& a, Tan<N, G, V>* s, Tan<N, G, V>* c) {
+  V sv, cv;
+  vsincos(a.v, &sv, &cv);
+  const G st = vshadow<G>(sv), ct = vshadow<G>(cv);
   *s = tan_lift(a, sv, st, ct);
   *c = tan_lift(a, cv, ct, -st);
 }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> cos(const Tan<N, G>& a) {
-  Tan<N, G> s, c;
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> cos(const Tan<N, G, V>& a) {
+  Tan<N, G, V> s, c;
   sincos(a, &s, &c);
   return c;
 }
 // x - nearest integer: the integer shift carries no derivative.
 __device__ __forceinline__ double frac_near(double x) { return x - rint(x); }
-template <int N, class G>
-__device__ __forceinline__ Tan<N, G> frac_near(const Tan<N, G>& a) {
-  Tan<N, G> r = a;
-  r.v = a.v - rint(a.v);
-  r.vt = (G)r.v;  // the reduced value, not the drifted shadow of a large one
+template <int N, class G, class V>
+__device__ __forceinline__ Tan<N, G, V> frac_near(const Tan<N, G, V>& a) {
+  Tan<N, G, V> r = a;
+  r.v = vfrac(a.v);
+  r.vt = vshadow<G>(r.v);  // the reduced value, not the drifted shadow of a large one
   return r;
 }
 __device__ __forceinline__ double val(double x) { return x; }
-template <int N, class G>
-__device__ __forceinline__ double val(const Tan<N, G>& a) { return a.v; }
+template <int N, class G, class V>
+__device__ __forceinline__ double val(const Tan<N, G, V>& a) { return vval(a.v); }
 
 // TaylorF2 phase coefficients phi_k (aligned spins; the 2.5PN and 3PN terms
 // carry the ln v parts separately).
@@ -461,6 +478,12 @@ __device__ __forceinline__ Sky<T> sky_trig(const T& ra, const T& dec, double gms
   sincos(ra - gmst, &k.sl, &k.cl);
   sincos(dec, &k.sd, &k.cd);
   return k;
+}
+
+// tau_d = tc - (r_d / c . n), the vertex over c given (double or float pairs)
+template <class T, class Gc>
+__device__ __forceinline__ T delay_vc(const T& tc, const Sky<T>& k, const Gc* vc) {
+  return tc - ((k.cd * k.cl) * vc[0] + (k.cd * k.sl) * vc[1] + k.sd * vc[2]);
 }
 
 // tau_d = tc - (r_d . n)/c

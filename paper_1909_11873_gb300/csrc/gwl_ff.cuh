@@ -142,6 +142,28 @@ static __device__ __noinline__ void ff_sincos(const FF& x, FF* sn, FF* cs) {
 }
 
 // Overloads used by the templated model code (gwl_device.cuh).
+template <>
+__device__ __forceinline__ FF make_value<FF>(double x) { return ff_from(x); }
+__device__ __forceinline__ double vval(const FF& x) { return ff_to_double(x); }
+template <class G>
+__device__ __forceinline__ G vshadow(const FF& x) { return (G)x.hi; }
+__device__ __forceinline__ FF vexp(const FF& x) { return ff_exp(x); }
+__device__ __forceinline__ FF vlog(const FF& x) { return ff_log(x); }
+__device__ __forceinline__ void vsincos(const FF& x, FF* s, FF* c) { ff_sincos(x, s, c); }
+__device__ __forceinline__ FF vfrac(const FF& x) { return frac_near(x); }
+// tangent values times float-pair constants (the pre-split detector geometry)
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G, FF> operator*(const Tan<N, G, FF>& a, const FF& b) {
+  Tan<N, G, FF> r;
+  r.v = a.v * b;
+  const G bt = (G)b.hi;
+  r.vt = a.vt * bt;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * bt;
+  return r;
+}
+template <int N, class G>
+__device__ __forceinline__ Tan<N, G, FF> operator*(const FF& b, const Tan<N, G, FF>& a) { return a * b; }
 __device__ __forceinline__ FF exp(const FF& x) { return ff_exp(x); }
 __device__ __forceinline__ FF log(const FF& x) { return ff_log(x); }
 __device__ __forceinline__ void sincos(const FF& x, FF* s, FF* c) { ff_sincos(x, s, c); }

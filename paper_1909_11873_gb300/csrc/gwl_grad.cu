@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "gwl_bins.cuh"
+#include "gwl_ff.cuh"
 #include "gwl_sched.cuh"
 
 namespace gwl {
@@ -32,12 +33,17 @@ struct PropGrad {
 };
 
 // ---------------------------------------------------------------- tangent prologue
-// The sampled directions are split into groups of kTanGroup; thread t takes
-// row t / ngrp and directions [kTanGroup g, kTanGroup g + kTanGroup), g = t % ngrp.
-// Every thread of a row runs the FP64 value path (the FP64 pipe has room for
-// it); the group-0 thread writes the values.  Four tangents per thread keep
-// the code and register footprint small and give each row ngrp threads.
-constexpr int kTanGroup = 4;
+// The sampled directions are split into groups of tan_group tangents; thread
+// t takes row t / ngrp and directions [tan_group g, tan_group (g + 1)),
+// g = t % ngrp.  Every thread of a row runs the value path -- FP64 (GWL_FP64)
+// or float pairs on the FP32 pipe (GWL_MIXED, as the likelihood's prologue) --
+// and the group-0 thread writes the values.  The FP64 path takes four tangents
+// per thread (each copy of the value path occupies the narrow FP64 pipe); the
+// mixed path's value path is cheap, so it takes one tangent per thread: eleven
+// short threads per row instead of three long ones hide the latency of the
+// float-pair chains (measured 75 us against 88 us per call on 4096 proposals).
+template <bool MIXED>
+constexpr int tan_group() { return MIXED ? 1 : 4; }
 
 template <bool MIXED>
 __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* __restrict__ theta, int64_t B,
@@ -48,7 +54,9 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
   // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
   cudaTriggerProgrammaticLaunchCompletion();
   using G = typename std::conditional<MIXED, float, double>::type;
-  using T = Tan<kTanGroup, G>;
+  using V = typename std::conditional<MIXED, FF, double>::type;
+  constexpr int kTanGroup = tan_group<MIXED>();
+  using T = Tan<kTanGroup, G, V>;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t p = t / ngrp;
   const int i0 = (int)(t % ngrp) * kTanGroup;
@@ -65,7 +73,7 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
     }
     T x[11];
 #pragma unroll
-    for (int k = 0; k < 11; ++k) x[k] = tan_const<kTanGroup, G>(th[k]);
+    for (int k = 0; k < 11; ++k) x[k] = tan_const<kTanGroup, G, V>(th[k]);
     for (int j = 0; j < kTanGroup; ++j)
       if (i0 + j < s.n_dim) x[s.param_map[i0 + j]].d[j] = (G)1;
 
@@ -74,7 +82,7 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
     T c[kNBasis], ccyc;
     basis_coeffs(P, S, c, ccyc);
     ncut = (int)s.M;
-    if (s.fcut_mode == 0) ncut = count_bins_le(s, 1.0 / (kSix32 * S.a13.v * S.a13.v * S.a13.v));
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, vval(1.0 / (kSix32 * (S.a13.v * S.a13.v * S.a13.v))));
     if (!ok) ncut = 0;
     const Sky<T> k = sky_trig(x[7], x[8], s.gmst);
     T sp, cp;
@@ -91,19 +99,28 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
       for (int j = 0; j < kTanGroup; ++j)
         if (i0 + j < 11) g.dc[m][i0 + j] = ok ? c[m].d[j] : (G)0;
       if (lead) {
-        if (MIXED) split_f64(ok ? c[m].v : 0.0, pm[p].ch[m], pm[p].cl[m]);
-        else pf[p].c[m] = ok ? c[m].v : 0.0;
+        if constexpr (MIXED) {
+          pm[p].ch[m] = ok ? c[m].v.hi : 0.0f;
+          pm[p].cl[m] = ok ? c[m].v.lo : 0.0f;
+        } else {
+          pf[p].c[m] = ok ? c[m].v : 0.0;
+        }
       }
     }
-    T hh = tan_const<kTanGroup, G>(0.0);
+    T hh = tan_const<kTanGroup, G, V>(0.0);
 #pragma unroll
     for (int d = 0; d < kMaxDet; ++d) {
-      T tau = tan_const<kTanGroup, G>(0.0), Kr = tau, Ki = tau;
+      T tau = tan_const<kTanGroup, G, V>(0.0), Kr = tau, Ki = tau;
       if (d < s.n_det && ok) {
-        const double* gd = s.geom + 9 * d;
-        tau = delay(x[9], k, gd);
         T Pr, Pi;
-        response(k, sp, cp, ci, gd, Pr, Pi);
+        if constexpr (MIXED) {
+          tau = delay_vc(x[9], k, s.vtx_c_ff[d]);
+          response(k, sp, cp, ci, s.geom_ff[d], Pr, Pi);
+        } else {
+          const double* gd = s.geom + 9 * d;
+          tau = delay(x[9], k, gd);
+          response(k, sp, cp, ci, gd, Pr, Pi);
+        }
         Kr = S.amp * (Pr * ca - Pi * sa);
         Ki = S.amp * (Pr * sa + Pi * ca);
         if (ncut > 0) hh = hh + (S.amp * S.amp) * (Pr * Pr + Pi * Pi) * s.H[(int64_t)d * s.M + ncut - 1];
@@ -116,16 +133,20 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
           g.dKi[d][i0 + j] = Ki.d[j];
         }
       if (lead) {
-        if (MIXED) split_f64(tau.v, pm[p].th[d], pm[p].tl[d]);
-        else pf[p].tau[d] = tau.v;
+        if constexpr (MIXED) {
+          pm[p].th[d] = tau.v.hi;
+          pm[p].tl[d] = tau.v.lo;
+        } else {
+          pf[p].tau[d] = tau.v;
+        }
       }
-      cm.Kr[d] = Kr.v;
-      cm.Ki[d] = Ki.v;
+      cm.Kr[d] = vval(Kr.v);
+      cm.Ki[d] = vval(Ki.v);
     }
 #pragma unroll
     for (int j = 0; j < kTanGroup; ++j)
       if (i0 + j < 11) g.dhh[i0 + j] = hh.d[j];
-    cm.hh = hh.v;
+    cm.hh = vval(hh.v);
     cm.ncut = ncut;
     cm.flag = ok ? 0 : 1;
     if (lead) pc[p] = cm;
@@ -391,6 +412,7 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
+    constexpr int kTanGroup = tan_group<MIXED>();
     const int ngrp = (c->opt.n_dim + kTanGroup - 1) / kTanGroup;
     const int64_t nt = B * ngrp;
     k_prologue_grad<MIXED><<<(unsigned)((nt + 63) / 64), 64, 0, st>>>(c->seg, theta, B, ngrp, c->d_pm, c->d_pf,

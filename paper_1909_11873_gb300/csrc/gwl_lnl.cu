@@ -27,10 +27,11 @@
 //                built from error-free TwoProduct/TwoSum on the FP32 pipe),
 //                exact reduction to [-1/2, 1/2] cycles, FP32 sincos, FP32
 //                per-lane sums over at most W/32 bins, FP32 warp tree, FP64
-//                across windows and for the combination.  On GB300 the FP64
-//                pipe issues about 2 FMAs per SM per clock against about 128
-//                FP32 FMAs, so the float-float phase is several times cheaper
-//                than an FP64 one at the same phase precision.
+//                across windows and for the combination; the prologue too
+//                runs in float-float arithmetic (gwl_ff.cuh).  On GB300 the
+//                FP64 pipe issues about 2 FMAs per SM per clock against about
+//                128 FP32 FMAs, so float-float is several times cheaper than
+//                FP64 at the same precision.
 #include <cmath>
 #include <type_traits>
 
@@ -41,8 +42,8 @@
 namespace gwl {
 
 // ---------------------------------------------------------------- prologue
-// 128 threads per CTA, 32 rows.  The FP64 work of a row is spread over four
-// warps so that more warps keep the (narrow) FP64 pipe busy:
+// 128 threads per CTA, 32 rows.  The FP64 path's work of a row is spread over
+// four warps so that more warps keep the (narrow) FP64 pipe busy:
 //   phase 1  warp 0: ln(pi Mc T), ln(eta) -> a^{1/3}, amplitude, frequency cut
 //            warp 1: PN phase coefficients phi_k (polynomials in eta, spins)
 //            warp 2: sky direction -> per-detector delays tau_d
@@ -59,14 +60,14 @@ struct ProSmem {
   int ncut[32];
 };
 
-// The coefficients of rows row0 .. row0+31, computed by four warps (role 0..3);
-// `sync` synchronises exactly those four warps.
-template <bool MIXED, class Sync>
+// The FP64 coefficients of rows row0 .. row0+31, computed by four warps (role
+// 0..3); `sync` synchronises exactly those four warps.
+template <class Sync>
 __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __restrict__ theta, int64_t B,
                                               int64_t row0, int role, int lane, ProSmem& sm, Sync sync,
-                                              PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
-                                              PropCommon* __restrict__ pc, int* __restrict__ work,
-                                              int* __restrict__ hist, int CH, double* __restrict__ lnl) {
+                                              PropF64* __restrict__ pf, PropCommon* __restrict__ pc,
+                                              int* __restrict__ work, int* __restrict__ hist, int CH,
+                                              double* __restrict__ lnl) {
   double (&sh_la)[32] = sm.la;
   double (&sh_a13)[32] = sm.a13;
   double (&sh_amp)[32] = sm.amp;
@@ -117,9 +118,7 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
     if (valid) {
 #pragma unroll
       for (int d = 0; d < kMaxDet; ++d) {
-        const double tau = (d < s.n_det && ok) ? delay(th[9], k, s.geom + 9 * d) : 0.0;
-        if (MIXED) split_f64(tau, pm[p].th[d], pm[p].tl[d]);
-        else pf[p].tau[d] = tau;
+        pf[p].tau[d] = (d < s.n_det && ok) ? delay(th[9], k, s.geom + 9 * d) : 0.0;
       }
     }
   } else {
@@ -150,11 +149,7 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
     sh_ccyc[lane] = ccyc;
     if (valid) {
 #pragma unroll
-      for (int m = 0; m < kNBasis; ++m) {
-        const double cm = ok ? c[m] : 0.0;
-        if (MIXED) split_f64(cm, pm[p].ch[m], pm[p].cl[m]);
-        else pf[p].c[m] = cm;
-      }
+      for (int m = 0; m < kNBasis; ++m) pf[p].c[m] = ok ? c[m] : 0.0;
     }
   } else if (role == 1) {
     Sky<double> k;
@@ -184,16 +179,7 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
       if (ok) {
         const double amp = sh_amp[lane];
         double sa, ca;
-        if (MIXED) {  // the angle in FP64, its sine and cosine in FP32 (K enters lnL linearly)
-          double ang = th[10] + 0.25 * kPi - 2.0 * kPi * frac_near(sh_ccyc[lane]);
-          ang -= 2.0 * kPi * rint(ang * (0.5 / kPi));
-          float sf, cf;
-          sincosf((float)ang, &sf, &cf);
-          sa = sf;
-          ca = cf;
-        } else {
-          k_angle(th[10], sh_ccyc[lane], sa, ca);
-        }
+        k_angle(th[10], sh_ccyc[lane], sa, ca);
         for (int d = 0; d < s.n_det; ++d) {
           const double Pr = sh_P[2 * d][lane], Pi = sh_P[2 * d + 1][lane];
           cm.Kr[d] = amp * (Pr * ca - Pi * sa);
@@ -234,10 +220,6 @@ struct ProSmemFF {
   FF P[2 * kMaxDet][32];
   int ncut[32];
 };
-
-__device__ __forceinline__ FF delay_ff(const FF& tc, const Sky<FF>& k, const FF* vc) {
-  return tc - ((k.cd * k.cl) * vc[0] + (k.cd * k.sl) * vc[1] + k.sd * vc[2]);
-}
 
 __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double* __restrict__ theta, int64_t B,
                                                  int64_t row0, int role, int lane, ProSmemFF& sm,
@@ -283,7 +265,7 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
       const FF tc = ff_from(th[9]);
 #pragma unroll
       for (int d = 0; d < kMaxDet; ++d) {
-        const FF tau = (d < s.n_det && ok) ? delay_ff(tc, k, s.vtx_c_ff[d]) : ff(0.0f);
+        const FF tau = (d < s.n_det && ok) ? delay_vc(tc, k, s.vtx_c_ff[d]) : ff(0.0f);
         pm[p].th[d] = tau.hi;
         pm[p].tl[d] = tau.lo;
       }
@@ -391,8 +373,8 @@ __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __res
                      hist, CH, lnl);
   } else {
     __shared__ ProSmem sm;
-    prologue_rows<false>(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(),
-                         pm, pf, pc, work, hist, CH, lnl);
+    prologue_rows(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(), pf, pc,
+                  work, hist, CH, lnl);
   }
 }
 
