@@ -260,7 +260,7 @@ template <int N, class G, class V = double>
 __device__ __forceinline__ Tan<N, G, V> tan_const(double x) {
   Tan<N, G, V> r;
   r.v = make_value<V>(x);
-  r.vt = (G)x;
+  r.vt = vshadow<G>(r.v);
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = (G)0;
   return r;

@@ -29,13 +29,42 @@ namespace gwl {
 // A double constant as a float pair (folded at compile time for literals).
 __host__ __device__ constexpr FF ffc(double x) { return FF{(float)x, (float)(x - (double)(float)x)}; }
 __device__ __forceinline__ FF ff(float x) { return FF{x, 0.0f}; }
-// A run-time double as a float pair, and back (f32<->f64 conversions: keep them few).
+// A run-time double as a float pair, and back, with integer operations: on
+// GB300 an f32<->f64 conversion instruction occupies the narrow FP64 unit.
+// hi = x truncated to 24 significant bits (an exact float), lo = the
+// remaining 29 mantissa bits rounded to a float (integer-valued floats built
+// by the 2^23 bias trick, then scaled by a power of two): hi + lo = x to about
+// 2^-48.  Zero and subnormal doubles give zero; |x| outside [2^-70, 2^100]
+// (not met by the prologues' inputs) takes the conversion instructions.
 __device__ __forceinline__ FF ff_from(double x) {
-  FF r;
-  split_f64(x, r.hi, r.lo);
-  return r;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return FF{0.0f, 0.0f};
+  if (e < 1023 - 70 || e > 1023 + 100) {
+    FF r;
+    split_f64(x, r.hi, r.lo);
+    return r;
+  }
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+  const unsigned ml = (unsigned)(m & 0x1FFFFFFFu);
+  const float a = __fsub_rn(__uint_as_float(0x4B000000u | (ml >> 23)), 8388608.0f);       // top 6 bits
+  const float c = __fsub_rn(__uint_as_float(0x4B000000u | (ml & 0x7FFFFFu)), 8388608.0f);  // low 23 bits
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);                   // 2^(e - 1075)
+  const float lo = __fmul_rn(__fmaf_rn(a, 8388608.0f, c), scale);
+  return FF{hi, sign ? -lo : lo};
 }
-__device__ __forceinline__ double ff_to_double(const FF& a) { return (double)a.hi + (double)a.lo; }
+// A float widened to double exactly (normal floats and zero; subnormal floats give zero).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)s);
+  return __longlong_as_double((long long)(s | ((unsigned long long)(e - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double ff_to_double(const FF& a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
 // s + e renormalised, for |e| <= |s| or s == 0 (Fast2Sum).
 __device__ __forceinline__ FF ff_norm(float s, float e) {
@@ -142,6 +171,13 @@ static __device__ __noinline__ void ff_sincos(const FF& x, FF* sn, FF* cs) {
 }
 
 // Overloads used by the templated model code (gwl_device.cuh).
+// K's phase angle: the float-pair sine and cosine reduce by pi/2 themselves, so
+// the 2 pi reduction (an FP64 rint) of the generic version is not needed.
+template <int N, class G>
+__device__ __forceinline__ void k_angle(const Tan<N, G, FF>& phic, const Tan<N, G, FF>& ccyc, Tan<N, G, FF>& sa,
+                                        Tan<N, G, FF>& ca) {
+  sincos(phic + (0.25 * kPi) - (2.0 * kPi) * frac_near(ccyc), &sa, &ca);
+}
 template <>
 __device__ __forceinline__ FF make_value<FF>(double x) { return ff_from(x); }
 __device__ __forceinline__ double vval(const FF& x) { return ff_to_double(x); }

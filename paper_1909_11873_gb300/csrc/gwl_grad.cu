@@ -123,7 +123,11 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
         }
         Kr = S.amp * (Pr * ca - Pi * sa);
         Ki = S.amp * (Pr * sa + Pi * ca);
-        if (ncut > 0) hh = hh + (S.amp * S.amp) * (Pr * Pr + Pi * Pi) * s.H[(int64_t)d * s.M + ncut - 1];
+        if (ncut > 0) {
+          const double Hd = s.H[(int64_t)d * s.M + ncut - 1];
+          if constexpr (MIXED) hh = hh + (S.amp * S.amp) * (Pr * Pr + Pi * Pi) * ff_from(Hd);
+          else hh = hh + (S.amp * S.amp) * (Pr * Pr + Pi * Pi) * Hd;
+        }
       }
 #pragma unroll
       for (int j = 0; j < kTanGroup; ++j)

@@ -436,25 +436,33 @@ __device__ __forceinline__ double combine_lnl(const PropCommon* __restrict__ c, 
   return t - 0.5 * c->hh;
 }
 
-// Node data of proposal p for the warp's calibration splines: lane o of the
-// 2 NDET nn outputs (spline s = 2 d + q, q = 0 amplitude, 1 phase; node k)
-// forms m_k = sum_i Q_ki y_i and stores (y_k, m_k), the phase scaled to cycles.
+// Node data of proposal p for the warp's calibration splines (spline
+// s = 2 d + q, q = 0 amplitude, 1 phase; node k): the lanes first store the
+// node values y_k (the phase scaled to cycles; in the mixed path each is read
+// from theta and narrowed once, by integer operations), then form the
+// curvatures m_k = sum_i Q_ki y_i from the stored values.
 template <int NDET, bool MIXED, typename Node>
 __device__ __forceinline__ void cal_nodes(const WinArgs& a, int64_t p, int lane, Node* __restrict__ nd) {
   using T = typename std::conditional<MIXED, float, double>::type;
-  const double* y = a.theta + p * a.stride + a.cal_par;
+  const double* y = a.theta + p * a.stride + a.cal_par;  // [NDET][2][nn], index s nn + k
   const T* Q = reinterpret_cast<const T*>(a.calQ);
   const int nn = a.nn;
   __syncwarp();  // the warp is done with the previous proposal's node data
   for (int o = lane; o < 2 * NDET * nn; o += 32) {
     const int sp = o / nn, k = o - sp * nn;
-    const double* ys = y + (int64_t)sp * nn;
+    const double yd = __ldg(y + o);
+    T yv;
+    if constexpr (MIXED) yv = ff_from(yd).hi;
+    else yv = yd;
+    reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k])[2 * (sp & 1)] = (sp & 1) ? yv * (T)(0.5 / kPi) : yv;
+  }
+  __syncwarp();
+  for (int o = lane; o < 2 * NDET * nn; o += 32) {
+    const int sp = o / nn, k = o - sp * nn;
+    const T* ys = reinterpret_cast<const T*>(&nd[(sp >> 1) * kMaxCalNodes]) + 2 * (sp & 1);  // stride 4 T
     T m = (T)0;
-    for (int i = 0; i < nn; ++i) m = fma(Q[k * nn + i], (T)__ldg(ys + i), m);
-    const T sc = (sp & 1) ? (T)(0.5 / kPi) : (T)1;
-    T* e = reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k]) + 2 * (sp & 1);
-    e[0] = (T)__ldg(ys + k) * sc;
-    e[1] = m * sc;
+    for (int i = 0; i < nn; ++i) m = fma(Q[k * nn + i], ys[4 * i], m);
+    reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k])[2 * (sp & 1) + 1] = m;
   }
   __syncwarp();
 }
