@@ -1,5 +1,9 @@
 """Accuracy of the float-float elementary functions that the mixed prologue computes on the FP32 pipe
-(gwl_ff_eval through the C ABI) against numpy's FP64 functions (correctly rounded to within 1 ulp)."""
+(gwl_ff_eval through the C ABI) against numpy's FP64 functions (correctly rounded to within 1 ulp).
+
+The argument itself is held as a float pair (about 48 bits: |dx| <= 2^-48 |x|), so each bar is 3e-14
+for the function plus the argument's representation error carried through it (2^-47 |x| for exp, sin
+and cos; 2^-47 for ln).  The prologue needs ~1e-12 (the phase coefficients)."""
 import numpy as np
 import pytest
 
@@ -24,14 +28,14 @@ def test_ff_exp(g):
     x = np.concatenate([np.linspace(-20.0, 20.0, 20001), np.random.default_rng(0).uniform(-12, 3, 20000),
                         [0.0, -0.0, 1e-12, -1e-12]])
     ref = np.exp(x)
-    assert np.max(np.abs(run(g, x, g.GWL_FF_EXP) - ref) / ref) < 6e-14
+    assert np.all(np.abs(run(g, x, g.GWL_FF_EXP) - ref) / ref < 3e-14 + 2.0 ** -47 * np.abs(x))
 
 
 def test_ff_log(g):
     x = np.concatenate([np.geomspace(1e-8, 1e8, 20001), np.random.default_rng(1).uniform(0.01, 2.0, 20000),
                         1.0 + np.linspace(-1e-6, 1e-6, 101)])
     ref = np.log(x)
-    assert np.max(np.abs(run(g, x, g.GWL_FF_LOG) - ref) / np.maximum(np.abs(ref), 1.0)) < 6e-14
+    assert np.all(np.abs(run(g, x, g.GWL_FF_LOG) - ref) / np.maximum(np.abs(ref), 1.0) < 3e-14 + 2.0 ** -47)
 
 
 @pytest.mark.parametrize("fn", ["sin", "cos"])
@@ -44,4 +48,4 @@ def test_ff_sin_cos(g, fn):
                         np.random.default_rng(2).uniform(-7.0, 7.0, 20000)])
     code = g.GWL_FF_SIN if fn == "sin" else g.GWL_FF_COS
     ref = np.sin(x) if fn == "sin" else np.cos(x)
-    assert np.max(np.abs(run(g, x, code) - ref)) < 6e-14
+    assert np.all(np.abs(run(g, x, code) - ref) < 3e-14 + 2.0 ** -47 * np.abs(x))
