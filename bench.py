@@ -339,11 +339,12 @@ def run_gwl(args):
     stream = torch.cuda.current_stream()
 
     def timed(ctx, steps, warmup, host=False, soak=0.0, nvtx=None):
-        pin_t = torch.from_numpy(theta_np).pin_memory() if host else None
-        pin_l = torch.empty(BATCH, dtype=torch.float64).pin_memory() if host else None
+        # pinned host buffers, as a caller would hold them (numpy views made once)
+        host_t = torch.from_numpy(theta_np).pin_memory().numpy() if host else None
+        host_l = torch.empty(BATCH, dtype=torch.float64).pin_memory().numpy() if host else None
         for _ in range(warmup):
             if host:
-                ctx.gwl_loglike_host(pin_t.numpy(), pin_l.numpy(), stream)
+                ctx.gwl_loglike_host(host_t, host_l, stream)
             else:
                 ctx.gwl_loglike(theta, lnl, stream)
         torch.cuda.synchronize()
@@ -366,7 +367,7 @@ def run_gwl(args):
             flush.fill_(1.0)
             e0.record(stream)
             if host:
-                ctx.gwl_loglike_host(pin_t.numpy(), pin_l.numpy(), stream)
+                ctx.gwl_loglike_host(host_t, host_l, stream)
             else:
                 ctx.gwl_loglike(theta, lnl, stream)
             e1.record(stream)

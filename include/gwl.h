@@ -123,8 +123,11 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
  * B >= 0 (B = 0 is a no-op). */
 int gwl_loglike(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, void* stream);
 
-/* As gwl_loglike with host buffers: copies theta to the device, evaluates,
- * copies lnL back and synchronises the stream before returning. */
+/* As gwl_loglike with host buffers, synchronising the stream before
+ * returning.  Page-locked (pinned) buffers are read and written in place by
+ * the kernels (device-accessible under unified addressing; on GB300 over the
+ * CPU-GPU link), so no staging copies are made; pageable buffers are copied
+ * through device memory. */
 int gwl_loglike_host(gwl_ctx* ctx, const double* theta_host, int64_t B, double* lnl_host,
                      void* stream);
 

@@ -165,6 +165,19 @@ int walk_supported(const gwl_ctx* c, const char* what) {
   return GWL_OK;
 }
 
+// The device address of a page-locked host buffer (device-accessible under
+// unified addressing), or null for pageable memory.
+template <class T>
+T* mapped_host(T* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<T*>(a.devicePointer);
+}
+
 int check_ctx(const gwl_ctx* c) {
   if (!c) return fail(GWL_ERR_ARG, "null context");
   int dev = -1;
@@ -341,11 +354,22 @@ int gwl_loglike_host(gwl_ctx* c, const double* theta_host, int64_t B, double* ln
   const int64_t nt = B * gwl::theta_stride(c);
   if ((rc = ensure_io(c, nt + B))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(c->d_io, theta_host, sizeof(double) * nt, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "copy theta");
-  if ((rc = gwl_loglike(c, c->d_io, B, c->d_io + nt, stream))) return rc;
-  e = cudaMemcpyAsync(lnl_host, c->d_io + nt, sizeof(double) * B, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return cuda_fail(e, "copy lnL");
+  // page-locked buffers are read and written in place by the kernels; pageable ones are staged
+  const double* th_dev = mapped_host(theta_host);
+  double* l_dev = mapped_host(lnl_host);
+  cudaError_t e = cudaSuccess;
+  if (!th_dev) {
+    th_dev = c->d_io;
+    e = cudaMemcpyAsync(c->d_io, theta_host, sizeof(double) * nt, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy theta");
+  }
+  const bool stage_out = l_dev == nullptr;
+  if (stage_out) l_dev = c->d_io + nt;
+  if ((rc = gwl_loglike(c, th_dev, B, l_dev, stream))) return rc;
+  if (stage_out) {
+    e = cudaMemcpyAsync(lnl_host, l_dev, sizeof(double) * B, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "copy lnL");
+  }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "synchronise");
   return GWL_OK;

@@ -143,3 +143,21 @@ def test_waveform_matches_oracle():
         ref = oracle.waveform(ev, th[b])
         got = h[b, ..., 0] + 1j * h[b, ..., 1]
         assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_entry_point_pinned_and_pageable(precision):
+    """gwl_loglike_host gives the device entry point's results bit for bit, with page-locked buffers (read
+    and written in place by the kernels), pageable buffers (staged) and a mix of the two."""
+    g = gwl()
+    ev = event("c2")
+    rows = np.ascontiguousarray(I.reduced(I.proposals(ev, 3000, 8), ev.sampling))
+    ctx = g.Context.from_event(ev, precision)
+    ref = g.loglike(ctx, torch.from_numpy(rows).cuda()).cpu().numpy()
+    pin_t = torch.from_numpy(rows).pin_memory().numpy()
+    pin_l = torch.zeros(3000, dtype=torch.float64).pin_memory().numpy()
+    page_l = np.zeros(3000)
+    for t, l in ((pin_t, pin_l), (rows, page_l), (pin_t, page_l), (rows, pin_l)):
+        l[:] = 0.0
+        ctx.gwl_loglike_host(t, l)
+        assert np.array_equal(l, ref)
