@@ -167,6 +167,8 @@ __device__ __forceinline__ void prologue_rows(const SegInfo& s, const double* __
     }
   }
   sync();
+  // the work counters (cleared by the preceding kernel) are touched from here on
+  cudaGridDependencySynchronize();
 
   // ---- phase 3
   if (role == 2) {
@@ -323,6 +325,8 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
     }
   }
   __syncthreads();
+  // the work counters (cleared by the preceding kernel) are touched from here on
+  cudaGridDependencySynchronize();
 
   // ---- phase 3
   if (role == 2) {
@@ -797,22 +801,39 @@ static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t sme
   return e;
 }
 
+// Clears the work counters; lets the prologue launch at once (it waits for
+// this grid only before its first counter update, in its last phase).
+__global__ void k_clear_work(int* __restrict__ work, int64_t n) {
+  cudaTriggerProgrammaticLaunchCompletion();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    work[i] = 0;
+}
+
+static cudaError_t launch_clear_work(gwl_ctx* c, int* work, int64_t n, cudaStream_t st) {
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  k_clear_work<<<nb < 64 ? nb : 64, 256, 0, st>>>(work, n);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 // Prologue of rows [0, B) of theta into the coefficient arrays at row offset
-// `off`, with `work` the counter region (zeroed by the caller).
+// `off`, with `work` the counter region (cleared just before, by a memset or
+// k_clear_work; launched as a programmatic dependent of the latter).
 static cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int64_t off, int precision,
                                    double* lnl, int* work, cudaStream_t st) {
   ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
   const unsigned nb = (unsigned)((B + 31) / 32);
   int* hist = work + 1 + nw_max(c);
   const int CH = window_of(c, precision);
+  cudaError_t e;
   if (precision == GWL_MIXED)
-    k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm + off, c->d_pf + off, c->d_pc + off, work, hist,
-                                         CH, lnl);
+    e = launch_pdl(k_prologue<true>, dim3(nb), dim3(128), 0, st, c->seg, theta, B, c->d_pm + off, c->d_pf + off,
+                   c->d_pc + off, work, hist, CH, lnl);
   else
-    k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm + off, c->d_pf + off, c->d_pc + off, work, hist,
-                                          CH, lnl);
+    e = launch_pdl(k_prologue<false>, dim3(nb), dim3(128), 0, st, c->seg, theta, B, c->d_pm + off, c->d_pf + off,
+                   c->d_pc + off, work, hist, CH, lnl);
   c->launches++;
-  return cudaGetLastError();
+  return e;
 }
 
 // The bin loop (which also forms lnL) of rows [off, off + B) of the batch.
@@ -876,7 +897,7 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
 // prologue drains and wait for its results).
 template <int NDET>
 static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
+  cudaError_t e = launch_clear_work(c, c->d_work, work_needed(c, B), st);
   if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st);
   if (e == cudaSuccess) e = launch_bins<NDET>(c, theta, B, 0, lnl, c->d_work, true, st);
   return e;
