@@ -262,8 +262,8 @@ __device__ __forceinline__ void bin_anchor(const float (&v)[4 * ((kNBasis + 2 * 
   ds = __fsub_rn(ds, nearest_int(ds));  // exact
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    const float x = __fadd_rn(ds, ad[d]);
-    float fr = __fsub_rn(x, nearest_int(x));
+    // |ds + ad| < 1.5 cycles: the hardware sine and cosine take it unreduced
+    float fr = __fadd_rn(ds, ad[d]);
     float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
     cal_apply<CAL>(fr, gr, gi, cb.A[d], cb.P[d], cb.H[d], X[d]);
     float sn, cs;
@@ -299,8 +299,8 @@ __device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBa
   const float ds = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    const float x = __fadd_rn(ds, ad[d]);
-    float fr = __fsub_rn(x, nearest_int(x));
+    // |ds + ad| < 1.5 cycles: the hardware sine and cosine take it unreduced
+    float fr = __fadd_rn(ds, ad[d]);
     float gr = v[kNBasis + 2 * d], gi = v[kNBasis + 2 * d + 1];
     cal_apply<CAL>(fr, gr, gi, cb.A[d], cb.P[d], cb.H[d], X[d]);
     float sn, cs;
