@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
       }
     }
     T hh = tan_const<kTanGroup, G, V>(0.0);
-#pragma unroll
-    for (int d = 0; d < kMaxDet; ++d) {
+#pragma unroll 1
+    for (int d = 0; d < kMaxDet; ++d) {  // rolled: the per-detector tangent code is long
       T tau = tan_const<kTanGroup, G, V>(0.0), Kr = tau, Ki = tau;
       if (d < s.n_det && ok) {
         T Pr, Pi;
