@@ -316,10 +316,13 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
     s.t_ref = opt->t_ref;
     s.n_dim = opt->n_dim;
     s.stride = opt->n_dim;
+    s.inv_df = 1.0 / df;
     for (int k = 0; k < GWL_N_PARAM; ++k) {
       s.fixed[k] = opt->fixed_theta[k];
       s.param_map[k] = k < opt->n_dim ? opt->param_map[k] : 0;
+      s.param_pos[k] = -1;
     }
+    for (int i = 0; i < opt->n_dim; ++i) s.param_pos[opt->param_map[i]] = i;
   } while (false);
   if (d_strain) cudaFree(d_strain);
   if (d_psd) cudaFree(d_psd);

@@ -116,7 +116,9 @@ struct SegInfo {
   int n_dim;
   int stride;
   int param_map[11];
+  int param_pos[11];  // inverse of param_map: the row position of parameter k, -1 when fixed
   double fixed[11];
+  double inv_df;      // 1 / df
   // float-float copies for the mixed prologue: the detector geometry, the
   // vertex over c (delays) and the amplitude constant
   // sqrt(5/24) pi^{-2/3} c / Mpc * amp_scale
@@ -200,10 +202,11 @@ constexpr double kSix32 = 14.696938456699069;           // 6^{3/2}
 constexpr double kAmpConst = 0.21278751013966343;       // sqrt(5/24) pi^{-2/3}
 
 // Full 11-D parameter vector from the sampled coordinates of one row.
+// One compile-time index per parameter: th stays in registers and the row's
+// loads are all issued before the first is used.
 __device__ __forceinline__ void expand_theta(const SegInfo& s, const double* row, double th[11]) {
 #pragma unroll
-  for (int k = 0; k < 11; ++k) th[k] = s.fixed[k];
-  for (int i = 0; i < s.n_dim; ++i) th[s.param_map[i]] = row[i];
+  for (int k = 0; k < 11; ++k) th[k] = s.param_pos[k] >= 0 ? row[s.param_pos[k]] : s.fixed[k];
 }
 
 __device__ __forceinline__ bool physical(const double th[11]) {
@@ -213,10 +216,19 @@ __device__ __forceinline__ bool physical(const double th[11]) {
   return ok;
 }
 
-// Number of bins with freqs[j] <= fc (bins ascend): estimate from the grid,
-// then settle against the stored FP64 frequencies so the decision matches a
-// per-bin comparison exactly.
+// Number of bins with freqs[j] <= fc (bins ascend).  The stored frequencies
+// lie within 1e-9 df of f0 + j df (checked when the context is made), so when
+// x = (fc - f0) / df is more than 1e-7 from an integer the count follows from
+// x alone; otherwise it is settled against the stored FP64 frequencies.  Either
+// way the decision matches a per-bin comparison exactly.
 __device__ __forceinline__ int count_bins_le(const SegInfo& s, double fc) {
+  const double x = (fc - s.f0) * s.inv_df;
+  const double jf = floor(x), r = x - jf;
+  if (r > 1e-7 && r < 1.0 - 1e-7) {
+    if (jf < 0.0) return 0;
+    if (jf >= (double)(s.M - 1)) return (int)s.M;
+    return (int)jf + 1;
+  }
   if (!(fc >= s.freqs[0])) return 0;
   if (fc >= s.freqs[s.M - 1]) return (int)s.M;
   int64_t j = (int64_t)floor((fc - s.f0) / s.df);
@@ -450,12 +462,21 @@ __device__ __forceinline__ Scale<T> mass_scale(const T& mc, const T& eta, const 
   return o;
 }
 
+// The 2.5PN term's constant phase phi5 (1 + ln a - 3 ln v_lso) in cycles,
+// v_lso = 6^{-1/2}, given pref = 3 / (128 eta) / (2 pi).
+template <class T>
+__device__ __forceinline__ T const_cycles(const T& pref, const T& p5c, const T& la) {
+  return pref * p5c * (la + (1.0 + 1.5 * kLn6));
+}
+template <class T>
+__device__ __forceinline__ T cycles_pref(const T& eta) { return (3.0 / (128.0 * 2.0 * kPi)) / eta; }
+
 // Basis coefficients c_m [cycles] and the constant PN phase [cycles]:
 // v^k = (a f)^{k/3}, so a^{k/3} folds into c_m; 3 ln v = ln a + ln f.
 template <class T>
 __device__ __forceinline__ void basis_coeffs(const PNCoeffs<T>& P, const Scale<T>& S, T (&c)[kNBasis], T& ccyc) {
   const T am13 = 1.0 / S.a13, am23 = am13 * am13;
-  const T pref = (3.0 / (128.0 * 2.0 * kPi)) / P.eta;  // radians -> cycles
+  const T pref = cycles_pref(P.eta);  // radians -> cycles
   c[0] = pref * am23 * am23 * am13;                                                // f^{-5/3}
   c[1] = pref * P.p2 * am23 * am13;                                                // f^{-1}
   c[2] = pref * P.p3 * am23;                                                       // f^{-2/3}
@@ -464,7 +485,7 @@ __device__ __forceinline__ void basis_coeffs(const PNCoeffs<T>& P, const Scale<T
   c[5] = pref * S.a13 * (P.p6c - (6848.0 / 21.0) * kLn4 - (6848.0 / 63.0) * S.la);  // f^{1/3}
   c[6] = pref * S.a13 * (-6848.0 / 63.0);                                          // f^{1/3} ln f
   c[7] = pref * P.p7 * S.a13 * S.a13;                                              // f^{2/3}
-  ccyc = pref * P.p5c * (S.la + (1.0 + 1.5 * kLn6));  // phi5 (1 + ln a - 3 ln v_lso), v_lso = 6^{-1/2}
+  ccyc = const_cycles(pref, P.p5c, S.la);
 }
 
 // Sky direction n = (cos dec cos lam, cos dec sin lam, sin dec), lam = ra - gmst.

@@ -74,8 +74,13 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
     T x[11];
 #pragma unroll
     for (int k = 0; k < 11; ++k) x[k] = tan_const<kTanGroup, G, V>(th[k]);
-    for (int j = 0; j < kTanGroup; ++j)
-      if (i0 + j < s.n_dim) x[s.param_map[i0 + j]].d[j] = (G)1;
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+      const int j = s.param_pos[k] - i0;  // this thread's tangent slot of parameter k, if any
+#pragma unroll
+      for (int jj = 0; jj < kTanGroup; ++jj)
+        if (j == jj) x[k].d[jj] = (G)1;
+    }
 
     const PNCoeffs<T> P = pn_coeffs(x[1], x[2], x[3]);
     const Scale<T> S = mass_scale(x[0], P.eta, x[4], s.amp_scale);

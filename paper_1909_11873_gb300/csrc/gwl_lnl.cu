@@ -215,11 +215,12 @@ struct CtaSync {
 // the double outputs K_d, <h|h>.  The phase of K_d also gets the float-float
 // sine and cosine.
 struct ProSmemFF {
-  FF lmc[32], leta[32], a13[32], amp[32], ccyc[32], eta[32];
+  FF lmc[32], leta[32], amp[32], eta[32];
   FF phi[6][32];
   FF sky[4][32];
   FF ori[3][32];
   FF P[2 * kMaxDet][32];
+  double Hc[kMaxDet][32];  // H_d at the cut bin
   int ncut[32];
 };
 
@@ -281,16 +282,15 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
   }
   __syncthreads();
 
-  // ---- phase 2
+  // ---- phase 2: the basis coefficients (warp 0), the antenna patterns (warp 1),
+  // K's phase angle (warp 2, which keeps it for phase 3) and the cut bin with the
+  // <h|h> prefix entries there (warp 3: its global loads leave phase 3 free of them)
+  FF sa, ca;
   if (role == 0) {
     Scale<FF> S;
     S.la = sm.lmc[lane] - 0.6 * sm.leta[lane];
     S.a13 = exp(S.la * (1.0 / 3.0));
     S.amp = sm.amp[lane];
-    sm.a13[lane] = S.a13;
-    int ncut = (int)s.M;
-    if (s.fcut_mode == 0) ncut = count_bins_le(s, ff_to_double(1.0 / (kSix32 * (S.a13 * S.a13 * S.a13))));
-    sm.ncut[lane] = ok ? ncut : 0;
     PNCoeffs<FF> P;
     P.eta = sm.eta[lane];
     P.p2 = sm.phi[0][lane];
@@ -301,7 +301,6 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
     P.p7 = sm.phi[5][lane];
     FF c[kNBasis], ccyc;
     basis_coeffs(P, S, c, ccyc);
-    sm.ccyc[lane] = ccyc;
     if (valid) {
 #pragma unroll
       for (int m = 0; m < kNBasis; ++m) {
@@ -323,6 +322,20 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
       sm.P[2 * d][lane] = Pr;
       sm.P[2 * d + 1][lane] = Pi;
     }
+  } else if (role == 2) {
+    // the same constant-phase cycles as basis_coeffs forms on warp 0
+    const FF la = sm.lmc[lane] - 0.6 * sm.leta[lane];
+    const FF ccyc = const_cycles(cycles_pref(sm.eta[lane]), sm.phi[3][lane], la);
+    sincos(ff_from(th[10]) + 0.25 * kPi - (2.0 * kPi) * frac_near(ccyc), &sa, &ca);
+  } else {
+    const FF la = sm.lmc[lane] - 0.6 * sm.leta[lane];
+    const FF a13 = exp(la * (1.0 / 3.0));
+    int ncut = (int)s.M;
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, ff_to_double(1.0 / (kSix32 * (a13 * a13 * a13))));
+    if (!ok) ncut = 0;
+    sm.ncut[lane] = ncut;
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) sm.Hc[d][lane] = (d < s.n_det && ncut > 0) ? s.H[(int64_t)d * s.M + ncut - 1] : 0.0;
   }
   __syncthreads();
   // the work counters (cleared by the preceding kernel) are touched from here on
@@ -338,14 +351,12 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
       FF hh = ff(0.0f);
       if (ok) {
         const FF amp = sm.amp[lane];
-        FF sa, ca;
-        sincos(ff_from(th[10]) + 0.25 * kPi - (2.0 * kPi) * frac_near(sm.ccyc[lane]), &sa, &ca);
         for (int d = 0; d < s.n_det; ++d) {
           const FF Pr = sm.P[2 * d][lane], Pi = sm.P[2 * d + 1][lane];
           const FF kr = amp * (Pr * ca - Pi * sa), ki = amp * (Pr * sa + Pi * ca);
           cm.Kr[d] = ff_to_double(kr);
           cm.Ki[d] = ff_to_double(ki);
-          if (ncut > 0) hh = hh + (kr * kr + ki * ki) * ff_from(s.H[(int64_t)d * s.M + ncut - 1]);
+          hh = hh + (kr * kr + ki * ki) * ff_from(sm.Hc[d][lane]);
         }
       }
       cm.hh = ff_to_double(hh);
