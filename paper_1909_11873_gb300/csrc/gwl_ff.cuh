@@ -9,12 +9,14 @@
 // instruction, and the elementary functions below are written from their
 // series:
 //   exp x   = 2^k e^r, k = rint(x / ln 2), |r| <= ln 2 / 2, e^r by its Taylor
-//             series to r^13 / 13! (truncation < 4e-18);
+//             series to r^13 / 13! (truncation < 4e-18), the orders from r^8 on
+//             (below 6e-9) summed in FP32 and the rest in float pairs;
 //   ln x    = y0 + ln(1 + t), y0 = the FP32 logarithm of the high part,
 //             1 + t = x e^{-y0} (|t| ~ 1e-7), ln(1 + t) = t - t^2/2 (+ O(t^3));
 //   sin/cos = reduction x = k pi/2 + r with |r| <= pi/4, the Taylor series of
 //             sin r to r^15 / 15! and cos r to r^16 / 16! (truncation < 5e-17),
-//             the quadrant k mod 4 selecting and signing them.
+//             the orders from r^11 (sin) and r^12 (cos) on in FP32, the
+//             quadrant k mod 4 selecting and signing them.
 // The series coefficients are the reciprocal factorials.  The reductions
 // subtract k c with c = ln 2 or pi/2 split into three floats (Cody & Waite
 // 1980): c1 with 12 significant bits (k c1 exact for |k| < 2^12), c2 and c3
@@ -107,8 +109,7 @@ __device__ __forceinline__ FF frac_near(const FF& a) {
   return FF{s, e};
 }
 
-// Series coefficients as float pairs (constant memory; indexed with
-// compile-time indices they become instruction operands):
+// Series coefficients as float pairs (constant memory):
 //   exp:  1/n!                    n = 0..13
 //   sin:  (-1)^n / (2n+1)!        n = 0..7   (sin r = r sum_n c_n r^{2n})
 //   cos:  (-1)^n / (2n)!          n = 0..8
@@ -134,13 +135,21 @@ __device__ __forceinline__ FF ff_reduce(const FF& x, float k, float c1, float c2
 
 // The elementary functions are out of line: each is a few hundred
 // instructions, called from several places, and one copy of each keeps the
-// prologue's code within the instruction cache.
+// prologues' code within the instruction cache.  In each series only the
+// orders whose FP32 rounding would show at the float-pair level are summed
+// as float pairs: the high orders of a Taylor series are small enough for
+// plain FP32, which takes about a fifth of the instructions.
 static __device__ __noinline__ FF ff_exp(const FF& x) {
   const float k = nearest_int(__fmul_rn(x.hi, 1.44269504088896341f));
   const FF r = ff_reduce(x, k, 0x1.62e000p-1f, 0x1.0bfbe8p-15f, 0x1.cf79acp-40f);  // ln 2
-  FF p = kExpCoef[13];
+  // orders 8..13 in FP32 (r^8 / 8! < 6e-9, so their rounding stays below 1e-15 relative)
+  const float rh = r.hi;
+  float q = kExpCoef[13].hi;
+#pragma unroll
+  for (int n = 12; n >= 8; --n) q = __fmaf_rn(q, rh, kExpCoef[n].hi);
+  FF p = ff(q);
 #pragma unroll 1
-  for (int n = 12; n >= 0; --n) p = p * r + kExpCoef[n];
+  for (int n = 7; n >= 0; --n) p = p * r + kExpCoef[n];
   const float s = __int_as_float((127 + (int)k) << 23);  // 2^k (|k| < 127 for these inputs)
   return FF{__fmul_rn(p.hi, s), __fmul_rn(p.lo, s)};
 }
@@ -155,10 +164,18 @@ static __device__ __noinline__ void ff_sincos(const FF& x, FF* sn, FF* cs) {
   const float k = nearest_int(__fmul_rn(x.hi, 0.636619772367581343f));
   const FF r = ff_reduce(x, k, 0x1.920000p+0f, 0x1.fb5444p-12f, 0x1.68c234p-39f);  // pi / 2
   const FF r2 = r * r;
-  FF ps = kSinCoef[7], pc = kCosCoef[8];
+  // sin: orders r^11.. and cos: orders r^12.. in FP32 (below 2e-9 and 2e-10), the rest as float pairs
+  const float h = r2.hi;
+  float qs = kSinCoef[7].hi, qc = kCosCoef[8].hi;
+  qs = __fmaf_rn(qs, h, kSinCoef[6].hi);
+  qs = __fmaf_rn(qs, h, kSinCoef[5].hi);
+  qc = __fmaf_rn(qc, h, kCosCoef[7].hi);
+  qc = __fmaf_rn(qc, h, kCosCoef[6].hi);
+  FF ps = ff(qs), pc = ff(qc);
+  pc = pc * r2 + kCosCoef[5];
 #pragma unroll 1
-  for (int n = 7; n >= 0; --n) {  // the two series interleaved
-    if (n < 7) ps = ps * r2 + kSinCoef[n];
+  for (int n = 4; n >= 0; --n) {  // the two series interleaved
+    ps = ps * r2 + kSinCoef[n];
     pc = pc * r2 + kCosCoef[n];
   }
   const FF s = r * ps, c = pc;
