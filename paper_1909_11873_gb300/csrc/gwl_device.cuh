@@ -216,6 +216,25 @@ __device__ __forceinline__ bool physical(const double th[11]) {
   return ok;
 }
 
+// Pull the lines of H_d[j-1 .. j+1] (all detectors) into L2, j an FP32
+// estimate of the last bin at or below the cut frequency 1 / (6^{3/2} pi M
+// T_sun): the exact count that is read later differs from it by at most a bin.
+__device__ __forceinline__ void prefetch_cut_H(const SegInfo& s, double mc, double q) {
+  int64_t j = s.M - 1;
+  if (s.fcut_mode == 0) {
+    const float qf = (float)q, opq = 1.0f + qf;
+    const float M = (float)mc * __powf(qf / (opq * opq), -0.6f);
+    const float fc = 1.0f / ((float)(kSix32 * kPi * kTsun) * M);
+    const float x = fminf(fmaxf(floorf((fc - (float)s.f0) * (float)s.inv_df), 0.0f), (float)(s.M - 1));
+    j = (int64_t)x;
+  }
+  const int64_t a = j > 0 ? j - 1 : 0, b = j + 1 < s.M ? j + 1 : s.M - 1;
+  for (int d = 0; d < s.n_det; ++d) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(s.H + d * s.M + a));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(s.H + d * s.M + b));
+  }
+}
+
 // Number of bins with freqs[j] <= fc (bins ascend).  The stored frequencies
 // lie within 1e-9 df of f0 + j df (checked when the context is made), so when
 // x = (fc - f0) / df is more than 1e-7 from an integer the count follows from

@@ -274,6 +274,7 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
       }
     }
   } else {
+    if (valid) prefetch_cut_H(s, th[0], th[1]);  // read on warp 3 in phase 2
     FF sp, cp;
     sincos(ff_from(th[6]), &sp, &cp);
     sm.ori[0][lane] = sp;
