@@ -59,7 +59,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one bin-loop launch on this workload, from the
 # ncu capture summarised in profiles/k_window_mixed_c2.md; None whenever the
 # kernel has changed since that capture.
-KWINDOW_DRAM_BYTES = 1582080 + 0
+KWINDOW_DRAM_BYTES = 1589504 + 0
 
 
 def parse():
@@ -456,7 +456,7 @@ def run_gwl(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": KWINDOW_DRAM_BYTES,
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_window<3,mixed> "
-                                      "launch (640-bin windows, 2 CTAs/SM; profiles/k_window_mixed_c2.md)",
+                                      "launch (704-bin windows, 2 CTAs/SM; profiles/k_window_mixed_c2.md)",
                      "kernel": "k_window<3,mixed> (windowed bin loop and lnL combination)",
                      "peak_basis": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 flop x {fclk / 1e6:.0f} MHz (derived)",
                      "flops_per_pair": FLOPS_PER_BIN_MIXED, "pairs_per_launch": int(pairs),
