@@ -119,6 +119,32 @@ def test_edge_rows(precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_cut_next_to_bin_frequencies(precision):
+    """ISCO cut frequencies 1e-8 and 1e-6 bin widths either side of bin frequencies (q = 1, so
+    M = 1 / (6^{3/2} pi T_sun f_cut)): the device's bin count, taken from the grid where the cut is
+    more than 1e-7 bins from a bin and settled against the stored frequencies otherwise, must match
+    the oracle's per-bin comparison -- one bin more or less moves lnL by that bin's term."""
+    ev = event("c2")
+    tsun = 4.925490947e-6
+    rows, offs = [], (-1e-6, -1e-8, 1e-8, 1e-6)
+    for j in (180, 333, 512, 601):
+        for d in offs:
+            fc = ev.freqs[j] + d * (ev.freqs[1] - ev.freqs[0])
+            m = 1.0 / (6.0 ** 1.5 * np.pi * tsun * fc)
+            r = ev.theta_inj.copy()
+            r[1] = 1.0
+            r[0] = m * 0.25 ** 0.6
+            rows.append(r)
+    rows = np.array(rows)
+    ref = oracle.loglike(ev, rows)
+    got = run_gpu(ev, rows, precision)
+    assert np.all(np.abs(got - ref) <= tol(precision, ref)), report(got, ref, precision)
+    # the offsets straddle a bin: the oracle's lnL steps there by much more than the bar
+    step = np.abs(ref.reshape(4, 4)[:, 2] - ref.reshape(4, 4)[:, 1])
+    assert np.all(step > 100 * tol(precision, ref.reshape(4, 4)[:, 1])), step
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_deterministic_and_host_entry(precision):
     ev = event("c2")
     th = I.proposals(ev, 3000, 9)
