@@ -332,6 +332,33 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
 }
 
 // ---------------------------------------------------------------- combination
+// One detector's kAccPerDet window sums, read as 16-byte vectors (the sums of
+// a detector start on a 16-byte boundary: 20 floats or doubles per detector).
+template <class G>
+__device__ __forceinline__ void load_sums(const G* __restrict__ qw, G (&v)[kAccPerDet]) {
+  if constexpr (sizeof(G) == 4) {
+    static_assert(kAccPerDet % 4 == 0, "float sums in float4 units");
+    const float4* src = reinterpret_cast<const float4*>(qw);
+#pragma unroll
+    for (int k = 0; k < kAccPerDet / 4; ++k) {
+      const float4 x = src[k];
+      v[4 * k] = x.x;
+      v[4 * k + 1] = x.y;
+      v[4 * k + 2] = x.z;
+      v[4 * k + 3] = x.w;
+    }
+  } else {
+    static_assert(kAccPerDet % 2 == 0, "double sums in double2 units");
+    const double2* src = reinterpret_cast<const double2*>(qw);
+#pragma unroll
+    for (int k = 0; k < kAccPerDet / 2; ++k) {
+      const double2 x = src[k];
+      v[2 * k] = x.x;
+      v[2 * k + 1] = x.y;
+    }
+  }
+}
+
 template <int NDET, bool MIXED>
 __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
                                 const PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
@@ -345,13 +372,19 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
   const int64_t p = t / n_dim;
   const int i = (int)(t % n_dim);
   if (p >= B) return;
+  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
+  // window 0's sums are read beside the proposal's record rather than after
+  // it (every proposal with an in-band bin has a window 0; for the others
+  // they are read but not used)
+  G A[NDET][kAccPerDet];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) load_sums(q + d * kAccPerDet, A[d]);
   const PropCommon c = pc[p];
   if (c.flag) {
     if (i == 0) lnl[p] = -INFINITY;
     grad[p * n_dim + i] = 0.0;
     return;
   }
-  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
   const int nwp = (c.ncut + CH - 1) / CH;
   double Z[NDET][2];
   G W[NDET][2 * kNW];
@@ -359,18 +392,22 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
   // the gradient in G precision and are summed in it
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    double z0 = 0.0, z1 = 0.0;
+    const bool any = nwp > 0;
+    Z[d][0] = any ? (double)A[d][0] : 0.0;
+    Z[d][1] = any ? (double)A[d][1] : 0.0;
 #pragma unroll
-    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)0;
-    for (int w = 0; w < nwp; ++w) {
-      const G* qw = q + w * (kAccPerDet * NDET) + d * kAccPerDet;
-      z0 += (double)qw[0];
-      z1 += (double)qw[1];
+    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = any ? A[d][2 + k] : (G)0;
+  }
+  for (int w = 1; w < nwp; ++w) {
 #pragma unroll
-      for (int k = 0; k < 2 * kNW; ++k) W[d][k] += qw[2 + k];
+    for (int d = 0; d < NDET; ++d) {
+      G v[kAccPerDet];
+      load_sums(q + w * (kAccPerDet * NDET) + d * kAccPerDet, v);
+      Z[d][0] += (double)v[0];
+      Z[d][1] += (double)v[1];
+#pragma unroll
+      for (int k = 0; k < 2 * kNW; ++k) W[d][k] += v[2 + k];
     }
-    Z[d][0] = z0;
-    Z[d][1] = z1;
   }
   if (i == 0) {
     double l = -0.5 * c.hh;
