@@ -180,7 +180,39 @@ struct GradArgs {
   int* work;
   const int* hist;    // [w] proposals whose last window is w
   int* status;
+  // a proposal whose cut falls in its first window is finished in the bin loop
+  const void* pg;     // PropGrad<G>[B]
+  double* lnl;        // [B]
+  double* grad;       // [B][n_dim]
+  int n_dim;
 };
+
+// lnL = sum_d [Re K_d Z_d] - <h|h>/2 and d lnL / d theta_i from the window
+// sums: Z(d, 0..1) the data-template sums (U, V), W(d, k) the basis-weighted
+// ones (re, im of B_0..B_7 and f).
+template <int NDET, class ZF>
+__device__ __forceinline__ double grad_lnl(const PropCommon* c, ZF Z) {
+  double l = -0.5 * c->hh;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) l += c->Kr[d] * Z(d, 0) - c->Ki[d] * Z(d, 1);
+  return l;
+}
+template <int NDET, class G, class ZF, class WF>
+__device__ __forceinline__ G grad_dir(const PropCommon* c, const PropGrad<G>& g, int i, ZF Z, WF W) {
+  const G twopi = (G)(2.0 * kPi);
+  G acc = (G)(-0.5) * g.dhh[i];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) {
+    G Sr = g.dtau[d][i] * W(d, 2 * kNBasis), Si = g.dtau[d][i] * W(d, 2 * kNBasis + 1);
+#pragma unroll
+    for (int m = 0; m < kNBasis; ++m) {
+      Sr += g.dc[m][i] * W(d, 2 * m);
+      Si += g.dc[m][i] * W(d, 2 * m + 1);
+    }
+    acc += g.dKr[d][i] * (G)Z(d, 0) - g.dKi[d][i] * (G)Z(d, 1) + twopi * ((G)c->Kr[d] * Si + (G)c->Ki[d] * Sr);
+  }
+  return acc;
+}
 
 template <int NDET, bool MIXED>
 __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restrict__ smv, int64_t p, int j0,
@@ -317,6 +349,17 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
         Elem A[NDET][kAccPerDet];
         grad_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, A);
+        if (ncut <= a.CH) {  // the proposal's only window (every lane holds the sums): finish it here
+          const PropCommon* c = a.pc + p;
+          auto Z = [&](int d, int k) { return (double)A[d][k]; };
+          if (lane == 0) a.lnl[p] = grad_lnl<NDET>(c, Z);
+          if (lane < a.n_dim) {
+            const PropGrad<Elem>& g = reinterpret_cast<const PropGrad<Elem>*>(a.pg)[p];
+            a.grad[p * a.n_dim + lane] =
+                (double)grad_dir<NDET>(c, g, lane, Z, [&](int d, int k) { return A[d][2 + k]; });
+          }
+          return;
+        }
         // lanes write the per-window sums cooperatively
         Elem* o = reinterpret_cast<Elem*>(a.partials) + (p * a.nw_total + w) * (kAccPerDet * NDET);
 #pragma unroll
@@ -386,6 +429,7 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
     return;
   }
   const int nwp = (c.ncut + CH - 1) / CH;
+  if (nwp == 1) return;  // finished in the bin loop
   double Z[NDET][2];
   G W[NDET][2 * kNW];
   // Z (enters lnL) is summed over windows in FP64; the basis-weighted W enter
@@ -409,28 +453,9 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
       for (int k = 0; k < 2 * kNW; ++k) W[d][k] += v[2 + k];
     }
   }
-  if (i == 0) {
-    double l = -0.5 * c.hh;
-#pragma unroll
-    for (int d = 0; d < NDET; ++d) l += c.Kr[d] * Z[d][0] - c.Ki[d] * Z[d][1];
-    lnl[p] = l;
-  }
-  const PropGrad<G>& g = pg[p];
-  const G twopi = (G)(2.0 * kPi);
-  {
-    G acc = (G)(-0.5) * g.dhh[i];
-#pragma unroll
-    for (int d = 0; d < NDET; ++d) {
-      G Sr = g.dtau[d][i] * W[d][2 * kNBasis], Si = g.dtau[d][i] * W[d][2 * kNBasis + 1];
-#pragma unroll
-      for (int m = 0; m < kNBasis; ++m) {
-        Sr += g.dc[m][i] * W[d][2 * m];
-        Si += g.dc[m][i] * W[d][2 * m + 1];
-      }
-      acc += g.dKr[d][i] * (G)Z[d][0] - g.dKi[d][i] * (G)Z[d][1] + twopi * ((G)c.Kr[d] * Si + (G)c.Ki[d] * Sr);
-    }
-    grad[p * n_dim + i] = (double)acc;
-  }
+  auto Zf = [&](int d, int k) { return Z[d][k]; };
+  if (i == 0) lnl[p] = grad_lnl<NDET>(&c, Zf);
+  grad[p * n_dim + i] = (double)grad_dir<NDET>(&c, pg[p], i, Zf, [&](int d, int k) { return W[d][k]; });
 }
 
 // ---------------------------------------------------------------- launchers
@@ -481,6 +506,10 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   a.work = c->d_work;
   a.hist = window_hist(c);
   a.status = c->d_status;
+  a.pg = c->d_pgrad;
+  a.lnl = lnl;
+  a.grad = grad;
+  a.n_dim = c->opt.n_dim;
   const size_t smem = (size_t)CH * a.row_elems * sizeof(G);
   static size_t smem_set = 0;
   if (smem > smem_set) {
