@@ -242,8 +242,10 @@ int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t see
  * (about 48 significant bits on the FP32 pipe) on n arguments, for checking
  * their accuracy against FP64 references.  (An interface addition without a
  * counterpart in the paper.)
- *   x_dev   dev [n] FP64 arguments (split into float pairs first);
- *           GWL_FF_LOG needs x > 0; arguments of moderate size (|x| < 2^20)
+ *   x_dev   dev [n] FP64 arguments (split into float pairs first); the
+ *           domains of the functions: exp |x| < 87 (a normal float result),
+ *           ln 2^-126 < x < 2^127, sin and cos |x| < 2^11 (the reduction by
+ *           pi/2 is exact there); outside them the results are unspecified
  *   fn      GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN or GWL_FF_COS
  *   out_dev dev [n] FP64 results (the float pair summed in FP64)
  * Enqueues one kernel on the stream and returns. */
