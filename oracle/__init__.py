@@ -9,11 +9,11 @@ static parallel nested sampler (Section 3, Algorithm 1).
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never loads it.
 
-Parity status: the TaylorF2 higher-order PN and spin-orbit phase coefficients
-are "parity unpinned" against any external waveform code (the paper has no
-waveform; no waveform library is available); everything else is pinned by
-closed forms, invariants, brute force or library routines in
-``tests/test_oracle_pins.py``.
+Parity status: the TaylorF2 2.5-3.5PN spin-orbit phase coefficients are
+"parity unpinned" against any external waveform code (no waveform library is
+available); the non-spinning phase through 3.5PN is pinned by its published
+coefficients, and everything else by closed forms, invariants, brute force or
+library routines in ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
 

@@ -27,10 +27,11 @@
 //
 // Parity status of the waveform: the Newtonian amplitude and phase, the
 // antenna patterns, the inner product and the time/phase structure are pinned
-// by closed forms and invariants in the tests.  The higher-order PN and
-// spin-orbit coefficients are "parity unpinned" against any external
-// waveform code: the paper does not contain TaylorF2 and no waveform library
-// is available; they are pinned only by limits (chi -> 0, q = 1 symmetry).
+// by closed forms and invariants in the tests; the non-spinning phase through
+// 3.5PN and the 1.5PN spin-orbit and 2PN spin-spin terms by their published
+// coefficients.  The 2.5-3.5PN spin-orbit coefficients are "parity unpinned"
+// against any external waveform code (no waveform library is available);
+// they are pinned only by limits (chi -> 0, q = 1 symmetry).
 //
 // Sums run in bin order with Neumaier compensation.  Built with -O3 and
 // without -ffast-math.

@@ -177,6 +177,40 @@ def test_newtonian_and_1pn_phase_coefficients_textbook():
         assert phi3 == pytest.approx(-16 * math.pi, rel=2e-3)
 
 
+@pytest.mark.parametrize("q", [1.0, 0.8, 0.35])
+def test_nonspinning_phase_series_to_3_5pn_published_coefficients(q):
+    """Non-spinning TaylorF2 phase through 3.5PN (App. A) against the published coefficients
+    (Arun, Iyer, Sathyaprakash & Sundararajan 2005; Buonanno, Iyer, Ochsner, Pan & Sathyaprakash
+    2009): Psi * 128 eta v^5 / 3 - 1 is exactly a combination of v^2 .. v^7, v^5 ln v and v^6 ln v,
+    so a least-squares fit over v in [0.05, 0.4] recovers each coefficient -- phi2, phi3 = -16 pi,
+    phi4, the 2.5PN term phi5 (1 + 3 ln(v / v_lso)) with v_lso = 6^{-1/2}, the 3PN term with
+    -6848/21 ln(4 v), and phi7 -- and every eta polynomial is checked at three mass ratios."""
+    mc = 1.2
+    eta = q / (1 + q) ** 2
+    M = mc * eta ** -0.6 * TSUN
+    v = np.linspace(0.05, 0.4, 40)
+    f = v ** 3 / (math.pi * M)
+    g = np.array([oracle.pn_psi(mc, q, 0.0, 0.0, fi) for fi in f]) * 128 * eta * v ** 5 / 3 - 1.0
+    A = np.stack([v ** 2, v ** 3, v ** 4, v ** 5, v ** 5 * np.log(v), v ** 6, v ** 6 * np.log(v), v ** 7], axis=1)
+    scale = np.abs(A).max(axis=0)
+    coef = np.linalg.lstsq(A / scale, g, rcond=None)[0] / scale
+    euler_gamma = 0.5772156649015329
+    phi5 = math.pi * (38645 / 756 - 65 * eta / 9)
+    published = [
+        3715 / 756 + 55 * eta / 9,
+        -16 * math.pi,
+        15293365 / 508032 + 27145 * eta / 504 + 3085 * eta ** 2 / 72,
+        phi5 * (1 + 1.5 * math.log(6)),
+        3 * phi5,
+        11583231236531 / 4694215680 - 640 * math.pi ** 2 / 3 - 6848 * euler_gamma / 21
+        - 6848 / 21 * math.log(4) + (-15737765635 / 3048192 + 2255 * math.pi ** 2 / 12) * eta
+        + 76055 * eta ** 2 / 1728 - 127825 * eta ** 3 / 1296,
+        -6848 / 21,
+        math.pi * (77096675 / 254016 + 378515 * eta / 1512 - 74045 * eta ** 2 / 756),
+    ]
+    assert coef == pytest.approx(published, rel=1e-8)
+
+
 def test_spin_orbit_and_spin_spin_terms_textbook_form():
     """1.5PN spin-orbit written as (113/3 - 76 eta/3) chi_s + (113/3) delta chi_a and 2PN aligned
     spin-spin as -10 eta (721/48 - 247/48) chi1 chi2: extracted from the oracle's series."""
