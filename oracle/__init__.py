@@ -61,6 +61,7 @@ def _L():
             _lib.oracle_grad.argtypes = [P, i64, P, P, P, i32, d, d, i32, P, i64, P, P, i32]
             _lib.oracle_loglike_cal.argtypes = [P, i64, P, P, P, i32, d, d, i32, i32, P, P, i64, P, i32]
             _lib.oracle_cal_spline.argtypes = [i32, P, P, i64, P, P]
+            _lib.oracle_grad_cal.argtypes = [P, i64, P, P, P, i32, d, d, i32, i32, P, P, i64, P, P, i32]
             _lib.oracle_inv_normal_cdf.argtypes = [i64, P, P]
             _lib.oracle_ns_replace_cal.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
                                                    + [i32, P, P]
@@ -175,6 +176,22 @@ def loglike_cal(ev, node_freqs, theta, n_threads: int | None = None) -> np.ndarr
     if rc:
         raise ValueError("calibration needs at least two nodes")
     return out
+
+
+def grad_cal(ev, node_freqs, theta, n_threads: int | None = None):
+    """(lnL [B], d lnL / d theta [B, D]) with the calibration model, D = 11 + 2 n_nodes n_det:
+    the derivatives with respect to the source parameters and to every node's amplitude and
+    phase correction, by forward-mode dual numbers (the layout of loglike_cal)."""
+    nf = _f64(node_freqs)
+    n_det = np.asarray(ev.geom).shape[0]
+    th = _f64(theta).reshape(-1, N_PARAM + 2 * nf.size * n_det)
+    out = np.zeros(th.shape[0])
+    g = np.zeros_like(th)
+    keep, a = _ev_args(ev)
+    rc = _L().oracle_grad_cal(*a, nf.size, _p(nf), _p(th), th.shape[0], _p(out), _p(g), n_threads or default_threads())
+    if rc:
+        raise ValueError("calibration needs at least two nodes")
+    return out, g
 
 
 def cal_spline(x, y, xq) -> np.ndarray:

@@ -325,11 +325,13 @@ T loglike_one(const Event& ev, const T* th) {
 //     = 6 [ (y_{k+1} - y_k) / h_k - (y_k - y_{k-1}) / h_{k-1} ],  h_k = x_{k+1} - x_k,
 // with m_0 = m_{n-1} = 0.  The tridiagonal system is strictly diagonally
 // dominant and is solved by forward elimination and back substitution.
-void natural_spline(int n, const double* x, const double* y, double* m) {
-  for (int k = 0; k < n; ++k) m[k] = 0.0;
+template <class T>
+void natural_spline(int n, const double* x, const T* y, T* m) {
+  for (int k = 0; k < n; ++k) m[k] = T(0.0);
   if (n < 3) return;
   const int ni = n - 2;  // unknowns m_1 .. m_{n-2}
-  std::vector<double> sub(ni), dia(ni), sup(ni), rhs(ni);
+  std::vector<double> sub(ni), dia(ni), sup(ni);
+  std::vector<T> rhs(ni);
   for (int i = 0; i < ni; ++i) {
     const int k = i + 1;
     const double hl = x[k] - x[k - 1], hr = x[k + 1] - x[k];
@@ -341,7 +343,7 @@ void natural_spline(int n, const double* x, const double* y, double* m) {
   for (int i = 1; i < ni; ++i) {
     const double w = sub[i] / dia[i - 1];
     dia[i] -= w * sup[i - 1];
-    rhs[i] -= w * rhs[i - 1];
+    rhs[i] = rhs[i] - w * rhs[i - 1];
   }
   m[ni] = rhs[ni - 1] / dia[ni - 1];
   for (int i = ni - 2; i >= 0; --i) m[i + 1] = (rhs[i] - sup[i] * m[i + 2]) / dia[i];
@@ -351,7 +353,8 @@ void natural_spline(int n, const double* x, const double* y, double* m) {
 // xq (the first or last piece outside the node range), in the standard form
 // with A = (x_{k+1} - xq)/h, B = (xq - x_k)/h:
 //   S = A y_k + B y_{k+1} + [(A^3 - A) m_k + (B^3 - B) m_{k+1}] h^2 / 6.
-double spline_eval(int n, const double* x, const double* y, const double* m, double xq) {
+template <class T>
+T spline_eval(int n, const double* x, const T* y, const T* m, double xq) {
   int k = 0;
   while (k < n - 2 && xq >= x[k + 1]) ++k;
   const double h = x[k + 1] - x[k];
@@ -359,40 +362,50 @@ double spline_eval(int n, const double* x, const double* y, const double* m, dou
   return A * y[k] + B * y[k + 1] + ((A * A * A - A) * m[k] + (B * B * B - B) * m[k + 1]) * (h * h / 6.0);
 }
 
-// lnL of one source parameter vector with the calibration factor applied per
-// bin: lnL = sum_d sum_j 4 df / S_d,j [ Re(conj(d_j) C_j h_j) - |C_j h_j|^2 / 2 ].
-double loglike_cal_one(const Event& ev, const double* th, int nn, const double* xn) {
-  if (!physical(th)) return -std::numeric_limits<double>::infinity();
+// lnL of one parameter vector (11 source parameters, then the calibration
+// node values) with the calibration factor applied per bin:
+// lnL = sum_d sum_j 4 df / S_d,j [ Re(conj(d_j) C_j h_j) - |C_j h_j|^2 / 2 ].
+// Templated like loglike_one: T = double for lnL, dual numbers for its
+// gradient (the spline is linear in the node values, the factor C is not).
+template <class T>
+T loglike_cal_T(const Event& ev, const T* th, int nn, const double* xn) {
+  using std::cos;
+  using std::sin;
+  if (!physical(th)) return T(-std::numeric_limits<double>::infinity());
   const double df = event_df(ev);
-  PNPhase<double> P = pn_phase(th[P_MC], th[P_Q], th[P_CHI1], th[P_CHI2]);
+  PNPhase<T> P = pn_phase(th[P_MC], th[P_Q], th[P_CHI1], th[P_CHI2]);
   const double fc = f_cut(ev, P);
-  const double amp = amplitude(th);
-  std::vector<double> ma(nn), mp(nn);
-  NeumaierSum<double> acc;
+  const T amp = amplitude(th);
+  std::vector<T> ma(nn), mp(nn);
+  NeumaierSum<T> acc;
   for (int d = 0; d < ev.n_det; ++d) {
-    const double* ya = th + P_N + 2 * nn * d;
-    const double* yp = ya + nn;
+    const T* ya = th + P_N + 2 * nn * d;
+    const T* yp = ya + nn;
     natural_spline(nn, xn, ya, ma.data());
     natural_spline(nn, xn, yp, mp.data());
-    double Fp, Fx, dt;
+    T Fp, Fx, dt;
     antenna(ev.geom + 9 * d, th[P_PSI], th[P_RA], th[P_DEC], ev.gmst, &Fp, &Fx, &dt);
     const double* dd = ev.strain + 2 * ev.M * d;
     const double* S = ev.psd + ev.M * d;
     for (int64_t j = 0; j < ev.M; ++j) {
       const double f = ev.freqs[j];
       if (f > fc) break;
-      double hr, hi;
+      T hr, hi;
       strain_bin(th, P, amp, Fp, Fx, dt, ev.t_ref, f, &hr, &hi);
       const double x = std::log(f);
-      const double dA = spline_eval(nn, xn, ya, ma.data(), x);
-      const double dphi = spline_eval(nn, xn, yp, mp.data(), x);
-      const double cr = (1.0 + dA) * std::cos(dphi), ci = (1.0 + dA) * std::sin(dphi);
-      const double gr = cr * hr - ci * hi, gi = cr * hi + ci * hr;  // C h
+      const T dA = spline_eval(nn, xn, ya, ma.data(), x);
+      const T dphi = spline_eval(nn, xn, yp, mp.data(), x);
+      const T cr = (1.0 + dA) * cos(dphi), ci = (1.0 + dA) * sin(dphi);
+      const T gr = cr * hr - ci * hi, gi = cr * hi + ci * hr;  // C h
       const double w = 4.0 * df / S[j];
       acc.add(w * ((dd[2 * j] * gr + dd[2 * j + 1] * gi) - 0.5 * (gr * gr + gi * gi)));
     }
   }
   return acc.result();
+}
+
+double loglike_cal_one(const Event& ev, const double* th, int nn, const double* xn) {
+  return loglike_cal_T<double>(ev, th, nn, xn);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,6 +647,35 @@ int oracle_grad(const double* freqs, int64_t M, const double* strain, const doub
     Dual<P_N> r = loglike_one<Dual<P_N>>(ev, th);
     lnl[b] = r.v;
     for (int k = 0; k < P_N; ++k) grad[P_N * b + k] = std::isfinite(r.v) ? r.d[k] : 0.0;
+  }
+  return 0;
+}
+
+// Batched lnL with the calibration model and its gradient with respect to all
+// D = 11 + 2 n_nodes n_det parameters (theta's layout) by forward-mode dual
+// numbers, sixteen directions per pass -> lnl[B], grad[B][D].
+int oracle_grad_cal(const double* freqs, int64_t M, const double* strain, const double* psd,
+                    const double* geom, int n_det, double gmst, double t_ref, int fcut_mode, int n_nodes,
+                    const double* node_f, const double* theta, int64_t B, double* lnl, double* grad,
+                    int n_threads) {
+  Event ev{freqs, M, strain, psd, geom, n_det, gmst, t_ref, fcut_mode};
+  if (n_nodes < 2) return -1;
+  std::vector<double> xn(n_nodes);
+  for (int k = 0; k < n_nodes; ++k) xn[k] = std::log(node_f[k]);
+  const int64_t D = P_N + 2 * (int64_t)n_nodes * n_det;
+  constexpr int NT = 16;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int64_t b = 0; b < B; ++b) {
+    std::vector<Dual<NT>> th(D);
+    for (int64_t c0 = 0; c0 < D; c0 += NT) {
+      for (int64_t k = 0; k < D; ++k) {
+        th[k] = Dual<NT>(theta[D * b + k]);
+        if (k >= c0 && k < c0 + NT) th[k].d[k - c0] = 1.0;
+      }
+      const Dual<NT> r = loglike_cal_T<Dual<NT>>(ev, th.data(), n_nodes, xn.data());
+      lnl[b] = r.v;
+      for (int64_t k = c0; k < D && k < c0 + NT; ++k) grad[D * b + k] = std::isfinite(r.v) ? r.d[k - c0] : 0.0;
+    }
   }
   return 0;
 }

@@ -560,6 +560,65 @@ def test_cal_loglike_brute_force_with_scipy_splines(c2):
         assert got == pytest.approx(ref, rel=1e-10, abs=1e-8)
 
 
+def test_cal_gradient_matches_central_differences(c2):
+    """Gradient of the calibrated lnL by dual numbers over all 11 + 60 parameters against central
+    differences of the calibrated lnL (h = 1e-6 relative for the source parameters, 1e-5 for the
+    node values; points where a mass step moves the ISCO bin are skipped)."""
+    nodes = I.cal_node_freqs(20.0, 1024.0)
+    th = I.calibrated_proposals(c2, 3, 12)
+    lnl, g = oracle.grad_cal(c2, nodes, th)
+    assert np.allclose(lnl, oracle.loglike_cal(c2, nodes, th), rtol=1e-13, atol=1e-10)
+    D = th.shape[1]
+
+    def ncut(t):
+        eta = t[1] / (1 + t[1]) ** 2
+        fi = 1 / (6 ** 1.5 * math.pi * t[0] * eta ** -0.6 * TSUN)
+        return np.searchsorted(c2.freqs, fi, side="right")
+
+    rows, idx, steps = [], [], []
+    for b in range(th.shape[0]):
+        for k in range(D):
+            hstep = 1e-6 * max(abs(th[b, k]), 1e-2) if k < 11 else 1e-5
+            tp, tm = th[b].copy(), th[b].copy()
+            tp[k] += hstep
+            tm[k] -= hstep
+            if k in (0, 1) and ncut(tp) != ncut(tm):
+                continue
+            rows += [tp, tm]
+            idx.append((b, k))
+            steps.append(hstep)
+    vals = oracle.loglike_cal(c2, nodes, np.array(rows)).reshape(-1, 2)
+    for (b, k), hstep, (lp, lm) in zip(idx, steps, vals):
+        fd = (lp - lm) / (2 * hstep)
+        assert abs(fd - g[b, k]) < 2e-4 * max(1.0, abs(g[b, k])), (b, k, fd, g[b, k])
+
+
+def test_cal_gradient_at_zero_corrections_closed_form(c2):
+    """With every correction zero, C = 1 and the node derivatives have closed forms in the cardinal
+    natural splines s_k (scipy, through the k-th unit vector, in ln f):
+      d lnL / d dA_d,k   = sum_j s_k(ln f_j) w_j [Re(conj(d_j) h_j) - |h_j|^2],
+      d lnL / d dphi_d,k = sum_j s_k(ln f_j) w_j Re(conj(d_j) i h_j),   w_j = 4 df / S_j,
+    with h the oracle's (pinned) waveform; the source derivatives are the uncalibrated gradient."""
+    from scipy.interpolate import CubicSpline
+    nodes = I.cal_node_freqs(20.0, 1024.0)
+    nn = nodes.size
+    x = np.log(c2.freqs)
+    s = np.stack([CubicSpline(np.log(nodes), np.eye(nn)[k], bc_type="natural")(x) for k in range(nn)])
+    w = 4.0 * c2.df / c2.psd
+    for t in I.proposals(c2, 2, 13):
+        zero = np.zeros((3, nn))
+        _, g = oracle.grad_cal(c2, nodes, _cal_theta(c2, t, zero, zero)[None])
+        _, g0 = oracle.grad(c2, t[None])
+        assert np.allclose(g[0, :11], g0[0], rtol=1e-10, atol=1e-9)
+        h = oracle.waveform(c2, t)
+        for d in range(3):
+            ta = w[d] * (np.real(np.conj(c2.strain[d]) * h[d]) - np.abs(h[d]) ** 2)
+            tp = w[d] * np.real(np.conj(c2.strain[d]) * 1j * h[d])
+            got = g[0, 11 + 2 * nn * d: 11 + 2 * nn * (d + 1)]
+            ref = np.concatenate([s @ ta, s @ tp])
+            assert np.allclose(got, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max()), (d, got, ref)
+
+
 def test_inverse_normal_cdf_is_scipy_ndtri():
     """The oracle's Phi^{-1} (calibration priors) equals scipy's ndtri from the far tails to the centre."""
     u = np.concatenate([np.geomspace(1e-300, 0.5, 400), 1.0 - np.geomspace(1e-16, 0.5, 400),
