@@ -179,7 +179,7 @@ def test_newtonian_and_1pn_phase_coefficients_textbook():
 
 @pytest.mark.parametrize("q", [1.0, 0.8, 0.35])
 def test_nonspinning_phase_series_to_3_5pn_published_coefficients(q):
-    """Non-spinning TaylorF2 phase through 3.5PN (App. A) against the published coefficients
+    """The oracle's non-spinning TaylorF2 phase through 3.5PN against the published coefficients
     (Arun, Iyer, Sathyaprakash & Sundararajan 2005; Buonanno, Iyer, Ochsner, Pan & Sathyaprakash
     2009): Psi * 128 eta v^5 / 3 - 1 is exactly a combination of v^2 .. v^7, v^5 ln v and v^6 ln v,
     so a least-squares fit over v in [0.05, 0.4] recovers each coefficient -- phi2, phi3 = -16 pi,
