@@ -96,11 +96,16 @@ __device__ __forceinline__ int start_window(const int* __restrict__ hist, int w_
   return s_res[0];
 }
 
-// Proposals per claim in a window with n_active active proposals of B.
+// Proposals per claim in a window with n_active active proposals of B: about
+// one active proposal per claim, or two (half the atomics on the window's
+// counter) when the window holds more than two active proposals per warp of
+// the grid, so that small batches keep every warp busy.
 __device__ __forceinline__ int claim_size(int64_t B, int n_active) {
   if (n_active <= 0) return 32;
-  const int64_t c = B / n_active;
-  return c < 1 ? 1 : (c > 32 ? 32 : (int)c);
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int per = n_active >= 2 * warps ? 2 : 1;
+  const int64_t c = per * B / n_active;
+  return c < per ? per : (c > 32 ? 32 : (int)c);
 }
 
 // Warp-level: drain the proposals of one window from its counter, `chunk` per
