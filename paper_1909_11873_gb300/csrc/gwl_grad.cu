@@ -10,9 +10,11 @@
 // basis-weighted sums W_d,m, W_d,f (one pass over the bins, same phase
 // arithmetic as the likelihood).  The per-proposal derivatives dc_m, dtau_d,
 // dK_d, d<h|h> come from the prologue evaluated on a forward-mode tangent type
-// whose value stays FP64 (the same numbers as the likelihood path) while the
-// tangents are carried in FP32 (GWL_MIXED) or FP64 (GWL_FP64).  The ISCO cut
-// index is held at its value: the gradient of the piecewise-smooth lnL.
+// whose value is FP64 (GWL_FP64) or a float pair (GWL_MIXED, the likelihood
+// prologue's arithmetic) while the tangents are carried in FP64 or FP32.  A
+// proposal whose cut falls in its first window is finished in the bin loop;
+// the combination kernel takes the others.  The ISCO cut index is held at its
+// value: the gradient of the piecewise-smooth lnL.
 #include <cmath>
 
 #include "gwl_bins.cuh"
@@ -417,8 +419,8 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
   if (p >= B) return;
   const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
   // window 0's sums are read beside the proposal's record rather than after
-  // it (every proposal with an in-band bin has a window 0; for the others
-  // they are read but not used)
+  // it (every proposal with an in-band bin has a window 0); rows without one,
+  // or finished in the bin loop, read them but do not use them
   G A[NDET][kAccPerDet];
 #pragma unroll
   for (int d = 0; d < NDET; ++d) load_sums(q + d * kAccPerDet, A[d]);
