@@ -7,31 +7,34 @@
 // template, regrouped so that per bin and detector only the phase, one
 // sincos and four multiply-adds remain.
 //
-// Work decomposition: a prologue kernel turns each parameter row into its
-// coefficients (two warps per 32 rows: one for the masses and spins, one for
-// the sky position and orientation).  The bins are cut into windows of W bins;
-// each CTA of the bin-loop kernel is assigned a window, stages the window's
-// table rows in shared memory with one bulk asynchronous copy (cp.async.bulk,
-// completion on an mbarrier, bounded wait), and its warps then take proposals
-// one at a time from the window's atomic counter, the 32 lanes striding over
-// the window's bins two bins per iteration.  Per-lane sums are reduced with
-// warp shuffles.  When the whole batch fits one window the warp forms lnL at
-// once; otherwise it writes one partial per (proposal, window) and a final
-// kernel adds them in window order (FP64).  The counters only schedule work:
-// no atomics touch the sums, so results are deterministic.  The three kernels
-// are chained with programmatic dependent launch.
+// Work decomposition: a clearing kernel zeroes the work counters; a prologue
+// kernel turns each parameter row into its coefficients (four warps per 32
+// rows); the bins are cut into windows of W bins, and each CTA of the
+// persistent bin-loop kernel starts in the window holding its share of the
+// work, stages the window's table rows in shared memory with one bulk
+// asynchronous copy (cp.async.bulk, completion on an mbarrier, bounded wait),
+// and its warps take proposals from the window's atomic counter in claims of
+// 1-32, the 32 lanes striding over the window's bins two blocks per iteration.
+// Per-lane sums are reduced with warp shuffles.  A proposal whose cut falls in
+// its only window is queued in the CTA's shared memory and combined there in
+// FP64 at the next window boundary; otherwise each window's warp publishes a
+// partial, and the warp that closes the proposal's last window adds them in
+// window order (FP64).  The counters only schedule work: no atomics touch the
+// sums, so results are deterministic.  The three kernels are chained with
+// programmatic dependent launch.
 //
 // Precision modes:
 //   GWL_FP64  -- phase as an FP64 FMA chain, FP64 sincospi, FP64 sums.
 //   GWL_MIXED -- phase in float-float arithmetic (about 48-bit significand,
-//                built from error-free TwoProduct/TwoSum on the FP32 pipe),
-//                exact reduction to [-1/2, 1/2] cycles, FP32 sincos, FP32
-//                per-lane sums over at most W/32 bins, FP32 warp tree, FP64
-//                across windows and for the combination; the prologue too
-//                runs in float-float arithmetic (gwl_ff.cuh).  On GB300 the
-//                FP64 pipe issues about 2 FMAs per SM per clock against about
-//                128 FP32 FMAs, so float-float is several times cheaper than
-//                FP64 at the same precision.
+//                built from error-free TwoProduct/TwoSum on the FP32 pipe) at
+//                an anchor bin every 32 bins, FP32 basis deltas within the
+//                block where its phase excursion is small, exact reduction of
+//                the anchor term, FP32 sincos, FP32 per-lane sums over at most
+//                W/32 bins, FP32 warp tree, FP64 across windows and for the
+//                combination; the prologue too runs in float-float arithmetic
+//                (gwl_ff.cuh).  On GB300 the FP64 pipe issues about 2 FMAs per
+//                SM per clock against about 128 FP32 FMAs, so float-float is
+//                several times cheaper than FP64 at the same precision.
 #include <cmath>
 #include <type_traits>
 
