@@ -9,7 +9,8 @@
 // the total work (CTA b of G at the weighted quantile b / G), drains it, and
 // sweeps on through the later windows, skipping those already drained.  Inside
 // a window warps claim proposals in chunks sized so that a claim holds about
-// one active proposal (B / n_w of them, 1 .. 32).
+// one active proposal (B / n_w of them, 1 .. 32), or two when the window holds
+// more than two active proposals per warp of the grid.
 #pragma once
 
 #include "gwl_device.cuh"
