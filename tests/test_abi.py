@@ -60,3 +60,28 @@ def test_argument_errors_are_synchronous(L):
     assert L.gwl_set_calibration(None, 10, f.ctypes.data, 0.1, 0.1) == -1
     assert L.gwl_get_calibration(None, None, None) == -1
     assert out.value is None
+
+
+def test_grid_tolerance_is_1e9_of_the_spacing(L):
+    """Frequencies are accepted within 1e-9 of the spacing of f0 + j df and refused beyond it: the
+    bin count at the ISCO cut is taken from the grid away from grid points on that bound.  After an
+    accepted grid a non-positive PSD stops the call, which shows which check refused it (no device
+    work happens before either check)."""
+    out = C.c_void_p()
+    f = np.arange(16, dtype=np.float64) + 20.0
+    s = np.zeros((1, 16, 2))
+    bad_psd = -np.ones((1, 16))
+    dets = gwl.detectors(np.zeros(9))
+    opt = gwl.GwlOptions()
+    opt.n_dim = 1
+    near = f.copy()
+    near[7] += 5e-10
+    assert L.gwl_create(near.ctypes.data, 16, s.ctypes.data, bad_psd.ctypes.data, dets, 1, C.byref(opt),
+                        C.byref(out)) == -1
+    assert b"psd" in L.gwl_last_error()
+    far = f.copy()
+    far[7] += 2e-9
+    assert L.gwl_create(far.ctypes.data, 16, s.ctypes.data, bad_psd.ctypes.data, dets, 1, C.byref(opt),
+                        C.byref(out)) == -1
+    assert b"uniformly" in L.gwl_last_error()
+    assert out.value is None
