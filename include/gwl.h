@@ -327,6 +327,16 @@ int gwl_set_walk(gwl_ctx* ctx, int walk_kind);
  * status (GWL_OK or GWL_ERR_TIMEOUT); clears the latch. */
 int gwl_sync(gwl_ctx* ctx);
 
+/* Diagnostic (an interface addition without a counterpart in the paper):
+ * exercises the timeout path of the kernels' bounded waits.  One thread
+ * waits on a shared-memory barrier phase that nothing completes, for about
+ * `seconds` of SM clock (0 < seconds <= 2), then latches the timeout status
+ * and leaves, as a kernel whose bulk copy never landed would; the next
+ * gwl_sync returns GWL_ERR_TIMEOUT and clears it, and the context stays
+ * usable.  Enqueues one kernel on the stream and returns; GWL_ERR_ARG for a
+ * null context or seconds outside (0, 2]. */
+int gwl_test_wait_timeout(gwl_ctx* ctx, double seconds, void* stream);
+
 /* Launch shape of the bin loops (the tile the hardware sees: a window of
  * `window` frequency bins staged in shared memory, drained by warps of 32
  * lanes, one proposal per warp; the grid is sized in CTAs per SM).  The

@@ -567,6 +567,37 @@ void gwl_multi_destroy(gwl_multi* h) {
   delete h;
 }
 
+}  // extern "C"
+
+namespace gwl {
+// One thread waits, bounded, on an mbarrier phase that nothing completes: the
+// wait runs out and latches the timeout status like a stalled copy would.
+__global__ void k_wait_unsignalled(int* __restrict__ status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_wait_bounded(&bar, 0, status, limit);
+  }
+}
+}  // namespace gwl
+
+extern "C" {
+
+int gwl_test_wait_timeout(gwl_ctx* c, double seconds, void* stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!(seconds > 0.0) || seconds > 2.0) return fail(GWL_ERR_ARG, "seconds=%g out of range (0, 2]", seconds);
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  const long long limit = (long long)(seconds * 2.07e9);  // SM clocks at the maximum clock
+  gwl::k_wait_unsignalled<<<1, 32, 0, st>>>(c->d_status, limit);
+  c->launches++;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gwl_test_wait_timeout");
+  return GWL_OK;
+}
+
 int gwl_sync(gwl_ctx* c) {
   int rc = check_ctx(c);
   if (rc) return rc;

@@ -180,12 +180,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for an mbarrier phase for at most ~1 s of SM clock; on timeout latch
-// kStatusTimeout and return false (the caller then leaves the kernel).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+// Wait for an mbarrier phase for at most `limit` SM clocks (default ~1 s);
+// on timeout latch kStatusTimeout and return false (the caller then leaves
+// the kernel).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status,
+                                                  long long limit = 2000000000LL) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > 2000000000LL) {
+    if (clock64() - t0 > limit) {
       atomicOr(status, kStatusTimeout);
       return false;
     }

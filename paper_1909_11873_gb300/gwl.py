@@ -27,7 +27,8 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
            "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
-           "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval")
+           "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
+           "gwl_test_wait_timeout")
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
@@ -98,6 +99,7 @@ def lib() -> C.CDLL:
         L.gwl_autotune.argtypes = [P, P, i64, i32, C.POINTER(GwlTuning), P]
         L.gwl_set_calibration.argtypes = [P, i32, P, d, d]
         L.gwl_ff_eval.argtypes = [P, i64, i32, P, P]
+        L.gwl_test_wait_timeout.argtypes = [P, C.c_double, P]
         L.gwl_get_calibration.argtypes = [P, C.POINTER(i32), C.POINTER(i64)]
         L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
@@ -258,6 +260,9 @@ class Context:
 
     def gwl_sync(self):
         _check(lib().gwl_sync(self._h), "gwl_sync")
+
+    def gwl_test_wait_timeout(self, seconds: float, stream=None):
+        _check(lib().gwl_test_wait_timeout(self._h, float(seconds), _stream(stream)), "gwl_test_wait_timeout")
 
     def gwl_set_walk(self, kind: int):
         _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
