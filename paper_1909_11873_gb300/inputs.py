@@ -29,13 +29,15 @@ IDX = {n: i for i, n in enumerate(PARAM_NAMES)}
 # prior kinds (unit-cube maps): 0 uniform, 1 uniform in volume, 2 sine on [0, pi], 3 cosine on [-pi/2, pi/2]
 UNIFORM, VOLUME, SINE, COSINE = 0, 1, 2, 3
 
-# Approximate Hanford-, Livingston- and Virgo-like sites: latitude, longitude
-# [deg] and x-arm bearing [deg from north, clockwise]; the y arm is the x arm
-# bearing minus 90 deg.  Arms are perpendicular and tangent to the sphere.
+# Approximate Hanford-, Livingston- and Virgo-like sites, and a KAGRA-like
+# fourth used only by four-detector events: latitude, longitude [deg] and
+# x-arm bearing [deg from north, clockwise]; the y arm is the x arm bearing
+# minus 90 deg.  Arms are perpendicular and tangent to the sphere.
 SITES = {
     "H": (46.455, -119.408, 324.0),
     "L": (30.563, -90.774, 252.3),
     "V": (43.631, 10.504, 19.4),
+    "K": (36.412, 137.306, 28.3),
 }
 
 
@@ -207,7 +209,7 @@ def make_event(name: str, seed: int, waveform: WaveformFn, snr2: Snr2Fn, cfg: di
         th[4] = math.sqrt(snr2(sk, th)) / snr_t
         sampling = sampling_c1(th)
     else:
-        sites = ("H", "L", "V")[:n_det]
+        sites = ("H", "L", "V", "K")[:n_det]
         geom = np.stack([site_geometry(*SITES[s]) for s in sites])
         src = BBH if cfg["source"] == "bbh" else BNS
         snr_t = float(rng.uniform(15.0, 30.0))
