@@ -1,6 +1,7 @@
-"""Four detectors, the library's maximum (GWL_MAX_DET): parity of the device likelihood (both
-precisions, one window and several, with and without the calibration model) and of the gradient
-with the FP64 oracle.  4 s of data, 20-512 Hz (1969 bins), 256 proposals."""
+"""Two and four detectors (four is the library's maximum, GWL_MAX_DET; three are covered by the
+configuration tests): parity of the device likelihood (both precisions, one window and several,
+with and without the calibration model) and of the gradient with the FP64 oracle.  4 s of data,
+20-512 Hz (1969 bins), 256 proposals."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ from paper_1909_11873_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-CFG = dict(n_det=4, T=4.0, f_low=20.0, f_high=512.0, noise=True, source="bbh", batch=256, gmst=0.7)
+CFG = dict(T=4.0, f_low=20.0, f_high=512.0, noise=True, source="bbh", batch=256, gmst=0.7)
 GTOL = {0: 1e-6, 1: 1e-3}
 
 
@@ -21,10 +22,10 @@ def built():
     build.build()
 
 
-@pytest.fixture(scope="module")
-def ev():
-    e = custom_event(CFG, 21)
-    assert e.geom.shape[0] == 4
+@pytest.fixture(scope="module", params=[2, 4], ids=["2det", "4det"])
+def ev(request):
+    e = custom_event(dict(CFG, n_det=request.param), 21)
+    assert e.geom.shape[0] == request.param
     return e
 
 
@@ -54,7 +55,7 @@ def test_four_detector_calibrated_loglike(ev, precision):
     from paper_1909_11873_gb300 import gwl
     th = I.proposals(ev, 256, 5)
     nodes = I.cal_node_freqs(20.0, 512.0)
-    cal = I.draw_calibration(np.random.default_rng(6), 256, 4)
+    cal = I.draw_calibration(np.random.default_rng(6), 256, ev.geom.shape[0])
     ref = oracle.loglike_cal(ev, nodes, np.concatenate([th, cal], axis=1))
     rows = np.ascontiguousarray(np.concatenate([I.reduced(th, ev.sampling), cal], axis=1))
     ctx = context(ev, precision)
