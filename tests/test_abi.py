@@ -59,6 +59,11 @@ def test_argument_errors_are_synchronous(L):
     assert L.gwl_get_tuning(None, None) == -1
     assert L.gwl_set_calibration(None, 10, f.ctypes.data, 0.1, 0.1) == -1
     assert L.gwl_get_calibration(None, None, None) == -1
+    assert L.gwl_test_wait_timeout(None, 0.05, None) == -1
+    assert L.gwl_ff_eval(None, 4, gwl.GWL_FF_EXP, None, None) == -1
+    assert L.gwl_ff_eval(f.ctypes.data, 4, 7, f.ctypes.data, None) == -1
+    assert L.gwl_ff_eval(f.ctypes.data, -1, gwl.GWL_FF_EXP, f.ctypes.data, None) == -1
+    assert L.gwl_ff_eval(None, 0, gwl.GWL_FF_EXP, None, None) == 0
     assert out.value is None
 
 
