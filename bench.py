@@ -5,22 +5,32 @@ Workload (one step): one gwl_loglike call over a batch of 8192 proposals for
 a 3-detector, 8 s, 20-1024 Hz network (8033 bins per detector, coloured
 Gaussian noise, 11-D aligned-spin BBH injection at SNR 15-30); half the
 proposals are prior draws and half perturb the injection.  Inputs are
-synthetic and seeded; the injection is produced by the device library's own
-template (gwl_waveform), so the GPU leg runs no oracle code.
+synthetic and seeded; the injections are produced by the device library's
+own template (gwl_waveform), so the GPU legs run no oracle code.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gwl|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gwl|reference] [--legs a,b,...]
 
 Prints one JSON line (rank 0).  ``value`` is the mixed-precision path's
 device-timed throughput with inputs resident in HBM; L2 (129 MB) is flushed
 by writing a 256 MB buffer between timed steps (the step inputs are < 1 MB).
-``e2e`` is the same metric through gwl_loglike_host (host buffers, copies in
-the timed region).  ``roofline`` refers to the dominant kernel (the windowed
-bin loop), timed by the library's CUDA events on the launch stream.
-``cpu_baseline`` times the FP64 oracle on the host cores on a bounded sample.
+``e2e`` is the same metric through gwl_loglike_host with page-locked host
+buffers, timed by the host clock around each call (the flush is issued and
+finished before the clock starts).  ``roofline`` refers to the dominant
+kernel (the windowed bin loop), timed by the library's CUDA events on the
+launch stream, with every pipe's algorithmic work reported and the largest
+fraction taken as the bound.  ``cpu_baseline`` times the FP64 oracle on the
+host cores on a bounded sample and runs the oracle comparisons of the other
+legs.  The other measurements come last in the line, compactly, under
+``legs``: the plain FP64 path, the FP64-phase mixed arm, the gradient, the
+calibrated likelihood, the 1-detector and 128 s workloads, the 64-event
+workload, the two walks' effective samples per second and a full nested
+sampling run.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
+import hashlib
 import json
 import math
 import os
@@ -41,25 +51,36 @@ METRIC = "lnL evals/s (BBH 3-det 8s, 11-D)"
 CONFIG = "c2"
 BATCH = 8192
 SEED = 2
-# Algorithmic work per in-band (proposal, bin) pair with 3 detectors (flops,
-# FMA = 2), counted from what the method must compute, not from the kernel's
-# instructions: the phase, 9 basis terms (9 FMA = 18 flop) and per detector
-# the delay term, nearest integer and subtraction (3 x 4 = 12 flop); the
-# inner-product accumulation, 4 FMA per detector (24 flop), and its
-# compensation (24 flop) -> 78 flop, plus 6 sine/cosine (MUFU, separate pipe).
-FLOPS_PER_BIN_MIXED = 78
-# The gradient adds per bin the combination of the three detectors' terms
-# (3 x 4 FMA) and the basis-weighted sums (10 FMA): 22 FMA = 44 flop -> 122.
-FLOPS_PER_BIN_GRAD = 122
-# Calibration model (Section 2.2), per bin and detector on top of the plain
-# likelihood: two spline values (4 FMA each, 16 flop), the phase shift (1),
-# the amplitude factor (1 + 2) and the <h|h> correction (4): 24 flop.
-FLOPS_PER_BIN_CAL = FLOPS_PER_BIN_MIXED + 3 * 24
+LEGS = ("fp64", "fp64ph", "grad", "cal", "c1", "c3", "c4", "c5", "ns")
+
+# Algorithmic work of the mixed likelihood bin loop per in-band (proposal, bin)
+# pair with 3 detectors, counted from the arithmetic the kernel carries out
+# for that pair (FMA = 2 flop; TwoProduct = 3, TwoSum = 6):
+#   FP32: the phase delta sum_m c_m dB_m over 8 basis terms (15), its nearest
+#     integer and subtraction (3); per detector the anchor-plus-lane term (1),
+#     the sum with the delta (1), the scaling to radians (1) and the four
+#     multiply-adds of U and V (8): 3 x 11 = 33; the block's float-float anchor
+#     term (about 180 flop per 32-bin block) -> 5: 56 flop.
+#   MUFU (special-function unit): sine and cosine per detector -> 6.
+#   FP64: the combination, about 40 flop per proposal (not per pair) -> 0.
+#   HBM: theta in (88 B) and lnL out (8 B) per proposal.
+PIPES_MIXED = {"fp32_flop": 56, "mufu": 6}
+HBM_BYTES_PER_EVAL = 96
+# The gradient bin loop per pair: the exact float-float phase per bin (the
+# 8-term sum, 112, and per detector the delay term, TwoSum and reduction,
+# 3 x 20) -> 172; per detector the data-weighted phasor (6), Z_d (2) and the
+# nine basis-weighted complex sums W_d,m (36) -> 3 x 44 = 132: 304 flop; 6 MUFU.
+PIPES_GRAD = {"fp32_flop": 304, "mufu": 6}
+# Calibration model (Section 2.2), per bin on top of the plain likelihood: the
+# four spline weights (9 flop, shared by the detectors); per detector two
+# spline values (2 x 7), the phase shift (1), the amplitude factor (3) and the
+# <h|h> correction (4): 9 + 3 x 22 = 75.
+PIPES_CAL = {"fp32_flop": 56 + 75, "mufu": 6}
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one bin-loop launch on this workload, from the
-# ncu capture summarised in profiles/k_window_mixed_c2.md; None whenever the
-# kernel has changed since that capture.
-KWINDOW_DRAM_BYTES = 1590272 + 0
+MUFU_PER_SM_CLK = 16
+# The kernel sources whose change invalidates a stored DRAM-traffic capture.
+KERNEL_SOURCES = ("gwl_lnl.cu", "gwl_bins.cuh", "gwl_sched.cuh", "gwl_device.cuh", "gwl_ff.cuh", "gwl_internal.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k_window_mixed_c2.txt")
 
 
 def parse():
@@ -71,6 +92,11 @@ def parse():
     ap.add_argument("--impl", default="gwl", choices=["gwl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--legs", default=",".join(LEGS), help="extra measurements to run (comma list; '' for none)")
+    ap.add_argument("--profile-only", default="", choices=["", "lnl", "grad", "cal", "fp64ph"],
+                    help="run one workload --warmup + --steps times without timing and exit (for profiler captures): "
+                         "lnl = the headline likelihood, grad = the 4096-proposal gradient, cal = the calibrated "
+                         "likelihood, fp64ph = the FP64-phase mixed arm")
     ap.add_argument("--shape", default="",
                     help="W,C: fixed likelihood launch shape (window bins, CTAs per SM) instead of the autotuner; "
                          "for profiler runs, whose timing would mislead the autotuner")
@@ -103,6 +129,22 @@ def max_over_ranks(values, device="cpu"):
 def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
     """Units processed by all replicas per second, over the slowest replica's time per step."""
     return world * units_per_rank / (ms * 1e-3)
+
+
+def r4(x):
+    """A number rounded to four significant digits (compact JSON)."""
+    if x is None:
+        return None
+    if isinstance(x, (list, tuple)):
+        return [r4(v) for v in x]
+    if isinstance(x, dict):
+        return {k: r4(v) for k, v in x.items()}
+    if isinstance(x, (bool, str)):
+        return x
+    if isinstance(x, (int, np.integer)):
+        return int(x)
+    x = float(x)
+    return x if x == 0.0 or not math.isfinite(x) else float(f"{x:.4g}")
 
 
 class ClockSampler:
@@ -166,8 +208,28 @@ def measured_peaks():
         return {}
 
 
-def device_event(ctx, precision, name=None):
-    """The benchmark event, with the injection made by the device library (no oracle on this leg)."""
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1909_11873_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic():
+    """DRAM bytes of one bin-loop launch from the committed one-pass ncu capture, or None when the
+    kernel sources have changed since that capture (its source hash no longer matches)."""
+    try:
+        kv = dict(ln.split(":", 1) for ln in open(TRAFFIC_FILE).read().splitlines() if ":" in ln)
+    except OSError:
+        return None, "no capture"
+    if kv.get("kernel_source_sha16", "").strip() != kernel_source_hash():
+        return None, "kernel changed since the capture"
+    return int(kv["dram_bytes_per_launch"].strip()), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+
+
+def device_event(name=None, seed=SEED, cfg=None, fcut_mode=0):
+    """A synthetic event whose injection comes from the device library's own template (no oracle)."""
     from paper_1909_11873_gb300 import gwl
     import torch
 
@@ -191,14 +253,10 @@ def device_event(ctx, precision, name=None):
         c = zero_ctx(ev)
         return -2.0 * float(gwl.loglike(c, torch.from_numpy(np.ascontiguousarray(th[None])).cuda()).cpu()[0])
 
-    ev = I.make_event(name or CONFIG, SEED, waveform, snr2)
+    ev = I.make_event(name or "custom", seed, waveform, snr2, cfg=cfg, fcut_mode=fcut_mode)
     for c in cache.values():
         c.close()
     return ev
-
-
-GRAD_BATCH = 4096
-NS_K, NS_CHAINS, NS_WALK = 250, 250, 20
 
 
 def in_band_pairs(ev, theta_full):
@@ -208,32 +266,54 @@ def in_band_pairs(ev, theta_full):
     return float(np.searchsorted(ev.freqs, fisco, side="right").sum())
 
 
-def run_grad(ev, args, flush, stream, peak_tflops):
+def pipe_roofline(pipes, pairs, kernel_ms, n_sm, fclk, n_eval):
+    """Every pipe's achieved rate against its derived peak; the bound is the largest fraction."""
+    s = kernel_ms * 1e-3
+    peaks = {"fp32_flop": n_sm * FP32_LANES_PER_SM * 2 * fclk, "mufu": n_sm * MUFU_PER_SM_CLK * fclk}
+    out = {}
+    for k, per_pair in pipes.items():
+        a = per_pair * pairs / s
+        out[k] = {"per_pair": per_pair, "achieved_T": a / 1e12, "peak_T": peaks[k] / 1e12, "frac": a / peaks[k]}
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    a = HBM_BYTES_PER_EVAL * n_eval / s / 1e9
+    out["hbm"] = {"per_eval_bytes": HBM_BYTES_PER_EVAL, "achieved_GBs": a, "peak_GBs": hbm, "frac": a / hbm}
+    bound = max(out, key=lambda k: out[k]["frac"])
+    return bound, out
+
+
+def time_device(fn, steps, flush, stream):
+    """Mean device time (ms) of fn() over `steps` calls, CUDA events on the launch stream, L2 flushed before each."""
+    import torch
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        flush.fill_(1.0)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+# ---------------------------------------------------------------- extra legs (rank 0)
+def leg_grad(ev, args, flush, stream, n_sm, fclk):
     """grad lnL evals/s on the same data (4096 proposals), device-timed, L2 flushed between steps."""
     import torch
 
     from paper_1909_11873_gb300 import gwl
 
-    th = I.proposals(ev, GRAD_BATCH, SEED + 7)
+    B = 4096
+    th = I.proposals(ev, B, SEED + 7)
     x = torch.from_numpy(I.reduced(th, ev.sampling)).cuda()
     ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
     tuning = ctx.gwl_autotune(x, gwl.GWL_TUNE_GRAD, stream)
-    out = torch.empty(GRAD_BATCH, dtype=torch.float64, device="cuda")
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
     g = torch.empty_like(x)
     for _ in range(args.warmup):
         ctx.gwl_grad(x, out, g, stream)
     torch.cuda.synchronize()
     steps = max(10, args.steps // 2)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for e0, e1 in evs:
-        flush.fill_(1.0)
-        e0.record(stream)
-        ctx.gwl_grad(x, out, g, stream)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ctx.gwl_sync()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    # the gradient bin loop's own time (library CUDA events on the launch stream)
+    ms = time_device(lambda: ctx.gwl_grad(x, out, g, stream), steps, flush, stream)
     ctx.gwl_profile(True)
     for _ in range(steps):
         flush.fill_(1.0)
@@ -241,21 +321,16 @@ def run_grad(ev, args, flush, stream, peak_tflops):
     torch.cuda.synchronize()
     kms, kn = ctx.gwl_profile_read(gwl.KERNEL_GRAD)
     ctx.gwl_profile(False)
+    ctx.gwl_sync()
     ctx.close()
-    pairs = in_band_pairs(ev, th)
-    achieved = FLOPS_PER_BIN_GRAD * pairs / (kms / kn * 1e-3) / 1e12
-    return {"value": GRAD_BATCH / (ms * 1e-3), "unit": "grad evals/s", "ms_per_step": ms, "batch": GRAD_BATCH,
-            "steps": steps, "precision": "mixed", "workload": "same 3-det 8 s data, 11-D gradient",
-            "grad_window": tuning["grad_window"],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "kernel": "k_window_grad<3,mixed>",
-                         "flops_per_pair": FLOPS_PER_BIN_GRAD, "pairs_per_launch": int(pairs),
-                         "kernel_ms": kms / kn}}
+    bound, pipes = pipe_roofline(PIPES_GRAD, in_band_pairs(ev, th), kms / kn, n_sm, fclk, B)
+    return {"v": B / (ms * 1e-3), "ms": ms, "B": B, "win": tuning["grad_window"], "kernel_ms": kms / kn,
+            "bound": bound, "frac": pipes[bound]["frac"], "fp32_frac": pipes["fp32_flop"]["frac"]}
 
 
-def run_cal(ev, args, flush, stream, peak_tflops):
+def leg_cal(ev, args, flush, stream, n_sm, fclk):
     """lnL evals/s with the calibration model (ten amplitude and ten phase nodes per detector, 71 parameters
-    per row) on the same data and batch, device-timed, L2 flushed between steps."""
+    per row) on the same data and batch size."""
     import torch
 
     from paper_1909_11873_gb300 import gwl
@@ -265,21 +340,13 @@ def run_cal(ev, args, flush, stream, peak_tflops):
     x = torch.from_numpy(rows).cuda()
     ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
     ctx.gwl_set_calibration(I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1])))
-    tuning = ctx.gwl_autotune(x, gwl.GWL_TUNE_LOGLIKE, stream)
+    ctx.gwl_autotune(x, gwl.GWL_TUNE_LOGLIKE, stream)
     out = torch.empty(BATCH, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
         ctx.gwl_loglike(x, out, stream)
     torch.cuda.synchronize()
     steps = max(10, args.steps // 2)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for e0, e1 in evs:
-        flush.fill_(1.0)
-        e0.record(stream)
-        ctx.gwl_loglike(x, out, stream)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ctx.gwl_sync()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    ms = time_device(lambda: ctx.gwl_loglike(x, out, stream), steps, flush, stream)
     ctx.gwl_profile(True)
     for _ in range(steps):
         flush.fill_(1.0)
@@ -287,24 +354,135 @@ def run_cal(ev, args, flush, stream, peak_tflops):
     torch.cuda.synchronize()
     kms, kn = ctx.gwl_profile_read(gwl.KERNEL_BINS)
     ctx.gwl_profile(False)
+    ctx.gwl_sync()
     ctx.close()
-    pairs = in_band_pairs(ev, th[:, :11])
-    achieved = FLOPS_PER_BIN_CAL * pairs / (kms / kn * 1e-3) / 1e12
-    return {"value": BATCH / (ms * 1e-3), "unit": "evals/s", "ms_per_step": ms, "batch": BATCH, "steps": steps,
-            "precision": "mixed", "dim": int(rows.shape[1]),
-            "workload": "same 3-det 8 s data, 11 source + 60 calibration parameters (10 nodes per detector)",
-            "window": tuning["window"], "ctas_per_sm": tuning["ctas_per_sm"],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tflops, "kernel": "k_window<3,mixed,calibrated>",
-                         "flops_per_pair": FLOPS_PER_BIN_CAL, "pairs_per_launch": int(pairs),
-                         "kernel_ms": kms / kn}}
+    bound, pipes = pipe_roofline(PIPES_CAL, in_band_pairs(ev, th[:, :11]), kms / kn, n_sm, fclk, BATCH)
+    return {"v": BATCH / (ms * 1e-3), "ms": ms, "dim": int(rows.shape[1]), "kernel_ms": kms / kn, "bound": bound,
+            "frac": pipes[bound]["frac"]}
 
 
-def run_ns(args):
+def lnl_rates(ev, B, seed, args, flush, stream, precisions, local_fraction=0.5, tune=True):
+    """Device-timed lnL evals/s of each precision mode on one event and batch."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    th = I.proposals(ev, B, seed, local_fraction=local_fraction)
+    x = torch.from_numpy(I.reduced(th, ev.sampling)).cuda()
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, prec in precisions:
+        ctx = gwl.Context.from_event(ev, prec)
+        if tune and prec == gwl.GWL_MIXED:
+            ctx.gwl_autotune(x, gwl.GWL_TUNE_LOGLIKE, stream)
+        ctx.gwl_loglike(x, out, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.gwl_loglike(x, out, stream)
+        torch.cuda.synchronize()
+        one = time.perf_counter() - t0
+        steps = int(min(max(3, args.steps // 4), max(3, 1.0 / max(one, 1e-6))))
+        ms = time_device(lambda: ctx.gwl_loglike(x, out, stream), steps, flush, stream)
+        ctx.gwl_sync()
+        ctx.close()
+        res[name] = B / (ms * 1e-3)
+    return res
+
+
+def four_d(ev):
+    """The event with (Mc, q, tc, phic) sampled in narrow priors around the injection, the other parameters at
+    the injection: a unimodal posterior on which lnZ comparisons are well posed."""
+    th = ev.theta_inj
+    bns = th[0] < 5
+    smp = I.Sampling(np.array([0, 1, 9, 10], dtype=np.int32), th.copy(), np.zeros(4, dtype=np.int32),
+                     np.array([th[0] * (0.995 if bns else 0.97), 0.7 if bns else 0.25, -0.02, 0.0]),
+                     np.array([th[0] * (1.005 if bns else 1.03), 1.0, 0.02, 2 * math.pi]),
+                     np.array([0, 0, 0, 1], dtype=np.int32))
+    return dataclasses.replace(ev, sampling=smp)
+
+
+C4_K, C4_CHAINS, C4_WALK, C4_SEED = 1000, 1000, 100, 4
+
+
+def leg_c4(args, flush, stream):
+    """64 events of {4..128} s (3 detectors, 20-1024 Hz, BBH or BNS): one batched lnL call over 1000
+    proposals per event vs per-event calls, and full nested-sampling runs of all events (K = 1000,
+    1000 chains, walk 100, 4-D sampling) as one graph per round vs 64 per-event ns_run calls."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    cfgs = I.c4_events(C4_SEED, 64)
+    evs = [four_d(device_event(cfg=c, seed=c["seed"])) for c in cfgs]
+    ths = [I.proposals(ev, C4_K, c["seed"]) for ev, c in zip(evs, cfgs)]
+    ctxs = [gwl.Context.from_event(ev, gwl.GWL_MIXED) for ev in evs]
+    mc = gwl.MultiContext(ctxs)
+    x = torch.from_numpy(np.concatenate([I.reduced(t, ev.sampling) for t, ev in zip(ths, evs)])).cuda()
+    xs = [x[i * C4_K:(i + 1) * C4_K] for i in range(len(evs))]
+    out = torch.empty(x.shape[0], dtype=torch.float64, device="cuda")
+    outs = [torch.empty(C4_K, dtype=torch.float64, device="cuda") for _ in evs]
+    mc.gwl_multi_loglike(x, out)
+    [c.gwl_loglike(xx, o) for c, xx, o in zip(ctxs, xs, outs)]
+    torch.cuda.synchronize()
+    ms_b = time_device(lambda: mc.gwl_multi_loglike(x, out, stream), 5, flush, stream)
+    ms_e = time_device(lambda: [c.gwl_loglike(xx, o, stream) for c, xx, o in zip(ctxs, xs, outs)], 5, flush, stream)
+    diff = float((torch.cat(outs) - out).abs().max())
+    # nested sampling: all events in one graph per round, then event by event
+    mc.gwl_multi_ns_run(C4_K, C4_CHAINS, C4_WALK, seed=1, dlogz=0.1, max_rounds=1)  # warm-up
+    t0 = time.perf_counter()
+    rb = mc.gwl_multi_ns_run(C4_K, C4_CHAINS, C4_WALK, seed=C4_SEED, dlogz=0.1)
+    wall_b = time.perf_counter() - t0
+    ctxs[0].ns_run(C4_K, C4_CHAINS, C4_WALK, seed=1, dlogz=0.1, max_rounds=1)  # warm-up
+    t0 = time.perf_counter()
+    re = [c.ns_run(C4_K, C4_CHAINS, C4_WALK, seed=C4_SEED + 1 + e, dlogz=0.1) for e, c in enumerate(ctxs)]
+    wall_e = time.perf_counter() - t0
+    z = np.array([[a["lnZ"] - b["lnZ"], math.hypot(a["lnZ_err"], b["lnZ_err"])] for a, b in zip(rb, re)])
+    mc.close()
+    for c in ctxs:
+        c.close()
+    return {"lnl_batched_ms": ms_b, "lnl_per_event_ms": ms_e, "lnl_x": ms_e / ms_b, "lnl_diff": diff,
+            "ns_graph_s": wall_b, "ns_per_event_s": wall_e, "ns_x": wall_e / wall_b,
+            "rounds": int(max(r["rounds"] for r in rb)),
+            "lnZ_graph_vs_per_event_max_sigma": float(np.max(np.abs(z[:, 0]) / z[:, 1])),
+            "durations": sorted({int(c["T"]) for c in cfgs})}
+
+
+def leg_c5(ev, args):
+    """Random walk vs gradient-informed (Galilean) walk inside nested sampling on the 3-detector 8 s event:
+    Kish effective samples per second over three seeds, in 4-D and 11-D (K = 500, walk 20)."""
+    from paper_1909_11873_gb300 import gwl
+
+    out = {}
+    for dims in (4, 11):
+        e = four_d(ev) if dims == 4 else ev
+        row = {}
+        for name, kind in (("random", gwl.GWL_WALK_RANDOM), ("galilean", gwl.GWL_WALK_GALILEAN)):
+            ctx = gwl.Context.from_event(e, gwl.GWL_MIXED)
+            ctx.gwl_set_walk(kind)
+            ctx.ns_run(500, 500, 20, seed=999, dlogz=0.1, max_rounds=1)  # warm-up
+            ess, lnz = [], []
+            for sd in range(3):
+                t0 = time.perf_counter()
+                r = ctx.ns_run(500, 500, 20, seed=100 + sd, dlogz=0.1, max_dead=400000)
+                wall = time.perf_counter() - t0
+                lw = r["dead_lnl"] + r["dead_logwt"]
+                w = np.exp(lw - lw.max())
+                ess.append(w.sum() ** 2 / (w ** 2).sum() / wall)
+                lnz.append(r["lnZ"])
+            ctx.close()
+            row[name] = {"ess_s": float(np.mean(ess)), "lnZ": float(np.mean(lnz)), "spread": float(np.std(lnz, ddof=1))}
+        out[f"{dims}d"] = row
+    return out
+
+
+NS_K, NS_CHAINS, NS_WALK = 250, 250, 20
+
+
+def leg_ns():
     """Wall time of a full nested-sampling run on the 1-detector 4 s zero-noise event (4-D)."""
     from paper_1909_11873_gb300 import gwl
 
-    ev1 = device_event(None, None, name="c1")
+    ev1 = device_event("c1")
     ctx = gwl.Context.from_event(ev1, gwl.GWL_MIXED)
     ctx.ns_run(NS_K, NS_CHAINS, NS_WALK, seed=1, dlogz=0.1, max_rounds=2)  # warm-up (graph build, scratch)
     t0 = time.perf_counter()
@@ -312,11 +490,28 @@ def run_ns(args):
     wall = time.perf_counter() - t0
     ctx.close()
     return {"wall_s": wall, "lnZ": r["lnZ"], "lnZ_err": r["lnZ_err"], "rounds": r["rounds"],
-            "n_proposals": r["n_proposals"], "consumed_per_round": r["consumed_per_round"],
-            "workload": f"1-det 4 s 20-512 Hz zero-noise, 4-D, K={NS_K}, {NS_CHAINS} chains, walk {NS_WALK}, "
-                        "dlogz 0.1, mixed precision"}
+            "consumed": r["consumed_per_round"], "eq5": NS_K * math.log(1 + NS_CHAINS / NS_K)}
 
 
+def leg_eq5():
+    """Candidates consumed per round against Eq. 5's K ln(1 + B/K), and the run's wall time, for several
+    batch sizes B at K = 250 (1-detector 4 s event, walk 20): the device analogue of the paper's Fig. 1."""
+    from paper_1909_11873_gb300 import gwl
+
+    ev1 = device_event("c1")
+    ctx = gwl.Context.from_event(ev1, gwl.GWL_MIXED)
+    ctx.ns_run(NS_K, 64, NS_WALK, seed=99, dlogz=0.1, max_rounds=2)  # warm-up
+    rows = []
+    for B in (25, 250, 1000, 4000):
+        t0 = time.perf_counter()
+        r = ctx.ns_run(NS_K, B, NS_WALK, seed=1000 + B, dlogz=0.1)
+        wall = time.perf_counter() - t0
+        rows.append([B, r["consumed_per_round"] / (NS_K * math.log(1 + B / NS_K)), int(r["rounds"]), wall])
+    ctx.close()
+    return {"cols": ["B", "consumed/eq5", "rounds", "wall_s"], "rows": rows}
+
+
+# ---------------------------------------------------------------- main leg
 def run_gwl(args):
     import torch
 
@@ -330,7 +525,8 @@ def run_gwl(args):
 
     if not os.path.exists(gwl.LIB_PATH):
         build.build()
-    ev = device_event(None, None)
+    legs = [x for x in args.legs.split(",") if x] if rank == 0 else []
+    ev = device_event(CONFIG)
     theta_full = I.proposals(ev, BATCH, rank_seed(rank))
     theta_np = np.ascontiguousarray(I.reduced(theta_full, ev.sampling))
     theta = torch.from_numpy(theta_np).cuda()
@@ -338,15 +534,9 @@ def run_gwl(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(ctx, steps, warmup, host=False, soak=0.0, nvtx=None):
-        # pinned host buffers, as a caller would hold them (numpy views made once)
-        host_t = torch.from_numpy(theta_np).pin_memory().numpy() if host else None
-        host_l = torch.empty(BATCH, dtype=torch.float64).pin_memory().numpy() if host else None
+    def timed(ctx, steps, warmup, soak=0.0, nvtx=None):
         for _ in range(warmup):
-            if host:
-                ctx.gwl_loglike_host(host_t, host_l, stream)
-            else:
-                ctx.gwl_loglike(theta, lnl, stream)
+            ctx.gwl_loglike(theta, lnl, stream)
         torch.cuda.synchronize()
         # untimed soak at load so that the clock sampler sees the GPU under this workload
         t_end = time.perf_counter() + soak
@@ -358,80 +548,71 @@ def run_gwl(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         l0 = ctx.launch_count()
         # an NVTX range around the timed steps lets a profiler list exactly these launches
         rng = torch.cuda.nvtx.range_start(nvtx) if nvtx else None
-        wall0 = time.perf_counter()
-        for e0, e1 in evs:
-            flush.fill_(1.0)
-            e0.record(stream)
-            if host:
-                ctx.gwl_loglike_host(host_t, host_l, stream)
-            else:
-                ctx.gwl_loglike(theta, lnl, stream)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
+        ms = time_device(lambda: ctx.gwl_loglike(theta, lnl, stream), steps, flush, stream)
         if rng is not None:
             torch.cuda.nvtx.range_end(rng)
         if world > 1:
             torch.distributed.barrier()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        return sum(ms) / len(ms), ctx.launch_count() - l0, wall
+        return ms, ctx.launch_count() - l0
 
-    results = {}
-    ctxs = {}
-    tuning = {}
-    for prec in (gwl.GWL_FP64, gwl.GWL_MIXED):
-        ctx = gwl.Context.from_event(ev, prec)
-        ctxs[prec] = ctx
-        # launch shape from the library's autotuner on this batch (untimed), or fixed by --shape
-        if args.shape and prec == gwl.GWL_MIXED:
-            w, c = (int(v) for v in args.shape.split(","))
-            ctx.gwl_set_tuning(window=w, ctas_per_sm=c)
-            tuning["mixed"] = dict(ctx.gwl_get_tuning(), fixed=True)
-        else:
-            tuning["mixed" if prec == gwl.GWL_MIXED else "fp64"] = ctx.gwl_autotune(theta, gwl.GWL_TUNE_LOGLIKE,
-                                                                                    stream)
-        steps = args.steps if prec == gwl.GWL_MIXED else max(3, args.steps // 5)
-        with ClockSampler(local) as clk:
-            ms, launches, wall = timed(ctx, steps, args.warmup, soak=args.soak_seconds,
-                                       nvtx="timed_mixed" if prec == gwl.GWL_MIXED else "timed_fp64")
-        ctx.gwl_sync()
-        results[prec] = dict(ms=ms, launches=launches, clocks=clk.summary(), steps=steps, wall=wall)
+    def timed_host(ctx, steps, warmup):
+        """End to end through the public host-buffer entry point: the host clock around each call (the call
+        synchronises before returning); the flush is issued and finished before the clock starts."""
+        host_t = torch.from_numpy(theta_np).pin_memory().numpy()
+        host_l = torch.empty(BATCH, dtype=torch.float64).pin_memory().numpy()
+        for _ in range(warmup):
+            ctx.gwl_loglike_host(host_t, host_l, stream)
+        if world > 1:
+            torch.distributed.barrier()
+        walls = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.gwl_loglike_host(host_t, host_l, stream)
+            walls.append(time.perf_counter() - t0)
+        if world > 1:
+            torch.distributed.barrier()
+        # the same calls bracketed by CUDA events instead (the host's submission and return fall outside)
+        dev = time_device(lambda: ctx.gwl_loglike_host(host_t, host_l, stream), steps, flush, stream)
+        return 1e3 * sum(walls) / len(walls), dev
 
-    mixed = ctxs[gwl.GWL_MIXED]
-    # dominant kernel timing (library CUDA events on the launch stream) over a separate timed pass
-    mixed.gwl_profile(True)
+    ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
+    if args.shape:
+        w, c = (int(v) for v in args.shape.split(","))
+        ctx.gwl_set_tuning(window=w, ctas_per_sm=c)
+        tuning = dict(ctx.gwl_get_tuning(), fixed=True)
+    else:
+        tuning = ctx.gwl_autotune(theta, gwl.GWL_TUNE_LOGLIKE, stream)
+    with ClockSampler(local) as clk:
+        ms, launches = timed(ctx, args.steps, args.warmup, soak=args.soak_seconds, nvtx="timed_mixed")
+    ctx.gwl_sync()
+    clocks = clk.summary()
+    # the bin loop's own time (library CUDA events on the launch stream) over a separate pass
+    ctx.gwl_profile(True)
     for _ in range(args.steps):
         flush.fill_(1.0)
-        mixed.gwl_loglike(theta, lnl, stream)
+        ctx.gwl_loglike(theta, lnl, stream)
     torch.cuda.synchronize()
-    prof = {k: mixed.gwl_profile_read(k) for k in (gwl.KERNEL_PROLOGUE, gwl.KERNEL_BINS, gwl.KERNEL_COMBINE)}
-    mixed.gwl_profile(False)
+    prof = {k: ctx.gwl_profile_read(k) for k in (gwl.KERNEL_PROLOGUE, gwl.KERNEL_BINS)}
+    ctx.gwl_profile(False)
+    ms_host, ms_host_dev = timed_host(ctx, max(5, args.steps // 2), args.warmup)
+    ctx.gwl_sync()
 
-    # end-to-end with host buffers
-    ms_e2e, _, _ = timed(mixed, max(5, args.steps // 2), args.warmup, host=True)
-    # algorithmic work of one launch: in-band (proposal, bin) pairs (ncut from the prologue's f_ISCO)
     pairs = in_band_pairs(ev, theta_full)
-    # the bin loop of one call (one launch; it also forms lnL)
-    bins_ms, bins_n = prof[gwl.KERNEL_BINS]
-    per_launch_s = bins_ms / args.steps * 1e-3
+    bins_ms = prof[gwl.KERNEL_BINS][0] / args.steps
     peaks = measured_peaks()
-    clk = results[gwl.GWL_MIXED]["clocks"]
-    fclk = (clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    import torch as _t
-    n_sm = _t.cuda.get_device_properties(local).multi_processor_count
-    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * fclk / 1e12
-    achieved = FLOPS_PER_BIN_MIXED * pairs / per_launch_s / 1e12
-    grad_res = run_grad(ev, args, flush, stream, peak_tflops) if rank == 0 else None
-    cal_res = run_cal(ev, args, flush, stream, peak_tflops) if rank == 0 else None
-    ns_res = run_ns(args) if rank == 0 else None
+    fclk = (clocks["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    bound, pipes = pipe_roofline(PIPES_MIXED, pairs, bins_ms, n_sm, fclk, BATCH)
+    traffic, traffic_basis = stored_traffic()
 
-    ms, ms64, mse = max_over_ranks([results[gwl.GWL_MIXED]["ms"], results[gwl.GWL_FP64]["ms"], ms_e2e], "cuda")
+    ms, mse = max_over_ranks([ms, ms_host], "cuda")
     value = whole_job_rate(BATCH, world, ms)
-
+    b = pipes[bound]
     out = {
         "metric": METRIC,
         "value": value,
@@ -446,46 +627,60 @@ def run_gwl(args):
         "dtype": "f32x2-phase/f32/f64",
         "data": "synthetic (seeded coloured Gaussian noise + TaylorF2 injection from the device template)",
         "config": {"workload": "3-det BBH, 8 s, 20-1024 Hz, 8033 bins/det, 11-D, batch 8192 proposals per GPU",
-                   "global_batch": BATCH * world, "bins_per_det": int(ev.M), "n_det": int(ev.n_det),
-                   "in_band_pairs_per_batch": int(pairs), "precision": "mixed",
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "fp64_path": {"value": whole_job_rate(BATCH, world, ms64), "ms_per_step": ms64, "steps": results[gwl.GWL_FP64]["steps"],
-                      "speedup_mixed_over_fp64": ms64 / ms},
-        "e2e": {"value": whole_job_rate(BATCH, world, mse), "unit": "evals/s", "h2d_bytes_per_step": int(theta_np.nbytes),
-                "d2h_bytes_per_step": int(BATCH * 8)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": KWINDOW_DRAM_BYTES,
-                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_window<3,mixed> "
-                                      "launch (704-bin windows, 2 CTAs/SM; profiles/k_window_mixed_c2.md)",
-                     "kernel": "k_window<3,mixed> (windowed bin loop and lnL combination)",
-                     "peak_basis": f"FP32 pipe: {n_sm} SMs x 128 lanes x 2 flop x {fclk / 1e6:.0f} MHz (derived)",
-                     "flops_per_pair": FLOPS_PER_BIN_MIXED, "pairs_per_launch": int(pairs),
-                     "kernel_ms": per_launch_s * 1e3,
-                     "share_of_step": bins_ms / args.steps / ms},
-        "kernel_ms": {"prologue": prof[gwl.KERNEL_PROLOGUE][0] / args.steps,
-                      "bins": bins_ms / args.steps,
-                      "combine": prof[gwl.KERNEL_COMBINE][0] / args.steps},
-        "tuning": {k: {f: v[f] for f in ("window", "ctas_per_sm", "ms_loglike", "n_tried")}
-                   for k, v in tuning.items()},
-        "clocks": clk,
-        "gpu_launches": int(results[gwl.GWL_MIXED]["launches"]),
-        "grad": grad_res,
-        "calibrated": cal_res,
-        "ns": ns_res,
+                   "global_batch": BATCH * world, "in_band_pairs_per_batch": int(pairs), "precision": "mixed",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
+                   "window": tuning["window"], "ctas_per_sm": tuning["ctas_per_sm"]},
+        "e2e": {"value": whole_job_rate(BATCH, world, mse), "unit": "evals/s", "ms_per_call_host_clock": mse,
+                "device_events_value": whole_job_rate(BATCH, world, ms_host_dev),
+                "h2d_bytes_per_step": int(theta_np.nbytes), "d2h_bytes_per_step": int(BATCH * 8)},
+        "roofline": {"bound": "alu", "pipe": bound, "achieved": b.get("achieved_T"), "peak": b.get("peak_T"),
+                     "unit": "Top/s" if bound == "mufu" else "TFLOP/s", "frac": b["frac"], "traffic": traffic,
+                     "traffic_basis": traffic_basis, "kernel": "k_window<3,mixed>", "kernel_ms": bins_ms,
+                     "pairs_per_launch": int(pairs), "share_of_step": bins_ms / ms,
+                     "pipes": r4({k: {"per": v.get("per_pair", v.get("per_eval_bytes")), "frac": v["frac"]}
+                                  for k, v in pipes.items()}),
+                     "peak_basis": f"derived: {n_sm} SMs x {fclk / 1e6:.0f} MHz x (128 FP32 lanes x 2 | 16 MUFU)"},
+        "kernel_ms": r4({"prologue": prof[gwl.KERNEL_PROLOGUE][0] / args.steps, "bins": bins_ms}),
+        "clocks": clocks,
+        "gpu_launches": int(launches),
     }
+    ctx.close()
+    legres = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(theta_full, args.cpu_seconds, use_device_event=ev)
-        out["accuracy"] = out["cpu_baseline"].pop("accuracy")
-        out["cpu_baseline"]["ns_wall_s"] = oracle_ns_wall()
-    for c in ctxs.values():
-        c.close()
+        out["cpu_baseline"] = cpu_baseline(theta_full, args.cpu_seconds, legs)
+    # extra measurements, compact, at the end of the line
+    if "fp64" in legs:
+        r = lnl_rates(ev, BATCH, rank_seed(rank), args, flush, stream, (("fp64", gwl.GWL_FP64),))
+        legres["fp64_c2"] = {"v": r["fp64"], "mixed_x": value / r["fp64"]}
+    if "grad" in legs:
+        legres["grad_c5"] = leg_grad(ev, args, flush, stream, n_sm, fclk)
+    if "cal" in legs:
+        legres["cal_c2"] = leg_cal(ev, args, flush, stream, n_sm, fclk)
+    if "c1" in legs:
+        legres["c1"] = lnl_rates(device_event("c1"), 1024, 1, args, flush, stream,
+                                 (("mixed", gwl.GWL_MIXED), ("fp64", gwl.GWL_FP64)), local_fraction=0.0)
+    if "c3" in legs:
+        legres["c3"] = lnl_rates(device_event("c3"), 2048, 3, args, flush, stream,
+                                 (("mixed", gwl.GWL_MIXED), ("fp64", gwl.GWL_FP64)))
+    if "ns" in legs:
+        legres["ns_c1"] = leg_ns()
+        legres["eq5"] = leg_eq5()
+    if "c5" in legs:
+        legres["c5_ess"] = leg_c5(ev, args)
+    if "c4" in legs:
+        legres["c4"] = leg_c4(args, flush, stream)
+    if legres:
+        out["legs"] = r4(legres)
+    if "cpu_baseline" in out and "checks" in out["cpu_baseline"]:
+        out["oracle_checks"] = r4(out["cpu_baseline"].pop("checks"))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def oracle_event():
+# ---------------------------------------------------------------- oracle (host cores): baseline and checks
+def oracle_event(name=CONFIG, seed=SEED, cfg=None):
     import oracle
 
     def wf(ev, th):
@@ -494,11 +689,30 @@ def oracle_event():
     def snr2(ev, th):
         return -2.0 * oracle.loglike(ev.with_strain(np.zeros_like(ev.strain)), th[None])[0]
 
-    return I.make_event(CONFIG, SEED, wf, snr2)
+    return I.make_event(name, seed, wf, snr2, cfg=cfg)
 
 
-def cpu_baseline(theta_full, seconds, use_device_event=None):
-    """The FP64 oracle (as it stands) on all host cores, repeated over the batch until ~seconds elapse."""
+def max_err(ev, theta_full, ref):
+    """max |lnL_device - lnL_oracle| of both device paths on the oracle's own event (bars 1e-6 / 1e-3)."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    x = torch.from_numpy(np.ascontiguousarray(I.reduced(theta_full, ev.sampling))).cuda()
+    out = {"rows": int(theta_full.shape[0])}
+    for name, prec in (("fp64", gwl.GWL_FP64), ("mixed", gwl.GWL_MIXED)):
+        ctx = gwl.Context.from_event(ev, prec)
+        got = gwl.loglike(ctx, x).cpu().numpy()
+        ctx.gwl_sync()
+        ctx.close()
+        out[name] = float(np.max(np.abs(got - ref)))
+        out[name + "_rel"] = float(np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))))
+    return out
+
+
+def cpu_baseline(theta_full, seconds, legs):
+    """The FP64 oracle (as it stands) on all host cores, repeated over the batch until ~seconds elapse; then
+    the oracle comparisons of the device legs (|dlnL| per workload, nested-sampling evidence)."""
     import oracle
 
     ev = oracle_event()
@@ -507,50 +721,52 @@ def cpu_baseline(theta_full, seconds, use_device_event=None):
     t0 = time.perf_counter()
     done = 0
     while True:
-        oracle.loglike(ev, sample, n_threads=n)
+        ref = oracle.loglike(ev, sample, n_threads=n)
         done += sample.shape[0]
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
+    checks = {"bars": [1e-6, 1e-3], "c2": max_err(ev, sample, ref)}
+    if "c1" in legs:
+        e1 = oracle_event("c1", 1)
+        th = I.proposals(e1, 1024, 1, local_fraction=0.0)
+        checks["c1"] = max_err(e1, th, oracle.loglike(e1, th, n_threads=n))
+    if "c3" in legs:
+        e3 = oracle_event("c3", 3)
+        th = I.proposals(e3, 2048, 3)[::32]  # 64 of the 2048 rows
+        checks["c3"] = max_err(e3, th, oracle.loglike(e3, th, n_threads=n))
+    if "ns" in legs:
+        e1 = oracle_event("c1", SEED)
+        t1 = time.perf_counter()
+        r = oracle.ns_run(e1, e1.sampling, NS_K, NS_CHAINS, NS_WALK, seed=2, dlogz=0.1)
+        checks["ns_c1_oracle"] = {"wall_s": time.perf_counter() - t1, "lnZ": r["lnZ"], "lnZ_err": r["lnZ_err"]}
+    if "c4" in legs:
+        checks["c4_lnZ"] = c4_oracle_lnz(n)
     return {"value": done / el, "unit": "evals/s", "cores": n, "kind": "oracle",
             "sample": f"{done} evaluations = repeated first 1024 proposals of the 8192-proposal batch "
-                      f"(same event, oracle-made injection), {el:.1f} s wall",
-            "accuracy": device_accuracy(ev, sample, oracle.loglike(ev, sample, n_threads=n))}
+                      f"(same event, oracle-made injection), {el:.1f} s wall", "checks": checks}
 
 
-def device_accuracy(ev, theta_full, ref):
-    """max |lnL_device - lnL_oracle| of both device paths on the oracle's own event (bars 1e-6 / 1e-3)."""
-    import torch
-
+def c4_oracle_lnz(n_threads):
+    """lnZ of the device's full-scale run (K = 1000, 1000 chains, walk 100, 4-D) against the oracle's on the
+    two shortest BBH events of the 64-event workload (oracle-made injections, same data for both)."""
     from paper_1909_11873_gb300 import gwl
-
-    x = torch.from_numpy(np.ascontiguousarray(I.reduced(theta_full, ev.sampling))).cuda()
-    out = {"rows": int(theta_full.shape[0]), "max_abs_lnL": float(np.max(np.abs(ref)))}
-    for name, prec in (("fp64", gwl.GWL_FP64), ("mixed", gwl.GWL_MIXED)):
-        ctx = gwl.Context.from_event(ev, prec)
-        got = gwl.loglike(ctx, x).cpu().numpy()
-        ctx.gwl_sync()
-        ctx.close()
-        out[f"{name}_max_abs_err"] = float(np.max(np.abs(got - ref)))
-    out["bars"] = {"fp64": 1e-6, "mixed": 1e-3}
-    return out
-
-
-def oracle_ns_wall():
-    """The oracle's nested sampler on the same 1-detector event and settings (host cores)."""
     import oracle
 
-    def wf(ev, th):
-        return oracle.waveform(ev, th)
-
-    def snr2(ev, th):
-        return -2.0 * oracle.loglike(ev.with_strain(np.zeros_like(ev.strain)), th[None])[0]
-
-    ev1 = I.make_event("c1", SEED, wf, snr2)
-    t0 = time.perf_counter()
-    r = oracle.ns_run(ev1, ev1.sampling, NS_K, NS_CHAINS, NS_WALK, seed=2, dlogz=0.1)
-    return {"wall_s": time.perf_counter() - t0, "lnZ": r["lnZ"], "lnZ_err": r["lnZ_err"], "rounds": r["rounds"],
-            "cores": os.cpu_count()}
+    cfgs = I.c4_events(C4_SEED, 64)
+    pick = sorted((c["T"], i) for i, c in enumerate(cfgs) if c["source"] == "bbh")[:2]
+    rows = []
+    for _, i in pick:
+        c = cfgs[i]
+        ev = four_d(oracle_event("custom", c["seed"], cfg=c))
+        ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
+        d = ctx.ns_run(C4_K, C4_CHAINS, C4_WALK, seed=C4_SEED + 1 + i, dlogz=0.1)
+        ctx.close()
+        t0 = time.perf_counter()
+        o = oracle.ns_run(ev, ev.sampling, C4_K, C4_CHAINS, C4_WALK, seed=C4_SEED + 101 + i, dlogz=0.1)
+        rows.append({"event": i, "T": c["T"], "dev": d["lnZ"], "orc": o["lnZ"],
+                     "sigma": math.hypot(d["lnZ_err"], o["lnZ_err"]), "oracle_s": time.perf_counter() - t0})
+    return rows
 
 
 def run_reference(args):
@@ -584,10 +800,50 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile_only(args):
+    """One workload's calls, untimed, for a profiler; the launch shape from --shape (else the defaults)."""
+    import torch
+
+    from paper_1909_11873_gb300 import build, gwl
+
+    if not os.path.exists(gwl.LIB_PATH):
+        build.build()
+    torch.cuda.set_device(0)
+    ev = device_event(CONFIG)
+    prec = {"fp64ph": getattr(gwl, "GWL_MIXED_F64PHASE", None)}.get(args.profile_only, gwl.GWL_MIXED)
+    ctx = gwl.Context.from_event(ev, prec)
+    B = 4096 if args.profile_only == "grad" else BATCH
+    if args.profile_only == "cal":
+        th = I.calibrated_proposals(ev, B, SEED + 11)
+        rows = np.concatenate([I.reduced(th[:, :11], ev.sampling), th[:, 11:]], axis=1)
+        ctx.gwl_set_calibration(I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1])))
+    else:
+        rows = I.reduced(I.proposals(ev, B, SEED + (7 if args.profile_only == "grad" else 0)), ev.sampling)
+    if args.shape:
+        w, c = (int(v) for v in args.shape.split(","))
+        ctx.gwl_set_tuning(window=w if args.profile_only != "grad" else 0, ctas_per_sm=c,
+                           grad_window=w if args.profile_only == "grad" else 0)
+    x = torch.from_numpy(np.ascontiguousarray(rows)).cuda()
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(x)
+    for _ in range(args.warmup + args.steps):
+        if args.profile_only == "grad":
+            ctx.gwl_grad(x, out, g)
+        else:
+            ctx.gwl_loglike(x, out)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    print(json.dumps({"profile_only": args.profile_only, "calls": args.warmup + args.steps, "B": B,
+                      "tuning": ctx.gwl_get_tuning(), "lnl0": float(out[0])}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_only:
+        run_profile_only(args)
     else:
         run_gwl(args)
 

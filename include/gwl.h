@@ -255,6 +255,16 @@ int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t see
 #define GWL_FF_COS 3
 int gwl_ff_eval(const double* x_dev, int64_t n, int fn, double* out_dev, void* stream);
 
+/* Diagnostic: the Philox4x32-10 generator of ns_replace and ns_run (Salmon,
+ * Moraes, Dror & Shaw 2011) on given counters and keys, so that the device
+ * generator can be checked against the generator's published known-answer
+ * vectors.  (An interface addition without a counterpart in the paper.)
+ *   in_dev  dev [n][6] uint32: counter words c0..c3, then key words k0, k1
+ *   out_dev dev [n][4] uint32: the output block x0..x3
+ * GWL_ERR_ARG for n < 0 or a null pointer with n > 0.  Enqueues one kernel
+ * on the stream and returns. */
+int gwl_test_philox(const uint32_t* in_dev, int64_t n, uint32_t* out_dev, void* stream);
+
 /* ---- many events in one batch ----
  * A multi-event context groups n_events contexts (same device, detector
  * count, precision and sampled dimension; different segment lengths and
@@ -295,9 +305,12 @@ void gwl_multi_destroy(gwl_multi* m);
  * library's CUDA module reserves on every device that loads it and keeps until
  * the process exits.  It calls no cudaMalloc, cudaFree or allocating routine;
  * per-kernel profiling (gwl_profile) is suspended for the call.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - gwl_create looks up the array's device address (cudaGetSymbolAddress)
+ *     on its device, afresh each time, so a context created after a
+ *     cudaDeviceReset uses the new array (a reset frees every context's
+ *     tables too: contexts from before it must not be used).  Only if that
+ *     look-up failed does the first call on the device repeat it; such a
+ *     first call must come before any stream capture.
  *   - A batch needs about (276 + 16 n_det ceil(n_bins / window)) bytes per
  *     proposal (24 n_det with the calibration model), window being the
  *     context's bin window (gwl_tuning.window); a
@@ -336,6 +349,19 @@ int gwl_sync(gwl_ctx* ctx);
  * usable.  Enqueues one kernel on the stream and returns; GWL_ERR_ARG for a
  * null context or seconds outside (0, 2]. */
 int gwl_test_wait_timeout(gwl_ctx* ctx, double seconds, void* stream);
+
+/* Diagnostic (an interface addition without a counterpart in the paper):
+ * counts the 32-bin blocks of the mixed likelihood bin loop whose phase
+ * deltas take the float-float form (blocks whose phase excursion bound is 16
+ * cycles or more: long signals in short segments, the low-frequency blocks
+ * of BNS signals), one count per block and proposal, so that tests can check
+ * that this path ran.  Counted on gwl_loglike and gwl_loglike_host calls.
+ *   enable  1: clear the counter and count from now on (synchronises the
+ *           device; allocates 8 bytes once); 0: stop counting; -1: unchanged
+ *   count   (may be NULL) receives the blocks counted since enabling; reading
+ *           it synchronises the device first (done before `enable` applies)
+ * GWL_ERR_ARG for a null context or another enable value. */
+int gwl_test_ffdelta_blocks(gwl_ctx* ctx, int enable, int64_t* count);
 
 /* Launch shape of the bin loops (the tile the hardware sees: a window of
  * `window` frequency bins staged in shared memory, drained by warps of 32

@@ -4,6 +4,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -245,6 +247,8 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
       rc = cuda_fail(e, "device attribute");
       break;
     }
+    // the fixed array of gwl_loglike_static: its address on this device, looked up afresh
+    if ((e = gwl::static_scratch_setup(c->device)) != cudaSuccess) { rc = cuda_fail(e, "static scratch"); break; }
     c->M = n_bins;
     c->n_det = n_det;
     c->f0 = f0;
@@ -598,6 +602,36 @@ int gwl_test_wait_timeout(gwl_ctx* c, double seconds, void* stream) {
   return GWL_OK;
 }
 
+int gwl_test_ffdelta_blocks(gwl_ctx* c, int enable, int64_t* count) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (count) {
+    unsigned long long n = 0;
+    if (c->d_ffc) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e == cudaSuccess) e = cudaMemcpy(&n, c->d_ffc, sizeof(n), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "gwl_test_ffdelta_blocks");
+    }
+    *count = (int64_t)n;
+  }
+  if (enable == 1) {
+    cudaError_t e = cudaSuccess;
+    if (!c->d_ffc) {
+      e = cudaMalloc((void**)&c->d_ffc, sizeof(unsigned long long));
+      if (e == cudaSuccess) c->bytes += (int64_t)sizeof(unsigned long long);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemset(c->d_ffc, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "gwl_test_ffdelta_blocks");
+    c->count_ff = true;
+  } else if (enable == 0) {
+    c->count_ff = false;
+  } else if (enable != -1) {
+    return fail(GWL_ERR_ARG, "gwl_test_ffdelta_blocks: enable=%d not in {-1, 0, 1}", enable);
+  }
+  return GWL_OK;
+}
+
 int gwl_sync(gwl_ctx* c) {
   int rc = check_ctx(c);
   if (rc) return rc;
@@ -777,6 +811,7 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_io, c->io_cap);
   dev_free(c, c->d_work, c->work_cap);
   dev_free(c, c->d_status, 4);
+  dev_free(c, c->d_ffc, 1);
   if (c->d_pgrad) cudaFree(c->d_pgrad);
   if (c->d_walk) cudaFree(c->d_walk);
   if (c->d_gmc) cudaFree(c->d_gmc);
@@ -788,6 +823,17 @@ void gwl_destroy(gwl_ctx* c) {
 }  // extern "C"
 
 namespace gwl {
+cudaError_t raise_smem_limit(const void* kernel, int device, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = set[std::make_pair(kernel, device)];
+  if (bytes <= have) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 static cudaEvent_t take_event(gwl_ctx* c) {
   if (!c->event_pool.empty()) {
     cudaEvent_t e = c->event_pool.back();

@@ -315,6 +315,7 @@ __device__ __forceinline__ void bin_anchor_exact(const float (&v)[4 * ((2 * kNBa
 // anchored phase; anc0 = the anchor row of bin j0 (shared or global memory).
 // With CAL, cal_sm holds the window's calibration rows (cal_row floats each),
 // nodes the proposal's node data, and X_d collects the <h|h> correction.
+// ffc (may be null) counts the blocks that take the float-float delta.
 // The result is per lane (the caller reduces over the warp).
 template <int NDET, bool CAL>
 __device__ __forceinline__ void anchored_sums_cal(const float* __restrict__ sm, int row_elems,
@@ -322,7 +323,8 @@ __device__ __forceinline__ void anchored_sums_cal(const float* __restrict__ sm, 
                                                   const PropMixed* __restrict__ P, int j0, int jend, int lane,
                                                   float (&U)[NDET], float (&V)[NDET],
                                                   const float* __restrict__ cal_sm, int cal_row,
-                                                  const float4* __restrict__ nodes, float (&X)[NDET]) {
+                                                  const float4* __restrict__ nodes, float (&X)[NDET],
+                                                  unsigned long long* __restrict__ ffc) {
   // anchored phase: the window starts on an anchor (windows are multiples of
   // kAnchor bins); lane l forms the anchor terms of block l of each batch of
   // 32 blocks and the warp shares them by shuffles
@@ -404,6 +406,7 @@ __device__ __forceinline__ void anchored_sums_cal(const float* __restrict__ sm, 
             bin_anchor<NDET, CAL>(v, ch, h ? ad1 : ad0, U, V, cb0, X);
           }
         } else if (jj < jend) {
+          if (ffc && lane == 0) atomicAdd(ffc, 1ull);  // lane 0 holds the block's first bin
           float v[RXF];
 #pragma unroll
           for (int k = 0; k < RXF / 4; ++k) *reinterpret_cast<float4*>(&v[4 * k]) = reinterpret_cast<const float4*>(row)[k];
@@ -419,9 +422,10 @@ template <int NDET>
 __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int row_elems,
                                               const float* __restrict__ anc0, float df,
                                               const PropMixed* __restrict__ P, int j0, int jend, int lane,
-                                              float (&U)[NDET], float (&V)[NDET]) {
+                                              float (&U)[NDET], float (&V)[NDET],
+                                              unsigned long long* __restrict__ ffc = nullptr) {
   float X[NDET];
-  anchored_sums_cal<NDET, false>(sm, row_elems, anc0, df, P, j0, jend, lane, U, V, nullptr, 0, nullptr, X);
+  anchored_sums_cal<NDET, false>(sm, row_elems, anc0, df, P, j0, jend, lane, U, V, nullptr, 0, nullptr, X, ffc);
 }
 
 template <int NDET>

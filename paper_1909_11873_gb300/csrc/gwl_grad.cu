@@ -513,13 +513,7 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   a.grad = grad;
   a.n_dim = c->opt.n_dim;
   const size_t smem = (size_t)CH * a.row_elems * sizeof(G);
-  static size_t smem_set = 0;
-  if (smem > smem_set) {
-    if ((e = cudaFuncSetAttribute(k_window_grad<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return e;
-    smem_set = smem;
-  }
+  if ((e = raise_smem_limit((const void*)k_window_grad<NDET, MIXED>, c->device, smem)) != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_GRAD, st);
     int64_t want = ((B + 7) / 8) * nw_total;

@@ -60,6 +60,8 @@ struct gwl_ctx {
   int* d_work = nullptr;         // [0] largest cut of the batch, [1 + w] proposal counter of window w
   int64_t work_cap = 0;          // in ints
   int* d_status = nullptr;       // [0] latched status bits
+  unsigned long long* d_ffc = nullptr;  // diagnostic: blocks of the mixed bin loop with float-float deltas
+  bool count_ff = false;                // count them (gwl_test_ffdelta_blocks)
 
   // tuning
   // tuning (gwl_set_tuning / gwl_autotune); the windows are set by gwl_create
@@ -97,6 +99,12 @@ inline size_t lnl_row_bytes(const gwl_ctx* c) {
 // Per-detector sums a bin loop keeps per (proposal, window): U, V (and the
 // calibrated <h|h> correction X).
 inline int sums_per_det(const gwl_ctx* c) { return c->n_cal_nodes ? 3 : 2; }
+
+// Raises the dynamic shared-memory limit of `kernel` on `device` (the current
+// device) to at least `bytes`.  The limit is a per-device attribute: the
+// largest value set so far is remembered per (kernel, device), under a lock,
+// so each device gets its own call.
+cudaError_t raise_smem_limit(const void* kernel, int device, size_t bytes);
 
 // Records a start event now and a stop event when it goes out of scope, on
 // the launch stream, if the context has profiling enabled.
@@ -147,6 +155,9 @@ int64_t multi_launches(const Multi* m);
 bool multi_has_calibration(const Multi* m);
 int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                  int64_t max_rounds, double scale0, double* res /* [E][11] */, cudaStream_t caller);
+
+// gwl_loglike_static's fixed array: look its device address up on `dev` (set-up, from gwl_create)
+cudaError_t static_scratch_setup(int dev);
 
 // device-path template, for diagnostics and injections
 cudaError_t launch_waveform(gwl_ctx* c, const double* theta, int64_t B, double* h, cudaStream_t st);

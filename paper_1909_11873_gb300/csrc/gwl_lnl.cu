@@ -424,6 +424,7 @@ struct WinArgs {
   int cal_par;           // first calibration parameter of a row
   int nn;                // calibration nodes
   const void* calQ;      // [nn][nn] natural-spline matrix m = Q y, float (mixed) or double
+  unsigned long long* ffc;  // diagnostic counter of float-float-delta blocks, or null
 };
 
 // lnL_p = sum_d [Re K_d U_d - Im K_d V_d - |K_d|^2 X_d / 2] - <h|h>/2 (FP64),
@@ -498,7 +499,7 @@ __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __rest
     const float* sa = smf + (int64_t)a.CH * a.row_elems;
     anchored_sums_cal<NDET, CAL>(smf, a.row_elems, sa, a.df, reinterpret_cast<const PropMixed*>(a.prop) + p, j0,
                                  jend, lane, U, V, smf + a.cal_smem, a.cal_row,
-                                 reinterpret_cast<const float4*>(nodes), X);
+                                 reinterpret_cast<const float4*>(nodes), X, a.ffc);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -797,12 +798,9 @@ int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
 
 template <int NDET, bool MIXED, bool CAL>
 static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, bool pdl, cudaStream_t st) {
-  static size_t smem_set = 0;  // per template instance: raise the dynamic shared-memory limit when it grows
-  if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_window<NDET, MIXED, CAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  {
+    const cudaError_t e = raise_smem_limit((const void*)k_window<NDET, MIXED, CAL>, c->device, smem);
     if (e != cudaSuccess) return e;
-    smem_set = smem;
   }
   ProfScope ps(c, GWL_KERNEL_BINS, st);
   cudaError_t e;
@@ -877,6 +875,7 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
   a.pdone = work + 1 + 2 * nw_max(c);
   a.lnl = lnl;
   a.status = c->d_status;
+  a.ffc = c->count_ff ? c->d_ffc : nullptr;
   // shared memory (elements): the window's rows, [mixed] its anchor rows, [calibration] its calibration rows
   int64_t elems = (int64_t)CH * a.row_elems;
   if (mixed) elems += (int64_t)((CH + kAnchor - 1) / kAnchor) * kAnchorRowFloats;

@@ -335,13 +335,7 @@ static cudaError_t multi_run(Multi* m, const double* theta, int64_t n_per, doubl
     rowmax = d.row_elems > rowmax ? d.row_elems : rowmax;
   }
   const size_t smem = (size_t)CHmax * rowmax * sizeof(Elem);
-  static size_t smem_set = 0;
-  if (smem > smem_set) {
-    if ((e = cudaFuncSetAttribute(k_mwindow<NDET, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      return e;
-    smem_set = smem;
-  }
+  if ((e = raise_smem_limit((const void*)k_mwindow<NDET, MIXED>, m->ctxs[0]->device, smem)) != cudaSuccess) return e;
   MultiArgs a;
   a.ev = m->d_ev;
   a.E = m->E;

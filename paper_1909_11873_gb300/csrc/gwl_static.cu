@@ -29,6 +29,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 
+// The array's device address on `dev` (current): looked up once and kept.
+cudaError_t lookup_scratch(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_scratch_addr[dev]) return cudaSuccess;
+  const cudaError_t e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_static_scratch);
+  if (e != cudaSuccess) g_scratch_addr[dev] = nullptr;
+  return e;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Bytes of the fixed array that a batch of B needs on this context.
@@ -43,6 +52,21 @@ size_t static_bytes_needed(const gwl_ctx* c, int64_t B) {
 }
 
 }  // namespace
+
+namespace gwl {
+// Set-up from gwl_create (device `dev` current): look the array's address up
+// afresh.  A cudaDeviceReset frees the array with everything else on the
+// device, and a context made afterwards must not see the address of the old
+// one; contexts made before the reset are invalid anyway.
+cudaError_t static_scratch_setup(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaSuccess;  // such devices are refused by the entry point
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_scratch_addr[dev] = nullptr;
+  }
+  return lookup_scratch(dev);
+}
+}  // namespace gwl
 
 extern "C" int gwl_loglike_static(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, void* stream) {
   if (!c) return gwl::set_error(GWL_ERR_ARG, "null context");
@@ -60,17 +84,14 @@ extern "C" int gwl_loglike_static(gwl_ctx* c, const double* theta_dev, int64_t B
                            (long long)need, (long long)GWL_STATIC_SCRATCH_BYTES);
   if (dev < 0 || dev >= kMaxDevices) return gwl::set_error(GWL_ERR_ARG, "device index %d unsupported", dev);
 
-  // One-time set-up per device: the device address of the fixed array.
+  // The device address of the fixed array (looked up by gwl_create on this
+  // device; looked up here only if that failed).
   void* base = nullptr;
   {
+    const cudaError_t e = lookup_scratch(dev);
+    if (e != cudaSuccess)
+      return gwl::set_error(GWL_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-      cudaError_t e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_static_scratch);
-      if (e != cudaSuccess) {
-        g_scratch_addr[dev] = nullptr;
-        return gwl::set_error(GWL_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      }
-    }
     base = g_scratch_addr[dev];
   }
 

@@ -872,12 +872,7 @@ cudaError_t launch_ns_round(gwl_ctx* c, const NsDev& s, uint64_t seed, int walk_
                   plnl, st);
   if (e != cudaSuccess) return e;
   const size_t csm = consume_smem_bytes(s.K, s.n_chains);
-  static size_t csm_set = 0;
-  if (csm > 48 * 1024 && csm > csm_set) {
-    e = cudaFuncSetAttribute(k_ns_consume, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
-    if (e != cudaSuccess) return e;
-    csm_set = csm;
-  }
+  if (csm > 48 * 1024 && (e = raise_smem_limit((const void*)k_ns_consume, c->device, csm)) != cudaSuccess) return e;
   k_ns_consume<<<1, 256, csm, st>>>(s);
   k_ns_stats<<<1, 256, 0, st>>>(s, walk_len, dlogz);
   c->launches += 2;
@@ -1234,3 +1229,31 @@ int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t s
 }
 
 }  // namespace gwl
+
+// ---------------------------------------------------------------- generator check
+namespace gwl {
+int set_error(int code, const char* fmt, ...);
+
+// One Philox4x32-10 block per record: in = [n][6] words (counter c0..c3, key
+// k0, k1), out = [n][4] words -- the device generator of the walks, exposed so
+// that it can be checked against the generator's published known answers.
+__global__ void k_philox_eval(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t* r = in + 6 * i;
+  const uint4 w = philox(make_uint4(r[0], r[1], r[2], r[3]), r[4], r[5]);
+  out[4 * i] = w.x;
+  out[4 * i + 1] = w.y;
+  out[4 * i + 2] = w.z;
+  out[4 * i + 3] = w.w;
+}
+}  // namespace gwl
+
+extern "C" int gwl_test_philox(const uint32_t* in_dev, int64_t n, uint32_t* out_dev, void* stream) {
+  if (n < 0 || (n > 0 && (!in_dev || !out_dev))) return gwl::set_error(GWL_ERR_ARG, "gwl_test_philox: bad arguments");
+  if (n == 0) return GWL_OK;
+  gwl::k_philox_eval<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in_dev, n, out_dev);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return gwl::set_error(GWL_ERR_CUDA, "gwl_test_philox: %s", cudaGetErrorString(e));
+  return GWL_OK;
+}

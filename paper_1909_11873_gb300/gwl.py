@@ -28,7 +28,8 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
            "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
            "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
-           "gwl_test_wait_timeout")
+           "gwl_test_wait_timeout", "gwl_test_philox",
+           "gwl_test_ffdelta_blocks")
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
@@ -100,6 +101,8 @@ def lib() -> C.CDLL:
         L.gwl_set_calibration.argtypes = [P, i32, P, d, d]
         L.gwl_ff_eval.argtypes = [P, i64, i32, P, P]
         L.gwl_test_wait_timeout.argtypes = [P, C.c_double, P]
+        L.gwl_test_philox.argtypes = [P, i64, P, P]
+        L.gwl_test_ffdelta_blocks.argtypes = [P, i32, C.POINTER(i64)]
         L.gwl_get_calibration.argtypes = [P, C.POINTER(i32), C.POINTER(i64)]
         L.gwl_set_walk.argtypes = [P, i32]
         L.gwl_profile.argtypes = [P, i32]
@@ -264,6 +267,12 @@ class Context:
     def gwl_test_wait_timeout(self, seconds: float, stream=None):
         _check(lib().gwl_test_wait_timeout(self._h, float(seconds), _stream(stream)), "gwl_test_wait_timeout")
 
+    def gwl_test_ffdelta_blocks(self, enable: int = -1) -> int:
+        """Blocks counted so far that took the float-float phase delta; then enable (1), stop (0) or keep (-1)."""
+        n = C.c_int64()
+        _check(lib().gwl_test_ffdelta_blocks(self._h, int(enable), C.byref(n)), "gwl_test_ffdelta_blocks")
+        return int(n.value)
+
     def gwl_set_walk(self, kind: int):
         _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
 
@@ -328,6 +337,16 @@ def ff_eval(x, fn, stream=None):
     out = torch.empty_like(x)
     _check(lib().gwl_ff_eval(_ptr(x), x.numel(), int(fn), _ptr(out), _stream(stream)), "gwl_ff_eval")
     return out
+
+
+def philox_eval(records, stream=None):
+    """The device Philox4x32-10 on an int64 CUDA tensor [n][6] of 32-bit words (counter c0..c3, key k0, k1);
+    returns the [n][4] output words (int64)."""
+    import torch
+    inp = records.to(torch.int32).contiguous()
+    out = torch.empty((inp.shape[0], 4), dtype=torch.int32, device=inp.device)
+    _check(lib().gwl_test_philox(_ptr(inp), inp.shape[0], _ptr(out), _stream(stream)), "gwl_test_philox")
+    return out.to(torch.int64) & 0xFFFFFFFF
 
 
 # ---- convenience wrappers used by tests and the benchmark (torch tensors in, torch tensors out)

@@ -25,6 +25,6 @@ def custom_event(cfg, seed, fcut_mode=0):
 
 
 def tol(precision, ref):
-    """|dlnL| bound: 1e-6 (FP64) / 1e-3 (mixed) absolute, relative beyond |lnL| = 1e4."""
+    """|dlnL| bound, absolute at every |lnL|: 1e-6 for the FP64 path, 1e-3 for the mixed paths."""
     base = 1e-6 if precision == 0 else 1e-3
-    return base * np.maximum(1.0, np.abs(ref) / 1e4)
+    return np.full(np.shape(ref), base)

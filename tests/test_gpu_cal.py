@@ -4,7 +4,7 @@ gwl_loglike through the C ABI) with the FP64 oracle's calibration model.
 The calibration model of Section 2.2 multiplies each detector's template by
 (1 + dA_d(f)) exp(i dphi_d(f)), natural cubic splines in ln f through per-node
 corrections.  Bars as for the plain likelihood: |dlnL| <= 1e-6 (GWL_FP64) and
-<= 1e-3 (GWL_MIXED), relative beyond |lnL| = 1e4.
+<= 1e-3 (GWL_MIXED), absolute at every |lnL|.
 """
 import numpy as np
 import pytest

@@ -27,6 +27,46 @@ def small_events():
     return evs
 
 
+def long_events():
+    """Config 4's longer segments: 32, 64 and 128 s at 20-1024 Hz (32,129 to 128,513 bins per detector), BBH
+    and BNS.  With 640-bin windows a BNS proposal spans up to ~200 windows, so the (event, window) task queue
+    and the cross-window combination carry most of the work; a BNS chirp in a 32 s segment moves several
+    cycles per bin, so its low-frequency blocks take the float-float phase delta."""
+    cfgs = [(32.0, "bns"), (64.0, "bbh"), (128.0, "bns"), (32.0, "bbh"), (64.0, "bns"), (128.0, "bbh")]
+    return [custom_event(dict(n_det=3, T=T, f_low=20.0, f_high=1024.0, noise=True, source=src, batch=64,
+                              gmst=1.7), 200 + i) for i, (T, src) in enumerate(cfgs)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_loglike_long_events(precision):
+    """Ragged multi-window proposals of 32-128 s events through gwl_multi_loglike: equal to the per-event
+    entry point and to the oracle on sampled rows; the float-float delta blocks ran (mixed)."""
+    from paper_1909_11873_gb300 import gwl
+    evs = long_events()
+    n = 160
+    ths = [I.proposals(ev, n, 31 + i) for i, ev in enumerate(evs)]
+    ctxs = [gwl.Context.from_event(ev, precision) for ev in evs]
+    mc = gwl.MultiContext(ctxs)
+    x = torch.from_numpy(np.concatenate([I.reduced(t, ev.sampling) for t, ev in zip(ths, evs)])).cuda()
+    out = torch.empty(x.shape[0], dtype=torch.float64, device="cuda")
+    mc.gwl_multi_loglike(x, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(len(evs), n)
+    ff = 0
+    for e, (ev, th, ctx) in enumerate(zip(evs, ths, ctxs)):
+        if precision == 1:
+            ctx.gwl_test_ffdelta_blocks(1)
+        single = gwl.loglike(ctx, torch.from_numpy(I.reduced(th, ev.sampling)).cuda()).cpu().numpy()
+        if precision == 1:
+            ff += ctx.gwl_test_ffdelta_blocks(0)
+        assert np.all(np.abs(got[e] - single) <= 0.1 * tol(precision, single)), e
+        idx = np.arange(0, n, 5)
+        ref = oracle.loglike(ev, th[idx])
+        assert np.all(np.abs(got[e, idx] - ref) <= tol(precision, ref)), (e, np.abs(got[e, idx] - ref).max())
+    if precision == 1:
+        assert ff > n, ff
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_multi_loglike_equals_single_and_oracle(precision):
     from paper_1909_11873_gb300 import gwl
@@ -74,5 +114,5 @@ def test_multi_ns_lnz_matches_oracle_per_event():
         o = oracle.ns_run(ev, ev.sampling, K, nch, wl, seed=4, dlogz=0.1)
         sig = math.hypot(r["lnZ_err"], o["lnZ_err"])
         assert np.isfinite(r["lnZ"]) and r["rounds"] > 3
-        assert abs(r["lnZ"] - o["lnZ"]) < 4 * sig + 0.2, (r, o)
+        assert abs(r["lnZ"] - o["lnZ"]) < 4 * sig, (r, o)
         assert r["consumed_per_round"] == pytest.approx(K * math.log(1 + nch / K), rel=0.12)

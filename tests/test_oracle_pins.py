@@ -391,6 +391,21 @@ def test_prior_transform_distributions(c2):
 
 
 # ---------------------------------------------------------------- random numbers
+def philox_kat():
+    """The published known-answer vectors of Philox4x32-10 (tests/golden/philox4x32_10_kat.json)."""
+    kat = json.load(open(os.path.join(HERE, "golden", "philox4x32_10_kat.json")))
+    return [([int(x, 16) for x in v["counter"]], [int(x, 16) for x in v["key"]], [int(x, 16) for x in v["output"]])
+            for v in kat["vectors"]]
+
+
+def test_philox_known_answers():
+    """The oracle's Philox4x32-10 reproduces the generator's published known-answer vectors (Salmon et
+    al. 2011): a swapped multiplier, a wrong key schedule or a permuted output word fails."""
+    for ctr, key, want in philox_kat():
+        got = [int(x) for x in oracle.philox(ctr, key)]
+        assert got == want, (ctr, key, [hex(x) for x in got])
+
+
 def test_philox_uniformity_and_counter_independence():
     """Philox4x32-10 words: uniform (chi^2 on 256 bins), distinct for neighbouring counters,
     and the Box-Muller normals of the walk stream are N(0,1) (KS)."""
