@@ -97,6 +97,8 @@ def parse():
                     help="run one workload --warmup + --steps times without timing and exit (for profiler captures): "
                          "lnl = the headline likelihood, grad = the 4096-proposal gradient, cal = the calibrated "
                          "likelihood, fp64ph = the FP64-phase mixed arm")
+    ap.add_argument("--bin-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="likelihood bin-loop layout for --shape / --profile-only runs (1 auto, 2 warp, 3 lane)")
     ap.add_argument("--shape", default="",
                     help="W,C: fixed likelihood launch shape (window bins, CTAs per SM) instead of the autotuner; "
                          "for profiler runs, whose timing would mislead the autotuner")
@@ -583,7 +585,7 @@ def run_gwl(args):
     ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
     if args.shape:
         w, c = (int(v) for v in args.shape.split(","))
-        ctx.gwl_set_tuning(window=w, ctas_per_sm=c)
+        ctx.gwl_set_tuning(window=w, ctas_per_sm=c, bin_kernel=args.bin_kernel)
         tuning = dict(ctx.gwl_get_tuning(), fixed=True)
     else:
         tuning = ctx.gwl_autotune(theta, gwl.GWL_TUNE_LOGLIKE, stream)
@@ -629,13 +631,15 @@ def run_gwl(args):
         "config": {"workload": "3-det BBH, 8 s, 20-1024 Hz, 8033 bins/det, 11-D, batch 8192 proposals per GPU",
                    "global_batch": BATCH * world, "in_band_pairs_per_batch": int(pairs), "precision": "mixed",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
-                   "window": tuning["window"], "ctas_per_sm": tuning["ctas_per_sm"]},
+                   "window": tuning["window"], "ctas_per_sm": tuning["ctas_per_sm"],
+                   "bin_kernel": {1: "auto", 2: "warp", 3: "lane"}.get(tuning.get("bin_kernel"), "?")},
         "e2e": {"value": whole_job_rate(BATCH, world, mse), "unit": "evals/s", "ms_per_call_host_clock": mse,
                 "device_events_value": whole_job_rate(BATCH, world, ms_host_dev),
                 "h2d_bytes_per_step": int(theta_np.nbytes), "d2h_bytes_per_step": int(BATCH * 8)},
         "roofline": {"bound": "alu", "pipe": bound, "achieved": b.get("achieved_T"), "peak": b.get("peak_T"),
                      "unit": "Top/s" if bound == "mufu" else "TFLOP/s", "frac": b["frac"], "traffic": traffic,
-                     "traffic_basis": traffic_basis, "kernel": "k_window<3,mixed>", "kernel_ms": bins_ms,
+                     "traffic_basis": traffic_basis,
+                     "kernel": "k_lanes<3>" if tuning.get("bin_kernel") == 3 else "k_window<3,mixed>", "kernel_ms": bins_ms,
                      "pairs_per_launch": int(pairs), "share_of_step": bins_ms / ms,
                      "pipes": r4({k: {"per": v.get("per_pair", v.get("per_eval_bytes")), "frac": v["frac"]}
                                   for k, v in pipes.items()}),
@@ -669,14 +673,51 @@ def run_gwl(args):
         legres["c5_ess"] = leg_c5(ev, args)
     if "c4" in legs:
         legres["c4"] = leg_c4(args, flush, stream)
-    if legres:
-        out["legs"] = r4(legres)
-    if "cpu_baseline" in out and "checks" in out["cpu_baseline"]:
-        out["oracle_checks"] = r4(out["cpu_baseline"].pop("checks"))
+    checks = out["cpu_baseline"].pop("checks") if "cpu_baseline" in out else None
+    if legres or checks:
+        # last in the line and compact, so that a reader keeping only the line's tail still has them
+        out["legs"] = compact_legs(legres, checks)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def compact_legs(legres, checks):
+    """The extra measurements in a short form (four significant digits; key legend in the design doc)."""
+    L = {}
+    g = legres.get
+    if g("fp64_c2"):
+        L["fp64_c2"] = [g("fp64_c2")["v"], g("fp64_c2")["mixed_x"]]
+    if g("fp64ph_c2"):
+        L["fp64ph_c2"] = [g("fp64ph_c2")["v"], g("fp64ph_c2")["mixed_x"]]
+    if g("grad_c5"):
+        L["grad_c5"] = [g("grad_c5")["v"], g("grad_c5")["kernel_ms"], g("grad_c5")["frac"]]
+    if g("cal_c2"):
+        L["cal_c2"] = [g("cal_c2")["v"], g("cal_c2")["kernel_ms"], g("cal_c2")["frac"]]
+    for k in ("c1", "c3"):
+        if g(k):
+            L[k] = [g(k)["mixed"], g(k)["fp64"]]
+    if g("ns_c1"):
+        n = g("ns_c1")
+        L["ns_c1"] = [n["wall_s"], n["lnZ"], n["lnZ_err"], n["consumed"] / n["eq5"]]
+    if g("eq5"):
+        L["eq5"] = [[r[0], r[1], r[3]] for r in g("eq5")["rows"]]
+    if g("c5_ess"):
+        L["c5"] = {d: {w: [v["ess_s"], v["lnZ"], v["spread"]] for w, v in row.items()} for d, row in g("c5_ess").items()}
+    if g("c4"):
+        c = g("c4")
+        L["c4"] = [c["lnl_x"], c["ns_graph_s"], c["ns_per_event_s"], c["rounds"], c["lnZ_graph_vs_per_event_max_sigma"]]
+    if checks:
+        for k in ("c1", "c2", "c3", "fp64ph_c2"):
+            if k in checks:
+                L["err_" + k] = [checks[k]["fp64"], checks[k]["mixed"], checks[k]["rows"]]
+        if "ns_c1_oracle" in checks:
+            o = checks["ns_c1_oracle"]
+            L["ns_c1_orc"] = [o["wall_s"], o["lnZ"]]
+        if "c4_lnZ" in checks:
+            L["c4_lnZ"] = [[r["T"], r["dev"], r["orc"], r["sigma"]] for r in checks["c4_lnZ"]]
+    return r4(L)
 
 
 # ---------------------------------------------------------------- oracle (host cores): baseline and checks
@@ -822,7 +863,7 @@ def run_profile_only(args):
     if args.shape:
         w, c = (int(v) for v in args.shape.split(","))
         ctx.gwl_set_tuning(window=w if args.profile_only != "grad" else 0, ctas_per_sm=c,
-                           grad_window=w if args.profile_only == "grad" else 0)
+                           grad_window=w if args.profile_only == "grad" else 0, bin_kernel=args.bin_kernel)
     x = torch.from_numpy(np.ascontiguousarray(rows)).cuda()
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     g = torch.empty_like(x)

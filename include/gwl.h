@@ -376,12 +376,35 @@ typedef struct gwl_tuning {
                         (ms) at the tuned batch; gwl_get_tuning: last tuned value or 0 */
   double ms_grad;    /* same for gwl_grad */
   int n_tried;       /* gwl_autotune output: launch shapes timed */
+  int bin_kernel;    /* likelihood bin loop layout, GWL_BINS_*; 0 keeps (set) */
+  int lane_chunk;    /* GWL_BINS_LANE: bins per chunk (a multiple of 32 dividing the
+                        window; chunks of one window on segments whose per-chunk sums
+                        would exceed 64 MB); 0 keeps (set) */
 } gwl_tuning;
 
+/* Layouts of the likelihood bin loop (gwl_tuning.bin_kernel).  Both compute
+ * the same sums (the anchored phase of the mixed path); they differ in the
+ * order in which the FP32 terms are added, within the parity tolerances.
+ *   WARP: one proposal per warp, its lanes striding over the bins of a
+ *         window (every precision, the calibration model, any batch).
+ *   LANE: one proposal per lane, the 32 lanes of a warp walking the same bins
+ *         together; proposals are grouped by their cut (the prologue files
+ *         them in buckets of their last chunk of 64 bins, or of one window on
+ *         long segments) and chunks of several proposals' sums are added in
+ *         FP64 in chunk order.  Mixed precision without the calibration
+ *         model; segments of at most 2048 chunks.  Elsewhere WARP runs.
+ *   AUTO: LANE for mixed batches of 2048 proposals or more where it is
+ *         available, WARP otherwise (the default). */
+#define GWL_BINS_AUTO 1
+#define GWL_BINS_WARP 2
+#define GWL_BINS_LANE 3
+
 /* Set the launch shape (fields as above; the ms/n_tried fields are ignored).
- * Windows are multiples of 32 bins.  A window that is not, or whose rows
- * exceed 200 KB of shared memory, a negative value or a ctas_per_sm above 16
- * returns GWL_ERR_ARG and changes nothing. */
+ * Windows and lane chunks are multiples of 32 bins.  A window or chunk that
+ * is not, a window whose rows exceed 200 KB of shared memory, a negative
+ * value, a ctas_per_sm above 16 or a bin_kernel outside 0..3 returns
+ * GWL_ERR_ARG and changes nothing.  A chunk that does not divide the window
+ * falls back to chunks of one window. */
 int gwl_set_tuning(gwl_ctx* ctx, const gwl_tuning* t);
 
 /* Read the context's current launch shape into *out. */
@@ -392,7 +415,9 @@ int gwl_get_tuning(const gwl_ctx* ctx, gwl_tuning* out);
 
 /* Autotuner: times gwl_loglike (what & GWL_TUNE_LOGLIKE) over every window in
  * {128, 192, ..., 1536} bins that fits in shared memory (at most the segment),
- * and every ctas_per_sm in {1, 2, 3, 4}, and gwl_grad
+ * every ctas_per_sm in {1, 2, 3, 4} and both bin-loop layouts (GWL_BINS_WARP,
+ * and GWL_BINS_LANE with chunks of 32 and 64 bins where it is available),
+ * and gwl_grad
  * (what & GWL_TUNE_GRAD) over the same windows, on the caller's batch
  * theta_dev (B x n_dim, device, row-major, read only) on `stream`, and keeps
  * the fastest shape of each in the context.  Each shape is timed with CUDA

@@ -74,6 +74,14 @@ int ensure_scratch(gwl_ctx* c, int64_t B) {
     if ((e = dev_alloc(c, &c->d_work, wneed)) != cudaSuccess) return cuda_fail(e, "scratch");
     c->work_cap = wneed;
   }
+  const int64_t lneed = gwl::lanes_list_ints(c, B);
+  if (lneed > c->blist_cap) {
+    int64_t cap = lneed > 2 * c->blist_cap ? lneed : 2 * c->blist_cap;
+    dev_free(c, c->d_blist, c->blist_cap);
+    c->blist_cap = 0;
+    if ((e = dev_alloc(c, &c->d_blist, cap)) != cudaSuccess) return cuda_fail(e, "scratch");
+    c->blist_cap = cap;
+  }
   const int64_t need = gwl::partials_needed(c, B);
   if (need > c->partials_cap) {
     int64_t cap = need > 2 * c->partials_cap ? need : 2 * c->partials_cap;
@@ -656,8 +664,10 @@ int gwl_set_walk(gwl_ctx* c, int walk_kind) {
 
 int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
   if (!c || !t) return fail(GWL_ERR_ARG, "null argument");
-  if (t->window < 0 || t->grad_window < 0 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16)
+  if (t->window < 0 || t->grad_window < 0 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16 || t->bin_kernel < 0 ||
+      t->bin_kernel > GWL_BINS_LANE)
     return fail(GWL_ERR_ARG, "bad tuning value");
+  if (t->lane_chunk < 0 || t->lane_chunk % 32) return fail(GWL_ERR_ARG, "lane_chunk must be a multiple of 32");
   if (t->window % 32 || t->grad_window % 32)
     return fail(GWL_ERR_ARG, "windows must be multiples of 32 bins (got %d/%d)", t->window, t->grad_window);
   // likelihood rows: the delta table (mixed) or the FP64 table; gradient rows: the mixed or FP64 table
@@ -669,6 +679,8 @@ int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
   if (t->window) c->window = t->window;
   if (t->grad_window) c->grad_window = t->grad_window;
   if (t->ctas_per_sm) c->ctas_per_sm = t->ctas_per_sm;
+  if (t->bin_kernel) c->bin_kernel = t->bin_kernel;
+  if (t->lane_chunk) c->lane_chunk = t->lane_chunk;
   return GWL_OK;
 }
 
@@ -680,6 +692,8 @@ int gwl_get_tuning(const gwl_ctx* c, gwl_tuning* out) {
   out->ms_loglike = c->tuned_ms[0];
   out->ms_grad = c->tuned_ms[1];
   out->n_tried = c->tuned_n;
+  out->bin_kernel = c->bin_kernel;
+  out->lane_chunk = c->lane_chunk;
   return GWL_OK;
 }
 
@@ -810,6 +824,7 @@ void gwl_destroy(gwl_ctx* c) {
   dev_free(c, c->d_partials, c->partials_cap);
   dev_free(c, c->d_io, c->io_cap);
   dev_free(c, c->d_work, c->work_cap);
+  dev_free(c, c->d_blist, c->blist_cap);
   dev_free(c, c->d_status, 4);
   dev_free(c, c->d_ffc, 1);
   if (c->d_pgrad) cudaFree(c->d_pgrad);

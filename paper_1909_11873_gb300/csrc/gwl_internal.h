@@ -57,6 +57,8 @@ struct gwl_ctx {
   int64_t pgrad_cap = 0;         // in bytes
   void* d_gpartials = nullptr;   // per-window sums of the gradient bin loop
   int64_t gpartials_cap = 0;     // in bytes
+  int* d_blist = nullptr;        // lane bin loop: bucket lists of proposals [chunks][B]
+  int64_t blist_cap = 0;         // in ints
   int* d_work = nullptr;         // [0] largest cut of the batch, [1 + w] proposal counter of window w
   int64_t work_cap = 0;          // in ints
   int* d_status = nullptr;       // [0] latched status bits
@@ -68,6 +70,8 @@ struct gwl_ctx {
   int window = 0;       // likelihood bin loop: bins per staged window
   int grad_window = 0;  // gradient bin loop: bins per staged window
   int ctas_per_sm = 3;  // likelihood bin loop grid: CTAs per SM
+  int bin_kernel = GWL_BINS_AUTO;  // likelihood bin loop layout
+  int lane_chunk = 64;             // lane bin loop: bins per chunk
   double tuned_ms[2] = {0.0, 0.0};  // autotuner: best gwl_loglike / gwl_grad time (ms)
   int tuned_n = 0;                  // autotuner: shapes timed
 
@@ -127,6 +131,12 @@ cudaError_t launch_cal_tables(gwl_ctx* c, const double* d_xnode, cudaStream_t st
 
 // a2-a6: batched log-likelihood
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st);
+// the lane-per-proposal bin loop (gwl_lanes.cu): chunk size (0: not used), scratch sizes, launch
+int lanes_seg(const gwl_ctx* c, int64_t B);
+int64_t lanes_list_ints(const gwl_ctx* c, int64_t B);
+int64_t lanes_slot_floats(const gwl_ctx* c, int64_t B);
+cudaError_t launch_lanes(gwl_ctx* c, int64_t B, double* lnl, int* work, int* hist, int* pdone, int* bcount, int seg,
+                         cudaStream_t st);
 
 // a8: log-likelihood and gradient
 cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st);

@@ -231,7 +231,7 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
                                                  int64_t row0, int role, int lane, ProSmemFF& sm,
                                                  PropMixed* __restrict__ pm, PropCommon* __restrict__ pc,
                                                  int* __restrict__ work, int* __restrict__ hist, int CH,
-                                                 double* __restrict__ lnl) {
+                                                 double* __restrict__ lnl, const Buckets& bk) {
   const int64_t p = row0 + lane;
   const bool valid = p < B;
   double th[11];
@@ -376,6 +376,7 @@ __device__ __forceinline__ void prologue_rows_ff(const SegInfo& s, const double*
     for (int off = 16; off > 0; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
     if (lane == 0 && nm > 0) atomicMax(&work[0], nm);
     hist_last_window(valid ? ncut : 0, CH, hist);
+    if (bk.count) bucket_push(valid ? ncut : 0, p, bk, B);
   }
 }
 
@@ -383,13 +384,14 @@ template <bool MIXED>
 __global__ void __launch_bounds__(128) k_prologue(SegInfo s, const double* __restrict__ theta, int64_t B,
                                                   PropMixed* __restrict__ pm, PropF64* __restrict__ pf,
                                                   PropCommon* __restrict__ pc, int* __restrict__ work,
-                                                  int* __restrict__ hist, int CH, double* __restrict__ lnl) {
+                                                  int* __restrict__ hist, int CH, double* __restrict__ lnl,
+                                                  Buckets bk) {
   // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
   cudaTriggerProgrammaticLaunchCompletion();
   if constexpr (MIXED) {
     __shared__ ProSmemFF sm;
     prologue_rows_ff(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, pm, pc, work,
-                     hist, CH, lnl);
+                     hist, CH, lnl, bk);
   } else {
     __shared__ ProSmem sm;
     prologue_rows(s, theta, B, (int64_t)blockIdx.x * 32, threadIdx.x >> 5, threadIdx.x & 31, sm, CtaSync(), pf, pc,
@@ -778,10 +780,14 @@ static int window_of(const gwl_ctx* c, int precision) {
   return c->window > c->M ? (int)c->M : c->window;
 }
 
+// Partial sums of either bin loop (in doubles): per (proposal, window) of the
+// warp kernel, per (proposal, chunk) of the lane kernel (floats).
 int64_t partials_needed(const gwl_ctx* c, int64_t B) {
   const int CH = window_of(c, c->opt.precision);
   const int64_t nw = (c->M + CH - 1) / CH;
-  return B * nw * sums_per_det(c) * c->n_det;
+  const int64_t warp = B * nw * sums_per_det(c) * c->n_det;
+  const int64_t lane = (lanes_slot_floats(c, B) + 1) / 2;
+  return warp > lane ? warp : lane;
 }
 
 // Windows of the likelihood or the gradient bin loop, whichever has more.
@@ -791,9 +797,11 @@ static int64_t nw_max(const gwl_ctx* c) {
   if (CHg < CH) CH = CHg;
   return (c->M + CH - 1) / CH;
 }
-// [0] largest cut, [1 + w] proposal counter of window w, [1 + nw_max + w]
-// histogram of last windows, [1 + 2 nw_max + p] windows of proposal p summed.
-int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + B; }
+// [0] largest cut, [1 + w] proposal (or item) counter of window w,
+// [1 + nw_max + w] histogram of last windows, [1 + 2 nw_max + p] windows (or
+// chunks) of proposal p summed, [1 + 2 nw_max + B + K] bucket counts of the
+// lane kernel (chunks of at least 32 bins).
+int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + B + (c->M + 31) / 32; }
 int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
 
 template <int NDET, bool MIXED, bool CAL>
@@ -833,7 +841,7 @@ static cudaError_t launch_clear_work(gwl_ctx* c, int* work, int64_t n, cudaStrea
 // `off`, with `work` the counter region (cleared just before, by a memset or
 // k_clear_work; launched as a programmatic dependent of the latter).
 static cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int64_t off, int precision,
-                                   double* lnl, int* work, cudaStream_t st) {
+                                   double* lnl, int* work, cudaStream_t st, Buckets bk = Buckets{nullptr, nullptr, 32}) {
   ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
   const unsigned nb = (unsigned)((B + 31) / 32);
   int* hist = work + 1 + nw_max(c);
@@ -841,10 +849,10 @@ static cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, i
   cudaError_t e;
   if (precision == GWL_MIXED)
     e = launch_pdl(k_prologue<true>, dim3(nb), dim3(128), 0, st, c->seg, theta, B, c->d_pm + off, c->d_pf + off,
-                   c->d_pc + off, work, hist, CH, lnl);
+                   c->d_pc + off, work, hist, CH, lnl, bk);
   else
     e = launch_pdl(k_prologue<false>, dim3(nb), dim3(128), 0, st, c->seg, theta, B, c->d_pm + off, c->d_pf + off,
-                   c->d_pc + off, work, hist, CH, lnl);
+                   c->d_pc + off, work, hist, CH, lnl, bk);
   c->launches++;
   return e;
 }
@@ -909,12 +917,19 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
 // Prologue (per-proposal coefficients, FP64) then the windowed bin loop, which
 // also forms lnL (programmatic dependent launch: its CTAs start while the
 // prologue drains and wait for its results).
+// With the lane kernel the prologue also files every proposal in the bucket
+// of its last chunk.
 template <int NDET>
 static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
+  const int seg = lanes_seg(c, B);
+  int* pdone = c->d_work + 1 + 2 * nw_max(c);
+  int* bcount = pdone + B;
+  const Buckets bk = seg ? Buckets{bcount, c->d_blist, seg} : Buckets{nullptr, nullptr, 32};
   cudaError_t e = launch_clear_work(c, c->d_work, work_needed(c, B), st);
-  if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st);
-  if (e == cudaSuccess) e = launch_bins<NDET>(c, theta, B, 0, lnl, c->d_work, true, st);
-  return e;
+  if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st, bk);
+  if (e != cudaSuccess) return e;
+  if (seg) return launch_lanes(c, B, lnl, c->d_work, c->d_work + 1 + nw_max(c), pdone, bcount, seg, st);
+  return launch_bins<NDET>(c, theta, B, 0, lnl, c->d_work, true, st);
 }
 
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {

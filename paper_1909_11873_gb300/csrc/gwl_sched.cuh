@@ -27,6 +27,30 @@ __device__ __forceinline__ void hist_last_window(int ncut, int CH, int* __restri
   if (L >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[L], __popc(peers));
 }
 
+// Bucket lists of the lane-per-proposal bin loop (gwl_lanes.cu): proposal p
+// with ncut > 0 goes to bucket K = (ncut - 1) / seg, the index of its last
+// chunk of seg bins, at a slot taken with one atomic per distinct bucket in
+// the warp: list[K * B + slot] = p.  The bin loop reads the buckets in
+// descending K, so the proposals active in chunk c (those with K >= c) are a
+// prefix of that order and neighbours in it have similar cuts.  All 32 lanes
+// must call it; ncut <= 0 marks a lane without an in-band proposal.
+struct Buckets {
+  int* count;  // [ceil(M / seg)] proposals per bucket (cleared before the prologue); null: no buckets
+  int* list;   // [ceil(M / seg)][B] proposal indices
+  int seg;     // bins per chunk (a multiple of 32)
+};
+
+__device__ __forceinline__ void bucket_push(int ncut, int64_t p, const Buckets& bk, int64_t B) {
+  const int K = ncut > 0 ? (ncut - 1) / bk.seg : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, K);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (K >= 0 && lane == leader) base = atomicAdd(&bk.count[K], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (K >= 0) bk.list[(int64_t)K * B + base + __popc(peers & ((1u << lane) - 1u))] = (int)p;
+}
+
 // CTA-level (256 threads, called by all): the window in [w_lo, nw) in which
 // CTA b of G starts, and (*n_start) the proposals active in it.  Returns nw
 // when no proposal is active in [w_lo, nw).  In units of CH / 2 bins, the

@@ -48,6 +48,7 @@ size_t static_bytes_needed(const gwl_ctx* c, int64_t B) {
   n += align256(sizeof(gwl::PropCommon) * (size_t)B);
   n += align256(sizeof(double) * (size_t)gwl::partials_needed(c, B));
   n += align256(sizeof(int) * (size_t)gwl::work_needed(c, B));
+  n += align256(sizeof(int) * (size_t)gwl::lanes_list_ints(c, B));
   return n;
 }
 
@@ -106,18 +107,22 @@ extern "C" int gwl_loglike_static(gwl_ctx* c, const double* theta_dev, int64_t B
   double* partials = reinterpret_cast<double*>(p);
   p += align256(sizeof(double) * (size_t)gwl::partials_needed(c, B));
   int* work = reinterpret_cast<int*>(p);
+  p += align256(sizeof(int) * (size_t)gwl::work_needed(c, B));
+  int* blist = reinterpret_cast<int*>(p);
 
   gwl::PropMixed* s_pm = c->d_pm;
   gwl::PropF64* s_pf = c->d_pf;
   gwl::PropCommon* s_pc = c->d_pc;
   double* s_part = c->d_partials;
   int* s_work = c->d_work;
+  int* s_blist = c->d_blist;
   const bool s_prof = c->profiling;
   c->d_pm = pm;
   c->d_pf = pf;
   c->d_pc = pc;
   c->d_partials = partials;
   c->d_work = work;
+  c->d_blist = blist;
   c->profiling = false;  // event pairs are created on demand; keep this call free of any allocation
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
@@ -127,6 +132,7 @@ extern "C" int gwl_loglike_static(gwl_ctx* c, const double* theta_dev, int64_t B
   c->d_pc = s_pc;
   c->d_partials = s_part;
   c->d_work = s_work;
+  c->d_blist = s_blist;
   c->profiling = s_prof;
   if (e != cudaSuccess) return gwl::set_error(GWL_ERR_CUDA, "gwl_loglike_static: %s", cudaGetErrorString(e));
   return GWL_OK;

@@ -104,22 +104,36 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
   double best_l = 1e30, best_g = 1e30;
   int tried = 0;
   if (what & GWL_TUNE_LOGLIKE) {
-    for (int ctas = 1; ctas <= 4 && !rc; ++ctas)
-      for (int w : windows) {
-        gwl_tuning s = saved;
-        s.window = w;
-        s.ctas_per_sm = ctas;
-        if ((rc = gwl_set_tuning(c, &s))) break;
-        double ms = 0.0;
-        rc = time_calls(t, st, [&] { return gwl_loglike(c, theta_dev, B, d_out, stream); }, &ms);
-        if (rc) break;
-        ++tried;
-        if (ms < best_l) {
-          best_l = ms;
-          best.window = w;
-          best.ctas_per_sm = ctas;
+    // (layout, lane chunk): the warp layout, then the lane layout with 32- and 64-bin chunks
+    const int variants[3][2] = {{GWL_BINS_WARP, 64}, {GWL_BINS_LANE, 32}, {GWL_BINS_LANE, 64}};
+    for (const auto& var : variants) {
+      if (rc) break;
+      for (int ctas = 1; ctas <= 4 && !rc; ++ctas)
+        for (int w : windows) {
+          gwl_tuning s = saved;
+          s.window = w;
+          s.ctas_per_sm = ctas;
+          s.bin_kernel = var[0];
+          s.lane_chunk = var[1];
+          if ((rc = gwl_set_tuning(c, &s))) break;
+          // the lane layout where it is available, with this chunk (not its whole-window fallback)
+          if (var[0] == GWL_BINS_LANE) {
+            const int seg = gwl::lanes_seg(c, B);
+            if (seg == 0 || (seg != var[1] && var[1] != 64)) continue;
+          }
+          double ms = 0.0;
+          rc = time_calls(t, st, [&] { return gwl_loglike(c, theta_dev, B, d_out, stream); }, &ms);
+          if (rc) break;
+          ++tried;
+          if (ms < best_l) {
+            best_l = ms;
+            best.window = w;
+            best.ctas_per_sm = ctas;
+            best.bin_kernel = var[0];
+            best.lane_chunk = var[1];
+          }
         }
-      }
+    }
   }
   if (!rc && (what & GWL_TUNE_GRAD)) {
     for (int w : gwindows) {

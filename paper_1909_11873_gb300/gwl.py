@@ -35,6 +35,7 @@ GWL_WALK_GALILEAN = 1
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
 GWL_TUNE_LOGLIKE = 1
 GWL_TUNE_GRAD = 2
+GWL_BINS_AUTO, GWL_BINS_WARP, GWL_BINS_LANE = 1, 2, 3
 
 
 class GwlDetector(C.Structure):
@@ -65,7 +66,8 @@ class GwlNsResult(C.Structure):
 
 class GwlTuning(C.Structure):
     _fields_ = [("window", C.c_int), ("ctas_per_sm", C.c_int), ("grad_window", C.c_int),
-                ("ms_loglike", C.c_double), ("ms_grad", C.c_double), ("n_tried", C.c_int)]
+                ("ms_loglike", C.c_double), ("ms_grad", C.c_double), ("n_tried", C.c_int), ("bin_kernel", C.c_int),
+                ("lane_chunk", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -276,8 +278,8 @@ class Context:
     def gwl_set_walk(self, kind: int):
         _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
 
-    def gwl_set_tuning(self, window=0, ctas_per_sm=0, grad_window=0):
-        t = GwlTuning(int(window), int(ctas_per_sm), int(grad_window), 0.0, 0.0, 0)
+    def gwl_set_tuning(self, window=0, ctas_per_sm=0, grad_window=0, bin_kernel=0, lane_chunk=0):
+        t = GwlTuning(int(window), int(ctas_per_sm), int(grad_window), 0.0, 0.0, 0, int(bin_kernel), int(lane_chunk))
         _check(lib().gwl_set_tuning(self._h, C.byref(t)), "gwl_set_tuning")
 
     def gwl_get_tuning(self) -> dict:

@@ -57,12 +57,13 @@ def test_c1_full_batch(precision):
     assert np.all(np.abs(got - ref) <= tol(precision, ref)), report(got, ref, precision)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_c2_full_batch_sampled(precision):
-    """8192 proposals (half prior draws, half near the injection) on the device; 384 rows checked."""
+@pytest.mark.parametrize("precision,bin_kernel", [(0, 1), (1, 2), (1, 3)])
+def test_c2_full_batch_sampled(precision, bin_kernel):
+    """8192 proposals (half prior draws, half near the injection) on the device; 384 rows checked; the mixed
+    path with both bin-loop layouts (one proposal per warp, one per lane)."""
     ev = event("c2")
     th = I.proposals(ev, 8192, 2)
-    got = run_gpu(ev, th, precision)
+    got = run_gpu(ev, th, precision, bin_kernel=bin_kernel)
     idx = np.random.default_rng(0).choice(th.shape[0], 384, replace=False)
     ref = oracle.loglike(ev, th[idx])
     assert np.all(np.abs(got[idx] - ref) <= tol(precision, ref)), report(got[idx], ref, precision)
@@ -90,16 +91,17 @@ def test_c3_long_segment_sampled(precision):
     assert np.all(np.abs(got[idx] - ref) <= tol(precision, ref)), report(got[idx], ref, precision)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision,bin_kernel", [(0, 1), (1, 2), (1, 3)])
 @pytest.mark.parametrize("fcut_mode", [0, 1])
-def test_several_windows_and_ragged_tails(precision, fcut_mode):
-    """3001 bins in windows of 992, 512 and 128 bins, 333 proposals (ragged everywhere)."""
+def test_several_windows_and_ragged_tails(precision, bin_kernel, fcut_mode):
+    """3001 bins in windows of 992, 512 and 128 bins, 333 proposals (ragged everywhere); the mixed path with
+    both bin-loop layouts (with one proposal per lane: chunks of one window at 992 bins, of 64 bins below)."""
     cfg = dict(n_det=3, T=8.0, f_low=20.0, f_high=395.0, noise=True, source="bbh", batch=333, gmst=0.9)
     ev = custom_event(cfg, 5, fcut_mode=fcut_mode)
     th = I.proposals(ev, 333, 5)
     ref = oracle.loglike(ev, th)
     for window, ctas in ((992, 3), (512, 2), (128, 4)):
-        got = run_gpu(ev, th, precision, window=window, ctas_per_sm=ctas)
+        got = run_gpu(ev, th, precision, window=window, ctas_per_sm=ctas, bin_kernel=bin_kernel)
         assert np.all(np.abs(got - ref) <= tol(precision, ref)), report(got, ref, precision)
 
 
@@ -155,12 +157,15 @@ def test_cut_next_to_bin_frequencies(precision):
     assert np.all(step > 100 * tol(precision, ref.reshape(4, 4)[:, 1])), step
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_deterministic_and_host_entry(precision):
+@pytest.mark.parametrize("precision,bin_kernel", [(0, 1), (1, 2), (1, 3)])
+def test_deterministic_and_host_entry(precision, bin_kernel):
+    """Repeated calls are bit-identical: with one proposal per lane the bucket order (and so which
+    proposals share a warp) changes from call to call, but every proposal's own arithmetic does not."""
     ev = event("c2")
     th = I.proposals(ev, 3000, 9)
     g = gwl()
     ctx = g.Context.from_event(ev, precision)
+    ctx.gwl_set_tuning(bin_kernel=bin_kernel)
     a = run_gpu(ev, th, precision, ctx=ctx)
     b = run_gpu(ev, th, precision, ctx=ctx)
     assert np.array_equal(a, b)

@@ -35,6 +35,7 @@ def test_autotune_keeps_parity(precision):
     assert t["window"] % 64 == 0 and 128 <= t["window"] <= 1536
     assert t["grad_window"] % 64 == 0 and 128 <= t["grad_window"] <= 1536
     assert 1 <= t["ctas_per_sm"] <= 4
+    assert t["bin_kernel"] in ((gwl.GWL_BINS_WARP, gwl.GWL_BINS_LANE) if precision else (gwl.GWL_BINS_WARP,))
     assert t["ms_loglike"] > 0 and t["ms_grad"] > 0 and t["n_tried"] > 8
     assert ctx.gwl_get_tuning() == t
     idx = np.random.default_rng(3).choice(th.shape[0], 128, replace=False)
@@ -60,7 +61,8 @@ def test_autotune_short_segment_and_bad_shapes():
     ref = oracle.loglike(ev, th)
     assert np.all(np.abs(gwl.loglike(ctx, d).cpu().numpy() - ref) <= tol(1, ref))
     before = ctx.gwl_get_tuning()
-    for bad in (dict(window=100000), dict(window=1000), dict(ctas_per_sm=99), dict(grad_window=-1)):
+    for bad in (dict(window=100000), dict(window=1000), dict(ctas_per_sm=99), dict(grad_window=-1),
+                dict(bin_kernel=4), dict(bin_kernel=-1)):
         with pytest.raises(gwl.GwlError):
             ctx.gwl_set_tuning(**bad)
     assert ctx.gwl_get_tuning() == before
