@@ -375,7 +375,7 @@ def lnl_rates(ev, B, seed, args, flush, stream, precisions, local_fraction=0.5, 
     res = {}
     for name, prec in precisions:
         ctx = gwl.Context.from_event(ev, prec)
-        if tune and prec == gwl.GWL_MIXED:
+        if tune and prec != gwl.GWL_FP64:
             ctx.gwl_autotune(x, gwl.GWL_TUNE_LOGLIKE, stream)
         ctx.gwl_loglike(x, out, stream)
         torch.cuda.synchronize()
@@ -656,6 +656,9 @@ def run_gwl(args):
     if "fp64" in legs:
         r = lnl_rates(ev, BATCH, rank_seed(rank), args, flush, stream, (("fp64", gwl.GWL_FP64),))
         legres["fp64_c2"] = {"v": r["fp64"], "mixed_x": value / r["fp64"]}
+    if "fp64ph" in legs:
+        r = lnl_rates(ev, BATCH, rank_seed(rank), args, flush, stream, (("f64ph", gwl.GWL_MIXED_F64PHASE),))
+        legres["fp64ph_c2"] = {"v": r["f64ph"], "mixed_x": value / r["f64ph"]}
     if "grad" in legs:
         legres["grad_c5"] = leg_grad(ev, args, flush, stream, n_sm, fclk)
     if "cal" in legs:
@@ -709,9 +712,9 @@ def compact_legs(legres, checks):
         c = g("c4")
         L["c4"] = [c["lnl_x"], c["ns_graph_s"], c["ns_per_event_s"], c["rounds"], c["lnZ_graph_vs_per_event_max_sigma"]]
     if checks:
-        for k in ("c1", "c2", "c3", "fp64ph_c2"):
+        for k in ("c1", "c2", "c3"):
             if k in checks:
-                L["err_" + k] = [checks[k]["fp64"], checks[k]["mixed"], checks[k]["rows"]]
+                L["err_" + k] = [checks[k]["fp64"], checks[k]["mixed"], checks[k]["f64ph"], checks[k]["rows"]]
         if "ns_c1_oracle" in checks:
             o = checks["ns_c1_oracle"]
             L["ns_c1_orc"] = [o["wall_s"], o["lnZ"]]
@@ -741,7 +744,7 @@ def max_err(ev, theta_full, ref):
 
     x = torch.from_numpy(np.ascontiguousarray(I.reduced(theta_full, ev.sampling))).cuda()
     out = {"rows": int(theta_full.shape[0])}
-    for name, prec in (("fp64", gwl.GWL_FP64), ("mixed", gwl.GWL_MIXED)):
+    for name, prec in (("fp64", gwl.GWL_FP64), ("mixed", gwl.GWL_MIXED), ("f64ph", gwl.GWL_MIXED_F64PHASE)):
         ctx = gwl.Context.from_event(ev, prec)
         got = gwl.loglike(ctx, x).cpu().numpy()
         ctx.gwl_sync()

@@ -55,6 +55,14 @@ extern "C" {
 #define GWL_FP64 0  /* plain FP64: phase, sincos and sums in double precision */
 #define GWL_MIXED 1 /* float-float phase, exact mod-1 reduction, FP32 sincos and
                        sums, FP64 combination */
+#define GWL_MIXED_F64PHASE 2 /* the phase in FP64 per bin and detector, reduced
+                       exactly modulo one cycle in FP64, then FP32 sincos and FP32
+                       sums, FP64 combination: the split without the float-float
+                       anchors of GWL_MIXED, for comparison.  Likelihood only
+                       (gwl_loglike, gwl_loglike_host, gwl_loglike_static, and the
+                       random walks of ns_replace / ns_run); gwl_grad, the Galilean
+                       walk, the calibration model and multi-event batches refuse it
+                       with GWL_ERR_ARG. */
 
 #define GWL_FCUT_ISCO 0 /* h = 0 above f_ISCO = 1/(6^{3/2} pi M) */
 #define GWL_FCUT_BAND 1 /* template continued to the top of the band */
@@ -84,7 +92,7 @@ typedef struct {
 } gwl_detector;
 
 typedef struct {
-  int precision;     /* GWL_FP64 or GWL_MIXED */
+  int precision;     /* GWL_FP64, GWL_MIXED or GWL_MIXED_F64PHASE */
   int fcut_mode;     /* GWL_FCUT_ISCO or GWL_FCUT_BAND */
   double gmst;       /* Greenwich sidereal angle [rad]; Earth rotation over the
                         segment is ignored; ra enters as ra - gmst */

@@ -168,10 +168,18 @@ int no_calibration(const gwl_ctx* c, const char* what) {
   if (c->n_cal_nodes) return fail(GWL_ERR_ARG, "%s is not available with the calibration model", what);
   return GWL_OK;
 }
+// The FP64-phase mixed mode is a likelihood-only comparison arm.
+int likelihood_only(const gwl_ctx* c, const char* what) {
+  if (c->opt.precision == GWL_MIXED_F64PHASE)
+    return fail(GWL_ERR_ARG, "%s is not available in GWL_MIXED_F64PHASE (likelihood only)", what);
+  return GWL_OK;
+}
 // The Galilean walk needs gwl_grad, which does not model calibration.
 int walk_supported(const gwl_ctx* c, const char* what) {
   if (c->n_cal_nodes && c->walk_kind == GWL_WALK_GALILEAN)
     return fail(GWL_ERR_ARG, "%s: the Galilean walk is not available with the calibration model", what);
+  if (c->walk_kind == GWL_WALK_GALILEAN && c->opt.precision == GWL_MIXED_F64PHASE)
+    return fail(GWL_ERR_ARG, "%s: the Galilean walk is not available in GWL_MIXED_F64PHASE", what);
   return GWL_OK;
 }
 
@@ -221,7 +229,8 @@ int gwl_create(const double* freqs, int64_t n_bins, const double* strain, const 
   if (!freqs || !strain || !psd || !dets || !opt) return fail(GWL_ERR_ARG, "null input pointer");
   if (n_bins < 2 || n_bins > (int64_t)1 << 30) return fail(GWL_ERR_ARG, "n_bins=%lld out of range", (long long)n_bins);
   if (n_det < 1 || n_det > GWL_MAX_DET) return fail(GWL_ERR_ARG, "n_det=%d out of range [1,%d]", n_det, GWL_MAX_DET);
-  if (opt->precision != GWL_FP64 && opt->precision != GWL_MIXED) return fail(GWL_ERR_ARG, "bad precision");
+  if (opt->precision != GWL_FP64 && opt->precision != GWL_MIXED && opt->precision != GWL_MIXED_F64PHASE)
+    return fail(GWL_ERR_ARG, "bad precision");
   if (opt->fcut_mode != GWL_FCUT_ISCO && opt->fcut_mode != GWL_FCUT_BAND) return fail(GWL_ERR_ARG, "bad fcut_mode");
   if (opt->n_dim < 1 || opt->n_dim > GWL_N_PARAM) return fail(GWL_ERR_ARG, "n_dim=%d out of range", opt->n_dim);
   bool used[GWL_N_PARAM] = {false};
@@ -411,6 +420,7 @@ int gwl_grad(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, do
   if (B == 0) return GWL_OK;
   if (!theta_dev || !lnl_dev || !grad_dev) return fail(GWL_ERR_ARG, "null device pointer");
   if ((rc = no_calibration(c, "gwl_grad"))) return rc;
+  if ((rc = likelihood_only(c, "gwl_grad"))) return rc;
   if ((rc = ensure_scratch(c, B))) return rc;
   if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * B))) return rc;
   if ((rc = ensure_bytes(c, &c->d_gpartials, &c->gpartials_cap, gwl::grad_partials_bytes(c, B)))) return rc;
@@ -517,6 +527,7 @@ int gwl_multi_create(gwl_ctx* const* ctxs, int n_events, gwl_multi** out) {
         c->opt.n_dim != ctxs[0]->opt.n_dim)
       return fail(GWL_ERR_ARG, "context %d differs in device, detectors, precision or dimension", e);
     if (c->n_cal_nodes) return fail(GWL_ERR_ARG, "context %d has the calibration model (not batched)", e);
+    if (c->opt.precision == GWL_MIXED_F64PHASE) return fail(GWL_ERR_ARG, "context %d is GWL_MIXED_F64PHASE", e);
   }
   int rc = check_ctx(ctxs[0]);
   if (rc) return rc;
@@ -700,6 +711,7 @@ int gwl_get_tuning(const gwl_ctx* c, gwl_tuning* out) {
 int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs, double sigma_amp, double sigma_phase) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if (n_nodes && (rc = likelihood_only(c, "the calibration model"))) return rc;
   if (n_nodes != 0 && (n_nodes < 2 || n_nodes > GWL_MAX_CAL_NODES))
     return fail(GWL_ERR_ARG, "n_nodes=%d outside {0} and [2, %d]", n_nodes, GWL_MAX_CAL_NODES);
   if (n_nodes && !node_freqs) return fail(GWL_ERR_ARG, "node_freqs is null");

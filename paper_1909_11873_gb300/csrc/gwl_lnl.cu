@@ -489,11 +489,82 @@ __device__ __forceinline__ void cal_nodes(const WinArgs& a, int64_t p, int lane,
   __syncwarp();
 }
 
-template <int NDET, bool MIXED, bool CAL, typename Acc, typename Node>
+// The FP64-phase mixed mode (GWL_MIXED_F64PHASE): per bin the FP64 phase
+// r_d = sum_m c_m B_m(f_j) + tau_d f_j, reduced exactly modulo one cycle in
+// FP64 (r - rint r), narrowed to FP32 for the hardware sine and cosine, and
+// FP32 sums.  The window's FP64 rows carry G_d as floats (narrowed once per
+// staged window, in place of the FP64 values).
+template <int NDET>
+__device__ __forceinline__ void f64phase_sums(const double* __restrict__ sm, int row_elems,
+                                              const PropF64* __restrict__ P, int j0, int jend, int lane,
+                                              float (&U)[NDET], float (&V)[NDET]) {
+  double c[kNBasis], tau[NDET];
+#pragma unroll
+  for (int m = 0; m < kNBasis; ++m) c[m] = P->c[m];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) tau[d] = P->tau[d];
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) U[d] = V[d] = 0.0f;
+  for (int j = j0 + lane; j < jend; j += 32) {
+    const double* row = sm + (int64_t)(j - j0) * row_elems;
+    double v[kNBasis + 1];
+#pragma unroll
+    for (int m = 0; m < kNBasis + 1; ++m) v[m] = row[m];
+    const float* g = reinterpret_cast<const float*>(row + kNBasis + 1);
+    double r = c[0] * v[0];
+#pragma unroll
+    for (int m = 1; m < kNBasis; ++m) r = fma(c[m], v[m], r);
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      double ph = fma(tau[d], v[kNBasis], r);
+      ph -= rint(ph);  // exact: |ph - rint ph| <= 1/2
+      float sn, cs;
+      __sincosf(6.283185307179586f * (float)ph, &sn, &cs);
+      const float gr = g[2 * d], gi = g[2 * d + 1];
+      U[d] = fmaf(gr, cs, fmaf(gi, sn, U[d]));
+      V[d] = fmaf(gi, cs, fmaf(-gr, sn, V[d]));
+    }
+  }
+}
+
+// In place: the staged FP64 rows' G_d (2 NDET doubles after the basis and f)
+// narrowed to floats at the start of the same space (all threads of the CTA;
+// each row by one thread).
+template <int NDET>
+__device__ __forceinline__ void narrow_window_g(double* sm, int row_elems, int nrows) {
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    double* g = sm + (int64_t)r * row_elems + kNBasis + 1;
+    float t[2 * NDET];
+#pragma unroll
+    for (int k = 0; k < 2 * NDET; ++k) t[k] = (float)g[k];
+    float* gf = reinterpret_cast<float*>(g);
+#pragma unroll
+    for (int k = 0; k < 2 * NDET; ++k) gf[k] = t[k];
+  }
+}
+
+template <int NDET, bool MIXED, bool CAL, bool F64PH, typename Acc, typename Node>
 __device__ __forceinline__ void window_sums(const WinArgs& a, const void* __restrict__ smv, const Node* nodes,
                                             int64_t p, int j0, int jend, int lane, Acc (&Ud)[NDET],
                                             Acc (&Vd)[NDET], Acc (&Xd)[NDET]) {
-  if constexpr (MIXED) {
+  if constexpr (F64PH) {
+    float U[NDET], V[NDET];
+    f64phase_sums<NDET>(reinterpret_cast<const double*>(smv), a.row_elems,
+                        reinterpret_cast<const PropF64*>(a.prop) + p, j0, jend, lane, U, V);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        U[d] += __shfl_xor_sync(0xffffffffu, U[d], off);
+        V[d] += __shfl_xor_sync(0xffffffffu, V[d], off);
+      }
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) {
+      Ud[d] = U[d];
+      Vd[d] = V[d];
+      Xd[d] = (Acc)0;
+    }
+  } else if constexpr (MIXED) {
     float U[NDET], V[NDET], X[NDET];
     // the window's anchor rows follow its delta rows in shared memory, its
     // calibration rows follow the anchor rows
@@ -610,7 +681,7 @@ __device__ __forceinline__ void stage_window(const WinArgs& a, void* sm, int j0,
              reinterpret_cast<const Elem*>(a.cal) + (int64_t)j0 * a.cal_row, cbytes, bar);
 }
 
-template <int NDET, bool MIXED, bool CAL>
+template <int NDET, bool MIXED, bool CAL, bool F64PH = false>
 __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
   using Node = typename std::conditional<MIXED, float4, CalNodeD>::type;
@@ -619,7 +690,8 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   __shared__ __align__(8) uint64_t bar;
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const int lane = threadIdx.x & 31;
-  using Acc = Elem;  // per-window partial sums: FP32 (mixed) or FP64
+  // per-window partial sums: FP32 (mixed, FP64-phase mixed) or FP64
+  using Acc = typename std::conditional<MIXED || F64PH, float, double>::type;
   __shared__ Pending<NDET, Acc, CAL> s_pend[kPendCap];
   __shared__ int s_npend;
   __shared__ __align__(32) Node s_nodes[CAL ? 8 * NDET * kMaxCalNodes : 1];
@@ -660,6 +732,12 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
         parity ^= 1u;
         w0_pending = false;
         if (w != 0) __syncthreads();  // every thread has seen the copy land before the barrier is armed again
+        if constexpr (F64PH) {
+          if (w == 0) {
+            narrow_window_g<NDET>(reinterpret_cast<double*>(sm), a.row_elems, j1 - j0);
+            __syncthreads();
+          }
+        }
       }
       if (w != 0) {
         if (threadIdx.x == 0) {
@@ -668,11 +746,15 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
         }
         if (!mbar_wait_bounded(&bar, parity, a.status)) return;
         parity ^= 1u;
+        if constexpr (F64PH) {
+          narrow_window_g<NDET>(reinterpret_cast<double*>(sm), a.row_elems, j1 - j0);
+          __syncthreads();
+        }
       }
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
         Acc U[NDET], V[NDET], X[NDET];
         if constexpr (CAL) cal_nodes<NDET, MIXED>(a, p, lane, nodes);
-        window_sums<NDET, MIXED, CAL>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, U, V, X);
+        window_sums<NDET, MIXED, CAL, F64PH>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, U, V, X);
         const int nwp = (ncut + a.CH - 1) / a.CH;
         if (nwp == 1) {  // the proposal's only window: queue it for the CTA's next combination
           int slot = 0;
@@ -804,18 +886,18 @@ static int64_t nw_max(const gwl_ctx* c) {
 int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + B + (c->M + 31) / 32; }
 int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
 
-template <int NDET, bool MIXED, bool CAL>
+template <int NDET, bool MIXED, bool CAL, bool F64PH = false>
 static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, bool pdl, cudaStream_t st) {
   {
-    const cudaError_t e = raise_smem_limit((const void*)k_window<NDET, MIXED, CAL>, c->device, smem);
+    const cudaError_t e = raise_smem_limit((const void*)k_window<NDET, MIXED, CAL, F64PH>, c->device, smem);
     if (e != cudaSuccess) return e;
   }
   ProfScope ps(c, GWL_KERNEL_BINS, st);
   cudaError_t e;
   if (pdl) {
-    e = launch_pdl(k_window<NDET, MIXED, CAL>, dim3(grid), dim3(256), smem, st, a);
+    e = launch_pdl(k_window<NDET, MIXED, CAL, F64PH>, dim3(grid), dim3(256), smem, st, a);
   } else {
-    k_window<NDET, MIXED, CAL><<<grid, 256, smem, st>>>(a);
+    k_window<NDET, MIXED, CAL, F64PH><<<grid, 256, smem, st>>>(a);
     e = cudaGetLastError();
   }
   c->launches++;
@@ -823,16 +905,26 @@ static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t sme
 }
 
 // Clears the work counters; lets the prologue launch at once (it waits for
-// this grid only before its first counter update, in its last phase).
-__global__ void k_clear_work(int* __restrict__ work, int64_t n) {
+// this grid only before its first counter update, in its last phase).  It
+// also asks L2 for the batch's parameter rows (one prefetch per 128-byte
+// line), so that their fetch from memory is under way while the prologue is
+// being launched.
+__global__ void k_clear_work(int* __restrict__ work, int64_t n, const double* __restrict__ theta, int64_t lines) {
   cudaTriggerProgrammaticLaunchCompletion();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    work[i] = 0;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  const char* base = reinterpret_cast<const char*>(theta);
+  for (int64_t i = t0; i < lines; i += nt) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + 128 * i));
+  for (int64_t i = t0; i < n; i += nt) work[i] = 0;
 }
 
-static cudaError_t launch_clear_work(gwl_ctx* c, int* work, int64_t n, cudaStream_t st) {
-  const unsigned nb = (unsigned)((n + 255) / 256);
-  k_clear_work<<<nb < 64 ? nb : 64, 256, 0, st>>>(work, n);
+static cudaError_t launch_clear_work(gwl_ctx* c, int* work, int64_t n, cudaStream_t st, const double* theta = nullptr,
+                                     int64_t theta_bytes = 0) {
+  // the rows' 128-byte lines (the first from the line holding theta[0])
+  const uintptr_t t = reinterpret_cast<uintptr_t>(theta), tl = t & ~(uintptr_t)127;
+  const int64_t lines = theta ? (int64_t)((t + theta_bytes - tl + 127) / 128) : 0;
+  const int64_t need = n > lines ? n : lines;
+  const unsigned nb = (unsigned)((need + 255) / 256);
+  k_clear_work<<<nb < 64 ? nb : 64, 256, 0, st>>>(work, n, reinterpret_cast<const double*>(tl), lines);
   c->launches++;
   return cudaGetLastError();
 }
@@ -876,8 +968,9 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
   a.pc = c->d_pc + off;
   a.prop = mixed ? (const void*)(c->d_pm + off) : (const void*)(c->d_pf + off);
   const bool cal = c->n_cal_nodes > 0;
+  const bool f64ph = c->opt.precision == GWL_MIXED_F64PHASE;
   a.partials = reinterpret_cast<char*>(c->d_partials) +
-               off * nw_total * sums_per_det(c) * NDET * (int64_t)(mixed ? sizeof(float) : sizeof(double));
+               off * nw_total * sums_per_det(c) * NDET * (int64_t)(mixed || f64ph ? sizeof(float) : sizeof(double));
   a.work = work;
   a.hist = work + 1 + nw_max(c);
   a.pdone = work + 1 + 2 * nw_max(c);
@@ -910,6 +1003,7 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
   if (cal)
     return mixed ? run_window<NDET, true, true>(c, a, grid, smem, pdl, st)
                  : run_window<NDET, false, true>(c, a, grid, smem, pdl, st);
+  if (f64ph) return run_window<NDET, false, false, true>(c, a, grid, smem, pdl, st);
   return mixed ? run_window<NDET, true, false>(c, a, grid, smem, pdl, st)
                : run_window<NDET, false, false>(c, a, grid, smem, pdl, st);
 }
@@ -925,7 +1019,8 @@ static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, doub
   int* pdone = c->d_work + 1 + 2 * nw_max(c);
   int* bcount = pdone + B;
   const Buckets bk = seg ? Buckets{bcount, c->d_blist, seg} : Buckets{nullptr, nullptr, 32};
-  cudaError_t e = launch_clear_work(c, c->d_work, work_needed(c, B), st);
+  cudaError_t e = launch_clear_work(c, c->d_work, work_needed(c, B), st, theta,
+                                    B * theta_stride(c) * (int64_t)sizeof(double));
   if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st, bk);
   if (e != cudaSuccess) return e;
   if (seg) return launch_lanes(c, B, lnl, c->d_work, c->d_work + 1 + nw_max(c), pdone, bcount, seg, st);

@@ -85,6 +85,8 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
   const bool mixed = c->opt.precision == GWL_MIXED;
   if ((what & GWL_TUNE_GRAD) && c->n_cal_nodes)
     return gwl::set_error(GWL_ERR_ARG, "autotune: gwl_grad is not available with the calibration model");
+  if ((what & GWL_TUNE_GRAD) && c->opt.precision == GWL_MIXED_F64PHASE)
+    return gwl::set_error(GWL_ERR_ARG, "autotune: gwl_grad is not available in GWL_MIXED_F64PHASE");
   const std::vector<int> windows = candidates(gwl::lnl_row_bytes(c));
   const std::vector<int> gwindows =
       candidates(mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles);

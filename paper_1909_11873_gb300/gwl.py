@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgwl.so")
 GWL_OK = 0
 GWL_FP64 = 0
 GWL_MIXED = 1
+GWL_MIXED_F64PHASE = 2
 GWL_FCUT_ISCO = 0
 GWL_FCUT_BAND = 1
 N_PARAM = 11

@@ -203,3 +203,36 @@ def test_host_entry_point_pinned_and_pageable(precision):
         l[:] = 0.0
         ctx.gwl_loglike_host(t, l)
         assert np.array_equal(l, ref)
+
+
+@pytest.mark.parametrize("name,B,rows", [("c1", 1024, 1024), ("c2", 8192, 256), ("c3", 2048, 64)])
+def test_fp64_phase_mixed_arm(name, B, rows):
+    """GWL_MIXED_F64PHASE -- the phase in FP64 per bin and detector, reduced exactly, then FP32 sine, cosine
+    and sums -- against the oracle within the mixed bar, on the three lnL workloads."""
+    g = gwl()
+    ev = event(name)
+    th = I.proposals(ev, B, 4, local_fraction=0.0 if name == "c1" else 0.5)
+    got = run_gpu(ev, th, g.GWL_MIXED_F64PHASE)
+    idx = np.random.default_rng(7).choice(B, rows, replace=False) if rows < B else np.arange(B)
+    ref = oracle.loglike(ev, th[idx])
+    assert np.all(np.abs(got[idx] - ref) <= tol(1, ref)), report(got[idx], ref, 1)
+
+
+def test_fp64_phase_mixed_arm_windows_and_refusals():
+    """Several windows with ragged tails; the entry points outside the likelihood refuse the mode."""
+    g = gwl()
+    cfg = dict(n_det=3, T=8.0, f_low=20.0, f_high=395.0, noise=True, source="bbh", batch=333, gmst=0.9)
+    ev = custom_event(cfg, 5)
+    th = I.proposals(ev, 333, 5)
+    ref = oracle.loglike(ev, th)
+    for window, ctas in ((992, 3), (128, 2)):
+        got = run_gpu(ev, th, g.GWL_MIXED_F64PHASE, window=window, ctas_per_sm=ctas)
+        assert np.all(np.abs(got - ref) <= tol(1, ref)), report(got, ref, 1)
+    ctx = g.Context.from_event(ev, g.GWL_MIXED_F64PHASE)
+    x = torch.from_numpy(I.reduced(th[:8], ev.sampling)).cuda()
+    with pytest.raises(g.GwlError):
+        g.grad(ctx, x)
+    with pytest.raises(g.GwlError):
+        ctx.gwl_set_calibration(I.cal_node_freqs(20.0, 395.0))
+    with pytest.raises(g.GwlError):
+        g.MultiContext([ctx])
