@@ -97,6 +97,8 @@ def parse():
                     help="run one workload --warmup + --steps times without timing and exit (for profiler captures): "
                          "lnl = the headline likelihood, grad = the 4096-proposal gradient, cal = the calibrated "
                          "likelihood, fp64ph = the FP64-phase mixed arm")
+    ap.add_argument("--profile-config", default="c2", choices=["c2", "c3"],
+                    help="--profile-only workload: c2 = the 3-detector 8 s batch, c3 = the 128 s BNS batch (2048)")
     ap.add_argument("--bin-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="likelihood bin-loop layout for --shape / --profile-only runs (1 auto, 2 warp, 3 lane)")
     ap.add_argument("--shape", default="",
@@ -853,10 +855,10 @@ def run_profile_only(args):
     if not os.path.exists(gwl.LIB_PATH):
         build.build()
     torch.cuda.set_device(0)
-    ev = device_event(CONFIG)
-    prec = {"fp64ph": getattr(gwl, "GWL_MIXED_F64PHASE", None)}.get(args.profile_only, gwl.GWL_MIXED)
+    ev = device_event(args.profile_config)
+    prec = {"fp64ph": gwl.GWL_MIXED_F64PHASE}.get(args.profile_only, gwl.GWL_MIXED)
     ctx = gwl.Context.from_event(ev, prec)
-    B = 4096 if args.profile_only == "grad" else BATCH
+    B = 4096 if args.profile_only == "grad" else (2048 if args.profile_config == "c3" else BATCH)
     if args.profile_only == "cal":
         th = I.calibrated_proposals(ev, B, SEED + 11)
         rows = np.concatenate([I.reduced(th[:, :11], ev.sampling), th[:, 11:]], axis=1)
