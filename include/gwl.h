@@ -158,13 +158,14 @@ int gwl_loglike_host(gwl_ctx* ctx, const double* theta_host, int64_t B, double* 
  *               ns_replace / ns_run map unit-cube coordinates to parameters
  *               (theta = sigma Phi^{-1}(u); never periodic)
  * A set-up call like gwl_create: it synchronises the device and builds
- * per-bin tables there (about 70 bytes per bin).  ns_replace and ns_run walk
- * in the n_dim + 2 n_nodes n_det coordinates (random walk only).  gwl_grad,
- * the Galilean walk, gwl_autotune with GWL_TUNE_GRAD and gwl_multi_create /
- * gwl_multi_loglike / gwl_multi_ns_run refuse a calibrated context with
- * GWL_ERR_ARG; gwl_waveform returns the template without the calibration
- * factor.  A non-finite calibration parameter gives a non-finite lnL.  The
- * likelihood window (gwl_tuning.window) shrinks, if needed, so that the
+ * per-bin tables there (about 70 bytes per bin).  gwl_grad then also returns
+ * the derivatives with respect to the calibration parameters, and ns_replace
+ * and ns_run walk in the n_dim + 2 n_nodes n_det coordinates (random or
+ * Galilean walk).  gwl_multi_create / gwl_multi_loglike / gwl_multi_ns_run
+ * refuse a calibrated context with GWL_ERR_ARG; gwl_waveform returns the
+ * template without the calibration factor.  A non-finite calibration
+ * parameter gives a non-finite lnL.  The likelihood and gradient windows
+ * (gwl_tuning.window, .grad_window) shrink, if needed, so that the
  * calibration rows fit in shared memory.  An argument error leaves the
  * context unchanged. */
 #define GWL_MAX_CAL_NODES 16
@@ -177,8 +178,16 @@ int gwl_get_calibration(const gwl_ctx* ctx, int* n_nodes, int64_t* theta_stride)
 
 /* Log-likelihood and its gradient with respect to the n_dim sampled
  * coordinates (adjoint accumulation over bins; the ISCO cut index is held
- * fixed, i.e. the gradient of the piecewise-smooth lnL).
- *   grad_dev dev [B][n_dim] FP64 output */
+ * fixed, i.e. the gradient of the piecewise-smooth lnL).  With the calibration
+ * model the rows of theta and of the gradient hold n_dim + 2 n_nodes n_det
+ * doubles (gwl_set_calibration's layout): the calibration derivatives are
+ * accumulated as moments of the spline weights over each spline interval,
+ * then mapped to the node values through the spline's linear dependence on
+ * them.
+ *   theta_dev dev [B][theta_stride] FP64 (see gwl_get_calibration)
+ *   lnl_dev   dev [B] FP64 output
+ *   grad_dev  dev [B][theta_stride] FP64 output
+ * GWL_MIXED_F64PHASE contexts are refused with GWL_ERR_ARG. */
 int gwl_grad(gwl_ctx* ctx, const double* theta_dev, int64_t B, double* lnl_dev, double* grad_dev,
              void* stream);
 
@@ -333,16 +342,28 @@ int gwl_loglike_static(gwl_ctx* ctx, const double* theta_dev, int64_t B, double*
 
 /* Walk used by ns_replace and ns_run. */
 #define GWL_WALK_RANDOM 0   /* Gaussian random walk (default) */
-#define GWL_WALK_GALILEAN 1 /* gradient-informed Galilean walk: chains keep a velocity
-                               v (initially scale * chol z, normals from step word
-                               0x40000000); a step tries x1 = u + v and moves if x1 is in
-                               the cube with lnL >= L*; a step leaving the cube reverses
-                               the offending velocity components; otherwise v is
-                               reflected off the contour, v' = v - 2 (v.n) n with n the
-                               unit gradient of lnL at x1 in the unit cube, and
-                               x2 = x1 + v' is tried (move keeping v', or stay with
-                               v <- -v).  out_nacc counts moves. */
+#define GWL_WALK_GALILEAN 1 /* gradient-informed Galilean walk (Skilling 2012): chains
+                               carry a velocity v, initially scale * chol z (normals of
+                               step word 0x40000000) and from the second step on partly
+                               refreshed, v <- rho v + sqrt(1 - rho^2) scale chol z
+                               (normals of the step's word; rho: gwl_set_galilean).  A
+                               step tries x1 = u + v and moves there if x1 is in the cube
+                               with lnL >= L*.  Otherwise v is reflected off the surface
+                               at x1 -- the contour (g = d lnL / du at x1) inside the cube,
+                               the crossed walls (g = their outward normals summed)
+                               outside it -- in the metric of Sigma = chol chol^T,
+                               v' = v - 2 (v.g) / (g.Sigma g) Sigma g, and x2 = x1 + v' is
+                               tried: the chain moves to x2 with v' if x2 is in the cube
+                               with lnL >= L*, else stays with v <- -v.  The map keeps the
+                               uniform distribution inside the contour and the velocity
+                               distribution invariant.  out_nacc counts moves. */
 int gwl_set_walk(gwl_ctx* ctx, int walk_kind);
+
+/* Velocity persistence rho of the Galilean walk, in [0, 1] (1: never
+ * refreshed; 0: a fresh velocity every step).  Default
+ * GWL_GALILEAN_PERSISTENCE.  GWL_ERR_ARG outside [0, 1]. */
+#define GWL_GALILEAN_PERSISTENCE 0.5
+int gwl_set_galilean(gwl_ctx* ctx, double persistence);
 
 /* Synchronise the context's last stream and return the latched device
  * status (GWL_OK or GWL_ERR_TIMEOUT); clears the latch. */
@@ -426,8 +447,9 @@ int gwl_get_tuning(const gwl_ctx* ctx, gwl_tuning* out);
  * every ctas_per_sm in {1, 2, 3, 4} and both bin-loop layouts (GWL_BINS_WARP,
  * and GWL_BINS_LANE with chunks of 32 and 64 bins where it is available),
  * and gwl_grad
- * (what & GWL_TUNE_GRAD) over the same windows, on the caller's batch
- * theta_dev (B x n_dim, device, row-major, read only) on `stream`, and keeps
+ * (what & GWL_TUNE_GRAD) over the same windows (those whose calibration
+ * scratch fits, with the calibration model), on the caller's batch
+ * theta_dev (B x theta_stride, device, row-major, read only) on `stream`, and keeps
  * the fastest shape of each in the context.  Each shape is timed with CUDA
  * events as the best of two runs of three back-to-back calls after one
  * warm-up call.  Outputs go to a device buffer the call allocates and frees;

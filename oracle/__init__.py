@@ -3,8 +3,9 @@
 Python access (ctypes) to ``gwl_oracle.cpp``: the plain per-bin definition of
 the frequency-domain Gaussian-noise log-likelihood (Eq. 2 of Smith et al.
 2020, read as the log-likelihood ratio), the same with the per-detector
-calibration model of Section 2.2, its dual-number gradient, and a plain
-static parallel nested sampler (Section 3, Algorithm 1).
+calibration model of Section 2.2, its dual-number gradient, a plain
+static parallel nested sampler (Section 3, Algorithm 1) with its constrained
+random walk, and the gradient-informed (Galilean) constrained walk.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never loads it.
@@ -75,6 +76,12 @@ def _L():
             _lib.oracle_ns_run.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
                                            + [i64, i64, i32, u64, d, i64, d, P, P, P, P, i64, i32])
             _lib.oracle_ns_run_gauss.argtypes = [i32, P, d, i64, i64, i32, u64, d, i64, d, P, i32]
+            _lib.oracle_gmc_replace.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
+                                                + [i32, P, P]
+                                                + [P, P, i64, i64, d, u64, u64, i64, i32, d, d, P, P, P, P, P, i32])
+            _lib.oracle_unit_grad.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
+                                              + [i32, P, P, P, i64, P, P, i32])
+            _lib.oracle_gmc_gauss.argtypes = [i32, P, d, P, P, i64, d, u64, u64, i32, d, d, P, P, P, P, i32]
         return _lib
 
 
@@ -303,6 +310,75 @@ def ns_replace_cal(ev, smp, cal, live_u, live_lnl, worst, lnl_star, seed, counte
     if rc != 0:
         raise ValueError("oracle_ns_replace_cal: bad arguments")
     return ou, ol, on, os_
+
+
+def _walk_cal_args(ev, cal):
+    """cal = None (no calibration model) or (node_freqs, sigma_amp, sigma_phase)."""
+    if cal is None:
+        return None, [0, None, None], 0
+    return _cal_args(ev, cal)
+
+
+GALILEAN_PERSISTENCE = 0.5
+
+
+def gmc_replace(ev, smp, live_u, live_lnl, worst, lnl_star, seed, counter, n_chains, walk_len, scale, chol,
+                cal=None, persistence=GALILEAN_PERSISTENCE, n_threads: int | None = None):
+    """Galilean (gradient-informed) constrained walks on the device sampler's stream, optionally with the
+    calibration model (cal as in ns_replace_cal); persistence = the velocity kept per step.  Returns
+    (out_u, out_lnl, out_nacc, start) as ns_replace."""
+    k3, c, nc = _walk_cal_args(ev, cal)
+    D = len(smp.param_map) + nc
+    lu = _f64(live_u).reshape(-1, D)
+    ll = _f64(live_lnl)
+    ch = _f64(chol).reshape(D, D)
+    ou = np.zeros((n_chains, D))
+    ol = np.zeros(n_chains)
+    on = np.zeros(n_chains, dtype=np.int32)
+    os_ = np.zeros(n_chains, dtype=np.int32)
+    k1, a = _ev_args(ev)
+    k2, b = _smp_args(smp)
+    rc = _L().oracle_gmc_replace(*a, *b, *c, _p(lu), _p(ll), lu.shape[0], int(worst), float(lnl_star), int(seed),
+                                 int(counter), int(n_chains), int(walk_len), float(scale), float(persistence), _p(ch),
+                                 _p(ou), _p(ol), _p(on), _p(os_), n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("oracle_gmc_replace: bad arguments")
+    return ou, ol, on, os_
+
+
+def unit_grad(ev, smp, u, cal=None, n_threads: int | None = None):
+    """lnL and d lnL / du at unit-cube points u [n, Dw] (Dw: sampled source coordinates, then the calibration
+    coordinates when cal is given) -> (lnl [n], grad [n, Dw])."""
+    k3, c, nc = _walk_cal_args(ev, cal)
+    Dw = len(smp.param_map) + nc
+    uu = _f64(u).reshape(-1, Dw)
+    lnl = np.zeros(uu.shape[0])
+    g = np.zeros_like(uu)
+    k1, a = _ev_args(ev)
+    k2, b = _smp_args(smp)
+    if _L().oracle_unit_grad(*a, *b, *c, _p(uu), uu.shape[0], _p(lnl), _p(g), n_threads or default_threads()):
+        raise ValueError("oracle_unit_grad: bad arguments")
+    return lnl, g
+
+
+def gmc_gauss(mu, sigma, periodic, u0, lnl_star, seed, counter, walk_len, scale, chol,
+              persistence=GALILEAN_PERSISTENCE, n_threads: int | None = None):
+    """Galilean walks on the Gaussian-in-a-box likelihood (ns_run_gauss's) from start points u0 [n, D]
+    -> (out_u, out_lnl, out_nacc)."""
+    m = _f64(mu)
+    D = m.size
+    pe = _i32(periodic)
+    uu = _f64(u0).reshape(-1, D)
+    ch = _f64(chol).reshape(D, D)
+    ou = np.zeros_like(uu)
+    ol = np.zeros(uu.shape[0])
+    on = np.zeros(uu.shape[0], dtype=np.int32)
+    if _L().oracle_gmc_gauss(D, _p(m), float(sigma), _p(pe), _p(uu), uu.shape[0], float(lnl_star), int(seed),
+                             int(counter), int(walk_len), float(scale), float(persistence), _p(ch), _p(ou), _p(ol),
+                             _p(on),
+                             n_threads or default_threads()):
+        raise ValueError("oracle_gmc_gauss: bad arguments")
+    return ou, ol, on
 
 
 def ns_run_cal(ev, smp, cal, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0,

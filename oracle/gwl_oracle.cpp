@@ -23,7 +23,9 @@
 //     to the template bin by bin (pinned against scipy's natural spline, a
 //     brute-force inner product and two closed forms);
 //   * static nested sampling with parallel (batched) constrained random walks,
-//     Section 3 and Algorithm 1 of the paper.
+//     Section 3 and Algorithm 1 of the paper;
+//   * the gradient-informed constrained walk (Galilean Monte Carlo), driven by
+//     dual-number derivatives in the unit cube.
 //
 // Parity status of the waveform: the Newtonian amplitude and phase, the
 // antenna patterns, the inner product and the time/phase structure are pinned
@@ -112,7 +114,10 @@ template <int N> Dual<N> cos(const Dual<N>& a) { return lift(a, std::cos(a.v), -
 template <int N> Dual<N> pow(const Dual<N>& a, double p) {
   return lift(a, std::pow(a.v, p), p * std::pow(a.v, p - 1.0));
 }
+template <int N> Dual<N> acos(const Dual<N>& a) { return lift(a, std::acos(a.v), -1.0 / std::sqrt(1.0 - a.v * a.v)); }
+template <int N> Dual<N> asin(const Dual<N>& a) { return lift(a, std::asin(a.v), 1.0 / std::sqrt(1.0 - a.v * a.v)); }
 
+using std::acos; using std::asin;
 using std::cbrt; using std::cos; using std::exp; using std::log; using std::pow; using std::sin; using std::sqrt;
 
 // ---------------------------------------------------------------------------
@@ -477,17 +482,19 @@ struct Sampling {
   const int* periodic;    // [D]
 };
 
-double prior_map(int kind, double lo, double hi, double u) {
+template <typename T>
+T prior_map(int kind, double lo, double hi, const T& u) {
   switch (kind) {
-    case 1: return std::cbrt(lo * lo * lo + u * (hi * hi * hi - lo * lo * lo));
-    case 2: return std::acos(1.0 - 2.0 * u);
-    case 3: return std::asin(2.0 * u - 1.0);
+    case 1: return cbrt(lo * lo * lo + u * (hi * hi * hi - lo * lo * lo));
+    case 2: return acos(1.0 - 2.0 * u);
+    case 3: return asin(2.0 * u - 1.0);
     default: return lo + u * (hi - lo);
   }
 }
 
-void unit_to_theta(const Sampling& s, const double* u, double* th) {
-  for (int k = 0; k < P_N; ++k) th[k] = s.fixed[k];
+template <typename T>
+void unit_to_theta(const Sampling& s, const T* u, T* th) {
+  for (int k = 0; k < P_N; ++k) th[k] = T(s.fixed[k]);
   for (int i = 0; i < s.D; ++i) th[s.param_map[i]] = prior_map(s.kind[i], s.lo[i], s.hi[i], u[i]);
 }
 
@@ -524,6 +531,92 @@ void random_walk(const UnitLike& like, const int* periodic, int D, const double*
     if (!inside) continue;
     double lp = like(up.data());
     if (lp >= lnl_star) { u = up; l = lp; ++nacc; }
+  }
+  std::copy(u.begin(), u.end(), u_out);
+  *l_out = l;
+  *nacc_out = nacc;
+}
+
+// Gradient-informed constrained walk: Galilean Monte Carlo (Skilling 2012),
+// with the velocity drawn from the random walk's proposal distribution and
+// reflections taken in that distribution's own metric.  The chain carries a
+// velocity, initially v = scale * L z (z: the normals of step word
+// 0x40000000), and from step 2 on partly refreshed before the step,
+//   v <- rho v + sqrt(1 - rho^2) scale L z  (z: the normals of the step's word),
+// an autoregressive move that keeps N(0, scale^2 L L^T).  With Sigma = L L^T,
+// a reflection of v off a surface of normal g is
+//   v' = v - 2 (v.g) / (g.Sigma g) Sigma g,
+// which keeps v^T Sigma^-1 v (so the velocity distribution) and undoes itself.
+// Each step tries x1 = u + v (periodic coordinates wrap):
+//   * x1 inside the cube with lnL(x1) >= L*: move to x1, keep v;
+//   * otherwise reflect at x1 -- off the likelihood contour (g = d lnL / du at
+//     x1) when x1 is inside the cube, off the walls it crossed when it is not
+//     (g = the outward unit normals of those walls summed) -- and try
+//     x2 = x1 + v'; inside the cube with lnL(x2) >= L*: move to x2 with v';
+//   * otherwise stay and reverse the velocity, v <- -v.
+// The normal depends on x1 alone, so the map (u, v) -> (u', -v') is an
+// involution and preserves volume: the uniform distribution inside the
+// contour times the velocity distribution is left invariant.
+using UnitLikeGrad = std::function<double(const double*, double*)>;  // lnL(u), writes d lnL / du
+
+void galilean_walk(const UnitLike& like, const UnitLikeGrad& like_grad, const int* periodic, int D,
+                   const double* u0, double l0, double lnl_star, uint64_t seed, uint64_t counter,
+                   uint32_t chain, int walk_len, double scale, double rho, const double* chol, double* u_out,
+                   double* l_out, int32_t* nacc_out) {
+  std::vector<double> u(u0, u0 + D), v(D), z(D), x1(D), x2(D), g(D), sg(D), v2(D), sigma(D * D, 0.0);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j)
+      for (int k = 0; k < D; ++k) sigma[i * D + j] += chol[i * D + k] * chol[j * D + k];
+  walk_normals(seed, counter, chain, 0x40000000u, D, z.data());
+  for (int i = 0; i < D; ++i) {
+    double dz = 0.0;
+    for (int k = 0; k <= i; ++k) dz += chol[i * D + k] * z[k];
+    v[i] = scale * dz;
+  }
+  auto step_to = [&](const std::vector<double>& from, const std::vector<double>& vel, std::vector<double>& to) {
+    bool inside = true;
+    for (int i = 0; i < D; ++i) {
+      double x = from[i] + vel[i];
+      if (periodic[i]) x -= std::floor(x);
+      else if (x < 0.0 || x > 1.0) inside = false;
+      to[i] = x;
+    }
+    return inside;
+  };
+  double l = l0;
+  int32_t nacc = 0;
+  for (int st = 1; st <= walk_len; ++st) {
+    if (st > 1 && rho < 1.0) {
+      walk_normals(seed, counter, chain, uint32_t(st), D, z.data());
+      for (int i = 0; i < D; ++i) {
+        double dz = 0.0;
+        for (int k = 0; k <= i; ++k) dz += chol[i * D + k] * z[k];
+        v[i] = rho * v[i] + std::sqrt(1.0 - rho * rho) * scale * dz;
+      }
+    }
+    if (step_to(u, v, x1)) {
+      const double l1 = like_grad(x1.data(), g.data());
+      if (l1 >= lnl_star) { u = x1; l = l1; ++nacc; continue; }
+    } else {
+      for (int i = 0; i < D; ++i) g[i] = (!periodic[i] && x1[i] > 1.0) ? 1.0 : (!periodic[i] && x1[i] < 0.0) ? -1.0 : 0.0;
+    }
+    double gsg = 0.0, vg = 0.0;
+    for (int i = 0; i < D; ++i) {
+      sg[i] = 0.0;
+      for (int j = 0; j < D; ++j) sg[i] += sigma[i * D + j] * g[j];
+      gsg += g[i] * sg[i];
+      vg += v[i] * g[i];
+    }
+    bool moved = false;
+    if (gsg > 0.0 && std::isfinite(gsg) && std::isfinite(vg)) {
+      for (int i = 0; i < D; ++i) v2[i] = v[i] - 2.0 * vg / gsg * sg[i];
+      if (step_to(x1, v2, x2)) {
+        const double l2 = like(x2.data());
+        if (l2 >= lnl_star) { u = x2; l = l2; v = v2; ++nacc; moved = true; }
+      }
+    }
+    if (!moved)
+      for (int i = 0; i < D; ++i) v[i] = -v[i];
   }
   std::copy(u.begin(), u.end(), u_out);
   *l_out = l;
@@ -896,6 +989,79 @@ UnitLike gw_like(const Event& ev, const Sampling& s) {
   return [ev, s](const double* u) { return loglike_unit(ev, s, u); };
 }
 
+// lnL of a unit-cube point and its derivatives with respect to the unit-cube
+// coordinates: dual numbers seeded on u and carried through the prior maps
+// (and, with the calibration model, through theta = sigma Phi^{-1}(u), whose
+// derivative is sigma / phi(Phi^{-1}(u))), sixteen directions per pass.
+UnitLikeGrad gw_like_grad(const Event& ev, const Sampling& s) {
+  return [ev, s](const double* u, double* g) {
+    using DT = Dual<P_N>;
+    DT uu[P_N], th[P_N];
+    for (int i = 0; i < s.D; ++i) {
+      uu[i] = DT(u[i]);
+      uu[i].d[i] = 1.0;
+    }
+    unit_to_theta(s, uu, th);
+    const DT r = loglike_one<DT>(ev, th);
+    for (int i = 0; i < s.D; ++i) g[i] = r.d[i];
+    return r.v;
+  };
+}
+
+UnitLikeGrad cal_like_grad(const Event& ev, const Sampling& s, int nn, const double* node_f, const double* sig) {
+  std::vector<double> xn(nn);
+  for (int k = 0; k < nn; ++k) xn[k] = std::log(node_f[k]);
+  const int nc = 2 * nn * ev.n_det;
+  const double sa = sig[0], sp = sig[1];
+  return [ev, s, nn, xn, nc, sa, sp](const double* u, double* g) {
+    constexpr int NT = 16;
+    using DT = Dual<NT>;
+    const int Dw = s.D + nc;
+    std::vector<DT> uu(s.D), th(P_N + nc);
+    double val = 0.0;
+    for (int c0 = 0; c0 < Dw; c0 += NT) {
+      auto seeded = [&](int k, double x) {
+        DT t(x);
+        if (k >= c0 && k < c0 + NT) t.d[k - c0] = 1.0;
+        return t;
+      };
+      for (int i = 0; i < s.D; ++i) uu[i] = seeded(i, u[i]);
+      unit_to_theta(s, uu.data(), th.data());
+      for (int c = 0; c < nc; ++c) {
+        const double sg = (c / nn) % 2 ? sp : sa, z = inv_normal_cdf(u[s.D + c]);
+        th[P_N + c] = lift(seeded(s.D + c, u[s.D + c]), sg * z, sg * std::sqrt(2.0 * kPi) * std::exp(0.5 * z * z));
+      }
+      const DT r = loglike_cal_T<DT>(ev, th.data(), nn, xn.data());
+      val = r.v;
+      for (int k = c0; k < Dw && k < c0 + NT; ++k) g[k] = r.d[k - c0];
+    }
+    return val;
+  };
+}
+
+UnitLikeGrad gauss_like_grad(int D, const double* mu, double sigma) {
+  std::vector<double> m(mu, mu + D);
+  const UnitLike f = gauss_like(D, mu, sigma);
+  return [m, D, sigma, f](const double* u, double* g) {
+    for (int i = 0; i < D; ++i) g[i] = -(u[i] - m[i]) / (sigma * sigma);
+    return f(u);
+  };
+}
+
+void gmc_replace_impl(const UnitLike& like, const UnitLikeGrad& like_grad, int D, const int* periodic,
+                      const double* live_u, const double* live_lnl, int64_t K, int64_t worst, double lnl_star,
+                      uint64_t seed, uint64_t counter, int64_t n_chains, int walk_len, double scale, double rho,
+                      const double* chol, double* out_u, double* out_lnl, int32_t* out_nacc, int32_t* out_start,
+                      int n_threads) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int64_t b = 0; b < n_chains; ++b) {
+    int st = pick_start(seed, counter, uint32_t(b), K, worst);
+    if (out_start) out_start[b] = st;
+    galilean_walk(like, like_grad, periodic, D, live_u + D * st, live_lnl[st], lnl_star, seed, counter,
+                  uint32_t(b), walk_len, scale, rho, chol, out_u + D * b, &out_lnl[b], &out_nacc[b]);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -973,6 +1139,69 @@ int oracle_ns_run_cal(const double* freqs, int64_t M, const double* strain, cons
   for (int i = 0; i < D; ++i) per[i] = periodic[i];
   ns_run_impl(cal_like(ev, s, n_nodes, node_f, sig), Dw, per.data(), K, n_chains, walk_len, seed, dlogz,
               max_rounds, scale0, res, nullptr, nullptr, nullptr, 0, n_threads);
+  return 0;
+}
+
+// Galilean (gradient-informed) constrained walks on the device sampler's
+// stream: chains pick their start as in oracle_ns_replace and walk as in
+// galilean_walk.  n_nodes = 0: no calibration model; otherwise the walk
+// coordinates are those of oracle_ns_replace_cal.
+int oracle_gmc_replace(const double* freqs, int64_t M, const double* strain, const double* psd,
+                       const double* geom, int n_det, double gmst, double t_ref, int fcut_mode,
+                       int D, const int* param_map, const double* fixed, const int* kind,
+                       const double* lo, const double* hi, const int* periodic, int n_nodes,
+                       const double* node_f, const double* sig, const double* live_u,
+                       const double* live_lnl, int64_t K, int64_t worst, double lnl_star,
+                       uint64_t seed, uint64_t counter, int64_t n_chains, int walk_len,
+                       double scale, double rho, const double* chol, double* out_u, double* out_lnl,
+                       int32_t* out_nacc, int32_t* out_start, int n_threads) {
+  if (K < 2 || worst < 0 || worst >= K || n_nodes == 1 || n_nodes < 0 || !(rho >= 0.0 && rho <= 1.0)) return -1;
+  Event ev{freqs, M, strain, psd, geom, n_det, gmst, t_ref, fcut_mode};
+  Sampling s{D, param_map, fixed, kind, lo, hi, periodic};
+  const int Dw = D + 2 * n_nodes * n_det;
+  std::vector<int> per(Dw, 0);
+  for (int i = 0; i < D; ++i) per[i] = periodic[i];
+  if (n_nodes)
+    gmc_replace_impl(cal_like(ev, s, n_nodes, node_f, sig), cal_like_grad(ev, s, n_nodes, node_f, sig), Dw,
+                     per.data(), live_u, live_lnl, K, worst, lnl_star, seed, counter, n_chains, walk_len, scale,
+                     rho, chol, out_u, out_lnl, out_nacc, out_start, n_threads);
+  else
+    gmc_replace_impl(gw_like(ev, s), gw_like_grad(ev, s), D, per.data(), live_u, live_lnl, K, worst, lnl_star,
+                     seed, counter, n_chains, walk_len, scale, rho, chol, out_u, out_lnl, out_nacc, out_start,
+                     n_threads);
+  return 0;
+}
+
+// lnL and d lnL / du at n unit-cube points u[n][Dw] (test hook; n_nodes as in
+// oracle_gmc_replace) -> lnl[n], grad[n][Dw].
+int oracle_unit_grad(const double* freqs, int64_t M, const double* strain, const double* psd,
+                     const double* geom, int n_det, double gmst, double t_ref, int fcut_mode, int D,
+                     const int* param_map, const double* fixed, const int* kind, const double* lo,
+                     const double* hi, const int* periodic, int n_nodes, const double* node_f,
+                     const double* sig, const double* u, int64_t n, double* lnl, double* grad, int n_threads) {
+  if (n_nodes == 1 || n_nodes < 0) return -1;
+  Event ev{freqs, M, strain, psd, geom, n_det, gmst, t_ref, fcut_mode};
+  Sampling s{D, param_map, fixed, kind, lo, hi, periodic};
+  const int Dw = D + 2 * n_nodes * n_det;
+  const UnitLikeGrad f = n_nodes ? cal_like_grad(ev, s, n_nodes, node_f, sig) : gw_like_grad(ev, s);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int64_t i = 0; i < n; ++i) lnl[i] = f(u + Dw * i, grad + Dw * i);
+  return 0;
+}
+
+// Galilean walks on the analytic Gaussian-in-a-box likelihood from given
+// start points u0[n][D] (test pin of the walk itself): chain b uses chain
+// word b of the stream.
+int oracle_gmc_gauss(int D, const double* mu, double sigma, const int* periodic, const double* u0, int64_t n,
+                     double lnl_star, uint64_t seed, uint64_t counter, int walk_len, double scale, double rho,
+                     const double* chol, double* out_u, double* out_lnl, int32_t* out_nacc, int n_threads) {
+  if (D < 1 || n < 0 || !(rho >= 0.0 && rho <= 1.0)) return -1;
+  const UnitLike f = gauss_like(D, mu, sigma);
+  const UnitLikeGrad fg = gauss_like_grad(D, mu, sigma);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int64_t b = 0; b < n; ++b)
+    galilean_walk(f, fg, periodic, D, u0 + D * b, f(u0 + D * b), lnl_star, seed, counter, uint32_t(b), walk_len,
+                  scale, rho, chol, out_u + D * b, &out_lnl[b], &out_nacc[b]);
   return 0;
 }
 

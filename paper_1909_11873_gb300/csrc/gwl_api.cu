@@ -174,10 +174,8 @@ int likelihood_only(const gwl_ctx* c, const char* what) {
     return fail(GWL_ERR_ARG, "%s is not available in GWL_MIXED_F64PHASE (likelihood only)", what);
   return GWL_OK;
 }
-// The Galilean walk needs gwl_grad, which does not model calibration.
+// The Galilean walk needs gwl_grad.
 int walk_supported(const gwl_ctx* c, const char* what) {
-  if (c->n_cal_nodes && c->walk_kind == GWL_WALK_GALILEAN)
-    return fail(GWL_ERR_ARG, "%s: the Galilean walk is not available with the calibration model", what);
   if (c->walk_kind == GWL_WALK_GALILEAN && c->opt.precision == GWL_MIXED_F64PHASE)
     return fail(GWL_ERR_ARG, "%s: the Galilean walk is not available in GWL_MIXED_F64PHASE", what);
   return GWL_OK;
@@ -419,7 +417,6 @@ int gwl_grad(gwl_ctx* c, const double* theta_dev, int64_t B, double* lnl_dev, do
   if (B < 0) return fail(GWL_ERR_ARG, "B < 0");
   if (B == 0) return GWL_OK;
   if (!theta_dev || !lnl_dev || !grad_dev) return fail(GWL_ERR_ARG, "null device pointer");
-  if ((rc = no_calibration(c, "gwl_grad"))) return rc;
   if ((rc = likelihood_only(c, "gwl_grad"))) return rc;
   if ((rc = ensure_scratch(c, B))) return rc;
   if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * B))) return rc;
@@ -484,7 +481,7 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
   const int64_t nb = n_chains > K ? n_chains : K;
   if ((rc = ensure_scratch(c, nb))) return rc;
   if (c->walk_kind == GWL_WALK_GALILEAN) {
-    const int D = c->opt.n_dim;
+    const int D = (int)gwl::theta_stride(c);
     if ((rc = ensure_bytes(c, (void**)&c->d_gmc, &c->gmc_cap, (int64_t)sizeof(double) * gwl::gmc_scratch_doubles(n_chains, D))))
       return rc;
     if ((rc = ensure_bytes(c, &c->d_pgrad, &c->pgrad_cap, gwl::prop_grad_bytes(c) * nb))) return rc;
@@ -673,6 +670,13 @@ int gwl_set_walk(gwl_ctx* c, int walk_kind) {
   return GWL_OK;
 }
 
+int gwl_set_galilean(gwl_ctx* c, double persistence) {
+  if (!c) return fail(GWL_ERR_ARG, "null context");
+  if (!(persistence >= 0.0 && persistence <= 1.0)) return fail(GWL_ERR_ARG, "persistence must be in [0, 1]");
+  c->gmc_persistence = persistence;
+  return GWL_OK;
+}
+
 int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
   if (!c || !t) return fail(GWL_ERR_ARG, "null argument");
   if (t->window < 0 || t->grad_window < 0 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16 || t->bin_kernel < 0 ||
@@ -687,6 +691,12 @@ int gwl_set_tuning(gwl_ctx* c, const gwl_tuning* t) {
   const size_t grow = mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles;
   if ((size_t)t->window * row > gwl::kWindowSmemMax || (size_t)t->grad_window * grow > gwl::kWindowSmemMax)
     return fail(GWL_ERR_ARG, "window of %d/%d bins exceeds shared memory", t->window, t->grad_window);
+  if (c->n_cal_nodes && t->grad_window &&
+      ((size_t)t->grad_window * (grow + (mixed ? sizeof(float) * c->row_cal_f : sizeof(double) * c->row_cal_d)) >
+           gwl::kWindowSmemMax ||
+       gwl::calgrad_smem(c, t->grad_window) > gwl::kCalGradSmemMax))
+    return fail(GWL_ERR_ARG, "gradient window of %d bins exceeds shared memory with the calibration model",
+                t->grad_window);
   if (t->window) c->window = t->window;
   if (t->grad_window) c->grad_window = t->grad_window;
   if (t->ctas_per_sm) c->ctas_per_sm = t->ctas_per_sm;
@@ -763,9 +773,14 @@ int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs, doubl
   c->seg.stride = c->opt.n_dim + 2 * n_nodes * c->n_det;
   c->cal_sigma[0] = sigma_amp;
   c->cal_sigma[1] = sigma_phase;
-  // the likelihood window must still fit shared memory with the calibration rows
+  // the likelihood and gradient windows must still fit shared memory with the calibration rows
   const size_t row = gwl::lnl_row_bytes(c);
   while (c->window > 32 && (size_t)c->window * row > gwl::kWindowSmemMax) c->window -= 32;
+  const bool mixed = c->opt.precision == GWL_MIXED;
+  const size_t grow = (mixed ? sizeof(float) * (c->row_floats + c->row_cal_f) : sizeof(double) * (c->row_doubles + c->row_cal_d));
+  while (c->grad_window > 32 && ((size_t)c->grad_window * grow > gwl::kWindowSmemMax ||
+                                 gwl::calgrad_smem(c, c->grad_window) > gwl::kCalGradSmemMax))
+    c->grad_window -= 32;
   return GWL_OK;
 }
 

@@ -61,10 +61,13 @@ __device__ __forceinline__ float nearest_int(float x) {
 //     detector r_d mod 1 = (S mod 1) + (p - rint p) + e (s - rint s and
 //     p - rint p are exact): two roundings of at most 2^-24 cycles each, and
 //     seven fewer FP32 operations per detector.
+// With shift (may be null) the phase of detector d is r_d - shift[d] (the
+// calibration model's phase correction, in cycles).
 template <int NDET, bool EXACT_SUM>
 __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], const float (&ch)[kNBasis],
                                             const float (&cl)[kNBasis], const float (&th)[NDET],
-                                            const float (&tl)[NDET], float (&sn)[NDET], float (&cs)[NDET]) {
+                                            const float (&tl)[NDET], float (&sn)[NDET], float (&cs)[NDET],
+                                            const float* shift = nullptr) {
   float s, lo;
   {
     float e;
@@ -89,8 +92,12 @@ __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], con
       e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
       two_sum(s, p, t, q);
       const float l = lo + (e + q);
-      const float fr = __fadd_rn(__fsub_rn(t, nearest_int(t)), l);  // t - rint t is exact
-      __sincosf(6.283185307179586f * fr, &sn[d], &cs[d]);
+      float fr = __fadd_rn(__fsub_rn(t, nearest_int(t)), l);  // t - rint t is exact
+      if (shift) fr = fr - shift[d];
+      // the gradient's basis-weighted sums amplify the absolute error of the
+      // hardware sine and cosine (~4e-7, a smooth function of the argument, so
+      // it adds up across bins): the accurate FP32 sincospi (|2 fr| <= ~1.1)
+      sincospif(2.0f * fr, &sn[d], &cs[d]);
     }
   } else {
     const float sf = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);
@@ -99,7 +106,8 @@ __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], con
       float p, e;
       two_prod(th[d], fh, p, e);
       e = __fmaf_rn(th[d], fl, __fmaf_rn(tl[d], fh, e));
-      const float fr = __fadd_rn(__fadd_rn(sf, __fsub_rn(p, nearest_int(p))), e);
+      float fr = __fadd_rn(__fadd_rn(sf, __fsub_rn(p, nearest_int(p))), e);
+      if (shift) fr = fr - shift[d];
       __sincosf(6.283185307179586f * fr, &sn[d], &cs[d]);
     }
   }
@@ -430,13 +438,18 @@ __device__ __forceinline__ void anchored_sums(const float* __restrict__ sm, int 
 
 template <int NDET>
 __device__ __forceinline__ void phase_f64(const double (&v)[RowD<NDET>::n], const double (&c)[kNBasis],
-                                          const double (&tau)[NDET], double (&sn)[NDET], double (&cs)[NDET]) {
+                                          const double (&tau)[NDET], double (&sn)[NDET], double (&cs)[NDET],
+                                          const double* shift = nullptr) {
   double r = c[0] * v[0];
 #pragma unroll
   for (int m = 1; m < kNBasis; ++m) r = fma(c[m], v[m], r);
   const double f = v[8];
 #pragma unroll
-  for (int d = 0; d < NDET; ++d) sincospi(2.0 * fma(tau[d], f, r), &sn[d], &cs[d]);
+  for (int d = 0; d < NDET; ++d) {
+    double ph = fma(tau[d], f, r);
+    if (shift) ph -= shift[d];
+    sincospi(2.0 * ph, &sn[d], &cs[d]);
+  }
 }
 
 template <int NDET>

@@ -226,4 +226,35 @@ __device__ __forceinline__ FF cos(const FF& x) {
   return c;
 }
 
+// Node data of one proposal for the warp's calibration splines (spline
+// s = 2 d + q, q = 0 amplitude, 1 phase; node k): the lanes first store the
+// node values y_k from the proposal's row of theta, y = [NDET][2][nn] (the
+// phase scaled to cycles; in the mixed path each is narrowed once, by integer
+// operations), then form the curvatures m_k = sum_i Q_ki y_i from the stored
+// values.  Nodes: (dA_k, m^A_k, dphi_k, m^phi_k) per detector and node.
+template <int NDET, bool MIXED, typename Node>
+__device__ __forceinline__ void cal_nodes_fill(const double* __restrict__ y, int nn, const void* __restrict__ calQ,
+                                               int lane, Node* __restrict__ nd) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  const T* Q = reinterpret_cast<const T*>(calQ);
+  __syncwarp();  // the warp is done with the previous proposal's node data
+  for (int o = lane; o < 2 * NDET * nn; o += 32) {
+    const int sp = o / nn, k = o - sp * nn;
+    const double yd = __ldg(y + o);
+    T yv;
+    if constexpr (MIXED) yv = ff_from(yd).hi;
+    else yv = yd;
+    reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k])[2 * (sp & 1)] = (sp & 1) ? yv * (T)(0.5 / kPi) : yv;
+  }
+  __syncwarp();
+  for (int o = lane; o < 2 * NDET * nn; o += 32) {
+    const int sp = o / nn, k = o - sp * nn;
+    const T* ys = reinterpret_cast<const T*>(&nd[(sp >> 1) * kMaxCalNodes]) + 2 * (sp & 1);  // stride 4 T
+    T m = (T)0;
+    for (int i = 0; i < nn; ++i) m = fma(Q[k * nn + i], ys[4 * i], m);
+    reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k])[2 * (sp & 1) + 1] = m;
+  }
+  __syncwarp();
+}
+
 }  // namespace gwl

@@ -185,8 +185,19 @@ struct GradArgs {
   // a proposal whose cut falls in its first window is finished in the bin loop
   const void* pg;     // PropGrad<G>[B]
   double* lnl;        // [B]
-  double* grad;       // [B][n_dim]
+  double* grad;       // [B][gstride]: the n_dim source directions first
   int n_dim;
+  int gstride;        // doubles per row of grad (and theta)
+  // calibration model (instances with CAL only): the window's calibration rows
+  // follow its table rows in shared memory (cal_smem elements in)
+  const void* cal;
+  int cal_row;
+  int cal_smem;
+  const double* theta;
+  int cal_par;        // first calibration parameter of a row of theta
+  int nn;             // calibration nodes
+  const void* calQ;   // [nn][nn] natural-spline matrix, float (mixed) or double
+  void* xpart;        // [B][nw_total][NDET] per-window <h|h> corrections X_d
 };
 
 // lnL = sum_d [Re K_d Z_d] - <h|h>/2 and d lnL / d theta_i from the window
@@ -216,15 +227,21 @@ __device__ __forceinline__ G grad_dir(const PropCommon* c, const PropGrad<G>& g,
   return acc;
 }
 
-template <int NDET, bool MIXED>
-__device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restrict__ smv, int64_t p, int j0,
-                                          int jend, int lane,
-                                          typename std::conditional<MIXED, float, double>::type (&A)[NDET][kAccPerDet]) {
+// With CAL, bin j's term of detector d is (1 + dA) G_d,j e^{-2 pi i (r_d,j - dphi)}
+// (calibration rows staged at cal_smem, the proposal's node data in nodes)
+// and X_d collects the <h|h> correction sum_j dA (2 + dA) dH_d,j.
+template <int NDET, bool MIXED, bool CAL, typename Node>
+__device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restrict__ smv, const Node* nodes,
+                                          int64_t p, int j0, int jend, int lane,
+                                          typename std::conditional<MIXED, float, double>::type (&A)[NDET][kAccPerDet],
+                                          typename std::conditional<MIXED, float, double>::type (&X)[NDET]) {
   using Acc = typename std::conditional<MIXED, float, double>::type;
 #pragma unroll
-  for (int d = 0; d < NDET; ++d)
+  for (int d = 0; d < NDET; ++d) {
+    X[d] = (Acc)0;
 #pragma unroll
     for (int k = 0; k < kAccPerDet; ++k) A[d][k] = (Acc)0;
+  }
   if constexpr (MIXED) {
     const float* sm = reinterpret_cast<const float*>(smv);
     const PropMixed* P = reinterpret_cast<const PropMixed*>(a.prop) + p;
@@ -243,10 +260,22 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
       float v[RowM<NDET>::n];
       load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
       float sn[NDET], cs[NDET];
-      phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs);
+      CalBin<NDET, float> cb;
+      if constexpr (CAL) {
+        cal_eval<NDET>(sm + a.cal_smem + (int64_t)(j - j0) * a.cal_row, reinterpret_cast<const float4*>(nodes), cb);
+        phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs, cb.P);
+      } else {
+        phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs);
+      }
 #pragma unroll
       for (int d = 0; d < NDET; ++d) {
-        const float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
+        float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
+        if constexpr (CAL) {
+          const float a1 = 1.0f + cb.A[d];
+          gr *= a1;
+          gi *= a1;
+          X[d] = fmaf(cb.A[d] * (2.0f + cb.A[d]), cb.H[d], X[d]);
+        }
         const float uw = fmaf(gr, cs[d], gi * sn[d]);
         const float vw = fmaf(gi, cs[d], -gr * sn[d]);
         A[d][0] += uw;
@@ -272,10 +301,22 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
       double v[RowD<NDET>::n];
       load_row<NDET>(sm + (int64_t)(j - j0) * a.row_elems, v);
       double sn[NDET], cs[NDET];
-      phase_f64<NDET>(v, c, tau, sn, cs);
+      CalBin<NDET, double> cb;
+      if constexpr (CAL) {
+        cal_eval<NDET>(sm + a.cal_smem + (int64_t)(j - j0) * a.cal_row, reinterpret_cast<const CalNodeD*>(nodes), cb);
+        phase_f64<NDET>(v, c, tau, sn, cs, cb.P);
+      } else {
+        phase_f64<NDET>(v, c, tau, sn, cs);
+      }
 #pragma unroll
       for (int d = 0; d < NDET; ++d) {
-        const double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
+        double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
+        if constexpr (CAL) {
+          const double a1 = 1.0 + cb.A[d];
+          gr *= a1;
+          gi *= a1;
+          X[d] = fma(cb.A[d] * (2.0 + cb.A[d]), cb.H[d], X[d]);
+        }
         const double uw = fma(gr, cs[d], gi * sn[d]);
         const double vw = fma(gi, cs[d], -gr * sn[d]);
         A[d][0] += uw;
@@ -293,26 +334,63 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-    for (int d = 0; d < NDET; ++d)
+    for (int d = 0; d < NDET; ++d) {
 #pragma unroll
       for (int k = 0; k < kAccPerDet; ++k) A[d][k] += __shfl_xor_sync(0xffffffffu, A[d][k], off);
+      if constexpr (CAL) X[d] += __shfl_xor_sync(0xffffffffu, X[d], off);
+    }
 }
 
-template <int NDET, bool MIXED>
+// The calibration model's terms of lnL and of the source directions' derivatives:
+// -1/2 sum_d |K_d|^2 X_d and its derivative -sum_d (Kr_d dKr_d + Ki_d dKi_d) X_d.
+template <int NDET, class XF>
+__device__ __forceinline__ double cal_lnl_term(const PropCommon* c, XF X) {
+  double t = 0.0;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) t -= 0.5 * (c->Kr[d] * c->Kr[d] + c->Ki[d] * c->Ki[d]) * (double)X(d);
+  return t;
+}
+template <int NDET, class G, class XF>
+__device__ __forceinline__ G cal_grad_term(const PropCommon* c, const PropGrad<G>& g, int i, XF X) {
+  G t = (G)0;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) t -= ((G)c->Kr[d] * g.dKr[d][i] + (G)c->Ki[d] * g.dKi[d][i]) * (G)X(d);
+  return t;
+}
+
+// One thread: bins [j0, j1) of the table into shared memory (bulk copy
+// completing on bar); with CAL the window's calibration rows follow at element
+// offset cal_smem, in pairs (a bulk copy moves whole 16-byte units; the table
+// has a zero row past the last bin).
+template <bool MIXED, bool CAL>
+__device__ __forceinline__ void grad_stage(const GradArgs& a, void* sm, int j0, int j1, uint64_t* bar) {
+  using Elem = typename std::conditional<MIXED, float, double>::type;
+  const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
+  const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
+  uint32_t cbytes = 0;
+  if constexpr (CAL) cbytes = (uint32_t)((j1 - j0 + 1) & ~1) * (uint32_t)a.cal_row * (uint32_t)sizeof(Elem);
+  mbar_arrive_expect_tx(bar, bytes + cbytes);
+  bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, bar);
+  if constexpr (CAL)
+    bulk_g2s(reinterpret_cast<Elem*>(sm) + a.cal_smem, reinterpret_cast<const Elem*>(a.cal) + (int64_t)j0 * a.cal_row,
+             cbytes, bar);
+}
+
+template <int NDET, bool MIXED, bool CAL>
 __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
+  using Node = typename std::conditional<MIXED, float4, CalNodeD>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(32) Node s_nodes[CAL ? 8 * NDET * kMaxCalNodes : 1];
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
-  const Elem* tab = reinterpret_cast<const Elem*>(a.tab);
   const int lane = threadIdx.x & 31;
+  Node* nodes = s_nodes + (CAL ? (threadIdx.x >> 5) * NDET * kMaxCalNodes : 0);
   // window 0 of the table is copied while the prologue finishes (see k_window)
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
-    const uint32_t bytes = (uint32_t)(a.CH < a.M ? a.CH : a.M) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
-    mbar_arrive_expect_tx(&bar, bytes);
-    bulk_g2s(sm, tab, bytes, &bar);
+    grad_stage<MIXED, CAL>(a, sm, 0, a.CH < a.M ? (int)a.CH : (int)a.M, &bar);
   }
   bool w0_pending = true;
   uint32_t parity = 0;
@@ -341,24 +419,25 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
       if (w != 0) {
         if (threadIdx.x == 0) {
           fence_proxy_async_smem();
-          const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)a.row_elems * (uint32_t)sizeof(Elem);
-          mbar_arrive_expect_tx(&bar, bytes);
-          bulk_g2s(sm, tab + (int64_t)j0 * a.row_elems, bytes, &bar);
+          grad_stage<MIXED, CAL>(a, sm, j0, j1, &bar);
         }
         if (!mbar_wait_bounded(&bar, parity, a.status)) return;
         parity ^= 1u;
       }
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
-        Elem A[NDET][kAccPerDet];
-        grad_sums<NDET, MIXED>(a, sm, p, j0, ncut < j1 ? ncut : j1, lane, A);
+        Elem A[NDET][kAccPerDet], X[NDET];
+        if constexpr (CAL) cal_nodes_fill<NDET, MIXED>(a.theta + p * a.gstride + a.cal_par, a.nn, a.calQ, lane, nodes);
+        grad_sums<NDET, MIXED, CAL>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, A, X);
         if (ncut <= a.CH) {  // the proposal's only window (every lane holds the sums): finish it here
           const PropCommon* c = a.pc + p;
           auto Z = [&](int d, int k) { return (double)A[d][k]; };
-          if (lane == 0) a.lnl[p] = grad_lnl<NDET>(c, Z);
+          auto Xf = [&](int d) { return X[d]; };
+          if (lane == 0) a.lnl[p] = grad_lnl<NDET>(c, Z) + (CAL ? cal_lnl_term<NDET>(c, Xf) : 0.0);
           if (lane < a.n_dim) {
             const PropGrad<Elem>& g = reinterpret_cast<const PropGrad<Elem>*>(a.pg)[p];
-            a.grad[p * a.n_dim + lane] =
-                (double)grad_dir<NDET>(c, g, lane, Z, [&](int d, int k) { return A[d][2 + k]; });
+            Elem d = grad_dir<NDET>(c, g, lane, Z, [&](int dd, int k) { return A[dd][2 + k]; });
+            if constexpr (CAL) d += cal_grad_term<NDET>(c, g, lane, Xf);
+            a.grad[p * a.gstride + lane] = (double)d;
           }
           return;
         }
@@ -369,6 +448,12 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
 #pragma unroll
           for (int k2 = 0; k2 < kAccPerDet; ++k2)
             if (lane == ((d * kAccPerDet + k2) & 31)) o[d * kAccPerDet + k2] = A[d][k2];
+        if constexpr (CAL) {
+          Elem* ox = reinterpret_cast<Elem*>(a.xpart) + (p * a.nw_total + w) * NDET;
+#pragma unroll
+          for (int d = 0; d < NDET; ++d)
+            if (lane == d) ox[d] = X[d];
+        }
       });
     }
     n_w -= __ldcg(&a.hist[w]);
@@ -404,47 +489,48 @@ __device__ __forceinline__ void load_sums(const G* __restrict__ qw, G (&v)[kAccP
   }
 }
 
-template <int NDET, bool MIXED>
+// Multi-window proposals: a thread per (proposal, direction of the row).  The
+// source directions add the windows' sums (Z in FP64, the basis-weighted W in
+// working precision; with CAL also the X_d corrections); the calibration
+// directions add the windows' derivatives of k_cal_moments in window order.
+template <int NDET, bool MIXED, bool CAL>
 __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
                                 const PropGrad<typename std::conditional<MIXED, float, double>::type>* __restrict__ pg,
-                                const void* __restrict__ partials_v, int64_t B, int CH, int nw_total, int n_dim,
-                                double* __restrict__ lnl, double* __restrict__ grad) {
+                                const void* __restrict__ partials_v, const void* __restrict__ xpart_v,
+                                const void* __restrict__ cpart_v, int64_t B, int CH, int nw_total, int n_dim,
+                                int gstride, int nq, double* __restrict__ lnl, double* __restrict__ grad) {
   cudaGridDependencySynchronize();
   using G = typename std::conditional<MIXED, float, double>::type;
-  // thread per (proposal, sampled direction): the n_dim threads of a proposal
-  // are adjacent, so their loads of its window sums coincide
+  // the directions of a proposal are adjacent threads, so their loads of its window sums coincide
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t p = t / n_dim;
-  const int i = (int)(t % n_dim);
+  const int64_t p = t / gstride;
+  const int i = (int)(t % gstride);
   if (p >= B) return;
-  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
-  // window 0's sums are read beside the proposal's record rather than after
-  // it (every proposal with an in-band bin has a window 0); rows without one,
-  // or finished in the bin loop, read them but do not use them
-  G A[NDET][kAccPerDet];
-#pragma unroll
-  for (int d = 0; d < NDET; ++d) load_sums(q + d * kAccPerDet, A[d]);
   const PropCommon c = pc[p];
   if (c.flag) {
     if (i == 0) lnl[p] = -INFINITY;
-    grad[p * n_dim + i] = 0.0;
+    grad[p * gstride + i] = 0.0;
     return;
   }
   const int nwp = (c.ncut + CH - 1) / CH;
-  if (nwp == 1) return;  // finished in the bin loop
-  double Z[NDET][2];
+  if (nwp == 1) return;  // finished in the bin loops
+  if (CAL && i >= n_dim) {  // a calibration direction
+    const G* q = reinterpret_cast<const G*>(cpart_v) + (int64_t)p * nw_total * (NDET * nq) + (i - n_dim);
+    double s = 0.0;
+    for (int w = 0; w < nwp; ++w) s += (double)q[(int64_t)w * (NDET * nq)];
+    grad[p * gstride + i] = s;
+    return;
+  }
+  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
+  double Z[NDET][2], X[NDET];
   G W[NDET][2 * kNW];
-  // Z (enters lnL) is summed over windows in FP64; the basis-weighted W enter
-  // the gradient in G precision and are summed in it
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    const bool any = nwp > 0;
-    Z[d][0] = any ? (double)A[d][0] : 0.0;
-    Z[d][1] = any ? (double)A[d][1] : 0.0;
+    Z[d][0] = Z[d][1] = X[d] = 0.0;
 #pragma unroll
-    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = any ? A[d][2 + k] : (G)0;
+    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)0;
   }
-  for (int w = 1; w < nwp; ++w) {
+  for (int w = 0; w < nwp; ++w) {
 #pragma unroll
     for (int d = 0; d < NDET; ++d) {
       G v[kAccPerDet];
@@ -453,33 +539,52 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
       Z[d][1] += (double)v[1];
 #pragma unroll
       for (int k = 0; k < 2 * kNW; ++k) W[d][k] += v[2 + k];
+      if constexpr (CAL) X[d] += (double)reinterpret_cast<const G*>(xpart_v)[((int64_t)p * nw_total + w) * NDET + d];
     }
   }
   auto Zf = [&](int d, int k) { return Z[d][k]; };
-  if (i == 0) lnl[p] = grad_lnl<NDET>(&c, Zf);
-  grad[p * n_dim + i] = (double)grad_dir<NDET>(&c, pg[p], i, Zf, [&](int d, int k) { return W[d][k]; });
+  auto Xf = [&](int d) { return X[d]; };
+  if (i == 0) lnl[p] = grad_lnl<NDET>(&c, Zf) + (CAL ? cal_lnl_term<NDET>(&c, Xf) : 0.0);
+  G g = grad_dir<NDET>(&c, pg[p], i, Zf, [&](int d, int k) { return W[d][k]; });
+  if constexpr (CAL) g += cal_grad_term<NDET>(&c, pg[p], i, Xf);
+  grad[p * gstride + i] = (double)g;
 }
 
 // ---------------------------------------------------------------- launchers
-int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B) {
-  const bool mixed = c->opt.precision == GWL_MIXED;
-  (void)mixed;
-  int CH = c->grad_window;
-  if (CH > c->M) CH = (int)c->M;
+// Per-window sums of the bin loop, then (calibration model) the X_d
+// corrections and the calibration directions' per-window derivatives.
+int64_t calgrad_part_elems(const gwl_ctx* c, int64_t B);
+cudaError_t launch_cal_moments(gwl_ctx* c, int64_t B, int* ctr, const int* hist, void* cpart, double* grad,
+                               const double* theta, cudaStream_t st);
+
+static int grad_window_of(const gwl_ctx* c) { return c->grad_window > c->M ? (int)c->M : c->grad_window; }
+static int64_t grad_sums_bytes(const gwl_ctx* c, int64_t B) {
+  const int CH = grad_window_of(c);
   const int64_t nw = (c->M + CH - 1) / CH;
-  return B * nw * kAccPerDet * c->n_det * (int64_t)(mixed ? sizeof(float) : sizeof(double));
+  return B * nw * kAccPerDet * c->n_det *
+         (int64_t)(c->opt.precision == GWL_MIXED ? sizeof(float) : sizeof(double));
+}
+static int64_t grad_x_bytes(const gwl_ctx* c, int64_t B) {
+  if (!c->n_cal_nodes) return 0;
+  const int CH = grad_window_of(c);
+  return B * ((c->M + CH - 1) / CH) * c->n_det * (int64_t)(c->opt.precision == GWL_MIXED ? sizeof(float) : sizeof(double));
+}
+int64_t grad_partials_bytes(const gwl_ctx* c, int64_t B) {
+  const int64_t el = c->opt.precision == GWL_MIXED ? sizeof(float) : sizeof(double);
+  const int64_t cp = c->n_cal_nodes ? calgrad_part_elems(c, B) * el : 0;
+  return ((grad_sums_bytes(c, B) + 255) & ~255ll) + ((grad_x_bytes(c, B) + 255) & ~255ll) + cp;
 }
 int64_t prop_grad_bytes(const gwl_ctx* c) {
   return c->opt.precision == GWL_MIXED ? (int64_t)sizeof(PropGrad<float>) : (int64_t)sizeof(PropGrad<double>);
 }
 int64_t work_needed(const gwl_ctx* c, int64_t B);
 int* window_hist(const gwl_ctx* c);
+int* calgrad_counters(const gwl_ctx* c, int64_t B);
 
-template <int NDET, bool MIXED>
+template <int NDET, bool MIXED, bool CAL>
 static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
   using G = typename std::conditional<MIXED, float, double>::type;
-  int CH = c->grad_window;
-  if (CH > c->M) CH = (int)c->M;
+  const int CH = grad_window_of(c);
   const int nw_total = (int)((c->M + CH - 1) / CH);
   cudaError_t e = cudaMemsetAsync(c->d_work, 0, sizeof(int) * (size_t)work_needed(c, B), st);
   if (e != cudaSuccess) return e;
@@ -495,6 +600,9 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  char* gp = reinterpret_cast<char*>(c->d_gpartials);
+  void* xpart = gp + ((grad_sums_bytes(c, B) + 255) & ~255ll);
+  void* cpart = reinterpret_cast<char*>(xpart) + ((grad_x_bytes(c, B) + 255) & ~255ll);
   GradArgs a;
   a.tab = MIXED ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
   a.row_elems = MIXED ? c->row_floats : c->row_doubles;
@@ -512,35 +620,66 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   a.lnl = lnl;
   a.grad = grad;
   a.n_dim = c->opt.n_dim;
-  const size_t smem = (size_t)CH * a.row_elems * sizeof(G);
-  if ((e = raise_smem_limit((const void*)k_window_grad<NDET, MIXED>, c->device, smem)) != cudaSuccess) return e;
+  a.gstride = (int)theta_stride(c);
+  int64_t elems = (int64_t)CH * a.row_elems;
+  a.cal = nullptr;
+  a.cal_row = 0;
+  a.cal_smem = (int)elems;
+  a.theta = theta;
+  a.cal_par = c->opt.n_dim;
+  a.nn = c->n_cal_nodes;
+  a.calQ = nullptr;
+  a.xpart = xpart;
+  if (CAL) {
+    a.cal = MIXED ? (const void*)c->d_cal_f : (const void*)c->d_cal_d;
+    a.cal_row = MIXED ? c->row_cal_f : c->row_cal_d;
+    a.calQ = MIXED ? (const void*)c->d_calQ_f : (const void*)c->d_calQ_d;
+    elems += (int64_t)(CH + 1) * a.cal_row;  // staged in pairs
+  }
+  const size_t smem = (size_t)elems * sizeof(G);
+  if ((e = raise_smem_limit((const void*)k_window_grad<NDET, MIXED, CAL>, c->device, smem)) != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_GRAD, st);
     int64_t want = ((B + 7) / 8) * nw_total;
     int grid = c->num_sms * 2;
     if (want < grid) grid = (int)(want > 0 ? want : 1);
-    e = launch_pdl(k_window_grad<NDET, MIXED>, dim3(grid), dim3(256), smem, st, a);
+    e = launch_pdl(k_window_grad<NDET, MIXED, CAL>, dim3(grid), dim3(256), smem, st, a);
     c->launches++;
+    if (e != cudaSuccess) return e;
+  }
+  if (CAL) {
+    e = launch_cal_moments(c, B, calgrad_counters(c, B), window_hist(c), cpart, grad, theta, st);
     if (e != cudaSuccess) return e;
   }
   {
     ProfScope ps(c, GWL_KERNEL_COMBINE, st);
-    const int64_t nt = B * c->opt.n_dim;
-    e = launch_pdl(k_finalize_grad<NDET, MIXED>, dim3((unsigned)((nt + 63) / 64)), dim3(64), 0, st,
-                   (const PropCommon*)c->d_pc, (const PropGrad<G>*)c->d_pgrad, (const void*)c->d_gpartials, B, CH,
-                   nw_total, c->opt.n_dim, lnl, grad);
+    const int64_t nt = B * a.gstride;
+    e = launch_pdl(k_finalize_grad<NDET, MIXED, CAL>, dim3((unsigned)((nt + 63) / 64)), dim3(64), 0, st,
+                   (const PropCommon*)c->d_pc, (const PropGrad<G>*)c->d_pgrad, (const void*)c->d_gpartials,
+                   (const void*)xpart, (const void*)cpart, B, CH, nw_total, c->opt.n_dim, a.gstride,
+                   2 * c->n_cal_nodes, lnl, grad);
     c->launches++;
   }
   return e;
 }
 
-cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
+template <int NDET>
+static cudaError_t run_grad_any(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad,
+                                cudaStream_t st) {
   const bool mixed = c->opt.precision == GWL_MIXED;
+  if (c->n_cal_nodes)
+    return mixed ? run_grad<NDET, true, true>(c, theta, B, lnl, grad, st)
+                 : run_grad<NDET, false, true>(c, theta, B, lnl, grad, st);
+  return mixed ? run_grad<NDET, true, false>(c, theta, B, lnl, grad, st)
+               : run_grad<NDET, false, false>(c, theta, B, lnl, grad, st);
+}
+
+cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
   switch (c->n_det) {
-    case 1: return mixed ? run_grad<1, true>(c, theta, B, lnl, grad, st) : run_grad<1, false>(c, theta, B, lnl, grad, st);
-    case 2: return mixed ? run_grad<2, true>(c, theta, B, lnl, grad, st) : run_grad<2, false>(c, theta, B, lnl, grad, st);
-    case 3: return mixed ? run_grad<3, true>(c, theta, B, lnl, grad, st) : run_grad<3, false>(c, theta, B, lnl, grad, st);
-    default: return mixed ? run_grad<4, true>(c, theta, B, lnl, grad, st) : run_grad<4, false>(c, theta, B, lnl, grad, st);
+    case 1: return run_grad_any<1>(c, theta, B, lnl, grad, st);
+    case 2: return run_grad_any<2>(c, theta, B, lnl, grad, st);
+    case 3: return run_grad_any<3>(c, theta, B, lnl, grad, st);
+    default: return run_grad_any<4>(c, theta, B, lnl, grad, st);
   }
 }
 

@@ -51,6 +51,7 @@ struct gwl_ctx {
   double* d_gmc = nullptr;       // Galilean walk scratch (velocity, reflected points, gradient)
   int64_t gmc_cap = 0;           // in doubles
   int walk_kind = GWL_WALK_RANDOM;
+  double gmc_persistence = GWL_GALILEAN_PERSISTENCE;  // velocity kept per Galilean step
   double* d_io = nullptr;        // staging for the host-buffer entry points
   int64_t io_cap = 0;            // in doubles
   void* d_pgrad = nullptr;       // per-proposal tangents of the gradient prologue
@@ -137,6 +138,11 @@ int64_t lanes_list_ints(const gwl_ctx* c, int64_t B);
 int64_t lanes_slot_floats(const gwl_ctx* c, int64_t B);
 cudaError_t launch_lanes(gwl_ctx* c, int64_t B, double* lnl, int* work, int* hist, int* pdone, int* bcount, int seg,
                          cudaStream_t st);
+
+// Largest dynamic shared memory of the calibrated gradient's second bin loop
+// (the rows plus eight warps' scratch) that a window may need.
+constexpr size_t kCalGradSmemMax = 220 * 1024;
+size_t calgrad_smem(const gwl_ctx* c, int CH);
 
 // a8: log-likelihood and gradient
 cudaError_t launch_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st);

@@ -458,35 +458,10 @@ __device__ __forceinline__ double combine_lnl(const PropCommon* __restrict__ c, 
   return t - 0.5 * c->hh;
 }
 
-// Node data of proposal p for the warp's calibration splines (spline
-// s = 2 d + q, q = 0 amplitude, 1 phase; node k): the lanes first store the
-// node values y_k (the phase scaled to cycles; in the mixed path each is read
-// from theta and narrowed once, by integer operations), then form the
-// curvatures m_k = sum_i Q_ki y_i from the stored values.
+// Node data of proposal p for the warp's calibration splines (cal_nodes_fill).
 template <int NDET, bool MIXED, typename Node>
 __device__ __forceinline__ void cal_nodes(const WinArgs& a, int64_t p, int lane, Node* __restrict__ nd) {
-  using T = typename std::conditional<MIXED, float, double>::type;
-  const double* y = a.theta + p * a.stride + a.cal_par;  // [NDET][2][nn], index s nn + k
-  const T* Q = reinterpret_cast<const T*>(a.calQ);
-  const int nn = a.nn;
-  __syncwarp();  // the warp is done with the previous proposal's node data
-  for (int o = lane; o < 2 * NDET * nn; o += 32) {
-    const int sp = o / nn, k = o - sp * nn;
-    const double yd = __ldg(y + o);
-    T yv;
-    if constexpr (MIXED) yv = ff_from(yd).hi;
-    else yv = yd;
-    reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k])[2 * (sp & 1)] = (sp & 1) ? yv * (T)(0.5 / kPi) : yv;
-  }
-  __syncwarp();
-  for (int o = lane; o < 2 * NDET * nn; o += 32) {
-    const int sp = o / nn, k = o - sp * nn;
-    const T* ys = reinterpret_cast<const T*>(&nd[(sp >> 1) * kMaxCalNodes]) + 2 * (sp & 1);  // stride 4 T
-    T m = (T)0;
-    for (int i = 0; i < nn; ++i) m = fma(Q[k * nn + i], ys[4 * i], m);
-    reinterpret_cast<T*>(&nd[(sp >> 1) * kMaxCalNodes + k])[2 * (sp & 1) + 1] = m;
-  }
-  __syncwarp();
+  cal_nodes_fill<NDET, MIXED>(a.theta + p * a.stride + a.cal_par, a.nn, a.calQ, lane, nd);
 }
 
 // The FP64-phase mixed mode (GWL_MIXED_F64PHASE): per bin the FP64 phase
@@ -882,9 +857,11 @@ static int64_t nw_max(const gwl_ctx* c) {
 // [0] largest cut, [1 + w] proposal (or item) counter of window w,
 // [1 + nw_max + w] histogram of last windows, [1 + 2 nw_max + p] windows (or
 // chunks) of proposal p summed, [1 + 2 nw_max + B + K] bucket counts of the
-// lane kernel (chunks of at least 32 bins).
-int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 2 * nw_max(c) + B + (c->M + 31) / 32; }
+// lane kernel (chunks of at least 32 bins), then the window counters of the
+// calibrated gradient's second bin loop.
+int64_t work_needed(const gwl_ctx* c, int64_t B) { return 1 + 3 * nw_max(c) + B + (c->M + 31) / 32; }
 int* window_hist(const gwl_ctx* c) { return c->d_work + 1 + nw_max(c); }
+int* calgrad_counters(const gwl_ctx* c, int64_t B) { return c->d_work + 1 + 2 * nw_max(c) + B + (c->M + 31) / 32; }
 
 template <int NDET, bool MIXED, bool CAL, bool F64PH = false>
 static cudaError_t run_window(gwl_ctx* c, const WinArgs& a, int grid, size_t smem, bool pdl, cudaStream_t st) {

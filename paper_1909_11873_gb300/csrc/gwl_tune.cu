@@ -7,6 +7,7 @@
 // caller's own batch and keeps the fastest.  Only public entry points are
 // called; every launch goes through gwl_loglike / gwl_grad.
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "gwl_internal.h"
@@ -83,17 +84,21 @@ extern "C" int gwl_autotune(gwl_ctx* c, const double* theta_dev, int64_t B, int 
     return ws;
   };
   const bool mixed = c->opt.precision == GWL_MIXED;
-  if ((what & GWL_TUNE_GRAD) && c->n_cal_nodes)
-    return gwl::set_error(GWL_ERR_ARG, "autotune: gwl_grad is not available with the calibration model");
   if ((what & GWL_TUNE_GRAD) && c->opt.precision == GWL_MIXED_F64PHASE)
     return gwl::set_error(GWL_ERR_ARG, "autotune: gwl_grad is not available in GWL_MIXED_F64PHASE");
   const std::vector<int> windows = candidates(gwl::lnl_row_bytes(c));
-  const std::vector<int> gwindows =
-      candidates(mixed ? sizeof(float) * c->row_floats : sizeof(double) * c->row_doubles);
+  // gradient rows carry the calibration rows too, and the moment pass stages one window of them
+  std::vector<int> gwindows =
+      candidates(mixed ? sizeof(float) * (c->row_floats + (c->n_cal_nodes ? c->row_cal_f : 0))
+                       : sizeof(double) * (c->row_doubles + (c->n_cal_nodes ? c->row_cal_d : 0)));
+  if (c->n_cal_nodes)
+    gwindows.erase(std::remove_if(gwindows.begin(), gwindows.end(),
+                                  [&](int w) { return gwl::calgrad_smem(c, w) > gwl::kCalGradSmemMax; }),
+                   gwindows.end());
   if (windows.empty() || gwindows.empty()) return gwl::set_error(GWL_ERR_ARG, "autotune: no window fits");
 
   double* d_out = nullptr;
-  const int64_t n_out = B * (1 + c->opt.n_dim);
+  const int64_t n_out = B * (1 + c->seg.stride);
   cudaError_t e = cudaMalloc(&d_out, sizeof(double) * (size_t)n_out);
   if (e != cudaSuccess) return gwl::set_error(GWL_ERR_NOMEM, "autotune: %s", cudaGetErrorString(e));
   Timer t;

@@ -175,6 +175,14 @@ __device__ __forceinline__ double prior_jac(int kind, double lo, double hi, doub
   }
 }
 
+// d theta / d u of walk coordinate i at theta: the source priors above, or for
+// a calibration parameter theta = sigma Phi^{-1}(u): sigma sqrt(2 pi) e^{z^2/2}, z = theta / sigma.
+__device__ __forceinline__ double coord_jac(const PriorInfo& pr, int i, double th) {
+  if (i < pr.n_src) return prior_jac(pr.kind[i], pr.lo[i], pr.hi[i], th);
+  const double sg = pr.cal_sigma[((i - pr.n_src) / pr.nn) & 1], z = th / sg;
+  return sg * 2.5066282746310002 * exp(0.5 * z * z);
+}
+
 __global__ void k_gmc_init(PriorInfo pr, const double* __restrict__ live_u, const double* __restrict__ live_lnl,
                            int64_t K, const WalkScalars* __restrict__ sc, const double* __restrict__ chol,
                            uint64_t seed, int64_t n_chains, double* __restrict__ cu, double* __restrict__ cl,
@@ -190,7 +198,7 @@ __global__ void k_gmc_init(PriorInfo pr, const double* __restrict__ live_u, cons
   cl[b] = live_lnl[st];
   cn[b] = 0;
   if (cstart) cstart[b] = (int32_t)st;
-  double z[11];
+  double z[kMaxWalkDim];
   walk_normals(seed, sc->counter, (uint32_t)b, 0x40000000u, D, z);
   for (int i = 0; i < D; ++i) {
     double dz = 0.0;
@@ -199,27 +207,52 @@ __global__ void k_gmc_init(PriorInfo pr, const double* __restrict__ live_u, cons
   }
 }
 
-// x1 = u + v; theta1 (NaN rows outside the cube)
-__global__ void k_gmc_step1(PriorInfo pr, int64_t n_chains, const double* __restrict__ cu,
-                            const double* __restrict__ vel, double* __restrict__ x1, double* __restrict__ th1) {
+// From the second step on, the velocity is partly refreshed,
+//   v <- rho v + sqrt(1 - rho^2) scale L z  (z: the normals of this step's word),
+// which keeps its distribution N(0, scale^2 L L^T); then x1 = u + v and
+// theta1 (NaN rows outside the cube).
+__global__ void k_gmc_step1(PriorInfo pr, const WalkScalars* __restrict__ sc, const double* __restrict__ chol,
+                            uint64_t seed, uint32_t step, double rho, int64_t n_chains,
+                            const double* __restrict__ cu, double* __restrict__ vel, double* __restrict__ x1,
+                            double* __restrict__ th1) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_chains) return;
   const int D = pr.D;
+  if (step > 1 && rho < 1.0) {
+    double z[kMaxWalkDim];
+    walk_normals(seed, sc->counter, (uint32_t)b, step, D, z);
+    const double a = sqrt(1.0 - rho * rho) * sc->scale;
+    for (int i = 0; i < D; ++i) {
+      double dz = 0.0;
+      for (int k = 0; k <= i; ++k) dz += chol[i * D + k] * z[k];
+      vel[b * D + i] = rho * vel[b * D + i] + a * dz;
+    }
+  }
   bool inside = true;
   for (int i = 0; i < D; ++i) {
     double x = cu[b * D + i] + vel[b * D + i];
-    if (pr.periodic[i]) x -= floor(x);
+    if (coord_periodic(pr, i)) x -= floor(x);
     else if (x < 0.0 || x > 1.0) inside = false;
     x1[b * D + i] = x;
   }
-  for (int i = 0; i < D; ++i) th1[b * D + i] = inside ? prior_map(pr.kind[i], pr.lo[i], pr.hi[i], x1[b * D + i]) : NAN;
+  for (int i = 0; i < D; ++i) th1[b * D + i] = inside ? coord_map(pr, i, x1[b * D + i]) : NAN;
 }
 
-// accept x1, or reflect: writes theta2 for the chains that reflect off the contour (NaN otherwise)
+// Accept x1, or reflect off the surface at x1 and set up the second trial.
+// The surface is the likelihood contour when x1 is inside the cube (normal g:
+// the gradient of lnL in the unit cube, chain rule through the coordinate
+// maps) and the walls x1 crossed when it is not (g: their outward unit
+// normals summed) -- either way a function of x1 alone.  The reflection is
+// taken in the metric of the step covariance Sigma = L L^T,
+//   v' = v - 2 (v.g) / (g.Sigma g) Sigma g,  Sigma g = L (L^T g),
+// so that it keeps the velocity distribution and undoes itself.  v' goes to
+// vel2 and theta2 = theta(x1 + v') is written for the chains that try x2.
+// mode: 0 moved to x1; 1 try x2; 2 stay and reverse v.
 __global__ void k_gmc_reflect(PriorInfo pr, const WalkScalars* __restrict__ sc, int64_t n_chains,
-                              const double* __restrict__ x1, const double* __restrict__ th1,
-                              const double* __restrict__ l1, const double* __restrict__ g1, double* __restrict__ cu,
-                              double* __restrict__ cl, int32_t* __restrict__ cn, double* __restrict__ vel,
+                              const double* __restrict__ chol, const double* __restrict__ x1,
+                              const double* __restrict__ th1, const double* __restrict__ l1,
+                              const double* __restrict__ g1, double* __restrict__ cu, double* __restrict__ cl,
+                              int32_t* __restrict__ cn, const double* __restrict__ vel, double* __restrict__ vel2,
                               double* __restrict__ x2, double* __restrict__ th2, int32_t* __restrict__ mode) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_chains) return;
@@ -227,57 +260,64 @@ __global__ void k_gmc_reflect(PriorInfo pr, const WalkScalars* __restrict__ sc, 
   bool inside = true;
   for (int i = 0; i < D; ++i) inside = inside && !isnan(th1[b * D + i]);
   for (int i = 0; i < D; ++i) th2[b * D + i] = NAN;
-  mode[b] = 0;
   if (inside && l1[b] >= sc->lstar) {  // move
     for (int i = 0; i < D; ++i) cu[b * D + i] = x1[b * D + i];
     cl[b] = l1[b];
     cn[b] += 1;
+    mode[b] = 0;
     return;
   }
-  if (!inside) {  // bounce off the cube walls
-    for (int i = 0; i < D; ++i) {
-      const double x = cu[b * D + i] + vel[b * D + i];
-      if (!pr.periodic[i] && (x < 0.0 || x > 1.0)) vel[b * D + i] = -vel[b * D + i];
-    }
-    return;
-  }
-  // reflect off the likelihood contour at x1
-  double n[11], nn = 0.0;
+  double g[kMaxWalkDim], m[kMaxWalkDim];
   for (int i = 0; i < D; ++i) {
-    n[i] = g1[b * D + i] * prior_jac(pr.kind[i], pr.lo[i], pr.hi[i], th1[b * D + i]);
-    nn += n[i] * n[i];
+    const double x = x1[b * D + i];
+    g[i] = inside ? g1[b * D + i] * coord_jac(pr, i, th1[b * D + i])
+                  : (coord_periodic(pr, i) ? 0.0 : (x > 1.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0)));
   }
-  if (!(nn > 0.0) || !isfinite(nn)) {
-    for (int i = 0; i < D; ++i) vel[b * D + i] = -vel[b * D + i];
+  double gsg = 0.0, vg = 0.0;
+  for (int k = 0; k < D; ++k) {  // m = L^T g
+    double t = 0.0;
+    for (int i = k; i < D; ++i) t += chol[i * D + k] * g[i];
+    m[k] = t;
+    gsg += t * t;
+    vg += vel[b * D + k] * g[k];
+  }
+  if (!(gsg > 0.0) || !isfinite(gsg) || !isfinite(vg)) {
+    mode[b] = 2;
     return;
   }
-  double vn = 0.0;
-  for (int i = 0; i < D; ++i) vn += vel[b * D + i] * n[i];
+  const double f = 2.0 * vg / gsg;
   bool in2 = true;
   for (int i = 0; i < D; ++i) {
-    const double v2 = vel[b * D + i] - 2.0 * vn * n[i] / nn;
+    double sgi = 0.0;  // (Sigma g)_i = (L m)_i
+    for (int k = 0; k <= i; ++k) sgi += chol[i * D + k] * m[k];
+    const double v2 = vel[b * D + i] - f * sgi;
     double x = x1[b * D + i] + v2;
-    if (pr.periodic[i]) x -= floor(x);
+    if (coord_periodic(pr, i)) x -= floor(x);
     else if (x < 0.0 || x > 1.0) in2 = false;
     x2[b * D + i] = x;
-    vel[b * D + i] = v2;  // tentatively reflected; undone below if x2 fails
+    vel2[b * D + i] = v2;
   }
   if (!in2) {
-    for (int i = 0; i < D; ++i) vel[b * D + i] = -vel[b * D + i];
-    mode[b] = 2;  // the reflected velocity reversed; nothing to evaluate
+    mode[b] = 2;
     return;
   }
-  for (int i = 0; i < D; ++i) th2[b * D + i] = prior_map(pr.kind[i], pr.lo[i], pr.hi[i], x2[b * D + i]);
+  for (int i = 0; i < D; ++i) th2[b * D + i] = coord_map(pr, i, x2[b * D + i]);
   mode[b] = 1;
 }
 
+// Move to x2 with v' (mode 1, lnL(x2) >= L*), or stay and reverse v (mode 1
+// below L*, mode 2).
 __global__ void k_gmc_step2(int D, const WalkScalars* __restrict__ sc, int64_t n_chains, const double* __restrict__ x2,
-                            const double* __restrict__ l2, const int32_t* __restrict__ mode, double* __restrict__ cu,
-                            double* __restrict__ cl, int32_t* __restrict__ cn, double* __restrict__ vel) {
+                            const double* __restrict__ l2, const int32_t* __restrict__ mode,
+                            const double* __restrict__ vel2, double* __restrict__ cu, double* __restrict__ cl,
+                            int32_t* __restrict__ cn, double* __restrict__ vel) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_chains || mode[b] != 1) return;
-  if (l2[b] >= sc->lstar) {
-    for (int i = 0; i < D; ++i) cu[b * D + i] = x2[b * D + i];
+  if (b >= n_chains || mode[b] == 0) return;
+  if (mode[b] == 1 && l2[b] >= sc->lstar) {
+    for (int i = 0; i < D; ++i) {
+      cu[b * D + i] = x2[b * D + i];
+      vel[b * D + i] = vel2[b * D + i];
+    }
     cl[b] = l2[b];
     cn[b] += 1;
   } else {
@@ -788,9 +828,11 @@ static cudaError_t launch_gmc(gwl_ctx* c, const double* live_u, const double* li
   const int D = (int)theta_stride(c);
   const unsigned nb = (unsigned)((n_chains + 127) / 128);
   const PriorInfo pr = prior_info(c);
-  // scratch after the random-walk proposal buffers: velocity, x2, theta2, gradient, l2, mode
+  // scratch after the random-walk proposal buffers: velocity, reflected velocity, x2, theta2, gradient,
+  // l2, mode
   double* vel = c->d_gmc;
-  double* x2 = vel + n_chains * D;
+  double* vel2 = vel + n_chains * D;
+  double* x2 = vel2 + n_chains * D;
   double* th2 = x2 + n_chains * D;
   double* g1 = th2 + n_chains * D;
   double* l2 = g1 + n_chains * D;
@@ -803,23 +845,24 @@ static cudaError_t launch_gmc(gwl_ctx* c, const double* live_u, const double* li
   }
   cudaError_t e = cudaGetLastError();
   for (int s = 1; s <= walk_len && e == cudaSuccess; ++s) {
-    k_gmc_step1<<<nb, 128, 0, st>>>(pr, n_chains, out_u, vel, pu, pth);
+    k_gmc_step1<<<nb, 128, 0, st>>>(pr, sc, chol, seed, (uint32_t)s, c->gmc_persistence, n_chains, out_u, vel, pu,
+                                    pth);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = launch_grad(c, pth, n_chains, plnl, g1, st)) != cudaSuccess) break;
-    k_gmc_reflect<<<nb, 128, 0, st>>>(pr, sc, n_chains, pu, pth, plnl, g1, out_u, out_lnl, out_nacc, vel, x2, th2,
-                                      mode);
+    k_gmc_reflect<<<nb, 128, 0, st>>>(pr, sc, n_chains, chol, pu, pth, plnl, g1, out_u, out_lnl, out_nacc, vel,
+                                      vel2, x2, th2, mode);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = launch_loglike(c, th2, n_chains, l2, st)) != cudaSuccess) break;
-    k_gmc_step2<<<nb, 128, 0, st>>>(D, sc, n_chains, x2, l2, mode, out_u, out_lnl, out_nacc, vel);
+    k_gmc_step2<<<nb, 128, 0, st>>>(D, sc, n_chains, x2, l2, mode, vel2, out_u, out_lnl, out_nacc, vel);
     c->launches++;
     e = cudaGetLastError();
   }
   return e;
 }
 
-size_t gmc_scratch_doubles(int64_t n_chains, int D) { return (size_t)n_chains * (4 * D + 2); }
+size_t gmc_scratch_doubles(int64_t n_chains, int D) { return (size_t)n_chains * (5 * D + 2); }
 
 cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t K, const void* scalars,
                         uint64_t seed, int64_t n_chains, int walk_len, const double* chol, double* out_u,

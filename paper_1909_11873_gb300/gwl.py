@@ -28,11 +28,12 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
            "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
-           "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
+           "gwl_set_galilean", "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
            "gwl_test_wait_timeout", "gwl_test_philox",
            "gwl_test_ffdelta_blocks")
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
+GWL_GALILEAN_PERSISTENCE = 0.5
 KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
 GWL_TUNE_LOGLIKE = 1
 GWL_TUNE_GRAD = 2
@@ -108,6 +109,7 @@ def lib() -> C.CDLL:
         L.gwl_test_ffdelta_blocks.argtypes = [P, i32, C.POINTER(i64)]
         L.gwl_get_calibration.argtypes = [P, C.POINTER(i32), C.POINTER(i64)]
         L.gwl_set_walk.argtypes = [P, i32]
+        L.gwl_set_galilean.argtypes = [P, C.c_double]
         L.gwl_profile.argtypes = [P, i32]
         L.gwl_profile_read.argtypes = [P, i32, C.POINTER(d), C.POINTER(i64)]
         L.gwl_device_bytes.argtypes = [P]
@@ -279,6 +281,9 @@ class Context:
     def gwl_set_walk(self, kind: int):
         _check(lib().gwl_set_walk(self._h, int(kind)), "gwl_set_walk")
 
+    def gwl_set_galilean(self, persistence: float):
+        _check(lib().gwl_set_galilean(self._h, float(persistence)), "gwl_set_galilean")
+
     def gwl_set_tuning(self, window=0, ctas_per_sm=0, grad_window=0, bin_kernel=0, lane_chunk=0):
         t = GwlTuning(int(window), int(ctas_per_sm), int(grad_window), 0.0, 0.0, 0, int(bin_kernel), int(lane_chunk))
         _check(lib().gwl_set_tuning(self._h, C.byref(t)), "gwl_set_tuning")
@@ -368,7 +373,8 @@ def waveform(ctx: Context, theta, stream=None):
 
 
 def grad(ctx: Context, theta, stream=None):
-    """(lnL [B], d lnL / d theta [B, n_dim]) via gwl_grad."""
+    """(lnL [B], d lnL / d theta [B, theta_stride]) via gwl_grad (theta_stride: n_dim, plus the
+    calibration parameters with the calibration model)."""
     import torch
     out = torch.empty(theta.shape[0], dtype=torch.float64, device=theta.device)
     g = torch.empty_like(theta)

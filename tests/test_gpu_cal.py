@@ -163,20 +163,17 @@ def test_calibration_edge_rows_and_entry_points(precision):
 
 
 def test_calibration_refused_where_not_modelled():
-    """gwl_grad, the Galilean walk and multi-event batches refuse a calibrated context (GWL_ERR_ARG);
-    invalid node sets and prior widths are refused."""
+    """Multi-event batches refuse a calibrated context and the FP64-phase arm refuses the model
+    (GWL_ERR_ARG); invalid node sets and prior widths are refused."""
     g = gwl()
     ev = event("c2")
     ctx = cal_context(ev, I.cal_node_freqs(20.0, 1024.0), 1)
-    th = torch.zeros((4, ctx.theta_stride), dtype=torch.float64, device="cuda")
-    with pytest.raises(g.GwlError, match="calibration"):
-        g.grad(ctx, th)
-    ctx.gwl_set_walk(g.GWL_WALK_GALILEAN)
-    with pytest.raises(g.GwlError, match="calibration"):
-        ctx.ns_run(64, 64, 4, 1)
-    ctx.gwl_set_walk(g.GWL_WALK_RANDOM)
     with pytest.raises(g.GwlError, match="calibration"):
         g.MultiContext([ctx])
+    f64ph = g.Context.from_event(ev, g.GWL_MIXED_F64PHASE)
+    with pytest.raises(g.GwlError):
+        f64ph.gwl_set_calibration(I.cal_node_freqs(20.0, 1024.0))
+    assert f64ph.gwl_get_calibration()[0] == 0
     for bad in ([20.0], [20.0, 20.0, 30.0], [-1.0, 30.0], np.geomspace(20, 1024, 17)):
         with pytest.raises(g.GwlError):
             ctx.gwl_set_calibration(bad)

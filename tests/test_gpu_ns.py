@@ -136,6 +136,47 @@ def test_galilean_walk_properties():
     assert np.all(ref >= ll[worst] - 1e-3)
 
 
+def top_live_set(ev, K, seed, n_draw=4096):
+    """The K best of n_draw prior points: a live set well inside the prior, so that walks meet the contour."""
+    u, ll = live_set(ev, n_draw, seed)
+    keep = np.argsort(ll)[-K:]
+    return np.ascontiguousarray(u[keep]), np.ascontiguousarray(ll[keep])
+
+
+@pytest.mark.parametrize("cfg,persistence", [("c1", 1.0), ("c1", 0.5), ("c1", 0.0), ("c2", 0.5)])
+def test_galilean_ns_replace_replays_oracle_walk_fp64(cfg, persistence):
+    """The Galilean walk against the oracle's (same Philox stream, FP64 likelihood and gradient), with the
+    step matrix of the live set's covariance (anisotropic reflections) and a live set that is the best
+    128 of 4096 prior points (reflections off the contour and the walls): identical start points and move
+    counts, end points to 1e-9."""
+    from paper_1909_11873_gb300 import gwl
+    ev = event(cfg)
+    u, ll = top_live_set(ev, 128, 8)
+    worst = int(np.argmin(ll))
+    D = ev.sampling.D
+    chol = np.linalg.cholesky(np.cov(u.T) + 1e-12 * np.eye(D))
+    n, wl, seed, ctr, scale = 96, 12, 0x6A11, 4, 0.5
+    ctx = gwl.Context.from_event(ev, 0)
+    ctx.gwl_set_walk(gwl.GWL_WALK_GALILEAN)
+    ctx.gwl_set_galilean(persistence)
+    ou = torch.zeros((n, D), dtype=torch.float64, device="cuda")
+    ol = torch.zeros(n, dtype=torch.float64, device="cuda")
+    on = torch.zeros(n, dtype=torch.int32, device="cuda")
+    os_ = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ctx.ns_replace(torch.from_numpy(u).cuda(), torch.from_numpy(ll).cuda(), worst, ll[worst], seed, ctr, n, wl, scale,
+                   torch.from_numpy(chol).cuda(), ou, ol, on, os_)
+    torch.cuda.synchronize()
+    ctx.gwl_sync()
+    gu, gl, gn, gs = ou.cpu().numpy(), ol.cpu().numpy(), on.cpu().numpy(), os_.cpu().numpy()
+    ru, rl, rn, rs = oracle.gmc_replace(ev, ev.sampling, u, ll, worst, ll[worst], seed, ctr, n, wl, scale, chol,
+                                        persistence=persistence)
+    assert np.array_equal(gs, rs)
+    assert np.array_equal(gn, rn)
+    assert np.allclose(gu, ru, rtol=0, atol=1e-9)
+    assert np.allclose(gl, rl, rtol=0, atol=1e-6)
+    assert 0 < gn.sum() < n * wl  # moves, and some steps that do not move
+
+
 def test_ns_run_galilean_c1_lnz_matches_oracle():
     from paper_1909_11873_gb300 import gwl
     ev = event("c1")
