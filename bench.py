@@ -51,7 +51,7 @@ METRIC = "lnL evals/s (BBH 3-det 8s, 11-D)"
 CONFIG = "c2"
 BATCH = 8192
 SEED = 2
-LEGS = ("fp64", "fp64ph", "grad", "cal", "c1", "c3", "c4", "c5", "ns")
+LEGS = ("fp64", "fp64ph", "grad", "cal", "calgrad", "c1", "c3", "c4", "c5", "ns")
 
 # Algorithmic work of the mixed likelihood bin loop per in-band (proposal, bin)
 # pair with 3 detectors, counted from the arithmetic the kernel carries out
@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--legs", default=",".join(LEGS), help="extra measurements to run (comma list; '' for none)")
-    ap.add_argument("--profile-only", default="", choices=["", "lnl", "grad", "cal", "fp64ph"],
+    ap.add_argument("--profile-only", default="", choices=["", "lnl", "grad", "cal", "calgrad", "fp64ph"],
                     help="run one workload --warmup + --steps times without timing and exit (for profiler captures): "
                          "lnl = the headline likelihood, grad = the 4096-proposal gradient, cal = the calibrated "
                          "likelihood, fp64ph = the FP64-phase mixed arm")
@@ -330,6 +330,41 @@ def leg_grad(ev, args, flush, stream, n_sm, fclk):
     bound, pipes = pipe_roofline(PIPES_GRAD, in_band_pairs(ev, th), kms / kn, n_sm, fclk, B)
     return {"v": B / (ms * 1e-3), "ms": ms, "B": B, "win": tuning["grad_window"], "kernel_ms": kms / kn,
             "bound": bound, "frac": pipes[bound]["frac"], "fp32_frac": pipes["fp32_flop"]["frac"]}
+
+
+def leg_calgrad(ev, args, flush, stream):
+    """grad lnL evals/s with the calibration model (71 parameters per row: the gradient's row is the same
+    size) on 4096 proposals of the same data; device time per call and the two bin passes' kernel times."""
+    import torch
+
+    from paper_1909_11873_gb300 import gwl
+
+    B = 4096
+    th = I.calibrated_proposals(ev, B, SEED + 13)
+    rows = np.ascontiguousarray(np.concatenate([I.reduced(th[:, :11], ev.sampling), th[:, 11:]], axis=1))
+    x = torch.from_numpy(rows).cuda()
+    ctx = gwl.Context.from_event(ev, gwl.GWL_MIXED)
+    ctx.gwl_set_calibration(I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1])))
+    tuning = ctx.gwl_autotune(x, gwl.GWL_TUNE_GRAD, stream)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(x)
+    for _ in range(args.warmup):
+        ctx.gwl_grad(x, out, g, stream)
+    torch.cuda.synchronize()
+    steps = max(10, args.steps // 2)
+    ms = time_device(lambda: ctx.gwl_grad(x, out, g, stream), steps, flush, stream)
+    ctx.gwl_profile(True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        ctx.gwl_grad(x, out, g, stream)
+    torch.cuda.synchronize()
+    gms, gn = ctx.gwl_profile_read(gwl.KERNEL_GRAD)
+    cms, cn = ctx.gwl_profile_read(gwl.KERNEL_CALGRAD)
+    ctx.gwl_profile(False)
+    ctx.gwl_sync()
+    ctx.close()
+    return {"v": B / (ms * 1e-3), "ms": ms, "dim": int(rows.shape[1]), "win": tuning["grad_window"],
+            "grad_bins_ms": gms / max(gn, 1), "cal_moments_ms": cms / max(cn, 1)}
 
 
 def leg_cal(ev, args, flush, stream, n_sm, fclk):
@@ -665,6 +700,8 @@ def run_gwl(args):
         legres["grad_c5"] = leg_grad(ev, args, flush, stream, n_sm, fclk)
     if "cal" in legs:
         legres["cal_c2"] = leg_cal(ev, args, flush, stream, n_sm, fclk)
+    if "calgrad" in legs:
+        legres["calgrad_c2"] = leg_calgrad(ev, args, flush, stream)
     if "c1" in legs:
         legres["c1"] = lnl_rates(device_event("c1"), 1024, 1, args, flush, stream,
                                  (("mixed", gwl.GWL_MIXED), ("fp64", gwl.GWL_FP64)), local_fraction=0.0)
@@ -700,6 +737,9 @@ def compact_legs(legres, checks):
         L["grad_c5"] = [g("grad_c5")["v"], g("grad_c5")["kernel_ms"], g("grad_c5")["frac"]]
     if g("cal_c2"):
         L["cal_c2"] = [g("cal_c2")["v"], g("cal_c2")["kernel_ms"], g("cal_c2")["frac"]]
+    if g("calgrad_c2"):
+        c = g("calgrad_c2")
+        L["calgrad_c2"] = [c["v"], c["ms"], c["grad_bins_ms"], c["cal_moments_ms"]]
     for k in ("c1", "c3"):
         if g(k):
             L[k] = [g(k)["mixed"], g(k)["fp64"]]
@@ -858,22 +898,23 @@ def run_profile_only(args):
     ev = device_event(args.profile_config)
     prec = {"fp64ph": gwl.GWL_MIXED_F64PHASE}.get(args.profile_only, gwl.GWL_MIXED)
     ctx = gwl.Context.from_event(ev, prec)
-    B = 4096 if args.profile_only == "grad" else (2048 if args.profile_config == "c3" else BATCH)
-    if args.profile_only == "cal":
-        th = I.calibrated_proposals(ev, B, SEED + 11)
+    grad = args.profile_only in ("grad", "calgrad")
+    B = 4096 if grad else (2048 if args.profile_config == "c3" else BATCH)
+    if args.profile_only in ("cal", "calgrad"):
+        th = I.calibrated_proposals(ev, B, SEED + (13 if grad else 11))
         rows = np.concatenate([I.reduced(th[:, :11], ev.sampling), th[:, 11:]], axis=1)
         ctx.gwl_set_calibration(I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1])))
     else:
-        rows = I.reduced(I.proposals(ev, B, SEED + (7 if args.profile_only == "grad" else 0)), ev.sampling)
+        rows = I.reduced(I.proposals(ev, B, SEED + (7 if grad else 0)), ev.sampling)
     if args.shape:
         w, c = (int(v) for v in args.shape.split(","))
-        ctx.gwl_set_tuning(window=w if args.profile_only != "grad" else 0, ctas_per_sm=c,
-                           grad_window=w if args.profile_only == "grad" else 0, bin_kernel=args.bin_kernel)
+        ctx.gwl_set_tuning(window=0 if grad else w, ctas_per_sm=c, grad_window=w if grad else 0,
+                           bin_kernel=args.bin_kernel)
     x = torch.from_numpy(np.ascontiguousarray(rows)).cuda()
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     g = torch.empty_like(x)
     for _ in range(args.warmup + args.steps):
-        if args.profile_only == "grad":
+        if grad:
             ctx.gwl_grad(x, out, g)
         else:
             ctx.gwl_loglike(x, out)

@@ -466,7 +466,8 @@ int gwl_autotune(gwl_ctx* ctx, const double* theta_dev, int64_t B, int what, gwl
 #define GWL_KERNEL_COMBINE 2  /* per-proposal combination */
 #define GWL_KERNEL_GRAD 3     /* windowed bin loop of gwl_grad */
 #define GWL_KERNEL_WALK 4     /* random-walk proposal/accept steps of ns_replace */
-#define GWL_KERNEL_KINDS 5
+#define GWL_KERNEL_CALGRAD 5  /* calibration-moment pass of gwl_grad (calibration model) */
+#define GWL_KERNEL_KINDS 6
 
 /* Enable (1) or disable (0) per-kernel timing: while enabled, the library
  * records a CUDA event pair around every launch of its kernels on the launch

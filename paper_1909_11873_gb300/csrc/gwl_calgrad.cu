@@ -434,7 +434,7 @@ static cudaError_t run_cal_moments(gwl_ctx* c, int64_t B, int* ctr, const int* h
   const int64_t want = ((B + 7) / 8) * a.nw_total;
   int grid = c->num_sms;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
-  ProfScope ps(c, GWL_KERNEL_GRAD, st);
+  ProfScope ps(c, GWL_KERNEL_CALGRAD, st);
   k_cal_moments<NDET, MIXED><<<grid, 256, smem, st>>>(a);
   c->launches++;
   return cudaGetLastError();

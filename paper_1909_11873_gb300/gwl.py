@@ -34,7 +34,7 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
 GWL_WALK_RANDOM = 0
 GWL_WALK_GALILEAN = 1
 GWL_GALILEAN_PERSISTENCE = 0.5
-KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK = range(5)
+KERNEL_PROLOGUE, KERNEL_BINS, KERNEL_COMBINE, KERNEL_GRAD, KERNEL_WALK, KERNEL_CALGRAD = range(6)
 GWL_TUNE_LOGLIKE = 1
 GWL_TUNE_GRAD = 2
 GWL_BINS_AUTO, GWL_BINS_WARP, GWL_BINS_LANE = 1, 2, 3
