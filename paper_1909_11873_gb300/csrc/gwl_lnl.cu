@@ -685,34 +685,129 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
   uint32_t parity = 0;
   cudaGridDependencySynchronize();  // the prologue's outputs are visible past this point
 
+  // Each warp takes its first claim in window 0 at once (the window's rows are
+  // being staged already), so that the claim's round trip overlaps the reads
+  // that place the CTA among the windows instead of following them.
+  const int64_t b_cap = a.B < 0x7fffffff ? a.B : 0x7fffffff;
+  const int chunk0 = claim_size(a.B, (int)b_cap);
+  int first = 0;
+  if (lane == 0) first = atomicAdd(a.work + 1, chunk0);
   const int maxn = a.work[0];
   int nw = (maxn + a.CH - 1) / a.CH;
   if (nw > a.nw_total) nw = a.nw_total;
-  int n_w = 0;
-  int w = nw < 1 ? 0 : start_window(a.hist, 0, nw, blockIdx.x, gridDim.x, &n_w);
+  // one window: every CTA works in it, on all the proposals
+  int n_w = (int)b_cap;
+  int w = nw > 1 ? start_window(a.hist, 0, nw, blockIdx.x, gridDim.x, &n_w) : 0;
+  auto window_end = [&](int ww) {
+    int64_t e = (int64_t)ww * a.CH + a.CH;
+    if (e > a.M) e = a.M;
+    if (e > maxn) e = maxn;
+    return (int)e;
+  };
+
+  // the proposal body of the drain: sums over [j0, j1) of window ww, then the
+  // combination (a proposal with one window) or the window's partial sums
+  auto body = [&](int ww, int j0, int j1, int64_t p, int ncut) {
+    Acc U[NDET], V[NDET], X[NDET];
+    if constexpr (CAL) cal_nodes<NDET, MIXED>(a, p, lane, nodes);
+    window_sums<NDET, MIXED, CAL, F64PH>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, U, V, X);
+    const int nwp = (ncut + a.CH - 1) / a.CH;
+    if (nwp == 1) {  // the proposal's only window: queue it for the CTA's next combination
+      int slot = 0;
+      if (lane == 0) slot = atomicAdd(&s_npend, 1);
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot < kPendCap) {
+        if (lane == 0) {
+          s_pend[slot].p = p;
+#pragma unroll
+          for (int d = 0; d < NDET; ++d) {
+            s_pend[slot].U[d] = U[d];
+            s_pend[slot].V[d] = V[d];
+            if constexpr (CAL) s_pend[slot].X[d] = X[d];
+          }
+        }
+      } else {  // queue full: combine here
+        const double l = combine_lnl<NDET, CAL>(a.pc + p, U, V, X, lane);
+        if (lane == 0) a.lnl[p] = l;
+      }
+      return;
+    }
+    // several windows: publish this one; the warp that closes the last one combines
+    int done = 0;
+    if (lane == 0) {
+      Acc* o = reinterpret_cast<Acc*>(a.partials) + (p * a.nw_total + ww) * (S * NDET);
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        o[S * d] = U[d];
+        o[S * d + 1] = V[d];
+        if constexpr (CAL) o[S * d + 2] = X[d];
+      }
+      __threadfence();
+      done = atomicAdd(&a.pdone[p], 1);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done != nwp - 1) return;
+    __threadfence();
+    // lanes take windows lane, lane + 32, ...; a fixed shuffle tree then sums
+    // the lanes (FP64, the same order whichever warp closes the proposal)
+    const Acc* q = reinterpret_cast<const Acc*>(a.partials) + p * a.nw_total * (S * NDET);
+    double Ud[NDET], Vd[NDET], Xd[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = Xd[d] = 0.0;
+    for (int v = lane; v < nwp; v += 32)
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        Ud[d] += (double)__ldcg(&q[v * (S * NDET) + S * d]);
+        Vd[d] += (double)__ldcg(&q[v * (S * NDET) + S * d + 1]);
+        if constexpr (CAL) Xd[d] += (double)__ldcg(&q[v * (S * NDET) + S * d + 2]);
+      }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int d = 0; d < NDET; ++d) {
+        Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
+        Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
+        if constexpr (CAL) Xd[d] += __shfl_xor_sync(0xffffffffu, Xd[d], off);
+      }
+    const double l = combine_lnl<NDET, CAL>(a.pc + p, Ud, Vd, Xd, lane);
+    if (lane == 0) a.lnl[p] = l;
+  };
+
+  // window 0's copy: let it land (and, on the FP64-phase arm, narrow its G)
+  auto window0_ready = [&](int j1) {
+    if (!mbar_wait_bounded(&bar, parity, a.status)) return false;
+    parity ^= 1u;
+    w0_pending = false;
+    if constexpr (F64PH) {
+      narrow_window_g<NDET>(reinterpret_cast<double*>(sm), a.row_elems, j1);
+      __syncthreads();
+    }
+    return true;
+  };
+
+  bool have_first = nw >= 1;
+  if (have_first && w != 0) {
+    // this CTA starts in a later window: its first claims (window 0) are summed first
+    const int j1 = window_end(0);
+    if (!window0_ready(j1)) return;
+    drain_window(a.work + 1, a.B, chunk0, a.pc, 0, lane,
+                 [&](int64_t p, int ncut) { body(0, 0, j1, p, ncut); }, first, chunk0, true);
+    have_first = false;
+  }
 
   for (; w < nw; ++w) {
     const int j0 = w * a.CH;
-    int64_t j1l = (int64_t)j0 + a.CH;
-    if (j1l > a.M) j1l = a.M;
-    if (j1l > maxn) j1l = maxn;
-    const int j1 = (int)j1l;  // > j0 because w < nw
+    const int j1 = window_end(w);  // > j0 because w < nw
     int* ctr = a.work + 1 + w;
-    // every warp is done with the previous window; a window whose proposals are all taken is skipped
-    const bool drained = __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
+    const bool use_first = have_first && w == 0;  // the same in every thread of the CTA
+    // every warp is done with the previous window; a window whose proposals are
+    // all taken is skipped (not checked where the warps hold a claim in it)
+    const bool drained = use_first ? false : __syncthreads_or(threadIdx.x == 0 && __ldcg(ctr) >= a.B);
     if (s_npend > 0) flush_pending<NDET, Acc, CAL>(s_pend, &s_npend, a.pc, a.lnl);
     if (!drained) {
       if (w0_pending) {  // window 0's copy: use it, or let it land before staging another window
-        if (!mbar_wait_bounded(&bar, parity, a.status)) return;
-        parity ^= 1u;
-        w0_pending = false;
+        if (!window0_ready(w == 0 ? j1 - j0 : window_end(0))) return;
         if (w != 0) __syncthreads();  // every thread has seen the copy land before the barrier is armed again
-        if constexpr (F64PH) {
-          if (w == 0) {
-            narrow_window_g<NDET>(reinterpret_cast<double*>(sm), a.row_elems, j1 - j0);
-            __syncthreads();
-          }
-        }
       }
       if (w != 0) {
         if (threadIdx.x == 0) {
@@ -726,72 +821,10 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
           __syncthreads();
         }
       }
-      drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
-        Acc U[NDET], V[NDET], X[NDET];
-        if constexpr (CAL) cal_nodes<NDET, MIXED>(a, p, lane, nodes);
-        window_sums<NDET, MIXED, CAL, F64PH>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, U, V, X);
-        const int nwp = (ncut + a.CH - 1) / a.CH;
-        if (nwp == 1) {  // the proposal's only window: queue it for the CTA's next combination
-          int slot = 0;
-          if (lane == 0) slot = atomicAdd(&s_npend, 1);
-          slot = __shfl_sync(0xffffffffu, slot, 0);
-          if (slot < kPendCap) {
-            if (lane == 0) {
-              s_pend[slot].p = p;
-#pragma unroll
-              for (int d = 0; d < NDET; ++d) {
-                s_pend[slot].U[d] = U[d];
-                s_pend[slot].V[d] = V[d];
-                if constexpr (CAL) s_pend[slot].X[d] = X[d];
-              }
-            }
-          } else {  // queue full: combine here
-            const double l = combine_lnl<NDET, CAL>(a.pc + p, U, V, X, lane);
-            if (lane == 0) a.lnl[p] = l;
-          }
-          return;
-        }
-        // several windows: publish this one; the warp that closes the last one combines
-        int done = 0;
-        if (lane == 0) {
-          Acc* o = reinterpret_cast<Acc*>(a.partials) + (p * a.nw_total + w) * (S * NDET);
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            o[S * d] = U[d];
-            o[S * d + 1] = V[d];
-            if constexpr (CAL) o[S * d + 2] = X[d];
-          }
-          __threadfence();
-          done = atomicAdd(&a.pdone[p], 1);
-        }
-        done = __shfl_sync(0xffffffffu, done, 0);
-        if (done != nwp - 1) return;
-        __threadfence();
-        // lanes take windows lane, lane + 32, ...; a fixed shuffle tree then sums
-        // the lanes (FP64, the same order whichever warp closes the proposal)
-        const Acc* q = reinterpret_cast<const Acc*>(a.partials) + p * a.nw_total * (S * NDET);
-        double Ud[NDET], Vd[NDET], Xd[NDET];
-#pragma unroll
-        for (int d = 0; d < NDET; ++d) Ud[d] = Vd[d] = Xd[d] = 0.0;
-        for (int v = lane; v < nwp; v += 32)
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            Ud[d] += (double)__ldcg(&q[v * (S * NDET) + S * d]);
-            Vd[d] += (double)__ldcg(&q[v * (S * NDET) + S * d + 1]);
-            if constexpr (CAL) Xd[d] += (double)__ldcg(&q[v * (S * NDET) + S * d + 2]);
-          }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-          for (int d = 0; d < NDET; ++d) {
-            Ud[d] += __shfl_xor_sync(0xffffffffu, Ud[d], off);
-            Vd[d] += __shfl_xor_sync(0xffffffffu, Vd[d], off);
-            if constexpr (CAL) Xd[d] += __shfl_xor_sync(0xffffffffu, Xd[d], off);
-          }
-        const double l = combine_lnl<NDET, CAL>(a.pc + p, Ud, Vd, Xd, lane);
-        if (lane == 0) a.lnl[p] = l;
-      });
+      drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane,
+                   [&](int64_t p, int ncut) { body(w, j0, j1, p, ncut); }, first, use_first ? chunk0 : 0);
     }
+    have_first = false;
     n_w -= __ldcg(&a.hist[w]);
   }
   __syncthreads();

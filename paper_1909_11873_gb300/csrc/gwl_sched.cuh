@@ -135,22 +135,33 @@ __device__ __forceinline__ int claim_size(int64_t B, int n_active) {
 
 // Warp-level: drain the proposals of one window from its counter, `chunk` per
 // claim; f(p, ncut) runs (on the whole warp) for every proposal with ncut > j0.
+// A claim taken earlier on the same counter (pre_chunk > 0: lane 0's pre, the
+// value its atomic returned, pre_chunk proposals) is processed first; with
+// only_pre the warp stops after it.
 template <class F>
 __device__ __forceinline__ void drain_window(int* ctr, int64_t B, int chunk, const PropCommon* __restrict__ pc,
-                                             int j0, int lane, F&& f) {
+                                             int j0, int lane, F&& f, int pre = 0, int pre_chunk = 0,
+                                             bool only_pre = false) {
   while (true) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(ctr, chunk);
+    int base = 0, n = chunk;
+    if (pre_chunk > 0) {
+      base = pre;
+      n = pre_chunk;
+    } else if (lane == 0) {
+      base = atomicAdd(ctr, chunk);
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= B) break;
     int nc = 0;
-    if (lane < chunk && base + lane < B) nc = pc[base + lane].ncut;
+    if (lane < n && base + lane < B) nc = pc[base + lane].ncut;
     unsigned act = __ballot_sync(0xffffffffu, nc > j0);
     while (act) {
       const int l = __ffs(act) - 1;
       act &= act - 1;
       f((int64_t)base + l, __shfl_sync(0xffffffffu, nc, l));
     }
+    if (only_pre && pre_chunk > 0) break;
+    pre_chunk = 0;
   }
 }
 
