@@ -161,9 +161,9 @@ int gwl_loglike_host(gwl_ctx* ctx, const double* theta_host, int64_t B, double* 
  * per-bin tables there (about 70 bytes per bin).  gwl_grad then also returns
  * the derivatives with respect to the calibration parameters, and ns_replace
  * and ns_run walk in the n_dim + 2 n_nodes n_det coordinates (random or
- * Galilean walk).  gwl_multi_create / gwl_multi_loglike / gwl_multi_ns_run
- * refuse a calibrated context with GWL_ERR_ARG; gwl_waveform returns the
- * template without the calibration factor.  A non-finite calibration
+ * Galilean walk).  Multi-event batches take calibrated contexts when all of
+ * them have the same number of nodes (see gwl_multi_create); gwl_waveform
+ * returns the template without the calibration factor.  A non-finite calibration
  * parameter gives a non-finite lnL.  The likelihood and gradient windows
  * (gwl_tuning.window, .grad_window) shrink, if needed, so that the
  * calibration rows fit in shared memory.  An argument error leaves the
@@ -284,20 +284,30 @@ int gwl_test_philox(const uint32_t* in_dev, int64_t n, uint32_t* out_dev, void* 
 
 /* ---- many events in one batch ----
  * A multi-event context groups n_events contexts (same device, detector
- * count, precision and sampled dimension; different segment lengths and
- * priors allowed).  It borrows them: they must outlive it. */
+ * count, precision, sampled dimension and number of calibration nodes;
+ * different segment lengths, priors, calibration node frequencies and
+ * calibration prior widths allowed).  GWL_MIXED_F64PHASE contexts are
+ * refused with GWL_ERR_ARG.  It borrows the contexts: they must outlive it.
+ * A context's calibration may be changed afterwards (the batch rebuilds its
+ * device descriptors on its next call), but gwl_multi_loglike and
+ * gwl_multi_ns_run return GWL_ERR_ARG while the contexts' node counts
+ * differ. */
 typedef struct gwl_multi gwl_multi;
 
 int gwl_multi_create(gwl_ctx* const* ctxs, int n_events, gwl_multi** out);
 
 /* Batched lnL of n_per proposals of every event in one launch sequence
  * (prologue, a persistent bin loop over (event, window) tasks, combination).
- *   theta_dev dev [n_events][n_per][n_dim], lnl_dev dev [n_events][n_per]. */
+ *   theta_dev dev [n_events][n_per][theta_stride] (n_dim sampled coordinates,
+ *             then with the calibration model each event's calibration
+ *             parameters in gwl_set_calibration's layout)
+ *   lnl_dev   dev [n_events][n_per] */
 int gwl_multi_loglike(gwl_multi* m, const double* theta_dev, int64_t n_per, double* lnl_dev, void* stream);
 
 /* ns_run for all events at once: every round is one sequence of launches
  * (CUDA graph) covering all events; each event has its own live set, walk
- * scale and Philox key seed + e * 0x9E3779B97F4A7C15.  Stops when every
+ * scale and Philox key seed + e * 0x9E3779B97F4A7C15, and walks in its
+ * theta_stride unit-cube coordinates (random walk).  Stops when every
  * event's stopping rule holds or after max_rounds.  out: [n_events] results
  * (no dead-point arrays).  Synchronises the stream. */
 int gwl_multi_ns_run(gwl_multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,

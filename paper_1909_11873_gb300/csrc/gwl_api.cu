@@ -523,7 +523,8 @@ int gwl_multi_create(gwl_ctx* const* ctxs, int n_events, gwl_multi** out) {
     if (c->device != ctxs[0]->device || c->n_det != ctxs[0]->n_det || c->opt.precision != ctxs[0]->opt.precision ||
         c->opt.n_dim != ctxs[0]->opt.n_dim)
       return fail(GWL_ERR_ARG, "context %d differs in device, detectors, precision or dimension", e);
-    if (c->n_cal_nodes) return fail(GWL_ERR_ARG, "context %d has the calibration model (not batched)", e);
+    if (c->n_cal_nodes != ctxs[0]->n_cal_nodes)
+      return fail(GWL_ERR_ARG, "context %d differs in its number of calibration nodes", e);
     if (c->opt.precision == GWL_MIXED_F64PHASE) return fail(GWL_ERR_ARG, "context %d is GWL_MIXED_F64PHASE", e);
   }
   int rc = check_ctx(ctxs[0]);
@@ -542,7 +543,8 @@ int gwl_multi_loglike(gwl_multi* h, const double* theta_dev, int64_t n_per, doub
   if (n_per < 0) return fail(GWL_ERR_ARG, "n_per < 0");
   if (n_per == 0) return GWL_OK;
   if (!theta_dev || !lnl_dev) return fail(GWL_ERR_ARG, "null device pointer");
-  if (gwl::multi_has_calibration(h->m)) return fail(GWL_ERR_ARG, "a context of the batch has the calibration model");
+  if (!gwl::multi_consistent(h->m))
+    return fail(GWL_ERR_ARG, "the batch's contexts no longer share their number of calibration nodes");
   cudaError_t e = gwl::multi_prepare(h->m, n_per);
   if (e != cudaSuccess) return cuda_fail(e, "gwl_multi_loglike");
   e = gwl::multi_loglike(h->m, theta_dev, n_per, lnl_dev, (cudaStream_t)stream);
@@ -556,7 +558,8 @@ int gwl_multi_ns_run(gwl_multi* h, int64_t K, int64_t n_chains, int walk_len, ui
   if (K < 2 || n_chains < 1 || walk_len < 1 || max_rounds < 0) return fail(GWL_ERR_ARG, "bad sizes");
   if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "gwl_multi_ns_run supports K, n_chains <= 4096");
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
-  if (gwl::multi_has_calibration(h->m)) return fail(GWL_ERR_ARG, "a context of the batch has the calibration model");
+  if (!gwl::multi_consistent(h->m))
+    return fail(GWL_ERR_ARG, "the batch's contexts no longer share their number of calibration nodes");
   std::vector<double> res((size_t)11 * h->E);
   const int r = gwl::multi_ns_run(h->m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res.data(),
                                   (cudaStream_t)stream);
@@ -741,6 +744,7 @@ int gwl_set_calibration(gwl_ctx* c, int n_nodes, const double* node_freqs, doubl
   dev_free(c, c->d_calQ_d, gwl::kMaxCalNodes * gwl::kMaxCalNodes);
   c->n_cal_nodes = 0;
   c->seg.stride = c->opt.n_dim;
+  c->cal_gen++;  // multi-event batches holding this context rebuild their descriptors
   if (n_nodes == 0) return GWL_OK;
 
   std::vector<double> x(n_nodes);

@@ -31,6 +31,7 @@ struct gwl_ctx {
 
   // calibration model (gwl_set_calibration); n_cal_nodes == 0: off
   int n_cal_nodes = 0;
+  int64_t cal_gen = 0;  // bumped by every gwl_set_calibration that changes the model
   float* d_cal_f = nullptr;      // [M][cal_row_floats]: spline weights, interval, dH_d
   double* d_cal_d = nullptr;     // [M][cal_row_doubles]
   float* d_calQ_f = nullptr;     // [n_nodes][n_nodes]: m = Q y (natural-spline curvatures)
@@ -168,7 +169,7 @@ void multi_delete(Multi* m);
 cudaError_t multi_prepare(Multi* m, int64_t n_per);
 cudaError_t multi_loglike(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st);
 int64_t multi_launches(const Multi* m);
-bool multi_has_calibration(const Multi* m);
+bool multi_consistent(const Multi* m);
 int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                  int64_t max_rounds, double scale0, double* res /* [E][11] */, cudaStream_t caller);
 

@@ -7,7 +7,11 @@
 // persistent: its CTAs take (event, window) tasks from one atomic queue,
 // stage that event's window of table rows in shared memory (cp.async.bulk on
 // an mbarrier, bounded wait) and drain that event's per-window proposal
-// counter; events with 4 s and 128 s segments thus share one launch.  The
+// counter; events with 4 s and 128 s segments thus share one launch.  With
+// the calibration model (every context of the batch with the same number of
+// nodes, each with its own node frequencies and tables) the window's
+// calibration rows are staged beside its table rows and each proposal's
+// spline node values beside the warp, as in the single-event bin loop.  The
 // nested-sampling rounds of all events likewise run as one sequence of
 // launches (one CTA or warp per event where the work is per event), captured
 // once in a CUDA graph and replayed.
@@ -15,6 +19,7 @@
 #include <vector>
 
 #include "gwl_bins.cuh"
+#include "gwl_ff.cuh"
 
 namespace gwl {
 
@@ -28,6 +33,11 @@ struct EvDesc {
   int nw_total;        // ceil(M / CH)
   int64_t part_off;    // offset of this event's partials block (elements)
   int64_t work_off;    // offset of this event's work block (ints): [0] max cut, [1 + w] counters
+  // calibration model (null cal: off)
+  const void* cal;     // [M][cal_row] calibration rows, float (mixed) or double
+  const void* calQ;    // [nn][nn] natural-spline matrix, float (mixed) or double
+  int cal_row;         // elements per calibration row
+  int nn;              // nodes
 };
 
 // ---------------------------------------------------------------- prologue (one thread per row)
@@ -41,7 +51,7 @@ __global__ void __launch_bounds__(128) k_mprologue(const EvDesc* __restrict__ ev
   const int e = (int)(p / n_per);
   const SegInfo& s = ev[e].seg;
   double th[11];
-  expand_theta(s, theta + p * s.n_dim, th);
+  expand_theta(s, theta + p * s.stride, th);
   const bool ok = physical(th);
   if (!ok) {
     th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
@@ -111,14 +121,23 @@ struct MultiArgs {
   int* work;
   int* task_counter;
   int* status;
+  // calibration model
+  const double* theta;  // [B][stride] parameter rows (the node values follow the n_dim sampled coordinates)
+  int64_t stride;
+  int cal_par;          // first calibration parameter of a row (= n_dim)
+  int cal_smem;         // element offset of the window's calibration rows in shared memory
 };
 
-template <int NDET, bool MIXED>
+template <int NDET, bool MIXED, bool CAL>
 __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
+  using Node = typename std::conditional<MIXED, float4, CalNodeD>::type;
+  constexpr int S = CAL ? 3 : 2;  // sums per detector in a partial
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int sh_task;
+  __shared__ __align__(32) Node s_nodes[CAL ? 8 * NDET * kMaxCalNodes : 1];
+  Node* nodes = s_nodes + (CAL ? (threadIdx.x >> 5) * NDET * kMaxCalNodes : 0);
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -155,8 +174,12 @@ __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
     if (threadIdx.x == 0) {
       fence_proxy_async_smem();
       const uint32_t bytes = (uint32_t)(j1 - j0) * (uint32_t)d.row_elems * (uint32_t)sizeof(Elem);
-      mbar_arrive_expect_tx(&bar, bytes);
+      // calibration rows in pairs: a bulk copy moves whole 16-byte units (the table has a row past the last bin)
+      const uint32_t cbytes = CAL ? (uint32_t)((j1 - j0 + 1) & ~1) * (uint32_t)d.cal_row * (uint32_t)sizeof(Elem) : 0u;
+      mbar_arrive_expect_tx(&bar, bytes + cbytes);
       bulk_g2s(sm, reinterpret_cast<const Elem*>(d.tab) + (int64_t)j0 * d.row_elems, bytes, &bar);
+      if constexpr (CAL)
+        bulk_g2s(sm + a.cal_smem, reinterpret_cast<const Elem*>(d.cal) + (int64_t)j0 * d.cal_row, cbytes, &bar);
     }
     if (!mbar_wait_bounded(&bar, parity, a.status)) return;
     parity ^= 1u;
@@ -170,12 +193,17 @@ __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
       const int ncut = a.pc[p].ncut;
       if (ncut <= j0) continue;
       const int jend = ncut < j1 ? ncut : j1;
-      Elem U[NDET], V[NDET];
+      Elem U[NDET], V[NDET], X[NDET];
 #pragma unroll
-      for (int q = 0; q < NDET; ++q) U[q] = V[q] = (Elem)0;
+      for (int q = 0; q < NDET; ++q) U[q] = V[q] = X[q] = (Elem)0;
+      if constexpr (CAL) {
+        cal_nodes_fill<NDET, MIXED>(a.theta + p * a.stride + a.cal_par, d.nn, d.calQ, lane, nodes);
+        __syncwarp();
+      }
       if constexpr (MIXED) {
-        anchored_sums<NDET>(sm, d.row_elems, d.anchor + (int64_t)(j0 / kAnchor) * kAnchorRowFloats, d.df,
-                            reinterpret_cast<const PropMixed*>(a.prop) + p, j0, jend, lane, U, V);
+        anchored_sums_cal<NDET, CAL>(sm, d.row_elems, d.anchor + (int64_t)(j0 / kAnchor) * kAnchorRowFloats, d.df,
+                                     reinterpret_cast<const PropMixed*>(a.prop) + p, j0, jend, lane, U, V,
+                                     sm + a.cal_smem, d.cal_row, reinterpret_cast<const float4*>(nodes), X, nullptr);
       } else {
         const PropF64* P = reinterpret_cast<const PropF64*>(a.prop) + p;
         double c[kNBasis], tau[NDET];
@@ -186,7 +214,14 @@ __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
         for (int j = j0 + lane; j < jend; j += 32) {
           double v[RowD<NDET>::n];
           load_row<NDET>(sm + (int64_t)(j - j0) * d.row_elems, v);
-          bin_f64<NDET>(v, c, tau, U, V);
+          if constexpr (CAL) {
+            CalBin<NDET, double> cb;
+            cal_eval<NDET>(reinterpret_cast<const double*>(sm) + a.cal_smem + (int64_t)(j - j0) * d.cal_row,
+                           reinterpret_cast<const CalNodeD*>(nodes), cb);
+            bin_f64_cal<NDET>(v, c, tau, cb, U, V, X);
+          } else {
+            bin_f64<NDET>(v, c, tau, U, V);
+          }
         }
       }
 #pragma unroll
@@ -195,23 +230,27 @@ __global__ void __launch_bounds__(256, 2) k_mwindow(MultiArgs a) {
         for (int q = 0; q < NDET; ++q) {
           U[q] += __shfl_xor_sync(0xffffffffu, U[q], off);
           V[q] += __shfl_xor_sync(0xffffffffu, V[q], off);
+          if (CAL) X[q] += __shfl_xor_sync(0xffffffffu, X[q], off);
         }
       if (lane == 0) {
-        Elem* o = reinterpret_cast<Elem*>(a.partials) + d.part_off + ((int64_t)pi * d.nw_total + w) * (2 * NDET);
+        Elem* o = reinterpret_cast<Elem*>(a.partials) + d.part_off + ((int64_t)pi * d.nw_total + w) * (S * NDET);
 #pragma unroll
         for (int q = 0; q < NDET; ++q) {
-          o[2 * q] = U[q];
-          o[2 * q + 1] = V[q];
+          o[S * q] = U[q];
+          o[S * q + 1] = V[q];
+          if constexpr (CAL) o[S * q + 2] = X[q];
         }
       }
+      if constexpr (CAL) __syncwarp();  // the warp's node data is replaced by its next proposal's
     }
     __syncthreads();  // all warps done with this window before the next task overwrites it
   }
 }
 
-template <int NDET, typename Acc>
+template <int NDET, typename Acc, bool CAL>
 __global__ void k_mfinalize(const EvDesc* __restrict__ ev, int64_t n_per, int64_t B, const PropCommon* __restrict__ pc,
                             const Acc* __restrict__ partials, double* __restrict__ lnl) {
+  constexpr int S = CAL ? 3 : 2;
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= B) return;
   const int e = (int)(p / n_per);
@@ -223,16 +262,18 @@ __global__ void k_mfinalize(const EvDesc* __restrict__ ev, int64_t n_per, int64_
     return;
   }
   const int nwp = (c.ncut + d.CH - 1) / d.CH;
-  const Acc* q = partials + d.part_off + pi * d.nw_total * (2 * NDET);
+  const Acc* q = partials + d.part_off + pi * d.nw_total * (S * NDET);
   double acc = 0.0;
 #pragma unroll
   for (int k = 0; k < NDET; ++k) {
-    double U = 0.0, V = 0.0;
+    double U = 0.0, V = 0.0, X = 0.0;
     for (int w = 0; w < nwp; ++w) {
-      U += (double)q[w * (2 * NDET) + 2 * k];
-      V += (double)q[w * (2 * NDET) + 2 * k + 1];
+      U += (double)q[w * (S * NDET) + S * k];
+      V += (double)q[w * (S * NDET) + S * k + 1];
+      if constexpr (CAL) X += (double)q[w * (S * NDET) + S * k + 2];
     }
     acc += c.Kr[k] * U - c.Ki[k] * V;
+    if constexpr (CAL) acc -= 0.5 * (c.Kr[k] * c.Kr[k] + c.Ki[k] * c.Ki[k]) * X;
   }
   lnl[p] = acc - 0.5 * c.hh;
 }
@@ -241,6 +282,9 @@ __global__ void k_mfinalize(const EvDesc* __restrict__ ev, int64_t n_per, int64_
 struct Multi {
   int E = 0;
   int n_det = 0, precision = 0, D = 0;
+  int n_dim = 0;
+  bool cal = false;
+  std::vector<int64_t> cal_gen;  // the contexts' calibration generations the descriptors were built from
   int64_t n_per = 0;
   std::vector<gwl_ctx*> ctxs;
   std::vector<EvDesc> host_ev;
@@ -276,11 +320,16 @@ static void multi_free_scratch(Multi* m) {
 
 // (Re)build the descriptors and scratch for n_per proposals per event.
 cudaError_t multi_prepare(Multi* m, int64_t n_per) {
-  if (n_per <= m->cap_per && m->d_ev) {
+  bool fresh = true;  // no context's calibration changed since the descriptors were built
+  for (int e = 0; e < m->E; ++e) fresh = fresh && m->cal_gen[e] == m->ctxs[e]->cal_gen;
+  if (fresh && n_per <= m->cap_per && m->d_ev) {
     m->n_per = n_per;
     return cudaSuccess;
   }
   multi_free_scratch(m);
+  m->D = (int)theta_stride(m->ctxs[0]);
+  m->cal = m->ctxs[0]->n_cal_nodes > 0;
+  for (int e = 0; e < m->E; ++e) m->cal_gen[e] = m->ctxs[e]->cal_gen;
   const bool mixed = m->precision == GWL_MIXED;
   m->host_ev.resize(m->E);
   int64_t part = 0, work = 0;
@@ -298,7 +347,16 @@ cudaError_t multi_prepare(Multi* m, int64_t n_per) {
     d.nw_total = (int)((c->M + CH - 1) / CH);
     d.part_off = part;
     d.work_off = work;
-    part += n_per * d.nw_total * 2 * m->n_det;
+    d.cal = nullptr;
+    d.calQ = nullptr;
+    d.cal_row = 0;
+    d.nn = c->n_cal_nodes;
+    if (c->n_cal_nodes) {
+      d.cal = mixed ? (const void*)c->d_cal_f : (const void*)c->d_cal_d;
+      d.calQ = mixed ? (const void*)c->d_calQ_f : (const void*)c->d_calQ_d;
+      d.cal_row = mixed ? c->row_cal_f : c->row_cal_d;
+    }
+    part += n_per * d.nw_total * (m->cal ? 3 : 2) * m->n_det;
     work += 1 + d.nw_total;
   }
   m->work_len = work + 1;  // + task counter
@@ -319,7 +377,7 @@ cudaError_t multi_prepare(Multi* m, int64_t n_per) {
   return cudaSuccess;
 }
 
-template <int NDET, bool MIXED>
+template <int NDET, bool MIXED, bool CAL>
 static cudaError_t multi_run(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st) {
   using Elem = typename std::conditional<MIXED, float, double>::type;
   const int64_t B = n_per * m->E;
@@ -329,13 +387,17 @@ static cudaError_t multi_run(Multi* m, const double* theta, int64_t n_per, doubl
                                                                    m->work);
   m->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int CHmax = 0, rowmax = 0;
+  int CHmax = 0, rowmax = 0, calmax = 0;
   for (const EvDesc& d : m->host_ev) {
     CHmax = d.CH > CHmax ? d.CH : CHmax;
     rowmax = d.row_elems > rowmax ? d.row_elems : rowmax;
+    calmax = d.cal_row > calmax ? d.cal_row : calmax;
   }
-  const size_t smem = (size_t)CHmax * rowmax * sizeof(Elem);
-  if ((e = raise_smem_limit((const void*)k_mwindow<NDET, MIXED>, m->ctxs[0]->device, smem)) != cudaSuccess) return e;
+  // the window's table rows, then (calibration) its calibration rows, staged in pairs
+  const int64_t cal_smem = (int64_t)CHmax * rowmax;
+  const size_t smem = (size_t)(cal_smem + (CAL ? (int64_t)(CHmax + 1) * calmax : 0)) * sizeof(Elem);
+  if ((e = raise_smem_limit((const void*)k_mwindow<NDET, MIXED, CAL>, m->ctxs[0]->device, smem)) != cudaSuccess)
+    return e;
   MultiArgs a;
   a.ev = m->d_ev;
   a.E = m->E;
@@ -346,22 +408,35 @@ static cudaError_t multi_run(Multi* m, const double* theta, int64_t n_per, doubl
   a.work = m->work;
   a.task_counter = m->work + m->work_len - 1;
   a.status = m->status;
-  k_mwindow<NDET, MIXED><<<m->num_sms * 2, 256, smem, st>>>(a);
+  a.theta = theta;
+  a.stride = m->D;
+  a.cal_par = m->n_dim;
+  a.cal_smem = (int)cal_smem;
+  k_mwindow<NDET, MIXED, CAL><<<m->num_sms * 2, 256, smem, st>>>(a);
   m->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_mfinalize<NDET, Elem><<<(unsigned)((B + 63) / 64), 64, 0, st>>>(m->d_ev, n_per, B, m->pc,
-                                                                      (const Elem*)m->partials, lnl);
+  k_mfinalize<NDET, Elem, CAL><<<(unsigned)((B + 63) / 64), 64, 0, st>>>(m->d_ev, n_per, B, m->pc,
+                                                                           (const Elem*)m->partials, lnl);
   m->launches++;
   return cudaGetLastError();
 }
 
-cudaError_t multi_loglike(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st) {
+template <int NDET>
+static cudaError_t multi_dispatch(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st) {
   const bool mixed = m->precision == GWL_MIXED;
+  if (m->cal)
+    return mixed ? multi_run<NDET, true, true>(m, theta, n_per, lnl, st)
+                 : multi_run<NDET, false, true>(m, theta, n_per, lnl, st);
+  return mixed ? multi_run<NDET, true, false>(m, theta, n_per, lnl, st)
+               : multi_run<NDET, false, false>(m, theta, n_per, lnl, st);
+}
+
+cudaError_t multi_loglike(Multi* m, const double* theta, int64_t n_per, double* lnl, cudaStream_t st) {
   switch (m->n_det) {
-    case 1: return mixed ? multi_run<1, true>(m, theta, n_per, lnl, st) : multi_run<1, false>(m, theta, n_per, lnl, st);
-    case 2: return mixed ? multi_run<2, true>(m, theta, n_per, lnl, st) : multi_run<2, false>(m, theta, n_per, lnl, st);
-    case 3: return mixed ? multi_run<3, true>(m, theta, n_per, lnl, st) : multi_run<3, false>(m, theta, n_per, lnl, st);
-    default: return mixed ? multi_run<4, true>(m, theta, n_per, lnl, st) : multi_run<4, false>(m, theta, n_per, lnl, st);
+    case 1: return multi_dispatch<1>(m, theta, n_per, lnl, st);
+    case 2: return multi_dispatch<2>(m, theta, n_per, lnl, st);
+    case 3: return multi_dispatch<3>(m, theta, n_per, lnl, st);
+    default: return multi_dispatch<4>(m, theta, n_per, lnl, st);
   }
 }
 
@@ -371,7 +446,10 @@ Multi* multi_new(gwl_ctx* const* ctxs, int E) {
   m->ctxs.assign(ctxs, ctxs + E);
   m->n_det = ctxs[0]->n_det;
   m->precision = ctxs[0]->opt.precision;
-  m->D = ctxs[0]->opt.n_dim;
+  m->n_dim = ctxs[0]->opt.n_dim;
+  m->D = (int)theta_stride(ctxs[0]);  // the sampled coordinates, then the calibration parameters
+  m->cal = ctxs[0]->n_cal_nodes > 0;
+  m->cal_gen.assign(E, -1);
   m->num_sms = ctxs[0]->num_sms;
   m->status = ctxs[0]->d_status;
   return m;
@@ -384,14 +462,16 @@ void multi_delete(Multi* m) {
 }
 
 int64_t multi_launches(const Multi* m) { return m ? m->launches : 0; }
-bool multi_has_calibration(const Multi* m) {
+// The contexts still share their number of calibration nodes (a context's
+// calibration may have been changed since the batch was made).
+bool multi_consistent(const Multi* m) {
   if (!m) return false;
-  for (int e = 0; e < m->E; ++e)
-    if (m->ctxs[e]->n_cal_nodes) return true;
-  return false;
+  for (int e = 1; e < m->E; ++e)
+    if (m->ctxs[e]->n_cal_nodes != m->ctxs[0]->n_cal_nodes) return false;
+  return true;
 }
 int multi_events(const Multi* m) { return m->E; }
-int multi_dim(const Multi* m) { return m->D; }
+int multi_dim(const Multi* m) { return (int)theta_stride(m->ctxs[0]); }  // walk dimension, current
 gwl_ctx* multi_ctx(const Multi* m, int e) { return m->ctxs[e]; }
 void multi_count(Multi* m, int64_t n) { m->launches += n; }
 

@@ -440,7 +440,8 @@ class MultiContext:
             pass
 
     def gwl_multi_loglike(self, theta, lnl, stream=None):
-        """theta [E * n_per, n_dim] (event-major), lnl [E * n_per]."""
+        """theta [E * n_per, theta_stride] (event-major; theta_stride = n_dim plus the calibration parameters),
+        lnl [E * n_per]."""
         n_per = theta.shape[0] // self.E
         _check(lib().gwl_multi_loglike(self._h, _ptr(theta), n_per, _ptr(lnl), _stream(stream)), "gwl_multi_loglike")
 

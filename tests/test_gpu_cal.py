@@ -163,13 +163,11 @@ def test_calibration_edge_rows_and_entry_points(precision):
 
 
 def test_calibration_refused_where_not_modelled():
-    """Multi-event batches refuse a calibrated context and the FP64-phase arm refuses the model
-    (GWL_ERR_ARG); invalid node sets and prior widths are refused."""
+    """The FP64-phase arm refuses the model (GWL_ERR_ARG); invalid node sets and prior widths are refused
+    (multi-event batches of calibrated contexts: tests/test_gpu_multi.py)."""
     g = gwl()
     ev = event("c2")
     ctx = cal_context(ev, I.cal_node_freqs(20.0, 1024.0), 1)
-    with pytest.raises(g.GwlError, match="calibration"):
-        g.MultiContext([ctx])
     f64ph = g.Context.from_event(ev, g.GWL_MIXED_F64PHASE)
     with pytest.raises(g.GwlError):
         f64ph.gwl_set_calibration(I.cal_node_freqs(20.0, 1024.0))

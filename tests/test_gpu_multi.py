@@ -116,3 +116,93 @@ def test_multi_ns_lnz_matches_oracle_per_event():
         assert np.isfinite(r["lnZ"]) and r["rounds"] > 3
         assert abs(r["lnZ"] - o["lnZ"]) < 4 * sig, (r, o)
         assert r["consumed_per_round"] == pytest.approx(K * math.log(1 + nch / K), rel=0.12)
+
+
+def cal_nodes_for(ev, n=10):
+    return I.cal_node_freqs(float(ev.freqs[0]), float(ev.freqs[-1]), n)
+
+
+def cal_multi(evs, precision, n_nodes=10, sig=(0.1, 0.1)):
+    from paper_1909_11873_gb300 import gwl
+    ctxs = []
+    for ev in evs:
+        c = gwl.Context.from_event(ev, precision)
+        c.gwl_set_calibration(cal_nodes_for(ev, n_nodes), *sig)
+        ctxs.append(c)
+    return ctxs, gwl.MultiContext(ctxs)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_loglike_calibrated(precision):
+    """Calibrated events in one batch (section 2.2's model, ten nodes per detector over each event's own band,
+    71 parameters per row): 4-16 s events plus a 32 s BNS and a 64 s BBH event whose proposals span many
+    windows; equal to the per-event entry point and to the oracle's calibrated likelihood on sampled rows."""
+    from paper_1909_11873_gb300 import gwl
+    evs = small_events() + [long_events()[0], long_events()[1]]
+    n = 64
+    ths = [I.proposals(ev, n, 51 + i) for i, ev in enumerate(evs)]
+    cals = [I.draw_calibration(np.random.default_rng(61 + i), n, 3) for i in range(len(evs))]
+    ctxs, mc = cal_multi(evs, precision)
+    rows = [np.concatenate([I.reduced(t, ev.sampling), c], axis=1) for t, c, ev in zip(ths, cals, evs)]
+    x = torch.from_numpy(np.ascontiguousarray(np.concatenate(rows))).cuda()
+    out = torch.empty(x.shape[0], dtype=torch.float64, device="cuda")
+    mc.gwl_multi_loglike(x, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(len(evs), n)
+    for e, (ev, th, cal, ctx, r) in enumerate(zip(evs, ths, cals, ctxs, rows)):
+        single = gwl.loglike(ctx, torch.from_numpy(np.ascontiguousarray(r)).cuda()).cpu().numpy()
+        assert np.all(np.abs(got[e] - single) <= 0.1 * tol(precision, single)), e
+        idx = np.arange(0, n, 4)
+        ref = oracle.loglike_cal(ev, cal_nodes_for(ev), np.concatenate([th, cal], axis=1)[idx])
+        assert np.all(np.abs(got[e, idx] - ref) <= tol(precision, ref)), (e, np.abs(got[e, idx] - ref).max())
+
+
+def test_multi_calibration_node_counts_must_agree():
+    """A batch's contexts share their node count; a context changed afterwards is refused until the counts
+    agree again, and the batch then follows the new tables."""
+    from paper_1909_11873_gb300 import gwl
+    evs = small_events()[:2]
+    ctxs, mc = cal_multi(evs, 1, n_nodes=6)
+    other = gwl.Context.from_event(evs[0], 1)
+    with pytest.raises(gwl.GwlError, match="calibration"):
+        gwl.MultiContext([ctxs[0], other])
+    n = 32
+    th = [np.concatenate([I.reduced(I.proposals(ev, n, 3 + i), ev.sampling),
+                          I.draw_calibration(np.random.default_rng(i), n, 3, n_nodes=6)], axis=1)
+          for i, ev in enumerate(evs)]
+    x = torch.from_numpy(np.ascontiguousarray(np.concatenate(th))).cuda()
+    out = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+    mc.gwl_multi_loglike(x, out)
+    first = out.clone()
+    ctxs[1].gwl_set_calibration(cal_nodes_for(evs[1], 4))
+    with pytest.raises(gwl.GwlError, match="calibration"):
+        mc.gwl_multi_loglike(x, out)
+    # same count, other node frequencies: the batch rebuilds its descriptors and follows them
+    ctxs[1].gwl_set_calibration(I.cal_node_freqs(25.0, 900.0, 6))
+    mc.gwl_multi_loglike(x, out)
+    torch.cuda.synchronize()
+    ref1 = gwl.loglike(ctxs[1], x[n:]).cpu().numpy()
+    assert np.allclose(out[n:].cpu().numpy(), ref1, rtol=0, atol=1e-4)
+    assert torch.equal(out[:n], first[:n])
+
+
+def test_multi_ns_calibrated_lnz_matches_oracle_per_event():
+    """Nested sampling of two calibrated events in one graph per round (4 source + 12 calibration
+    coordinates each: two nodes per detector) against the oracle's calibrated NS of each event: the mean lnZ
+    of two runs on each side (a constant calibration phase is degenerate with phi_c, a ridge that single
+    random-walk runs explore unevenly)."""
+    from paper_1909_11873_gb300 import gwl
+    evs = [four_d(ev) for ev in small_events()[:2]]
+    K, nch, wl = 200, 200, 60
+    ctxs, mc = cal_multi(evs, 1, n_nodes=2)
+    runs = [mc.gwl_multi_ns_run(K, nch, wl, seed=s, dlogz=0.1) for s in (5, 7)]
+    for e, ev in enumerate(evs):
+        g = [r[e] for r in runs]
+        o = [oracle.ns_run_cal(ev, ev.sampling, (cal_nodes_for(ev, 2), 0.1, 0.1), K, nch, wl, seed=s, dlogz=0.1)
+             for s in (6, 8)]
+        for r in g:
+            assert np.isfinite(r["lnZ"]) and r["rounds"] > 3
+        gm = np.mean([r["lnZ"] for r in g])
+        om = np.mean([r["lnZ"] for r in o])
+        sig = math.sqrt(np.mean([r["lnZ_err"] ** 2 for r in g]) / 2 + np.mean([r["lnZ_err"] ** 2 for r in o]) / 2)
+        assert abs(gm - om) < 4 * sig, (e, g, o)
