@@ -255,6 +255,34 @@ int ns_run(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t see
            int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
            double* dead_u, gwl_ns_result* out, void* stream);
 
+/* Checkpoint and resume of ns_run (an interface addition without a
+ * counterpart in the paper).  The state of a run between rounds is its live
+ * set (u and lnL), the walk's L*, scale, worst index and round counter, the
+ * evidence and information accumulators, and the dead points so far.  The
+ * walk's normals come from a counter-based generator keyed by the round
+ * counter, so a run split into calls continues bit for bit: calls with
+ * max_rounds R1, R2, ..., each resuming from the previous call's checkpoint
+ * and all other arguments equal, give the same results, dead points and
+ * checkpoints as one call with R1 + R2 + ....
+ *   resume      host [ns_state_doubles(K, D, m)] or NULL: a checkpoint written
+ *               by an earlier call with the same K and walk dimension D (m
+ *               that call's max_dead); the run continues from it, so scale0
+ *               and the seed's initial draw are unused
+ *   checkpoint  host [ns_state_doubles(K, D, max_dead)] or NULL: receives the
+ *               state after this call's last round, before the final live
+ *               points join the dead list
+ * out and the dead-point arrays are filled as by ns_run, as if the run
+ * stopped after this call.  Dead points beyond the max_dead of the call that
+ * wrote a checkpoint are not carried in it.  A resume buffer of another
+ * format, K or D gives GWL_ERR_ARG.  Synchronises the stream. */
+int ns_run_resumable(gwl_ctx* ctx, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                     int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+                     double* dead_u, gwl_ns_result* out, const double* resume, double* checkpoint, void* stream);
+
+/* Doubles in a checkpoint of a run with K live points in D walk dimensions
+ * keeping up to max_dead dead points; -1 for K < 2, D < 1 or max_dead < 0. */
+int64_t ns_state_doubles(int64_t K, int64_t D, int64_t max_dead);
+
 /* Diagnostic: the float-float elementary functions of the mixed prologue
  * (about 48 significant bits on the FP32 pipe) on n arguments, for checking
  * their accuracy against FP64 references.  (An interface addition without a

@@ -466,12 +466,30 @@ int ns_replace(gwl_ctx* c, const double* live_u, const double* live_lnl, int64_t
   return GWL_OK;
 }
 
+int64_t ns_state_doubles(int64_t K, int64_t D, int64_t max_dead) {
+  if (K < 2 || D < 1 || max_dead < 0) return -1;
+  return gwl::state_doubles(K, D, max_dead);
+}
+
 int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz, int64_t max_rounds,
            double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt, double* dead_u, gwl_ns_result* out,
            void* stream) {
+  return ns_run_resumable(c, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, max_dead, dead_lnl, dead_logwt,
+                          dead_u, out, nullptr, nullptr, stream);
+}
+
+int ns_run_resumable(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                     int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
+                     double* dead_u, gwl_ns_result* out, const double* resume, double* checkpoint, void* stream) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!out) return fail(GWL_ERR_ARG, "out is null");
+  if (resume) {
+    const int bad = gwl::state_check(resume, K, gwl::theta_stride(c));
+    if (bad == 1) return fail(GWL_ERR_ARG, "resume: not a checkpoint of this format");
+    if (bad == 2) return fail(GWL_ERR_ARG, "resume: the checkpoint is for another K or walk dimension");
+    if (bad) return fail(GWL_ERR_ARG, "resume: inconsistent dead-point count");
+  }
   if (K < 2 || n_chains < 1 || walk_len < 1 || max_rounds < 0 || max_dead < 0)
     return fail(GWL_ERR_ARG, "bad sizes (K >= 2, n_chains >= 1, walk_len >= 1 needed)");
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
@@ -491,7 +509,7 @@ int ns_run(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed,
   c->last_stream = st;
   double res[11];
   const int r = gwl::ns_run_impl(c, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, max_dead, dead_lnl,
-                                 dead_logwt, dead_u, res, st, 1);
+                                 dead_logwt, dead_u, res, st, 1, resume, checkpoint);
   if (r != 0) return fail(GWL_ERR_CUDA, "ns_run: %s", cudaGetErrorString(cudaGetLastError()));
   out->lnZ = res[0];
   out->lnZ_err = res[1];

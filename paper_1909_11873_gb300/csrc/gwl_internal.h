@@ -160,7 +160,10 @@ size_t gmc_scratch_doubles(int64_t n_chains, int D);
 void set_walk_scalars(void* host_buf, double lstar, double scale, int64_t worst, uint64_t counter);
 int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                 int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
-                double* dead_u, double* res, cudaStream_t st, int use_graph);
+                double* dead_u, double* res, cudaStream_t st, int use_graph, const double* resume,
+                double* checkpoint);
+int64_t state_doubles(int64_t K, int64_t D, int64_t max_dead);
+int state_check(const double* in, int64_t K, int64_t D);
 
 // many events in one batched evaluation
 struct Multi;

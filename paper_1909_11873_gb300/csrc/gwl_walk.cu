@@ -935,18 +935,108 @@ void set_walk_scalars(void* host_buf, double lstar, double scale, int64_t worst,
 // Static nested sampling run with all state on the device.
 static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                      int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
-                     double* dead_u, double* res, cudaStream_t st, int use_graph);
+                     double* dead_u, double* res, cudaStream_t st, int use_graph, const double* resume,
+                     double* checkpoint);
+
+// ---------------------------------------------------------------- checkpoint / resume
+// The state of a run between rounds, in host doubles (ns_state_doubles):
+//   [0] kStateMagic, [1] format version, [2] K, [3] D, [4] dead points stored
+//   n, [5] the dead-list capacity of the run that wrote it, [6] L*, [7] walk
+//   scale, [8] worst index, [9] round counter, [10, 10 + NS_NSTATS) the
+//   accumulators, then live u [K][D], live lnL [K], dead lnL [n], dead
+//   ln dX [n], dead u [n][D].
+// The walk draws its normals from a counter-based generator keyed by the round
+// counter, so a run restored from this state continues bit for bit.
+constexpr double kStateMagic = 5.4217e15;
+constexpr double kStateVersion = 1.0;
+constexpr int kStateHeader = 10 + NS_NSTATS;
+
+// max_dead: the caller's dead-point capacity (the device list holds at least one slot)
+static cudaError_t state_save(const NsDev& s, int64_t max_dead, double* out, cudaStream_t st) {
+  double stats[NS_NSTATS];
+  WalkScalars w;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(stats, s.stats, sizeof(stats), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(&w, s.ws, sizeof(w), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  const int64_t nd = (int64_t)stats[NS_NDEAD];
+  const int64_t n = nd < max_dead ? nd : max_dead;
+  out[0] = kStateMagic;
+  out[1] = kStateVersion;
+  out[2] = (double)s.K;
+  out[3] = (double)s.D;
+  out[4] = (double)n;
+  out[5] = (double)max_dead;
+  out[6] = w.lstar;
+  out[7] = w.scale;
+  out[8] = (double)w.worst;
+  out[9] = (double)w.counter;
+  for (int i = 0; i < NS_NSTATS; ++i) out[10 + i] = stats[i];
+  double* p = out + kStateHeader;
+  if ((e = cudaMemcpy(p, s.lu, sizeof(double) * s.K * s.D, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+  p += s.K * s.D;
+  if ((e = cudaMemcpy(p, s.ll, sizeof(double) * s.K, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+  p += s.K;
+  if (n > 0) {
+    if ((e = cudaMemcpy(p, s.dl, sizeof(double) * n, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(p + n, s.dw, sizeof(double) * n, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(p + 2 * n, s.du, sizeof(double) * n * s.D, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t state_restore(const NsDev& s, const double* in, cudaStream_t st) {
+  double stats[NS_NSTATS];
+  for (int i = 0; i < NS_NSTATS; ++i) stats[i] = in[10 + i];
+  WalkScalars w;
+  w.lstar = in[6];
+  w.scale = in[7];
+  w.worst = (long long)in[8];
+  w.counter = (unsigned long long)in[9];
+  const int64_t stored = (int64_t)in[4];
+  const int64_t n = stored < s.cap ? stored : s.cap;
+  const double* p = in + kStateHeader;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s.stats, stats, sizeof(stats), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(s.ws, &w, sizeof(w), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(s.lu, p, sizeof(double) * s.K * s.D, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(s.ll, p + s.K * s.D, sizeof(double) * s.K, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  p += s.K * (s.D + 1);
+  if (n > 0) {
+    if ((e = cudaMemcpyAsync(s.dl, p, sizeof(double) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(s.dw, p + stored, sizeof(double) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(s.du, p + 2 * stored, sizeof(double) * n * s.D, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return e;
+  }
+  return cudaStreamSynchronize(st);  // the host buffer may be released after the call
+}
+
+int64_t state_doubles(int64_t K, int64_t D, int64_t max_dead) {
+  return kStateHeader + K * (D + 1) + max_dead * (D + 2);
+}
+
+// A resume buffer's header against this run's sizes: 0 when it matches.
+int state_check(const double* in, int64_t K, int64_t D) {
+  if (in[0] != kStateMagic || in[1] != kStateVersion) return 1;
+  if (in[2] != (double)K || in[3] != (double)D) return 2;
+  if (!(in[4] >= 0.0) || !(in[4] <= in[5])) return 3;
+  return 0;
+}
 
 // The run is captured into a CUDA graph, which needs a capturable stream: it
 // runs on a private non-blocking stream after the caller's stream drains.
 int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                 int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
-                double* dead_u, double* res, cudaStream_t caller, int use_graph) {
+                double* dead_u, double* res, cudaStream_t caller, int use_graph, const double* resume,
+                double* checkpoint) {
   if (cudaStreamSynchronize(caller) != cudaSuccess) return -2;
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -2;
   const int rc = ns_run_on(c, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, max_dead, dead_lnl, dead_logwt,
-                           dead_u, res, st, use_graph);
+                           dead_u, res, st, use_graph, resume, checkpoint);
   cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   return rc;
@@ -954,7 +1044,8 @@ int ns_run_impl(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t 
 
 static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                      int64_t max_rounds, double scale0, int64_t max_dead, double* dead_lnl, double* dead_logwt,
-                     double* dead_u, double* res, cudaStream_t st, int use_graph) {
+                     double* dead_u, double* res, cudaStream_t st, int use_graph, const double* resume,
+                     double* checkpoint) {
   const int D = (int)theta_stride(c);
   const int64_t cap = max_dead > 0 ? max_dead : 1;
   const int64_t rbuf = n_chains > K ? n_chains : K;
@@ -1010,7 +1101,11 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
     if ((e = cudaMemcpyAsync(s.stats, st0, sizeof(st0), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(s.ws, &w0, sizeof(w0), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
     if ((e = launch_ns_init(c, seed, K, s.lu, pth, st)) != cudaSuccess) break;
-    if ((e = launch_loglike(c, pth, K, s.ll, st)) != cudaSuccess) break;
+    if (resume) {  // continue a checkpointed run: its state replaces the initial draw
+      if ((e = state_restore(s, resume, st)) != cudaSuccess) break;
+    } else if ((e = launch_loglike(c, pth, K, s.ll, st)) != cudaSuccess) {
+      break;
+    }
     if (c->walk_kind == GWL_WALK_GALILEAN) {  // warm the gradient path (kernel attributes) before capture
       const int64_t nw = K < n_chains ? K : n_chains;
       if ((e = launch_grad(c, pth, nw, plnl, c->d_gmc, st)) != cudaSuccess) break;
@@ -1046,6 +1141,8 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) break;
+    // the state after the last round, before the final live points join the dead list
+    if (checkpoint && (e = state_save(s, max_dead, checkpoint, st)) != cudaSuccess) break;
     // rounds after the stopping rule held are no-ops only if none ran: the
     // loop checks every `check` rounds, so report the rounds actually run
     k_ns_final<<<1, 256, 0, st>>>(s);

@@ -28,7 +28,7 @@ EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static"
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
            "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
-           "gwl_set_galilean", "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
+           "gwl_set_galilean", "ns_run_resumable", "ns_state_doubles", "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
            "gwl_test_wait_timeout", "gwl_test_philox",
            "gwl_test_ffdelta_blocks")
 GWL_WALK_RANDOM = 0
@@ -98,6 +98,10 @@ def lib() -> C.CDLL:
         L.gwl_waveform.argtypes = [P, P, i64, P, P]
         L.ns_replace.argtypes = [P, P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, P]
         L.ns_run.argtypes = [P, i64, i64, i32, u64, d, i64, d, i64, P, P, P, C.POINTER(GwlNsResult), P]
+        L.ns_run_resumable.argtypes = [P, i64, i64, i32, u64, d, i64, d, i64, P, P, P, C.POINTER(GwlNsResult), P, P,
+                                       P]
+        L.ns_state_doubles.argtypes = [i64, i64, i64]
+        L.ns_state_doubles.restype = i64
         L.gwl_sync.argtypes = [P]
         L.gwl_set_tuning.argtypes = [P, C.POINTER(GwlTuning)]
         L.gwl_get_tuning.argtypes = [P, C.POINTER(GwlTuning)]
@@ -249,22 +253,52 @@ class Context:
                "ns_replace")
 
     def ns_run(self, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0, max_dead=0,
-               stream=None):
-        """Static parallel nested sampling on the device; returns a dict (plus dead points if max_dead > 0)."""
+               stream=None, resume=None, checkpoint=False):
+        """Static parallel nested sampling on the device; returns a dict (plus dead points if max_dead > 0).
+        resume: a checkpoint (float64 array) to continue from; checkpoint=True adds the state after this call's
+        rounds as out["state"] (ns_run_resumable)."""
         r = GwlNsResult()
         D = self.theta_stride
         dl = np.zeros(max(max_dead, 1))
         dw = np.zeros(max(max_dead, 1))
         du = np.zeros((max(max_dead, 1), D))
-        _check(lib().ns_run(self._h, int(K), int(n_chains), int(walk_len), int(seed), float(dlogz), int(max_rounds),
-                            float(scale0), int(max_dead), dl.ctypes.data if max_dead else None,
-                            dw.ctypes.data if max_dead else None, du.ctypes.data if max_dead else None, C.byref(r),
-                            _stream(stream)), "ns_run")
+        res = None if resume is None else np.ascontiguousarray(resume, dtype=np.float64)
+        state = np.zeros(lib().ns_state_doubles(int(K), D, int(max_dead))) if checkpoint else None
+        _check(lib().ns_run_resumable(self._h, int(K), int(n_chains), int(walk_len), int(seed), float(dlogz),
+                                      int(max_rounds), float(scale0), int(max_dead),
+                                      dl.ctypes.data if max_dead else None, dw.ctypes.data if max_dead else None,
+                                      du.ctypes.data if max_dead else None, C.byref(r),
+                                      None if res is None else res.ctypes.data,
+                                      None if state is None else state.ctypes.data, _stream(stream)),
+               "ns_run_resumable")
         out = {k: getattr(r, k) for k, _ in GwlNsResult._fields_}
         if max_dead:
             n = r.n_dead_returned
             out.update(dead_lnl=dl[:n], dead_logwt=dw[:n], dead_u=du[:n])
+        if checkpoint:
+            out["state"] = state
         return out
+
+    def ns_run_checkpointed(self, path, K, n_chains, walk_len, seed, every, dlogz=0.1, max_rounds=100000,
+                            scale0=1.0, max_dead=0):
+        """ns_run in calls of `every` rounds, the state written to the .npz file `path` after each; a run whose
+        file exists continues from it.  Returns the last call's result (the whole run's)."""
+        import os
+        state, before = None, 0
+        if os.path.exists(path):
+            f = np.load(path)
+            state, before = f["state"], int(f["rounds"])
+        while True:
+            todo = max(min(every, max_rounds - before), 0)
+            out = self.ns_run(K, n_chains, walk_len, seed, dlogz, todo, scale0, max_dead, resume=state,
+                              checkpoint=True)
+            state = out.pop("state")
+            tmp = path + ".tmp.npz"
+            np.savez(tmp, state=state, rounds=out["rounds"])
+            os.replace(tmp, path)
+            if out["rounds"] - before < todo or out["rounds"] >= max_rounds or todo == 0:
+                return out
+            before = out["rounds"]
 
     def gwl_sync(self):
         _check(lib().gwl_sync(self._h), "gwl_sync")
