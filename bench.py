@@ -68,9 +68,11 @@ PIPES_MIXED = {"fp32_flop": 56, "mufu": 6}
 HBM_BYTES_PER_EVAL = 96
 # The gradient bin loop per pair: the exact float-float phase per bin (the
 # 8-term sum, 112, and per detector the delay term, TwoSum and reduction,
-# 3 x 20) -> 172; per detector the data-weighted phasor (6), Z_d (2) and the
-# nine basis-weighted complex sums W_d,m (36) -> 3 x 44 = 132: 304 flop; 6 MUFU.
-PIPES_GRAD = {"fp32_flop": 304, "mufu": 6}
+# 3 x 20) -> 172; per detector the data-weighted phasor (6), Z_d (2), the
+# imaginary part of K_d times it (3), its f-weighted sum (2) and the sum over
+# detectors (1) -> 3 x 14 = 42; the eight basis-weighted sums of that total
+# (16): 230 flop; 6 MUFU.
+PIPES_GRAD = {"fp32_flop": 230, "mufu": 6}
 # Calibration model (Section 2.2), per bin on top of the plain likelihood: the
 # four spline weights (9 flop, shared by the detectors); per detector two
 # spline values (2 x 7), the phase shift (1), the amplitude factor (3) and the

@@ -3,12 +3,14 @@
 // With lnL = sum_d Re[K_d Z_d] - <h|h>/2,  Z_d = sum_j G_d,j e^{-2 pi i r_d,j},
 // r_d,j = sum_m c_m B_m(f_j) + tau_d f_j, the derivative along a sampled
 // coordinate theta_k is
-//   d lnL = sum_d { Re[dK_d Z_d] + 2 pi Im[K_d S_d] } - d<h|h>/2,
-//   S_d  = sum_m dc_m W_d,m + dtau_d W_d,f,
-//   W_d,m = sum_j G_d,j e^{-2 pi i r_d,j} B_m(f_j),   W_d,f = sum_j ... f_j.
-// The bin loop therefore accumulates, per detector, Z_d and the nine complex
-// basis-weighted sums W_d,m, W_d,f (one pass over the bins, same phase
-// arithmetic as the likelihood).  The per-proposal derivatives dc_m, dtau_d,
+//   d lnL = sum_d Re[dK_d Z_d] + 2 pi [sum_m dc_m A_m + sum_d dtau_d T_d] - d<h|h>/2,
+//   y_d,j = Im(K_d G_d,j e^{-2 pi i r_d,j}),
+//   A_m = sum_j B_m(f_j) sum_d y_d,j,   T_d = sum_j f_j y_d,j
+// (d/dc_m of the phasor is -2 pi i B_m times it, and Re(-i z) = Im z).  K_d is
+// known before the bin loop, so the detectors are combined per bin: the loop
+// accumulates Z_d (complex), T_d and A_m -- 3 NDET + 8 real sums, one pass
+// over the bins with the likelihood's phase arithmetic.  The per-proposal
+// derivatives dc_m, dtau_d,
 // dK_d, d<h|h> come from the prologue evaluated on a forward-mode tangent type
 // whose value is FP64 (GWL_FP64) or a float pair (GWL_MIXED, the likelihood
 // prologue's arithmetic) while the tangents are carried in FP64 or FP32.  A
@@ -23,8 +25,14 @@
 
 namespace gwl {
 
-constexpr int kNW = kNBasis + 1;  // basis-weighted sums per detector (B_0..B_7, f)
-constexpr int kAccPerDet = 2 + 2 * kNW;  // U, V, W (re, im) x 9
+// The window sums of a proposal: [2d] U_d, [2d + 1] V_d (Z_d = U_d + i V_d),
+// [2 NDET + d] T_d, [3 NDET + m] A_m; padded to a multiple of four (16-byte
+// vector loads in the combination).
+template <int NDET>
+struct GradSums {
+  static constexpr int n = (3 * NDET + kNBasis + 3) / 4 * 4;
+};
+static int grad_sums_per_row(int n_det) { return (3 * n_det + kNBasis + 3) / 4 * 4; }
 
 template <class G>
 struct PropGrad {
@@ -178,7 +186,7 @@ struct GradArgs {
   int nw_total;
   const PropCommon* pc;
   const void* prop;
-  void* partials;  // [B][nw_total][kAccPerDet * NDET]
+  void* partials;  // [B][nw_total][GradSums<NDET>::n]
   int* work;
   const int* hist;    // [w] proposals whose last window is w
   int* status;
@@ -201,8 +209,8 @@ struct GradArgs {
 };
 
 // lnL = sum_d [Re K_d Z_d] - <h|h>/2 and d lnL / d theta_i from the window
-// sums: Z(d, 0..1) the data-template sums (U, V), W(d, k) the basis-weighted
-// ones (re, im of B_0..B_7 and f).
+// sums: Z(d, 0..1) the data-template sums (U, V), S(k) the sums T_d
+// (k = 2 NDET + d) and A_m (k = 3 NDET + m) in working precision.
 template <int NDET, class ZF>
 __device__ __forceinline__ double grad_lnl(const PropCommon* c, ZF Z) {
   double l = -0.5 * c->hh;
@@ -210,21 +218,18 @@ __device__ __forceinline__ double grad_lnl(const PropCommon* c, ZF Z) {
   for (int d = 0; d < NDET; ++d) l += c->Kr[d] * Z(d, 0) - c->Ki[d] * Z(d, 1);
   return l;
 }
-template <int NDET, class G, class ZF, class WF>
-__device__ __forceinline__ G grad_dir(const PropCommon* c, const PropGrad<G>& g, int i, ZF Z, WF W) {
-  const G twopi = (G)(2.0 * kPi);
+template <int NDET, class G, class ZF, class SF>
+__device__ __forceinline__ G grad_dir(const PropCommon* c, const PropGrad<G>& g, int i, ZF Z, SF S) {
+  G ph = (G)0;  // the phase part: sum_m dc_m A_m + sum_d dtau_d T_d
+#pragma unroll
+  for (int m = 0; m < kNBasis; ++m) ph += g.dc[m][i] * S(3 * NDET + m);
   G acc = (G)(-0.5) * g.dhh[i];
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    G Sr = g.dtau[d][i] * W(d, 2 * kNBasis), Si = g.dtau[d][i] * W(d, 2 * kNBasis + 1);
-#pragma unroll
-    for (int m = 0; m < kNBasis; ++m) {
-      Sr += g.dc[m][i] * W(d, 2 * m);
-      Si += g.dc[m][i] * W(d, 2 * m + 1);
-    }
-    acc += g.dKr[d][i] * (G)Z(d, 0) - g.dKi[d][i] * (G)Z(d, 1) + twopi * ((G)c->Kr[d] * Si + (G)c->Ki[d] * Sr);
+    ph += g.dtau[d][i] * S(2 * NDET + d);
+    acc += g.dKr[d][i] * (G)Z(d, 0) - g.dKi[d][i] * (G)Z(d, 1);
   }
-  return acc;
+  return acc + (G)(2.0 * kPi) * ph;
 }
 
 // With CAL, bin j's term of detector d is (1 + dA) G_d,j e^{-2 pi i (r_d,j - dphi)}
@@ -233,14 +238,21 @@ __device__ __forceinline__ G grad_dir(const PropCommon* c, const PropGrad<G>& g,
 template <int NDET, bool MIXED, bool CAL, typename Node>
 __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restrict__ smv, const Node* nodes,
                                           int64_t p, int j0, int jend, int lane,
-                                          typename std::conditional<MIXED, float, double>::type (&A)[NDET][kAccPerDet],
+                                          typename std::conditional<MIXED, float, double>::type (&S)[GradSums<NDET>::n],
                                           typename std::conditional<MIXED, float, double>::type (&X)[NDET]) {
   using Acc = typename std::conditional<MIXED, float, double>::type;
+  constexpr int T0 = 2 * NDET, A0 = 3 * NDET;
+#pragma unroll
+  for (int k = 0; k < GradSums<NDET>::n; ++k) S[k] = (Acc)0;
+#pragma unroll
+  for (int d = 0; d < NDET; ++d) X[d] = (Acc)0;
+  // the proposal's amplitudes K_d in working precision
+  const PropCommon* pcp = a.pc + p;
+  Acc kr[NDET], ki[NDET];
 #pragma unroll
   for (int d = 0; d < NDET; ++d) {
-    X[d] = (Acc)0;
-#pragma unroll
-    for (int k = 0; k < kAccPerDet; ++k) A[d][k] = (Acc)0;
+    kr[d] = (Acc)pcp->Kr[d];
+    ki[d] = (Acc)pcp->Ki[d];
   }
   if constexpr (MIXED) {
     const float* sm = reinterpret_cast<const float*>(smv);
@@ -267,6 +279,7 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
       } else {
         phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs);
       }
+      float Y = 0.0f;
 #pragma unroll
       for (int d = 0; d < NDET; ++d) {
         float gr = v[18 + 2 * d], gi = v[19 + 2 * d];
@@ -278,16 +291,14 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
         }
         const float uw = fmaf(gr, cs[d], gi * sn[d]);
         const float vw = fmaf(gi, cs[d], -gr * sn[d]);
-        A[d][0] += uw;
-        A[d][1] += vw;
-#pragma unroll
-        for (int m = 0; m < kNBasis; ++m) {
-          A[d][2 + 2 * m] = fmaf(uw, v[m], A[d][2 + 2 * m]);
-          A[d][3 + 2 * m] = fmaf(vw, v[m], A[d][3 + 2 * m]);
-        }
-        A[d][2 + 2 * kNBasis] = fmaf(uw, v[16], A[d][2 + 2 * kNBasis]);
-        A[d][3 + 2 * kNBasis] = fmaf(vw, v[16], A[d][3 + 2 * kNBasis]);
+        S[2 * d] += uw;
+        S[2 * d + 1] += vw;
+        const float y = fmaf(kr[d], vw, ki[d] * uw);  // Im(K_d (uw + i vw))
+        S[T0 + d] = fmaf(y, v[16], S[T0 + d]);
+        Y += y;
       }
+#pragma unroll
+      for (int m = 0; m < kNBasis; ++m) S[A0 + m] = fmaf(Y, v[m], S[A0 + m]);
     }
   } else {
     const double* sm = reinterpret_cast<const double*>(smv);
@@ -308,6 +319,7 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
       } else {
         phase_f64<NDET>(v, c, tau, sn, cs);
       }
+      double Y = 0.0;
 #pragma unroll
       for (int d = 0; d < NDET; ++d) {
         double gr = v[9 + 2 * d], gi = v[10 + 2 * d];
@@ -319,26 +331,24 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
         }
         const double uw = fma(gr, cs[d], gi * sn[d]);
         const double vw = fma(gi, cs[d], -gr * sn[d]);
-        A[d][0] += uw;
-        A[d][1] += vw;
-#pragma unroll
-        for (int m = 0; m < kNBasis; ++m) {
-          A[d][2 + 2 * m] = fma(uw, v[m], A[d][2 + 2 * m]);
-          A[d][3 + 2 * m] = fma(vw, v[m], A[d][3 + 2 * m]);
-        }
-        A[d][2 + 2 * kNBasis] = fma(uw, v[8], A[d][2 + 2 * kNBasis]);
-        A[d][3 + 2 * kNBasis] = fma(vw, v[8], A[d][3 + 2 * kNBasis]);
+        S[2 * d] += uw;
+        S[2 * d + 1] += vw;
+        const double y = fma(kr[d], vw, ki[d] * uw);
+        S[T0 + d] = fma(y, v[8], S[T0 + d]);
+        Y += y;
       }
+#pragma unroll
+      for (int m = 0; m < kNBasis; ++m) S[A0 + m] = fma(Y, v[m], S[A0 + m]);
     }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
+  for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int d = 0; d < NDET; ++d) {
+    for (int k = 0; k < A0 + kNBasis; ++k) S[k] += __shfl_xor_sync(0xffffffffu, S[k], off);
 #pragma unroll
-      for (int k = 0; k < kAccPerDet; ++k) A[d][k] += __shfl_xor_sync(0xffffffffu, A[d][k], off);
+    for (int d = 0; d < NDET; ++d)
       if constexpr (CAL) X[d] += __shfl_xor_sync(0xffffffffu, X[d], off);
-    }
+  }
 }
 
 // The calibration model's terms of lnL and of the source directions' derivatives:
@@ -425,29 +435,28 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
         parity ^= 1u;
       }
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
-        Elem A[NDET][kAccPerDet], X[NDET];
+        Elem S[GradSums<NDET>::n], X[NDET];
         if constexpr (CAL) cal_nodes_fill<NDET, MIXED>(a.theta + p * a.gstride + a.cal_par, a.nn, a.calQ, lane, nodes);
-        grad_sums<NDET, MIXED, CAL>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, A, X);
+        grad_sums<NDET, MIXED, CAL>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, S, X);
         if (ncut <= a.CH) {  // the proposal's only window (every lane holds the sums): finish it here
           const PropCommon* c = a.pc + p;
-          auto Z = [&](int d, int k) { return (double)A[d][k]; };
+          auto Z = [&](int d, int k) { return (double)S[2 * d + k]; };
+          auto Sf = [&](int k) { return S[k]; };
           auto Xf = [&](int d) { return X[d]; };
           if (lane == 0) a.lnl[p] = grad_lnl<NDET>(c, Z) + (CAL ? cal_lnl_term<NDET>(c, Xf) : 0.0);
           if (lane < a.n_dim) {
             const PropGrad<Elem>& g = reinterpret_cast<const PropGrad<Elem>*>(a.pg)[p];
-            Elem d = grad_dir<NDET>(c, g, lane, Z, [&](int dd, int k) { return A[dd][2 + k]; });
+            Elem d = grad_dir<NDET>(c, g, lane, Z, Sf);
             if constexpr (CAL) d += cal_grad_term<NDET>(c, g, lane, Xf);
             a.grad[p * a.gstride + lane] = (double)d;
           }
           return;
         }
         // lanes write the per-window sums cooperatively
-        Elem* o = reinterpret_cast<Elem*>(a.partials) + (p * a.nw_total + w) * (kAccPerDet * NDET);
+        Elem* o = reinterpret_cast<Elem*>(a.partials) + (p * a.nw_total + w) * GradSums<NDET>::n;
 #pragma unroll
-        for (int d = 0; d < NDET; ++d)
-#pragma unroll
-          for (int k2 = 0; k2 < kAccPerDet; ++k2)
-            if (lane == ((d * kAccPerDet + k2) & 31)) o[d * kAccPerDet + k2] = A[d][k2];
+        for (int k2 = 0; k2 < GradSums<NDET>::n; ++k2)
+          if (lane == k2) o[k2] = S[k2];
         if constexpr (CAL) {
           Elem* ox = reinterpret_cast<Elem*>(a.xpart) + (p * a.nw_total + w) * NDET;
 #pragma unroll
@@ -462,15 +471,15 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
 }
 
 // ---------------------------------------------------------------- combination
-// One detector's kAccPerDet window sums, read as 16-byte vectors (the sums of
-// a detector start on a 16-byte boundary: 20 floats or doubles per detector).
-template <class G>
-__device__ __forceinline__ void load_sums(const G* __restrict__ qw, G (&v)[kAccPerDet]) {
+// One window's sums of a proposal, read as 16-byte vectors (each window's
+// block starts on a 16-byte boundary: GradSums<NDET>::n is a multiple of four).
+template <int N, class G>
+__device__ __forceinline__ void load_sums(const G* __restrict__ qw, G (&v)[N]) {
   if constexpr (sizeof(G) == 4) {
-    static_assert(kAccPerDet % 4 == 0, "float sums in float4 units");
+    static_assert(N % 4 == 0, "float sums in float4 units");
     const float4* src = reinterpret_cast<const float4*>(qw);
 #pragma unroll
-    for (int k = 0; k < kAccPerDet / 4; ++k) {
+    for (int k = 0; k < N / 4; ++k) {
       const float4 x = src[k];
       v[4 * k] = x.x;
       v[4 * k + 1] = x.y;
@@ -478,10 +487,10 @@ __device__ __forceinline__ void load_sums(const G* __restrict__ qw, G (&v)[kAccP
       v[4 * k + 3] = x.w;
     }
   } else {
-    static_assert(kAccPerDet % 2 == 0, "double sums in double2 units");
+    static_assert(N % 2 == 0, "double sums in double2 units");
     const double2* src = reinterpret_cast<const double2*>(qw);
 #pragma unroll
-    for (int k = 0; k < kAccPerDet / 2; ++k) {
+    for (int k = 0; k < N / 2; ++k) {
       const double2 x = src[k];
       v[2 * k] = x.x;
       v[2 * k + 1] = x.y;
@@ -490,8 +499,8 @@ __device__ __forceinline__ void load_sums(const G* __restrict__ qw, G (&v)[kAccP
 }
 
 // Multi-window proposals: a thread per (proposal, direction of the row).  The
-// source directions add the windows' sums (Z in FP64, the basis-weighted W in
-// working precision; with CAL also the X_d corrections); the calibration
+// source directions add the windows' sums (Z in FP64, T_d and A_m in working
+// precision; with CAL also the X_d corrections); the calibration
 // directions add the windows' derivatives of k_cal_moments in window order.
 template <int NDET, bool MIXED, bool CAL>
 __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
@@ -521,31 +530,31 @@ __global__ void k_finalize_grad(const PropCommon* __restrict__ pc,
     grad[p * gstride + i] = s;
     return;
   }
-  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * (kAccPerDet * NDET);
+  constexpr int N = GradSums<NDET>::n;
+  const G* q = reinterpret_cast<const G*>(partials_v) + (int64_t)p * nw_total * N;
   double Z[NDET][2], X[NDET];
-  G W[NDET][2 * kNW];
+  G S[N];
 #pragma unroll
-  for (int d = 0; d < NDET; ++d) {
-    Z[d][0] = Z[d][1] = X[d] = 0.0;
+  for (int d = 0; d < NDET; ++d) Z[d][0] = Z[d][1] = X[d] = 0.0;
 #pragma unroll
-    for (int k = 0; k < 2 * kNW; ++k) W[d][k] = (G)0;
-  }
+  for (int k = 0; k < N; ++k) S[k] = (G)0;
   for (int w = 0; w < nwp; ++w) {
+    G v[N];
+    load_sums(q + (int64_t)w * N, v);
 #pragma unroll
     for (int d = 0; d < NDET; ++d) {
-      G v[kAccPerDet];
-      load_sums(q + w * (kAccPerDet * NDET) + d * kAccPerDet, v);
-      Z[d][0] += (double)v[0];
-      Z[d][1] += (double)v[1];
-#pragma unroll
-      for (int k = 0; k < 2 * kNW; ++k) W[d][k] += v[2 + k];
+      Z[d][0] += (double)v[2 * d];
+      Z[d][1] += (double)v[2 * d + 1];
       if constexpr (CAL) X[d] += (double)reinterpret_cast<const G*>(xpart_v)[((int64_t)p * nw_total + w) * NDET + d];
     }
+#pragma unroll
+    for (int k = 2 * NDET; k < N; ++k) S[k] += v[k];
   }
   auto Zf = [&](int d, int k) { return Z[d][k]; };
+  auto Sf = [&](int k) { return S[k]; };
   auto Xf = [&](int d) { return X[d]; };
   if (i == 0) lnl[p] = grad_lnl<NDET>(&c, Zf) + (CAL ? cal_lnl_term<NDET>(&c, Xf) : 0.0);
-  G g = grad_dir<NDET>(&c, pg[p], i, Zf, [&](int d, int k) { return W[d][k]; });
+  G g = grad_dir<NDET>(&c, pg[p], i, Zf, Sf);
   if constexpr (CAL) g += cal_grad_term<NDET>(&c, pg[p], i, Xf);
   grad[p * gstride + i] = (double)g;
 }
@@ -561,7 +570,7 @@ static int grad_window_of(const gwl_ctx* c) { return c->grad_window > c->M ? (in
 static int64_t grad_sums_bytes(const gwl_ctx* c, int64_t B) {
   const int CH = grad_window_of(c);
   const int64_t nw = (c->M + CH - 1) / CH;
-  return B * nw * kAccPerDet * c->n_det *
+  return B * nw * grad_sums_per_row(c->n_det) *
          (int64_t)(c->opt.precision == GWL_MIXED ? sizeof(float) : sizeof(double));
 }
 static int64_t grad_x_bytes(const gwl_ctx* c, int64_t B) {
