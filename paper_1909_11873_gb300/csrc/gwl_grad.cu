@@ -176,6 +176,214 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
   if ((threadIdx.x & 31) == 0 && ncut > 0) atomicMax(&work[0], ncut);
 }
 
+// The mixed path's tangent prologue in the shape of the likelihood's: a CTA of
+// four warps takes 32 rows along one sampled direction (blockIdx.y), and its
+// warps play the likelihood prologue's roles on tangent values (float-pair
+// value, FP32 tangent along that direction), exchanging them through shared
+// memory, so that each warp's chain is one role's instead of the whole model's.
+//   phase 1: ln(pi Mc T_sun) and the amplitude (warp 0); the PN coefficients
+//            and ln eta (warp 1); the sky angles and the delays tau_d (warp 2);
+//            psi and iota (warp 3)
+//   phase 2: the basis coefficients c_m (warp 0); the antenna patterns
+//            (warp 1); K's phase angle (warp 2); the cut and H_d there (warp 3)
+//   phase 3: K_d and its <h|h> term on warp d, then <h|h> on warp 0.
+// The direction-0 CTAs also write the rows' values (coefficients, delays, K_d,
+// <h|h>, cut) and count them in the work counters.
+struct ProSmemTan {
+  using T = Tan<1, float, FF>;
+  T lmc[32], leta[32], amp[32], eta[32];
+  T phi[6][32];
+  T sky[4][32];
+  T ori[3][32];
+  T P[2 * kMaxDet][32];
+  T ang[2][32];           // sin, cos of K's phase angle
+  T hh[kMaxDet][32];      // per-detector <h|h> terms
+  double Hc[kMaxDet][32]; // H_d at the cut bin
+  int ncut[32];
+};
+
+__global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const double* __restrict__ theta, int64_t B,
+                                                              PropMixed* __restrict__ pm, PropCommon* __restrict__ pc,
+                                                              PropGrad<float>* __restrict__ pg, int* __restrict__ work,
+                                                              int* __restrict__ hist, int CH) {
+  // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
+  cudaTriggerProgrammaticLaunchCompletion();
+  using T = Tan<1, float, FF>;
+  __shared__ ProSmemTan sm;
+  const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dir = blockIdx.y;  // the sampled direction whose tangents this CTA carries
+  const bool values = dir == 0;
+  const int64_t p = (int64_t)blockIdx.x * 32 + lane;
+  const bool valid = p < B;
+  double th[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) th[k] = 1.0;
+  if (valid) expand_theta(s, theta + p * s.stride, th);
+  const bool ok = valid && physical(th);
+  if (!ok) {  // keep every function below on a harmless argument
+    th[0] = 10.0; th[1] = 0.5; th[2] = th[3] = 0.0; th[4] = 100.0;
+#pragma unroll
+    for (int k = 5; k < 11; ++k) th[k] = 0.0;
+  }
+  auto tan_of = [&](int k) {
+    T x = tan_const<1, float, FF>(th[k]);
+    if (s.param_pos[k] == dir) x.d[0] = 1.0f;
+    return x;
+  };
+  PropGrad<float>* g = valid ? pg + p : nullptr;
+
+  // ---- phase 1
+  if (role == 0) {
+    const T lmc = log(tan_of(0) * (kPi * kTsun));  // ln(pi Mc T_sun)
+    sm.lmc[lane] = lmc;
+    sm.amp[lane] = exp((lmc - kLnPi) * (5.0 / 6.0)) * (kAmpConst * kC / kMpc * s.amp_scale) / tan_of(4);
+  } else if (role == 1) {
+    const PNCoeffs<T> P = pn_coeffs(tan_of(1), tan_of(2), tan_of(3));
+    sm.leta[lane] = log(P.eta);
+    sm.eta[lane] = P.eta;
+    sm.phi[0][lane] = P.p2;
+    sm.phi[1][lane] = P.p3;
+    sm.phi[2][lane] = P.p4;
+    sm.phi[3][lane] = P.p5c;
+    sm.phi[4][lane] = P.p6c;
+    sm.phi[5][lane] = P.p7;
+  } else if (role == 2) {
+    const Sky<T> k = sky_trig(tan_of(7), tan_of(8), s.gmst);
+    sm.sky[0][lane] = k.sl;
+    sm.sky[1][lane] = k.cl;
+    sm.sky[2][lane] = k.sd;
+    sm.sky[3][lane] = k.cd;
+    const T tc = tan_of(9);
+#pragma unroll 1
+    for (int d = 0; d < kMaxDet; ++d) {
+      T tau = tan_const<1, float, FF>(0.0);
+      if (d < s.n_det && ok) tau = delay_vc(tc, k, s.vtx_c_ff[d]);
+      if (valid) {
+        g->dtau[d][dir] = tau.d[0];
+        if (values) {
+          pm[p].th[d] = tau.v.hi;
+          pm[p].tl[d] = tau.v.lo;
+        }
+      }
+    }
+  } else {
+    if (valid && values) prefetch_cut_H(s, th[0], th[1]);  // read on warp 3 in phase 2
+    T sp, cp;
+    sincos(tan_of(6), &sp, &cp);
+    sm.ori[0][lane] = sp;
+    sm.ori[1][lane] = cp;
+    sm.ori[2][lane] = cos(tan_of(5));
+  }
+  __syncthreads();
+
+  // ---- phase 2
+  if (role == 0) {
+    Scale<T> S;
+    S.la = sm.lmc[lane] - 0.6 * sm.leta[lane];
+    S.a13 = exp(S.la * (1.0 / 3.0));
+    S.amp = sm.amp[lane];
+    PNCoeffs<T> P;
+    P.eta = sm.eta[lane];
+    P.p2 = sm.phi[0][lane];
+    P.p3 = sm.phi[1][lane];
+    P.p4 = sm.phi[2][lane];
+    P.p5c = sm.phi[3][lane];
+    P.p6c = sm.phi[4][lane];
+    P.p7 = sm.phi[5][lane];
+    T c[kNBasis], ccyc;
+    basis_coeffs(P, S, c, ccyc);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < kNBasis; ++m) {
+        g->dc[m][dir] = ok ? c[m].d[0] : 0.0f;
+        if (values) {
+          pm[p].ch[m] = ok ? c[m].v.hi : 0.0f;
+          pm[p].cl[m] = ok ? c[m].v.lo : 0.0f;
+        }
+      }
+    }
+  } else if (role == 1) {
+    Sky<T> k;
+    k.sl = sm.sky[0][lane];
+    k.cl = sm.sky[1][lane];
+    k.sd = sm.sky[2][lane];
+    k.cd = sm.sky[3][lane];
+    const T sp = sm.ori[0][lane], cp = sm.ori[1][lane], ci = sm.ori[2][lane];
+#pragma unroll 1
+    for (int d = 0; d < kMaxDet; ++d) {
+      T Pr = tan_const<1, float, FF>(0.0), Pi = Pr;
+      if (d < s.n_det) response(k, sp, cp, ci, s.geom_ff[d], Pr, Pi);
+      sm.P[2 * d][lane] = Pr;
+      sm.P[2 * d + 1][lane] = Pi;
+    }
+  } else if (role == 2) {
+    // the same constant-phase cycles as basis_coeffs forms on warp 0
+    const T la = sm.lmc[lane] - 0.6 * sm.leta[lane];
+    const T ccyc = const_cycles(cycles_pref(sm.eta[lane]), sm.phi[3][lane], la);
+    T sa, ca;
+    k_angle(tan_of(10), ccyc, sa, ca);
+    sm.ang[0][lane] = sa;
+    sm.ang[1][lane] = ca;
+  } else {
+    const T la = sm.lmc[lane] - 0.6 * sm.leta[lane];
+    const T a13 = exp(la * (1.0 / 3.0));
+    int ncut = (int)s.M;
+    if (s.fcut_mode == 0) ncut = count_bins_le(s, vval(1.0 / (kSix32 * (a13.v * a13.v * a13.v))));
+    if (!ok) ncut = 0;
+    sm.ncut[lane] = ncut;
+#pragma unroll
+    for (int d = 0; d < kMaxDet; ++d) sm.Hc[d][lane] = (d < s.n_det && ncut > 0) ? s.H[(int64_t)d * s.M + ncut - 1] : 0.0;
+  }
+  __syncthreads();
+
+  // ---- phase 3: detector d on warp d
+  const int ncut = sm.ncut[lane];
+  if (role < s.n_det) {
+    const int d = role;
+    T Kr = tan_const<1, float, FF>(0.0), Ki = Kr, hd = Kr;
+    if (ok) {
+      const T amp = sm.amp[lane], Pr = sm.P[2 * d][lane], Pi = sm.P[2 * d + 1][lane];
+      const T sa = sm.ang[0][lane], ca = sm.ang[1][lane];
+      Kr = amp * (Pr * ca - Pi * sa);
+      Ki = amp * (Pr * sa + Pi * ca);
+      if (ncut > 0) hd = (amp * amp) * (Pr * Pr + Pi * Pi) * ff_from(sm.Hc[d][lane]);
+    }
+    sm.hh[d][lane] = hd;
+    if (valid) {
+      g->dKr[d][dir] = Kr.d[0];
+      g->dKi[d][dir] = Ki.d[0];
+      if (values) {
+        pc[p].Kr[d] = vval(Kr.v);
+        pc[p].Ki[d] = vval(Ki.v);
+      }
+    }
+  } else if (role < kMaxDet && valid) {
+    g->dKr[role][dir] = 0.0f;
+    g->dKi[role][dir] = 0.0f;
+    if (values) pc[p].Kr[role] = pc[p].Ki[role] = 0.0;
+  }
+  __syncthreads();
+  if (role == 0) {
+    T hh = tan_const<1, float, FF>(0.0);
+    for (int d = 0; d < s.n_det; ++d) hh = hh + sm.hh[d][lane];  // detector order, as the single-thread form
+    if (valid) {
+      g->dhh[dir] = hh.d[0];
+      if (values) {
+        pc[p].hh = vval(hh.v);
+        pc[p].ncut = ncut;
+        pc[p].flag = ok ? 0 : 1;
+      }
+    }
+    if (values) {
+      hist_last_window(valid ? ncut : 0, CH, hist);
+      int nm = valid ? ncut : 0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
+      if (lane == 0 && nm > 0) atomicMax(&work[0], nm);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- bin loop
 struct GradArgs {
   const void* tab;
@@ -599,13 +807,25 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
-    constexpr int kTanGroup = tan_group<MIXED>();
-    const int ngrp = (c->opt.n_dim + kTanGroup - 1) / kTanGroup;
-    const int64_t nt = B * ngrp;
-    k_prologue_grad<MIXED><<<(unsigned)((nt + 63) / 64), 64, 0, st>>>(c->seg, theta, B, ngrp, c->d_pm, c->d_pf,
-                                                                          c->d_pc,
-                                                                          reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
-                                                                          c->d_work, window_hist(c), CH);
+    // the role form while its CTAs stay within about five per SM (measured on the
+    // 8 s workload, 11-D: prologue 12.9 / 14.5 / 18.5 us against 19.7 / 18.7 /
+    // 20.0 us at B = 256 / 1024 / 2048; beyond, its four threads per row and
+    // direction outgrow a wave and one thread per row and direction is faster)
+    const int64_t role_ctas = (B + 31) / 32 * c->opt.n_dim;
+    if (MIXED && role_ctas <= 5 * (int64_t)c->num_sms) {
+      const dim3 grid((unsigned)((B + 31) / 32), (unsigned)c->opt.n_dim);
+      k_prologue_grad_roles<<<grid, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pc,
+                                                  reinterpret_cast<PropGrad<float>*>(c->d_pgrad), c->d_work,
+                                                  window_hist(c), CH);
+    } else {
+      constexpr int kTanGroup = tan_group<MIXED>();
+      const int ngrp = (c->opt.n_dim + kTanGroup - 1) / kTanGroup;
+      const int64_t nt = B * ngrp;
+      k_prologue_grad<MIXED><<<(unsigned)((nt + 63) / 64), 64, 0, st>>>(c->seg, theta, B, ngrp, c->d_pm, c->d_pf,
+                                                                            c->d_pc,
+                                                                            reinterpret_cast<PropGrad<G>*>(c->d_pgrad),
+                                                                            c->d_work, window_hist(c), CH);
+    }
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
