@@ -67,12 +67,15 @@ LEGS = ("fp64", "fp64ph", "grad", "cal", "calgrad", "c1", "c3", "c4", "c5", "ns"
 PIPES_MIXED = {"fp32_flop": 56, "mufu": 6}
 HBM_BYTES_PER_EVAL = 96
 # The gradient bin loop per pair: the exact float-float phase per bin (the
-# 8-term sum, 112, and per detector the delay term, TwoSum and reduction,
-# 3 x 20) -> 172; per detector the data-weighted phasor (6), Z_d (2), the
-# imaginary part of K_d times it (3), its f-weighted sum (2) and the sum over
-# detectors (1) -> 3 x 14 = 42; the eight basis-weighted sums of that total
-# (16): 230 flop; 6 MUFU.
-PIPES_GRAD = {"fp32_flop": 230, "mufu": 6}
+# 8-term sum, pairwise: 8 TwoProducts, 7 TwoSums and the low-part terms, 114;
+# per detector the delay term, TwoSum and reduction, 3 x 20) -> 174; per
+# detector the sine and cosine of the reduced phase by their series on the
+# FP32 pipe (reduction 5, the two polynomials 18, scaling 2: 25) -> 75; per
+# detector the data-weighted phasor (6), Z_d (2), the imaginary part of K_d
+# times it (3), its f-weighted sum (2) and the sum over detectors (1) ->
+# 3 x 14 = 42; the eight basis-weighted sums of that total (16): 307 flop;
+# no MUFU.
+PIPES_GRAD = {"fp32_flop": 307, "mufu": 0}
 # Calibration model (Section 2.2), per bin on top of the plain likelihood: the
 # four spline weights (9 flop, shared by the detectors); per detector two
 # spline values (2 x 7), the phase shift (1), the amplitude factor (3) and the

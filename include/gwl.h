@@ -285,19 +285,26 @@ int64_t ns_state_doubles(int64_t K, int64_t D, int64_t max_dead);
 
 /* Diagnostic: the float-float elementary functions of the mixed prologue
  * (about 48 significant bits on the FP32 pipe) on n arguments, for checking
- * their accuracy against FP64 references.  (An interface addition without a
+ * their accuracy against FP64 references, and the FP32 sin(pi x), cos(pi x)
+ * of the mixed gradient's bin loop.  (An interface addition without a
  * counterpart in the paper.)
- *   x_dev   dev [n] FP64 arguments (split into float pairs first); the
- *           domains of the functions: exp |x| < 87 (a normal float result),
- *           ln 2^-126 < x < 2^127, sin and cos |x| < 2^11 (the reduction by
- *           pi/2 is exact there); outside them the results are unspecified
- *   fn      GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN or GWL_FF_COS
- *   out_dev dev [n] FP64 results (the float pair summed in FP64)
+ *   x_dev   dev [n] FP64 arguments (split into float pairs first; rounded to
+ *           FP32 for GWL_F32_SINPI and GWL_F32_COSPI); the domains of the
+ *           functions: exp |x| < 87 (a normal float result), ln 2^-126 < x <
+ *           2^127, sin and cos |x| < 2^11 (the reduction by pi/2 is exact
+ *           there), sinpi and cospi |x| <= 1.5; outside them the results are
+ *           unspecified
+ *   fn      GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN, GWL_FF_COS, GWL_F32_SINPI or
+ *           GWL_F32_COSPI
+ *   out_dev dev [n] FP64 results (the float pair summed in FP64, or the
+ *           FP32 result widened)
  * Enqueues one kernel on the stream and returns. */
 #define GWL_FF_EXP 0
 #define GWL_FF_LOG 1
 #define GWL_FF_SIN 2
 #define GWL_FF_COS 3
+#define GWL_F32_SINPI 4
+#define GWL_F32_COSPI 5
 int gwl_ff_eval(const double* x_dev, int64_t n, int fn, double* out_dev, void* stream);
 
 /* Diagnostic: the Philox4x32-10 generator of ns_replace and ns_run (Salmon,

@@ -49,6 +49,33 @@ __device__ __forceinline__ float nearest_int(float x) {
   return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
 }
 
+// sin(pi x) and cos(pi x) for |x| <= ~1.5 half-turns: x = q/2 + r with q the
+// nearest integer to 2x (by the 1.5 * 2^23 shift, whose low mantissa bits are
+// q mod 4) and |r| <= 1/4 exact; sin(pi r) and cos(pi r) from their Taylor
+// series through r^9 and r^10 (truncation below 3e-9), Horner's rule on r^2;
+// then the rotation by q quarter turns.
+__device__ __forceinline__ void sincospi_small(float x, float* s, float* c) {
+  const float t = __fadd_rn(2.0f * x, 12582912.0f);
+  const int qi = __float_as_int(t) & 3;
+  const float r = __fmaf_rn(__fsub_rn(t, 12582912.0f), -0.5f, x);
+  const float r2 = r * r;
+  // (-1)^k pi^(2k+1) / (2k+1)! and (-1)^k pi^(2k) / (2k)!
+  float ps = 0.08214588661112819f;
+  ps = __fmaf_rn(ps, r2, -0.5992645293207919f);
+  ps = __fmaf_rn(ps, r2, 2.550164039877345f);
+  ps = __fmaf_rn(ps, r2, -5.167712780049969f);
+  ps = __fmaf_rn(ps, r2, 3.141592653589793f);
+  float pc = -0.02580689139001405f;
+  pc = __fmaf_rn(pc, r2, 0.23533063035889312f);
+  pc = __fmaf_rn(pc, r2, -1.3352627688545893f);
+  pc = __fmaf_rn(pc, r2, 4.058712126416768f);
+  pc = __fmaf_rn(pc, r2, -4.934802200544679f);
+  const float sp = ps * r, cp = __fmaf_rn(pc, r2, 1.0f);
+  float ss = (qi & 1) ? cp : sp, cc = (qi & 1) ? sp : cp;
+  *s = (qi & 2) ? -ss : ss;
+  *c = ((qi + 1) & 2) ? -cc : cc;
+}
+
 // Phase of one bin in float-float arithmetic, reduced modulo one cycle, and its
 // sine and cosine: (sn_d, cs_d) = sin/cos 2 pi r_d, r_d = S + tau_d f.
 // S = sum_m c_m B_m is summed as an unevaluated float pair (s, lo); tau_d f is
@@ -69,19 +96,45 @@ __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], con
                                             const float (&tl)[NDET], float (&sn)[NDET], float (&cs)[NDET],
                                             const float* shift = nullptr) {
   float s, lo;
-  {
-    float e;
-    two_prod(ch[0], v[0], s, e);
-    lo = __fmaf_rn(cl[0], v[0], __fmaf_rn(ch[0], v[kNBasis], e));
-  }
+  if constexpr (EXACT_SUM) {
+    // the eight products' high parts summed pairwise (three levels of TwoSum
+    // instead of a chain of seven), their errors and the low-part terms in two
+    // running sums
+    static_assert(kNBasis == 8, "pairwise sum written for eight basis functions");
+    float p[kNBasis], l2[2] = {0.0f, 0.0f};
 #pragma unroll
-  for (int m = 1; m < kNBasis; ++m) {
-    const float bh = v[m], bl = v[kNBasis + m];
-    float p, e, t, q;
-    two_prod(ch[m], bh, p, e);
-    two_sum(s, p, t, q);
-    s = t;
-    lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
+    for (int m = 0; m < kNBasis; ++m) {
+      float e;
+      two_prod(ch[m], v[m], p[m], e);
+      l2[m & 1] = __fmaf_rn(ch[m], v[kNBasis + m], __fmaf_rn(cl[m], v[m], l2[m & 1] + e));
+    }
+    float a[4], qa = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float q;
+      two_sum(p[2 * k], p[2 * k + 1], a[k], q);
+      qa += q;
+    }
+    float b0, b1, q0, q1, qc;
+    two_sum(a[0], a[1], b0, q0);
+    two_sum(a[2], a[3], b1, q1);
+    two_sum(b0, b1, s, qc);
+    lo = (l2[0] + l2[1]) + (qa + ((q0 + q1) + qc));
+  } else {
+    {
+      float e;
+      two_prod(ch[0], v[0], s, e);
+      lo = __fmaf_rn(cl[0], v[0], __fmaf_rn(ch[0], v[kNBasis], e));
+    }
+#pragma unroll
+    for (int m = 1; m < kNBasis; ++m) {
+      const float bh = v[m], bl = v[kNBasis + m];
+      float p, e, t, q;
+      two_prod(ch[m], bh, p, e);
+      two_sum(s, p, t, q);
+      s = t;
+      lo = __fmaf_rn(ch[m], bl, __fmaf_rn(cl[m], bh, lo + (q + e)));
+    }
   }
   const float fh = v[16], fl = v[17];
   if constexpr (EXACT_SUM) {
@@ -96,8 +149,9 @@ __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], con
       if (shift) fr = fr - shift[d];
       // the gradient's basis-weighted sums amplify the absolute error of the
       // hardware sine and cosine (~4e-7, a smooth function of the argument, so
-      // it adds up across bins): the accurate FP32 sincospi (|2 fr| <= ~1.1)
-      sincospif(2.0f * fr, &sn[d], &cs[d]);
+      // it adds up across bins): the series on the reduced argument instead
+      // (|2 fr| <= ~1.1)
+      sincospi_small(2.0f * fr, &sn[d], &cs[d]);
     }
   } else {
     const float sf = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);

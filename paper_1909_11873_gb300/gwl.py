@@ -370,11 +370,12 @@ class Context:
         return lib().gwl_launch_count(self._h)
 
 
-GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN, GWL_FF_COS = range(4)
+GWL_FF_EXP, GWL_FF_LOG, GWL_FF_SIN, GWL_FF_COS, GWL_F32_SINPI, GWL_F32_COSPI = range(6)
 
 
 def ff_eval(x, fn, stream=None):
-    """The library's float-float exp / log / sin / cos (GWL_FF_*) of a float64 CUDA tensor."""
+    """The library's float-float exp / log / sin / cos (GWL_FF_*), or the FP32 sin(pi x) / cos(pi x) of the
+    gradient's bin loop (GWL_F32_*), of a float64 CUDA tensor."""
     import torch
     out = torch.empty_like(x)
     _check(lib().gwl_ff_eval(_ptr(x), x.numel(), int(fn), _ptr(out), _stream(stream)), "gwl_ff_eval")

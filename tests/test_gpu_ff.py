@@ -49,3 +49,24 @@ def test_ff_sin_cos(g, fn):
     code = g.GWL_FF_SIN if fn == "sin" else g.GWL_FF_COS
     ref = np.sin(x) if fn == "sin" else np.cos(x)
     assert np.all(np.abs(run(g, x, code) - ref) < 3e-14 + 2.0 ** -47 * np.abs(x))
+
+
+@pytest.mark.parametrize("fn", ["sinpi", "cospi"])
+def test_f32_sincospi(g, fn):
+    """The FP32 sin(pi x), cos(pi x) of the mixed gradient's bin loop (Taylor series on the argument reduced
+    to |r| <= 1/4, then the quarter-turn rotation) over |x| <= 1.5, with the quarter-turn boundaries and
+    their neighbours: absolute error against FP64 at the FP32 argument below 2^-22 (the hardware sine's is
+    ~4e-7), and exact values at the quarter turns' zeros and ones."""
+    k = np.arange(-6, 7) / 4.0
+    x = np.concatenate([np.linspace(-1.5, 1.5, 60001), k, np.nextafter(k.astype(np.float32), np.float32(2)),
+                        np.nextafter(k.astype(np.float32), np.float32(-2)),
+                        np.random.default_rng(3).uniform(-1.2, 1.2, 40000)]).astype(np.float32).astype(np.float64)
+    code = g.GWL_F32_SINPI if fn == "sinpi" else g.GWL_F32_COSPI
+    ref = np.sin(np.pi * x) if fn == "sinpi" else np.cos(np.pi * x)
+    got = run(g, x, code)
+    assert np.max(np.abs(got - ref)) < 2.0 ** -22
+    # at the multiples of 1/2 the reduced argument is zero: the results are exactly 0 or +-1
+    h = np.arange(-3, 4) / 2.0
+    got_h = run(g, h, code)
+    ref_h = np.round(np.sin(np.pi * h) if fn == "sinpi" else np.cos(np.pi * h))
+    assert np.array_equal(np.abs(got_h), np.abs(ref_h)) and np.all(got_h * ref_h >= 0)
