@@ -687,7 +687,10 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
 
   // Each warp takes its first claim in window 0 at once (the window's rows are
   // being staged already), so that the claim's round trip overlaps the reads
-  // that place the CTA among the windows instead of following them.
+  // that place the CTA among the windows instead of following them.  That
+  // claim takes two proposals where the window holds more than two per warp;
+  // the later claims hold about one active proposal each, which shortens the
+  // tail of the last claims.
   const int64_t b_cap = a.B < 0x7fffffff ? a.B : 0x7fffffff;
   const int chunk0 = claim_size(a.B, (int)b_cap);
   int first = 0;
@@ -821,7 +824,7 @@ __global__ void __launch_bounds__(256, 2) k_window(WinArgs a) {
           __syncthreads();
         }
       }
-      drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane,
+      drain_window(ctr, a.B, claim_size(a.B, n_w, false), a.pc, j0, lane,
                    [&](int64_t p, int ncut) { body(w, j0, j1, p, ncut); }, first, use_first ? chunk0 : 0);
     }
     have_first = false;

@@ -10,7 +10,8 @@
 // sweeps on through the later windows, skipping those already drained.  Inside
 // a window warps claim proposals in chunks sized so that a claim holds about
 // one active proposal (B / n_w of them, 1 .. 32), or two when the window holds
-// more than two active proposals per warp of the grid.
+// more than two active proposals per warp of the grid (the likelihood's bin
+// loop takes pairs in its first claim only).
 #pragma once
 
 #include "gwl_device.cuh"
@@ -122,13 +123,13 @@ __device__ __forceinline__ int start_window(const int* __restrict__ hist, int w_
 }
 
 // Proposals per claim in a window with n_active active proposals of B: about
-// one active proposal per claim, or two (half the atomics on the window's
-// counter) when the window holds more than two active proposals per warp of
-// the grid, so that small batches keep every warp busy.
-__device__ __forceinline__ int claim_size(int64_t B, int n_active) {
+// one active proposal per claim, or (pair) two, half the atomics on the
+// window's counter, when the window holds more than two active proposals per
+// warp of the grid, so that small batches keep every warp busy.
+__device__ __forceinline__ int claim_size(int64_t B, int n_active, bool pair = true) {
   if (n_active <= 0) return 32;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int per = n_active >= 2 * warps ? 2 : 1;
+  const int per = pair && n_active >= 2 * warps ? 2 : 1;
   const int64_t c = per * B / n_active;
   return c < per ? per : (c > 32 ? 32 : (int)c);
 }
