@@ -177,10 +177,11 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
 }
 
 // The mixed path's tangent prologue in the shape of the likelihood's: a CTA of
-// four warps takes 32 rows along one sampled direction (blockIdx.y), and its
-// warps play the likelihood prologue's roles on tangent values (float-pair
-// value, FP32 tangent along that direction), exchanging them through shared
-// memory, so that each warp's chain is one role's instead of the whole model's.
+// four warps takes 32 rows along N sampled directions (N blockIdx.y, ...,
+// N blockIdx.y + N - 1), and its warps play the likelihood prologue's roles on
+// tangent values (float-pair value, FP32 tangents along those directions),
+// exchanging them through shared memory, so that each warp's chain is one
+// role's instead of the whole model's.
 //   phase 1: ln(pi Mc T_sun) and the amplitude (warp 0); the PN coefficients
 //            and ln eta (warp 1); the sky angles and the delays tau_d (warp 2);
 //            psi and iota (warp 3)
@@ -189,8 +190,9 @@ __global__ void __launch_bounds__(64) k_prologue_grad(SegInfo s, const double* _
 //   phase 3: K_d and its <h|h> term on warp d, then <h|h> on warp 0.
 // The direction-0 CTAs also write the rows' values (coefficients, delays, K_d,
 // <h|h>, cut) and count them in the work counters.
+template <int N>
 struct ProSmemTan {
-  using T = Tan<1, float, FF>;
+  using T = Tan<N, float, FF>;
   T lmc[32], leta[32], amp[32], eta[32];
   T phi[6][32];
   T sky[4][32];
@@ -202,17 +204,21 @@ struct ProSmemTan {
   int ncut[32];
 };
 
+template <int N>
 __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const double* __restrict__ theta, int64_t B,
                                                               PropMixed* __restrict__ pm, PropCommon* __restrict__ pc,
                                                               PropGrad<float>* __restrict__ pg, int* __restrict__ work,
                                                               int* __restrict__ hist, int CH) {
   // let the bin loop launch now: its CTAs stage table rows, then wait for this grid to complete
   cudaTriggerProgrammaticLaunchCompletion();
-  using T = Tan<1, float, FF>;
-  __shared__ ProSmemTan sm;
+  using T = Tan<N, float, FF>;
+  __shared__ ProSmemTan<N> sm;
   const int role = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int dir = blockIdx.y;  // the sampled direction whose tangents this CTA carries
+  const int dir = blockIdx.y * N;  // the first sampled direction whose tangents this CTA carries
   const bool values = dir == 0;
+  // tangent j goes to slot dir + j of the row's derivative arrays (slots past
+  // the eleventh are not written; those past n_dim carry zero tangents)
+  auto slot_ok = [&](int j) { return dir + j < 11; };
   const int64_t p = (int64_t)blockIdx.x * 32 + lane;
   const bool valid = p < B;
   double th[11];
@@ -226,8 +232,10 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
     for (int k = 5; k < 11; ++k) th[k] = 0.0;
   }
   auto tan_of = [&](int k) {
-    T x = tan_const<1, float, FF>(th[k]);
-    if (s.param_pos[k] == dir) x.d[0] = 1.0f;
+    T x = tan_const<N, float, FF>(th[k]);
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (s.param_pos[k] == dir + j) x.d[j] = 1.0f;
     return x;
   };
   PropGrad<float>* g = valid ? pg + p : nullptr;
@@ -256,10 +264,12 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
     const T tc = tan_of(9);
 #pragma unroll 1
     for (int d = 0; d < kMaxDet; ++d) {
-      T tau = tan_const<1, float, FF>(0.0);
+      T tau = tan_const<N, float, FF>(0.0);
       if (d < s.n_det && ok) tau = delay_vc(tc, k, s.vtx_c_ff[d]);
       if (valid) {
-        g->dtau[d][dir] = tau.d[0];
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+          if (slot_ok(j)) g->dtau[d][dir + j] = tau.d[j];
         if (values) {
           pm[p].th[d] = tau.v.hi;
           pm[p].tl[d] = tau.v.lo;
@@ -295,7 +305,9 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
     if (valid) {
 #pragma unroll
       for (int m = 0; m < kNBasis; ++m) {
-        g->dc[m][dir] = ok ? c[m].d[0] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+          if (slot_ok(j)) g->dc[m][dir + j] = ok ? c[m].d[j] : 0.0f;
         if (values) {
           pm[p].ch[m] = ok ? c[m].v.hi : 0.0f;
           pm[p].cl[m] = ok ? c[m].v.lo : 0.0f;
@@ -311,7 +323,7 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
     const T sp = sm.ori[0][lane], cp = sm.ori[1][lane], ci = sm.ori[2][lane];
 #pragma unroll 1
     for (int d = 0; d < kMaxDet; ++d) {
-      T Pr = tan_const<1, float, FF>(0.0), Pi = Pr;
+      T Pr = tan_const<N, float, FF>(0.0), Pi = Pr;
       if (d < s.n_det) response(k, sp, cp, ci, s.geom_ff[d], Pr, Pi);
       sm.P[2 * d][lane] = Pr;
       sm.P[2 * d + 1][lane] = Pi;
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
   const int ncut = sm.ncut[lane];
   if (role < s.n_det) {
     const int d = role;
-    T Kr = tan_const<1, float, FF>(0.0), Ki = Kr, hd = Kr;
+    T Kr = tan_const<N, float, FF>(0.0), Ki = Kr, hd = Kr;
     if (ok) {
       const T amp = sm.amp[lane], Pr = sm.P[2 * d][lane], Pi = sm.P[2 * d + 1][lane];
       const T sa = sm.ang[0][lane], ca = sm.ang[1][lane];
@@ -350,24 +362,34 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
     }
     sm.hh[d][lane] = hd;
     if (valid) {
-      g->dKr[d][dir] = Kr.d[0];
-      g->dKi[d][dir] = Ki.d[0];
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        if (slot_ok(j)) {
+          g->dKr[d][dir + j] = Kr.d[j];
+          g->dKi[d][dir + j] = Ki.d[j];
+        }
       if (values) {
         pc[p].Kr[d] = vval(Kr.v);
         pc[p].Ki[d] = vval(Ki.v);
       }
     }
   } else if (role < kMaxDet && valid) {
-    g->dKr[role][dir] = 0.0f;
-    g->dKi[role][dir] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (slot_ok(j)) {
+        g->dKr[role][dir + j] = 0.0f;
+        g->dKi[role][dir + j] = 0.0f;
+      }
     if (values) pc[p].Kr[role] = pc[p].Ki[role] = 0.0;
   }
   __syncthreads();
   if (role == 0) {
-    T hh = tan_const<1, float, FF>(0.0);
+    T hh = tan_const<N, float, FF>(0.0);
     for (int d = 0; d < s.n_det; ++d) hh = hh + sm.hh[d][lane];  // detector order, as the single-thread form
     if (valid) {
-      g->dhh[dir] = hh.d[0];
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+        if (slot_ok(j)) g->dhh[dir + j] = hh.d[j];
       if (values) {
         pc[p].hh = vval(hh.v);
         pc[p].ncut = ncut;
@@ -798,6 +820,21 @@ int64_t work_needed(const gwl_ctx* c, int64_t B);
 int* window_hist(const gwl_ctx* c);
 int* calgrad_counters(const gwl_ctx* c, int64_t B);
 
+// Directions per CTA of the role-form tangent prologue, and how many of its
+// CTAs an SM holds (from the kernel's registers and shared memory).
+constexpr int kRoleTangents = 3;
+static int role_ctas_per_sm() {
+  static const int n = [] {
+    int k = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_prologue_grad_roles<kRoleTangents>, 128, 0) != cudaSuccess) {
+      cudaGetLastError();
+      k = 0;
+    }
+    return k;
+  }();
+  return n;
+}
+
 template <int NDET, bool MIXED, bool CAL>
 static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* lnl, double* grad, cudaStream_t st) {
   using G = typename std::conditional<MIXED, float, double>::type;
@@ -807,16 +844,17 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   if (e != cudaSuccess) return e;
   {
     ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
-    // the role form while its CTAs stay within about five per SM (measured on the
-    // 8 s workload, 11-D: prologue 12.9 / 14.5 / 18.5 us against 19.7 / 18.7 /
-    // 20.0 us at B = 256 / 1024 / 2048; beyond, its four threads per row and
-    // direction outgrow a wave and one thread per row and direction is faster)
-    const int64_t role_ctas = (B + 31) / 32 * c->opt.n_dim;
-    if (MIXED && role_ctas <= 5 * (int64_t)c->num_sms) {
-      const dim3 grid((unsigned)((B + 31) / 32), (unsigned)c->opt.n_dim);
-      k_prologue_grad_roles<<<grid, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pc,
-                                                  reinterpret_cast<PropGrad<float>*>(c->d_pgrad), c->d_work,
-                                                  window_hist(c), CH);
+    // the role form, three directions per CTA, while its CTAs fit one wave
+    // (measured on the 8 s workload, 11-D, gradient call: 27.5 / 35.2 / 37.3 /
+    // 48.6 us at B = 256 / 1024 / 2048 / 4096 against 29.3 / 35.0 / 38.5 us
+    // with one direction per CTA and 52.2 us with one thread per row and
+    // direction at B = 4096); beyond one wave, the one-thread form
+    const int64_t role_ctas = (B + 31) / 32 * ((c->opt.n_dim + kRoleTangents - 1) / kRoleTangents);
+    if (MIXED && role_ctas <= (int64_t)role_ctas_per_sm() * c->num_sms) {
+      const dim3 grid((unsigned)((B + 31) / 32), (unsigned)((c->opt.n_dim + kRoleTangents - 1) / kRoleTangents));
+      k_prologue_grad_roles<kRoleTangents><<<grid, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pc,
+                                                                 reinterpret_cast<PropGrad<float>*>(c->d_pgrad),
+                                                                 c->d_work, window_hist(c), CH);
     } else {
       constexpr int kTanGroup = tan_group<MIXED>();
       const int ngrp = (c->opt.n_dim + kTanGroup - 1) / kTanGroup;
