@@ -63,6 +63,23 @@ def test_grad_matches_oracle_dual_numbers(precision):
     assert within_bars(err, precision), f"99th pct {np.percentile(err.max(axis=1), 99):.3e}, max {err.max():.3e}"
 
 
+@pytest.mark.parametrize("B", [256, 8192])
+def test_mixed_grad_both_prologue_forms(B):
+    """The mixed tangent prologue runs in the role form (three directions per CTA) while its CTAs fit one wave
+    and one thread per row and direction beyond (11-D: above about 7,000 rows on 152 SMs); both forms against
+    the oracle's dual numbers on sampled rows, same bars."""
+    ev = event("c5")
+    th = I.proposals(ev, B, 15)
+    lnl, g = run(ev, th, 1)
+    idx = np.random.default_rng(3).choice(B, min(B, 128), replace=False)
+    ref_l, ref_g = oracle.grad(ev, th[idx])
+    assert np.all(np.abs(lnl[idx] - ref_l) <= tol(1, ref_l))
+    width = ev.sampling.hi - ev.sampling.lo
+    s = np.maximum(np.abs(ref_g) * width, 1.0)
+    err = np.abs(g[idx] - ref_g) * width / s
+    assert within_bars(err, 1), f"99th pct {np.percentile(err.max(axis=1), 99):.3e}, max {err.max():.3e}"
+
+
 @pytest.mark.parametrize("precision", [1])
 def test_c1_grad_4d(precision):
     ev = event("c1")
