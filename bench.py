@@ -69,13 +69,14 @@ HBM_BYTES_PER_EVAL = 96
 # The gradient bin loop per pair: the exact float-float phase per bin (the
 # 8-term sum, pairwise: 8 TwoProducts, 7 TwoSums and the low-part terms, 114;
 # per detector the delay term, TwoSum and reduction, 3 x 20) -> 174; per
-# detector the sine and cosine of the reduced phase by their series on the
-# FP32 pipe (reduction 5, the two polynomials 18, scaling 2: 25) -> 75; per
+# detector the sine and cosine of the reduced phase from a table of the
+# 64th-cycle points and short series on the FP32 pipe (reduction 5, scaling
+# 1, the two series 8, the rotation 6: 20) -> 60; per
 # detector the data-weighted phasor (6), Z_d (2), the imaginary part of K_d
 # times it (3), its f-weighted sum (2) and the sum over detectors (1) ->
-# 3 x 14 = 42; the eight basis-weighted sums of that total (16): 307 flop;
+# 3 x 14 = 42; the eight basis-weighted sums of that total (16): 292 flop;
 # no MUFU.
-PIPES_GRAD = {"fp32_flop": 307, "mufu": 0}
+PIPES_GRAD = {"fp32_flop": 292, "mufu": 0}
 # Calibration model (Section 2.2), per bin on top of the plain likelihood: the
 # four spline weights (9 flop, shared by the detectors); per detector two
 # spline values (2 x 7), the phase shift (1), the amplitude factor (3) and the

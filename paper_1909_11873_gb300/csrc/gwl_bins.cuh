@@ -1,6 +1,7 @@
 // gwl_bins.cuh -- per-bin arithmetic shared by the likelihood and gradient bin loops.
 #pragma once
 
+#include <cmath>
 #include <type_traits>
 
 #include "gwl_internal.h"
@@ -49,31 +50,42 @@ __device__ __forceinline__ float nearest_int(float x) {
   return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
 }
 
-// sin(pi x) and cos(pi x) for |x| <= ~1.5 half-turns: x = q/2 + r with q the
-// nearest integer to 2x (by the 1.5 * 2^23 shift, whose low mantissa bits are
-// q mod 4) and |r| <= 1/4 exact; sin(pi r) and cos(pi r) from their Taylor
-// series through r^9 and r^10 (truncation below 3e-9), Horner's rule on r^2;
-// then the rotation by q quarter turns.
-__device__ __forceinline__ void sincospi_small(float x, float* s, float* c) {
-  const float t = __fadd_rn(2.0f * x, 12582912.0f);
-  const int qi = __float_as_int(t) & 3;
-  const float r = __fmaf_rn(__fsub_rn(t, 12582912.0f), -0.5f, x);
-  const float r2 = r * r;
-  // (-1)^k pi^(2k+1) / (2k+1)! and (-1)^k pi^(2k) / (2k)!
-  float ps = 0.08214588661112819f;
-  ps = __fmaf_rn(ps, r2, -0.5992645293207919f);
-  ps = __fmaf_rn(ps, r2, 2.550164039877345f);
-  ps = __fmaf_rn(ps, r2, -5.167712780049969f);
-  ps = __fmaf_rn(ps, r2, 3.141592653589793f);
-  float pc = -0.02580689139001405f;
-  pc = __fmaf_rn(pc, r2, 0.23533063035889312f);
-  pc = __fmaf_rn(pc, r2, -1.3352627688545893f);
-  pc = __fmaf_rn(pc, r2, 4.058712126416768f);
-  pc = __fmaf_rn(pc, r2, -4.934802200544679f);
-  const float sp = ps * r, cp = __fmaf_rn(pc, r2, 1.0f);
-  float ss = (qi & 1) ? cp : sp, cc = (qi & 1) ? sp : cp;
-  *s = (qi & 2) ? -ss : ss;
-  *c = ((qi + 1) & 2) ? -cc : cc;
+// Sine and cosine of the 64th-cycle points 2 pi k / 64, k = 0 .. 63, for the
+// gradient bin loop's sine and cosine (kernel argument, copied to shared
+// memory).  The first quadrant comes from the FP64 library functions, the
+// others by symmetry, so that the quarter-turn points are exactly 0 and +-1.
+struct SinCosTab {
+  float2 v[64];
+};
+inline SinCosTab make_sincos_tab() {
+  SinCosTab t;
+  for (int k = 0; k < 64; ++k) {
+    const int q = k / 16, m = k % 16;  // k = 16 q + m: angle q pi/2 + m pi/32
+    const double sm = m ? std::sin(kPi * m / 32.0) : 0.0, cm = m ? std::cos(kPi * m / 32.0) : 1.0;
+    const double s = q == 0 ? sm : q == 1 ? cm : q == 2 ? -sm : -cm;
+    const double c = q == 0 ? cm : q == 1 ? -sm : q == 2 ? -cm : sm;
+    t.v[k] = make_float2((float)s, (float)c);
+  }
+  return t;
+}
+
+// sin and cos of 2 pi fr (|fr| below about 0.6 cycles) from a table of the
+// 64th-cycle points: k the nearest integer to 64 fr (by the 1.5 * 2^23 shift,
+// whose low mantissa bits are k mod 64), rho = fr - k/64 (|rho| <= 1/128,
+// exact), (sin, cos)(2 pi k/64) = tab[k mod 64], and sin and cos of
+// u = 2 pi rho from their Taylor series through u^3 and u^4 (truncation below
+// 3e-9 for |u| <= pi/64), then the rotation by the table's angle.
+__device__ __forceinline__ void sincos_cycles_tab(float fr, const float2* __restrict__ tab, float* s, float* c) {
+  const float t = __fadd_rn(64.0f * fr, 12582912.0f);
+  const int k = __float_as_int(t) & 63;
+  const float rho = __fmaf_rn(__fsub_rn(t, 12582912.0f), -0.015625f, fr);
+  const float u = 6.283185307179586f * rho;
+  const float u2 = u * u;
+  const float sr = __fmaf_rn(u * u2, -0.16666666666666666f, u);
+  const float cr = __fmaf_rn(u2, __fmaf_rn(u2, 0.041666666666666664f, -0.5f), 1.0f);
+  const float2 e = tab[k];
+  *s = __fmaf_rn(e.x, cr, e.y * sr);
+  *c = __fmaf_rn(e.y, cr, -(e.x * sr));
 }
 
 // Phase of one bin in float-float arithmetic, reduced modulo one cycle, and its
@@ -89,12 +101,13 @@ __device__ __forceinline__ void sincospi_small(float x, float* s, float* c) {
 //     p - rint p are exact): two roundings of at most 2^-24 cycles each, and
 //     seven fewer FP32 operations per detector.
 // With shift (may be null) the phase of detector d is r_d - shift[d] (the
-// calibration model's phase correction, in cycles).
+// calibration model's phase correction, in cycles).  EXACT_SUM takes the
+// sine/cosine table sct (make_sincos_tab's values, in shared memory).
 template <int NDET, bool EXACT_SUM>
 __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], const float (&ch)[kNBasis],
                                             const float (&cl)[kNBasis], const float (&th)[NDET],
                                             const float (&tl)[NDET], float (&sn)[NDET], float (&cs)[NDET],
-                                            const float* shift = nullptr) {
+                                            const float* shift = nullptr, const float2* __restrict__ sct = nullptr) {
   float s, lo;
   if constexpr (EXACT_SUM) {
     // the eight products' high parts summed pairwise (three levels of TwoSum
@@ -149,9 +162,9 @@ __device__ __forceinline__ void phase_mixed(const float (&v)[RowM<NDET>::n], con
       if (shift) fr = fr - shift[d];
       // the gradient's basis-weighted sums amplify the absolute error of the
       // hardware sine and cosine (~4e-7, a smooth function of the argument, so
-      // it adds up across bins): the series on the reduced argument instead
-      // (|2 fr| <= ~1.1)
-      sincospi_small(2.0f * fr, &sn[d], &cs[d]);
+      // it adds up across bins): the table of 64th-cycle points and short
+      // series instead (sct, in shared memory)
+      sincos_cycles_tab(fr, sct, &sn[d], &cs[d]);
     }
   } else {
     const float sf = __fadd_rn(__fsub_rn(s, nearest_int(s)), lo);

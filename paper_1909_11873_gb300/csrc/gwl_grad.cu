@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(128) k_prologue_grad_roles(SegInfo s, const do
 
 // ---------------------------------------------------------------- bin loop
 struct GradArgs {
+  SinCosTab sct;  // the mixed phase's sine/cosine table
   const void* tab;
   int row_elems;
   int64_t M;
@@ -467,7 +468,7 @@ __device__ __forceinline__ G grad_dir(const PropCommon* c, const PropGrad<G>& g,
 // and X_d collects the <h|h> correction sum_j dA (2 + dA) dH_d,j.
 template <int NDET, bool MIXED, bool CAL, typename Node>
 __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restrict__ smv, const Node* nodes,
-                                          int64_t p, int j0, int jend, int lane,
+                                          const float2* __restrict__ sct, int64_t p, int j0, int jend, int lane,
                                           typename std::conditional<MIXED, float, double>::type (&S)[GradSums<NDET>::n],
                                           typename std::conditional<MIXED, float, double>::type (&X)[NDET]) {
   using Acc = typename std::conditional<MIXED, float, double>::type;
@@ -505,9 +506,9 @@ __device__ __forceinline__ void grad_sums(const GradArgs& a, const void* __restr
       CalBin<NDET, float> cb;
       if constexpr (CAL) {
         cal_eval<NDET>(sm + a.cal_smem + (int64_t)(j - j0) * a.cal_row, reinterpret_cast<const float4*>(nodes), cb);
-        phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs, cb.P);
+        phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs, cb.P, sct);
       } else {
-        phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs);
+        phase_mixed<NDET, true>(v, ch, cl, th, tl, sn, cs, nullptr, sct);
       }
       float Y = 0.0f;
 #pragma unroll
@@ -626,12 +627,16 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
   Elem* sm = reinterpret_cast<Elem*>(smem_raw);
   const int lane = threadIdx.x & 31;
   Node* nodes = s_nodes + (CAL ? (threadIdx.x >> 5) * NDET * kMaxCalNodes : 0);
+  // the mixed phase's sine/cosine table
+  __shared__ float2 s_sct[64];
+  if (MIXED && threadIdx.x < 64) s_sct[threadIdx.x] = a.sct.v[threadIdx.x];
   // window 0 of the table is copied while the prologue finishes (see k_window)
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
     grad_stage<MIXED, CAL>(a, sm, 0, a.CH < a.M ? (int)a.CH : (int)a.M, &bar);
   }
+  __syncthreads();
   bool w0_pending = true;
   uint32_t parity = 0;
   cudaGridDependencySynchronize();
@@ -667,7 +672,7 @@ __global__ void __launch_bounds__(256, 2) k_window_grad(GradArgs a) {
       drain_window(ctr, a.B, claim_size(a.B, n_w), a.pc, j0, lane, [&](int64_t p, int ncut) {
         Elem S[GradSums<NDET>::n], X[NDET];
         if constexpr (CAL) cal_nodes_fill<NDET, MIXED>(a.theta + p * a.gstride + a.cal_par, a.nn, a.calQ, lane, nodes);
-        grad_sums<NDET, MIXED, CAL>(a, sm, nodes, p, j0, ncut < j1 ? ncut : j1, lane, S, X);
+        grad_sums<NDET, MIXED, CAL>(a, sm, nodes, s_sct, p, j0, ncut < j1 ? ncut : j1, lane, S, X);
         if (ncut <= a.CH) {  // the proposal's only window (every lane holds the sums): finish it here
           const PropCommon* c = a.pc + p;
           auto Z = [&](int d, int k) { return (double)S[2 * d + k]; };
@@ -870,7 +875,9 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
   char* gp = reinterpret_cast<char*>(c->d_gpartials);
   void* xpart = gp + ((grad_sums_bytes(c, B) + 255) & ~255ll);
   void* cpart = reinterpret_cast<char*>(xpart) + ((grad_x_bytes(c, B) + 255) & ~255ll);
+  static const SinCosTab sct = make_sincos_tab();
   GradArgs a;
+  a.sct = sct;
   a.tab = MIXED ? (const void*)c->d_tab_mixed : (const void*)c->d_tab_f64;
   a.row_elems = MIXED ? c->row_floats : c->row_doubles;
   a.M = c->M;

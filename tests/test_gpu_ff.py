@@ -53,10 +53,10 @@ def test_ff_sin_cos(g, fn):
 
 @pytest.mark.parametrize("fn", ["sinpi", "cospi"])
 def test_f32_sincospi(g, fn):
-    """The FP32 sin(pi x), cos(pi x) of the mixed gradient's bin loop (Taylor series on the argument reduced
-    to |r| <= 1/4, then the quarter-turn rotation) over |x| <= 1.5, with the quarter-turn boundaries and
-    their neighbours: absolute error against FP64 at the FP32 argument below 2^-22 (the hardware sine's is
-    ~4e-7), and exact values at the quarter turns' zeros and ones."""
+    """The FP32 sin(pi x), cos(pi x) of the mixed gradient's bin loop (a table of the 64th-cycle points and
+    short series on the remainder, |u| <= pi/64, then the rotation) over |x| <= 1.5, with the quarter-turn
+    boundaries and their neighbours: absolute error against FP64 at the FP32 argument below 2^-22 (the
+    hardware sine's is ~4e-7), and exact values at the quarter turns' zeros and ones."""
     k = np.arange(-6, 7) / 4.0
     x = np.concatenate([np.linspace(-1.5, 1.5, 60001), k, np.nextafter(k.astype(np.float32), np.float32(2)),
                         np.nextafter(k.astype(np.float32), np.float32(-2)),
