@@ -732,7 +732,19 @@ def run_gwl(args):
 
 
 def compact_legs(legres, checks):
-    """The extra measurements in a short form (four significant digits; key legend in the design doc)."""
+    """The extra measurements in a short form (four significant digits):
+      fp64_c2, fp64ph_c2  [evals/s, times slower than the mixed path]
+      grad_c5, cal_c2     [evals/s, bin-loop ms, roofline fraction of the bound pipe]
+      calgrad_c2          [grad evals/s, ms per call, gradient bin-loop ms, calibration-moment ms]
+      c1, c3              [mixed evals/s, FP64 evals/s]
+      ns_c1               [wall s, lnZ, its error, consumed per round / K ln(1 + B/K)]
+      eq5                 [[B, consumed / K ln(1 + B/K), wall s], ...]
+      c5                  {dims: {walk: [ESS/s, lnZ, lnZ spread over seeds]}}
+      c4                  [batched / per-event lnL speed-up, NS s in one graph, NS s per event, rounds,
+                           largest lnZ difference between the two in sigma]
+      err_c1..c3          [FP64 |dlnL|, mixed |dlnL|, FP64-phase mixed |dlnL|, rows] against the oracle
+      ns_c1_orc           [the oracle's NS wall s, lnZ]
+      c4_lnZ              [[duration s, device lnZ, oracle lnZ, sigma], ...]"""
     L = {}
     g = legres.get
     if g("fp64_c2"):
