@@ -94,6 +94,23 @@ def test_c1_grad_4d(precision):
     assert within_bars(err, precision), f"99th pct {np.percentile(err.max(axis=1), 99):.3e}, max {err.max():.3e}"
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c3_grad_long_segment_sampled(precision):
+    """3 detectors, 128 s BNS, 259,585 bins: every proposal spans hundreds of gradient windows, whose
+    partial sums the combination kernel adds in window order; 16 sampled rows against the oracle."""
+    ev = event("c3")
+    th = I.proposals(ev, 256, 16)
+    lnl, g = run(ev, th, precision)
+    idx = np.random.default_rng(4).choice(256, 16, replace=False)
+    ref_l, ref_g = oracle.grad(ev, th[idx])
+    ref_g = ref_g[:, ev.sampling.param_map]
+    width = ev.sampling.hi - ev.sampling.lo
+    s = np.maximum(np.abs(ref_g) * width, 1.0)
+    err = np.abs(g[idx] - ref_g) * width / s
+    assert np.all(np.abs(lnl[idx] - ref_l) <= tol(precision, ref_l))
+    assert within_bars(err, precision), f"99th pct {np.percentile(err.max(axis=1), 99):.3e}, max {err.max():.3e}"
+
+
 def test_grad_matches_central_differences_of_device_lnl():
     """Central differences (h = 1e-6 relative) of the FP64 device lnL at rows whose ISCO bin does not move."""
     from paper_1909_11873_gb300 import gwl
