@@ -146,6 +146,10 @@ def _ptr(t) -> int:
     if isinstance(t, np.ndarray):
         if not t.flags.c_contiguous:
             raise ValueError("array must be C-contiguous")
+        if t.flags.writeable and t.nbytes:
+            # the buffer's address without building numpy's ctypes helper object (about a
+            # microsecond less per array on the host-buffer entry point)
+            return C.addressof(C.c_char.from_buffer(t))
         return t.ctypes.data
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
