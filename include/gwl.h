@@ -348,6 +348,27 @@ int gwl_multi_loglike(gwl_multi* m, const double* theta_dev, int64_t n_per, doub
 int gwl_multi_ns_run(gwl_multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                      int64_t max_rounds, double scale0, gwl_ns_result* out, void* stream);
 
+/* gwl_multi_ns_run continued from a checkpoint and/or writing one (the
+ * counterpart of ns_run_resumable for a batch of events; no dead points).
+ *   resume      host [gwl_multi_ns_state_doubles(m, K)] or NULL: a state
+ *               written by an earlier call on the same batch with the same K;
+ *               the run continues from it bit for bit (the walks' random
+ *               numbers are keyed by each event's round counter, which the
+ *               state carries)
+ *   checkpoint  host [gwl_multi_ns_state_doubles(m, K)] or NULL: receives
+ *               every event's state after this call's rounds, before the
+ *               final live points are added to the evidence
+ * A resume buffer of another format, event count, K or walk dimension gives
+ * GWL_ERR_ARG.  Synchronises the stream. */
+int gwl_multi_ns_run_resumable(gwl_multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                               int64_t max_rounds, double scale0, gwl_ns_result* out, const double* resume,
+                               double* checkpoint, void* stream);
+
+/* Doubles in a checkpoint of gwl_multi_ns_run_resumable for this batch and
+ * K (5 + n_events (10 + NS statistics + K (D + 1)) with D the batch's walk
+ * dimensions); -1 for a null batch or K < 2. */
+int64_t gwl_multi_ns_state_doubles(const gwl_multi* m, int64_t K);
+
 /* Kernel launches issued by the multi-event context. */
 int64_t gwl_multi_launch_count(const gwl_multi* m);
 

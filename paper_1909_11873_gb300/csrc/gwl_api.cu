@@ -572,7 +572,21 @@ int gwl_multi_loglike(gwl_multi* h, const double* theta_dev, int64_t n_per, doub
 
 int gwl_multi_ns_run(gwl_multi* h, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
                      int64_t max_rounds, double scale0, gwl_ns_result* out, void* stream) {
+  return gwl_multi_ns_run_resumable(h, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, out, nullptr, nullptr,
+                                    stream);
+}
+
+int64_t gwl_multi_ns_state_doubles(const gwl_multi* h, int64_t K) {
+  if (!h || K < 2) return -1;
+  return gwl::multi_state_doubles(h->E, K, gwl::multi_dim(h->m));
+}
+
+int gwl_multi_ns_run_resumable(gwl_multi* h, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
+                               int64_t max_rounds, double scale0, gwl_ns_result* out, const double* resume,
+                               double* checkpoint, void* stream) {
   if (!h || !out) return fail(GWL_ERR_ARG, "null argument");
+  if (resume && K >= 2 && gwl::multi_state_check(resume, h->E, K, gwl::multi_dim(h->m)) != 0)
+    return fail(GWL_ERR_ARG, "resume buffer does not match this batch, K and walk dimensions");
   if (K < 2 || n_chains < 1 || walk_len < 1 || max_rounds < 0) return fail(GWL_ERR_ARG, "bad sizes");
   if (K > 4096 || n_chains > 4096) return fail(GWL_ERR_ARG, "gwl_multi_ns_run supports K, n_chains <= 4096");
   if (!(scale0 > 0.0)) return fail(GWL_ERR_ARG, "scale0 must be positive");
@@ -580,7 +594,7 @@ int gwl_multi_ns_run(gwl_multi* h, int64_t K, int64_t n_chains, int walk_len, ui
     return fail(GWL_ERR_ARG, "the batch's contexts no longer share their number of calibration nodes");
   std::vector<double> res((size_t)11 * h->E);
   const int r = gwl::multi_ns_run(h->m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res.data(),
-                                  (cudaStream_t)stream);
+                                  (cudaStream_t)stream, resume, checkpoint);
   if (r != 0) return fail(GWL_ERR_CUDA, "gwl_multi_ns_run: %s", cudaGetErrorString(cudaGetLastError()));
   for (int e = 0; e < h->E; ++e) {
     const double* x = res.data() + 11 * e;

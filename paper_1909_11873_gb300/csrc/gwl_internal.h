@@ -174,7 +174,11 @@ cudaError_t multi_loglike(Multi* m, const double* theta, int64_t n_per, double* 
 int64_t multi_launches(const Multi* m);
 bool multi_consistent(const Multi* m);
 int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
-                 int64_t max_rounds, double scale0, double* res /* [E][11] */, cudaStream_t caller);
+                 int64_t max_rounds, double scale0, double* res /* [E][11] */, cudaStream_t caller,
+                 const double* resume = nullptr, double* checkpoint = nullptr);
+int64_t multi_state_doubles(int E, int64_t K, int64_t D);
+int multi_state_check(const double* in, int E, int64_t K, int64_t D);
+int multi_dim(const Multi* m);
 
 // gwl_loglike_static's fixed array: look its device address up on `dev` (set-up, from gwl_create)
 cudaError_t static_scratch_setup(int dev);

@@ -1190,8 +1190,27 @@ void multi_count(Multi* m, int64_t n);
 // Nested sampling of E events at once: every round is one sequence of
 // launches covering all events (per-event kernels run one CTA per event; the
 // walk steps evaluate all events' chains in one multi-event batch).
+// A multi-event run's state between rounds: [0] kMultiStateMagic, [1] format
+// version, [2] events E, [3] K, [4] D, then each event's state in the
+// single-event format without dead points (state_doubles(K, D, 0) doubles).
+constexpr double kMultiStateMagic = 5.4218e15;
+constexpr int kMultiStateHeader = 5;
+
+int64_t multi_state_doubles(int E, int64_t K, int64_t D) { return kMultiStateHeader + E * state_doubles(K, D, 0); }
+
+int multi_state_check(const double* in, int E, int64_t K, int64_t D) {
+  if (in[0] != kMultiStateMagic || in[1] != kStateVersion) return 1;
+  if (in[2] != (double)E || in[3] != (double)K || in[4] != (double)D) return 2;
+  for (int i = 0; i < E; ++i) {
+    const double* b = in + kMultiStateHeader + i * state_doubles(K, D, 0);
+    if (state_check(b, K, D) != 0 || b[4] != 0.0) return 3;
+  }
+  return 0;
+}
+
 static int multi_ns_run_on(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
-                           int64_t max_rounds, double scale0, double* res, cudaStream_t st) {
+                           int64_t max_rounds, double scale0, double* res, cudaStream_t st, const double* resume,
+                           double* checkpoint) {
   const int E = multi_events(m);
   const int D = multi_dim(m);
   const int64_t rbuf = n_chains > K ? n_chains : K;
@@ -1269,14 +1288,19 @@ static int multi_ns_run_on(Multi* m, int64_t K, int64_t n_chains, int walk_len, 
       break;
     if ((e = cudaMemcpyAsync(ws, w0.data(), sizeof(WalkScalars) * E, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       break;
-    // initial live points of every event, one batched likelihood call
-    for (int i = 0; i < E && e == cudaSuccess; ++i) {
-      k_ns_init<<<(unsigned)((K + 127) / 128), 128, 0, st>>>(hpr[i], event_key(seed, i), K, hns[i].lu,
-                                                             pth + (int64_t)i * K * D);
-      e = cudaGetLastError();
+    const int64_t per = state_doubles(K, D, 0);
+    if (resume) {  // every event's live set, accumulators and walk state from the checkpoint
+      for (int i = 0; i < E && e == cudaSuccess; ++i) e = state_restore(hns[i], resume + kMultiStateHeader + i * per, st);
+      if (e != cudaSuccess) break;
+    } else {  // initial live points of every event, one batched likelihood call
+      for (int i = 0; i < E && e == cudaSuccess; ++i) {
+        k_ns_init<<<(unsigned)((K + 127) / 128), 128, 0, st>>>(hpr[i], event_key(seed, i), K, hns[i].lu,
+                                                               pth + (int64_t)i * K * D);
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) break;
+      if ((e = multi_loglike(m, pth, K, ll, st)) != cudaSuccess) break;
     }
-    if (e != cudaSuccess) break;
-    if ((e = multi_loglike(m, pth, K, ll, st)) != cudaSuccess) break;
     // one round, captured
     const size_t csm = consume_smem_bytes(K, n_chains);
     if (csm > 48 * 1024) {
@@ -1327,6 +1351,15 @@ static int multi_ns_run_on(Multi* m, int64_t K, int64_t n_chains, int walk_len, 
     cudaGraphExecDestroy(gexec);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) break;
+    if (checkpoint) {  // the state after this call's rounds, before the live points join the evidence
+      checkpoint[0] = kMultiStateMagic;
+      checkpoint[1] = kStateVersion;
+      checkpoint[2] = (double)E;
+      checkpoint[3] = (double)K;
+      checkpoint[4] = (double)D;
+      for (int i = 0; i < E && e == cudaSuccess; ++i) e = state_save(hns[i], 0, checkpoint + kMultiStateHeader + i * per, st);
+      if (e != cudaSuccess) break;
+    }
     k_mns_final<<<E, 256, 0, st>>>(d_ns);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(hst.data(), stats, sizeof(double) * hst.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -1358,11 +1391,13 @@ static int multi_ns_run_on(Multi* m, int64_t K, int64_t n_chains, int walk_len, 
 }
 
 int multi_ns_run(Multi* m, int64_t K, int64_t n_chains, int walk_len, uint64_t seed, double dlogz,
-                 int64_t max_rounds, double scale0, double* res, cudaStream_t caller) {
+                 int64_t max_rounds, double scale0, double* res, cudaStream_t caller, const double* resume,
+                 double* checkpoint) {
   if (cudaStreamSynchronize(caller) != cudaSuccess) return -2;
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -2;
-  const int rc = multi_ns_run_on(m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res, st);
+  const int rc = multi_ns_run_on(m, K, n_chains, walk_len, seed, dlogz, max_rounds, scale0, res, st, resume,
+                                 checkpoint);
   cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   return rc;

@@ -27,7 +27,8 @@ MAX_DET = 4
 EXPORTS = ("gwl_create", "gwl_loglike", "gwl_loglike_host", "gwl_loglike_static", "ns_run", "gwl_grad", "gwl_waveform", "ns_replace",
            "gwl_sync", "gwl_set_tuning", "gwl_profile", "gwl_profile_read", "gwl_device_bytes",
            "gwl_launch_count", "gwl_destroy", "gwl_last_error", "gwl_multi_create", "gwl_multi_loglike",
-           "gwl_multi_ns_run", "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
+           "gwl_multi_ns_run", "gwl_multi_ns_run_resumable", "gwl_multi_ns_state_doubles",
+           "gwl_multi_launch_count", "gwl_multi_destroy", "gwl_set_walk",
            "gwl_set_galilean", "ns_run_resumable", "ns_state_doubles", "gwl_get_tuning", "gwl_autotune", "gwl_set_calibration", "gwl_get_calibration", "gwl_ff_eval",
            "gwl_test_wait_timeout", "gwl_test_philox",
            "gwl_test_ffdelta_blocks")
@@ -126,6 +127,9 @@ def lib() -> C.CDLL:
         L.gwl_multi_create.argtypes = [P, i32, C.POINTER(P)]
         L.gwl_multi_loglike.argtypes = [P, P, i64, P, P]
         L.gwl_multi_ns_run.argtypes = [P, i64, i64, i32, u64, d, i64, d, P, P]
+        L.gwl_multi_ns_run_resumable.argtypes = [P, i64, i64, i32, u64, d, i64, d, P, P, P, P]
+        L.gwl_multi_ns_state_doubles.argtypes = [P, i64]
+        L.gwl_multi_ns_state_doubles.restype = i64
         L.gwl_multi_launch_count.argtypes = [P]
         L.gwl_multi_launch_count.restype = i64
         L.gwl_multi_destroy.argtypes = [P]
@@ -484,12 +488,22 @@ class MultiContext:
         n_per = theta.shape[0] // self.E
         _check(lib().gwl_multi_loglike(self._h, _ptr(theta), n_per, _ptr(lnl), _stream(stream)), "gwl_multi_loglike")
 
-    def gwl_multi_ns_run(self, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0, stream=None):
+    def gwl_multi_ns_run(self, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0, stream=None,
+                         resume=None, checkpoint=False):
+        """ns_run for every event in one graph per round; a list of per-event results.  resume: a checkpoint
+        (float64 array) to continue from; checkpoint=True returns (results, state) with the state after this
+        call's rounds (gwl_multi_ns_run_resumable)."""
         res = (GwlNsResult * self.E)()
-        _check(lib().gwl_multi_ns_run(self._h, int(K), int(n_chains), int(walk_len), int(seed), float(dlogz),
-                                      int(max_rounds), float(scale0), C.cast(res, C.c_void_p), _stream(stream)),
-               "gwl_multi_ns_run")
-        return [{k: getattr(r, k) for k, _ in GwlNsResult._fields_} for r in res]
+        state = np.zeros(lib().gwl_multi_ns_state_doubles(self._h, int(K))) if checkpoint else None
+        if resume is not None:
+            resume = np.ascontiguousarray(resume, dtype=np.float64)
+        _check(lib().gwl_multi_ns_run_resumable(self._h, int(K), int(n_chains), int(walk_len), int(seed),
+                                                float(dlogz), int(max_rounds), float(scale0),
+                                                C.cast(res, C.c_void_p), _ptr(resume), _ptr(state),
+                                                _stream(stream)),
+               "gwl_multi_ns_run_resumable")
+        out = [{k: getattr(r, k) for k, _ in GwlNsResult._fields_} for r in res]
+        return (out, state) if checkpoint else out
 
     def launch_count(self) -> int:
         return lib().gwl_multi_launch_count(self._h)

@@ -97,3 +97,29 @@ def test_resume_buffer_checks():
     bad[0] = 1.0
     with pytest.raises(gwl.GwlError, match="format"):
         ctx.ns_run(K=64, max_rounds=2, resume=bad, **kw)
+
+
+def test_multi_split_run_equals_uninterrupted():
+    """gwl_multi_ns_run_resumable: three events run in three calls through checkpoints give, event by event,
+    the uninterrupted run's results exactly; the buffer is checked against the batch and K."""
+    from paper_1909_11873_gb300 import gwl
+    from test_gpu_multi import four_d, small_events
+    evs = [four_d(ev) for ev in small_events()[:3]]
+    mc = gwl.MultiContext([gwl.Context.from_event(ev, 1) for ev in evs])
+    kw = dict(K=150, n_chains=150, walk_len=16, seed=3, dlogz=0.1)
+    whole = mc.gwl_multi_ns_run(max_rounds=100000, **kw)
+    assert all(r["rounds"] > 8 for r in whole)
+    state = None
+    for rounds in (5, 6, 100000):
+        out, state = mc.gwl_multi_ns_run(max_rounds=rounds, resume=state, checkpoint=True, **kw)
+    for a, b in zip(whole, out):
+        for k in KEYS:
+            assert a[k] == b[k], (k, a[k], b[k])
+    assert state.size == gwl.lib().gwl_multi_ns_state_doubles(mc._h, 150)
+    with pytest.raises(gwl.GwlError, match="does not match"):
+        mc.gwl_multi_ns_run(K=200, n_chains=150, walk_len=16, seed=3, max_rounds=2,
+                            resume=np.concatenate([state, np.zeros(200000)]))
+    bad = state.copy()
+    bad[0] = 1.0
+    with pytest.raises(gwl.GwlError, match="does not match"):
+        mc.gwl_multi_ns_run(max_rounds=2, resume=bad, **kw)
