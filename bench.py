@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--legs", default=",".join(LEGS), help="extra measurements to run (comma list; '' for none)")
-    ap.add_argument("--profile-only", default="", choices=["", "lnl", "grad", "cal", "calgrad", "fp64ph"],
+    ap.add_argument("--profile-only", default="", choices=["", "lnl", "grad", "cal", "calgrad", "fp64ph", "fp64"],
                     help="run one workload --warmup + --steps times without timing and exit (for profiler captures): "
                          "lnl = the headline likelihood, grad = the 4096-proposal gradient, cal = the calibrated "
                          "likelihood, fp64ph = the FP64-phase mixed arm")
@@ -914,7 +914,7 @@ def run_profile_only(args):
         build.build()
     torch.cuda.set_device(0)
     ev = device_event(args.profile_config)
-    prec = {"fp64ph": gwl.GWL_MIXED_F64PHASE}.get(args.profile_only, gwl.GWL_MIXED)
+    prec = {"fp64ph": gwl.GWL_MIXED_F64PHASE, "fp64": gwl.GWL_FP64}.get(args.profile_only, gwl.GWL_MIXED)
     ctx = gwl.Context.from_event(ev, prec)
     grad = args.profile_only in ("grad", "calgrad")
     B = 4096 if grad else (2048 if args.profile_config == "c3" else BATCH)
