@@ -133,6 +133,10 @@ cudaError_t launch_cal_tables(gwl_ctx* c, const double* d_xnode, cudaStream_t st
 
 // a2-a6: batched log-likelihood
 cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st);
+// the same after a kernel that cleared the work counters (work_needed(c, B)
+// ints of d_work) and wrote theta: no clearing kernel
+cudaError_t launch_loglike_cleared(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st);
+int64_t work_needed(const gwl_ctx* c, int64_t B);
 // the lane-per-proposal bin loop (gwl_lanes.cu): chunk size (0: not used), scratch sizes, launch
 int lanes_seg(const gwl_ctx* c, int64_t B);
 int64_t lanes_list_ints(const gwl_ctx* c, int64_t B);

@@ -945,19 +945,31 @@ static cudaError_t launch_clear_work(gwl_ctx* c, int* work, int64_t n, cudaStrea
 // Prologue of rows [0, B) of theta into the coefficient arrays at row offset
 // `off`, with `work` the counter region (cleared just before, by a memset or
 // k_clear_work; launched as a programmatic dependent of the latter).
+// pdl: a programmatic dependent launch of the clearing kernel before it;
+// otherwise an ordinary launch (after a kernel that wrote theta).
 static cudaError_t launch_prologue(gwl_ctx* c, const double* theta, int64_t B, int64_t off, int precision,
-                                   double* lnl, int* work, cudaStream_t st, Buckets bk = Buckets{nullptr, nullptr, 32}) {
+                                   double* lnl, int* work, cudaStream_t st, Buckets bk = Buckets{nullptr, nullptr, 32},
+                                   bool pdl = true) {
   ProfScope ps(c, GWL_KERNEL_PROLOGUE, st);
   const unsigned nb = (unsigned)((B + 31) / 32);
   int* hist = work + 1 + nw_max(c);
   const int CH = window_of(c, precision);
   cudaError_t e;
-  if (precision == GWL_MIXED)
+  if (!pdl) {
+    if (precision == GWL_MIXED)
+      k_prologue<true><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm + off, c->d_pf + off, c->d_pc + off, work, hist,
+                                           CH, lnl, bk);
+    else
+      k_prologue<false><<<nb, 128, 0, st>>>(c->seg, theta, B, c->d_pm + off, c->d_pf + off, c->d_pc + off, work,
+                                            hist, CH, lnl, bk);
+    e = cudaGetLastError();
+  } else if (precision == GWL_MIXED) {
     e = launch_pdl(k_prologue<true>, dim3(nb), dim3(128), 0, st, c->seg, theta, B, c->d_pm + off, c->d_pf + off,
                    c->d_pc + off, work, hist, CH, lnl, bk);
-  else
+  } else {
     e = launch_pdl(k_prologue<false>, dim3(nb), dim3(128), 0, st, c->seg, theta, B, c->d_pm + off, c->d_pf + off,
                    c->d_pc + off, work, hist, CH, lnl, bk);
+  }
   c->launches++;
   return e;
 }
@@ -1026,15 +1038,20 @@ static cudaError_t launch_bins(gwl_ctx* c, const double* theta, int64_t B, int64
 // prologue drains and wait for its results).
 // With the lane kernel the prologue also files every proposal in the bucket
 // of its last chunk.
+// cleared: the work counters were cleared by the kernel just before (which
+// also wrote theta), so no clearing kernel runs and the prologue is an
+// ordinary launch after it.
 template <int NDET>
-static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
+static cudaError_t run_pipeline(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st,
+                                bool cleared = false) {
   const int seg = lanes_seg(c, B);
   int* pdone = c->d_work + 1 + 2 * nw_max(c);
   int* bcount = pdone + B;
   const Buckets bk = seg ? Buckets{bcount, c->d_blist, seg} : Buckets{nullptr, nullptr, 32};
-  cudaError_t e = launch_clear_work(c, c->d_work, work_needed(c, B), st, theta,
-                                    B * theta_stride(c) * (int64_t)sizeof(double));
-  if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st, bk);
+  cudaError_t e = cleared ? cudaSuccess
+                          : launch_clear_work(c, c->d_work, work_needed(c, B), st, theta,
+                                              B * theta_stride(c) * (int64_t)sizeof(double));
+  if (e == cudaSuccess) e = launch_prologue(c, theta, B, 0, c->opt.precision, lnl, c->d_work, st, bk, !cleared);
   if (e != cudaSuccess) return e;
   if (seg) return launch_lanes(c, B, lnl, c->d_work, c->d_work + 1 + nw_max(c), pdone, bcount, seg, st);
   return launch_bins<NDET>(c, theta, B, 0, lnl, c->d_work, true, st);
@@ -1046,6 +1063,15 @@ cudaError_t launch_loglike(gwl_ctx* c, const double* theta, int64_t B, double* l
     case 2: return run_pipeline<2>(c, theta, B, lnl, st);
     case 3: return run_pipeline<3>(c, theta, B, lnl, st);
     default: return run_pipeline<4>(c, theta, B, lnl, st);
+  }
+}
+
+cudaError_t launch_loglike_cleared(gwl_ctx* c, const double* theta, int64_t B, double* lnl, cudaStream_t st) {
+  switch (c->n_det) {
+    case 1: return run_pipeline<1>(c, theta, B, lnl, st, true);
+    case 2: return run_pipeline<2>(c, theta, B, lnl, st, true);
+    case 3: return run_pipeline<3>(c, theta, B, lnl, st, true);
+    default: return run_pipeline<4>(c, theta, B, lnl, st, true);
   }
 }
 

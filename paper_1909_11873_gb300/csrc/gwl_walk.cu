@@ -122,11 +122,10 @@ __global__ void k_walk_init(const double* __restrict__ live_u, const double* __r
   if (cstart) cstart[b] = (int32_t)st;
 }
 
-__global__ void k_walk_propose(PriorInfo pr, const WalkScalars* __restrict__ sc, const double* __restrict__ chol,
-                               uint64_t seed, uint32_t step, int64_t n_chains, const double* __restrict__ cu,
-                               double* __restrict__ pu, double* __restrict__ ptheta) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_chains) return;
+__device__ __forceinline__ void walk_propose_row(const PriorInfo& pr, const WalkScalars* __restrict__ sc,
+                                                 const double* __restrict__ chol, uint64_t seed, uint32_t step,
+                                                 int64_t b, const double* __restrict__ cu, double* __restrict__ pu,
+                                                 double* __restrict__ ptheta) {
   const int D = pr.D;
   double z[kMaxWalkDim];
   walk_normals(seed, sc->counter, (uint32_t)b, step, D, z);
@@ -143,17 +142,38 @@ __global__ void k_walk_propose(PriorInfo pr, const WalkScalars* __restrict__ sc,
   for (int i = 0; i < D; ++i) ptheta[b * D + i] = inside ? coord_map(pr, i, pu[b * D + i]) : NAN;
 }
 
-__global__ void k_walk_accept(const WalkScalars* __restrict__ sc, int D, int64_t n_chains,
-                              const double* __restrict__ pu, const double* __restrict__ plnl, double* __restrict__ cu,
-                              double* __restrict__ cl, int32_t* __restrict__ cn) {
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_chains) return;
+__device__ __forceinline__ void walk_accept_row(const WalkScalars* __restrict__ sc, int D, int64_t b,
+                                                const double* __restrict__ pu, const double* __restrict__ plnl,
+                                                double* __restrict__ cu, double* __restrict__ cl,
+                                                int32_t* __restrict__ cn) {
   const double l = plnl[b];
   if (l >= sc->lstar) {  // NaN rows (steps outside the cube) give -inf and fail
     for (int i = 0; i < D; ++i) cu[b * D + i] = pu[b * D + i];
     cl[b] = l;
     cn[b] += 1;
   }
+}
+
+__global__ void k_walk_accept(const WalkScalars* __restrict__ sc, int D, int64_t n_chains,
+                              const double* __restrict__ pu, const double* __restrict__ plnl, double* __restrict__ cu,
+                              double* __restrict__ cl, int32_t* __restrict__ cn) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n_chains) walk_accept_row(sc, D, b, pu, plnl, cu, cl, cn);
+}
+
+// One launch per walk step: the previous step's accept/reject (step > 1),
+// this step's proposals, and the work counters of the likelihood call that
+// follows cleared (that call then launches no clearing kernel of its own).
+__global__ void k_walk_step(PriorInfo pr, const WalkScalars* __restrict__ sc, const double* __restrict__ chol,
+                            uint64_t seed, uint32_t step, int64_t n_chains, const double* __restrict__ plnl,
+                            double* __restrict__ cu, double* __restrict__ cl, int32_t* __restrict__ cn,
+                            double* __restrict__ pu, double* __restrict__ ptheta, int* __restrict__ work,
+                            int64_t nwork) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t0; i < nwork; i += nt) work[i] = 0;
+  if (t0 >= n_chains) return;
+  if (step > 1) walk_accept_row(sc, pr.D, t0, pu, plnl, cu, cl, cn);
+  walk_propose_row(pr, sc, chol, seed, step, t0, cu, pu, ptheta);
 }
 
 // ---------------------------------------------------------------- Galilean walk
@@ -881,19 +901,21 @@ cudaError_t launch_walk(gwl_ctx* c, const double* live_u, const double* live_lnl
     c->launches++;
   }
   cudaError_t e = cudaGetLastError();
+  const int64_t nwork = work_needed(c, n_chains);
   for (int s = 1; s <= walk_len && e == cudaSuccess; ++s) {
     {
       ProfScope ps(c, GWL_KERNEL_WALK, st);
-      k_walk_propose<<<nb, 128, 0, st>>>(pr, sc, chol, seed, (uint32_t)s, n_chains, out_u, pu, pth);
+      k_walk_step<<<nb, 128, 0, st>>>(pr, sc, chol, seed, (uint32_t)s, n_chains, plnl, out_u, out_lnl, out_nacc, pu,
+                                      pth, c->d_work, nwork);
       c->launches++;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if ((e = launch_loglike(c, pth, n_chains, plnl, st)) != cudaSuccess) break;
-    {
-      ProfScope ps(c, GWL_KERNEL_WALK, st);
-      k_walk_accept<<<nb, 128, 0, st>>>(sc, D, n_chains, pu, plnl, out_u, out_lnl, out_nacc);
-      c->launches++;
-    }
+    e = launch_loglike_cleared(c, pth, n_chains, plnl, st);
+  }
+  if (e == cudaSuccess && walk_len > 0) {  // the last step's accept/reject
+    ProfScope ps(c, GWL_KERNEL_WALK, st);
+    k_walk_accept<<<nb, 128, 0, st>>>(sc, D, n_chains, pu, plnl, out_u, out_lnl, out_nacc);
+    c->launches++;
     e = cudaGetLastError();
   }
   return e;
@@ -1113,10 +1135,14 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     const bool prof = c->profiling;
+    int64_t per_round = 0;  // kernels in one round's graph
     if (use_graph) {
       c->profiling = false;
       if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+      const int64_t l0 = c->launches;
       cudaError_t er = launch_ns_round(c, s, seed, walk_len, dlogz, pu, pth, plnl, st);
+      per_round = c->launches - l0;
+      c->launches = l0;
       e = cudaStreamEndCapture(st, &graph);
       c->profiling = prof;
       if (er != cudaSuccess) e = er;
@@ -1130,7 +1156,7 @@ static int ns_run_on(gwl_ctx* c, int64_t K, int64_t n_chains, int walk_len, uint
       const int64_t todo = (max_rounds - r) < check ? (max_rounds - r) : check;
       for (int64_t i = 0; i < todo && e == cudaSuccess; ++i) {
         e = use_graph ? cudaGraphLaunch(gexec, st) : launch_ns_round(c, s, seed, walk_len, dlogz, pu, pth, plnl, st);
-        if (e == cudaSuccess) c->launches += use_graph ? (int64_t)(4 + walk_len * 5) : 0;
+        if (e == cudaSuccess) c->launches += use_graph ? per_round : 0;
       }
       if (e != cudaSuccess) break;
       r += todo;
