@@ -103,3 +103,18 @@ def test_checkpoint_size_and_argument_errors(L):
     res = gwl.GwlNsResult()
     assert L.ns_run_resumable(None, 10, 10, 1, 0, 0.1, 1, 1.0, 0, None, None, None, C.byref(res), None, None,
                               None) == -1
+
+
+def test_binding_buffer_addresses():
+    """The binding's host-buffer addresses (taken without numpy's ctypes helper where the buffer is
+    writable) equal numpy's own for whole arrays, row views, read-only and empty arrays; a
+    non-contiguous array is refused."""
+    import numpy as np
+    from paper_1909_11873_gb300 import gwl
+    a = np.zeros((10, 11))
+    ro = np.zeros(5)
+    ro.flags.writeable = False
+    for t in (a, a[3:], a[3:4], ro, np.zeros(0), np.zeros((0, 11))):
+        assert gwl._ptr(t) == t.ctypes.data
+    with pytest.raises(ValueError):
+        gwl._ptr(a[:, 1:])
