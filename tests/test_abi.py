@@ -94,7 +94,8 @@ def test_grid_tolerance_is_1e9_of_the_spacing(L):
 
 def test_checkpoint_size_and_argument_errors(L):
     """ns_state_doubles: a header of 26 doubles, the live set (K (D + 1)) and up to max_dead dead points
-    (D + 2 each); invalid sizes give -1; ns_run_resumable refuses a null context synchronously."""
+    (D + 2 each); invalid sizes give -1; ns_run_resumable and the multi-event entry points refuse a null
+    context or batch synchronously."""
     assert L.ns_state_doubles(250, 4, 1000) == 26 + 250 * 5 + 1000 * 6
     assert L.ns_state_doubles(2, 1, 0) == 26 + 2 * 2
     assert L.ns_state_doubles(1, 4, 0) == -1
@@ -103,6 +104,9 @@ def test_checkpoint_size_and_argument_errors(L):
     res = gwl.GwlNsResult()
     assert L.ns_run_resumable(None, 10, 10, 1, 0, 0.1, 1, 1.0, 0, None, None, None, C.byref(res), None, None,
                               None) == -1
+    # the multi-event counterparts: a null batch is refused synchronously
+    assert L.gwl_multi_ns_state_doubles(None, 250) == -1
+    assert L.gwl_multi_ns_run_resumable(None, 10, 10, 1, 0, 0.1, 1, 1.0, C.byref(res), None, None, None) == -1
 
 
 def test_binding_buffer_addresses():
