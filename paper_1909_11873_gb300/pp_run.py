@@ -3,12 +3,12 @@
   python -m paper_1909_11873_gb300.pp_run [--n 100] [--K 250] [--walk 20] [--precision mixed]
 
 N injections are drawn from a fixed 4-D prior (chirp mass, mass ratio, coalescence
-time, phase) on config 2's three-detector network with coloured noise
+time, phase) on the three-detector 8 s BBH network with coloured noise
 (inputs.make_pp_event); for each, ns_run samples the same prior and the
 credible level of the true value, C_k = sum_i w_i [theta_i,k < theta_true,k] /
 sum_i w_i over the weighted dead points (and the final live set), is recorded.
 If the sampler's posteriors are calibrated, each parameter's C_k is uniform on
-[0, 1]: the driver reports the Kolmogorov-Smirnov statistic and p-value per
+[0, 1]: this script reports the Kolmogorov-Smirnov statistic and p-value per
 parameter and Fisher's combination.  Injections are made with the library's
 own template.
 """
