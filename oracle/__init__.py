@@ -10,11 +10,11 @@ random walk, and the gradient-informed (Galilean) constrained walk.
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never loads it.
 
-Parity status: the TaylorF2 2.5-3.5PN spin-orbit phase coefficients are
-"parity unpinned" against any external waveform code (no waveform library is
-available); the non-spinning phase through 3.5PN is pinned by its published
-coefficients, and everything else by closed forms, invariants, brute force or
-library routines in ``tests/test_oracle_pins.py``.
+Parity status: the non-spinning phase through 3.5PN is pinned by its published
+coefficients; the spin-orbit phase terms (1.5, 2.5, 3 and 3.5PN) by a
+stationary-phase derivation from the published spin-orbit binding energy and
+flux; everything else by closed forms, invariants, brute force or library
+routines in ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
 

@@ -30,10 +30,9 @@
 // Parity status of the waveform: the Newtonian amplitude and phase, the
 // antenna patterns, the inner product and the time/phase structure are pinned
 // by closed forms and invariants in the tests; the non-spinning phase through
-// 3.5PN and the 1.5PN spin-orbit and 2PN spin-spin terms by their published
-// coefficients.  The 2.5-3.5PN spin-orbit coefficients are "parity unpinned"
-// against any external waveform code (no waveform library is available);
-// they are pinned only by limits (chi -> 0, q = 1 symmetry).
+// 3.5PN and the 2PN spin-spin term by their published coefficients; the
+// spin-orbit terms at 1.5, 2.5, 3 and 3.5PN by a stationary-phase derivation
+// from the published spin-orbit binding energy and energy flux.
 //
 // Sums run in bin order with Neumaier compensation.  Built with -O3 and
 // without -ffast-math.

@@ -237,6 +237,90 @@ def test_spin_orbit_and_spin_spin_terms_textbook_form():
     assert d4 / v ** 4 == pytest.approx(ss, rel=1e-5)
 
 
+def _taylorf2_from_energy_and_flux(q, chi1, chi2):
+    """phi_k of Psi * 128 eta v^5 / 3 = sum phi_k v^k (k != 5) and the v^5 ln v coefficient L5,
+    derived from the binding energy and the energy flux by the stationary-phase approximation.
+
+    E(v) = -(eta v^2 / 2) e(v) and F(v) = (32/5) eta^2 v^10 f(v) with v = (pi M f)^(1/3), M = 1.  The
+    orbit obeys dt/dv = -E'(v) / F(v) and d(phi_orb)/dt = v^3; the stationary point of the dominant
+    harmonic gives Psi(f) = 2 pi f t(v_f) - 2 phi_orb(v_f) - pi/4, i.e. up to terms linear in f and
+    constants Psi = 2 int_{v_f} (v_f^3 - v^3) E'(v)/F(v) dv.  Writing E'/F = -(5 / (32 eta)) v^-9 *
+    sum a_k v^k, the lower limit of the v^k term gives (15 / (16 eta)) a_k v_f^(k-5) / ((k-8)(k-5)),
+    so phi_k = 40 a_k / ((k-8)(k-5)); at k = 5 it gives -(5 / (16 eta)) a_5 ln v_f, so L5 = -(40/3) a_5.
+
+    Energy and flux: the non-spinning terms through 2PN and the 1.5PN tail of the flux, and the
+    spin-orbit terms -- energy at 1.5, 2.5 and 3.5PN, flux at 1.5, 2.5, 3 (tail) and 3.5PN --
+    in the spin variables S = m1^2 chi1 + m2^2 chi2 and Sigma = M (m2 chi2 - m1 chi1) (masses in
+    units of M), as collected in Blanchet's review (Living Rev. Relativ. 17, 2, 2014), from
+    Blanchet, Buonanno & Faye (2006, 2011) and Bohe, Marsat, Faye & Blanchet (2013)."""
+    x1, x2 = 1.0 / (1.0 + q), q / (1.0 + q)
+    eta, d = x1 * x2, x1 - x2
+    S, Sg = x1 * x1 * chi1 + x2 * x2 * chi2, x2 * chi2 - x1 * chi1
+    pi = math.pi
+    e = np.zeros(8)
+    e[0] = 1.0
+    e[2] = -0.75 - eta / 12
+    e[3] = 14 / 3 * S + 2 * d * Sg
+    e[4] = -27 / 8 + 19 / 8 * eta - eta ** 2 / 24
+    e[5] = (11 - 61 / 9 * eta) * S + d * (3 - 10 / 3 * eta) * Sg
+    e[7] = (135 / 4 - 367 / 4 * eta + 29 / 12 * eta ** 2) * S + d * (27 / 4 - 39 * eta + 5 / 4 * eta ** 2) * Sg
+    f = np.zeros(8)
+    f[0] = 1.0
+    f[2] = -1247 / 336 - 35 / 12 * eta
+    f[3] = 4 * pi - 4 * S - 5 / 4 * d * Sg
+    f[4] = -44711 / 9072 + 9271 / 504 * eta + 65 / 18 * eta ** 2
+    f[5] = (-9 / 2 + 272 / 9 * eta) * S + (-13 / 16 + 43 / 4 * eta) * d * Sg
+    f[6] = -16 * pi * S - 31 / 6 * pi * d * Sg
+    f[7] = ((476645 / 6804 + 6172 / 189 * eta - 2810 / 27 * eta ** 2) * S
+            + (9535 / 336 + 1849 / 126 * eta - 1501 / 36 * eta ** 2) * d * Sg)
+    num = np.array([(k + 2) / 2 * e[k] for k in range(8)])  # E'(v) / (-eta v)
+    a = np.zeros(8)
+    for k in range(8):                                       # series quotient num / f
+        a[k] = num[k] - sum(f[j] * a[k - j] for j in range(1, k + 1))
+    phi = {k: 40 * a[k] / ((k - 8) * (k - 5)) for k in (2, 3, 4, 6, 7)}
+    return phi, -40 / 3 * a[5]
+
+
+def test_energy_flux_derivation_reproduces_published_nonspinning_terms():
+    """The stationary-phase derivation from the energy and the flux, at zero spin, gives the
+    published 1PN, 1.5PN and 2PN phase coefficients: this checks the derivation that the next
+    test uses on the spin-orbit terms."""
+    for q in (1.0, 0.6, 0.2):
+        eta = q / (1 + q) ** 2
+        phi, l5 = _taylorf2_from_energy_and_flux(q, 0.0, 0.0)
+        assert phi[2] == pytest.approx(3715 / 756 + 55 * eta / 9, rel=1e-13)
+        assert phi[3] == pytest.approx(-16 * math.pi, rel=1e-13)
+        assert phi[4] == pytest.approx(15293365 / 508032 + 27145 * eta / 504 + 3085 * eta ** 2 / 72, rel=1e-13)
+
+
+@pytest.mark.parametrize("q", [1.0, 0.7, 0.25])
+def test_spin_orbit_phase_terms_follow_from_energy_and_flux(q):
+    """Every spin-orbit term of the oracle's phase -- 1.5PN, the 2.5PN v^5 ln v term, 3PN and
+    3.5PN -- equals the one derived from the published spin-orbit energy and flux
+    (`_taylorf2_from_energy_and_flux`), for each spin separately.  The part linear in one spin
+    is taken by a central difference, which removes the spin-spin term, and is exactly a
+    combination of v^3, v^5, v^5 ln v, v^6 and v^7 in Psi * 128 eta v^5 / 3; a least-squares
+    fit recovers each coefficient.  The constant v^5 coefficient is a constant phase (absorbed
+    in the coalescence phase) and is not compared."""
+    mc, h = 1.2, 0.5
+    eta = q / (1 + q) ** 2
+    M = mc * eta ** -0.6 * TSUN
+    v = np.linspace(0.05, 0.4, 40)
+    f = v ** 3 / (math.pi * M)
+    A = np.stack([v ** 3, v ** 5, v ** 5 * np.log(v), v ** 6, v ** 7], axis=1)
+    scale = np.abs(A).max(axis=0)
+    for spin in ((h, 0.0), (0.0, h)):
+        neg = (-spin[0], -spin[1])
+        g = np.array([oracle.pn_psi(mc, q, *spin, fi) - oracle.pn_psi(mc, q, *neg, fi) for fi in f])
+        g *= 128 * eta * v ** 5 / 3 / (2 * h)
+        coef = np.linalg.lstsq(A / scale, g, rcond=None)[0] / scale
+        pp, lp = _taylorf2_from_energy_and_flux(q, *spin)
+        pm, lm = _taylorf2_from_energy_and_flux(q, *neg)
+        lin = {k: (pp[k] - pm[k]) / (2 * h) for k in (3, 6, 7)}
+        derived = [lin[3], (lp - lm) / (2 * h), lin[6], lin[7]]
+        assert [coef[0], coef[2], coef[3], coef[4]] == pytest.approx(derived, rel=1e-10)
+
+
 def test_chirp_time_newtonian():
     """t(f) = (1/2pi) dPsi/df -> -(5/256) Mc (pi Mc f)^(-8/3) at low v (textbook chirp time)."""
     mc, q = 30.0, 0.9
