@@ -18,6 +18,8 @@
 // the combination kernel takes the others.  The ISCO cut index is held at its
 // value: the gradient of the piecewise-smooth lnL.
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "gwl_bins.cuh"
 #include "gwl_ff.cuh"
@@ -828,16 +830,21 @@ int* calgrad_counters(const gwl_ctx* c, int64_t B);
 // Directions per CTA of the role-form tangent prologue, and how many of its
 // CTAs an SM holds (from the kernel's registers and shared memory).
 constexpr int kRoleTangents = 3;
-static int role_ctas_per_sm() {
-  static const int n = [] {
-    int k = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_prologue_grad_roles<kRoleTangents>, 128, 0) != cudaSuccess) {
-      cudaGetLastError();
-      k = 0;
-    }
-    return k;
-  }();
-  return n;
+// resident CTAs of the role form per SM on the context's device (asked once per
+// device; the current device is the context's while a call runs)
+static int role_ctas_per_sm(int device) {
+  static std::mutex mu;
+  static std::map<int, int> per_device;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = per_device.find(device);
+  if (it != per_device.end()) return it->second;
+  int k = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_prologue_grad_roles<kRoleTangents>, 128, 0) != cudaSuccess) {
+    cudaGetLastError();
+    k = 0;
+  }
+  per_device[device] = k;
+  return k;
 }
 
 template <int NDET, bool MIXED, bool CAL>
@@ -855,7 +862,7 @@ static cudaError_t run_grad(gwl_ctx* c, const double* theta, int64_t B, double* 
     // with one direction per CTA and 52.2 us with one thread per row and
     // direction at B = 4096); beyond one wave, the one-thread form
     const int64_t role_ctas = (B + 31) / 32 * ((c->opt.n_dim + kRoleTangents - 1) / kRoleTangents);
-    if (MIXED && role_ctas <= (int64_t)role_ctas_per_sm() * c->num_sms) {
+    if (MIXED && role_ctas <= (int64_t)role_ctas_per_sm(c->device) * c->num_sms) {
       const dim3 grid((unsigned)((B + 31) / 32), (unsigned)((c->opt.n_dim + kRoleTangents - 1) / kRoleTangents));
       k_prologue_grad_roles<kRoleTangents><<<grid, 128, 0, st>>>(c->seg, theta, B, c->d_pm, c->d_pc,
                                                                  reinterpret_cast<PropGrad<float>*>(c->d_pgrad),
