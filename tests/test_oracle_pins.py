@@ -526,19 +526,38 @@ def gauss_box_lnz(D, mu, sigma):
                for m in mu)
 
 
+def gauss_box_information(mu, sigma):
+    """H = int P ln(L / Z) for the normalised Gaussian L in the unit cube: per coordinate, with the
+    truncated normal's standardised bounds a, b and mass Z_i, E[z^2] = 1 - (b phi(b) - a phi(a)) / Z_i
+    and H_i = -ln(2 pi sigma^2) / 2 - E[z^2] / 2 - ln Z_i."""
+    h = 0.0
+    for m in mu:
+        a, b = -m / sigma, (1 - m) / sigma
+        z = stats.norm.cdf(b) - stats.norm.cdf(a)
+        ez2 = 1 - (b * stats.norm.pdf(b) - a * stats.norm.pdf(a)) / z
+        h += -0.5 * math.log(2 * math.pi * sigma ** 2) - 0.5 * ez2 - math.log(z)
+    return h
+
+
 @pytest.mark.slow
 def test_ns_gaussian_in_box_evidence():
-    """Oracle NS recovers lnZ of a Gaussian in the unit cube (closed form with erf) over 8 seeds."""
+    """Oracle NS recovers lnZ of a Gaussian in the unit cube (closed form with erf) over 8 seeds,
+    and its information H (which sets lnZ_err = sqrt(H / K)) the truncated normal's closed form."""
     D, sigma = 3, 0.08
     mu = np.array([0.1, 0.55, 0.9])
     truth = gauss_box_lnz(D, mu, sigma)
-    errs, sig = [], []
+    h_true = gauss_box_information(mu, sigma)
+    errs, sig, hs = [], [], []
     for s in range(8):
         r = oracle.ns_run_gauss(D, mu, sigma, K=200, n_chains=100, walk_len=25, seed=1000 + s, dlogz=0.05)
         errs.append(r["lnZ"] - truth)
         sig.append(r["lnZ_err"])
+        hs.append(r["H"])
         assert abs(r["lnZ"] - truth) < 4 * r["lnZ_err"]
+        assert r["lnZ_err"] == pytest.approx(math.sqrt(r["H"] / 200), rel=1e-12)
+        assert abs(r["H"] - h_true) < 0.6      # the runs' H scatter by ~0.13 (K = 200)
     assert abs(np.mean(errs)) < 3 * np.mean(sig) / math.sqrt(len(errs)) + 0.02
+    assert abs(np.mean(hs) - h_true) < 0.15
 
 
 @pytest.mark.slow
