@@ -75,7 +75,7 @@ def _L():
                                                + [P, P, i64, i64, d, u64, u64, i64, i32, d, P, P, P, P, P, i32])
             _lib.oracle_ns_run.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
                                            + [i64, i64, i32, u64, d, i64, d, P, P, P, P, i64, i32])
-            _lib.oracle_ns_run_gauss.argtypes = [i32, P, d, i64, i64, i32, u64, d, i64, d, P, i32]
+            _lib.oracle_ns_run_gauss.argtypes = [i32, P, d, i64, i64, i32, u64, d, i64, d, P, P, P, P, i64, i32]
             _lib.oracle_gmc_replace.argtypes = ([P, i64, P, P, P, i32, d, d, i32, i32, P, P, P, P, P, P]
                                                 + [i32, P, P]
                                                 + [P, P, i64, i64, d, u64, u64, i64, i32, d, d, P, P, P, P, P, i32])
@@ -394,10 +394,19 @@ def ns_run_cal(ev, smp, cal, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=
 
 
 def ns_run_gauss(D, mu, sigma, K, n_chains, walk_len, seed, dlogz=0.1, max_rounds=100000, scale0=1.0,
-                 n_threads: int | None = None):
-    """Nested sampling of an isotropic Gaussian likelihood in the unit cube."""
+                 max_dead=0, n_threads: int | None = None):
+    """Nested sampling of an isotropic Gaussian likelihood in the unit cube (with max_dead > 0, also
+    the first max_dead dead points, final live points included: dead_lnl, dead_logwt, dead_u)."""
     res = np.zeros(9)
     m = _f64(mu)
+    dl = np.zeros(max(max_dead, 1))
+    dw = np.zeros(max(max_dead, 1))
+    du = np.zeros((max(max_dead, 1), D))
     _L().oracle_ns_run_gauss(int(D), _p(m), float(sigma), int(K), int(n_chains), int(walk_len), int(seed),
-                             float(dlogz), int(max_rounds), float(scale0), _p(res), n_threads or default_threads())
-    return dict(zip(NS_KEYS, res.tolist()))
+                             float(dlogz), int(max_rounds), float(scale0), _p(res), _p(dl), _p(dw), _p(du),
+                             int(max_dead), n_threads or default_threads())
+    out = dict(zip(NS_KEYS, res.tolist()))
+    if max_dead:
+        n = min(int(res[3]), max_dead)
+        out.update(dead_lnl=dl[:n], dead_logwt=dw[:n], dead_u=du[:n])
+    return out

@@ -1212,11 +1212,12 @@ void oracle_inv_normal_cdf(int64_t n, const double* u, double* out) {
 // Nested sampling of the analytic Gaussian-in-a-box likelihood (test pin).
 int oracle_ns_run_gauss(int D, const double* mu, double sigma, int64_t K, int64_t n_chains,
                         int walk_len, uint64_t seed, double dlogz, int64_t max_rounds,
-                        double scale0, double* res, int n_threads) {
+                        double scale0, double* res, double* dead_lnl, double* dead_logwt,
+                        double* dead_u, int64_t max_dead, int n_threads) {
   if (K < 2 || D < 1) return -1;
   std::vector<int> per(D, 0);
   ns_run_impl(gauss_like(D, mu, sigma), D, per.data(), K, n_chains, walk_len, seed, dlogz,
-              max_rounds, scale0, res, nullptr, nullptr, nullptr, 0, n_threads);
+              max_rounds, scale0, res, dead_lnl, dead_logwt, dead_u, max_dead, n_threads);
   return 0;
 }
 

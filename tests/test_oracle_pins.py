@@ -561,6 +561,41 @@ def test_ns_gaussian_in_box_evidence():
 
 
 @pytest.mark.slow
+def test_ns_gaussian_in_box_posterior_moments():
+    """The dead points weighted by L_i dX_i / Z (final live points included, Algorithm 1) reproduce the
+    truncated normal's mean mu + sigma (phi(a) - phi(b)) / Z_i and standard deviation
+    sigma sqrt(1 + (a phi(a) - b phi(b)) / Z_i - ((phi(a) - phi(b)) / Z_i)^2) per coordinate: per run
+    within 5 standard errors of the weighted sample (effective size from the weights), and over 8
+    runs within 4."""
+    D, sigma = 3, 0.08
+    mu = np.array([0.1, 0.55, 0.9])
+    a, b = -mu / sigma, (1 - mu) / sigma
+    z = stats.norm.cdf(b) - stats.norm.cdf(a)
+    pa, pb = stats.norm.pdf(a), stats.norm.pdf(b)
+    mean_t = mu + sigma * (pa - pb) / z
+    sd_t = sigma * np.sqrt(1 + (a * pa - b * pb) / z - ((pa - pb) / z) ** 2)
+    means, sds, ess_all = [], [], []
+    for s in range(8):
+        r = oracle.ns_run_gauss(D, mu, sigma, K=200, n_chains=100, walk_len=25, seed=1000 + s, dlogz=0.05,
+                                max_dead=100000)
+        assert len(r["dead_lnl"]) == r["n_dead"]
+        w = np.exp(r["dead_lnl"] + r["dead_logwt"] - r["lnZ"])
+        assert w.sum() == pytest.approx(1.0, rel=1e-12)
+        u = r["dead_u"]
+        m = (w[:, None] * u).sum(0)
+        sd = np.sqrt((w[:, None] * (u - m) ** 2).sum(0))
+        ess = 1.0 / (w ** 2).sum()
+        assert np.all(np.abs(m - mean_t) < 5 * sd_t / math.sqrt(ess))
+        assert np.all(np.abs(sd / sd_t - 1) < 5 / math.sqrt(2 * ess))
+        means.append(m)
+        sds.append(sd)
+        ess_all.append(ess)
+    n_eff = len(means) * np.mean(ess_all)
+    assert np.all(np.abs(np.mean(means, 0) - mean_t) < 4 * sd_t / math.sqrt(n_eff))
+    assert np.all(np.abs(np.mean(sds, 0) / sd_t - 1) < 4 / math.sqrt(2 * n_eff))
+
+
+@pytest.mark.slow
 def test_ns_consumption_follows_eq5():
     """Mean candidates consumed per round ~ K ln(1 + B/K) (Eq. 5) for several batch sizes."""
     D, sigma = 2, 0.1
