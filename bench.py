@@ -99,7 +99,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--legs", default=",".join(LEGS), help="extra measurements to run (comma list; '' for none)")
-    ap.add_argument("--profile-only", default="", choices=["", "lnl", "grad", "cal", "calgrad", "fp64ph", "fp64"],
+    ap.add_argument("--profile-only", default="",
+                    choices=["", "lnl", "grad", "cal", "calgrad", "fp64ph", "fp64", "ns"],
                     help="run one workload --warmup + --steps times without timing and exit (for profiler captures): "
                          "lnl = the headline likelihood, grad = the 4096-proposal gradient, cal = the calibrated "
                          "likelihood, fp64ph = the FP64-phase mixed arm")
@@ -913,6 +914,8 @@ def run_profile_only(args):
     if not os.path.exists(gwl.LIB_PATH):
         build.build()
     torch.cuda.set_device(0)
+    if args.profile_only == "ns":
+        return run_profile_ns(args)
     ev = device_event(args.profile_config)
     prec = {"fp64ph": gwl.GWL_MIXED_F64PHASE, "fp64": gwl.GWL_FP64}.get(args.profile_only, gwl.GWL_MIXED)
     ctx = gwl.Context.from_event(ev, prec)
@@ -940,6 +943,24 @@ def run_profile_only(args):
     ctx.gwl_sync()
     print(json.dumps({"profile_only": args.profile_only, "calls": args.warmup + args.steps, "B": B,
                       "tuning": ctx.gwl_get_tuning(), "lnl0": float(out[0])}))
+    ctx.close()
+
+
+def run_profile_ns(args):
+    """Device nested sampling on the 1-detector 4 s event (K = 250, 250 chains, walk 20): a warm-up run
+    of --warmup rounds, then one of --steps rounds, timed by the host clock (per round and per walk
+    step) -- the launch sequence of the sampler's rounds for a profiler's launch list."""
+    from paper_1909_11873_gb300 import gwl
+
+    ctx = gwl.Context.from_event(device_event("c1"), gwl.GWL_MIXED)
+    ctx.ns_run(NS_K, NS_CHAINS, NS_WALK, seed=1, dlogz=0.0, max_rounds=max(args.warmup, 1))
+    t0 = time.perf_counter()
+    r = ctx.ns_run(NS_K, NS_CHAINS, NS_WALK, seed=2, dlogz=0.0, max_rounds=args.steps)
+    wall = time.perf_counter() - t0
+    n = int(r["rounds"])
+    print(json.dumps({"profile_only": "ns", "rounds": n, "wall_ms": wall * 1e3,
+                      "ms_per_round": wall * 1e3 / max(n, 1), "us_per_step": wall * 1e6 / max(n * NS_WALK, 1),
+                      "launches": ctx.launch_count()}))
     ctx.close()
 
 

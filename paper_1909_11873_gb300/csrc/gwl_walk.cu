@@ -526,38 +526,55 @@ __device__ void ns_prep_body(const NsDev& s) {
   }
 }
 
+// Order key of a log-likelihood: a signed 64-bit integer whose order is the
+// values' order (IEEE bits; negative values with all bits but the sign
+// flipped), so that the replacement loop compares on the integer pipe instead
+// of the narrow FP64 one.  -0 takes +0's key, so the two tie as they compare
+// equal; log-likelihoods are never NaN (rows the likelihood cannot evaluate
+// give -inf), and a NaN takes -inf's key.
+__device__ __forceinline__ long long lnl_key(double x) {
+  if (x != x) x = -INFINITY;
+  long long i = __double_as_longlong(x);
+  if (i == (long long)0x8000000000000000ull) i = 0;
+  return i < 0 ? i ^ 0x7fffffffffffffffll : i;
+}
+__device__ __forceinline__ double key_lnl(long long k) {
+  return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffll : k);
+}
+
 // Consumption of the round's candidates.  The sequential replacement loop
-// (warp 0) touches only shared memory: the live lnL, the candidates' lnL and,
-// per live slot, where its point currently comes from (an original live point
-// or a candidate).  The unit-cube coordinates of dead points and of the
-// replaced slots are then copied by the whole CTA.
+// (warp 0) touches only shared memory: the order keys of the live lnL and of
+// the candidates' lnL and, per live slot, where its point currently comes from
+// (an original live point or a candidate); it records each dead point's lnL
+// and slot.  The dead points' prior weights, the unit-cube coordinates of
+// dead points and of the replaced slots are then written by the whole CTA.
 __device__ void ns_consume_body(const NsDev& s) {
   if (s.stats[NS_DONE] > 0.5) return;
   extern __shared__ __align__(16) unsigned char smc[];
-  double* ll = reinterpret_cast<double*>(smc);     // [K]
-  double* cl = ll + s.K;                           // [n_chains]
+  long long* ll = reinterpret_cast<long long*>(smc);  // [K]   keys of the live lnL
+  long long* cl = ll + s.K;                           // [n_chains] keys of the candidates' lnL
   int* src = reinterpret_cast<int*>(cl + s.n_chains);  // [K]   -1: original, else candidate index
   int* rslot = src + s.K;                          // [n_chains] slot replaced at step r
   int* rsrc = rslot + s.n_chains;                  // [n_chains] source of the dead point at step r
   __shared__ int sh_nrep;
+  __shared__ double sh_lw1;
   const int t = threadIdx.x, lane = t & 31;
   const int D = s.D;
   for (int64_t k = t; k < s.K; k += blockDim.x) {
-    ll[k] = s.ll[k];
+    ll[k] = lnl_key(s.ll[k]);
     src[k] = -1;
   }
-  for (int64_t b = t; b < s.n_chains; b += blockDim.x) cl[b] = s.cl[b];
+  for (int64_t b = t; b < s.n_chains; b += blockDim.x) cl[b] = lnl_key(s.cl[b]);
   __syncthreads();
   const int64_t nd0 = (int64_t)s.stats[NS_NDEAD];
   if (t < 32) {
     int64_t ptr = 0;
     int nrep = 0;
-    const double lw1 = log1p(-::exp(-1.0 / (double)s.K));
     while (true) {
-      double bv = INFINITY;
+      long long bv = 0x7fffffffffffffffll;
       int bi = 0;
       for (int k = lane; k < s.K; k += 32) {
-        const double v = ll[k];
+        const long long v = ll[k];
         if (v < bv || (v == bv && k < bi)) {
           bv = v;
           bi = k;
@@ -565,7 +582,7 @@ __device__ void ns_consume_body(const NsDev& s) {
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double v = __shfl_xor_sync(0xffffffffu, bv, off);
+        const long long v = __shfl_xor_sync(0xffffffffu, bv, off);
         const int i = __shfl_xor_sync(0xffffffffu, bi, off);
         if (v < bv || (v == bv && i < bi)) {
           bv = v;
@@ -575,14 +592,7 @@ __device__ void ns_consume_body(const NsDev& s) {
       while (ptr < s.n_chains && !(cl[ptr] > bv)) ++ptr;
       if (ptr >= s.n_chains) break;
       if (lane == 0) {
-        const int64_t nd = nd0 + nrep + 1;
-        const double lw = -(double)(nd - 1) / (double)s.K + lw1;  // ln(X_{i-1} - X_i)
-        s.rx[nrep] = bv + lw;
-        s.rl[nrep] = bv;
-        if (nd <= s.cap) {
-          s.dl[nd - 1] = bv;
-          s.dw[nd - 1] = lw;
-        }
+        s.rl[nrep] = key_lnl(bv);
         rslot[nrep] = bi;
         rsrc[nrep] = src[bi];
         src[bi] = (int)ptr;
@@ -593,9 +603,23 @@ __device__ void ns_consume_body(const NsDev& s) {
       ++nrep;
     }
     if (lane == 0) sh_nrep = nrep;
+  } else if (t == 32) {  // beside the loop: ln(1 - e^{-1/K})
+    sh_lw1 = log1p(-::exp(-1.0 / (double)s.K));
   }
   __syncthreads();
   const int nrep = sh_nrep;
+  // the dead points' prior weights ln(X_{i-1} - X_i) and weighted values
+  const double lw1 = sh_lw1;
+  for (int r = t; r < nrep; r += blockDim.x) {
+    const int64_t nd = nd0 + r + 1;
+    const double lw = -(double)(nd - 1) / (double)s.K + lw1;
+    const double l = s.rl[r];
+    s.rx[r] = l + lw;
+    if (nd <= s.cap) {
+      s.dl[nd - 1] = l;
+      s.dw[nd - 1] = lw;
+    }
+  }
   // dead points' coordinates (before any live slot is overwritten)
   for (int64_t x = t; x < (int64_t)nrep * D; x += blockDim.x) {
     const int r = (int)(x / D), i = (int)(x % D);
@@ -613,7 +637,10 @@ __device__ void ns_consume_body(const NsDev& s) {
     const int sr = src[k];
     if (sr >= 0) s.lu[x] = s.cu[(int64_t)sr * D + i];
   }
-  for (int64_t k = t; k < s.K; k += blockDim.x) s.ll[k] = ll[k];
+  for (int64_t k = t; k < s.K; k += blockDim.x) {
+    const int sr = src[k];
+    if (sr >= 0) s.ll[k] = s.cl[sr];
+  }
   if (t == 0) {
     s.stats[NS_NDEAD] = (double)(nd0 + nrep);
     s.stats[NS_CONSUMED] += (double)nrep;
@@ -621,7 +648,7 @@ __device__ void ns_consume_body(const NsDev& s) {
 }
 
 size_t consume_smem_bytes(int64_t K, int64_t n_chains) {
-  return sizeof(double) * (size_t)(K + n_chains) + sizeof(int) * (size_t)(K + 2 * n_chains);
+  return sizeof(long long) * (size_t)(K + n_chains) + sizeof(int) * (size_t)(K + 2 * n_chains);
 }
 
 // Fold n weighted points x_i = lnL_i + ln dX_i (with lnL_i) into the running
